@@ -1,0 +1,1340 @@
+/* FP64 CPU oracle of the per-step collisional PIC update for XFEL-heated
+ * solid Al (Royle, Sentoku, Mancini, Paraschiv, Johzaki; PICLS).
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the
+ * CPU-baseline legs of the bench.  Plain, sequential per cell, written for
+ * checking by eye against the paper, not for speed.  It shares no code with
+ * the CUDA path.
+ *
+ * One step, in order (the paper leaves the order within a PIC step open;
+ * Fig. 1 gives the radiation cycle):
+ *   0. every rad_every-th step: photon march along +x (Sec. II, simplified
+ *      to ballistic transport of the pulse, attenuated by photoionization)
+ *   per cell, on the particles whose position lies in the cell:
+ *   1. canonical random order of electrons and of ions (Philox keys)
+ *   2. FP64 cell moments: densities, T_e = (2/3) E_ave (Sec. II), Zbar,
+ *      continuum lowering (Sec. V, Eqs. 4, 5), Coulomb logarithm
+ *   3. binary e-e then e-i collisions (Sec. IV, by citation: Takizuka-Abe
+ *      pairing and angle, relativistic centre-of-momentum rotation)
+ *   4. Lotz impact ionization with the cell-average probability and the
+ *      constant-factor energy payment (Sec. IV, Eq. 3)
+ *   5. EOS-clamped three-body recombination (Sec. IV)
+ *   6. rad steps: subshell photoionization (Sec. III, Eq. 2, partial
+ *      ionization) then K-vacancy decay with Auger/K-alpha branching
+ *      (Sec. III)
+ *   then over all particles:
+ *   7. relativistic Boris push, charge-conserving (Esirkepov) deposit
+ *   8. Yee field update, subcycled, periodic in y, first-order Mur in x
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ---------------- physical constants (CODATA 2018) ---------------- */
+#define PI 3.14159265358979323846
+static const double C_CM_FS = 2.99792458e-5;     /* speed of light, cm/fs */
+static const double C_NM_FS = 299.792458;        /* nm/fs */
+static const double ME_C2 = 510998.95;           /* eV */
+static const double R_E_CM = 2.8179403262e-13;   /* classical electron radius */
+static const double Q_E = 1.602176634e-19;       /* C */
+static const double EPS0 = 8.8541878128e-12;     /* F/m */
+static const double ME_KG = 9.1093837015e-31;      /* kg */
+static const double C_SI = 299792458.0;          /* m/s */
+static const double HBARC_EVNM = 197.3269804;    /* eV nm */
+static const double P_MIN = 1.0;                 /* eV, floor of lowered binding */
+
+/* Philox stream purposes (counter word 3) */
+enum { PU_PAIR_E = 1, PU_PAIR_I = 2, PU_COLL_EE = 3, PU_COLL_EI = 4,
+       PU_COLL_IE = 5, PU_ION = 6, PU_PHOTO_A = 7, PU_PHOTO_B = 8, PU_DECAY = 9 };
+/* kinds of created electrons (high id word = ((step+1) << 2) | kind) */
+enum { K_IMPACT = 1, K_PHOTO = 2, K_AUGER = 3 };
+
+static const int SUB_CAP[ORC_NS] = {2, 2, 6, 2, 6};
+
+/* ---------------- Philox4x32-10 (Salmon et al., SC'11) ---------------- */
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        c0 = hi1 ^ c1 ^ k0;
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ k1;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* uniform in the open interval (0,1): top 24 bits, centred */
+double orc_u01(uint32_t x) { return ((double)(x >> 8) + 0.5) * (1.0 / 16777216.0); }
+
+static void draw4(uint64_t seed, uint64_t id, uint32_t step, uint32_t purpose, double r[4])
+{
+    uint32_t ctr[4] = {(uint32_t)id, (uint32_t)(id >> 32), step, purpose};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t o[4];
+    orc_philox(ctr, key, o);
+    for (int k = 0; k < 4; ++k) r[k] = orc_u01(o[k]);
+}
+
+static uint64_t key64(uint64_t seed, uint64_t id, uint32_t step, uint32_t purpose)
+{
+    uint32_t ctr[4] = {(uint32_t)id, (uint32_t)(id >> 32), step, purpose};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t o[4];
+    orc_philox(ctr, key, o);
+    return ((uint64_t)o[0] << 32) | o[1];
+}
+
+/* ---------------- atomic structure helpers ---------------- */
+/* Lowest-energy filling of nb bound electrons with nk extra K vacancies:
+ * K holds min(nb,2)-nk, the rest fill 2s 2p 3s 3p in order (Sec. III: N_b
+ * from the lowest-energy configuration; the K-vacancy count is the only
+ * other state an ion carries). Returns 0 for an impossible state. */
+int orc_occ(int nb, int nk, int occ[ORC_NS])
+{
+    int k = (nb < 2 ? nb : 2) - nk;
+    if (nb < 0 || nk < 0 || k < 0) return 0;
+    occ[0] = k;
+    int rest = nb - k;
+    for (int s = 1; s < ORC_NS; ++s) {
+        int t = rest < SUB_CAP[s] ? rest : SUB_CAP[s];
+        occ[s] = t;
+        rest -= t;
+    }
+    return rest == 0;
+}
+
+static int outermost(int nb, int nk)
+{
+    int occ[ORC_NS];
+    if (!orc_occ(nb, nk, occ)) return -1;
+    for (int s = ORC_NS - 1; s >= 0; --s)
+        if (occ[s] > 0) return s;
+    return -1;
+}
+
+/* remove one electron of subshell s from (Z, nK): Z+1, K-vacancy count
+ * recomputed so the remaining K occupancy is kept */
+static void remove_electron(int *Z, int *nK, int s)
+{
+    int nb = 13 - *Z, occ[ORC_NS];
+    orc_occ(nb, *nK, occ);
+    int kocc = occ[0] - (s == 0 ? 1 : 0);
+    int nb2 = nb - 1;
+    *Z += 1;
+    *nK = (nb2 < 2 ? nb2 : 2) - kocc;
+}
+
+/* IPD-lowered binding of subshell s in charge state z */
+static double lowered(const orc_tables *t, int z, int s, double dE)
+{
+    double p = t->E_bind[z][s] - dE;
+    return p > P_MIN ? p : P_MIN;
+}
+
+/* energy to remove the outermost electron of (Z, nK) */
+static double ion_energy(const orc_tables *t, int Z, int nK, const double *dE)
+{
+    int s = outermost(13 - Z, nK);
+    if (s < 0) return 0.0;
+    return lowered(t, Z, s, dE[Z]);
+}
+
+/* ---------------- continuum lowering (Sec. V) ---------------- */
+/* Eq. 4 (Ecker-Kroll, n > n_crit branch, C = 1) and Eq. 5 (Stewart-Pyatt,
+ * T_i = T_e, z* = Zbar).  Densities in cm^-3, T in eV, result in eV. */
+double orc_ipd(int model, int z, double n_e, double n_i, double T_e, double zbar)
+{
+    double e_4pe0 = Q_E / (4.0 * PI * EPS0);   /* V m */
+    if (model == 1) {
+        double n = (n_e + n_i) * 1e6;
+        if (n <= 0.0) return 0.0;
+        double r = cbrt(3.0 / (4.0 * PI * n));
+        return (z + 1) * e_4pe0 / r;
+    }
+    if (model == 2) {
+        if (T_e <= 0.0 || n_e <= 0.0) return 0.0;
+        double lam = sqrt(EPS0 * T_e / (Q_E * n_e * 1e6 * (zbar + 1.0)));
+        double K = (z + 1) * e_4pe0 / (lam * T_e);
+        double zs = zbar;
+        return T_e / (2.0 * (zs + 1.0)) * (pow(3.0 * (zs + 1.0) * K + 1.0, 2.0 / 3.0) - 1.0);
+    }
+    return 0.0;
+}
+
+/* ---------------- Lotz cross section (Eq. 3) ---------------- */
+/* Charge state z in its lowest-energy configuration, every subshell binding
+ * lowered by dE; a subshell adds nothing below its binding.  cm^2. */
+double orc_lotz(const orc_tables *t, int z, double dE, double E)
+{
+    int occ[ORC_NS];
+    if (z >= 13 || !orc_occ(13 - z, 0, occ)) return 0.0;
+    double sig = 0.0;
+    for (int s = 0; s < ORC_NS; ++s) {
+        if (!occ[s]) continue;
+        double P = lowered(t, z, s, dE);
+        if (E <= P) continue;
+        double x = E / P;
+        sig += t->lotz_a[s] * occ[s] * log(x) / (E * P)
+               * (1.0 - t->lotz_b[s] * exp(-t->lotz_c[s] * (x - 1.0)));
+    }
+    return sig;
+}
+
+/* Coulomb logarithm stand-in (the paper defers to its refs): ln(lambda_D /
+ * b_min), b_min the larger of the classical distance of closest approach and
+ * the de Broglie length at 3T, floored at 2. */
+double orc_coulomb_log(double n_e, double T_e, double zbar)
+{
+    if (n_e <= 0.0 || T_e <= 0.0) return 2.0;
+    double lam = sqrt(EPS0 * T_e / (Q_E * n_e * 1e6)) * 1e9;   /* nm */
+    double zz = zbar > 1.0 ? zbar : 1.0;
+    double bcl = zz * (Q_E / (4.0 * PI * EPS0)) * 1e9 / (3.0 * T_e); /* nm */
+    double bqm = HBARC_EVNM / (2.0 * sqrt(3.0 * T_e * ME_C2));
+    double b = bcl > bqm ? bcl : bqm;
+    double L = log(lam / b);
+    return L > 2.0 ? L : 2.0;
+}
+
+/* EOS table, bilinear on the given (n, T) grids, clamped at the ends */
+static double interp1(const double *g, int n, double x, int *i0)
+{
+    if (n == 1 || x <= g[0]) { *i0 = 0; return 0.0; }
+    if (x >= g[n - 1]) { *i0 = n - 2; return 1.0; }
+    int lo = 0, hi = n - 1;
+    while (hi - lo > 1) {
+        int m = (lo + hi) / 2;
+        if (g[m] <= x) lo = m; else hi = m;
+    }
+    *i0 = lo;
+    return (x - g[lo]) / (g[lo + 1] - g[lo]);
+}
+
+double orc_eos(const orc_tables *t, double n_i, double T_e)
+{
+    int a, b;
+    double fa = interp1(t->eos_n, t->n_n, n_i, &a);
+    double fb = interp1(t->eos_T, t->n_T, T_e, &b);
+    int a1 = t->n_n > 1 ? a + 1 : a, b1 = t->n_T > 1 ? b + 1 : b;
+    const double *Z = t->eos_Z;
+    double z00 = Z[a * t->n_T + b], z01 = Z[a * t->n_T + b1];
+    double z10 = Z[a1 * t->n_T + b], z11 = Z[a1 * t->n_T + b1];
+    return (1 - fa) * ((1 - fb) * z00 + fb * z01) + fa * ((1 - fb) * z10 + fb * z11);
+}
+
+/* ---------------- kinematics ---------------- */
+static double gam(const double u[3]) { return sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]); }
+/* kinetic energy m c^2 (gamma - 1), written as u^2/(gamma+1) */
+static double kin(const double u[3], double m)
+{
+    double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    return m * ME_C2 * u2 / (sqrt(1.0 + u2) + 1.0);
+}
+
+/* Scale the kinetic energy of momentum u by f (direction kept). */
+static void scale_ke(double u[3], double f)
+{
+    double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    if (u2 == 0.0) return;
+    double g1 = u2 / (sqrt(1.0 + u2) + 1.0);            /* gamma - 1 */
+    double s = sqrt(f * (2.0 + f * g1) / (2.0 + g1));    /* |u'|/|u| */
+    u[0] *= s; u[1] *= s; u[2] *= s;
+}
+
+/* One binary Coulomb collision (Takizuka-Abe angle, relativistic
+ * centre-of-momentum rotation, weighted acceptance).  Momenta u in units of
+ * m c of each particle, masses in m_e, charges in e, n_l in cm^-3, dtc in
+ * fs; r[0..3] uniforms.  Returns 1 if a rotation was computed. */
+int orc_collide(double ua[3], double ub[3], double ma, double mb, double qa,
+                double qb, double wa, double wb, double n_l, double lnL,
+                double dtc, const double r[4])
+{
+    if (qa == 0.0 || qb == 0.0) return 0;
+    double ga = gam(ua), gb = gam(ub);
+    double dv[3] = {ua[0] / ga - ub[0] / gb, ua[1] / ga - ub[1] / gb, ua[2] / ga - ub[2] / gb};
+    double vrel = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+    if (vrel < 1e-10) return 0;
+    double mu = ma * mb / (ma + mb);
+    double var = 2.0 * PI * (qa * qb) * (qa * qb) * R_E_CM * R_E_CM * C_CM_FS * n_l * lnL * dtc
+                 / (mu * mu * vrel * vrel * vrel);
+    double delta = sqrt(var) * sqrt(-2.0 * log(r[0])) * cos(2.0 * PI * r[1]);
+    double phi = 2.0 * PI * r[2];
+
+    double pa[3], pb[3], P[3], bc[3];
+    for (int k = 0; k < 3; ++k) { pa[k] = ma * ua[k]; pb[k] = mb * ub[k]; P[k] = pa[k] + pb[k]; }
+    double Ea = ma * ga, Eb = mb * gb, E = Ea + Eb;
+    for (int k = 0; k < 3; ++k) bc[k] = P[k] / E;
+    double bc2 = bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2];
+    double gc = 1.0 / sqrt(1.0 - bc2);
+    double h = gc * gc / (gc + 1.0);                      /* (gc-1)/bc^2 */
+    double bp = bc[0] * pa[0] + bc[1] * pa[1] + bc[2] * pa[2];
+    double ps[3];
+    for (int k = 0; k < 3; ++k) ps[k] = pa[k] + (h * bp - gc * Ea) * bc[k];
+    double p = sqrt(ps[0] * ps[0] + ps[1] * ps[1] + ps[2] * ps[2]);
+    if (p == 0.0) return 0;
+    double n[3] = {ps[0] / p, ps[1] / p, ps[2] / p};
+    double st = 2.0 * delta / (1.0 + delta * delta);
+    double ct = (1.0 - delta * delta) / (1.0 + delta * delta);
+    double e1[3], e2[3];
+    double np = sqrt(n[0] * n[0] + n[1] * n[1]);
+    if (np > 0.0) {
+        e1[0] = n[0] * n[2] / np; e1[1] = n[1] * n[2] / np; e1[2] = -np;
+        e2[0] = -n[1] / np; e2[1] = n[0] / np; e2[2] = 0.0;
+    } else {
+        e1[0] = 1.0; e1[1] = 0.0; e1[2] = 0.0;
+        e2[0] = 0.0; e2[1] = 1.0; e2[2] = 0.0;
+    }
+    double cp = cos(phi), sp = sin(phi);
+    double qa_s[3];
+    for (int k = 0; k < 3; ++k)
+        qa_s[k] = p * (ct * n[k] + st * cp * e1[k] + st * sp * e2[k]);
+    double Eas = sqrt(ma * ma + p * p), Ebs = sqrt(mb * mb + p * p);
+    double bq = bc[0] * qa_s[0] + bc[1] * qa_s[1] + bc[2] * qa_s[2];
+    double pa2[3], pb2[3];
+    for (int k = 0; k < 3; ++k) {
+        pa2[k] = qa_s[k] + (h * bq + gc * Eas) * bc[k];
+        pb2[k] = -qa_s[k] + (-h * bq + gc * Ebs) * bc[k];
+    }
+    double wm = wa > wb ? wa : wb;
+    if (r[3] < wb / wm)
+        for (int k = 0; k < 3; ++k) ua[k] = pa2[k] / ma;
+    if (r[3] < wa / wm)
+        for (int k = 0; k < 3; ++k) ub[k] = pb2[k] / mb;
+    return 1;
+}
+
+/* relativistic Boris rotation, q/m in e/m_e, dt in fs, normalized fields */
+void orc_boris(double u[3], const double e[3], const double b[3], double qm, double dt)
+{
+    double h = 0.5 * qm * dt;
+    double um[3] = {u[0] + h * e[0], u[1] + h * e[1], u[2] + h * e[2]};
+    double g = sqrt(1.0 + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+    double t[3] = {h * b[0] / g, h * b[1] / g, h * b[2] / g};
+    double t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+    double s[3] = {2 * t[0] / (1 + t2), 2 * t[1] / (1 + t2), 2 * t[2] / (1 + t2)};
+    double up[3] = {um[0] + um[1] * t[2] - um[2] * t[1],
+                    um[1] + um[2] * t[0] - um[0] * t[2],
+                    um[2] + um[0] * t[1] - um[1] * t[0]};
+    double uq[3] = {um[0] + up[1] * s[2] - up[2] * s[1],
+                    um[1] + up[2] * s[0] - up[0] * s[2],
+                    um[2] + up[0] * s[1] - up[1] * s[0]};
+    u[0] = uq[0] + h * e[0]; u[1] = uq[1] + h * e[1]; u[2] = uq[2] + h * e[2];
+}
+
+/* ---------------- pairing order ---------------- */
+typedef struct { uint64_t key, id; int idx; } keyrec;
+static int cmp_keyrec(const void *a, const void *b)
+{
+    const keyrec *x = a, *y = b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    if (x->id != y->id) return x->id < y->id ? -1 : 1;
+    return 0;
+}
+
+/* random permutation: ascending Philox key, ties broken by id */
+void orc_pair_order(int n, const uint64_t *id, uint32_t step, uint32_t purpose,
+                    uint64_t seed, int *perm)
+{
+    keyrec *k = malloc(sizeof(keyrec) * (n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) {
+        k[i].key = key64(seed, id[i], step, purpose);
+        k[i].id = id[i];
+        k[i].idx = i;
+    }
+    qsort(k, n, sizeof(keyrec), cmp_keyrec);
+    for (int i = 0; i < n; ++i) perm[i] = k[i].idx;
+    free(k);
+}
+
+/* like-particle pairs over positions of the permuted list: odd n >= 3 puts
+ * the first three in a triangle at half time step (Takizuka-Abe). */
+int orc_ee_pairs(int n, int *pa, int *pb, double *frac)
+{
+    int m = 0, start = 0;
+    if (n < 2) return 0;
+    if (n % 2 == 1) {
+        pa[0] = 0; pb[0] = 1; frac[0] = 0.5;
+        pa[1] = 1; pb[1] = 2; frac[1] = 0.5;
+        pa[2] = 2; pb[2] = 0; frac[2] = 0.5;
+        m = 3; start = 3;
+    }
+    for (int k = start; k + 1 < n; k += 2) {
+        pa[m] = k; pb[m] = k + 1; frac[m] = 1.0; ++m;
+    }
+    return m;
+}
+
+/* ---------------- deposit ---------------- */
+static double cic(double X, int node) { double d = fabs(X - node); return d < 1.0 ? 1.0 - d : 0.0; }
+static int wrapy(int j, int ny) { j %= ny; return j < 0 ? j + ny : j; }
+
+static void dep_seg(int nx, int ny, double dx, double dy, double dt, double X0, double Y0,
+                    double X1, double Y1, double vz, double vy, double qw, double frac, double *j3)
+{
+    double *jx = j3, *jy = j3 + (size_t)ny * (nx + 1), *jz = j3 + 2 * (size_t)ny * (nx + 1);
+    int i0 = (int)floor(X0);
+    double S0x[4], S1x[4], DSx[4];
+    for (int a = 0; a < 4; ++a) {
+        S0x[a] = cic(X0, i0 - 1 + a);
+        S1x[a] = cic(X1, i0 - 1 + a);
+        DSx[a] = S1x[a] - S0x[a];
+    }
+    if (ny == 1) {
+        double acc = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            acc += DSx[a];
+            int i = i0 - 1 + a;
+            if (i >= 0 && i < nx) jx[i] += -qw * (dx / dt) * acc;
+        }
+        for (int a = 0; a < 4; ++a) {
+            int i = i0 - 1 + a;
+            if (i < 0 || i > nx) continue;
+            double s = 0.5 * (S0x[a] + S1x[a]);
+            jy[i] += qw * vy * s * frac;
+            jz[i] += qw * vz * s * frac;
+        }
+        return;
+    }
+    int j0 = (int)floor(Y0);
+    double S0y[4], S1y[4], DSy[4];
+    for (int b = 0; b < 4; ++b) {
+        S0y[b] = cic(Y0, j0 - 1 + b);
+        S1y[b] = cic(Y1, j0 - 1 + b);
+        DSy[b] = S1y[b] - S0y[b];
+    }
+    for (int b = 0; b < 4; ++b) {
+        int jj = wrapy(j0 - 1 + b, ny);
+        double acc = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            acc += DSx[a] * (S0y[b] + 0.5 * DSy[b]);
+            int i = i0 - 1 + a;
+            if (i >= 0 && i < nx) jx[(size_t)jj * (nx + 1) + i] += -qw * (dx / dt) * acc;
+        }
+    }
+    for (int a = 0; a < 4; ++a) {
+        int i = i0 - 1 + a;
+        if (i < 0 || i > nx) continue;
+        double acc = 0.0;
+        for (int b = 0; b < 3; ++b) {
+            acc += DSy[b] * (S0x[a] + 0.5 * DSx[a]);
+            int jj = wrapy(j0 - 1 + b, ny);
+            jy[(size_t)jj * (nx + 1) + i] += -qw * (dy / dt) * acc;
+        }
+        for (int b = 0; b < 4; ++b) {
+            int jj = wrapy(j0 - 1 + b, ny);
+            double wz = S0x[a] * S0y[b] + 0.5 * DSx[a] * S0y[b] + 0.5 * S0x[a] * DSy[b]
+                        + DSx[a] * DSy[b] / 3.0;
+            jz[(size_t)jj * (nx + 1) + i] += qw * vz * wz * frac;
+        }
+    }
+}
+
+/* Charge-conserving current of one particle moving (X0,Y0)->(X1,Y1) in one
+ * step (cell units), split into equal segments shorter than one cell.
+ * j3 = [jx, jy, jz] on [ny][nx+1], units e*n_ref*nm/fs; jx at (i+1/2, j),
+ * jy at (i, j+1/2), jz at (i, j).  In 1D (ny == 1) jy, jz use the
+ * time-averaged x shape. */
+void orc_deposit(int nx, int ny, double dx, double dy, double dt, double X0,
+                 double Y0, double X1, double Y1, double vz, double vy,
+                 double qw, double *j3)
+{
+    double ax = fabs(X1 - X0), ay = ny > 1 ? fabs(Y1 - Y0) : 0.0;
+    double m = ax > ay ? ax : ay;
+    int nseg = (int)floor(m) + 1;
+    for (int k = 0; k < nseg; ++k) {
+        double a0 = (double)k / nseg, a1 = (double)(k + 1) / nseg;
+        double xa = X0 + a0 * (X1 - X0), xb = X0 + a1 * (X1 - X0);
+        double ya = Y0 + a0 * (Y1 - Y0), yb = Y0 + a1 * (Y1 - Y0);
+        dep_seg(nx, ny, dx, dy, dt, xa, ya, xb, yb, vz, vy, qw, 1.0 / nseg, j3);
+    }
+}
+
+/* CIC charge density of one particle on the node grid [ny][nx+1] */
+void orc_rho(int nx, int ny, double X, double Y, double qw, double *rho)
+{
+    int i0 = (int)floor(X);
+    for (int a = 0; a < 2; ++a) {
+        int i = i0 + a;
+        if (i < 0 || i > nx) continue;
+        double sx = cic(X, i);
+        if (ny == 1) { rho[i] += qw * sx; continue; }
+        int j0 = (int)floor(Y);
+        for (int b = 0; b < 2; ++b) {
+            int jj = wrapy(j0 + b, ny);
+            rho[(size_t)jj * (nx + 1) + i] += qw * sx * cic(Y, j0 + b);
+        }
+    }
+}
+
+/* ---------------- slab state ---------------- */
+typedef struct { double X, Y, u[3], w; uint64_t id; int alive; } elec;
+typedef struct { double X, Y, u[3], zf; uint32_t id; int Z, nK; } ionr;
+
+struct orc_slab {
+    orc_params p;
+    orc_tables t;
+    double *hv_tab, *sigma, *eos_T, *eos_n, *eos_Z;
+    orc_pulse pulse;
+    int have_pulse;
+    double *hv_b, *sig_b;       /* per bin: photon energy, sigma[s][b] */
+    elec *e; int ne, cap_e;
+    ionr *ion; int ni;
+    double *f;                  /* [6][ny][nx+1] ex ey ez bx by bz */
+    double *j;                  /* [3][ny][nx+1] */
+    double *ph;                 /* [ny][nx][nb] */
+    uint32_t step;
+    double tally[ORC_NT];
+    uint64_t cnt[ORC_NC];
+};
+
+static double *dupd(const double *a, size_t n)
+{
+    double *b = malloc(sizeof(double) * (n ? n : 1));
+    if (n) memcpy(b, a, sizeof(double) * n);
+    return b;
+}
+
+orc_slab *orc_create(const orc_params *p, const orc_tables *t)
+{
+    orc_slab *s = calloc(1, sizeof(orc_slab));
+    s->p = *p;
+    s->t = *t;
+    s->hv_tab = dupd(t->hv_tab, t->n_hv);
+    s->sigma = dupd(t->sigma, (size_t)ORC_NS * t->n_hv);
+    s->eos_T = dupd(t->eos_T, t->n_T);
+    s->eos_n = dupd(t->eos_n, t->n_n);
+    s->eos_Z = dupd(t->eos_Z, (size_t)t->n_T * t->n_n);
+    s->t.hv_tab = s->hv_tab; s->t.sigma = s->sigma;
+    s->t.eos_T = s->eos_T; s->t.eos_n = s->eos_n; s->t.eos_Z = s->eos_Z;
+    size_t ng = (size_t)p->ny * (p->nx + 1);
+    s->f = calloc(6 * ng, sizeof(double));
+    s->j = calloc(3 * ng, sizeof(double));
+    return s;
+}
+
+void orc_destroy(orc_slab *s)
+{
+    if (!s) return;
+    free(s->hv_tab); free(s->sigma); free(s->eos_T); free(s->eos_n); free(s->eos_Z);
+    free(s->hv_b); free(s->sig_b); free(s->e); free(s->ion); free(s->f); free(s->j); free(s->ph);
+    free(s);
+}
+
+/* photoionization cross section of the table at hv: log-log interpolation,
+ * held constant beyond the table ends */
+static double sigma_at(const orc_tables *t, int sub, double hv)
+{
+    const double *g = t->hv_tab, *v = t->sigma + (size_t)sub * t->n_hv;
+    int n = t->n_hv;
+    if (hv <= g[0]) return v[0];
+    if (hv >= g[n - 1]) return v[n - 1];
+    int lo = 0, hi = n - 1;
+    while (hi - lo > 1) { int m = (lo + hi) / 2; if (g[m] <= hv) lo = m; else hi = m; }
+    if (v[lo] <= 0.0 || v[lo + 1] <= 0.0) {
+        double f = (hv - g[lo]) / (g[lo + 1] - g[lo]);
+        return v[lo] + f * (v[lo + 1] - v[lo]);
+    }
+    double f = log(hv / g[lo]) / log(g[lo + 1] / g[lo]);
+    return exp(log(v[lo]) + f * log(v[lo + 1] / v[lo]));
+}
+
+void orc_set_pulse(orc_slab *s, const orc_pulse *pl)
+{
+    int nb = pl->n_bins;
+    s->pulse = *pl;
+    s->have_pulse = 1;
+    free(s->hv_b); free(s->sig_b); free(s->ph);
+    s->hv_b = malloc(sizeof(double) * nb);
+    s->sig_b = malloc(sizeof(double) * nb * ORC_NS);
+    for (int b = 0; b < nb; ++b) {
+        s->hv_b[b] = pl->hv + pl->bandwidth * ((b + 0.5) / nb - 0.5);
+        for (int q = 0; q < ORC_NS; ++q) s->sig_b[q * nb + b] = sigma_at(&s->t, q, s->hv_b[b]);
+    }
+    s->ph = calloc((size_t)s->p.ny * s->p.nx * nb, sizeof(double));
+}
+
+void orc_set_step(orc_slab *s, uint32_t n) { s->step = n; }
+uint32_t orc_get_step(const orc_slab *s) { return s->step; }
+
+static void ensure_e(orc_slab *s, int n)
+{
+    if (n <= s->cap_e) return;
+    int c = s->cap_e ? s->cap_e : 1024;
+    while (c < n) c *= 2;
+    s->e = realloc(s->e, sizeof(elec) * c);
+    s->cap_e = c;
+}
+
+void orc_load_electrons(orc_slab *s, int n, const double *X, const double *Y,
+                        const double *u, const double *w, const uint64_t *id)
+{
+    s->ne = 0;
+    ensure_e(s, n);
+    for (int k = 0; k < n; ++k) {
+        elec *e = &s->e[k];
+        e->X = X[k]; e->Y = Y[k];
+        e->u[0] = u[3 * k]; e->u[1] = u[3 * k + 1]; e->u[2] = u[3 * k + 2];
+        e->w = w[k]; e->id = id[k]; e->alive = 1;
+    }
+    s->ne = n;
+}
+
+void orc_load_ions(orc_slab *s, int n, const double *X, const double *Y,
+                   const double *u, const double *zf, const int32_t *Z,
+                   const int32_t *nK, const uint32_t *id)
+{
+    free(s->ion);
+    s->ion = malloc(sizeof(ionr) * (n ? n : 1));
+    for (int k = 0; k < n; ++k) {
+        ionr *q = &s->ion[k];
+        q->X = X[k]; q->Y = Y[k];
+        q->u[0] = u[3 * k]; q->u[1] = u[3 * k + 1]; q->u[2] = u[3 * k + 2];
+        q->zf = zf[k]; q->Z = Z[k]; q->nK = nK[k]; q->id = id[k];
+    }
+    s->ni = n;
+}
+
+int orc_n_electrons(const orc_slab *s) { return s->ne; }
+int orc_n_ions(const orc_slab *s) { return s->ni; }
+
+void orc_get_electrons(const orc_slab *s, double *X, double *Y, double *u, double *w, uint64_t *id)
+{
+    for (int k = 0; k < s->ne; ++k) {
+        const elec *e = &s->e[k];
+        X[k] = e->X; Y[k] = e->Y;
+        u[3 * k] = e->u[0]; u[3 * k + 1] = e->u[1]; u[3 * k + 2] = e->u[2];
+        w[k] = e->w; id[k] = e->id;
+    }
+}
+
+void orc_get_ions(const orc_slab *s, double *X, double *Y, double *u, double *zf,
+                  int32_t *Z, int32_t *nK, uint32_t *id)
+{
+    for (int k = 0; k < s->ni; ++k) {
+        const ionr *q = &s->ion[k];
+        X[k] = q->X; Y[k] = q->Y;
+        u[3 * k] = q->u[0]; u[3 * k + 1] = q->u[1]; u[3 * k + 2] = q->u[2];
+        zf[k] = q->zf; Z[k] = q->Z; nK[k] = q->nK; id[k] = q->id;
+    }
+}
+
+void orc_set_fields(orc_slab *s, const double *f6)
+{
+    memcpy(s->f, f6, sizeof(double) * 6 * (size_t)s->p.ny * (s->p.nx + 1));
+}
+void orc_get_fields(const orc_slab *s, double *f6)
+{
+    memcpy(f6, s->f, sizeof(double) * 6 * (size_t)s->p.ny * (s->p.nx + 1));
+}
+void orc_get_current(const orc_slab *s, double *j3)
+{
+    memcpy(j3, s->j, sizeof(double) * 3 * (size_t)s->p.ny * (s->p.nx + 1));
+}
+void orc_set_photons(orc_slab *s, const double *ph)
+{
+    if (s->have_pulse) memcpy(s->ph, ph, sizeof(double) * (size_t)s->p.ny * s->p.nx * s->pulse.n_bins);
+}
+void orc_get_photons(const orc_slab *s, double *ph)
+{
+    if (s->have_pulse) memcpy(ph, s->ph, sizeof(double) * (size_t)s->p.ny * s->p.nx * s->pulse.n_bins);
+}
+
+/* ---------------- photon march (every rad step) ---------------- */
+static double pulse_I(const orc_pulse *pl, double tau)
+{
+    if (pl->shape == 1) return fabs(tau - pl->t_peak) <= 0.5 * pl->fwhm ? pl->I_peak : 0.0;
+    double d = (tau - pl->t_peak) / pl->fwhm;
+    return pl->I_peak * exp(-4.0 * log(2.0) * d * d);
+}
+
+/* photon number density (units n_ref) entering x = 0 at time tau in bin b */
+static double source(const orc_slab *s, int b, double tau, int row)
+{
+    double I = pulse_I(&s->pulse, tau);                       /* W/cm^2 */
+    double n = I / (C_CM_FS * 1e15 * s->hv_b[b] * Q_E) / s->pulse.n_bins;  /* cm^-3 */
+    if (s->pulse.spot_sigma > 0.0 && s->p.ny > 1) {
+        double y = (row + 0.5) * s->p.dy - 0.5 * s->p.ny * s->p.dy;
+        n *= exp(-0.5 * y * y / (s->pulse.spot_sigma * s->pulse.spot_sigma));
+    }
+    return n / s->p.n_ref;
+}
+
+/* Advance the photon field by one rad step: every cell's content moves
+ * c*dt_rad along +x, split linearly between the two destination cells;
+ * the region x < 0 holds the pulse at retarded time; what passes x = L is
+ * transmitted. */
+static void march(orc_slab *s)
+{
+    int nx = s->p.nx, ny = s->p.ny, nb = s->pulse.n_bins;
+    double dtr = s->p.rad_every * s->p.dt;
+    double sh = C_NM_FS * dtr / s->p.dx;
+    int m = (int)floor(sh);
+    double f = sh - m;
+    double tprev = (double)s->step * s->p.dt - dtr;
+    double *col = malloc(sizeof(double) * nx);
+    for (int row = 0; row < ny; ++row)
+        for (int b = 0; b < nb; ++b) {
+            double *ph = s->ph + (size_t)row * nx * nb;
+            for (int k = 0; k < nx; ++k) col[k] = ph[(size_t)k * nb + b];
+            double trans = 0.0, inc = 0.0;
+            for (int k = 0; k < nx; ++k) ph[(size_t)k * nb + b] = 0.0;
+            for (int j = -(m + 1); j < nx; ++j) {
+                double v;
+                if (j < 0) v = source(s, b, tprev - (j + 0.5) * s->p.dx / C_NM_FS, row);
+                else v = col[j];
+                if (v == 0.0) continue;
+                int d0 = j + m, d1 = j + m + 1;
+                double v0 = (1.0 - f) * v, v1 = f * v;
+                if (j < 0) {
+                    if (d0 >= 0) inc += v0;
+                    if (d1 >= 0) inc += v1;
+                }
+                if (d0 >= nx) trans += v0; else if (d0 >= 0) ph[(size_t)d0 * nb + b] += v0;
+                if (d1 >= nx) trans += v1; else if (d1 >= 0) ph[(size_t)d1 * nb + b] += v1;
+            }
+            s->tally[ORC_T_INC] += inc * s->hv_b[b];
+            s->tally[ORC_T_TRANS] += trans * s->hv_b[b];
+        }
+    free(col);
+}
+
+/* ---------------- per-cell physics ---------------- */
+typedef struct {
+    double X, Y, u[3], w; uint64_t id;
+} newe;
+
+typedef struct {
+    newe *ne; int n, cap;
+    double tally_ion, ka_esc;
+    uint64_t cnt[ORC_NC];
+} cellout;
+
+static void push_new(cellout *o, double X, double Y, const double u[3], double w, uint64_t id)
+{
+    if (o->n == o->cap) {
+        o->cap = o->cap ? 2 * o->cap : 16;
+        o->ne = realloc(o->ne, sizeof(newe) * o->cap);
+    }
+    newe *q = &o->ne[o->n++];
+    q->X = X; q->Y = Y; q->u[0] = u[0]; q->u[1] = u[1]; q->u[2] = u[2]; q->w = w; q->id = id;
+}
+
+static void iso_u(double ke, double rc, double rp, double u[3])
+{
+    double x = ke / ME_C2;
+    double um = sqrt(x * (2.0 + x));
+    double ct = 2.0 * rc - 1.0;
+    double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+    double ph = 2.0 * PI * rp;
+    u[0] = um * st * cos(ph); u[1] = um * st * sin(ph); u[2] = um * ct;
+}
+
+static void cell_physics(orc_slab *S, int cell, int *eidx, int ne, int *iidx, int ni, cellout *o)
+{
+    const orc_params *p = &S->p;
+    const orc_tables *t = &S->t;
+    uint32_t step = S->step;
+    uint64_t seed = p->seed;
+    double wi = p->w_ion;
+    int rad = p->rad_every > 0 && (step % (uint32_t)p->rad_every) == 0;
+
+    /* 1. canonical order: ascending Philox key, ties by id */
+    int *pe = malloc(sizeof(int) * (ne + 1)), *pi = malloc(sizeof(int) * (ni + 1));
+    {
+        uint64_t *ids = calloc((ne > ni ? ne : ni) + 1, sizeof(uint64_t));
+        int *perm = malloc(sizeof(int) * (ne > ni ? ne : ni) + 8);
+        for (int k = 0; k < ne; ++k) ids[k] = S->e[eidx[k]].id;
+        orc_pair_order(ne, ids, step, PU_PAIR_E, seed, perm);
+        for (int k = 0; k < ne; ++k) pe[k] = eidx[perm[k]];
+        for (int k = 0; k < ni; ++k) ids[k] = S->ion[iidx[k]].id;
+        orc_pair_order(ni, ids, step, PU_PAIR_I, seed, perm);
+        for (int k = 0; k < ni; ++k) pi[k] = iidx[perm[k]];
+        free(ids); free(perm);
+    }
+
+    /* 2. moments (FP64) */
+    double We = 0, Wb = 0, Kb = 0, Q = 0;
+    for (int k = 0; k < ne; ++k) {
+        elec *e = &S->e[pe[k]];
+        double ke = kin(e->u, 1.0);
+        We += e->w;
+        if (p->E_bulk <= 0.0 || ke < p->E_bulk) { Wb += e->w; Kb += e->w * ke; }
+    }
+    for (int k = 0; k < ni; ++k) Q += S->ion[pi[k]].Z + S->ion[pi[k]].zf;
+    double n_e = We * p->n_ref, n_i = ni * wi * p->n_ref;
+    double Te = Wb > 0 ? (2.0 / 3.0) * Kb / Wb : 0.0;
+    double zbar = ni > 0 ? Q / ni : 0.0;
+    double dE[ORC_NZ];
+    for (int z = 0; z < ORC_NZ; ++z) dE[z] = orc_ipd(p->ipd_model, z, n_e, n_i, Te, zbar);
+    double lnL = p->coulomb_log > 0 ? p->coulomb_log : orc_coulomb_log(n_e, Te, zbar);
+
+    /* kinetic energy of the cell before the collisions */
+    int coll = (p->flags & (ORC_F_COLL_EE | ORC_F_COLL_EI)) != 0;
+    double Kpre = 0.0;
+    if (coll) {
+        for (int k = 0; k < ne; ++k) Kpre += S->e[pe[k]].w * kin(S->e[pe[k]].u, 1.0);
+        for (int k = 0; k < ni; ++k) Kpre += wi * kin(S->ion[pi[k]].u, p->m_ion);
+    }
+
+    /* 3a. e-e collisions */
+    if ((p->flags & ORC_F_COLL_EE) && ne >= 2) {
+        int *pa = malloc(sizeof(int) * (ne + 3)), *pb = malloc(sizeof(int) * (ne + 3));
+        double *fr = malloc(sizeof(double) * (ne + 3));
+        int np = orc_ee_pairs(ne, pa, pb, fr);
+        for (int k = 0; k < np; ++k) {
+            elec *a = &S->e[pe[pa[k]]], *b = &S->e[pe[pb[k]]];
+            double r[4];
+            draw4(seed, a->id, step, PU_COLL_EE, r);
+            o->cnt[ORC_C_EE] += orc_collide(a->u, b->u, 1.0, 1.0, -1.0, -1.0, a->w, b->w,
+                                            n_e, lnL, p->dt * fr[k], r);
+        }
+        free(pa); free(pb); free(fr);
+    }
+    /* 3b. e-i collisions: the longer list in order, the shorter cycled.
+     * Density of a pair: the cycled species' density times
+     * max(w_a, w_b) / w_cycled, so that with the acceptance min(1,
+     * w_other/w_self) every real electron sees n_i and every real ion n_e
+     * (Takizuka-Abe pairing with Nanbu-Yonemura weights). */
+    if ((p->flags & ORC_F_COLL_EI) && ne >= 1 && ni >= 1) {
+        int nmax = ne >= ni ? ne : ni;
+        for (int k = 0; k < nmax; ++k) {
+            elec *a; ionr *b; double r[4], npair;
+            if (ne >= ni) {
+                a = &S->e[pe[k]]; b = &S->ion[pi[k % ni]];
+                draw4(seed, a->id, step, PU_COLL_EI, r);
+                npair = n_i * (a->w > wi ? a->w : wi) / wi;
+            } else {
+                b = &S->ion[pi[k]]; a = &S->e[pe[k % ne]];
+                draw4(seed, b->id, step, PU_COLL_IE, r);
+                npair = n_e * (a->w > wi ? a->w : wi) / a->w;
+            }
+            o->cnt[ORC_C_EI] += orc_collide(a->u, b->u, 1.0, p->m_ion, -1.0, b->Z + b->zf,
+                                            a->w, wi, npair, lnL, p->dt, r);
+        }
+    }
+
+    /* 3c. weighted pairs conserve energy only on average: restore the cell's
+     * kinetic energy exactly by the constant-factor scaling of the electron
+     * kinetic energies (the operator Sec. IV uses for ionization) */
+    if (coll && ne >= 1) {
+        double Ke = 0.0, Ki = 0.0;
+        for (int k = 0; k < ne; ++k) Ke += S->e[pe[k]].w * kin(S->e[pe[k]].u, 1.0);
+        for (int k = 0; k < ni; ++k) Ki += wi * kin(S->ion[pi[k]].u, p->m_ion);
+        if (Ke > 0.0) {
+            double f = 1.0 + (Kpre - Ke - Ki) / Ke;
+            if (f > 0.0)
+                for (int k = 0; k < ne; ++k) scale_ke(S->e[pe[k]].u, f);
+        }
+    }
+
+    /* 4. Lotz impact ionization with cell-average probability per charge state */
+    int nnew_imp = 0;
+    if ((p->flags & ORC_F_IONIZE) && ne >= 1 && ni >= 1) {
+        int present[ORC_NZ] = {0};
+        for (int k = 0; k < ni; ++k) if (S->ion[pi[k]].Z < 13) present[S->ion[pi[k]].Z] = 1;
+        double Pz[ORC_NZ] = {0};
+        double Kt = 0.0;
+        for (int k = 0; k < ne; ++k) Kt += S->e[pe[k]].w * kin(S->e[pe[k]].u, 1.0);
+        for (int z = 0; z < 13; ++z) {
+            if (!present[z]) continue;
+            double R = 0.0;
+            for (int k = 0; k < ne; ++k) {
+                elec *e = &S->e[pe[k]];
+                double g = gam(e->u);
+                double beta = sqrt(e->u[0] * e->u[0] + e->u[1] * e->u[1] + e->u[2] * e->u[2]) / g;
+                R += e->w * beta * orc_lotz(t, z, dE[z], kin(e->u, 1.0));
+            }
+            Pz[z] = p->dt * C_CM_FS * p->n_ref * R;
+            if (Pz[z] > 1.0) o->cnt[ORC_C_PGT1]++;
+        }
+        double paid = 0.0;
+        int stop = 0;
+        for (int k = 0; k < ni; ++k) {
+            ionr *q = &S->ion[pi[k]];
+            if (q->Z >= 13) continue;
+            double r[4];
+            draw4(seed, q->id, step, PU_ION, r);
+            if (!(r[0] < Pz[q->Z])) continue;
+            double I = ion_energy(t, q->Z, q->nK, dE);
+            if (stop || paid + wi * I > Kt) { stop = 1; o->cnt[ORC_C_ION_REJ]++; continue; }
+            paid += wi * I;
+            int s = outermost(13 - q->Z, q->nK);
+            remove_electron(&q->Z, &q->nK, s);
+            double u0[3] = {0, 0, 0};
+            push_new(o, q->X, q->Y, u0, wi, ((uint64_t)(((step + 1u) << 2) | K_IMPACT) << 32) | q->id);
+            o->cnt[ORC_C_ION]++;
+            ++nnew_imp;
+        }
+        if (paid > 0.0) {
+            double f = 1.0 - paid / Kt;
+            for (int k = 0; k < ne; ++k) scale_ke(S->e[pe[k]].u, f);
+            o->tally_ion += paid;
+        }
+    }
+
+    /* 5. EOS-clamped three-body recombination */
+    if ((p->flags & ORC_F_RECOMB) && ni >= 1) {
+        double Q2 = 0.0;
+        for (int k = 0; k < ni; ++k) Q2 += S->ion[pi[k]].Z + S->ion[pi[k]].zf;
+        double zb = Q2 / ni;
+        double Wb2 = 0.0, Kb2 = 0.0, Wex = 0.0;
+        for (int k = 0; k < ne; ++k) {
+            elec *e = &S->e[pe[k]];
+            double ke = kin(e->u, 1.0);
+            Wex += e->w;
+            if (p->E_bulk <= 0.0 || ke < p->E_bulk) { Wb2 += e->w; Kb2 += e->w * ke; }
+        }
+        for (int k = o->n - nnew_imp; k < o->n; ++k) {  /* new zero-energy electrons */
+            if (p->E_bulk <= 0.0 || 0.0 < p->E_bulk) Wb2 += o->ne[k].w;
+        }
+        double Te2 = Wb2 > 0 ? (2.0 / 3.0) * Kb2 / Wb2 : 0.0;
+        double zeos = orc_eos(t, n_i, Te2);
+        int Kev = 0;
+        if (zb > zeos) Kev = (int)floor((zb - zeos) * ni + 0.5);
+        /* events are dealt round-robin over the ions in canonical order; an
+         * ion can take several in one step (no limit on the instantaneous
+         * rate), at most as many as its charge */
+        int elig = 0;
+        for (int k = 0; k < ni; ++k) elig += S->ion[pi[k]].Z;
+        if (Kev > elig) Kev = elig;
+        int wcap = (int)floor(Wex / wi + 1e-9);
+        if (Kev > wcap) Kev = wcap;
+        if (Kev > 0) {
+            int *nrec = calloc(ni, sizeof(int));
+            int left = Kev;
+            while (left > 0) {
+                for (int k = 0; k < ni && left > 0; ++k)
+                    if (S->ion[pi[k]].Z - nrec[k] >= 1) { nrec[k]++; --left; }
+            }
+            double Wrem = Kev * wi;
+            /* electrons give up weight in canonical order */
+            double *take = calloc(ne + 1, sizeof(double));
+            double before = 0.0, remKE = 0.0;
+            for (int k = 0; k < ne; ++k) {
+                elec *e = &S->e[pe[k]];
+                double tk = Wrem - before;
+                if (tk > e->w) tk = e->w;
+                if (tk < 0.0) tk = 0.0;
+                take[k] = tk;
+                before += e->w;
+                remKE += tk * kin(e->u, 1.0);
+            }
+            /* binding released: Z -> Z-1 -> ... for each event of an ion */
+            double bind = 0.0;
+            for (int k = 0; k < ni; ++k) {
+                ionr *q = &S->ion[pi[k]];
+                for (int r = 1; r <= nrec[k]; ++r)
+                    bind += wi * ion_energy(t, q->Z - r, q->nK, dE);
+            }
+            /* bulk energy left to scale */
+            double Krem = 0.0;
+            for (int k = 0; k < ne; ++k) {
+                elec *e = &S->e[pe[k]];
+                double ke = kin(e->u, 1.0);
+                if (p->E_bulk <= 0.0 || ke < p->E_bulk) Krem += (e->w - take[k]) * ke;
+            }
+            if (Krem > 0.0) {
+                double f = 1.0 + (remKE + bind) / Krem;
+                for (int k = 0; k < ne; ++k) {
+                    elec *e = &S->e[pe[k]];
+                    double ke = kin(e->u, 1.0);
+                    int bulk = p->E_bulk <= 0.0 || ke < p->E_bulk;
+                    e->w -= take[k];
+                    if (take[k] > 0.0 && e->w <= 0.0) { e->w = 0.0; e->alive = 0; }
+                    if (bulk && e->alive) scale_ke(e->u, f);
+                }
+                for (int k = 0; k < ni; ++k) S->ion[pi[k]].Z -= nrec[k];
+                o->tally_ion -= bind;
+                o->cnt[ORC_C_REC] += (uint64_t)Kev;
+            }
+            free(take); free(nrec);
+        }
+    }
+
+    /* 6. rad step: photoionization then K-vacancy decay */
+    if (rad && (p->flags & (ORC_F_PHOTO | ORC_F_DECAY)) && ni >= 1) {
+        int nb = S->have_pulse ? S->pulse.n_bins : 0;
+        double dtr = p->rad_every * p->dt;
+        double *ph = nb ? S->ph + (size_t)cell * nb : NULL;
+        if ((p->flags & ORC_F_PHOTO) && nb) {
+            double cph = C_CM_FS * dtr * p->n_ref;
+            double *n0 = malloc(sizeof(double) * nb);
+            memcpy(n0, ph, sizeof(double) * nb);
+            for (int k = 0; k < ni; ++k) {
+                ionr *q = &S->ion[pi[k]];
+                int nbd = 13 - q->Z, occ[ORC_NS];
+                if (nbd <= 0 || !orc_occ(nbd, q->nK, occ)) continue;
+                double ra[4], rb[4];
+                draw4(seed, q->id, step, PU_PHOTO_A, ra);
+                draw4(seed, q->id, step, PU_PHOTO_B, rb);
+                double rs[ORC_NS] = {ra[0], ra[1], ra[2], ra[3], rb[0]};
+                int sub = -1; double Ps = 0.0, edge = 0.0;
+                for (int q2 = 0; q2 < ORC_NS; ++q2) {
+                    if (!occ[q2]) continue;
+                    double ed = lowered(t, q->Z, q2, dE[q->Z]);
+                    double acc = 0.0;
+                    for (int b = 0; b < nb; ++b)
+                        if (S->hv_b[b] > ed) acc += n0[b] * S->sig_b[q2 * nb + b];
+                    double P = cph * occ[q2] * acc;
+                    if (rs[q2] < P) { sub = q2; Ps = P; edge = ed; break; }
+                }
+                if (sub < 0) continue;
+                double target = rb[1] * Ps, cum = 0.0;
+                int bin = -1, lastpos = -1;
+                for (int b = 0; b < nb; ++b) {
+                    double c = (S->hv_b[b] > edge) ? cph * occ[sub] * n0[b] * S->sig_b[sub * nb + b] : 0.0;
+                    if (c > 0.0) lastpos = b;
+                    cum += c;
+                    if (cum > target) { bin = b; break; }
+                }
+                if (bin < 0) bin = lastpos;
+                if (bin < 0) continue;
+                double g = ph[bin] < wi ? ph[bin] : wi;
+                if (g <= 0.0) continue;
+                ph[bin] -= g;
+                if (g == wi) {
+                    remove_electron(&q->Z, &q->nK, sub);
+                } else {
+                    q->zf += g / wi;
+                    o->cnt[ORC_C_PART]++;
+                    if (q->zf >= 1.0) {
+                        q->zf -= 1.0;
+                        int so = outermost(13 - q->Z, q->nK);
+                        if (so >= 0) remove_electron(&q->Z, &q->nK, so);
+                    }
+                }
+                double u[3];
+                iso_u(S->hv_b[bin] - edge, rb[2], rb[3], u);
+                push_new(o, q->X, q->Y, u, g, ((uint64_t)(((step + 1u) << 2) | K_PHOTO) << 32) | q->id);
+                o->tally_ion += g * edge;
+                o->cnt[ORC_C_PH0 + sub]++;
+            }
+            free(n0);
+        }
+        if (p->flags & ORC_F_DECAY) {
+            for (int k = 0; k < ni; ++k) {
+                ionr *q = &S->ion[pi[k]];
+                if (q->nK <= 0) continue;
+                int nbd = 13 - q->Z, occ[ORC_NS];
+                if (!orc_occ(nbd, q->nK, occ)) continue;
+                double tau = t->tauK[nbd][q->nK - 1];
+                if (tau <= 0.0) continue;
+                double r[4];
+                draw4(seed, q->id, step, PU_DECAY, r);
+                if (!(r[0] < dtr / tau)) continue;
+                double om = t->omegaK[nbd][q->nK - 1];
+                int nl = occ[1] + occ[2];
+                if (r[1] < 1.0 - om) {
+                    if (nl < 2) continue;
+                    double e2s = lowered(t, q->Z, 1, dE[q->Z]), e2p = lowered(t, q->Z, 2, dE[q->Z]);
+                    double EA = t->E_Ka[q->Z] - (occ[1] * e2s + occ[2] * e2p) / nl;
+                    if (EA < 0.0) EA = 0.0;
+                    int kocc = occ[0] + 1, nb2 = nbd - 1;
+                    q->Z += 1;
+                    q->nK = (nb2 < 2 ? nb2 : 2) - kocc;
+                    double u[3];
+                    iso_u(EA, r[2], r[3], u);
+                    push_new(o, q->X, q->Y, u, wi, ((uint64_t)(((step + 1u) << 2) | K_AUGER) << 32) | q->id);
+                    o->tally_ion -= wi * EA;
+                    o->cnt[ORC_C_AUG]++;
+                } else {
+                    if (occ[2] < 1) continue;
+                    double Eka = t->E_Ka[q->Z];
+                    q->nK -= 1;
+                    int hit = -1;
+                    if (nb) {
+                        double hw = 0.5 * S->pulse.bandwidth / nb;
+                        for (int b = 0; b < nb; ++b)
+                            if (Eka >= S->hv_b[b] - hw && Eka < S->hv_b[b] + hw) { hit = b; break; }
+                    }
+                    if (hit >= 0) ph[hit] += wi * Eka / S->hv_b[hit];
+                    else o->ka_esc += wi * Eka;
+                    o->tally_ion -= wi * Eka;
+                    o->cnt[ORC_C_KA]++;
+                }
+            }
+        }
+    }
+    free(pe); free(pi);
+}
+
+/* ---------------- fields ---------------- */
+static double kappa_J(const orc_slab *s)
+{
+    double E0 = ME_KG * C_SI / (Q_E * 1e-15);
+    return Q_E * s->p.n_ref * 1e6 * 1e-9 / (EPS0 * E0);
+}
+
+#define IX(j, i) ((size_t)(j) * W + (i))
+/* B half step: dB/dt = -c curl E */
+static void b_half(double *f, int nx, int ny, double dx, double dy, double h)
+{
+    int W = nx + 1;
+    size_t ng = (size_t)ny * W;
+    double *ex = f, *ey = f + ng, *ez = f + 2 * ng, *bx = f + 3 * ng, *by = f + 4 * ng, *bz = f + 5 * ng;
+    for (int j = 0; j < ny; ++j) {
+        int jp = (j + 1) % ny;
+        for (int i = 0; i <= nx; ++i)
+            bx[IX(j, i)] -= h * C_NM_FS * (ez[IX(jp, i)] - ez[IX(j, i)]) / dy;
+        for (int i = 0; i < nx; ++i) {
+            by[IX(j, i)] += h * C_NM_FS * (ez[IX(j, i + 1)] - ez[IX(j, i)]) / dx;
+            bz[IX(j, i)] -= h * C_NM_FS * ((ey[IX(j, i + 1)] - ey[IX(j, i)]) / dx
+                                           - (ex[IX(jp, i)] - ex[IX(j, i)]) / dy);
+        }
+    }
+}
+
+/* E full step: dE/dt = c curl B - kappa J; first-order Mur at x = 0, L */
+static void e_full(double *f, const double *jc, int nx, int ny, double dx, double dy,
+                   double dtf, double kap)
+{
+    int W = nx + 1;
+    size_t ng = (size_t)ny * W;
+    double *ex = f, *ey = f + ng, *ez = f + 2 * ng, *bx = f + 3 * ng, *by = f + 4 * ng, *bz = f + 5 * ng;
+    const double *jx = jc, *jy = jc + ng, *jz = jc + 2 * ng;
+    double mur = (C_NM_FS * dtf - dx) / (C_NM_FS * dtf + dx);
+    for (int j = 0; j < ny; ++j) {
+        int jm = (j - 1 + ny) % ny;
+        double y0 = ey[IX(j, 0)], y1 = ey[IX(j, 1)], yn1 = ey[IX(j, nx - 1)], yn = ey[IX(j, nx)];
+        double z0 = ez[IX(j, 0)], z1 = ez[IX(j, 1)], zn1 = ez[IX(j, nx - 1)], zn = ez[IX(j, nx)];
+        for (int i = 0; i < nx; ++i)
+            ex[IX(j, i)] += dtf * (C_NM_FS * (bz[IX(j, i)] - bz[IX(jm, i)]) / dy - kap * jx[IX(j, i)]);
+        for (int i = 1; i < nx; ++i) {
+            ey[IX(j, i)] += dtf * (-C_NM_FS * (bz[IX(j, i)] - bz[IX(j, i - 1)]) / dx - kap * jy[IX(j, i)]);
+            ez[IX(j, i)] += dtf * (C_NM_FS * ((by[IX(j, i)] - by[IX(j, i - 1)]) / dx
+                                              - (bx[IX(j, i)] - bx[IX(jm, i)]) / dy)
+                                   - kap * jz[IX(j, i)]);
+        }
+        ey[IX(j, 0)] = y1 + mur * (ey[IX(j, 1)] - y0);
+        ez[IX(j, 0)] = z1 + mur * (ez[IX(j, 1)] - z0);
+        ey[IX(j, nx)] = yn1 + mur * (ey[IX(j, nx - 1)] - yn);
+        ez[IX(j, nx)] = zn1 + mur * (ez[IX(j, nx - 1)] - zn);
+    }
+}
+#undef IX
+
+/* number of field subcycles per particle step: Yee stability with margin
+ * cfl (the particle step c*dt exceeds the cell size) */
+static int n_subcycles(const orc_params *p)
+{
+    double inv = 1.0 / (p->dx * p->dx) + (p->ny > 1 ? 1.0 / (p->dy * p->dy) : 0.0);
+    int n = (int)ceil(C_NM_FS * p->dt * sqrt(inv) / p->cfl);
+    return n < 1 ? 1 : n;
+}
+
+static void field_step(orc_slab *s)
+{
+    const orc_params *p = &s->p;
+    int nsub = n_subcycles(p);
+    double dtf = p->dt / nsub, kap = kappa_J(s);
+    for (int it = 0; it < nsub; ++it) {
+        b_half(s->f, p->nx, p->ny, p->dx, p->dy, 0.5 * dtf);
+        e_full(s->f, s->j, p->nx, p->ny, p->dx, p->dy, dtf, kap);
+        b_half(s->f, p->nx, p->ny, p->dx, p->dy, 0.5 * dtf);
+    }
+}
+
+/* field at (X, Y): CIC from the staggered grid, zero outside [0, nx] */
+static double grid_at(const double *F, int nx, int ny, double X, double Y, int hx, int hy)
+{
+    double xs = X - (hx ? 0.5 : 0.0), ys = Y - (hy ? 0.5 : 0.0);
+    int i0 = (int)floor(xs), j0 = (int)floor(ys);
+    double fx = xs - i0, fy = ys - j0;
+    int imax = hx ? nx - 1 : nx;
+    double v = 0.0;
+    for (int a = 0; a < 2; ++a) {
+        int i = i0 + a;
+        if (i < 0 || i > imax) continue;
+        double wx = a ? fx : 1.0 - fx;
+        for (int b = 0; b < 2; ++b) {
+            int jj = wrapy(j0 + b, ny);
+            double wy = b ? fy : 1.0 - fy;
+            v += wx * wy * F[(size_t)jj * (nx + 1) + i];
+        }
+    }
+    return v;
+}
+
+static void gather(const orc_slab *s, double X, double Y, double e[3], double b[3])
+{
+    int nx = s->p.nx, ny = s->p.ny;
+    size_t ng = (size_t)ny * (nx + 1);
+    const double *f = s->f;
+    e[0] = grid_at(f, nx, ny, X, Y, 1, 0);
+    e[1] = grid_at(f + ng, nx, ny, X, Y, 0, 1);
+    e[2] = grid_at(f + 2 * ng, nx, ny, X, Y, 0, 0);
+    b[0] = grid_at(f + 3 * ng, nx, ny, X, Y, 0, 1);
+    b[1] = grid_at(f + 4 * ng, nx, ny, X, Y, 1, 0);
+    b[2] = grid_at(f + 5 * ng, nx, ny, X, Y, 1, 1);
+}
+
+/* push one particle; returns 0 if it left through an x boundary */
+static int push_one(orc_slab *s, double *X, double *Y, double u[3], double qm, double qw)
+{
+    const orc_params *p = &s->p;
+    double e[3], b[3];
+    gather(s, *X, *Y, e, b);
+    orc_boris(u, e, b, qm, p->dt);
+    double g = gam(u);
+    double X1 = *X + u[0] / g * C_NM_FS * p->dt / p->dx;
+    double Y1 = p->ny > 1 ? *Y + u[1] / g * C_NM_FS * p->dt / p->dy : *Y;
+    if (p->flags & ORC_F_FIELD)
+        orc_deposit(p->nx, p->ny, p->dx, p->dy, p->dt, *X, *Y, X1, Y1,
+                    u[2] / g * C_NM_FS, u[1] / g * C_NM_FS, qw, s->j);
+    if (p->ny > 1) {
+        Y1 = fmod(Y1, (double)p->ny);
+        if (Y1 < 0.0) Y1 += p->ny;
+        if (Y1 >= p->ny) Y1 -= p->ny;
+    }
+    *X = X1; *Y = Y1;
+    return X1 >= 0.0 && X1 < p->nx;
+}
+
+/* ---------------- step ---------------- */
+static int cell_of(const orc_slab *s, double X, double Y)
+{
+    int i = (int)floor(X), j = s->p.ny > 1 ? (int)floor(Y) : 0;
+    return j * s->p.nx + i;
+}
+
+void orc_step(orc_slab *s, int nsteps, int nthreads)
+{
+    const orc_params *p = &s->p;
+    int ncell = p->nx * p->ny;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    for (int it = 0; it < nsteps; ++it) {
+        int rad = p->rad_every > 0 && (s->step % (uint32_t)p->rad_every) == 0;
+        if (rad && (p->flags & ORC_F_PHOTO) && s->have_pulse) march(s);
+
+        /* bucket by cell (counting sort) */
+        int *cse = calloc(ncell + 1, sizeof(int)), *csi = calloc(ncell + 1, sizeof(int));
+        int *oe = malloc(sizeof(int) * (s->ne + 1)), *oi = malloc(sizeof(int) * (s->ni + 1));
+        for (int k = 0; k < s->ne; ++k) cse[cell_of(s, s->e[k].X, s->e[k].Y) + 1]++;
+        for (int k = 0; k < s->ni; ++k) csi[cell_of(s, s->ion[k].X, s->ion[k].Y) + 1]++;
+        for (int c = 0; c < ncell; ++c) { cse[c + 1] += cse[c]; csi[c + 1] += csi[c]; }
+        {
+            int *fe = calloc(ncell, sizeof(int)), *fi = calloc(ncell, sizeof(int));
+            for (int k = 0; k < s->ne; ++k) { int c = cell_of(s, s->e[k].X, s->e[k].Y); oe[cse[c] + fe[c]++] = k; }
+            for (int k = 0; k < s->ni; ++k) { int c = cell_of(s, s->ion[k].X, s->ion[k].Y); oi[csi[c] + fi[c]++] = k; }
+            free(fe); free(fi);
+        }
+        cellout *co = calloc(ncell, sizeof(cellout));
+#pragma omp parallel for schedule(dynamic, 16)
+        for (int c = 0; c < ncell; ++c)
+            cell_physics(s, c, oe + cse[c], cse[c + 1] - cse[c], oi + csi[c], csi[c + 1] - csi[c], &co[c]);
+        /* merge: new electrons in cell order, tallies */
+        int add = 0;
+        for (int c = 0; c < ncell; ++c) add += co[c].n;
+        int ne_old = s->ne;
+        ensure_e(s, s->ne + add);
+        for (int c = 0; c < ncell; ++c) {
+            for (int k = 0; k < co[c].n; ++k) {
+                elec *e = &s->e[s->ne++];
+                newe *q = &co[c].ne[k];
+                e->X = q->X; e->Y = q->Y; e->u[0] = q->u[0]; e->u[1] = q->u[1]; e->u[2] = q->u[2];
+                e->w = q->w; e->id = q->id; e->alive = 1;
+            }
+            s->tally[ORC_T_ION] += co[c].tally_ion;
+            s->tally[ORC_T_KA_ESC] += co[c].ka_esc;
+            for (int q = 0; q < ORC_NC; ++q) s->cnt[q] += co[c].cnt[q];
+            free(co[c].ne);
+        }
+        (void)ne_old;
+        free(co); free(cse); free(csi); free(oe); free(oi);
+
+        /* push + deposit */
+        size_t ng = (size_t)p->ny * (p->nx + 1);
+        memset(s->j, 0, sizeof(double) * 3 * ng);
+        if (p->flags & ORC_F_PUSH) {
+            for (int k = 0; k < s->ne; ++k) {
+                elec *e = &s->e[k];
+                if (!e->alive) continue;
+                double ke = kin(e->u, 1.0);
+                if (!push_one(s, &e->X, &e->Y, e->u, -1.0, -e->w)) {
+                    e->alive = 0;
+                    s->tally[ORC_T_ESC] += e->w * ke;
+                    s->cnt[ORC_C_ESC_E]++;
+                }
+            }
+            int w = 0;
+            for (int k = 0; k < s->ni; ++k) {
+                ionr *q = &s->ion[k];
+                double qc = q->Z + q->zf;
+                double ke = kin(q->u, p->m_ion);
+                int in = push_one(s, &q->X, &q->Y, q->u, qc / p->m_ion, qc * p->w_ion);
+                if (!in) { s->tally[ORC_T_ESC] += p->w_ion * ke; s->cnt[ORC_C_ESC_I]++; continue; }
+                s->ion[w++] = *q;
+            }
+            s->ni = w;
+        }
+        /* drop dead electrons */
+        {
+            int w = 0;
+            for (int k = 0; k < s->ne; ++k) if (s->e[k].alive && s->e[k].w > 0.0) s->e[w++] = s->e[k];
+            s->ne = w;
+        }
+        if (p->flags & ORC_F_FIELD) field_step(s);
+        s->step++;
+    }
+}
+
+void orc_tallies(orc_slab *s, double *t, uint64_t *c)
+{
+    const orc_params *p = &s->p;
+    double kee = 0.0, kei = 0.0, ph = 0.0, fe = 0.0;
+    for (int k = 0; k < s->ne; ++k) kee += s->e[k].w * kin(s->e[k].u, 1.0);
+    for (int k = 0; k < s->ni; ++k) kei += p->w_ion * kin(s->ion[k].u, p->m_ion);
+    if (s->have_pulse) {
+        int nb = s->pulse.n_bins;
+        for (size_t q = 0; q < (size_t)p->ny * p->nx * nb; ++q) ph += s->ph[q] * s->hv_b[q % nb];
+    }
+    size_t ng = (size_t)p->ny * (p->nx + 1);
+    for (size_t q = 0; q < 6 * ng; ++q) fe += s->f[q] * s->f[q];
+    double E0 = ME_KG * C_SI / (Q_E * 1e-15);
+    fe *= EPS0 * E0 * E0 / (2.0 * p->n_ref * 1e6 * Q_E);
+    for (int q = 0; q < ORC_NT; ++q) t[q] = s->tally[q];
+    t[ORC_T_KE_E] = kee; t[ORC_T_KE_I] = kei; t[ORC_T_PHOT] = ph; t[ORC_T_FIELD] = fe;
+    for (int q = 0; q < ORC_NC; ++q) c[q] = s->cnt[q];
+}
+
+/* charge-state distribution (fractional charges split between Z and Z+1)
+ * and the electron energy distribution on n_E log bins 0.1 eV .. E_max */
+void orc_diag(const orc_slab *s, double *csd, int n_E, double E_max, double *eedf)
+{
+    for (int z = 0; z < ORC_NZ; ++z) csd[z] = 0.0;
+    double tot = 0.0;
+    for (int k = 0; k < s->ni; ++k) {
+        const ionr *q = &s->ion[k];
+        csd[q->Z] += 1.0 - q->zf;
+        if (q->zf > 0.0 && q->Z < 13) csd[q->Z + 1] += q->zf;
+        tot += 1.0;
+    }
+    for (int z = 0; z < ORC_NZ; ++z) csd[z] = tot > 0 ? csd[z] / tot : 0.0;
+    for (int b = 0; b < n_E; ++b) eedf[b] = 0.0;
+    double W = 0.0, lo = 0.1, lr = log(E_max / lo);
+    for (int k = 0; k < s->ne; ++k) {
+        double ke = kin(s->e[k].u, 1.0);
+        int b = ke <= lo ? 0 : (int)floor(log(ke / lo) / lr * n_E);
+        if (b < 0) b = 0;
+        if (b >= n_E) b = n_E - 1;
+        eedf[b] += s->e[k].w;
+        W += s->e[k].w;
+    }
+    for (int b = 0; b < n_E; ++b) eedf[b] = W > 0 ? eedf[b] / W : 0.0;
+}

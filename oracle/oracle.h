@@ -1,0 +1,112 @@
+/* FP64 CPU oracle for the collisional PIC step of Royle et al. (PICLS,
+ * "Kinetic modeling of x-ray laser-driven solid Al plasmas via particle-in-
+ * cell simulation").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load this library.  It shares
+ * no code, header, table or constant with the CUDA path.
+ *
+ * Units: lengths nm (positions in cell units), times fs, energies eV,
+ * momenta u = gamma*v/c, weights in units of n_ref*V_cell, fields
+ * normalized by E0 = m_e c/(e*1fs) and B0 = m_e/(e*1fs).
+ */
+#ifndef PIC_ORACLE_H
+#define PIC_ORACLE_H
+#include <stdint.h>
+
+#define ORC_NS 5      /* subshells 1s 2s 2p 3s 3p */
+#define ORC_NZ 14     /* charge states 0..13 of Al */
+
+enum {
+    ORC_F_COLL_EE = 1, ORC_F_COLL_EI = 2, ORC_F_IONIZE = 4, ORC_F_RECOMB = 8,
+    ORC_F_PHOTO = 16, ORC_F_DECAY = 32, ORC_F_PUSH = 64, ORC_F_FIELD = 128
+};
+
+typedef struct {
+    int nx, ny;
+    double dx, dy, dt;
+    int rad_every;
+    uint64_t seed;
+    double cfl;
+    double n_ref;        /* cm^-3 */
+    double w_ion;        /* common ion weight */
+    double m_ion;        /* ion mass / m_e */
+    double E_bulk;       /* <= 0: all electrons are bulk */
+    int ipd_model;       /* 0 none, 1 Ecker-Kroll, 2 Stewart-Pyatt */
+    double coulomb_log;  /* <= 0: computed per cell */
+    unsigned flags;
+} orc_params;
+
+typedef struct {
+    double lotz_a[ORC_NS], lotz_b[ORC_NS], lotz_c[ORC_NS];
+    double E_bind[ORC_NZ][ORC_NS];
+    double tauK[ORC_NZ][2], omegaK[ORC_NZ][2], E_Ka[ORC_NZ];
+    int n_hv;
+    const double *hv_tab;     /* [n_hv] */
+    const double *sigma;      /* [ORC_NS][n_hv] cm^2 per electron */
+    int n_T, n_n;
+    const double *eos_T, *eos_n, *eos_Z;   /* eos_Z[n_n][n_T] */
+} orc_tables;
+
+typedef struct {
+    int shape;           /* 0 Gaussian, 1 flat-top */
+    double I_peak, fwhm, t_peak, hv, bandwidth;
+    int n_bins;
+    double spot_sigma;   /* nm, <= 0 uniform */
+} orc_pulse;
+
+/* energy tallies (weighted eV, units n_ref*V_cell) and event counters */
+enum { ORC_T_KE_E, ORC_T_KE_I, ORC_T_ION, ORC_T_PHOT, ORC_T_INC, ORC_T_TRANS,
+       ORC_T_KA_ESC, ORC_T_ESC, ORC_T_FIELD, ORC_NT };
+enum { ORC_C_ION, ORC_C_ION_REJ, ORC_C_REC, ORC_C_PH0, ORC_C_PH1, ORC_C_PH2,
+       ORC_C_PH3, ORC_C_PH4, ORC_C_PART, ORC_C_AUG, ORC_C_KA, ORC_C_PGT1,
+       ORC_C_ESC_E, ORC_C_ESC_I, ORC_C_EE, ORC_C_EI, ORC_NC };
+
+typedef struct orc_slab orc_slab;
+
+orc_slab *orc_create(const orc_params *p, const orc_tables *t);
+void orc_destroy(orc_slab *s);
+void orc_set_pulse(orc_slab *s, const orc_pulse *pl);
+void orc_set_step(orc_slab *s, uint32_t n);
+uint32_t orc_get_step(const orc_slab *s);
+void orc_load_electrons(orc_slab *s, int n, const double *X, const double *Y,
+                        const double *u, const double *w, const uint64_t *id);
+void orc_load_ions(orc_slab *s, int n, const double *X, const double *Y,
+                   const double *u, const double *zf, const int32_t *Z,
+                   const int32_t *nK, const uint32_t *id);
+int orc_n_electrons(const orc_slab *s);
+int orc_n_ions(const orc_slab *s);
+void orc_get_electrons(const orc_slab *s, double *X, double *Y, double *u,
+                       double *w, uint64_t *id);
+void orc_get_ions(const orc_slab *s, double *X, double *Y, double *u,
+                  double *zf, int32_t *Z, int32_t *nK, uint32_t *id);
+void orc_set_fields(orc_slab *s, const double *f6);   /* [6][ny][nx+1] */
+void orc_get_fields(const orc_slab *s, double *f6);
+void orc_get_current(const orc_slab *s, double *j3);  /* [3][ny][nx+1] */
+void orc_set_photons(orc_slab *s, const double *ph);  /* [ny][nx][nb] */
+void orc_get_photons(const orc_slab *s, double *ph);
+void orc_step(orc_slab *s, int nsteps, int nthreads);
+void orc_tallies(orc_slab *s, double *t, uint64_t *c);
+void orc_diag(const orc_slab *s, double *csd, int n_E, double E_max, double *eedf);
+
+/* building blocks exposed for the closed-form and invariant pins */
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+double orc_u01(uint32_t x);
+int orc_occ(int nb, int nk, int occ[ORC_NS]);
+double orc_ipd(int model, int z, double n_e, double n_i, double T_e, double zbar);
+double orc_lotz(const orc_tables *t, int z, double dE, double E);
+double orc_coulomb_log(double n_e, double T_e, double zbar);
+int orc_collide(double ua[3], double ub[3], double ma, double mb, double qa,
+                double qb, double wa, double wb, double n_l, double lnL,
+                double dtc, const double r[4]);
+void orc_boris(double u[3], const double e[3], const double b[3], double qm, double dt);
+void orc_pair_order(int n, const uint64_t *id, uint32_t step, uint32_t purpose,
+                    uint64_t seed, int *perm);
+int orc_ee_pairs(int n, int *pa, int *pb, double *frac);
+void orc_deposit(int nx, int ny, double dx, double dy, double dt, double X0,
+                 double Y0, double X1, double Y1, double vz_nmfs, double vy_nmfs,
+                 double qw, double *j3);
+void orc_rho(int nx, int ny, double X, double Y, double qw, double *rho);
+double orc_eos(const orc_tables *t, double n_i, double T_e);
+
+#endif

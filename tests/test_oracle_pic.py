@@ -1,0 +1,169 @@
+"""Pins of the oracle's push / deposit / field step (CPU only).
+
+The paper's PICLS is a PIC code (Sec. I, VI: absorbing boundaries, sheath
+fields) but prints none of its particle or field algorithms; the oracle
+uses a relativistic Boris push, Esirkepov's charge-conserving deposit with
+linear shapes and a subcycled Yee solver with first-order Mur boundaries.
+Pinned by: the discrete continuity equation, Gauss's law carried by the
+solver, the cold plasma frequency, exact vacuum propagation at the magic
+time step, and determinism across thread counts.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import pic_inputs as P
+
+C_NM_FS = 299.792458
+
+
+def _div_j(j3, dx, dy, ny):
+    jx, jy = j3[0], j3[1]
+    d = np.zeros_like(jx)
+    d[:, 1:] += (jx[:, 1:] - jx[:, :-1]) / dx
+    d[:, 0] += jx[:, 0] / dx
+    if ny > 1:
+        d += (jy - np.roll(jy, 1, axis=0)) / dy
+    return d
+
+
+@pytest.mark.parametrize("ny", [1, 6])
+def test_deposit_continuity(ny):
+    """(rho1 - rho0)/dt + div J = 0 node by node, including moves longer
+    than a cell (split into sub-cell segments)."""
+    rng = np.random.default_rng(11)
+    nx, dx, dy, dt = 24, 2.0, 3.0, 0.02
+    j3 = np.zeros((3, ny, nx + 1))
+    r0 = np.zeros((ny, nx + 1))
+    r1 = np.zeros((ny, nx + 1))
+    for _ in range(400):
+        X0 = rng.uniform(6, nx - 6)
+        Y0 = rng.uniform(0, ny) if ny > 1 else 0.5
+        step = rng.uniform(-2.6, 2.6, 2) * (rng.random() < 0.3) + rng.uniform(-0.9, 0.9, 2)
+        X1 = X0 + step[0]
+        Y1 = Y0 + (step[1] if ny > 1 else 0.0)
+        qw = rng.uniform(-1, 1)
+        oracle.deposit(nx, ny, dx, dy, dt, X0, Y0, X1, Y1, 0.3, 0.2, qw, j3)
+        oracle.rho(nx, ny, X0, Y0, qw, r0)
+        Y1w = Y1 % ny if ny > 1 else Y1
+        oracle.rho(nx, ny, X1, Y1w, qw, r1)
+    res = (r1 - r0) / dt + _div_j(j3, dx, dy, ny)
+    assert np.abs(res).max() < 1e-10 * np.abs(r1 - r0).max() / dt
+
+
+def _kappa(n_ref_cm3):
+    qe, eps0, me, c = 1.602176634e-19, 8.8541878128e-12, 9.1093837015e-31, 299792458.0
+    E0 = me * c / (qe * 1e-15)
+    return qe * n_ref_cm3 * 1e6 * 1e-9 / (eps0 * E0)
+
+
+def test_gauss_law_carried_by_solver():
+    """Starting from zero fields, the interior divergence of E tracks the
+    deposited charge: div e = kappa (rho(t) - rho(0)) at every interior node
+    after many push + deposit + field steps (2D)."""
+    cfg = P.cfg_small_1d(flags=P.F_PUSH | P.F_FIELD, nx=20, ny=8, dx_nm=2.0, dy_nm=2.0,
+                         ppc_e=16, ppc_i=4, T_e_eV=50.0, beam_frac=0.0)
+    st = P.init_particles(cfg)
+    o = oracle.OracleSlab(cfg, P.standin_tables())
+    o.load(st)
+
+    def rho():
+        r = np.zeros((cfg.ny, cfg.nx + 1))
+        e, i = o.electrons(), o.ions()
+        for X, Y, w in zip(e["X"], e["Y"], e["w"]):
+            oracle.rho(cfg.nx, cfg.ny, X, Y, -w, r)
+        for X, Y, Z, zf in zip(i["X"], i["Y"], i["Z"], i["zf"]):
+            oracle.rho(cfg.nx, cfg.ny, X, Y, (Z + zf) * cfg.w_ion, r)
+        return r
+
+    r0 = rho()
+    o.step(15)
+    r1 = rho()
+    f = o.fields()
+    ex, ey = f["ex"], f["ey"]
+    div = np.zeros_like(ex)
+    div[:, 1:] = (ex[:, 1:] - ex[:, :-1]) / cfg.dx_nm
+    div += (ey - np.roll(ey, 1, axis=0)) / cfg.dy_nm
+    k = _kappa(cfg.n_ref_cm3)
+    inner = slice(3, cfg.nx - 2)
+    lhs = div[:, inner]
+    rhs = k * (r1 - r0)[:, inner]
+    assert np.abs(rhs).max() > 0
+    assert np.abs(lhs - rhs).max() < 1e-9 * np.abs(rhs).max()
+
+
+def test_cold_plasma_frequency():
+    """A cold electron fluid displaced sinusoidally oscillates at
+    omega_pe = sqrt(n_e e^2 / (eps0 m_e)) (leapfrog shift negligible here),
+    within 2 %."""
+    cfg = P.cfg_small_1d(flags=P.F_PUSH | P.F_FIELD, nx=64, T_e_eV=0.0, T_i_eV=0.0,
+                         beam_frac=0.0, dt_fs=0.005, ppc_e=64, ppc_i=16)
+    st = P.init_particles(cfg)
+    st.eu[:, 0] = 1e-5 * np.sin(2 * np.pi * st.eX / cfg.nx)
+    o = oracle.OracleSlab(cfg, P.standin_tables())
+    o.load(st)
+    n = 1200
+    sig = np.zeros(n)
+    for k in range(n):
+        o.step(1)
+        sig[k] = o.fields()["ex"][0, cfg.nx // 4]
+    t = (np.arange(n) + 1) * cfg.dt_fs
+    # zero crossings of Ex at one node
+    s = np.sign(sig)
+    idx = np.where(s[:-1] * s[1:] < 0)[0]
+    tz = t[idx] - sig[idx] * cfg.dt_fs / (sig[idx + 1] - sig[idx])
+    w_meas = math.pi / np.mean(np.diff(tz))
+    qe, eps0, me = 1.602176634e-19, 8.8541878128e-12, 9.1093837015e-31
+    ne = cfg.Z_init * cfg.n_ref_cm3 * 1e6
+    w_pe = math.sqrt(ne * qe * qe / (eps0 * me)) * 1e-15
+    assert abs(w_meas / w_pe - 1) < 0.02
+
+
+def test_vacuum_pulse_magic_step_and_mur():
+    """1D vacuum: at c dt_f = dx the Yee scheme moves a pulse by exactly one
+    cell per subcycle, and first-order Mur lets it leave without
+    reflection."""
+    dx = 2.0
+    cfg = P.cfg_small_1d(flags=P.F_FIELD, nx=200, dx_nm=dx, dt_fs=2 * dx / C_NM_FS, cfl=1.0,
+                         ppc_e=1, ppc_i=1, beam_frac=0.0)
+    o = oracle.OracleSlab(cfg, P.standin_tables())
+    st = P.init_particles(cfg)
+    st.eX = st.eX[:0]; st.eY = st.eY[:0]; st.eu = st.eu[:0]; st.ew = st.ew[:0]; st.eid = st.eid[:0]
+    st.iX = st.iX[:0]; st.iY = st.iY[:0]; st.iu = st.iu[:0]; st.izf = st.izf[:0]
+    st.iZ = st.iZ[:0]; st.inK = st.inK[:0]; st.iid = st.iid[:0]
+    o.load(st)
+    x_node = np.arange(cfg.nx + 1)
+    x_half = x_node + 0.5
+    f = {k: np.zeros((1, cfg.nx + 1)) for k in ("ex", "ey", "ez", "bx", "by", "bz")}
+    x0, w = 60.0, 6.0
+    f["ey"][0] = np.exp(-((x_node - x0) / w) ** 2)
+    # Bz one half cell ahead in space and half a subcycle in time
+    f["bz"][0] = np.exp(-((x_half - 0.5 - x0) / w) ** 2)
+    f["bz"][0, -1] = 0.0
+    o.set_fields(f)
+    e0 = (f["ey"] ** 2).sum()
+    o.step(30)                      # 60 subcycles: 60 cells
+    ey = o.fields()["ey"][0]
+    assert abs(np.argmax(ey) - (x0 + 60)) <= 1
+    o.step(100)
+    f1 = o.fields()
+    left = sum((f1[k] ** 2).sum() for k in f1)
+    assert left < 1e-6 * e0
+
+
+def test_oracle_deterministic_across_threads(tables):
+    cfg = P.cfg_small_1d(nx=32, flags=P.F_ALL, rad_every=2)
+    pl = P.Pulse(I_peak_Wcm2=5e16, fwhm_fs=20.0, t_peak_fs=0.0, hv_eV=1700.0)
+    st = P.init_particles(cfg)
+    outs = []
+    for th in (1, 4):
+        o = oracle.OracleSlab(cfg, tables, pl)
+        o.load(st)
+        o.step(12, threads=th)
+        e = o.electrons()
+        outs.append((e["u"].copy(), e["id"].copy(), o.fields()["ex"].copy()))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert np.array_equal(outs[0][2], outs[1][2])
