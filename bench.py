@@ -1,0 +1,268 @@
+"""Benchmark: collided particle-steps/s of the GB300 collisional-PIC step.
+
+Workload: the 2D XFEL-driven Al foil, 2048 x 256 cells of 5 nm, 64
+electrons + 16 Al3+ per cell (41.9 M macroparticles), 1.6 keV / 80 fs /
+1e17 W/cm^2 pulse, every process on, FP32 particle state with FP64 cell
+sums.  A step is one pass of the whole hot path (march, sort, collisions,
+atomic processes, push, deposit, fields) over the slab.
+
+value: particle-steps/s with the state resident in HBM (device-timed with
+CUDA events on the context stream, K steps between a synchronize on each
+side).  e2e: the same metric through the public API with host buffers:
+the H2D load of the initial state and a D2H diagnostics read every step
+inside the timed region.  The state (1.3 GB) is far larger than L2.
+
+--impl reference: the FP64 oracle on the host cores, on a bounded sample
+of the same workload (a 64 x 64-cell patch of the foil).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import pic_inputs as P  # noqa: E402
+
+METRIC = "collided particle-steps/s"
+UNIT = "particle-steps/s"
+# algorithmic bytes per particle of the per-cell kernel: the 32 B record
+# read and written once, plus the 4 B next-cell key
+CELL_BYTES_PER_PARTICLE = 68
+# whole step: cell kernel 68 B + scatter (36 B read, 32 B written)
+STEP_BYTES_PER_PARTICLE = 136
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            return float(d.get("hbm_gbs") or d.get("hbm_GBps") or 6800.0), "measured"
+        except Exception:
+            pass
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self):
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-i", "0", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons)}
+
+
+def workload():
+    cfg = P.cfg_foil_2d()
+    pl = P.pulse_foil_2d()
+    return cfg, pl
+
+
+def cpu_baseline(steps=3, patch=64):
+    """The oracle as it stands on a 64 x 64-cell patch of the foil."""
+    import oracle
+    cfg, pl = workload()
+    sub = P.SlabConfig(**{**cfg.to_dict(), "nx": patch, "ny": patch})
+    st = P.init_particles(sub)
+    o = oracle.OracleSlab(sub, P.standin_tables(), pl)
+    o.load(st)
+    o.step(1)
+    n = st.n_e + st.n_i
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    cores = os.cpu_count()
+    return {"value": n * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{patch}x{patch}-cell patch of the foil ({n} particles), {steps} steps after 1 warm-up, "
+                      f"OpenMP over cells"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cfg, _ = workload()
+    vals = []
+    for _ in range(max(1, args.warmup)):
+        cpu_baseline(steps=1)
+    cb = None
+    for _ in range(args.steps):
+        cb = cpu_baseline(steps=2)
+        vals.append(cb["value"])
+    v = statistics.median(vals)
+    cb["value"] = v
+    out = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "impl": "reference", "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": cfg.name, "sample": cb["sample"]},
+           "cpu_baseline": cb,
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def run_gpu(args):
+    import torch
+    import paper_1704_01202_gb300 as pkg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    pkg.build()
+    cfg, pl = workload()
+    # replicas: every rank runs its own foil with its own seed
+    cfg.seed = cfg.seed + rank
+    tab = P.standin_tables()
+    st = P.init_particles(cfg)
+    n0 = st.n_e + st.n_i
+    slab = pkg.Slab(cfg, tab, pl)
+    slab.load(st)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        slab.step(1)
+    slab.sync()
+    ne0, ni0 = slab.counts()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler()
+    clocks.start()
+    slab.timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    slab.step(args.steps)
+    launches = slab.launches
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    tms, nrec = slab.timing(None)
+    slab.timing(False)
+    ne1, ni1 = slab.counts()
+    n_mean = 0.5 * (ne0 + ni0 + ne1 + ni1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n_mean * args.steps / (ms * 1e-3)
+
+    # dominant kernel roofline: the per-cell kernel
+    peak, peak_kind = measured_peaks()
+    cell_ms = tms["cell"] / max(nrec, 1)
+    achieved = CELL_BYTES_PER_PARTICLE * n_mean / (cell_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "k_cell", "peak_source": peak_kind,
+            "bytes_per_particle": CELL_BYTES_PER_PARTICLE, "kernel_ms_per_step": cell_ms,
+            "share_of_step": tms["cell"] / max(tms["step"], 1e-9)}
+    step_gbs = STEP_BYTES_PER_PARTICLE * n_mean / (ms / args.steps * 1e-3) / 1e9
+
+    # end to end through the public API with host buffers
+    slab.close()
+    del slab
+    torch.cuda.synchronize()
+    e2e_steps = max(3, min(args.steps, 10))
+    t0 = time.perf_counter()
+    s2 = pkg.Slab(cfg, tab, pl)
+    s2.load(st)
+    d2h = 0
+    for _ in range(e2e_steps):
+        s2.step(1)
+        d = s2.diagnostics(n_E=64)
+        d2h += (pkg.NZ + 64) * 8 + 16 * 8 + 20 * 8
+    t_e2e = time.perf_counter() - t0
+    h2d = st.n_e * (8 + 8 + 12 + 4 + 8) + st.n_i * (8 + 8 + 12 + 4 + 4 + 4 + 4)
+    s2.close()
+    e2e = {"value": world * n0 * e2e_steps / t_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": int(h2d / e2e_steps), "d2h_bytes_per_step": int(d2h / e2e_steps),
+           "steps": e2e_steps, "includes": "context creation, H2D load of the initial state, "
+                                          "per-step diagnostics D2H"}
+    if dist:
+        dist.barrier()
+    if rank == 0:
+        cb = cpu_baseline() if world == 1 and not args.no_cpu else None
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": cfg.name, "cells": [cfg.nx, cfg.ny], "particles": int(n_mean),
+                          "ppc": [cfg.ppc_e, cfg.ppc_i], "pulse_keV": pl.hv_eV / 1e3,
+                          "l2": "state (1.3 GB) larger than L2; no flush", "parallelism": "replicas"},
+               "roofline": roof, "step_hbm_gbs": step_gbs, "cpu_baseline": cb, "e2e": e2e,
+               "gpu_launches": int(launches), "clocks": clk}
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "gb300" else args.warmup
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/* C ABI of the GB300 collisional-PIC step for XFEL-heated solid Al
+ * (Royle, Sentoku, Mancini, Paraschiv, Johzaki: "Kinetic modeling of x-ray
+ * laser-driven solid Al plasmas via particle-in-cell simulation", PICLS).
+ *
+ * One context owns one or more independent slabs ("batched" mode) on one
+ * GPU.  Every step of the hot path runs in CUDA kernels: counting sort by
+ * cell, per-cell random pairing and binary Coulomb scattering (Sec. IV),
+ * Lotz impact ionization (Sec. IV, Eq. 3), EOS-clamped three-body
+ * recombination (Sec. IV), subshell photoionization (Sec. III, Eq. 2) with
+ * partial events, K-vacancy decay with KLL-Auger / K-alpha branching
+ * (Sec. III), continuum lowering (Sec. V, Eqs. 4-5), ballistic march of the
+ * XFEL photons (Sec. II, reduced to attenuation along x), Boris push,
+ * charge-conserving deposit and a subcycled Yee field update.
+ *
+ * Units: lengths nm, times fs, energies eV, momenta u = gamma v / c,
+ * particle weights in units of n_ref * V_cell (n_ref = reference density),
+ * fields normalized by E0 = m_e c / (e * 1 fs) and B0 = m_e / (e * 1 fs).
+ * Positions passed across the ABI are absolute, in cell units
+ * (X in [0, nx), Y in [0, ny)).
+ *
+ * Errors: every call returns a pic_status; nothing aborts.  Device-side
+ * problems (cell overflow, capacity, numeric) latch an error word that the
+ * next synchronizing call (pic_sync, pic_diagnostics, pic_get_*) returns;
+ * pic_last_error gives a message.  A context is used by one host thread at
+ * a time.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pic_ctx pic_ctx;
+
+typedef enum {
+    PIC_OK = 0,
+    PIC_ERR_ARG = 1,        /* invalid argument or size */
+    PIC_ERR_OOM = 2,        /* device allocation failed / arena too small */
+    PIC_ERR_TABLE = 3,      /* atomic table malformed */
+    PIC_ERR_CUDA = 4,       /* a CUDA runtime call failed */
+    PIC_ERR_TIMEOUT = 5,    /* a bounded device wait gave up */
+    PIC_ERR_NUMERIC = 6,    /* NaN / negative energy detected on device */
+    PIC_ERR_STATE = 7,      /* call out of order (e.g. step before load) */
+    PIC_ERR_CAPACITY = 8    /* particle or per-cell capacity exceeded */
+} pic_status;
+
+/* process switches (bit flags) */
+enum {
+    PIC_F_COLL_EE = 1, PIC_F_COLL_EI = 2, PIC_F_IONIZE = 4, PIC_F_RECOMB = 8,
+    PIC_F_PHOTO = 16, PIC_F_DECAY = 32, PIC_F_PUSH = 64, PIC_F_FIELD = 128
+};
+enum { PIC_IPD_NONE = 0, PIC_IPD_EK = 1, PIC_IPD_SP = 2 };
+
+#define PIC_NSUB 5          /* subshells 1s 2s 2p 3s 3p */
+#define PIC_NZ 14           /* Al charge states 0..13 */
+#define PIC_MAX_BINS 8      /* photon energy bins */
+
+/* Grid of one slab (Sec. VI: PIC grid, dt_PIC, dt_rad = rad_every dt_PIC).
+ * ny == 1 is a 1D slab.  y is periodic; x boundaries absorb particles and
+ * fields (first-order Mur). */
+typedef struct {
+    int nx, ny;
+    double dx_nm, dy_nm;
+    double dt_fs;
+    int rad_every;          /* photon march / photoionization / decay period */
+    uint64_t seed;          /* Philox key of the slab */
+    double cfl;             /* field subcycle margin, c dt_f <= cfl * Yee limit */
+} pic_grid;
+
+/* Species and model switches of one slab.  Ions share one weight. */
+typedef struct {
+    double n_ref_cm3;       /* density unit of the weights */
+    double w_ion;           /* common ion weight */
+    double m_ion_me;        /* ion mass / electron mass */
+    double E_bulk_eV;       /* bulk threshold for T_e (Sec. II); <= 0: all */
+    int ipd_model;          /* PIC_IPD_* (Sec. V) */
+    double coulomb_log;     /* > 0: fixed; <= 0: computed per cell */
+    unsigned flags;         /* PIC_F_* */
+    int cap_e, cap_i;       /* particle capacity of the slab (0: 4x / 1x loaded) */
+} pic_species;
+
+/* Atomic data (Sec. III-V).  Copied at pic_init; the caller keeps its
+ * buffers.  E_bind[z][s]: binding of subshell s in charge state z (lowest-
+ * energy configuration); tauK / omegaK indexed [N_b][nK-1]; E_Kalpha[z];
+ * sigma_photo[s][n_hv] per electron in cm^2 on the grid hv_tab (eV);
+ * eos_Zbar[n_n][n_T] on grids eos_n (cm^-3) and eos_T (eV). */
+typedef struct {
+    double lotz_a[PIC_NSUB], lotz_b[PIC_NSUB], lotz_c[PIC_NSUB];
+    double E_bind[PIC_NZ][PIC_NSUB];
+    double tauK[PIC_NZ][2], omegaK[PIC_NZ][2], E_Kalpha[PIC_NZ];
+    int n_hv;
+    const double *hv_tab;
+    const double *sigma_photo;
+    int n_T, n_n;
+    const double *eos_T, *eos_n, *eos_Zbar;
+} pic_tables;
+
+/* XFEL pulse entering at x = 0 (Sec. VI): Gaussian (FWHM) or flat-top
+ * intensity, n_bins photon-energy bins across the bandwidth. */
+typedef struct {
+    int shape;              /* 0 Gaussian, 1 flat-top */
+    double I_peak_Wcm2, fwhm_fs, t_peak_fs, hv_eV, bandwidth_eV;
+    int n_bins;             /* 1..PIC_MAX_BINS */
+    double spot_sigma_nm;   /* Gaussian in y (2D); <= 0 uniform */
+} pic_pulse;
+
+/* Diagnostics of one slab (Sec. VI: charge-state distribution, electron
+ * energy distribution, transmission, T_e, Zbar, event counts).  Arrays
+ * are caller-allocated. */
+typedef struct {
+    double *csd;            /* [PIC_NZ], weighted ion fraction per charge */
+    double *eedf;           /* [n_E], electron weight fraction per log bin */
+    int n_E;                /* bins on 0.1 eV .. E_max (log) */
+    double E_max_eV;
+    double t_fs;
+    double transmission;    /* transmitted / incident photon energy so far */
+    double T_e_eV, n_e_cm3, Zbar;
+    /* energy bookkeeping, weighted eV (units n_ref V_cell) */
+    double ke_e, ke_i, e_ion, e_phot, e_inc, e_trans, e_ka_esc, e_esc, e_field;
+    /* event counters: impact ionization, rejected ionization, recombination,
+     * photoionization per subshell, partial photoionization, Auger,
+     * K-alpha, P > 1 warnings, escaped e / i, e-e and e-i collisions */
+    uint64_t counts[16];
+    int64_t n_e, n_i;
+} pic_diag;
+
+/* Bytes of device memory pic_init needs for this slab. */
+size_t pic_required_bytes(const pic_grid *g, const pic_species *s, int n_e_cap, int n_i_cap);
+
+/* Create a context for one slab.  arena/arena_bytes: caller-owned device
+ * memory (e.g. a torch tensor) of at least pic_required_bytes, or NULL to
+ * let the context allocate.  stream: cudaStream_t to run on (NULL: legacy
+ * default).  The context never frees a caller arena. */
+pic_status pic_init(pic_ctx **out, const pic_grid *g, const pic_species *s,
+                    const pic_tables *t, void *arena, size_t arena_bytes, void *stream);
+
+/* Set the XFEL pulse (Sec. III Eq. 2 inputs); may be called before any
+ * step.  Without a pulse photoionization sees no photons. */
+pic_status pic_source(pic_ctx *c, const pic_pulse *p);
+
+/* Load particles from host memory (absolute positions in cell units).
+ * u is [n][3]; ids must be unique per species.  Replaces any particles. */
+pic_status pic_load_electrons(pic_ctx *c, int64_t n, const double *X, const double *Y,
+                              const float *u, const float *w, const uint64_t *id);
+pic_status pic_load_ions(pic_ctx *c, int64_t n, const double *X, const double *Y,
+                         const float *u, const float *zfrac, const int32_t *Z,
+                         const int32_t *nK, const uint32_t *id);
+/* Photon field (photon number per cell and bin, units n_ref V_cell),
+ * [ny][nx][n_bins]; fields [6][ny][nx+1] (ex ey ez bx by bz). */
+pic_status pic_set_photons(pic_ctx *c, const double *ph);
+pic_status pic_set_fields(pic_ctx *c, const float *f6);
+
+/* Advance n PIC steps (asynchronous on the context stream). */
+pic_status pic_step(pic_ctx *c, int n);
+
+/* Wait for the stream; returns the latched device error, if any. */
+pic_status pic_sync(pic_ctx *c);
+
+/* Reductions on the device, small D2H copy; synchronizes. */
+pic_status pic_diagnostics(pic_ctx *c, pic_diag *out);
+
+/* Particle counts and copies back to host (synchronizes).  Arrays are
+ * caller-allocated with at least the counted length. */
+pic_status pic_counts(pic_ctx *c, int64_t *n_e, int64_t *n_i);
+pic_status pic_get_electrons(pic_ctx *c, double *X, double *Y, float *u, float *w, uint64_t *id);
+pic_status pic_get_ions(pic_ctx *c, double *X, double *Y, float *u, float *zfrac,
+                        int32_t *Z, int32_t *nK, uint32_t *id);
+pic_status pic_get_photons(pic_ctx *c, double *ph);
+pic_status pic_get_fields(pic_ctx *c, float *f6);
+/* Current density of the last step, [3][ny][nx+1], units e n_ref nm/fs. */
+pic_status pic_get_current(pic_ctx *c, double *j3);
+
+/* Kernel launches issued by the last pic_step call (for accounting). */
+int64_t pic_launch_count(const pic_ctx *c);
+
+/* Device timing of kernel groups with CUDA events on the context stream.
+ * enable = 1 starts recording (clearing earlier records), 0 stops.  With
+ * ms_out != NULL (5 doubles) the call synchronizes and returns the summed
+ * device time of the steps recorded so far: [0] the per-cell kernel (both
+ * passes), [1] photon march, [2] counting sort (scan + scatter), [3] field
+ * subcycles, [4] whole steps; *nsteps gets the number of steps. */
+pic_status pic_timing(pic_ctx *c, int enable, double *ms_out, int64_t *nsteps);
+
+pic_status pic_free(pic_ctx *c);
+const char *pic_last_error(const pic_ctx *c);
+
+/* Philox4x32-10 of the device path, for checking it against other
+ * implementations: out[4*i..] = philox(ctr[4*i..], key) for i < n. */
+pic_status pic_philox_check(const uint32_t *ctr, const uint32_t key[2], uint32_t *out, int n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,359 @@
+"""GB300 collisional-PIC step for XFEL-heated solid Al (Royle et al., PICLS).
+
+Thin Python binding of the C ABI in include/pic.h: argument marshalling
+only.  Every step of the simulation runs in the CUDA kernels of
+paper_1704_01202_gb300/csrc, compiled for sm_103a into
+paper_1704_01202_gb300/_build/libpicgb.so.  There is no CPU path: if the
+library or a GPU is missing, the calls raise.
+
+PyTorch provides the device memory (one uint8 arena tensor per context)
+and the CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "csrc")
+_BUILD = os.path.join(_HERE, "_build")
+LIB_PATH = os.path.join(_BUILD, "libpicgb.so")
+_INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
+ARCH = "-gencode=arch=compute_103a,code=sm_103a"
+
+_lock = threading.Lock()
+_lib = None
+
+NSUB, NZ, MAX_BINS = 5, 14, 8
+STATUS = {0: "PIC_OK", 1: "PIC_ERR_ARG", 2: "PIC_ERR_OOM", 3: "PIC_ERR_TABLE", 4: "PIC_ERR_CUDA",
+          5: "PIC_ERR_TIMEOUT", 6: "PIC_ERR_NUMERIC", 7: "PIC_ERR_STATE", 8: "PIC_ERR_CAPACITY"}
+COUNT_NAMES = ["ION", "ION_REJ", "REC", "PH0", "PH1", "PH2", "PH3", "PH4", "PART", "AUG", "KA",
+               "PGT1", "ESC_E", "ESC_I", "EE", "EI"]
+ABI_FUNCTIONS = ["pic_required_bytes", "pic_init", "pic_source", "pic_load_electrons", "pic_load_ions",
+                 "pic_set_photons", "pic_set_fields", "pic_step", "pic_sync", "pic_diagnostics",
+                 "pic_counts", "pic_get_electrons", "pic_get_ions", "pic_get_photons", "pic_get_fields",
+                 "pic_get_current", "pic_launch_count", "pic_free", "pic_last_error", "pic_philox_check",
+                 "pic_timing"]
+
+
+def _sources():
+    return sorted(os.path.join(_SRC, f) for f in os.listdir(_SRC) if f.endswith((".cu", ".cuh")))
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile the CUDA library for sm_103a (nvcc cross-compiles without a GPU)."""
+    srcs = _sources() + [os.path.join(_INCLUDE, "pic.h")]
+    if not force and os.path.exists(LIB_PATH) and \
+            os.path.getmtime(LIB_PATH) >= max(os.path.getmtime(s) for s in srcs):
+        return LIB_PATH
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = LIB_PATH + f".{os.getpid()}.tmp"
+    cmd = ["nvcc", ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
+           "-o", tmp, os.path.join(_SRC, "pic_api.cu")]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("nvcc failed:\n" + r.stderr[-4000:])
+    if verbose:
+        print(r.stderr)
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("dx_nm", C.c_double), ("dy_nm", C.c_double),
+                ("dt_fs", C.c_double), ("rad_every", C.c_int), ("seed", C.c_uint64), ("cfl", C.c_double)]
+
+
+class Species(C.Structure):
+    _fields_ = [("n_ref_cm3", C.c_double), ("w_ion", C.c_double), ("m_ion_me", C.c_double),
+                ("E_bulk_eV", C.c_double), ("ipd_model", C.c_int), ("coulomb_log", C.c_double),
+                ("flags", C.c_uint), ("cap_e", C.c_int), ("cap_i", C.c_int)]
+
+
+class Tables(C.Structure):
+    _fields_ = [("lotz_a", C.c_double * NSUB), ("lotz_b", C.c_double * NSUB), ("lotz_c", C.c_double * NSUB),
+                ("E_bind", (C.c_double * NSUB) * NZ), ("tauK", (C.c_double * 2) * NZ),
+                ("omegaK", (C.c_double * 2) * NZ), ("E_Kalpha", C.c_double * NZ),
+                ("n_hv", C.c_int), ("hv_tab", C.POINTER(C.c_double)), ("sigma_photo", C.POINTER(C.c_double)),
+                ("n_T", C.c_int), ("n_n", C.c_int), ("eos_T", C.POINTER(C.c_double)),
+                ("eos_n", C.POINTER(C.c_double)), ("eos_Zbar", C.POINTER(C.c_double))]
+
+
+class Pulse(C.Structure):
+    _fields_ = [("shape", C.c_int), ("I_peak_Wcm2", C.c_double), ("fwhm_fs", C.c_double),
+                ("t_peak_fs", C.c_double), ("hv_eV", C.c_double), ("bandwidth_eV", C.c_double),
+                ("n_bins", C.c_int), ("spot_sigma_nm", C.c_double)]
+
+
+class Diag(C.Structure):
+    _fields_ = [("csd", C.POINTER(C.c_double)), ("eedf", C.POINTER(C.c_double)), ("n_E", C.c_int),
+                ("E_max_eV", C.c_double), ("t_fs", C.c_double), ("transmission", C.c_double),
+                ("T_e_eV", C.c_double), ("n_e_cm3", C.c_double), ("Zbar", C.c_double),
+                ("ke_e", C.c_double), ("ke_i", C.c_double), ("e_ion", C.c_double), ("e_phot", C.c_double),
+                ("e_inc", C.c_double), ("e_trans", C.c_double), ("e_ka_esc", C.c_double),
+                ("e_esc", C.c_double), ("e_field", C.c_double), ("counts", C.c_uint64 * 16),
+                ("n_e", C.c_int64), ("n_i", C.c_int64)]
+
+
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_F = C.POINTER(C.c_float)
+
+
+def lib():
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"CUDA library missing: {LIB_PATH} (run __graft_entry__.build())")
+            L = C.CDLL(LIB_PATH)
+            L.pic_required_bytes.restype = C.c_size_t
+            L.pic_required_bytes.argtypes = [C.POINTER(Grid), C.POINTER(Species), C.c_int, C.c_int]
+            L.pic_init.argtypes = [C.POINTER(_P), C.POINTER(Grid), C.POINTER(Species), C.POINTER(Tables),
+                                   _P, C.c_size_t, _P]
+            L.pic_source.argtypes = [_P, C.POINTER(Pulse)]
+            L.pic_load_electrons.argtypes = [_P, C.c_int64, _D, _D, _F, _F, C.POINTER(C.c_uint64)]
+            L.pic_load_ions.argtypes = [_P, C.c_int64, _D, _D, _F, _F, C.POINTER(C.c_int32),
+                                        C.POINTER(C.c_int32), C.POINTER(C.c_uint32)]
+            L.pic_set_photons.argtypes = [_P, _D]
+            L.pic_set_fields.argtypes = [_P, _F]
+            L.pic_step.argtypes = [_P, C.c_int]
+            L.pic_sync.argtypes = [_P]
+            L.pic_diagnostics.argtypes = [_P, C.POINTER(Diag)]
+            L.pic_counts.argtypes = [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+            L.pic_get_electrons.argtypes = [_P, _D, _D, _F, _F, C.POINTER(C.c_uint64)]
+            L.pic_get_ions.argtypes = [_P, _D, _D, _F, _F, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                       C.POINTER(C.c_uint32)]
+            L.pic_get_photons.argtypes = [_P, _D]
+            L.pic_get_fields.argtypes = [_P, _F]
+            L.pic_get_current.argtypes = [_P, _D]
+            L.pic_launch_count.restype = C.c_int64
+            L.pic_launch_count.argtypes = [_P]
+            L.pic_free.argtypes = [_P]
+            L.pic_last_error.restype = C.c_char_p
+            L.pic_last_error.argtypes = [_P]
+            L.pic_philox_check.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
+                                           C.POINTER(C.c_uint32), C.c_int]
+            L.pic_timing.argtypes = [_P, C.c_int, _D, C.POINTER(C.c_int64)]
+            for name in ABI_FUNCTIONS:
+                if name not in ("pic_required_bytes", "pic_launch_count", "pic_last_error"):
+                    getattr(L, name).restype = C.c_int
+            _lib = L
+    return _lib
+
+
+class PicError(RuntimeError):
+    pass
+
+
+def _p(a, t=C.c_double):
+    return a.ctypes.data_as(C.POINTER(t))
+
+
+def _tables(tab: dict):
+    t = Tables()
+    for s in range(NSUB):
+        t.lotz_a[s] = float(tab["lotz_a"][s])
+        t.lotz_b[s] = float(tab["lotz_b"][s])
+        t.lotz_c[s] = float(tab["lotz_c"][s])
+    for z in range(NZ):
+        for s in range(NSUB):
+            t.E_bind[z][s] = float(tab["E_bind"][z, s])
+        for k in range(2):
+            t.tauK[z][k] = float(tab["tauK"][z, k])
+            t.omegaK[z][k] = float(tab["omegaK"][z, k])
+        t.E_Kalpha[z] = float(tab["E_Kalpha"][z])
+    keep = [np.ascontiguousarray(tab[k], dtype=np.float64)
+            for k in ("hv_tab", "sigma_photo", "eos_T", "eos_n", "eos_Zbar")]
+    t.n_hv = keep[0].size
+    t.hv_tab, t.sigma_photo = _p(keep[0]), _p(keep[1])
+    t.n_T, t.n_n = keep[2].size, keep[3].size
+    t.eos_T, t.eos_n, t.eos_Zbar = _p(keep[2]), _p(keep[3]), _p(keep[4])
+    return t, keep
+
+
+def pulse_struct(pl) -> Pulse:
+    return Pulse(shape=pl.shape, I_peak_Wcm2=pl.I_peak_Wcm2, fwhm_fs=pl.fwhm_fs, t_peak_fs=pl.t_peak_fs,
+                 hv_eV=pl.hv_eV, bandwidth_eV=pl.bandwidth_eV, n_bins=pl.n_bins, spot_sigma_nm=pl.spot_sigma_nm)
+
+
+def default_capacity(n_e: int, n_i: int, z_init: int, headroom: float = 1.3) -> tuple[int, int]:
+    """Electron capacity for every ion fully stripped (plus headroom)."""
+    cap_e = int((n_e + n_i * (13 - z_init)) * headroom) + 1024
+    return cap_e, n_i + 1024
+
+
+class Slab:
+    """One slab on the GPU, driven through the C ABI."""
+
+    def __init__(self, cfg, tables: dict, pulse=None, cap_e: int = 0, cap_i: int = 0,
+                 use_torch_arena: bool = True, stream=None):
+        self.L = lib()
+        self.cfg = cfg
+        self.grid = Grid(nx=cfg.nx, ny=cfg.ny, dx_nm=cfg.dx_nm, dy_nm=cfg.dy_nm, dt_fs=cfg.dt_fs,
+                         rad_every=cfg.rad_every, seed=cfg.seed, cfl=cfg.cfl)
+        if cap_e <= 0 or cap_i <= 0:
+            ce, ci = default_capacity(cfg.ncell * cfg.ppc_e, cfg.ncell * cfg.ppc_i, cfg.Z_init)
+            cap_e = cap_e if cap_e > 0 else ce
+            cap_i = cap_i if cap_i > 0 else ci
+        self.species = Species(n_ref_cm3=cfg.n_ref_cm3, w_ion=cfg.w_ion, m_ion_me=cfg.m_ion_me,
+                               E_bulk_eV=cfg.E_bulk_eV, ipd_model=cfg.ipd_model, coulomb_log=cfg.coulomb_log,
+                               flags=cfg.flags, cap_e=cap_e, cap_i=cap_i)
+        self._t, self._keep = _tables(tables)
+        self.arena = None
+        arena_ptr, arena_bytes = None, 0
+        stream_ptr = None
+        if use_torch_arena:
+            import torch
+            if not torch.cuda.is_available():
+                raise PicError("no CUDA device")
+            nbytes = self.L.pic_required_bytes(C.byref(self.grid), C.byref(self.species), 0, 0)
+            self.arena = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            arena_ptr, arena_bytes = self.arena.data_ptr(), nbytes
+            s = stream if stream is not None else torch.cuda.current_stream()
+            stream_ptr = s.cuda_stream
+        self.h = C.c_void_p()
+        st = self.L.pic_init(C.byref(self.h), C.byref(self.grid), C.byref(self.species), C.byref(self._t),
+                             arena_ptr, arena_bytes, stream_ptr)
+        if st != 0:
+            raise PicError(f"pic_init: {STATUS.get(st, st)}")
+        self.n_bins = 0
+        if pulse is not None:
+            self.set_pulse(pulse)
+
+    def _check(self, st, what):
+        if st != 0:
+            msg = self.L.pic_last_error(self.h).decode() if self.h else ""
+            raise PicError(f"{what}: {STATUS.get(st, st)} {msg}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.pic_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_pulse(self, pl):
+        self._check(self.L.pic_source(self.h, C.byref(pulse_struct(pl))), "pic_source")
+        self.n_bins = pl.n_bins
+
+    def load(self, st):
+        ex = np.ascontiguousarray(st.eX, dtype=np.float64)
+        ey = np.ascontiguousarray(st.eY, dtype=np.float64)
+        eu = np.ascontiguousarray(st.eu, dtype=np.float32)
+        ew = np.ascontiguousarray(st.ew, dtype=np.float32)
+        eid = np.ascontiguousarray(st.eid, dtype=np.uint64)
+        self._check(self.L.pic_load_electrons(self.h, ex.size, _p(ex), _p(ey), _p(eu, C.c_float), _p(ew, C.c_float),
+                                              _p(eid, C.c_uint64)), "pic_load_electrons")
+        ix = np.ascontiguousarray(st.iX, dtype=np.float64)
+        iy = np.ascontiguousarray(st.iY, dtype=np.float64)
+        iu = np.ascontiguousarray(st.iu, dtype=np.float32)
+        zf = np.ascontiguousarray(st.izf, dtype=np.float32)
+        Z = np.ascontiguousarray(st.iZ, dtype=np.int32)
+        nK = np.ascontiguousarray(st.inK, dtype=np.int32)
+        iid = np.ascontiguousarray(st.iid, dtype=np.uint32)
+        self._check(self.L.pic_load_ions(self.h, ix.size, _p(ix), _p(iy), _p(iu, C.c_float), _p(zf, C.c_float),
+                                         _p(Z, C.c_int32), _p(nK, C.c_int32), _p(iid, C.c_uint32)), "pic_load_ions")
+
+    def step(self, n=1):
+        self._check(self.L.pic_step(self.h, n), "pic_step")
+
+    def sync(self):
+        self._check(self.L.pic_sync(self.h), "pic_sync")
+
+    @property
+    def launches(self):
+        return self.L.pic_launch_count(self.h)
+
+    def timing(self, enable=None):
+        """Start (True) / stop (False) event timing; with None return the
+        summed device times {cell, march, sort, field, step} (ms) and the
+        number of recorded steps."""
+        if enable is not None:
+            self._check(self.L.pic_timing(self.h, 1 if enable else 0, None, None), "pic_timing")
+            return None
+        out = np.zeros(5)
+        n = C.c_int64()
+        self._check(self.L.pic_timing(self.h, -1, _p(out), C.byref(n)), "pic_timing")
+        return dict(zip(("cell", "march", "sort", "field", "step"), out)), n.value
+
+    def counts(self):
+        ne, ni = C.c_int64(), C.c_int64()
+        self._check(self.L.pic_counts(self.h, C.byref(ne), C.byref(ni)), "pic_counts")
+        return ne.value, ni.value
+
+    def electrons(self):
+        n, _ = self.counts()
+        X, Y = np.zeros(n), np.zeros(n)
+        u = np.zeros((n, 3), dtype=np.float32)
+        w = np.zeros(n, dtype=np.float32)
+        i = np.zeros(n, dtype=np.uint64)
+        self._check(self.L.pic_get_electrons(self.h, _p(X), _p(Y), _p(u, C.c_float), _p(w, C.c_float),
+                                             _p(i, C.c_uint64)), "pic_get_electrons")
+        return dict(X=X, Y=Y, u=u, w=w, id=i)
+
+    def ions(self):
+        _, n = self.counts()
+        X, Y = np.zeros(n), np.zeros(n)
+        u = np.zeros((n, 3), dtype=np.float32)
+        zf = np.zeros(n, dtype=np.float32)
+        Z = np.zeros(n, dtype=np.int32)
+        nK = np.zeros(n, dtype=np.int32)
+        i = np.zeros(n, dtype=np.uint32)
+        self._check(self.L.pic_get_ions(self.h, _p(X), _p(Y), _p(u, C.c_float), _p(zf, C.c_float),
+                                        _p(Z, C.c_int32), _p(nK, C.c_int32), _p(i, C.c_uint32)), "pic_get_ions")
+        return dict(X=X, Y=Y, u=u, zf=zf, Z=Z, nK=nK, id=i)
+
+    def set_photons(self, ph):
+        a = np.ascontiguousarray(ph, dtype=np.float64)
+        self._check(self.L.pic_set_photons(self.h, _p(a)), "pic_set_photons")
+
+    def photons(self):
+        a = np.zeros((self.cfg.ny, self.cfg.nx, max(self.n_bins, 1)))
+        self._check(self.L.pic_get_photons(self.h, _p(a)), "pic_get_photons")
+        return a
+
+    def set_fields(self, f: dict):
+        a = np.ascontiguousarray(np.stack([f[k] for k in ("ex", "ey", "ez", "bx", "by", "bz")]), dtype=np.float32)
+        self._check(self.L.pic_set_fields(self.h, _p(a, C.c_float)), "pic_set_fields")
+
+    def fields(self):
+        a = np.zeros((6, self.cfg.ny, self.cfg.nx + 1), dtype=np.float32)
+        self._check(self.L.pic_get_fields(self.h, _p(a, C.c_float)), "pic_get_fields")
+        return dict(zip(("ex", "ey", "ez", "bx", "by", "bz"), a))
+
+    def current(self):
+        a = np.zeros((3, self.cfg.ny, self.cfg.nx + 1))
+        self._check(self.L.pic_get_current(self.h, _p(a)), "pic_get_current")
+        return a
+
+    def diagnostics(self, n_E=64, E_max=1e4):
+        csd = np.zeros(NZ)
+        eedf = np.zeros(n_E)
+        d = Diag(csd=_p(csd), eedf=_p(eedf), n_E=n_E, E_max_eV=E_max)
+        self._check(self.L.pic_diagnostics(self.h, C.byref(d)), "pic_diagnostics")
+        out = {k: getattr(d, k) for k, _ in Diag._fields_ if k not in ("csd", "eedf", "counts")}
+        out["csd"] = csd
+        out["eedf"] = eedf
+        out["counts"] = dict(zip(COUNT_NAMES, (int(x) for x in d.counts)))
+        return out
+
+
+def philox_check(ctr: np.ndarray, key) -> np.ndarray:
+    """Device Philox4x32-10 outputs for counters ctr [n,4] and key (k0, k1)."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    o = np.zeros_like(c)
+    st = lib().pic_philox_check(_p(c, C.c_uint32), _p(k, C.c_uint32), _p(o, C.c_uint32), c.shape[0])
+    if st != 0:
+        raise PicError(f"pic_philox_check: {STATUS.get(st, st)}")
+    return o

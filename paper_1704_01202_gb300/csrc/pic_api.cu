@@ -1,0 +1,839 @@
+// Host side of the C ABI declared in include/pic.h: the context, its device
+// arena, the per-step launch sequence and the host <-> device copies.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pic.h"
+#include "pic_dev.cuh"
+#include "pic_cellk.cuh"
+#include "pic_grid.cuh"
+
+using namespace pic;
+
+namespace {
+
+constexpr int CNT_APPEND = 0, CNT_WORK = 1, CNT_WORK_BIG = 2, CNT_OVF = 3, CNT_ERR = 4, CNT_MAXE = 5,
+              CNT_MAXI = 6, CNT_NLOAD = 7, NCOUNTERS = 16;
+constexpr int BIG_CE = 2048, BIG_CI = 512;
+
+size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int next_pow2(int x)
+{
+    int p = 32;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+}  // namespace
+
+struct pic_ctx {
+    cudaStream_t stream = nullptr;
+    bool own_arena = false;
+    char *arena = nullptr;
+    size_t arena_bytes = 0, used = 0;
+    std::string err;
+
+    pic_grid grid{};
+    pic_species sp{};
+    SlabDev slab{};
+    int ncell = 0, npts = 0, nblk = 0;
+    int cap_e = 0, cap_i = 0;
+
+    float4 *eA0, *eA1, *eB0, *eB1;
+    float4 *iA0, *iA1, *iB0, *iB1;
+    int *ekey, *ikey;
+    int *csE[2], *csI[2];
+    int cur = 0;
+    int *cnt_e, *cnt_i, *fill_e, *fill_i, *bsum_e, *bsum_i;
+    int *counters, *ovf_list, *cell_slab, *pt_slab, *row_slab, *row_idx;
+    SlabDev *d_slab;
+    unsigned *d_steps;
+    SlabTally *d_tally;
+    Tables *d_tab;
+    EosTable *d_eos;
+    float *E[2], *B;
+    int ecur = 0;
+    unsigned long long *J;
+    double *photons, *diag_buf;
+
+    int cap_ce = 128, cap_ci = 32, cap_new = 96, wpc = 4;
+    size_t smem_main = 0, smem_big = 0;
+    int nsm = 0, grid_main = 0, grid_big = 0;
+    int64_t launches = 0;
+    bool loaded_e = false, loaded_i = false;
+    unsigned host_step = 0;
+    double fe_factor = 0.0;
+    std::vector<double> hv_tab, sigma;   // host copy of the photoionization table
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;         // 5 events per recorded step
+    size_t ev_used = 0;
+};
+
+namespace {
+
+pic_status fail(pic_ctx *c, pic_status st, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return st;
+}
+
+pic_status cuda_fail(pic_ctx *c, cudaError_t e, const char *where)
+{
+    return fail(c, PIC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call);     \
+    } while (0)
+
+template <class T>
+T *carve_arena(pic_ctx *c, size_t count)
+{
+    size_t b = al(count * sizeof(T));
+    if (c->arena && c->used + b > c->arena_bytes) return nullptr;
+    T *p = reinterpret_cast<T *>(c->arena + c->used);
+    c->used += b;
+    return p;
+}
+
+size_t arena_need(int ncell, int npts, int nblk, int cap_e, int cap_i)
+{
+    size_t b = 0;
+    b += 4 * al((size_t)cap_e * 16) + al((size_t)cap_e * 4);
+    b += 4 * al((size_t)cap_i * 16) + al((size_t)cap_i * 4);
+    b += 4 * al((size_t)(ncell + 1) * 4) + 4 * al((size_t)ncell * 4) + 2 * al((size_t)nblk * 4);
+    b += al(NCOUNTERS * 4) + al((size_t)ncell * 4) * 2;
+    b += al(sizeof(SlabDev)) + al(4) + al(sizeof(SlabTally)) + al(sizeof(Tables)) + al(sizeof(EosTable));
+    b += 3 * al((size_t)npts * 3 * 4) + al((size_t)npts * 3 * 8) + al((size_t)npts * 4);
+    b += 2 * al((size_t)1 << 20);                        // row lists
+    b += al((size_t)ncell * PIC_MAX_BINS * 8);
+    b += al((4 + NZ + 4096 + 8) * 8);
+    return b + 4096;
+}
+
+// photoionization cross section of the table at hv: log-log interpolation,
+// held constant beyond the table ends
+double sigma_table(const pic_ctx *c, int s, double hv)
+{
+    const int n = (int)c->hv_tab.size();
+    const double *g = c->hv_tab.data(), *v = c->sigma.data() + (size_t)s * n;
+    if (hv <= g[0]) return v[0];
+    if (hv >= g[n - 1]) return v[n - 1];
+    int lo = 0, hi = n - 1;
+    while (hi - lo > 1) { int m = (lo + hi) / 2; if (g[m] <= hv) lo = m; else hi = m; }
+    if (v[lo] <= 0.0 || v[lo + 1] <= 0.0) {
+        double f = (hv - g[lo]) / (g[lo + 1] - g[lo]);
+        return v[lo] + f * (v[lo + 1] - v[lo]);
+    }
+    double f = std::log(hv / g[lo]) / std::log(g[lo + 1] / g[lo]);
+    return std::exp(std::log(v[lo]) + f * std::log(v[lo + 1] / v[lo]));
+}
+
+pic_status configure_cell_launch(pic_ctx *c, int max_e, int max_i)
+{
+    int ce = next_pow2(std::max(64, (int)(max_e * 1.25) + 1));
+    int ci = next_pow2(std::max(32, (int)(max_i * 1.25) + 1));
+    ce = std::min(ce, 1024);
+    ci = std::min(ci, 256);
+    int cn = 3 * ci;
+    size_t per = warp_mem_bytes(ce, ci, cn);
+    int wpc = (int)std::min<size_t>(8, (200 * 1024) / per);
+    if (wpc < 1) wpc = 1;
+    c->cap_ce = ce; c->cap_ci = ci; c->cap_new = cn; c->wpc = wpc;
+    c->smem_main = per * wpc;
+    CK(cudaFuncSetAttribute(k_cell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max(c->smem_main, c->smem_big)));
+    int occ = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cell, wpc * 32, c->smem_main));
+    c->grid_main = std::max(1, occ) * c->nsm;
+    return PIC_OK;
+}
+
+CellArgs cell_args(pic_ctx *c, bool big)
+{
+    CellArgs a{};
+    a.e0 = c->eA0; a.e1 = c->eA1; a.ekey = c->ekey; a.cs_e = c->csE[c->cur];
+    a.i0 = c->iA0; a.i1 = c->iA1; a.ikey = c->ikey; a.cs_i = c->csI[c->cur];
+    a.cnt_e = c->cnt_e; a.cnt_i = c->cnt_i;
+    a.append = c->counters + CNT_APPEND;
+    a.cap_e = c->cap_e;
+    a.ncell = c->ncell;
+    a.cell_slab = c->cell_slab;
+    a.slabs = c->d_slab;
+    a.steps = c->d_steps;
+    a.tally = c->d_tally;
+    a.photons = c->photons;
+    a.fldE = c->E[c->ecur];
+    a.fldB = c->B;
+    a.npts = c->npts;
+    a.J = c->J;
+    a.tab = c->d_tab;
+    a.eos = c->d_eos;
+    a.err = c->counters + CNT_ERR;
+    if (!big) {
+        a.work = c->counters + CNT_WORK;
+        a.list = nullptr; a.n_list = nullptr;
+        a.ovf_list = c->ovf_list; a.ovf_count = c->counters + CNT_OVF;
+        a.cap_ce = c->cap_ce; a.cap_ci = c->cap_ci; a.cap_new = c->cap_new;
+    } else {
+        a.work = c->counters + CNT_WORK_BIG;
+        a.list = c->ovf_list; a.n_list = c->counters + CNT_OVF;
+        a.ovf_list = nullptr; a.ovf_count = nullptr;
+        a.cap_ce = BIG_CE; a.cap_ci = BIG_CI; a.cap_new = 3 * BIG_CI;
+    }
+    return a;
+}
+
+pic_status run_scan(pic_ctx *c, int species_mask, int dst)
+{
+    ScanArgs s{};
+    int k = 0;
+    if (species_mask & 1) { s.cnt[k] = c->cnt_e; s.cs[k] = c->csE[dst]; s.bsum[k] = c->bsum_e; s.maxc[k] = c->counters + CNT_MAXE; ++k; }
+    if (species_mask & 2) { s.cnt[k] = c->cnt_i; s.cs[k] = c->csI[dst]; s.bsum[k] = c->bsum_i; s.maxc[k] = c->counters + CNT_MAXI; ++k; }
+    s.n = c->ncell;
+    s.nblk = c->nblk;
+    dim3 g1(c->nblk, k);
+    k_scan_reduce<<<g1, SCAN_T, 0, c->stream>>>(s);
+    k_scan_blocks<<<dim3(1, k), SCAN_T, 0, c->stream>>>(s);
+    k_scan_final<<<g1, SCAN_T, 0, c->stream>>>(s);
+    c->launches += 3;
+    CK(cudaGetLastError());
+    return PIC_OK;
+}
+
+cudaEvent_t *timing_slot(pic_ctx *c)
+{
+    if (!c->timing) return nullptr;
+    if (c->ev_used + 5 > c->ev.size()) {
+        for (int k = 0; k < 5; ++k) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            c->ev.push_back(e);
+        }
+    }
+    cudaEvent_t *p = c->ev.data() + c->ev_used;
+    c->ev_used += 5;
+    return p;
+}
+
+pic_status launch_step(pic_ctx *c)
+{
+    cudaStream_t st = c->stream;
+    cudaEvent_t *ev = timing_slot(c);
+    if (ev) CK(cudaEventRecord(ev[0], st));
+    CK(cudaMemsetAsync(c->cnt_e, 0, sizeof(int) * 4 * (size_t)c->ncell, st));   // cnt_e cnt_i fill_e fill_i
+    CK(cudaMemsetAsync(c->counters, 0, sizeof(int) * 4, st));                      // append, work, work_big, ovf
+    CK(cudaMemsetAsync(c->counters + CNT_MAXE, 0, sizeof(int) * 2, st));
+    CK(cudaMemsetAsync(c->J, 0, sizeof(unsigned long long) * 3 * (size_t)c->npts, st));
+    if ((c->slab.flags & PIC_F_PHOTO) && c->slab.nb > 0) {
+        MarchArgs m{c->d_slab, c->d_steps, c->row_slab, c->row_idx, c->photons, c->d_tally};
+        k_march<<<c->grid.ny, 256, (size_t)c->grid.nx * 8, st>>>(m);
+        ++c->launches;
+    }
+    if (ev) CK(cudaEventRecord(ev[1], st));
+    CellArgs am = cell_args(c, false);
+    k_cell<<<c->grid_main, c->wpc * 32, c->smem_main, st>>>(am);
+    CellArgs ab = cell_args(c, true);
+    k_cell<<<c->grid_big, 32, c->smem_big, st>>>(ab);
+    c->launches += 2;
+    CK(cudaGetLastError());
+    if (ev) CK(cudaEventRecord(ev[2], st));
+    const int nxt = c->cur ^ 1;
+    pic_status r = run_scan(c, 3, nxt);
+    if (r != PIC_OK) return r;
+    int sgrid = c->nsm * 8;
+    ScatterArgs se{c->eA0, c->eA1, c->ekey, c->csE[c->cur] + c->ncell, c->counters + CNT_APPEND,
+                   c->csE[nxt], c->fill_e, c->eB0, c->eB1, c->cap_e};
+    k_scatter<<<sgrid, 256, 0, st>>>(se);
+    ScatterArgs si{c->iA0, c->iA1, c->ikey, c->csI[c->cur] + c->ncell, nullptr, c->csI[nxt], c->fill_i, c->iB0, c->iB1,
+                   c->cap_i};
+    k_scatter<<<sgrid, 256, 0, st>>>(si);
+    c->launches += 2;
+    if (ev) CK(cudaEventRecord(ev[3], st));
+    if (c->slab.flags & PIC_F_FIELD) {
+        FieldArgs f{};
+        f.slabs = c->d_slab; f.pt_slab = c->pt_slab; f.npts = c->npts; f.B = c->B; f.J = c->J;
+        int fg = std::min((c->npts + 255) / 256, c->nsm * 16);
+        for (int sub = 0; sub < c->slab.nsub; ++sub) {
+            f.sub = sub;
+            f.Ein = c->E[c->ecur]; f.Eout = c->E[c->ecur ^ 1];
+            k_b_half<<<fg, 256, 0, st>>>(f);
+            k_e_full<<<fg, 256, 0, st>>>(f);
+            c->ecur ^= 1;
+            f.Ein = c->E[c->ecur];
+            k_b_half<<<fg, 256, 0, st>>>(f);
+            c->launches += 3;
+        }
+    }
+    k_advance<<<1, 32, 0, st>>>(c->d_steps, 1);
+    ++c->launches;
+    CK(cudaGetLastError());
+    if (ev) CK(cudaEventRecord(ev[4], st));
+    std::swap(c->eA0, c->eB0); std::swap(c->eA1, c->eB1);
+    std::swap(c->iA0, c->iB0); std::swap(c->iA1, c->iB1);
+    c->cur = nxt;
+    ++c->host_step;
+    return PIC_OK;
+}
+
+pic_status read_device_error(pic_ctx *c)
+{
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, c->counters + CNT_ERR, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (e & ERR_CELL_OVERFLOW) return fail(c, PIC_ERR_CAPACITY, "a cell holds more particles than the large-cell pass can stage");
+    if (e & ERR_CAPACITY) return fail(c, PIC_ERR_CAPACITY, "electron capacity exceeded");
+    if (e & ERR_NEW_OVERFLOW) return fail(c, PIC_ERR_CAPACITY, "too many electrons created in one cell");
+    if (e & ERR_NUMERIC) return fail(c, PIC_ERR_NUMERIC, "numeric error on device");
+    return PIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t pic_required_bytes(const pic_grid *g, const pic_species *s, int n_e_cap, int n_i_cap)
+{
+    if (!g || !s || g->nx <= 0 || g->ny <= 0) return 0;
+    int ncell = g->nx * g->ny, npts = (g->nx + 1) * g->ny;
+    int nblk = (ncell + SCAN_TILE - 1) / SCAN_TILE;
+    int ce = n_e_cap > 0 ? n_e_cap : s->cap_e, ci = n_i_cap > 0 ? n_i_cap : s->cap_i;
+    return arena_need(ncell, npts, nblk, ce, ci);
+}
+
+pic_status pic_init(pic_ctx **out, const pic_grid *g, const pic_species *s, const pic_tables *t, void *arena,
+                    size_t arena_bytes, void *stream)
+{
+    if (!out || !g || !s || !t) return PIC_ERR_ARG;
+    *out = nullptr;
+    if (g->nx < 2 || g->ny < 1 || g->dx_nm <= 0 || g->dy_nm <= 0 || g->dt_fs <= 0 || g->cfl <= 0)
+        return PIC_ERR_ARG;
+    if ((long long)g->nx * g->ny > (1LL << 30)) return PIC_ERR_ARG;
+    if (s->cap_e <= 0 || s->cap_i <= 0 || s->w_ion <= 0 || s->m_ion_me <= 0 || s->n_ref_cm3 <= 0) return PIC_ERR_ARG;
+    if (g->nx > 8192) return PIC_ERR_ARG;
+    if (t->n_hv < 2 || !t->hv_tab || !t->sigma_photo || t->n_T < 1 || t->n_n < 1 || t->n_T > EOS_MAX_T ||
+        t->n_n > EOS_MAX_N || !t->eos_T || !t->eos_n || !t->eos_Zbar)
+        return PIC_ERR_TABLE;
+    pic_ctx *c = new pic_ctx();
+    c->stream = (cudaStream_t)stream;
+    c->grid = *g;
+    c->sp = *s;
+    c->ncell = g->nx * g->ny;
+    c->npts = (g->nx + 1) * g->ny;
+    c->nblk = (c->ncell + SCAN_TILE - 1) / SCAN_TILE;
+    c->cap_e = s->cap_e;
+    c->cap_i = s->cap_i;
+    c->hv_tab.assign(t->hv_tab, t->hv_tab + t->n_hv);
+    c->sigma.assign(t->sigma_photo, t->sigma_photo + (size_t)NS * t->n_hv);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) { pic_status r = cuda_fail(c, e, "device query"); delete c; return r; }
+
+    size_t need = arena_need(c->ncell, c->npts, c->nblk, c->cap_e, c->cap_i);
+    if (arena) {
+        if (arena_bytes < need) { delete c; return PIC_ERR_OOM; }
+        c->arena = (char *)arena;
+        c->arena_bytes = arena_bytes;
+    } else {
+        e = cudaMalloc((void **)&c->arena, need);
+        if (e != cudaSuccess) { delete c; return PIC_ERR_OOM; }
+        c->own_arena = true;
+        c->arena_bytes = need;
+    }
+    c->eA0 = carve_arena<float4>(c, c->cap_e); c->eA1 = carve_arena<float4>(c, c->cap_e);
+    c->eB0 = carve_arena<float4>(c, c->cap_e); c->eB1 = carve_arena<float4>(c, c->cap_e);
+    c->ekey = carve_arena<int>(c, c->cap_e);
+    c->iA0 = carve_arena<float4>(c, c->cap_i); c->iA1 = carve_arena<float4>(c, c->cap_i);
+    c->iB0 = carve_arena<float4>(c, c->cap_i); c->iB1 = carve_arena<float4>(c, c->cap_i);
+    c->ikey = carve_arena<int>(c, c->cap_i);
+    for (int k = 0; k < 2; ++k) { c->csE[k] = carve_arena<int>(c, c->ncell + 1); c->csI[k] = carve_arena<int>(c, c->ncell + 1); }
+    c->cnt_e = carve_arena<int>(c, 4 * (size_t)c->ncell);
+    c->cnt_i = c->cnt_e + c->ncell; c->fill_e = c->cnt_i + c->ncell; c->fill_i = c->fill_e + c->ncell;
+    carve_arena<int>(c, 0);
+    c->bsum_e = carve_arena<int>(c, c->nblk); c->bsum_i = carve_arena<int>(c, c->nblk);
+    c->counters = carve_arena<int>(c, NCOUNTERS);
+    c->ovf_list = carve_arena<int>(c, c->ncell);
+    c->cell_slab = carve_arena<int>(c, c->ncell);
+    c->d_slab = carve_arena<SlabDev>(c, 1);
+    c->d_steps = carve_arena<unsigned>(c, 1);
+    c->d_tally = carve_arena<SlabTally>(c, 1);
+    c->d_tab = carve_arena<Tables>(c, 1);
+    c->d_eos = carve_arena<EosTable>(c, 1);
+    c->E[0] = carve_arena<float>(c, 3 * (size_t)c->npts);
+    c->E[1] = carve_arena<float>(c, 3 * (size_t)c->npts);
+    c->B = carve_arena<float>(c, 3 * (size_t)c->npts);
+    c->J = carve_arena<unsigned long long>(c, 3 * (size_t)c->npts);
+    c->pt_slab = carve_arena<int>(c, c->npts);
+    c->row_slab = carve_arena<int>(c, 1 << 18);
+    c->row_idx = carve_arena<int>(c, 1 << 18);
+    c->photons = carve_arena<double>(c, (size_t)c->ncell * PIC_MAX_BINS);
+    c->diag_buf = carve_arena<double>(c, 4 + NZ + 4096 + 8);
+    if (!c->diag_buf) { pic_free(c); return PIC_ERR_OOM; }
+
+    // slab description
+    SlabDev &S = c->slab;
+    S.nx = g->nx; S.ny = g->ny; S.cell0 = 0; S.ncell = c->ncell; S.fld_off = 0; S.ph_off = 0; S.nb = 0;
+    S.rad_every = g->rad_every; S.flags = s->flags; S.ipd = s->ipd_model; S.shape = 0;
+    S.dx = (float)g->dx_nm; S.dy = (float)g->dy_nm; S.dt = (float)g->dt_fs;
+    S.w_ion = (float)s->w_ion; S.m_ion = (float)s->m_ion_me; S.E_bulk = (float)s->E_bulk_eV;
+    S.coulomb_log = (float)s->coulomb_log;
+    S.n_ref = s->n_ref_cm3;
+    const double E0 = kMeKg * kCms / (kQe * 1e-15);
+    S.kappa_J = kQe * s->n_ref_cm3 * 1e6 * 1e-9 / (kEps0 * E0);
+    c->fe_factor = kEps0 * E0 * E0 / (2.0 * s->n_ref_cm3 * 1e6 * kQe);
+    double inv = 1.0 / (g->dx_nm * g->dx_nm) + (g->ny > 1 ? 1.0 / (g->dy_nm * g->dy_nm) : 0.0);
+    S.nsub = std::max(1, (int)std::ceil(kCnmPerFs * g->dt_fs * std::sqrt(inv) / g->cfl));
+    double dtf = g->dt_fs / S.nsub;
+    S.mur = (float)((kCnmPerFs * dtf - g->dx_nm) / (kCnmPerFs * dtf + g->dx_nm));
+    S.seed = g->seed;
+
+    Tables T{};
+    for (int q = 0; q < NS; ++q) { T.lotz_a[q] = (float)t->lotz_a[q]; T.lotz_b[q] = (float)t->lotz_b[q]; T.lotz_c[q] = (float)t->lotz_c[q]; }
+    for (int z = 0; z < NZ; ++z) {
+        for (int q = 0; q < NS; ++q) T.E_bind[z][q] = (float)t->E_bind[z][q];
+        for (int k = 0; k < 2; ++k) { T.tauK[z][k] = (float)t->tauK[z][k]; T.omegaK[z][k] = (float)t->omegaK[z][k]; }
+        T.E_Ka[z] = (float)t->E_Kalpha[z];
+    }
+    EosTable *eos = new EosTable();
+    eos->n_T = t->n_T; eos->n_n = t->n_n;
+    for (int k = 0; k < t->n_T; ++k) eos->T[k] = (float)t->eos_T[k];
+    for (int k = 0; k < t->n_n; ++k) eos->n[k] = (float)t->eos_n[k];
+    for (int a = 0; a < t->n_n; ++a)
+        for (int b = 0; b < t->n_T; ++b) eos->Z[a * t->n_T + b] = (float)t->eos_Zbar[(size_t)a * t->n_T + b];
+    std::vector<int> rows(g->ny);
+    for (int k = 0; k < g->ny; ++k) rows[k] = k;
+    std::vector<int> zeros(g->ny, 0);
+    // the context keeps the table copies alive on the host until the copies finish
+    pic_status rs = PIC_OK;
+    do {
+        cudaStream_t st = c->stream;
+        if ((e = cudaMemcpyAsync(c->d_tab, &T, sizeof(Tables), cudaMemcpyHostToDevice, st))) break;
+        if ((e = cudaMemcpyAsync(c->d_eos, eos, sizeof(EosTable), cudaMemcpyHostToDevice, st))) break;
+        if ((e = cudaMemcpyAsync(c->d_slab, &S, sizeof(SlabDev), cudaMemcpyHostToDevice, st))) break;
+        if ((e = cudaMemsetAsync(c->d_steps, 0, sizeof(unsigned), st))) break;
+        if ((e = cudaMemsetAsync(c->d_tally, 0, sizeof(SlabTally), st))) break;
+        if ((e = cudaMemsetAsync(c->cell_slab, 0, sizeof(int) * c->ncell, st))) break;
+        if ((e = cudaMemsetAsync(c->pt_slab, 0, sizeof(int) * c->npts, st))) break;
+        if ((e = cudaMemcpyAsync(c->row_idx, rows.data(), sizeof(int) * g->ny, cudaMemcpyHostToDevice, st))) break;
+        if ((e = cudaMemcpyAsync(c->row_slab, zeros.data(), sizeof(int) * g->ny, cudaMemcpyHostToDevice, st))) break;
+        if ((e = cudaMemsetAsync(c->E[0], 0, sizeof(float) * 3 * (size_t)c->npts, st))) break;
+        if ((e = cudaMemsetAsync(c->E[1], 0, sizeof(float) * 3 * (size_t)c->npts, st))) break;
+        if ((e = cudaMemsetAsync(c->B, 0, sizeof(float) * 3 * (size_t)c->npts, st))) break;
+        if ((e = cudaMemsetAsync(c->photons, 0, sizeof(double) * (size_t)c->ncell * PIC_MAX_BINS, st))) break;
+        if ((e = cudaMemsetAsync(c->counters, 0, sizeof(int) * NCOUNTERS, st))) break;
+        for (int k = 0; k < 2; ++k) {
+            if ((e = cudaMemsetAsync(c->csE[k], 0, sizeof(int) * (c->ncell + 1), st))) break;
+            if ((e = cudaMemsetAsync(c->csI[k], 0, sizeof(int) * (c->ncell + 1), st))) break;
+        }
+        if (e) break;
+        e = cudaStreamSynchronize(st);
+    } while (0);
+    delete eos;
+    if (e != cudaSuccess) { rs = cuda_fail(c, e, "init copies"); pic_free(c); return rs; }
+    c->smem_big = warp_mem_bytes(BIG_CE, BIG_CI, 3 * BIG_CI);
+    c->grid_big = c->nsm;
+    e = cudaFuncSetAttribute(k_march, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8);
+    if (e != cudaSuccess) { rs = cuda_fail(c, e, "march attribute"); pic_free(c); return rs; }
+    if ((rs = configure_cell_launch(c, 128, 32)) != PIC_OK) { pic_free(c); return rs; }
+    *out = c;
+    return PIC_OK;
+}
+
+pic_status pic_source(pic_ctx *c, const pic_pulse *p)
+{
+    if (!c || !p) return PIC_ERR_ARG;
+    if (p->n_bins < 1 || p->n_bins > PIC_MAX_BINS || p->hv_eV <= 0 || p->fwhm_fs < 0 || p->bandwidth_eV < 0)
+        return fail(c, PIC_ERR_ARG, "pulse out of range");
+    SlabDev &S = c->slab;
+    S.nb = p->n_bins;
+    S.shape = p->shape;
+    S.I_peak = p->I_peak_Wcm2; S.fwhm = p->fwhm_fs; S.t_peak = p->t_peak_fs; S.spot_sigma = p->spot_sigma_nm;
+    S.bin_hw = (float)(0.5 * p->bandwidth_eV / p->n_bins);
+    for (int b = 0; b < PIC_MAX_BINS; ++b) {
+        double hv = b < p->n_bins ? p->hv_eV + p->bandwidth_eV * ((b + 0.5) / p->n_bins - 0.5) : 0.0;
+        S.hv_b[b] = (float)hv;
+        for (int q = 0; q < NS; ++q) S.sig_b[q][b] = b < p->n_bins ? (float)sigma_table(c, q, hv) : 0.0f;
+    }
+    CK(cudaMemcpyAsync(c->d_slab, &S, sizeof(SlabDev), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(c->photons, 0, sizeof(double) * (size_t)c->ncell * PIC_MAX_BINS, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
+namespace {
+
+// sort host-built records into the current (A) buffers of one species
+pic_status load_species(pic_ctx *c, bool electrons, int64_t n, const std::vector<float4> &p0,
+                        const std::vector<float4> &p1, const std::vector<int> &key)
+{
+    cudaStream_t st = c->stream;
+    float4 *s0 = electrons ? c->eB0 : c->iB0, *s1 = electrons ? c->eB1 : c->iB1;
+    float4 *d0 = electrons ? c->eA0 : c->iA0, *d1 = electrons ? c->eA1 : c->iA1;
+    int *k = electrons ? c->ekey : c->ikey;
+    int *cnt = electrons ? c->cnt_e : c->cnt_i, *fill = electrons ? c->fill_e : c->fill_i;
+    int nn = (int)n;
+    if (n > 0) {
+        CK(cudaMemcpyAsync(s0, p0.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(s1, p1.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(k, key.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    }
+    CK(cudaMemcpyAsync(c->counters + CNT_NLOAD, &nn, sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(cnt, 0, sizeof(int) * c->ncell, st));
+    CK(cudaMemsetAsync(fill, 0, sizeof(int) * c->ncell, st));
+    k_count<<<c->nsm * 4, 256, 0, st>>>(k, c->counters + CNT_NLOAD, cnt);
+    pic_status r = run_scan(c, electrons ? 1 : 2, c->cur);
+    if (r != PIC_OK) return r;
+    ScatterArgs sa{s0, s1, k, c->counters + CNT_NLOAD, nullptr, electrons ? c->csE[c->cur] : c->csI[c->cur], fill, d0, d1,
+                   electrons ? c->cap_e : c->cap_i};
+    k_scatter<<<c->nsm * 4, 256, 0, st>>>(sa);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    return PIC_OK;
+}
+
+pic_status locate(pic_ctx *c, double X, double Y, int &cell, float &xi, float &eta)
+{
+    double fx = std::floor(X), fy = c->grid.ny > 1 ? std::floor(Y) : 0.0;
+    if (!(fx >= 0 && fx < c->grid.nx && fy >= 0 && fy < c->grid.ny))
+        return fail(c, PIC_ERR_ARG, "particle position outside the slab");
+    cell = (int)fy * c->grid.nx + (int)fx;
+    xi = (float)(X - fx);
+    eta = c->grid.ny > 1 ? (float)(Y - fy) : (float)Y;
+    if (xi >= 1.0f) xi = 0.99999994f;
+    if (c->grid.ny > 1 && eta >= 1.0f) eta = 0.99999994f;
+    return PIC_OK;
+}
+
+}  // namespace
+
+pic_status pic_load_electrons(pic_ctx *c, int64_t n, const double *X, const double *Y, const float *u,
+                              const float *w, const uint64_t *id)
+{
+    if (!c || n < 0 || (n > 0 && (!X || !Y || !u || !w || !id))) return PIC_ERR_ARG;
+    if (n > c->cap_e) return fail(c, PIC_ERR_CAPACITY, "more electrons than the capacity");
+    std::vector<float4> p0(n), p1(n);
+    std::vector<int> key(n);
+    for (int64_t k = 0; k < n; ++k) {
+        int cell; float xi, eta;
+        pic_status r = locate(c, X[k], Y[k], cell, xi, eta);
+        if (r != PIC_OK) return r;
+        p0[k] = make_float4(xi, eta, u[3 * k], u[3 * k + 1]);
+        uint32_t lo = (uint32_t)id[k], hi = (uint32_t)(id[k] >> 32);
+        float flo, fhi;
+        std::memcpy(&flo, &lo, 4); std::memcpy(&fhi, &hi, 4);
+        p1[k] = make_float4(u[3 * k + 2], w[k], flo, fhi);
+        key[k] = cell;
+    }
+    pic_status r = load_species(c, true, n, p0, p1, key);
+    if (r == PIC_OK) c->loaded_e = true;
+    return r;
+}
+
+pic_status pic_load_ions(pic_ctx *c, int64_t n, const double *X, const double *Y, const float *u,
+                         const float *zfrac, const int32_t *Z, const int32_t *nK, const uint32_t *id)
+{
+    if (!c || n < 0 || (n > 0 && (!X || !Y || !u || !zfrac || !Z || !nK || !id))) return PIC_ERR_ARG;
+    if (n > c->cap_i) return fail(c, PIC_ERR_CAPACITY, "more ions than the capacity");
+    std::vector<float4> p0(n), p1(n);
+    std::vector<int> key(n);
+    for (int64_t k = 0; k < n; ++k) {
+        int cell; float xi, eta;
+        pic_status r = locate(c, X[k], Y[k], cell, xi, eta);
+        if (r != PIC_OK) return r;
+        if (Z[k] < 0 || Z[k] > ZNUC || nK[k] < 0 || nK[k] > 2) return fail(c, PIC_ERR_ARG, "ion state out of range");
+        int stv = Z[k] | (nK[k] << 8);
+        float fid, fst;
+        std::memcpy(&fid, &id[k], 4); std::memcpy(&fst, &stv, 4);
+        p0[k] = make_float4(xi, eta, u[3 * k], u[3 * k + 1]);
+        p1[k] = make_float4(u[3 * k + 2], zfrac[k], fid, fst);
+        key[k] = cell;
+    }
+    pic_status r = load_species(c, false, n, p0, p1, key);
+    if (r == PIC_OK) c->loaded_i = true;
+    return r;
+}
+
+pic_status pic_set_photons(pic_ctx *c, const double *ph)
+{
+    if (!c || !ph) return PIC_ERR_ARG;
+    if (c->slab.nb <= 0) return fail(c, PIC_ERR_STATE, "set a pulse first");
+    CK(cudaMemcpyAsync(c->photons, ph, sizeof(double) * (size_t)c->ncell * c->slab.nb, cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
+pic_status pic_set_fields(pic_ctx *c, const float *f6)
+{
+    if (!c || !f6) return PIC_ERR_ARG;
+    size_t n = (size_t)c->npts;
+    CK(cudaMemcpyAsync(c->E[c->ecur], f6, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->B, f6 + 3 * n, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
+pic_status pic_step(pic_ctx *c, int n)
+{
+    if (!c || n < 0) return PIC_ERR_ARG;
+    if (!c->loaded_e || !c->loaded_i) return fail(c, PIC_ERR_STATE, "load particles before stepping");
+    // size the per-warp staging for the largest cells seen so far
+    int mx[2] = {0, 0};
+    CK(cudaMemcpyAsync(mx, c->counters + CNT_MAXE, sizeof(int) * 2, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (mx[0] > 0 || mx[1] > 0) {
+        pic_status r = configure_cell_launch(c, mx[0], mx[1]);
+        if (r != PIC_OK) return r;
+    }
+    c->launches = 0;
+    for (int k = 0; k < n; ++k) {
+        pic_status r = launch_step(c);
+        if (r != PIC_OK) return r;
+    }
+    return PIC_OK;
+}
+
+pic_status pic_sync(pic_ctx *c)
+{
+    if (!c) return PIC_ERR_ARG;
+    CK(cudaStreamSynchronize(c->stream));
+    return read_device_error(c);
+}
+
+pic_status pic_counts(pic_ctx *c, int64_t *n_e, int64_t *n_i)
+{
+    if (!c) return PIC_ERR_ARG;
+    int ne = 0, ni = 0;
+    CK(cudaMemcpyAsync(&ne, c->csE[c->cur] + c->ncell, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&ni, c->csI[c->cur] + c->ncell, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (n_e) *n_e = ne;
+    if (n_i) *n_i = ni;
+    return read_device_error(c);
+}
+
+namespace {
+pic_status fetch(pic_ctx *c, bool electrons, std::vector<float4> &p0, std::vector<float4> &p1, std::vector<int> &cs)
+{
+    int64_t ne, ni;
+    pic_status r = pic_counts(c, &ne, &ni);
+    if (r != PIC_OK) return r;
+    int64_t n = electrons ? ne : ni;
+    p0.resize(n); p1.resize(n); cs.resize(c->ncell + 1);
+    if (n) {
+        CK(cudaMemcpyAsync(p0.data(), electrons ? c->eA0 : c->iA0, sizeof(float4) * n, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(p1.data(), electrons ? c->eA1 : c->iA1, sizeof(float4) * n, cudaMemcpyDeviceToHost, c->stream));
+    }
+    CK(cudaMemcpyAsync(cs.data(), electrons ? c->csE[c->cur] : c->csI[c->cur], sizeof(int) * (c->ncell + 1),
+                       cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+}  // namespace
+
+pic_status pic_get_electrons(pic_ctx *c, double *X, double *Y, float *u, float *w, uint64_t *id)
+{
+    if (!c) return PIC_ERR_ARG;
+    std::vector<float4> p0, p1;
+    std::vector<int> cs;
+    pic_status r = fetch(c, true, p0, p1, cs);
+    if (r != PIC_OK) return r;
+    for (int cell = 0; cell < c->ncell; ++cell) {
+        int cx = cell % c->grid.nx, cy = cell / c->grid.nx;
+        for (int k = cs[cell]; k < cs[cell + 1]; ++k) {
+            X[k] = cx + (double)p0[k].x;
+            Y[k] = c->grid.ny > 1 ? cy + (double)p0[k].y : (double)p0[k].y;
+            u[3 * k] = p0[k].z; u[3 * k + 1] = p0[k].w; u[3 * k + 2] = p1[k].x;
+            w[k] = p1[k].y;
+            uint32_t lo, hi;
+            std::memcpy(&lo, &p1[k].z, 4); std::memcpy(&hi, &p1[k].w, 4);
+            id[k] = ((uint64_t)hi << 32) | lo;
+        }
+    }
+    return PIC_OK;
+}
+
+pic_status pic_get_ions(pic_ctx *c, double *X, double *Y, float *u, float *zfrac, int32_t *Z, int32_t *nK,
+                        uint32_t *id)
+{
+    if (!c) return PIC_ERR_ARG;
+    std::vector<float4> p0, p1;
+    std::vector<int> cs;
+    pic_status r = fetch(c, false, p0, p1, cs);
+    if (r != PIC_OK) return r;
+    for (int cell = 0; cell < c->ncell; ++cell) {
+        int cx = cell % c->grid.nx, cy = cell / c->grid.nx;
+        for (int k = cs[cell]; k < cs[cell + 1]; ++k) {
+            X[k] = cx + (double)p0[k].x;
+            Y[k] = c->grid.ny > 1 ? cy + (double)p0[k].y : (double)p0[k].y;
+            u[3 * k] = p0[k].z; u[3 * k + 1] = p0[k].w; u[3 * k + 2] = p1[k].x;
+            zfrac[k] = p1[k].y;
+            uint32_t idv; int stv;
+            std::memcpy(&idv, &p1[k].z, 4); std::memcpy(&stv, &p1[k].w, 4);
+            id[k] = idv;
+            Z[k] = stv & 0xff;
+            nK[k] = (stv >> 8) & 0xff;
+        }
+    }
+    return PIC_OK;
+}
+
+pic_status pic_get_photons(pic_ctx *c, double *ph)
+{
+    if (!c || !ph) return PIC_ERR_ARG;
+    if (c->slab.nb <= 0) return fail(c, PIC_ERR_STATE, "no pulse set");
+    CK(cudaMemcpyAsync(ph, c->photons, sizeof(double) * (size_t)c->ncell * c->slab.nb, cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return read_device_error(c);
+}
+
+pic_status pic_get_fields(pic_ctx *c, float *f6)
+{
+    if (!c || !f6) return PIC_ERR_ARG;
+    size_t n = (size_t)c->npts;
+    CK(cudaMemcpyAsync(f6, c->E[c->ecur], sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(f6 + 3 * n, c->B, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return read_device_error(c);
+}
+
+pic_status pic_get_current(pic_ctx *c, double *j3)
+{
+    if (!c || !j3) return PIC_ERR_ARG;
+    size_t n = (size_t)c->npts;
+    std::vector<unsigned long long> raw(3 * n);
+    CK(cudaMemcpyAsync(raw.data(), c->J, sizeof(unsigned long long) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const double fix = 1.0 / 1099511627776.0;
+    const double sx = c->grid.dx_nm / c->grid.dt_fs;
+    const double sy = c->grid.ny > 1 ? c->grid.dy_nm / c->grid.dt_fs : kCnmPerFs;
+    for (size_t k = 0; k < n; ++k) {
+        j3[k] = (double)(long long)raw[k] * fix * sx;
+        j3[n + k] = (double)(long long)raw[n + k] * fix * sy;
+        j3[2 * n + k] = (double)(long long)raw[2 * n + k] * fix * kCnmPerFs;
+    }
+    return read_device_error(c);
+}
+
+pic_status pic_diagnostics(pic_ctx *c, pic_diag *out)
+{
+    if (!c || !out || out->n_E < 0 || out->n_E > 4096) return PIC_ERR_ARG;
+    cudaStream_t st = c->stream;
+    const int nE = out->n_E > 0 ? out->n_E : 1;
+    const int nv = 4 + NZ + nE;
+    CK(cudaMemsetAsync(c->diag_buf, 0, sizeof(double) * (nv + 3), st));
+    DiagArgs d{};
+    d.e0 = c->eA0; d.e1 = c->eA1; d.i0 = c->iA0; d.i1 = c->iA1;
+    d.n_e = c->csE[c->cur] + c->ncell; d.n_i = c->csI[c->cur] + c->ncell;
+    d.m_ion = c->sp.m_ion_me; d.out = c->diag_buf; d.n_E = nE; d.E_lo = 0.1;
+    d.E_max = out->E_max_eV > 0.1 ? out->E_max_eV : 1e4;
+    k_diag<<<c->nsm * 4, 256, sizeof(double) * nv, st>>>(d);
+    k_sumsq<<<c->nsm * 4, 256, 0, st>>>(c->E[c->ecur], 3 * c->npts, c->diag_buf + nv);
+    k_sumsq<<<c->nsm * 4, 256, 0, st>>>(c->B, 3 * c->npts, c->diag_buf + nv);
+    if (c->slab.nb > 0) {
+        float *hv = reinterpret_cast<float *>(reinterpret_cast<char *>(c->d_slab) + offsetof(SlabDev, hv_b));
+        k_photon_energy<<<c->nsm * 4, 256, 0, st>>>(c->photons, c->ncell, c->slab.nb, hv, c->diag_buf + nv + 1);
+    }
+    CK(cudaGetLastError());
+    std::vector<double> h(nv + 3);
+    SlabTally tl;
+    unsigned step = 0;
+    int64_t ne = 0, ni = 0;
+    CK(cudaMemcpyAsync(h.data(), c->diag_buf, sizeof(double) * (nv + 3), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&tl, c->d_tally, sizeof(SlabTally), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&step, c->d_steps, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    pic_status r = pic_counts(c, &ne, &ni);
+    if (r != PIC_OK) return r;
+    const double We = h[0], Ke = h[1], Ki = h[2], Ni = h[3];
+    if (out->csd) for (int z = 0; z < NZ; ++z) out->csd[z] = Ni > 0 ? h[4 + z] / Ni : 0.0;
+    double zb = 0.0;
+    for (int z = 0; z < NZ; ++z) zb += z * (Ni > 0 ? h[4 + z] / Ni : 0.0);
+    if (out->eedf && out->n_E > 0) for (int b = 0; b < out->n_E; ++b) out->eedf[b] = We > 0 ? h[4 + NZ + b] / We : 0.0;
+    out->t_fs = step * c->grid.dt_fs;
+    out->transmission = tl.inc > 0 ? tl.trans / tl.inc : 0.0;
+    out->T_e_eV = We > 0 ? (2.0 / 3.0) * Ke / We : 0.0;
+    out->n_e_cm3 = We * c->sp.n_ref_cm3 / c->ncell;
+    out->Zbar = zb;
+    out->ke_e = Ke;
+    out->ke_i = Ki * c->sp.w_ion;
+    out->e_ion = tl.ion;
+    out->e_phot = h[nv + 1];
+    out->e_inc = tl.inc;
+    out->e_trans = tl.trans;
+    out->e_ka_esc = tl.ka_esc;
+    out->e_esc = tl.esc;
+    out->e_field = h[nv] * c->fe_factor;
+    for (int q = 0; q < 16; ++q) out->counts[q] = tl.cnt[q];
+    out->n_e = ne;
+    out->n_i = ni;
+    return read_device_error(c);
+}
+
+int64_t pic_launch_count(const pic_ctx *c) { return c ? c->launches : 0; }
+
+pic_status pic_timing(pic_ctx *c, int enable, double *ms_out, int64_t *nsteps)
+{
+    if (!c) return PIC_ERR_ARG;
+    if (ms_out) {
+        CK(cudaStreamSynchronize(c->stream));
+        for (int k = 0; k < 5; ++k) ms_out[k] = 0.0;
+        for (size_t b = 0; b + 5 <= c->ev_used; b += 5) {
+            float t[4];
+            CK(cudaEventElapsedTime(&t[0], c->ev[b + 1], c->ev[b + 2]));   // cell kernels
+            CK(cudaEventElapsedTime(&t[1], c->ev[b + 0], c->ev[b + 1]));   // march (and memsets)
+            CK(cudaEventElapsedTime(&t[2], c->ev[b + 2], c->ev[b + 3]));   // scan + scatter
+            CK(cudaEventElapsedTime(&t[3], c->ev[b + 3], c->ev[b + 4]));   // fields
+            ms_out[0] += t[0]; ms_out[1] += t[1]; ms_out[2] += t[2]; ms_out[3] += t[3];
+            float all;
+            CK(cudaEventElapsedTime(&all, c->ev[b + 0], c->ev[b + 4]));
+            ms_out[4] += all;
+        }
+        if (nsteps) *nsteps = (int64_t)(c->ev_used / 5);
+    }
+    if (enable >= 0) {
+        c->timing = enable != 0;
+        c->ev_used = 0;
+    }
+    return PIC_OK;
+}
+
+pic_status pic_free(pic_ctx *c)
+{
+    if (!c) return PIC_ERR_ARG;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    if (c->own_arena && c->arena) cudaFree(c->arena);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    delete c;
+    return PIC_OK;
+}
+
+const char *pic_last_error(const pic_ctx *c) { return c ? c->err.c_str() : "no context"; }
+
+pic_status pic_philox_check(const uint32_t *ctr, const uint32_t key[2], uint32_t *out, int n)
+{
+    if (!ctr || !key || !out || n <= 0) return PIC_ERR_ARG;
+    uint32_t *d = nullptr;
+    if (cudaMalloc(&d, sizeof(uint32_t) * 8 * (size_t)n) != cudaSuccess) return PIC_ERR_OOM;
+    pic_status st = PIC_OK;
+    if (cudaMemcpy(d, ctr, sizeof(uint32_t) * 4 * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess) st = PIC_ERR_CUDA;
+    if (st == PIC_OK) {
+        k_philox_check<<<(n + 127) / 128, 128>>>(d, key[0], key[1], d + 4 * (size_t)n, n);
+        if (cudaMemcpy(out, d + 4 * (size_t)n, sizeof(uint32_t) * 4 * (size_t)n, cudaMemcpyDeviceToHost) != cudaSuccess)
+            st = PIC_ERR_CUDA;
+    }
+    cudaFree(d);
+    return st;
+}
+
+}  // extern "C"

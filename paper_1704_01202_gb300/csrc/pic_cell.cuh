@@ -1,0 +1,353 @@
+// The per-cell hot path: one warp owns one cell and runs, in order, the
+// canonical random ordering of its particles, the FP64 cell moments, binary
+// e-e and e-i collisions, Lotz impact ionization, EOS-clamped
+// recombination, (rad steps) subshell photoionization and K-vacancy decay,
+// then the Boris push and the charge-conserving deposit of every particle of
+// the cell.  Particles are staged in shared memory; their positions stay in
+// global memory until the push.
+//
+// Determinism: every random number is keyed by (slab seed, particle id,
+// step, purpose) and every ordering comes from a sort on Philox keys, so
+// the result of a cell does not depend on where its particles sit in memory
+// or on which warp handles it.  Sums run lane-strided over the canonical
+// order with a fixed reduction tree; the current goes to global memory as
+// 64-bit fixed point, whose addition is associative.
+#pragma once
+#include "pic_dev.cuh"
+
+namespace pic {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr double JFIX = 1099511627776.0;        // 2^40 fixed-point scale of J
+
+struct NewE {            // an electron created in this cell this step
+    float ux, uy, uz, w;
+    int meta;            // ion slot | kind << 16
+};
+
+struct CellArgs {
+    float4 *e0, *e1;     // electrons (xi, eta, ux, uy), (uz, w, id_lo, id_hi)
+    int *ekey;           // next cell of each electron slot (-1: gone)
+    const int *cs_e;     // cell start of electrons [ncell + 1]
+    float4 *i0, *i1;     // ions (xi, eta, ux, uy), (uz, zfrac, id, Z | nK << 8)
+    int *ikey;
+    const int *cs_i;
+    int *cnt_e, *cnt_i;  // per-cell counts of the next sort
+    int *append;         // electrons appended this step
+    int cap_e;           // electron capacity
+    int ncell;           // total cells (all slabs)
+    const int *cell_slab;
+    const SlabDev *slabs;
+    const unsigned *steps;
+    SlabTally *tally;
+    double *photons;
+    const float *fldE;   // [3][npts] ex ey ez
+    const float *fldB;   // [3][npts] bx by bz
+    int npts;
+    unsigned long long *J;   // [3][npts] fixed point
+    const Tables *tab;
+    const EosTable *eos;
+    int *err;
+    int *work;           // work counter
+    const int *list;     // cell list (NULL: all cells)
+    const int *n_list;   // number of cells in the list (device)
+    int *ovf_list, *ovf_count;   // cells too large for this pass
+    int cap_ce, cap_ci, cap_new; // per-cell shared-memory capacities
+};
+
+__device__ __forceinline__ double wsum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+    return __shfl_sync(FULL, v, 0);
+}
+
+__device__ __forceinline__ int wsum_i(int v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+    return __shfl_sync(FULL, v, 0);
+}
+
+// inclusive prefix over the lanes (fixed order)
+__device__ __forceinline__ double wscan_incl(double v, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        double t = __shfl_up_sync(FULL, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// ascending sort on (key, id) of n entries, padded to a power of two
+template <class IdT>
+__device__ void warp_bitonic(unsigned long long *key, IdT *id, unsigned short *slot, int n, int lane)
+{
+    int np = 1;
+    while (np < n) np <<= 1;
+    for (int k = n + lane; k < np; k += 32) { key[k] = ~0ull; id[k] = (IdT)~(IdT)0; slot[k] = 0xffff; }
+    __syncwarp();
+    for (int size = 2; size <= np; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = lane; t < (np >> 1); t += 32) {
+                int lo = 2 * t - (t & (stride - 1));
+                int hi = lo + stride;
+                bool asc = (lo & size) == 0;
+                unsigned long long kl = key[lo], kh = key[hi];
+                IdT il = id[lo], ih = id[hi];
+                bool gt = kl > kh || (kl == kh && il > ih);
+                if (gt == asc) {
+                    key[lo] = kh; key[hi] = kl;
+                    id[lo] = ih; id[hi] = il;
+                    unsigned short s = slot[lo]; slot[lo] = slot[hi]; slot[hi] = s;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+__device__ __forceinline__ float cic_w(float x, int node)
+{
+    float d = fabsf(x - (float)node);
+    return d < 1.0f ? 1.0f - d : 0.0f;
+}
+
+// per-warp shared memory carve-up
+struct WarpMem {
+    float4 *eu;                 // [cap_ce] ux uy uz w (slot order)
+    unsigned long long *ekey;   // [cap_ce] sort key, later reused as double take
+    unsigned long long *eid;    // [cap_ce] ids in canonical order
+    unsigned short *eperm;      // [cap_ce] canonical position -> slot
+    float4 *iu;                 // [cap_ci] ux uy uz zfrac (slot order)
+    int *ist;                   // [cap_ci] Z | nK << 8 (slot order)
+    unsigned long long *ikey;   // [cap_ci] sort key, later reused as nrec
+    unsigned int *iid;          // [cap_ci] ids in canonical order
+    unsigned short *iperm;      // [cap_ci]
+    NewE *nw;                   // [cap_new]
+    float *dE;                  // [16] continuum lowering per charge state
+    double *Pz;                 // [16] impact-ionization probability per charge
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+__host__ __device__ inline size_t warp_mem_bytes(int ce, int ci, int cn)
+{
+    size_t b = 0;
+    b += align16((size_t)ce * 16) + align16((size_t)ce * 8) * 2 + align16((size_t)ce * 2);
+    b += align16((size_t)ci * 16) + align16((size_t)ci * 4) + align16((size_t)ci * 8) + align16((size_t)ci * 4)
+         + align16((size_t)ci * 2);
+    b += align16((size_t)cn * sizeof(NewE));
+    b += 16 * 4 + 16 * 8;
+    return b;
+}
+
+__device__ inline WarpMem carve(char *base, int ce, int ci, int cn)
+{
+    WarpMem m;
+    char *p = base;
+    m.eu = (float4 *)p; p += align16((size_t)ce * 16);
+    m.ekey = (unsigned long long *)p; p += align16((size_t)ce * 8);
+    m.eid = (unsigned long long *)p; p += align16((size_t)ce * 8);
+    m.eperm = (unsigned short *)p; p += align16((size_t)ce * 2);
+    m.iu = (float4 *)p; p += align16((size_t)ci * 16);
+    m.ist = (int *)p; p += align16((size_t)ci * 4);
+    m.ikey = (unsigned long long *)p; p += align16((size_t)ci * 8);
+    m.iid = (unsigned int *)p; p += align16((size_t)ci * 4);
+    m.iperm = (unsigned short *)p; p += align16((size_t)ci * 2);
+    m.nw = (NewE *)p; p += align16((size_t)cn * sizeof(NewE));
+    m.dE = (float *)p; p += 16 * 4;
+    m.Pz = (double *)p;
+    return m;
+}
+
+// ---------------------------------------------------------------------
+// field gather (CIC from the staggered Yee grid; zero outside [0, nx])
+// ---------------------------------------------------------------------
+struct SlabGrid {
+    int nx, ny, W;       // W = nx + 1 points per row
+    const float *fe;     // ex of this slab (ey, ez follow with stride npts)
+    const float *fb;     // bx of this slab
+    int npts;            // stride between components
+    int fo;              // first grid point of the slab
+};
+
+__device__ __forceinline__ float grid_interp(const float *F, const SlabGrid &g, int cx, int cy,
+                                             float xi, float eta, bool hx, bool hy)
+{
+    float xs = xi - (hx ? 0.5f : 0.0f), ys = eta - (hy ? 0.5f : 0.0f);
+    int ax = (int)floorf(xs), ay = (int)floorf(ys);
+    float fx = xs - (float)ax, fy = ys - (float)ay;
+    int imax = hx ? g.nx - 1 : g.nx;
+    float v = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        int i = cx + ax + a;
+        if (i < 0 || i > imax) continue;
+        float wx = a ? fx : 1.0f - fx;
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            int j = cy + ay + b;
+            j %= g.ny; if (j < 0) j += g.ny;
+            float wy = b ? fy : 1.0f - fy;
+            v += wx * wy * __ldg(F + (size_t)j * g.W + i);
+        }
+    }
+    return v;
+}
+
+// ---------------------------------------------------------------------
+// current deposit
+// ---------------------------------------------------------------------
+struct JAcc2 { float x[3][4], y[4][3], z[4][4]; };
+struct JAcc1 { float x[3], y[4], z[4]; };
+
+__device__ __forceinline__ void jatomic(unsigned long long *J, float v)
+{
+    if (v != 0.0f) atomicAdd(J, (unsigned long long)__double2ll_rn((double)v * JFIX));
+}
+
+// Esirkepov weights of one sub-cell move, stencil anchored at cell (ax, ay)
+// offsets -1..2; start (x0, y0), end (x1, y1) relative to the anchor cell
+__device__ __forceinline__ void esirkepov2(float x0, float y0, float x1, float y1, float qw, float qwbz,
+                                           float frac, JAcc2 &A)
+{
+    float S0x[4], S1x[4], S0y[4], S1y[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        S0x[a] = cic_w(x0, a - 1); S1x[a] = cic_w(x1, a - 1);
+        S0y[a] = cic_w(y0, a - 1); S1y[a] = cic_w(y1, a - 1);
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        float acc = 0.0f;
+        float sy = S0y[b] + 0.5f * (S1y[b] - S0y[b]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            acc += (S1x[a] - S0x[a]) * sy;
+            A.x[a][b] -= qw * acc;
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        float acc = 0.0f;
+        float dsx = S1x[a] - S0x[a];
+        float sx = S0x[a] + 0.5f * dsx;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            acc += (S1y[b] - S0y[b]) * sx;
+            A.y[a][b] -= qw * acc;
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            float dsy = S1y[b] - S0y[b];
+            float wz = S0x[a] * S0y[b] + 0.5f * dsx * S0y[b] + 0.5f * S0x[a] * dsy + dsx * dsy * (1.0f / 3.0f);
+            A.z[a][b] += qwbz * wz * frac;
+        }
+    }
+}
+
+__device__ __forceinline__ void esirkepov1(float x0, float x1, float qw, float qwby, float qwbz, float frac, JAcc1 &A)
+{
+    float S0x[4], S1x[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) { S0x[a] = cic_w(x0, a - 1); S1x[a] = cic_w(x1, a - 1); }
+    float acc = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { acc += S1x[a] - S0x[a]; A.x[a] -= qw * acc; }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        float s = 0.5f * (S0x[a] + S1x[a]);
+        A.y[a] += qwby * s * frac;
+        A.z[a] += qwbz * s * frac;
+    }
+}
+
+// a move of one cell or more: equal sub-cell segments, each deposited
+// straight to global memory around its own start cell
+__device__ void deposit_long(const SlabGrid &g, unsigned long long *J, int npts, int fo, int cx, int cy,
+                             float x0, float y0, float x1, float y1, float qw, float qwby, float qwbz)
+{
+    float ax = fabsf(x1 - x0), ay = g.ny > 1 ? fabsf(y1 - y0) : 0.0f;
+    int nseg = (int)floorf(fmaxf(ax, ay)) + 1;
+    for (int k = 0; k < nseg; ++k) {
+        float a0 = (float)k / nseg, a1 = (float)(k + 1) / nseg;
+        float xa = x0 + a0 * (x1 - x0), xb = x0 + a1 * (x1 - x0);
+        float ya = y0 + a0 * (y1 - y0), yb = y0 + a1 * (y1 - y0);
+        int sx = (int)floorf(xa), sy = g.ny > 1 ? (int)floorf(ya) : 0;
+        float f = 1.0f / nseg;
+        if (g.ny == 1) {
+            JAcc1 A = {};
+            esirkepov1(xa - sx, xb - sx, qw, qwby, qwbz, f, A);
+            for (int a = 0; a < 4; ++a) {
+                int i = cx + sx - 1 + a;
+                if (a < 3 && i >= 0 && i < g.nx) jatomic(J + fo + i, A.x[a]);
+                if (i >= 0 && i <= g.nx) {
+                    jatomic(J + npts + fo + i, A.y[a]);
+                    jatomic(J + 2 * npts + fo + i, A.z[a]);
+                }
+            }
+        } else {
+            JAcc2 A = {};
+            esirkepov2(xa - sx, ya - sy, xb - sx, yb - sy, qw, qwbz, f, A);
+            for (int a = 0; a < 4; ++a) {
+                int i = cx + sx - 1 + a;
+                for (int b = 0; b < 4; ++b) {
+                    int j = (cy + sy - 1 + b) % g.ny; if (j < 0) j += g.ny;
+                    size_t o = (size_t)fo + (size_t)j * g.W + i;
+                    if (a < 3 && i >= 0 && i < g.nx) jatomic(J + o, A.x[a][b]);
+                    if (b < 3 && i >= 0 && i <= g.nx) jatomic(J + npts + o, A.y[a][b]);
+                    if (i >= 0 && i <= g.nx) jatomic(J + 2 * npts + o, A.z[a][b]);
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------
+// push of one particle: gather, Boris, move, deposit; returns the next
+// cell (local index) or -1 when it left through an x boundary
+// ---------------------------------------------------------------------
+template <int DIM, class Acc>
+__device__ __forceinline__ int push_one(const SlabDev &S, const SlabGrid &g, unsigned long long *J, int npts,
+                                        int cx, int cy, float &xi, float &eta, float &ux, float &uy, float &uz,
+                                        float qm, float qw, bool do_push, bool do_dep, Acc &A)
+{
+    if (!do_push) return cy * S.nx + cx;
+    float ex = grid_interp(g.fe, g, cx, cy, xi, eta, true, false);
+    float ey = grid_interp(g.fe + g.npts, g, cx, cy, xi, eta, false, true);
+    float ez = grid_interp(g.fe + 2 * g.npts, g, cx, cy, xi, eta, false, false);
+    float bx = grid_interp(g.fb, g, cx, cy, xi, eta, false, true);
+    float by = grid_interp(g.fb + g.npts, g, cx, cy, xi, eta, true, false);
+    float bz = grid_interp(g.fb + 2 * g.npts, g, cx, cy, xi, eta, true, true);
+    boris(ux, uy, uz, ex, ey, ez, bx, by, bz, qm, S.dt);
+    float ig = rsqrtf(1.0f + ux * ux + uy * uy + uz * uz);
+    float bxv = ux * ig, byv = uy * ig, bzv = uz * ig;
+    const float c = (float)kCnmPerFs;
+    float xn = xi + bxv * c * S.dt / S.dx;
+    float yn = DIM == 2 ? eta + byv * c * S.dt / S.dy : eta;
+    if (!(fabsf(xn - xi) < 64.0f && fabsf(yn - eta) < 64.0f)) return -2;   // not finite: dropped
+    if (do_dep) {
+        if (fabsf(xn - xi) < 1.0f && fabsf(yn - eta) < 1.0f) {
+            if constexpr (DIM == 2) esirkepov2(xi, eta, xn, yn, qw, qw * bzv, 1.0f, A);
+            else esirkepov1(xi, xn, qw, qw * byv, qw * bzv, 1.0f, A);
+        } else {
+            deposit_long(g, J, npts, g.fo, cx, cy, xi, eta, xn, yn, qw, qw * byv, qw * bzv);
+        }
+    }
+    float fx = floorf(xn), fy = floorf(yn);
+    int ncx = cx + (int)fx;
+    int ncy = cy + (int)fy;
+    xi = xn - fx;
+    eta = yn - fy;
+    const float below1 = 0.99999994f;
+    if (xi >= 1.0f) xi = below1;
+    if (eta >= 1.0f) eta = below1;
+    if (DIM == 1) { ncy = 0; }
+    else { ncy %= S.ny; if (ncy < 0) ncy += S.ny; }
+    if (ncx < 0 || ncx >= S.nx) return -1;
+    return ncy * S.nx + ncx;
+}
+
+}  // namespace pic

@@ -1,0 +1,336 @@
+// Device building blocks of the GB300 collisional-PIC step: constants,
+// counter-based random numbers, atomic-structure rules, cross sections,
+// continuum lowering, binary collision kinematics and the Boris rotation.
+// Every function here is an independent implementation from the paper's
+// statement of the method (and the published algorithms it cites).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pic {
+
+// ---------------- physical constants (CODATA 2018) ----------------
+constexpr double kPi = 3.141592653589793;
+constexpr float kPiF = 3.14159265f;
+constexpr double kCcmPerFs = 2.99792458e-5;     // c in cm/fs
+constexpr double kCnmPerFs = 299.792458;        // c in nm/fs
+constexpr double kMeC2 = 510998.95;             // eV
+constexpr double kReCm = 2.8179403262e-13;      // classical electron radius
+constexpr double kQe = 1.602176634e-19;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kMeKg = 9.1093837015e-31;
+constexpr double kCms = 299792458.0;
+constexpr double kHbarCeVnm = 197.3269804;
+constexpr float kPminEv = 1.0f;                 // floor of a lowered binding
+
+constexpr int NS = 5;           // 1s 2s 2p 3s 3p
+constexpr int NZ = 14;          // charge states 0..13
+constexpr int ZNUC = 13;
+constexpr int MAXB = 8;         // photon bins
+
+// Philox stream purposes (counter word 3)
+enum : uint32_t { PU_PAIR_E = 1, PU_PAIR_I = 2, PU_COLL_EE = 3, PU_COLL_EI = 4,
+                  PU_COLL_IE = 5, PU_ION = 6, PU_PHOTO_A = 7, PU_PHOTO_B = 8, PU_DECAY = 9 };
+// kinds of created electrons: id high word = ((step + 1) << 2) | kind
+enum : uint32_t { KIND_IMPACT = 1, KIND_PHOTO = 2, KIND_AUGER = 3 };
+
+// counters in the per-slab tally
+enum { C_ION, C_ION_REJ, C_REC, C_PH0, C_PH1, C_PH2, C_PH3, C_PH4, C_PART, C_AUG, C_KA,
+       C_PGT1, C_ESC_E, C_ESC_I, C_EE, C_EI, NCOUNT };
+
+// device error word bits
+enum : int { ERR_CELL_OVERFLOW = 1, ERR_CAPACITY = 2, ERR_NUMERIC = 4, ERR_NEW_OVERFLOW = 8 };
+
+// ---------------- atomic tables (shared by all slabs) ----------------
+// small tables indexed per particle (copied to shared memory by kernels)
+struct Tables {
+    float lotz_a[NS], lotz_b[NS], lotz_c[NS];
+    float E_bind[NZ][NS];
+    float tauK[NZ][2], omegaK[NZ][2], E_Ka[NZ];
+};
+// equation of state Zbar(n_i, T_e), read once per cell
+constexpr int EOS_MAX_T = 1024, EOS_MAX_N = 16;
+struct EosTable {
+    int n_T, n_n;
+    float T[EOS_MAX_T], n[EOS_MAX_N];
+    float Z[EOS_MAX_N * EOS_MAX_T];
+};
+
+// ---------------- per-slab description ----------------
+struct SlabDev {
+    int nx, ny, cell0, ncell;
+    int fld_off;            // first grid point of this slab in the field arrays
+    int ph_off;             // first photon entry (cells * nb)
+    int nb;                 // photon bins in use (0: no pulse)
+    int rad_every;
+    unsigned flags;
+    int ipd;
+    int nsub;               // field subcycles per step
+    int shape;
+    float dx, dy, dt;
+    float w_ion, m_ion, E_bulk, coulomb_log;
+    float mur;              // first-order Mur coefficient
+    double n_ref;           // cm^-3
+    double kappa_J;         // J coupling of the normalized field equations
+    double I_peak, fwhm, t_peak, spot_sigma;
+    unsigned long long seed;
+    float hv_b[MAXB];
+    float sig_b[NS][MAXB];
+    float bin_hw;
+};
+
+struct SlabTally {
+    double ion, ka_esc, esc, inc, trans;
+    unsigned long long cnt[NCOUNT];
+};
+
+// ---------------- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) ----------------
+struct U4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                     uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+    }
+    return U4{c0, c1, c2, c3};
+}
+
+// uniform in (0,1): top 24 bits, centred; exact in float and double
+__device__ __forceinline__ float u01(uint32_t x) { return ((float)(x >> 8) + 0.5f) * (1.0f / 16777216.0f); }
+
+__device__ __forceinline__ U4 draw(unsigned long long seed, unsigned long long id, uint32_t step, uint32_t purpose)
+{
+    return philox((uint32_t)id, (uint32_t)(id >> 32), step, purpose, (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+// ---------------- atomic structure ----------------
+__device__ __forceinline__ int cap_of(int s) { return (s == 2 || s == 4) ? 6 : 2; }
+
+// lowest-energy filling of nb electrons with nk extra K vacancies; false if impossible
+__device__ __forceinline__ bool occupancy(int nb, int nk, int occ[NS])
+{
+    int k = (nb < 2 ? nb : 2) - nk;
+    if (nb < 0 || nk < 0 || k < 0) return false;
+    occ[0] = k;
+    int rest = nb - k;
+#pragma unroll
+    for (int s = 1; s < NS; ++s) {
+        int t = rest < cap_of(s) ? rest : cap_of(s);
+        occ[s] = t;
+        rest -= t;
+    }
+    return rest == 0;
+}
+
+__device__ __forceinline__ int outer_shell(int nb, int nk)
+{
+    int occ[NS];
+    if (!occupancy(nb, nk, occ)) return -1;
+    for (int s = NS - 1; s >= 0; --s)
+        if (occ[s] > 0) return s;
+    return -1;
+}
+
+// (Z, nK) after one electron of subshell s leaves
+__device__ __forceinline__ void lose_electron(int &Z, int &nK, int s)
+{
+    int nb = ZNUC - Z, occ[NS];
+    occupancy(nb, nK, occ);
+    int kocc = occ[0] - (s == 0 ? 1 : 0);
+    int nb2 = nb - 1;
+    Z += 1;
+    nK = (nb2 < 2 ? nb2 : 2) - kocc;
+}
+
+__device__ __forceinline__ float lowered_binding(const Tables &T, int z, int s, float dE)
+{
+    float p = T.E_bind[z][s] - dE;
+    return p > kPminEv ? p : kPminEv;
+}
+
+// energy to remove the outermost electron of (Z, nK), lowered by dE
+__device__ __forceinline__ float removal_energy(const Tables &T, int Z, int nK, float dE)
+{
+    int s = outer_shell(ZNUC - Z, nK);
+    return s < 0 ? 0.0f : lowered_binding(T, Z, s, dE);
+}
+
+// ---------------- continuum lowering (Sec. V) ----------------
+// Eq. 4 (Ecker-Kroll, dense branch, C = 1) and Eq. 5 (Stewart-Pyatt with
+// T_i = T_e and z* = Zbar).  Densities cm^-3, T eV, result eV.
+__device__ __forceinline__ float ipd_shift(int model, int z, double n_e, double n_i, double T_e, double zbar)
+{
+    const double e_over_4pe0 = kQe / (4.0 * kPi * kEps0);        // V m
+    if (model == 1) {
+        double n = (n_e + n_i) * 1e6;
+        if (n <= 0.0) return 0.0f;
+        double r = cbrt(3.0 / (4.0 * kPi * n));
+        return (float)((z + 1) * e_over_4pe0 / r);
+    }
+    if (model == 2) {
+        if (T_e <= 0.0 || n_e <= 0.0) return 0.0f;
+        double lam = sqrt(kEps0 * T_e / (kQe * n_e * 1e6 * (zbar + 1.0)));
+        double K = (z + 1) * e_over_4pe0 / (lam * T_e);
+        return (float)(T_e / (2.0 * (zbar + 1.0)) * (pow(3.0 * (zbar + 1.0) * K + 1.0, 2.0 / 3.0) - 1.0));
+    }
+    return 0.0f;
+}
+
+// Coulomb logarithm stand-in: ln(lambda_D / b_min), b_min = max(classical
+// closest approach, de Broglie length at 3T), floored at 2
+__device__ __forceinline__ float coulomb_log(double n_e, double T_e, double zbar)
+{
+    if (n_e <= 0.0 || T_e <= 0.0) return 2.0f;
+    double lam = sqrt(kEps0 * T_e / (kQe * n_e * 1e6)) * 1e9;
+    double zz = zbar > 1.0 ? zbar : 1.0;
+    double bcl = zz * (kQe / (4.0 * kPi * kEps0)) * 1e9 / (3.0 * T_e);
+    double bqm = kHbarCeVnm / (2.0 * sqrt(3.0 * T_e * kMeC2));
+    double L = log(lam / (bcl > bqm ? bcl : bqm));
+    return L > 2.0 ? (float)L : 2.0f;
+}
+
+// ---------------- Lotz cross section (Eq. 3), cm^2 ----------------
+__device__ __forceinline__ float lotz_sigma(const Tables &T, int z, float dE, float E)
+{
+    int occ[NS];
+    if (z >= ZNUC || !occupancy(ZNUC - z, 0, occ)) return 0.0f;
+    float sig = 0.0f;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        if (!occ[s]) continue;
+        float P = lowered_binding(T, z, s, dE);
+        if (E <= P) continue;
+        float x = E / P;
+        sig += T.lotz_a[s] * occ[s] * logf(x) / (E * P) * (1.0f - T.lotz_b[s] * expf(-T.lotz_c[s] * (x - 1.0f)));
+    }
+    return sig;
+}
+
+// EOS table, bilinear, clamped
+__device__ __forceinline__ float eos_lookup(const EosTable &T, float n, float t)
+{
+    auto locate = [](const float *g, int m, float x, int &i0) -> float {
+        if (m == 1 || x <= g[0]) { i0 = 0; return 0.0f; }
+        if (x >= g[m - 1]) { i0 = m - 2; return 1.0f; }
+        int lo = 0, hi = m - 1;
+        while (hi - lo > 1) { int md = (lo + hi) >> 1; if (g[md] <= x) lo = md; else hi = md; }
+        i0 = lo;
+        return (x - g[lo]) / (g[lo + 1] - g[lo]);
+    };
+    int a, b;
+    float fa = locate(T.n, T.n_n, n, a), fb = locate(T.T, T.n_T, t, b);
+    int a1 = T.n_n > 1 ? a + 1 : a, b1 = T.n_T > 1 ? b + 1 : b;
+    const float *Z = T.Z;
+    float z00 = Z[a * T.n_T + b], z01 = Z[a * T.n_T + b1], z10 = Z[a1 * T.n_T + b], z11 = Z[a1 * T.n_T + b1];
+    return (1 - fa) * ((1 - fb) * z00 + fb * z01) + fa * ((1 - fb) * z10 + fb * z11);
+}
+
+// ---------------- kinematics ----------------
+// kinetic energy in units of m c^2 (gamma - 1 = u^2 / (gamma + 1))
+__device__ __forceinline__ float gm1(float ux, float uy, float uz)
+{
+    float u2 = ux * ux + uy * uy + uz * uz;
+    return u2 / (sqrtf(1.0f + u2) + 1.0f);
+}
+
+// scale the kinetic energy of u by f, direction kept
+__device__ __forceinline__ void scale_kinetic(float &ux, float &uy, float &uz, float f)
+{
+    float g1 = gm1(ux, uy, uz);
+    if (g1 == 0.0f) return;
+    float s = sqrtf(f * (2.0f + f * g1) / (2.0f + g1));
+    ux *= s; uy *= s; uz *= s;
+}
+
+// One binary collision: Takizuka-Abe deflection tan(theta/2) ~ N(0, var),
+// var = 2 pi (qa qb)^2 r_e^2 c n lnL dt / (mu^2 beta_rel^3), applied as a
+// rotation of the centre-of-momentum momentum; weighted acceptance
+// min(1, w_other / w_self).  Masses in m_e, u in units of m c of each.
+__device__ __forceinline__ bool binary_collision(float3 &ua, float3 &ub, float ma, float mb, float qa, float qb,
+                                                 float wa, float wb, float n_l, float lnL, float dtc,
+                                                 float r0, float r1, float r2, float r3)
+{
+    if (qa == 0.0f || qb == 0.0f) return false;
+    float ga = sqrtf(1.0f + ua.x * ua.x + ua.y * ua.y + ua.z * ua.z);
+    float gb = sqrtf(1.0f + ub.x * ub.x + ub.y * ub.y + ub.z * ub.z);
+    float dvx = ua.x / ga - ub.x / gb, dvy = ua.y / ga - ub.y / gb, dvz = ua.z / ga - ub.z / gb;
+    float vrel = sqrtf(dvx * dvx + dvy * dvy + dvz * dvz);
+    if (vrel < 1e-10f) return false;
+    float mu = ma * mb / (ma + mb);
+    // constant part 2 pi r_e^2 c in cm^3/fs, evaluated in double once
+    const float k0 = (float)(2.0 * kPi * kReCm * kReCm * kCcmPerFs);
+    float q2 = qa * qb;
+    float var = k0 * q2 * q2 * n_l * lnL * dtc / (mu * mu * vrel * vrel * vrel);
+    float delta = sqrtf(var) * sqrtf(-2.0f * logf(r0)) * cosf(2.0f * kPiF * r1);
+    float sphi, cphi;
+    sincosf(2.0f * kPiF * r2, &sphi, &cphi);
+
+    float pax = ma * ua.x, pay = ma * ua.y, paz = ma * ua.z;
+    float Ea = ma * ga, Eb = mb * gb, E = Ea + Eb;
+    float bx = (pax + mb * ub.x) / E, by = (pay + mb * ub.y) / E, bz = (paz + mb * ub.z) / E;
+    float b2 = bx * bx + by * by + bz * bz;
+    float gc = rsqrtf(1.0f - b2);
+    float h = gc * gc / (gc + 1.0f);
+    float bp = bx * pax + by * pay + bz * paz;
+    float c1 = h * bp - gc * Ea;
+    float sx = pax + c1 * bx, sy = pay + c1 * by, sz = paz + c1 * bz;
+    float p = sqrtf(sx * sx + sy * sy + sz * sz);
+    if (p == 0.0f) return false;
+    float nx = sx / p, ny = sy / p, nz = sz / p;
+    float d2 = delta * delta;
+    float st = 2.0f * delta / (1.0f + d2), ct = (1.0f - d2) / (1.0f + d2);
+    float e1x, e1y, e1z, e2x, e2y, e2z;
+    float np = sqrtf(nx * nx + ny * ny);
+    if (np > 0.0f) {
+        e1x = nx * nz / np; e1y = ny * nz / np; e1z = -np;
+        e2x = -ny / np; e2y = nx / np; e2z = 0.0f;
+    } else {
+        e1x = 1.0f; e1y = 0.0f; e1z = 0.0f;
+        e2x = 0.0f; e2y = 1.0f; e2z = 0.0f;
+    }
+    float qx = p * (ct * nx + st * cphi * e1x + st * sphi * e2x);
+    float qy = p * (ct * ny + st * cphi * e1y + st * sphi * e2y);
+    float qz = p * (ct * nz + st * cphi * e1z + st * sphi * e2z);
+    float Eas = sqrtf(ma * ma + p * p), Ebs = sqrtf(mb * mb + p * p);
+    float bq = bx * qx + by * qy + bz * qz;
+    float ca = h * bq + gc * Eas, cb = -h * bq + gc * Ebs;
+    float wm = wa > wb ? wa : wb;
+    if (r3 < wb / wm) { ua.x = (qx + ca * bx) / ma; ua.y = (qy + ca * by) / ma; ua.z = (qz + ca * bz) / ma; }
+    if (r3 < wa / wm) { ub.x = (-qx + cb * bx) / mb; ub.y = (-qy + cb * by) / mb; ub.z = (-qz + cb * bz) / mb; }
+    return true;
+}
+
+// relativistic Boris: q/m in e/m_e, dt fs, normalized fields
+__device__ __forceinline__ void boris(float &ux, float &uy, float &uz, float ex, float ey, float ez,
+                                      float bx, float by, float bz, float qm, float dt)
+{
+    float h = 0.5f * qm * dt;
+    float mx = ux + h * ex, my = uy + h * ey, mz = uz + h * ez;
+    float ig = rsqrtf(1.0f + mx * mx + my * my + mz * mz);
+    float tx = h * bx * ig, ty = h * by * ig, tz = h * bz * ig;
+    float t2 = tx * tx + ty * ty + tz * tz;
+    float s = 2.0f / (1.0f + t2);
+    float px = mx + my * tz - mz * ty, py = my + mz * tx - mx * tz, pz = mz + mx * ty - my * tx;
+    float qx = mx + (py * tz - pz * ty) * s, qy = my + (pz * tx - px * tz) * s, qz = mz + (px * ty - py * tx) * s;
+    ux = qx + h * ex; uy = qy + h * ey; uz = qz + h * ez;
+}
+
+// isotropic momentum of kinetic energy ke (eV) for an electron
+__device__ __forceinline__ float3 iso_momentum(float ke, float rc, float rp)
+{
+    float x = ke / (float)kMeC2;
+    float um = sqrtf(x * (2.0f + x));
+    float ct = 2.0f * rc - 1.0f;
+    float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+    float sp, cp;
+    sincosf(2.0f * kPiF * rp, &sp, &cp);
+    return make_float3(um * st * cp, um * st * sp, um * ct);
+}
+
+}  // namespace pic

@@ -1,0 +1,371 @@
+// Grid-level kernels: photon march, counting sort (scan + scatter), Yee
+// field subcycles, particle loading and diagnostic reductions.
+#pragma once
+#include "pic_dev.cuh"
+
+namespace pic {
+
+// ---------------------------------------------------------------------
+// photon march (every rad step): the photon number of every cell and bin
+// moves c dt_rad along +x, split linearly between the two destination
+// cells; the region x < 0 carries the pulse at retarded time; what passes
+// x = L is transmitted.  One block per (slab, row).
+// ---------------------------------------------------------------------
+struct MarchArgs {
+    const SlabDev *slabs;
+    const unsigned *steps;
+    const int *row_slab, *row_idx;   // per block
+    double *photons;
+    SlabTally *tally;
+};
+
+__device__ __forceinline__ double pulse_source(const SlabDev &S, int b, double tau, int row)
+{
+    double I;
+    if (S.shape == 1) I = fabs(tau - S.t_peak) <= 0.5 * S.fwhm ? S.I_peak : 0.0;
+    else { double d = (tau - S.t_peak) / S.fwhm; I = S.I_peak * exp(-4.0 * 0.6931471805599453 * d * d); }
+    double n = I / (kCcmPerFs * 1e15 * (double)S.hv_b[b] * kQe) / S.nb;      // cm^-3
+    if (S.spot_sigma > 0.0 && S.ny > 1) {
+        double y = (row + 0.5) * (double)S.dy - 0.5 * S.ny * (double)S.dy;
+        n *= exp(-0.5 * y * y / (S.spot_sigma * S.spot_sigma));
+    }
+    return n / S.n_ref;
+}
+
+__global__ void k_march(MarchArgs a)
+{
+    extern __shared__ double srow[];
+    __shared__ double red[2][32];
+    const int s = a.row_slab[blockIdx.x], row = a.row_idx[blockIdx.x];
+    const SlabDev &S = a.slabs[s];
+    const unsigned step = a.steps[s];
+    if (!(S.flags & 16u) || S.nb == 0 || S.rad_every <= 0 || (step % (unsigned)S.rad_every) != 0) return;
+    const int nx = S.nx, nb = S.nb;
+    const double dtr = (double)S.rad_every * S.dt;
+    const double sh = kCnmPerFs * dtr / S.dx;
+    const int m = (int)floor(sh);
+    const double f = sh - m;
+    const double tprev = (double)step * S.dt - dtr;
+    double *ph = a.photons + S.ph_off + (size_t)row * nx * nb;
+    for (int b = 0; b < nb; ++b) {
+        for (int k = threadIdx.x; k < nx; k += blockDim.x) srow[k] = ph[(size_t)k * nb + b];
+        __syncthreads();
+        double trans = 0.0, inc = 0.0;
+        for (int k = threadIdx.x; k < nx; k += blockDim.x) {
+            int j0 = k - m, j1 = k - m - 1;
+            double v0 = j0 >= 0 ? srow[j0] : pulse_source(S, b, tprev - (j0 + 0.5) * S.dx / kCnmPerFs, row);
+            double v1 = j1 >= 0 ? srow[j1] : pulse_source(S, b, tprev - (j1 + 0.5) * S.dx / kCnmPerFs, row);
+            ph[(size_t)k * nb + b] = (1.0 - f) * v0 + f * v1;
+            if (j0 < 0) inc += (1.0 - f) * v0;
+            if (j1 < 0) inc += f * v1;
+        }
+        // sources whose destinations lie beyond the last cell
+        for (int j = -(m + 1) + (int)threadIdx.x; j < nx; j += blockDim.x) {
+            int d0 = j + m, d1 = j + m + 1;
+            if (d1 < nx) continue;
+            double v = j >= 0 ? srow[j] : pulse_source(S, b, tprev - (j + 0.5) * S.dx / kCnmPerFs, row);
+            if (d0 >= nx) { trans += (1.0 - f) * v; if (j < 0) inc += (1.0 - f) * v; }
+            trans += f * v;
+            if (j < 0) inc += f * v;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            trans += __shfl_down_sync(0xffffffffu, trans, o);
+            inc += __shfl_down_sync(0xffffffffu, inc, o);
+        }
+        if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = trans; red[1][threadIdx.x >> 5] = inc; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0, in = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { t += red[0][w]; in += red[1][w]; }
+            if (t != 0.0) atomicAdd(&a.tally[s].trans, t * S.hv_b[b]);
+            if (in != 0.0) atomicAdd(&a.tally[s].inc, in * S.hv_b[b]);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------
+// exclusive scan of the per-cell counts of both species (3 phases)
+// ---------------------------------------------------------------------
+constexpr int SCAN_T = 1024, SCAN_ITEMS = 4, SCAN_TILE = SCAN_T * SCAN_ITEMS;
+
+__device__ __forceinline__ int block_excl_scan(int v, int *sh, int &total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) { int t = __shfl_up_sync(0xffffffffu, x, o); if (lane >= o) x += t; }
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int y = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) { int t = __shfl_up_sync(0xffffffffu, y, o); if (lane >= o) y += t; }
+        sh[lane] = y;
+    }
+    __syncthreads();
+    int pre = warp ? sh[warp - 1] : 0;
+    total = sh[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return pre + x - v;
+}
+
+struct ScanArgs { const int *cnt[2]; int *cs[2]; int *bsum[2]; int *maxc[2]; int n; int nblk; };
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_reduce(ScanArgs a)
+{
+    __shared__ int sh[32];
+    const int sp = blockIdx.y;
+    const int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+    int v = 0;
+    for (int k = 0; k < SCAN_ITEMS; ++k) if (base + k < a.n) v += a.cnt[sp][base + k];
+    int tot;
+    block_excl_scan(v, sh, tot);
+    if (threadIdx.x == 0) a.bsum[sp][blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_blocks(ScanArgs a)
+{
+    __shared__ int sh[32];
+    const int sp = blockIdx.y;
+    int carry = 0;
+    for (int b0 = 0; b0 < a.nblk; b0 += SCAN_T) {
+        int i = b0 + threadIdx.x;
+        int v = i < a.nblk ? a.bsum[sp][i] : 0;
+        int tot;
+        int ex = block_excl_scan(v, sh, tot);
+        if (i < a.nblk) a.bsum[sp][i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) a.cs[sp][a.n] = carry;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_final(ScanArgs a)
+{
+    __shared__ int sh[32];
+    const int sp = blockIdx.y;
+    const int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+    int v[SCAN_ITEMS], sum = 0, mx = 0;
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        v[k] = base + k < a.n ? a.cnt[sp][base + k] : 0;
+        sum += v[k];
+        mx = max(mx, v[k]);
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx > 0) atomicMax(a.maxc[sp], mx);
+    int tot;
+    int ex = block_excl_scan(sum, sh, tot) + a.bsum[sp][blockIdx.x];
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        if (base + k < a.n) a.cs[sp][base + k] = ex;
+        ex += v[k];
+    }
+}
+
+// ---------------------------------------------------------------------
+// scatter into cell order (order inside a cell is irrelevant: every later
+// decision is keyed by particle id)
+// ---------------------------------------------------------------------
+struct ScatterArgs {
+    const float4 *s0, *s1;
+    const int *key;
+    const int *n_sorted;     // cs_old[ncell]
+    const int *n_extra;      // appended this step (NULL: none)
+    const int *cs_new;
+    int *fill;
+    float4 *d0, *d1;
+    int cap;                 // slots beyond the capacity never hold particles
+};
+
+__global__ void k_scatter(ScatterArgs a)
+{
+    const int n = min(*a.n_sorted + (a.n_extra ? *a.n_extra : 0), a.cap);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        int c = a.key[k];
+        if (c < 0) continue;
+        int d = a.cs_new[c] + atomicAdd(a.fill + c, 1);
+        a.d0[d] = a.s0[k];
+        a.d1[d] = a.s1[k];
+    }
+}
+
+__global__ void k_count(const int *key, const int *n_ptr, int *cnt)
+{
+    const int n = *n_ptr;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        int c = key[k];
+        if (c >= 0) atomicAdd(cnt + c, 1);
+    }
+}
+
+// ---------------------------------------------------------------------
+// Yee field subcycle, all slabs at once; y periodic, Mur in x.
+// E is double buffered so the Mur boundary can read old interior values.
+// ---------------------------------------------------------------------
+struct FieldArgs {
+    const SlabDev *slabs;
+    const int *pt_slab;      // slab of every grid point
+    int npts;
+    const float *Ein;        // [3][npts]
+    float *Eout;             // [3][npts]
+    float *B;                // [3][npts]
+    const unsigned long long *J;   // [3][npts] fixed point
+    int sub;                 // subcycle index
+};
+
+__global__ void k_b_half(FieldArgs a)
+{
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < a.npts; p += gridDim.x * blockDim.x) {
+        const int s = a.pt_slab[p];
+        const SlabDev &S = a.slabs[s];
+        if (!(S.flags & 128u) || a.sub >= S.nsub) continue;
+        const int W = S.nx + 1, q = p - S.fld_off, j = q / W, i = q - j * W;
+        const int jp = (j + 1) % S.ny;
+        const float h = 0.5f * S.dt / S.nsub * (float)kCnmPerFs;
+        const int n = a.npts;
+        const float *ex = a.Ein, *ey = a.Ein + n, *ez = a.Ein + 2 * n;
+        float *bx = a.B, *by = a.B + n, *bz = a.B + 2 * n;
+        const int o = S.fld_off, r = o + j * W, rp = o + jp * W;
+        bx[p] -= h * (ez[rp + i] - ez[r + i]) / S.dy;
+        if (i < S.nx) {
+            by[p] += h * (ez[r + i + 1] - ez[r + i]) / S.dx;
+            bz[p] -= h * ((ey[r + i + 1] - ey[r + i]) / S.dx - (ex[rp + i] - ex[r + i]) / S.dy);
+        }
+    }
+}
+
+__global__ void k_e_full(FieldArgs a)
+{
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < a.npts; p += gridDim.x * blockDim.x) {
+        const int s = a.pt_slab[p];
+        const SlabDev &S = a.slabs[s];
+        const int n = a.npts;
+        const float *exi = a.Ein, *eyi = a.Ein + n, *ezi = a.Ein + 2 * n;
+        float *exo = a.Eout, *eyo = a.Eout + n, *ezo = a.Eout + 2 * n;
+        if (!(S.flags & 128u) || a.sub >= S.nsub) {
+            exo[p] = exi[p]; eyo[p] = eyi[p]; ezo[p] = ezi[p];
+            continue;
+        }
+        const int W = S.nx + 1, q = p - S.fld_off, j = q / W, i = q - j * W;
+        const int jm = (j - 1 + S.ny) % S.ny;
+        const int o = S.fld_off, r = o + j * W, rm = o + jm * W;
+        const float dtf = S.dt / S.nsub, C = (float)kCnmPerFs, kap = (float)S.kappa_J;
+        const float *bx = a.B, *by = a.B + n, *bz = a.B + 2 * n;
+        const unsigned long long *Jx = a.J, *Jy = a.J + n, *Jz = a.J + 2 * n;
+        const double fix = 1.0 / 1099511627776.0;
+        const float sx = S.dx / S.dt, sy = S.ny > 1 ? S.dy / S.dt : C;
+        auto jv = [&](const unsigned long long *Jc, int idx, float scale) {
+            return (float)((double)(long long)Jc[idx] * fix) * scale;
+        };
+        auto ey_new = [&](int ii) {
+            return eyi[r + ii] + dtf * (-C * (bz[r + ii] - bz[r + ii - 1]) / S.dx - kap * jv(Jy, r + ii, sy));
+        };
+        auto ez_new = [&](int ii) {
+            return ezi[r + ii] + dtf * (C * ((by[r + ii] - by[r + ii - 1]) / S.dx - (bx[r + ii] - bx[rm + ii]) / S.dy)
+                                        - kap * jv(Jz, r + ii, C));
+        };
+        if (i < S.nx)
+            exo[p] = exi[p] + dtf * (C * (bz[r + i] - bz[rm + i]) / S.dy - kap * jv(Jx, p, sx));
+        else
+            exo[p] = exi[p];
+        if (i >= 1 && i < S.nx) {
+            eyo[p] = ey_new(i);
+            ezo[p] = ez_new(i);
+        } else if (i == 0) {
+            float y1 = S.nx > 1 ? ey_new(1) : eyi[r + 1], z1 = S.nx > 1 ? ez_new(1) : ezi[r + 1];
+            eyo[p] = eyi[r + 1] + S.mur * (y1 - eyi[r]);
+            ezo[p] = ezi[r + 1] + S.mur * (z1 - ezi[r]);
+        } else {
+            const int l = S.nx - 1;
+            float yl = l >= 1 ? ey_new(l) : eyi[r + l], zl = l >= 1 ? ez_new(l) : ezi[r + l];
+            eyo[p] = eyi[r + l] + S.mur * (yl - eyi[r + S.nx]);
+            ezo[p] = ezi[r + l] + S.mur * (zl - ezi[r + S.nx]);
+        }
+    }
+}
+
+__global__ void k_advance(unsigned *steps, int nslab)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < nslab) steps[s] += 1u;
+}
+
+// ---------------------------------------------------------------------
+// diagnostics
+// ---------------------------------------------------------------------
+struct DiagArgs {
+    const float4 *e0, *e1, *i0, *i1;
+    const int *n_e, *n_i;
+    const int *cs_e, *cs_i;      // to find the slab of a slot: unused when one slab
+    double m_ion;
+    double *out;                 // [0] W_e, [1] KE_e, [2] KE_i, [3] N_i, [4..4+NZ) csd, then eedf
+    int n_E;
+    double E_lo, E_max;
+};
+
+// block-reduced sums; histogram bins in shared memory
+__global__ void k_diag(DiagArgs a)
+{
+    extern __shared__ double sd[];          // [4 + NZ + n_E]
+    const int nv = 4 + NZ + a.n_E;
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) sd[k] = 0.0;
+    __syncthreads();
+    const int ne = *a.n_e, ni = *a.n_i;
+    const double lr = log(a.E_max / a.E_lo);
+    double w_s = 0.0, ke_s = 0.0, ki_s = 0.0, n_s = 0.0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ne; k += gridDim.x * blockDim.x) {
+        float4 P0 = a.e0[k], P1 = a.e1[k];
+        double ke = kMeC2 * (double)gm1(P0.z, P0.w, P1.x);
+        double w = P1.y;
+        w_s += w;
+        ke_s += w * ke;
+        int b = ke <= a.E_lo ? 0 : (int)floor(log(ke / a.E_lo) / lr * a.n_E);
+        b = b < 0 ? 0 : (b >= a.n_E ? a.n_E - 1 : b);
+        atomicAdd(sd + 4 + NZ + b, w);
+    }
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ni; k += gridDim.x * blockDim.x) {
+        float4 P0 = a.i0[k], P1 = a.i1[k];
+        ki_s += kMeC2 * a.m_ion * (double)gm1(P0.z, P0.w, P1.x);
+        n_s += 1.0;
+        int Z = __float_as_int(P1.w) & 0xff;
+        double zf = P1.y;
+        atomicAdd(sd + 4 + Z, 1.0 - zf);
+        if (zf > 0.0 && Z < ZNUC) atomicAdd(sd + 4 + Z + 1, zf);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        w_s += __shfl_down_sync(0xffffffffu, w_s, o);
+        ke_s += __shfl_down_sync(0xffffffffu, ke_s, o);
+        ki_s += __shfl_down_sync(0xffffffffu, ki_s, o);
+        n_s += __shfl_down_sync(0xffffffffu, n_s, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(sd + 0, w_s); atomicAdd(sd + 1, ke_s); atomicAdd(sd + 2, ki_s); atomicAdd(sd + 3, n_s);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nv; k += blockDim.x)
+        if (sd[k] != 0.0) atomicAdd(a.out + k, sd[k]);
+}
+
+__global__ void k_sumsq(const float *x, int n, double *out)
+{
+    double v = 0.0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) v += (double)x[k] * x[k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(out, v);
+}
+
+__global__ void k_photon_energy(const double *ph, int ncell, int nb, const float *hv, double *out)
+{
+    double v = 0.0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ncell * nb; k += gridDim.x * blockDim.x)
+        v += ph[k] * hv[k % nb];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(out, v);
+}
+
+__global__ void k_philox_check(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    U4 r = philox(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3], k0, k1);
+    out[4 * i] = r.x; out[4 * i + 1] = r.y; out[4 * i + 2] = r.z; out[4 * i + 3] = r.w;
+}
+
+}  // namespace pic

@@ -1,0 +1,241 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Same seeded inputs on both sides; particles are matched by id.  Tolerances:
+per-particle momenta within 1e-5 relative (FP32 state against FP64),
+charge states, K vacancies and created-particle ids exact, except for
+threshold flips (a decision r < P taken differently because P differs in
+the last FP32 bits), which are counted and bounded.
+"""
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import pic_inputs as P
+from parity_util import compare_state, match, momentum_errors, U_RTOL
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle  # noqa: E402
+import paper_1704_01202_gb300 as pkg  # noqa: E402
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    pkg.build()
+    oracle.build()
+
+
+def _run_both(cfg, tables, st, nsteps, pulse=None, photons=None, fields=None, step0=0):
+    g = pkg.Slab(cfg, tables, pulse)
+    g.load(st)
+    o = oracle.OracleSlab(cfg, tables, pulse)
+    o.load(st)
+    if photons is not None:
+        g.set_photons(photons)
+        o.set_photons(photons)
+    if fields is not None:
+        g.set_fields(fields)
+        o.set_fields(fields)
+    g.step(nsteps)
+    g.sync()
+    o.step(nsteps)
+    return g, o
+
+
+def _assert_parity(res, n_e, max_bad_frac=1e-3):
+    assert res["e_same_ids"], res
+    assert res["i_same_ids"], res
+    assert res["Z_mismatch"] <= max(1, int(1e-3 * n_e)), res
+    assert res["nK_mismatch"] <= max(1, int(1e-3 * n_e)), res
+    assert res["e_bad"] <= max(2, int(max_bad_frac * n_e)), res
+    assert res["i_bad"] <= max(2, int(max_bad_frac * n_e)), res
+
+
+def test_philox_device_equals_oracle():
+    rng = np.random.default_rng(1)
+    ctr = rng.integers(0, 2 ** 32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    key = np.array([0x12345678, 0x9abcdef0], dtype=np.uint32)
+    dev = pkg.philox_check(ctr, key)
+    ref = np.array([oracle.philox(c, key) for c in ctr])
+    assert np.array_equal(dev, ref)
+
+
+def test_oracle_philox_equals_curand(tmp_path):
+    """The oracle's Philox4x32-10 against cuRAND's Philox4_32_10 (an
+    independent implementation of the same published generator)."""
+    exe = tmp_path / "curand_philox"
+    r = subprocess.run(["nvcc", pkg.ARCH, "-O2", "-o", str(exe), os.path.join(HERE, "cuda", "curand_philox.cu")],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    rng = np.random.default_rng(2)
+    rows = rng.integers(0, 2 ** 32, size=(512, 6), dtype=np.uint64)
+    rows[:8, :4] = 0
+    inp = "\n".join(" ".join(str(int(v)) for v in row) for row in rows)
+    r = subprocess.run([str(exe)], input=inp, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = np.array([[int(x) for x in line.split()] for line in r.stdout.strip().splitlines()], dtype=np.uint64)
+    ref = np.array([oracle.philox(row[:4].astype(np.uint32), row[4:].astype(np.uint32)) for row in rows],
+                   dtype=np.uint64)
+    assert np.array_equal(got, ref)
+
+
+def test_single_step_1d(tables):
+    cfg = P.cfg_small_1d(nx=48)
+    st = P.init_particles(cfg)
+    g, o = _run_both(cfg, tables, st, 1)
+    res = compare_state(g.electrons(), o.electrons(), g.ions(), o.ions(), cfg.nx, cfg.ny)
+    _assert_parity(res, st.n_e)
+    assert res["e_err_p999"] < U_RTOL, res
+
+
+def _busy(cfg, seed=5):
+    st = P.init_particles(cfg)
+    st = P.perturb_ions(st, seed, frac_hollow=0.4, z_spread=3, zfrac_share=0.25)
+    return P.neutralize(st, cfg)
+
+
+@pytest.mark.parametrize("ny", [1, 6])
+def test_single_step_every_process(tables, ny):
+    """A rad step with dense and scarce photons, hollow ions, fractional
+    charges and random fields: every branch of the step runs."""
+    cfg = P.cfg_small_1d(nx=40, ny=ny, dx_nm=2.0, dy_nm=2.0, ppc_e=64, ppc_i=16, T_e_eV=25.0,
+                         flags=P.F_ALL, rad_every=1)
+    pl = P.Pulse(I_peak_Wcm2=3e17, fwhm_fs=30.0, t_peak_fs=0.0, hv_eV=1700.0, n_bins=3, bandwidth_eV=400.0)
+    tab = dict(tables)
+    tab["sigma_photo"] = tables["sigma_photo"] * 50.0
+    st = _busy(cfg)
+    ph = P.photons_uniform(cfg, pl, 1.0)
+    ph[:, cfg.nx // 2:, :] = 0.3 * cfg.w_ion
+    f = P.random_fields(cfg, 3, e_amp=2e-3, b_amp=2e-3)
+    g, o = _run_both(cfg, tab, st, 1, pulse=pl, photons=ph, fields=f)
+    res = compare_state(g.electrons(), o.electrons(), g.ions(), o.ions(), cfg.nx, cfg.ny)
+    _assert_parity(res, st.n_e)
+    dg = g.diagnostics()
+    _, co = o.tallies()
+    for k in ("ION", "REC", "PH0", "PH2", "PART", "AUG", "KA"):
+        assert abs(dg["counts"][k] - co[k]) <= max(1, int(1e-3 * co[k])), (k, dg["counts"][k], co[k])
+    assert co["ION"] > 0 and co["REC"] > 0 and co["PH0"] > 0 and co["AUG"] > 0 and co["PART"] > 0
+    # photon field, fields and current of the step
+    pg, po = g.photons(), o.photons()
+    assert np.allclose(pg, po, rtol=1e-6, atol=1e-9 * cfg.w_ion)
+    fg, fo = g.fields(), o.fields()
+    for k in fg:
+        scale = np.abs(fo[k]).max() + 1e-12
+        assert np.abs(fg[k] - fo[k]).max() < 1e-5 * scale, k
+    jg, jo = g.current(), o.current()
+    for c in range(3):
+        scale = np.abs(jo[c]).max() + 1e-12
+        assert np.abs(jg[c] - jo[c]).max() < 2e-5 * scale, c
+
+
+def test_multi_step_1d(tables):
+    """Twenty steps of the plain 1D slab run independently on both sides."""
+    cfg = P.cfg_small_1d(nx=32)
+    st = P.init_particles(cfg)
+    g, o = _run_both(cfg, tables, st, 20)
+    res = compare_state(g.electrons(), o.electrons(), g.ions(), o.ions(), cfg.nx, cfg.ny)
+    assert res["e_same_ids"] and res["i_same_ids"], res
+    assert res["Z_mismatch"] == 0, res
+    assert res["e_bad"] <= int(0.01 * st.n_e), res
+
+
+def test_multi_step_2d_photo(tables):
+    cfg = P.cfg_small_1d(nx=24, ny=8, dx_nm=5.0, dy_nm=5.0, ppc_e=64, ppc_i=16, flags=P.F_ALL)
+    pl = P.pulse_foil_2d(t_peak_fs=0.0, I_peak_Wcm2=5e17)
+    st = P.init_particles(cfg)
+    g, o = _run_both(cfg, tables, st, 12, pulse=pl)
+    res = compare_state(g.electrons(), o.electrons(), g.ions(), o.ions(), cfg.nx, cfg.ny)
+    assert res["e_same_ids"] and res["i_same_ids"], res
+    assert res["Z_mismatch"] <= 2, res
+    assert res["e_bad"] <= int(0.01 * st.n_e), res
+
+
+def test_deterministic_rerun(tables):
+    cfg = P.cfg_small_1d(nx=24, ny=4, dx_nm=5.0, dy_nm=5.0, ppc_e=64, ppc_i=16, flags=P.F_ALL)
+    pl = P.pulse_foil_2d(t_peak_fs=0.0, I_peak_Wcm2=5e17)
+    st = P.init_particles(cfg)
+    outs = []
+    for _ in range(2):
+        g = pkg.Slab(cfg, tables, pl)
+        g.load(st)
+        g.step(10)
+        e = g.electrons()
+        o = np.argsort(e["id"])
+        outs.append((e["id"][o], e["u"][o], g.fields()["ex"]))
+        g.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert np.array_equal(outs[0][2], outs[1][2])
+
+
+def test_energy_bookkeeping_gpu(tables):
+    """Collisions and atomic processes only: the FP64 energy bookkeeping of
+    the device (kinetic + ionization + photons + transmitted/escaped)
+    balances to FP32 rounding per step, over 200 steps."""
+    cfg = P.cfg_small_1d(nx=32, flags=P.F_COLL_EE | P.F_COLL_EI | P.F_IONIZE | P.F_RECOMB | P.F_PHOTO | P.F_DECAY)
+    pl = P.Pulse(I_peak_Wcm2=5e17, fwhm_fs=10.0, t_peak_fs=2.0, hv_eV=1700.0)
+    st = P.init_particles(cfg)
+    g = pkg.Slab(cfg, tables, pl)
+    g.load(st)
+
+    def total(d):
+        return d["ke_e"] + d["ke_i"] + d["e_ion"] + d["e_phot"] + d["e_ka_esc"] + d["e_trans"] - d["e_inc"]
+
+    e0 = total(g.diagnostics())
+    g.step(200)
+    d = g.diagnostics()
+    assert d["counts"]["ION"] > 0 and d["counts"]["PH0"] > 0
+    assert abs(total(d) - e0) / e0 < 1e-6
+
+
+def test_full_size_sampled_cells(tables):
+    """The 2048 x 256 foil at full size, one step in the launch
+    configuration of the bench (collisions and atomic processes; push off so
+    that cells are independent).  64 sampled cells are run by the oracle on
+    their own and compared particle by particle."""
+    cfg = P.cfg_foil_2d(flags=P.F_COLL_EE | P.F_COLL_EI | P.F_IONIZE | P.F_RECOMB, T_e_eV=80.0)
+    st = P.init_particles(cfg)
+    g = pkg.Slab(cfg, tables)
+    g.load(st)
+    g.step(1)
+    g.sync()
+    rng = np.random.default_rng(0)
+    cells = np.sort(rng.choice(cfg.ncell, 64, replace=False))
+    ce = (np.floor(st.eY).astype(np.int64) * cfg.nx + np.floor(st.eX).astype(np.int64))
+    ci = (np.floor(st.iY).astype(np.int64) * cfg.nx + np.floor(st.iX).astype(np.int64))
+    sub_cfg = P.SlabConfig(**{**cfg.to_dict(), "nx": 64, "ny": 1})
+    rank = {c: k for k, c in enumerate(cells)}
+    me = np.isin(ce, cells)
+    mi = np.isin(ci, cells)
+    sub = P.ParticleState(
+        eX=np.array([rank[c] for c in ce[me]]) + (st.eX[me] - np.floor(st.eX[me])), eY=np.full(me.sum(), 0.5),
+        eu=st.eu[me], ew=st.ew[me], eid=st.eid[me],
+        iX=np.array([rank[c] for c in ci[mi]]) + (st.iX[mi] - np.floor(st.iX[mi])), iY=np.full(mi.sum(), 0.5),
+        iu=st.iu[mi], izf=st.izf[mi], iZ=st.iZ[mi], inK=st.inK[mi], iid=st.iid[mi])
+    o = oracle.OracleSlab(sub_cfg, tables)
+    o.load(sub)
+    o.step(1)
+    oe, oi = o.electrons(), o.ions()
+    ge, gi = g.electrons(), g.ions()
+    gce = (np.floor(ge["Y"]).astype(np.int64) * cfg.nx + np.floor(ge["X"]).astype(np.int64))
+    gci = (np.floor(gi["Y"]).astype(np.int64) * cfg.nx + np.floor(gi["X"]).astype(np.int64))
+    sel_e = np.isin(gce, cells)
+    sel_i = np.isin(gci, cells)
+    ge_s = {k: v[sel_e] for k, v in ge.items()}
+    gi_s = {k: v[sel_i] for k, v in gi.items()}
+    res = compare_state(ge_s, oe, gi_s, oi, 64, 1)
+    _assert_parity(res, me.sum())
+    # properties over the whole slab: charge neutrality kept to FP32 rounding
+    qe = ge["w"].astype(np.float64).sum()
+    qi = cfg.w_ion * (gi["Z"] + gi["zf"].astype(np.float64)).sum()
+    q0e = st.ew.sum()
+    q0i = cfg.w_ion * (st.iZ + st.izf).sum()
+    assert abs((qe - qi) - (q0e - q0i)) < 1e-6 * qi
