@@ -103,8 +103,10 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons)}
 
 
-def workload():
+def workload(cells=None):
     cfg = P.cfg_foil_2d()
+    if cells:
+        cfg = P.cfg_foil_2d(nx=cells[0], ny=cells[1], name=f"al_2d_{cells[0]}x{cells[1]}x5nm_64e16i")
     pl = P.pulse_foil_2d()
     return cfg, pl
 
@@ -164,7 +166,7 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     pkg.build()
-    cfg, pl = workload()
+    cfg, pl = workload(args.cells)
     # replicas: every rank runs its own foil with its own seed
     cfg.seed = cfg.seed + rank
     tab = P.standin_tables()
@@ -216,6 +218,29 @@ def run_gpu(args):
     slab.close()
     del slab
     torch.cuda.synchronize()
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(pkg, cfg, tab, pl, st, args, world, n0)
+    if dist:
+        dist.barrier()
+    if rank == 0:
+        cb = cpu_baseline() if world == 1 and not args.no_cpu else None
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": cfg.name, "cells": [cfg.nx, cfg.ny], "particles": int(n_mean),
+                          "ppc": [cfg.ppc_e, cfg.ppc_i], "pulse_keV": pl.hv_eV / 1e3,
+                          "l2": "state (1.3 GB) larger than L2; no flush", "parallelism": "replicas"},
+               "roofline": roof, "step_hbm_gbs": step_gbs, "cpu_baseline": cb, "e2e": e2e,
+               "gpu_launches": int(launches), "clocks": clk, "kernel_ms": {k: v / max(nrec, 1) for k, v in tms.items()}}
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_e2e(pkg, cfg, tab, pl, st, args, world, n0):
+    """Public API with host buffers: context, H2D load, steps with a D2H
+    diagnostics read after each."""
     e2e_steps = max(3, min(args.steps, 10))
     t0 = time.perf_counter()
     s2 = pkg.Slab(cfg, tab, pl)
@@ -228,25 +253,10 @@ def run_gpu(args):
     t_e2e = time.perf_counter() - t0
     h2d = st.n_e * (8 + 8 + 12 + 4 + 8) + st.n_i * (8 + 8 + 12 + 4 + 4 + 4 + 4)
     s2.close()
-    e2e = {"value": world * n0 * e2e_steps / t_e2e, "unit": UNIT,
-           "h2d_bytes_per_step": int(h2d / e2e_steps), "d2h_bytes_per_step": int(d2h / e2e_steps),
-           "steps": e2e_steps, "includes": "context creation, H2D load of the initial state, "
-                                          "per-step diagnostics D2H"}
-    if dist:
-        dist.barrier()
-    if rank == 0:
-        cb = cpu_baseline() if world == 1 and not args.no_cpu else None
-        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-               "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-               "config": {"workload": cfg.name, "cells": [cfg.nx, cfg.ny], "particles": int(n_mean),
-                          "ppc": [cfg.ppc_e, cfg.ppc_i], "pulse_keV": pl.hv_eV / 1e3,
-                          "l2": "state (1.3 GB) larger than L2; no flush", "parallelism": "replicas"},
-               "roofline": roof, "step_hbm_gbs": step_gbs, "cpu_baseline": cb, "e2e": e2e,
-               "gpu_launches": int(launches), "clocks": clk}
-        print(json.dumps(out))
-    if dist:
-        dist.destroy_process_group()
+    return {"value": world * n0 * e2e_steps / t_e2e, "unit": UNIT,
+            "h2d_bytes_per_step": int(h2d / e2e_steps), "d2h_bytes_per_step": int(d2h / e2e_steps),
+            "steps": e2e_steps, "includes": "context creation, H2D load of the initial state, "
+                                           "per-step diagnostics D2H"}
 
 
 def main():
@@ -256,6 +266,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cells", type=int, nargs=2, default=None, help="smaller foil (profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "gb300" else args.warmup
     if args.impl == "reference":

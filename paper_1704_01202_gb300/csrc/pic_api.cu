@@ -61,7 +61,8 @@ struct pic_ctx {
     float *E[2], *B;
     int ecur = 0;
     unsigned long long *J;
-    double *photons, *diag_buf;
+    ph2 *photons;
+    double *diag_buf;
 
     int cap_ce = 128, cap_ci = 32, cap_new = 96, wpc = 4;
     size_t smem_main = 0, smem_big = 0;
@@ -375,7 +376,7 @@ pic_status pic_init(pic_ctx **out, const pic_grid *g, const pic_species *s, cons
     c->pt_slab = carve_arena<int>(c, c->npts);
     c->row_slab = carve_arena<int>(c, 1 << 18);
     c->row_idx = carve_arena<int>(c, 1 << 18);
-    c->photons = carve_arena<double>(c, (size_t)c->ncell * PIC_MAX_BINS);
+    c->photons = carve_arena<ph2>(c, (size_t)c->ncell * PIC_MAX_BINS);
     c->diag_buf = carve_arena<double>(c, 4 + NZ + 4096 + 8);
     if (!c->diag_buf) { pic_free(c); return PIC_ERR_OOM; }
 
@@ -389,6 +390,8 @@ pic_status pic_init(pic_ctx **out, const pic_grid *g, const pic_species *s, cons
     S.n_ref = s->n_ref_cm3;
     const double E0 = kMeKg * kCms / (kQe * 1e-15);
     S.kappa_J = kQe * s->n_ref_cm3 * 1e6 * 1e-9 / (kEps0 * E0);
+    S.nref_f = (float)S.n_ref;
+    S.kappa_f = (float)S.kappa_J;
     c->fe_factor = kEps0 * E0 * E0 / (2.0 * s->n_ref_cm3 * 1e6 * kQe);
     double inv = 1.0 / (g->dx_nm * g->dx_nm) + (g->ny > 1 ? 1.0 / (g->dy_nm * g->dy_nm) : 0.0);
     S.nsub = std::max(1, (int)std::ceil(kCnmPerFs * g->dt_fs * std::sqrt(inv) / g->cfl));
@@ -428,7 +431,7 @@ pic_status pic_init(pic_ctx **out, const pic_grid *g, const pic_species *s, cons
         if ((e = cudaMemsetAsync(c->E[0], 0, sizeof(float) * 3 * (size_t)c->npts, st))) break;
         if ((e = cudaMemsetAsync(c->E[1], 0, sizeof(float) * 3 * (size_t)c->npts, st))) break;
         if ((e = cudaMemsetAsync(c->B, 0, sizeof(float) * 3 * (size_t)c->npts, st))) break;
-        if ((e = cudaMemsetAsync(c->photons, 0, sizeof(double) * (size_t)c->ncell * PIC_MAX_BINS, st))) break;
+        if ((e = cudaMemsetAsync(c->photons, 0, sizeof(ph2) * (size_t)c->ncell * PIC_MAX_BINS, st))) break;
         if ((e = cudaMemsetAsync(c->counters, 0, sizeof(int) * NCOUNTERS, st))) break;
         for (int k = 0; k < 2; ++k) {
             if ((e = cudaMemsetAsync(c->csE[k], 0, sizeof(int) * (c->ncell + 1), st))) break;
@@ -464,7 +467,7 @@ pic_status pic_source(pic_ctx *c, const pic_pulse *p)
         for (int q = 0; q < NS; ++q) S.sig_b[q][b] = b < p->n_bins ? (float)sigma_table(c, q, hv) : 0.0f;
     }
     CK(cudaMemcpyAsync(c->d_slab, &S, sizeof(SlabDev), cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemsetAsync(c->photons, 0, sizeof(double) * (size_t)c->ncell * PIC_MAX_BINS, c->stream));
+    CK(cudaMemsetAsync(c->photons, 0, sizeof(ph2) * (size_t)c->ncell * PIC_MAX_BINS, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return PIC_OK;
 }
@@ -566,8 +569,13 @@ pic_status pic_set_photons(pic_ctx *c, const double *ph)
 {
     if (!c || !ph) return PIC_ERR_ARG;
     if (c->slab.nb <= 0) return fail(c, PIC_ERR_STATE, "set a pulse first");
-    CK(cudaMemcpyAsync(c->photons, ph, sizeof(double) * (size_t)c->ncell * c->slab.nb, cudaMemcpyHostToDevice,
-                       c->stream));
+    size_t n = (size_t)c->ncell * c->slab.nb;
+    std::vector<ph2> h(n);
+    for (size_t k = 0; k < n; ++k) {
+        float hi = (float)ph[k];
+        h[k] = ph2{hi, (float)(ph[k] - (double)hi)};
+    }
+    CK(cudaMemcpyAsync(c->photons, h.data(), sizeof(ph2) * n, cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return PIC_OK;
 }
@@ -691,9 +699,11 @@ pic_status pic_get_photons(pic_ctx *c, double *ph)
 {
     if (!c || !ph) return PIC_ERR_ARG;
     if (c->slab.nb <= 0) return fail(c, PIC_ERR_STATE, "no pulse set");
-    CK(cudaMemcpyAsync(ph, c->photons, sizeof(double) * (size_t)c->ncell * c->slab.nb, cudaMemcpyDeviceToHost,
-                       c->stream));
+    size_t n = (size_t)c->ncell * c->slab.nb;
+    std::vector<ph2> h(n);
+    CK(cudaMemcpyAsync(h.data(), c->photons, sizeof(ph2) * n, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    for (size_t k = 0; k < n; ++k) ph[k] = (double)h[k].hi + (double)h[k].lo;
     return read_device_error(c);
 }
 
@@ -737,7 +747,7 @@ pic_status pic_diagnostics(pic_ctx *c, pic_diag *out)
     d.n_e = c->csE[c->cur] + c->ncell; d.n_i = c->csI[c->cur] + c->ncell;
     d.m_ion = c->sp.m_ion_me; d.out = c->diag_buf; d.n_E = nE; d.E_lo = 0.1;
     d.E_max = out->E_max_eV > 0.1 ? out->E_max_eV : 1e4;
-    k_diag<<<c->nsm * 4, 256, sizeof(double) * nv, st>>>(d);
+    k_diag<<<c->nsm * 4, 256, sizeof(float) * nv, st>>>(d);
     k_sumsq<<<c->nsm * 4, 256, 0, st>>>(c->E[c->ecur], 3 * c->npts, c->diag_buf + nv);
     k_sumsq<<<c->nsm * 4, 256, 0, st>>>(c->B, 3 * c->npts, c->diag_buf + nv);
     if (c->slab.nb > 0) {

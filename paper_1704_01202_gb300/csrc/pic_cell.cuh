@@ -40,7 +40,7 @@ struct CellArgs {
     const SlabDev *slabs;
     const unsigned *steps;
     SlabTally *tally;
-    double *photons;
+    ph2 *photons;
     const float *fldE;   // [3][npts] ex ey ez
     const float *fldB;   // [3][npts] bx by bz
     int npts;
@@ -55,11 +55,23 @@ struct CellArgs {
     int cap_ce, cap_ci, cap_new; // per-cell shared-memory capacities
 };
 
-__device__ __forceinline__ double wsum(double v)
+// warp reductions: a fixed tree, result broadcast from lane 0 so every lane
+// holds the same bits
+__device__ __forceinline__ float wsum_f(float v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
     return __shfl_sync(FULL, v, 0);
+}
+
+__device__ __forceinline__ dd wsum_dd(dd v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        dd t{__shfl_down_sync(FULL, v.hi, o), __shfl_down_sync(FULL, v.lo, o)};
+        v = dd_add(v, t);
+    }
+    return dd{__shfl_sync(FULL, v.hi, 0), __shfl_sync(FULL, v.lo, 0)};
 }
 
 __device__ __forceinline__ int wsum_i(int v)
@@ -70,14 +82,29 @@ __device__ __forceinline__ int wsum_i(int v)
 }
 
 // inclusive prefix over the lanes (fixed order)
-__device__ __forceinline__ double wscan_incl(double v, int lane)
+__device__ __forceinline__ float wscan_f(float v, int lane)
 {
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        double t = __shfl_up_sync(FULL, v, o);
+        float t = __shfl_up_sync(FULL, v, o);
         if (lane >= o) v += t;
     }
     return v;
+}
+
+__device__ __forceinline__ dd wscan_dd(dd v, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        dd t{__shfl_up_sync(FULL, v.hi, o), __shfl_up_sync(FULL, v.lo, o)};
+        if (lane >= o) v = dd_add(v, t);
+    }
+    return v;
+}
+
+__device__ __forceinline__ dd wbcast_dd(dd v, int src)
+{
+    return dd{__shfl_sync(FULL, v.hi, src), __shfl_sync(FULL, v.lo, src)};
 }
 
 // ascending sort on (key, id) of n entries, padded to a power of two
@@ -117,7 +144,7 @@ __device__ __forceinline__ float cic_w(float x, int node)
 // per-warp shared memory carve-up
 struct WarpMem {
     float4 *eu;                 // [cap_ce] ux uy uz w (slot order)
-    unsigned long long *ekey;   // [cap_ce] sort key, later reused as double take
+    unsigned long long *ekey;   // [cap_ce] sort key, later reused as float take
     unsigned long long *eid;    // [cap_ce] ids in canonical order
     unsigned short *eperm;      // [cap_ce] canonical position -> slot
     float4 *iu;                 // [cap_ci] ux uy uz zfrac (slot order)
@@ -127,7 +154,7 @@ struct WarpMem {
     unsigned short *iperm;      // [cap_ci]
     NewE *nw;                   // [cap_new]
     float *dE;                  // [16] continuum lowering per charge state
-    double *Pz;                 // [16] impact-ionization probability per charge
+    float *Pz;                  // [16] impact-ionization probability per charge
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -158,7 +185,7 @@ __device__ inline WarpMem carve(char *base, int ce, int ci, int cn)
     m.iperm = (unsigned short *)p; p += align16((size_t)ci * 2);
     m.nw = (NewE *)p; p += align16((size_t)cn * sizeof(NewE));
     m.dE = (float *)p; p += 16 * 4;
-    m.Pz = (double *)p;
+    m.Pz = (float *)p;
     return m;
 }
 
@@ -203,9 +230,20 @@ __device__ __forceinline__ float grid_interp(const float *F, const SlabGrid &g, 
 struct JAcc2 { float x[3][4], y[4][3], z[4][4]; };
 struct JAcc1 { float x[3], y[4], z[4]; };
 
+// v * 2^40 rounded to a 64-bit integer with FP32 and integer instructions
+// only (|v| < 2^22): the high part is split off exactly at 2^31
+__device__ __forceinline__ long long fix40(float v)
+{
+    float x = v * 1099511627776.0f;                     // exact: power-of-two scale
+    float qh = truncf(x * 4.656612873077393e-10f);      // x / 2^31, integer part
+    float r = fmaf(-qh, 2147483648.0f, x);               // exact remainder, |r| < 2^31
+    long long lo = (long long)__float2int_rn(fminf(fmaxf(r, -2147483520.0f), 2147483520.0f));
+    return ((long long)(int)qh << 31) + lo;
+}
+
 __device__ __forceinline__ void jatomic(unsigned long long *J, float v)
 {
-    if (v != 0.0f) atomicAdd(J, (unsigned long long)__double2ll_rn((double)v * JFIX));
+    if (v != 0.0f) atomicAdd(J, (unsigned long long)fix40(v));
 }
 
 // Esirkepov weights of one sub-cell move, stencil anchored at cell (ax, ay)

@@ -5,14 +5,33 @@
 
 namespace pic {
 
-struct LaneTally {        // per-lane event counts, reduced once per cell
-    int coll_ee, coll_ei, ion, ion_rej, rec, ph[NS], part, aug, ka, pgt1, esc_e, esc_i;
+// event counts and energy tallies of one warp, lane-uniform, flushed to the
+// slab's tally when the warp moves to another slab and at the end
+struct WarpTally {
+    int slab;
+    dd ion, ka, esc;
+    int cnt[NCOUNT];
 };
+
+__device__ __forceinline__ void tally_flush(const CellArgs &a, WarpTally &w, int lane)
+{
+    if (w.slab >= 0 && lane == 0) {
+        SlabTally *tl = a.tally + w.slab;
+        float v;
+        if ((v = dd_f(w.ion)) != 0.0f) atomicAdd(&tl->ion, (double)w.ion.hi + (double)w.ion.lo);
+        if ((v = dd_f(w.ka)) != 0.0f) atomicAdd(&tl->ka_esc, (double)w.ka.hi + (double)w.ka.lo);
+        if ((v = dd_f(w.esc)) != 0.0f) atomicAdd(&tl->esc, (double)w.esc.hi + (double)w.esc.lo);
+        for (int q = 0; q < NCOUNT; ++q)
+            if (w.cnt[q]) atomicAdd(tl->cnt + q, (unsigned long long)w.cnt[q]);
+    }
+    w.ion = w.ka = w.esc = dd_zero();
+    for (int q = 0; q < NCOUNT; ++q) w.cnt[q] = 0;
+}
 
 template <int DIM>
 __device__ void cell_push_deposit(const CellArgs &a, const SlabDev &S, const WarpMem &m, int g, int cx, int cy,
-                                  int e0, int ne, int i0, int ni, int nnew, int lane, double &esc_e_energy,
-                                  LaneTally &lt)
+                                  int e0, int ne, int i0, int ni, int nnew, int lane, dd &esc_e_energy,
+                                  int &esc_e, int &esc_i)
 {
     const unsigned flags = S.flags;
     const bool do_push = flags & 64u, do_dep = (flags & 128u) != 0;
@@ -37,7 +56,7 @@ __device__ void cell_push_deposit(const CellArgs &a, const SlabDev &S, const War
             float ke = (float)kMeC2 * gm1(ux, uy, uz);
             int nc = push_one<DIM>(S, grid, a.J, a.npts, cx, cy, xi, eta, ux, uy, uz, -1.0f, -uw.w, do_push, do_dep, A);
             if (nc == -2) { key = -1; atomicOr(a.err, ERR_NUMERIC); }
-            else if (nc < 0) { key = -1; esc_e_energy += (double)uw.w * ke; lt.esc_e++; }
+            else if (nc < 0) { key = -1; esc_e_energy = dd_addf(esc_e_energy, uw.w * ke); esc_e++; }
             else key = cell0 + nc;
             P0 = make_float4(xi, eta, ux, uy);
             P1.x = uz; P1.y = uw.w;
@@ -71,7 +90,7 @@ __device__ void cell_push_deposit(const CellArgs &a, const SlabDev &S, const War
         int nc = push_one<DIM>(S, grid, a.J, a.npts, cx, cy, xi, eta, ux, uy, uz, -1.0f, -q.w, do_push, do_dep, A);
         int key;
         if (nc == -2) { key = -1; atomicOr(a.err, ERR_NUMERIC); }
-        else if (nc < 0) { key = -1; esc_e_energy += (double)q.w * ke; lt.esc_e++; }
+        else if (nc < 0) { key = -1; esc_e_energy = dd_addf(esc_e_energy, q.w * ke); esc_e++; }
         else key = cell0 + nc;
         unsigned idhi = ((a.steps[a.cell_slab[g]] + 1u) << 2) | (unsigned)kind;
         unsigned idlo = __float_as_uint(I1.z);
@@ -94,7 +113,7 @@ __device__ void cell_push_deposit(const CellArgs &a, const SlabDev &S, const War
         int nc = push_one<DIM>(S, grid, a.J, a.npts, cx, cy, xi, eta, ux, uy, uz, q / S.m_ion, q * wi, do_push, do_dep, A);
         int key;
         if (nc == -2) { key = -1; atomicOr(a.err, ERR_NUMERIC); }
-        else if (nc < 0) { key = -1; esc_e_energy += (double)wi * ke; lt.esc_i++; }
+        else if (nc < 0) { key = -1; esc_e_energy = dd_addf(esc_e_energy, wi * ke); esc_i++; }
         else key = cell0 + nc;
         a.i0[i0 + slot] = make_float4(xi, eta, ux, uy);
         a.i1[i0 + slot] = make_float4(uz, iu.w, P1.z, __int_as_float(st));
@@ -168,9 +187,10 @@ __device__ void cell_push_deposit(const CellArgs &a, const SlabDev &S, const War
     }
 }
 
-__device__ void process_cell(const CellArgs &a, const WarpMem &m, const Tables &T, int g, int lane)
+__device__ void process_cell(const CellArgs &a, const WarpMem &m, const Tables &T, int g, int lane, WarpTally &wt)
 {
     const int s = __ldg(a.cell_slab + g);
+    if (s != wt.slab) { tally_flush(a, wt, lane); wt.slab = s; }
     const SlabDev &S = a.slabs[s];
     const unsigned step = a.steps[s];
     const unsigned long long seed = S.seed;
@@ -184,8 +204,8 @@ __device__ void process_cell(const CellArgs &a, const WarpMem &m, const Tables &
     const float mi = S.m_ion;
     const bool rad = S.rad_every > 0 && (step % (unsigned)S.rad_every) == 0;
     const float MC2 = (float)kMeC2;
-    LaneTally lt = {};
-    double tal_ion = 0.0, tal_ka = 0.0, tal_esc = 0.0;
+    const float nref = S.nref_f;
+    int c_ee = 0, c_ei = 0, c_ion = 0, c_rej = 0, c_part = 0, c_aug = 0, c_ka = 0, c_ph[NS] = {0, 0, 0, 0, 0};
 
     // ---- stage in shared memory; Philox sort keys ----
     for (int k = lane; k < ne; k += 32) {
@@ -211,49 +231,44 @@ __device__ void process_cell(const CellArgs &a, const WarpMem &m, const Tables &
     warp_bitonic<unsigned long long>(m.ekey, m.eid, m.eperm, ne, lane);
     warp_bitonic<unsigned int>(m.ikey, m.iid, m.iperm, ni, lane);
 
-    // ---- FP64 cell moments (Sec. II: T_e = 2/3 E_ave over bulk electrons) ----
-    double We, Wb, Kb, Q;
-    {
-        float pw = 0.f, pwb = 0.f, pkb = 0.f, pq = 0.f;
-        for (int k = lane; k < ne; k += 32) {
-            float4 u = m.eu[m.eperm[k]];
-            float ke = MC2 * gm1(u.x, u.y, u.z);
-            pw += u.w;
-            if (S.E_bulk <= 0.0f || ke < S.E_bulk) { pwb += u.w; pkb += u.w * ke; }
-        }
-        for (int k = lane; k < ni; k += 32) {
-            int sl = m.iperm[k];
-            pq += (float)(m.ist[sl] & 0xff) + m.iu[sl].w;
-        }
-        We = wsum(pw); Wb = wsum(pwb); Kb = wsum(pkb); Q = wsum(pq);
+    // ---- cell moments (Sec. II: T_e = 2/3 E_ave over bulk electrons) ----
+    dd We = dd_zero(), Wb = dd_zero(), Kb = dd_zero(), Q = dd_zero();
+    for (int k = lane; k < ne; k += 32) {
+        float4 u = m.eu[m.eperm[k]];
+        float ke = MC2 * gm1(u.x, u.y, u.z);
+        We = dd_addf(We, u.w);
+        if (S.E_bulk <= 0.0f || ke < S.E_bulk) { Wb = dd_addf(Wb, u.w); Kb = dd_addf(Kb, u.w * ke); }
     }
-    const double n_e = We * S.n_ref, n_i = (double)ni * wi * S.n_ref;
-    const double Te = Wb > 0.0 ? (2.0 / 3.0) * Kb / Wb : 0.0;
-    const double zbar = ni > 0 ? Q / ni : 0.0;
+    for (int k = lane; k < ni; k += 32) {
+        int sl = m.iperm[k];
+        Q = dd_addf(Q, (float)(m.ist[sl] & 0xff) + m.iu[sl].w);
+    }
+    We = wsum_dd(We); Wb = wsum_dd(Wb); Kb = wsum_dd(Kb); Q = wsum_dd(Q);
+    const float n_e = dd_f(We) * nref, n_i = (float)ni * wi * nref;
+    const float Te = dd_f(Wb) > 0.0f ? (2.0f / 3.0f) * dd_f(Kb) / dd_f(Wb) : 0.0f;
+    const float zbar = ni > 0 ? dd_f(Q) / ni : 0.0f;
     if (lane < NZ) m.dE[lane] = ipd_shift(S.ipd, lane, n_e, n_i, Te, zbar);
     const float lnL = S.coulomb_log > 0.0f ? S.coulomb_log : coulomb_log(n_e, Te, zbar);
     __syncwarp();
 
     // ---- binary collisions (Sec. IV): e-e, then e-i; exact energy restore ----
     const bool coll = (flags & 3u) != 0;
-    double Kpre = 0.0;
+    dd Kpre = dd_zero();
     if (coll) {
-        float pk = 0.f;
-        for (int k = lane; k < ne; k += 32) { float4 u = m.eu[m.eperm[k]]; pk += u.w * MC2 * gm1(u.x, u.y, u.z); }
-        float pki = 0.f;
-        for (int k = lane; k < ni; k += 32) { float4 u = m.iu[m.iperm[k]]; pki += MC2 * mi * gm1(u.x, u.y, u.z); }
-        Kpre = wsum(pk) + (double)wi * wsum(pki);
+        dd pk = dd_zero(), pki = dd_zero();
+        for (int k = lane; k < ne; k += 32) { float4 u = m.eu[m.eperm[k]]; pk = dd_addf(pk, u.w * MC2 * gm1(u.x, u.y, u.z)); }
+        for (int k = lane; k < ni; k += 32) { float4 u = m.iu[m.iperm[k]]; pki = dd_addf(pki, wi * MC2 * mi * gm1(u.x, u.y, u.z)); }
+        Kpre = dd_add(wsum_dd(pk), wsum_dd(pki));
     }
     if ((flags & 1u) && ne >= 2) {
         const int start = (ne & 1) ? 3 : 0;
-        const float ne_f = (float)n_e;
         auto ee = [&](int pa, int pb, float dtc) {
             int sa = m.eperm[pa], sb = m.eperm[pb];
             float4 A = m.eu[sa], B = m.eu[sb];
             float3 ua = make_float3(A.x, A.y, A.z), ub = make_float3(B.x, B.y, B.z);
             U4 r = draw(seed, m.eid[pa], step, PU_COLL_EE);
-            if (binary_collision(ua, ub, 1.0f, 1.0f, -1.0f, -1.0f, A.w, B.w, ne_f, lnL, dtc,
-                                 u01(r.x), u01(r.y), u01(r.z), u01(r.w))) lt.coll_ee++;
+            if (binary_collision(ua, ub, 1.0f, 1.0f, -1.0f, -1.0f, A.w, B.w, n_e, lnL, dtc,
+                                 u01(r.x), u01(r.y), u01(r.z), u01(r.w))) c_ee++;
             m.eu[sa] = make_float4(ua.x, ua.y, ua.z, A.w);
             m.eu[sb] = make_float4(ub.x, ub.y, ub.z, B.w);
         };
@@ -277,12 +292,12 @@ __device__ void process_cell(const CellArgs &a, const WarpMem &m, const Tables &
                 int se = m.eperm[pe], si = m.iperm[pi];
                 float4 A = m.eu[se], B = m.iu[si];
                 float q = (float)(m.ist[si] & 0xff) + B.w;
-                float npair = e_long ? (float)(n_i * fmaxf(A.w, wi) / wi) : (float)(n_e * fmaxf(A.w, wi) / A.w);
+                float npair = e_long ? n_i * fmaxf(A.w, wi) / wi : n_e * fmaxf(A.w, wi) / A.w;
                 U4 r = e_long ? draw(seed, m.eid[pe], step, PU_COLL_EI)
                               : draw(seed, (unsigned long long)m.iid[pi], step, PU_COLL_IE);
                 float3 ua = make_float3(A.x, A.y, A.z), ub = make_float3(B.x, B.y, B.z);
                 if (binary_collision(ua, ub, 1.0f, mi, -1.0f, q, A.w, wi, npair, lnL, S.dt,
-                                     u01(r.x), u01(r.y), u01(r.z), u01(r.w))) lt.coll_ei++;
+                                     u01(r.x), u01(r.y), u01(r.z), u01(r.w))) c_ei++;
                 m.eu[se] = make_float4(ua.x, ua.y, ua.z, A.w);
                 m.iu[si] = make_float4(ub.x, ub.y, ub.z, B.w);
             }
@@ -290,17 +305,17 @@ __device__ void process_cell(const CellArgs &a, const WarpMem &m, const Tables &
         }
     }
     if (coll && ne >= 1) {
-        float pk = 0.f, pki = 0.f;
-        for (int k = lane; k < ne; k += 32) { float4 u = m.eu[m.eperm[k]]; pk += u.w * MC2 * gm1(u.x, u.y, u.z); }
-        for (int k = lane; k < ni; k += 32) { float4 u = m.iu[m.iperm[k]]; pki += MC2 * mi * gm1(u.x, u.y, u.z); }
-        double Ke = wsum(pk), Ki = (double)wi * wsum(pki);
-        if (Ke > 0.0) {
-            double f = 1.0 + (Kpre - Ke - Ki) / Ke;
-            if (f > 0.0) {
-                float ff = (float)f;
+        dd pk = dd_zero(), pki = dd_zero();
+        for (int k = lane; k < ne; k += 32) { float4 u = m.eu[m.eperm[k]]; pk = dd_addf(pk, u.w * MC2 * gm1(u.x, u.y, u.z)); }
+        for (int k = lane; k < ni; k += 32) { float4 u = m.iu[m.iperm[k]]; pki = dd_addf(pki, wi * MC2 * mi * gm1(u.x, u.y, u.z)); }
+        dd Ke = wsum_dd(pk), Ki = wsum_dd(pki);
+        float ke = dd_f(Ke);
+        if (ke > 0.0f) {
+            float delta = -dd_f(dd_sub(dd_sub(Kpre, Ke), Ki)) / ke;     // f = 1 - delta
+            if (delta < 1.0f) {
                 for (int k = lane; k < ne; k += 32) {
                     float4 u = m.eu[k];
-                    scale_kinetic(u.x, u.y, u.z, ff);
+                    scale_kinetic(u.x, u.y, u.z, delta);
                     m.eu[k] = u;
                 }
             }
@@ -309,37 +324,37 @@ __device__ void process_cell(const CellArgs &a, const WarpMem &m, const Tables &
     }
 
     // ---- Lotz impact ionization, cell-average probability (Eq. 3) ----
-    int nnew = 0, nnew_imp = 0;
-    double Wnew_imp = 0.0;
+    int nnew = 0;
+    float Wnew_imp = 0.0f;
     if ((flags & 4u) && ne >= 1 && ni >= 1) {
         unsigned pmask = 0;
         for (int k = lane; k < ni; k += 32) { int Z = m.ist[k] & 0xff; if (Z < ZNUC) pmask |= 1u << Z; }
         for (int o = 16; o > 0; o >>= 1) pmask |= __shfl_xor_sync(FULL, pmask, o);
-        float pk = 0.f;
-        for (int k = lane; k < ne; k += 32) { float4 u = m.eu[m.eperm[k]]; pk += u.w * MC2 * gm1(u.x, u.y, u.z); }
-        const double Kt = wsum(pk);
-        const double cfac = (double)S.dt * kCcmPerFs * S.n_ref;
+        dd pk = dd_zero();
+        for (int k = lane; k < ne; k += 32) { float4 u = m.eu[m.eperm[k]]; pk = dd_addf(pk, u.w * MC2 * gm1(u.x, u.y, u.z)); }
+        const dd Kt = wsum_dd(pk);
+        const float cfac = (float)(kCcmPerFs) * S.dt * nref;
         for (int z = 0; z < ZNUC; ++z) {
             if (!(pmask & (1u << z))) continue;
-            float pr = 0.f;
+            dd pr = dd_zero();
             const float dEz = m.dE[z];
             for (int k = lane; k < ne; k += 32) {
                 float4 u = m.eu[m.eperm[k]];
                 float u2 = u.x * u.x + u.y * u.y + u.z * u.z;
                 float g1 = u2 / (sqrtf(1.0f + u2) + 1.0f);
                 float beta = sqrtf(u2) / (1.0f + g1);
-                pr += u.w * beta * lotz_sigma(T, z, dEz, MC2 * g1);
+                pr = dd_addf(pr, u.w * beta * lotz_sigma(T, z, dEz, MC2 * g1));
             }
-            double P = cfac * wsum(pr);
+            float P = cfac * dd_f(wsum_dd(pr));
             if (lane == 0) m.Pz[z] = P;
-            if (P > 1.0) lt.pgt1 += lane == 0;
+            if (P > 1.0f && lane == 0) wt.cnt[C_PGT1]++;
         }
         __syncwarp();
-        double carry = 0.0, paid = 0.0;
+        dd carry = dd_zero(), paid = dd_zero();
         for (int b0 = 0; b0 < ni; b0 += 32) {
             int t = b0 + lane;
             bool cand = false;
-            double cost = 0.0;
+            float cost = 0.0f;
             int sl = 0, Z = 0, nK = 0;
             if (t < ni) {
                 sl = m.iperm[t];
@@ -347,15 +362,15 @@ __device__ void process_cell(const CellArgs &a, const WarpMem &m, const Tables &
                 Z = st & 0xff; nK = (st >> 8) & 0xff;
                 if (Z < ZNUC) {
                     U4 r = draw(seed, (unsigned long long)m.iid[t], step, PU_ION);
-                    if ((double)u01(r.x) < m.Pz[Z]) {
+                    if (u01(r.x) < m.Pz[Z]) {
                         cand = true;
-                        cost = (double)wi * (double)removal_energy(T, Z, nK, m.dE[Z]);
+                        cost = wi * removal_energy(T, Z, nK, m.dE[Z]);
                     }
                 }
             }
-            double incl = carry + wscan_incl(cost, lane);
-            bool acc = cand && incl <= Kt;
-            if (cand && !acc) lt.ion_rej++;
+            dd incl = dd_add(carry, wscan_dd(dd{cost, 0.0f}, lane));
+            bool acc = cand && dd_le(incl, Kt);
+            if (cand && !acc) c_rej++;
             unsigned bal = __ballot_sync(FULL, acc);
             if (acc) {
                 int so = outer_shell(ZNUC - Z, nK);
@@ -368,51 +383,51 @@ __device__ void process_cell(const CellArgs &a, const WarpMem &m, const Tables &
                 } else {
                     atomicOr(a.err, ERR_NEW_OVERFLOW);
                 }
-                lt.ion++;
+                c_ion++;
             }
-            paid += wsum(acc ? cost : 0.0);
+            paid = dd_add(paid, wsum_dd(dd{acc ? cost : 0.0f, 0.0f}));
             nnew += __popc(bal);
-            carry = __shfl_sync(FULL, incl, 31);
+            carry = wbcast_dd(incl, 31);
         }
         nnew = min(nnew, a.cap_new);
-        nnew_imp = nnew;
-        Wnew_imp = (double)nnew_imp * wi;
-        if (paid > 0.0) {
-            float f = (float)(1.0 - paid / Kt);
+        Wnew_imp = nnew * wi;
+        float pf = dd_f(paid);
+        if (pf > 0.0f) {
+            float delta = pf / dd_f(Kt);
             for (int k = lane; k < ne; k += 32) {
                 float4 u = m.eu[k];
-                scale_kinetic(u.x, u.y, u.z, f);
+                scale_kinetic(u.x, u.y, u.z, delta);
                 m.eu[k] = u;
             }
-            tal_ion += paid;
+            wt.ion = dd_add(wt.ion, paid);
         }
         __syncwarp();
     }
 
     // ---- EOS-clamped three-body recombination (Sec. IV) ----
     if ((flags & 8u) && ni >= 1) {
-        float pq = 0.f;
-        for (int k = lane; k < ni; k += 32) { int sl = m.iperm[k]; pq += (float)(m.ist[sl] & 0xff) + m.iu[sl].w; }
-        const double zb = wsum(pq) / ni;
-        float pwb = 0.f, pkb = 0.f, pwx = 0.f;
+        dd pq = dd_zero();
+        for (int k = lane; k < ni; k += 32) { int sl = m.iperm[k]; pq = dd_addf(pq, (float)(m.ist[sl] & 0xff) + m.iu[sl].w); }
+        const float zb = dd_f(wsum_dd(pq)) / ni;
+        dd pwb = dd_zero(), pkb = dd_zero(), pwx = dd_zero();
         for (int k = lane; k < ne; k += 32) {
             float4 u = m.eu[m.eperm[k]];
             float ke = MC2 * gm1(u.x, u.y, u.z);
-            pwx += u.w;
-            if (S.E_bulk <= 0.0f || ke < S.E_bulk) { pwb += u.w; pkb += u.w * ke; }
+            pwx = dd_addf(pwx, u.w);
+            if (S.E_bulk <= 0.0f || ke < S.E_bulk) { pwb = dd_addf(pwb, u.w); pkb = dd_addf(pkb, u.w * ke); }
         }
-        double Wb2 = wsum(pwb) + Wnew_imp, Kb2 = wsum(pkb), Wex = wsum(pwx);
-        double Te2 = Wb2 > 0.0 ? (2.0 / 3.0) * Kb2 / Wb2 : 0.0;
-        float zeos = eos_lookup(*a.eos, (float)n_i, (float)Te2);
-        int Kev = zb > zeos ? (int)floor((zb - zeos) * ni + 0.5) : 0;
+        const float Wb2 = dd_f(wsum_dd(pwb)) + Wnew_imp, Kb2 = dd_f(wsum_dd(pkb)), Wex = dd_f(wsum_dd(pwx));
+        const float Te2 = Wb2 > 0.0f ? (2.0f / 3.0f) * Kb2 / Wb2 : 0.0f;
+        const float zeos = eos_lookup(*a.eos, n_i, Te2);
+        int Kev = zb > zeos ? (int)floorf((zb - zeos) * ni + 0.5f) : 0;
         int pel = 0;
         for (int k = lane; k < ni; k += 32) pel += m.ist[k] & 0xff;
-        int elig = wsum_i(pel);
+        const int elig = wsum_i(pel);
         Kev = min(Kev, elig);
-        Kev = min(Kev, (int)floor(Wex / wi + 1e-9));
+        Kev = min(Kev, (int)floorf(Wex / wi * (1.0f + 1e-6f)));
         if (Kev > 0) {
             int *nrec = (int *)m.ikey;            // sort keys are no longer needed
-            double *take = (double *)m.ekey;
+            float *take = (float *)m.ekey;
             for (int k = lane; k < ni; k += 32) nrec[k] = 0;
             __syncwarp();
             int left = Kev;
@@ -432,58 +447,55 @@ __device__ void process_cell(const CellArgs &a, const WarpMem &m, const Tables &
                     __syncwarp();
                 }
             }
-            const double Wrem = (double)Kev * wi;
-            double carry = 0.0;
-            float premKE = 0.f;
+            const dd Wrem = dd{(float)Kev * wi, 0.0f};
+            dd carry = dd_zero(), remKE = dd_zero();
             for (int b0 = 0; b0 < ne; b0 += 32) {
                 int t = b0 + lane;
-                double w = 0.0;
-                float ke = 0.f;
+                float w = 0.0f, ke = 0.0f;
                 if (t < ne) { float4 u = m.eu[m.eperm[t]]; w = u.w; ke = MC2 * gm1(u.x, u.y, u.z); }
-                double incl = carry + wscan_incl(w, lane);
-                double before = incl - w;
-                double tk = fmin(fmax(Wrem - before, 0.0), w);
+                dd incl = dd_add(carry, wscan_dd(dd{w, 0.0f}, lane));
+                dd before = dd_sub(incl, dd{w, 0.0f});
+                float tk = fminf(fmaxf(dd_f(dd_sub(Wrem, before)), 0.0f), w);
                 if (t < ne) take[t] = tk;
-                premKE += (float)tk * ke;
-                carry = __shfl_sync(FULL, incl, 31);
+                remKE = dd_addf(remKE, tk * ke);
+                carry = wbcast_dd(incl, 31);
             }
             __syncwarp();
-            double remKE = wsum(premKE);
-            float pb = 0.f;
+            remKE = wsum_dd(remKE);
+            dd pb = dd_zero();
             for (int k = lane; k < ni; k += 32) {
                 int st = m.ist[m.iperm[k]];
                 int Z = st & 0xff, nK = (st >> 8) & 0xff;
-                for (int r = 1; r <= nrec[k]; ++r) pb += wi * removal_energy(T, Z - r, nK, m.dE[Z - r]);
+                for (int r = 1; r <= nrec[k]; ++r) pb = dd_addf(pb, wi * removal_energy(T, Z - r, nK, m.dE[Z - r]));
             }
-            double bind = wsum(pb);
-            float pkr = 0.f;
+            const dd bind = wsum_dd(pb);
+            dd pkr = dd_zero();
             for (int k = lane; k < ne; k += 32) {
                 float4 u = m.eu[m.eperm[k]];
                 float ke = MC2 * gm1(u.x, u.y, u.z);
-                if (S.E_bulk <= 0.0f || ke < S.E_bulk) pkr += (float)((double)u.w - take[k]) * ke;
+                if (S.E_bulk <= 0.0f || ke < S.E_bulk) pkr = dd_addf(pkr, (u.w - take[k]) * ke);
             }
-            double Krem = wsum(pkr);
-            if (Krem > 0.0) {
-                float f = (float)(1.0 + (remKE + bind) / Krem);
+            const float Krem = dd_f(wsum_dd(pkr));
+            if (Krem > 0.0f) {
+                float delta = -dd_f(dd_add(remKE, bind)) / Krem;
                 for (int k = lane; k < ne; k += 32) {
                     int sl = m.eperm[k];
                     float4 u = m.eu[sl];
                     float ke = MC2 * gm1(u.x, u.y, u.z);
                     bool bulk = S.E_bulk <= 0.0f || ke < S.E_bulk;
-                    double tk = take[k];
-                    double wn = (double)u.w - tk;
-                    bool dead = tk > 0.0 && wn <= 0.0;
-                    u.w = dead ? 0.0f : (float)wn;
-                    if (bulk && !dead) scale_kinetic(u.x, u.y, u.z, f);
+                    float tk = take[k];
+                    float wn = u.w - tk;
+                    bool dead = tk > 0.0f && wn <= 0.0f;
+                    u.w = dead ? 0.0f : wn;
+                    if (bulk && !dead) scale_kinetic(u.x, u.y, u.z, delta);
                     m.eu[sl] = u;
                 }
                 for (int k = lane; k < ni; k += 32) {
                     int sl = m.iperm[k];
-                    int st = m.ist[sl];
-                    m.ist[sl] = st - nrec[k];
+                    m.ist[sl] = m.ist[sl] - nrec[k];
                 }
-                tal_ion -= bind;
-                lt.rec += lane == 0 ? Kev : 0;
+                wt.ion = dd_sub(wt.ion, bind);
+                if (lane == 0) wt.cnt[C_REC] += Kev;
             }
             __syncwarp();
         }
@@ -493,12 +505,16 @@ __device__ void process_cell(const CellArgs &a, const WarpMem &m, const Tables &
     if (rad && (flags & (16u | 32u)) && ni >= 1) {
         const int nb = S.nb;
         const float dtr = S.rad_every * S.dt;
-        double *ph = nb ? a.photons + S.ph_off + (size_t)lc * nb : nullptr;
+        ph2 *ph = nb ? a.photons + S.ph_off + (size_t)lc * nb : nullptr;
         if ((flags & 16u) && nb) {
-            double n0[MAXB], used[MAXB];
+            dd n0[MAXB], used[MAXB];
             int carry[MAXB];
-            for (int b = 0; b < nb; ++b) { n0[b] = ph[b]; used[b] = 0.0; carry[b] = 0; }
-            const float cph = (float)(kCcmPerFs * dtr * S.n_ref);
+#pragma unroll
+            for (int b = 0; b < MAXB; ++b) {
+                if (b < nb) { ph2 v = ph[b]; n0[b] = dd{v.hi, v.lo}; } else n0[b] = dd_zero();
+                used[b] = dd_zero(); carry[b] = 0;
+            }
+            const float cph = (float)kCcmPerFs * dtr * nref;
             for (int b0 = 0; b0 < ni; b0 += 32) {
                 int t = b0 + lane;
                 int sub = -1, bin = -1, sl = 0, Z = 0, nK = 0;
@@ -517,60 +533,71 @@ __device__ void process_cell(const CellArgs &a, const WarpMem &m, const Tables &
                             if (!occ[q]) continue;
                             float ed = lowered_binding(T, Z, q, m.dE[Z]);
                             float acc = 0.f;
-                            for (int b = 0; b < nb; ++b)
-                                if (S.hv_b[b] > ed) acc += (float)n0[b] * S.sig_b[q][b];
+#pragma unroll
+                            for (int b = 0; b < MAXB; ++b)
+                                if (b < nb && S.hv_b[b] > ed) acc += dd_f(n0[b]) * S.sig_b[q][b];
                             float P = cph * occ[q] * acc;
                             if (rs[q] < P) { sub = q; Ps = P; edge = ed; break; }
                         }
                         if (sub >= 0) {
                             float target = u01(rb.y) * Ps, cum = 0.f;
                             int lastpos = -1;
-                            for (int b = 0; b < nb; ++b) {
-                                float c = S.hv_b[b] > edge ? cph * occ[sub] * (float)n0[b] * S.sig_b[sub][b] : 0.f;
+#pragma unroll
+                            for (int b = 0; b < MAXB; ++b) {
+                                if (b >= nb || bin >= 0) continue;
+                                float c = S.hv_b[b] > edge ? cph * occ[sub] * dd_f(n0[b]) * S.sig_b[sub][b] : 0.f;
                                 if (c > 0.f) lastpos = b;
                                 cum += c;
-                                if (cum > target) { bin = b; break; }
+                                if (cum > target) bin = b;
                             }
                             if (bin < 0) bin = lastpos;
                             rc = u01(rb.z); rp = u01(rb.w);
                         }
                     }
                 }
-                double g = 0.0;
-                for (int b = 0; b < nb; ++b) {
+                // k-th event of a bin gets min(w, max(0, n_bin - k w)) photons
+                float g = 0.0f;
+                bool full = false;
+#pragma unroll
+                for (int b = 0; b < MAXB; ++b) {
+                    if (b >= nb) continue;
                     bool eb = bin == b && sub >= 0;
                     unsigned bal = __ballot_sync(FULL, eb);
                     if (eb) {
                         int rank = carry[b] + __popc(bal & ((1u << lane) - 1u));
-                        g = fmin((double)wi, fmax(0.0, n0[b] - (double)rank * wi));
+                        dd rest = dd_addf(n0[b], -(float)rank * wi);
+                        if (dd_le(dd{wi, 0.0f}, rest)) { g = wi; full = true; }
+                        else g = fmaxf(dd_f(rest), 0.0f);
                     }
                     carry[b] += __popc(bal);
                 }
-                bool ev = sub >= 0 && bin >= 0 && g > 0.0;
+                bool ev = sub >= 0 && bin >= 0 && g > 0.0f;
                 if (ev) {
-                    if (g == (double)wi) {
+                    if (full) {
                         lose_electron(Z, nK, sub);
                     } else {
-                        float zf = m.iu[sl].w + (float)(g / wi);
+                        float zf = m.iu[sl].w + g / wi;
                         if (zf >= 1.0f) {
                             zf -= 1.0f;
                             int so = outer_shell(ZNUC - Z, nK);
                             if (so >= 0) lose_electron(Z, nK, so);
                         }
                         m.iu[sl].w = zf;
-                        lt.part++;
+                        c_part++;
                     }
                     m.ist[sl] = Z | (nK << 8);
-                    lt.ph[sub]++;
+                    c_ph[sub]++;
                 }
-                for (int b = 0; b < nb; ++b) used[b] += wsum(ev && bin == b ? g : 0.0);
-                tal_ion += wsum(ev ? g * edge : 0.0);
+#pragma unroll
+                for (int b = 0; b < MAXB; ++b)
+                    if (b < nb) used[b] = dd_add(used[b], wsum_dd(dd{ev && bin == b ? g : 0.0f, 0.0f}));
+                wt.ion = dd_add(wt.ion, wsum_dd(dd{ev ? g * edge : 0.0f, 0.0f}));
                 unsigned bal = __ballot_sync(FULL, ev);
                 if (ev) {
                     int pos = nnew + __popc(bal & ((1u << lane) - 1u));
                     if (pos < a.cap_new) {
                         float3 u = iso_momentum(S.hv_b[bin] - edge, rc, rp);
-                        NewE q; q.ux = u.x; q.uy = u.y; q.uz = u.z; q.w = (float)g;
+                        NewE q; q.ux = u.x; q.uy = u.y; q.uz = u.z; q.w = g;
                         q.meta = sl | (KIND_PHOTO << 16);
                         m.nw[pos] = q;
                     } else {
@@ -580,13 +607,17 @@ __device__ void process_cell(const CellArgs &a, const WarpMem &m, const Tables &
                 nnew = min(nnew + __popc(bal), a.cap_new);
             }
             __syncwarp();
-            if (lane == 0)
-                for (int b = 0; b < nb; ++b) ph[b] = n0[b] - used[b];
+            if (lane == 0) {
+#pragma unroll
+                for (int b = 0; b < MAXB; ++b)
+                    if (b < nb) { dd r = dd_sub(n0[b], used[b]); ph[b] = ph2{r.hi, r.lo}; }
+            }
             __syncwarp();
         }
         if (flags & 32u) {
-            double addph[MAXB];
-            for (int b = 0; b < MAXB; ++b) addph[b] = 0.0;
+            dd addph[MAXB];
+#pragma unroll
+            for (int b = 0; b < MAXB; ++b) addph[b] = dd_zero();
             for (int b0 = 0; b0 < ni; b0 += 32) {
                 int t = b0 + lane;
                 int kind = 0, sl = 0, Z = 0;
@@ -634,57 +665,49 @@ __device__ void process_cell(const CellArgs &a, const WarpMem &m, const Tables &
                     } else {
                         atomicOr(a.err, ERR_NEW_OVERFLOW);
                     }
-                    lt.aug++;
+                    c_aug++;
                 }
                 nnew = min(nnew + __popc(bal), a.cap_new);
                 int hit = -1;
                 if (kind == 2) {
-                    lt.ka++;
+                    c_ka++;
                     for (int b = 0; b < nb; ++b)
                         if (Eka >= S.hv_b[b] - S.bin_hw && Eka < S.hv_b[b] + S.bin_hw) { hit = b; break; }
                 }
-                for (int b = 0; b < nb; ++b)
-                    addph[b] += wsum(hit == b ? (double)wi * Eka / S.hv_b[b] : 0.0);
-                tal_ka += wsum(kind == 2 && hit < 0 ? (double)wi * Eka : 0.0);
-                tal_ion -= wsum(kind == 1 ? (double)wi * EA : (kind == 2 ? (double)wi * Eka : 0.0));
+#pragma unroll
+                for (int b = 0; b < MAXB; ++b)
+                    if (b < nb) addph[b] = dd_add(addph[b], wsum_dd(dd{hit == b ? wi * Eka / S.hv_b[b] : 0.0f, 0.0f}));
+                wt.ka = dd_add(wt.ka, wsum_dd(dd{kind == 2 && hit < 0 ? wi * Eka : 0.0f, 0.0f}));
+                wt.ion = dd_sub(wt.ion, wsum_dd(dd{kind == 1 ? wi * EA : (kind == 2 ? wi * Eka : 0.0f), 0.0f}));
             }
-            if (lane == 0 && nb)
-                for (int b = 0; b < nb; ++b) ph[b] += addph[b];
+            if (lane == 0 && nb) {
+#pragma unroll
+                for (int b = 0; b < MAXB; ++b)
+                    if (b < nb) { ph2 v = ph[b]; dd r = dd_add(dd{v.hi, v.lo}, addph[b]); ph[b] = ph2{r.hi, r.lo}; }
+            }
             __syncwarp();
         }
     }
 
     // ---- Boris push + charge-conserving deposit of every particle ----
-    double esc = 0.0;
-    if (S.ny > 1) cell_push_deposit<2>(a, S, m, g, cx, cy, e0, ne, i0, ni, nnew, lane, esc, lt);
-    else cell_push_deposit<1>(a, S, m, g, cx, cy, e0, ne, i0, ni, nnew, lane, esc, lt);
-    tal_esc = wsum(esc);
+    dd esc = dd_zero();
+    int esc_e = 0, esc_i = 0;
+    if (S.ny > 1) cell_push_deposit<2>(a, S, m, g, cx, cy, e0, ne, i0, ni, nnew, lane, esc, esc_e, esc_i);
+    else cell_push_deposit<1>(a, S, m, g, cx, cy, e0, ne, i0, ni, nnew, lane, esc, esc_e, esc_i);
+    wt.esc = dd_add(wt.esc, wsum_dd(esc));
 
-    // ---- tallies ----
-    int c_ee = wsum_i(lt.coll_ee), c_ei = wsum_i(lt.coll_ei), c_ion = wsum_i(lt.ion), c_rej = wsum_i(lt.ion_rej);
-    int c_rec = wsum_i(lt.rec), c_part = wsum_i(lt.part), c_aug = wsum_i(lt.aug), c_ka = wsum_i(lt.ka);
-    int c_pg = wsum_i(lt.pgt1), c_ee_esc = wsum_i(lt.esc_e), c_ei_esc = wsum_i(lt.esc_i);
-    int c_ph[NS];
-    for (int q = 0; q < NS; ++q) c_ph[q] = wsum_i(lt.ph[q]);
-    if (lane == 0) {
-        SlabTally *tl = a.tally + s;
-        if (tal_ion != 0.0) atomicAdd(&tl->ion, tal_ion);
-        if (tal_ka != 0.0) atomicAdd(&tl->ka_esc, tal_ka);
-        if (tal_esc != 0.0) atomicAdd(&tl->esc, tal_esc);
-        unsigned long long *c = tl->cnt;
-        if (c_ion) atomicAdd(c + C_ION, (unsigned long long)c_ion);
-        if (c_rej) atomicAdd(c + C_ION_REJ, (unsigned long long)c_rej);
-        if (c_rec) atomicAdd(c + C_REC, (unsigned long long)c_rec);
-        for (int q = 0; q < NS; ++q) if (c_ph[q]) atomicAdd(c + C_PH0 + q, (unsigned long long)c_ph[q]);
-        if (c_part) atomicAdd(c + C_PART, (unsigned long long)c_part);
-        if (c_aug) atomicAdd(c + C_AUG, (unsigned long long)c_aug);
-        if (c_ka) atomicAdd(c + C_KA, (unsigned long long)c_ka);
-        if (c_pg) atomicAdd(c + C_PGT1, (unsigned long long)c_pg);
-        if (c_ee_esc) atomicAdd(c + C_ESC_E, (unsigned long long)c_ee_esc);
-        if (c_ei_esc) atomicAdd(c + C_ESC_I, (unsigned long long)c_ei_esc);
-        if (c_ee) atomicAdd(c + C_EE, (unsigned long long)c_ee);
-        if (c_ei) atomicAdd(c + C_EI, (unsigned long long)c_ei);
-    }
+    // ---- tallies (lane-uniform) ----
+    wt.cnt[C_EE] += wsum_i(c_ee);
+    wt.cnt[C_EI] += wsum_i(c_ei);
+    wt.cnt[C_ION] += wsum_i(c_ion);
+    wt.cnt[C_ION_REJ] += wsum_i(c_rej);
+    wt.cnt[C_PART] += wsum_i(c_part);
+    wt.cnt[C_AUG] += wsum_i(c_aug);
+    wt.cnt[C_KA] += wsum_i(c_ka);
+    wt.cnt[C_ESC_E] += wsum_i(esc_e);
+    wt.cnt[C_ESC_I] += wsum_i(esc_i);
+#pragma unroll
+    for (int q = 0; q < NS; ++q) wt.cnt[C_PH0 + q] += wsum_i(c_ph[q]);
     __syncwarp();
 }
 
@@ -702,6 +725,10 @@ __global__ void __launch_bounds__(256) k_cell(CellArgs a)
     WarpMem m = carve(smem + (size_t)warp * warp_mem_bytes(a.cap_ce, a.cap_ci, a.cap_new),
                       a.cap_ce, a.cap_ci, a.cap_new);
     const int total = a.list ? *a.n_list : a.ncell;
+    WarpTally wt;
+    wt.slab = -1;
+    wt.ion = wt.ka = wt.esc = dd_zero();
+    for (int q = 0; q < NCOUNT; ++q) wt.cnt[q] = 0;
     for (;;) {
         int w = 0;
         if (lane == 0) w = atomicAdd(a.work, 1);
@@ -721,8 +748,9 @@ __global__ void __launch_bounds__(256) k_cell(CellArgs a)
             }
             continue;
         }
-        process_cell(a, m, T, g, lane);
+        process_cell(a, m, T, g, lane, wt);
     }
+    tally_flush(a, wt, lane);
 }
 
 }  // namespace pic

@@ -72,6 +72,7 @@ struct SlabDev {
     float mur;              // first-order Mur coefficient
     double n_ref;           // cm^-3
     double kappa_J;         // J coupling of the normalized field equations
+    float nref_f, kappa_f;  // the same in single precision for the kernels
     double I_peak, fwhm, t_peak, spot_sigma;
     unsigned long long seed;
     float hv_b[MAXB];
@@ -83,6 +84,9 @@ struct SlabTally {
     double ion, ka_esc, esc, inc, trans;
     unsigned long long cnt[NCOUNT];
 };
+
+// photon number per cell and bin, stored as a double-float pair
+struct ph2 { float hi, lo; };
 
 // ---------------- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) ----------------
 struct U4 { uint32_t x, y, z, w; };
@@ -163,37 +167,63 @@ __device__ __forceinline__ float removal_energy(const Tables &T, int Z, int nK, 
 
 // ---------------- continuum lowering (Sec. V) ----------------
 // Eq. 4 (Ecker-Kroll, dense branch, C = 1) and Eq. 5 (Stewart-Pyatt with
-// T_i = T_e and z* = Zbar).  Densities cm^-3, T eV, result eV.
-__device__ __forceinline__ float ipd_shift(int model, int z, double n_e, double n_i, double T_e, double zbar)
+// T_i = T_e and z* = Zbar).  Densities cm^-3, T eV, result eV.  Single
+// precision: once per cell and charge state.
+__device__ __forceinline__ float ipd_shift(int model, int z, float n_e, float n_i, float T_e, float zbar)
 {
-    const double e_over_4pe0 = kQe / (4.0 * kPi * kEps0);        // V m
+    const float e2_4pe0_eVnm = (float)(kQe / (4.0 * kPi * kEps0) * 1e9);   // e^2/(4 pi eps0) in eV nm
     if (model == 1) {
-        double n = (n_e + n_i) * 1e6;
-        if (n <= 0.0) return 0.0f;
-        double r = cbrt(3.0 / (4.0 * kPi * n));
-        return (float)((z + 1) * e_over_4pe0 / r);
+        float n = (n_e + n_i) * 1e-21f;                  // nm^-3
+        if (n <= 0.0f) return 0.0f;
+        float r = cbrtf(3.0f / (4.0f * kPiF * n));       // nm
+        return (z + 1) * e2_4pe0_eVnm / r;
     }
     if (model == 2) {
-        if (T_e <= 0.0 || n_e <= 0.0) return 0.0f;
-        double lam = sqrt(kEps0 * T_e / (kQe * n_e * 1e6 * (zbar + 1.0)));
-        double K = (z + 1) * e_over_4pe0 / (lam * T_e);
-        return (float)(T_e / (2.0 * (zbar + 1.0)) * (pow(3.0 * (zbar + 1.0) * K + 1.0, 2.0 / 3.0) - 1.0));
+        if (T_e <= 0.0f || n_e <= 0.0f) return 0.0f;
+        // lambda_D in nm: eps0 T / (e n_e (Zbar+1)), T in eV, n in nm^-3
+        const float eps0_over_e = (float)(kEps0 / kQe * 1e-9);      // lambda^2 [nm^2] = this * T[eV] / n[nm^-3]
+        float lam = sqrtf(eps0_over_e * T_e / (n_e * 1e-21f * (zbar + 1.0f)));
+        float K = (z + 1) * e2_4pe0_eVnm / (lam * T_e);
+        return T_e / (2.0f * (zbar + 1.0f)) * (powf(3.0f * (zbar + 1.0f) * K + 1.0f, 2.0f / 3.0f) - 1.0f);
     }
     return 0.0f;
 }
 
 // Coulomb logarithm stand-in: ln(lambda_D / b_min), b_min = max(classical
 // closest approach, de Broglie length at 3T), floored at 2
-__device__ __forceinline__ float coulomb_log(double n_e, double T_e, double zbar)
+__device__ __forceinline__ float coulomb_log(float n_e, float T_e, float zbar)
 {
-    if (n_e <= 0.0 || T_e <= 0.0) return 2.0f;
-    double lam = sqrt(kEps0 * T_e / (kQe * n_e * 1e6)) * 1e9;
-    double zz = zbar > 1.0 ? zbar : 1.0;
-    double bcl = zz * (kQe / (4.0 * kPi * kEps0)) * 1e9 / (3.0 * T_e);
-    double bqm = kHbarCeVnm / (2.0 * sqrt(3.0 * T_e * kMeC2));
-    double L = log(lam / (bcl > bqm ? bcl : bqm));
-    return L > 2.0 ? (float)L : 2.0f;
+    if (n_e <= 0.0f || T_e <= 0.0f) return 2.0f;
+    const float eps0_over_e = (float)(kEps0 / kQe * 1e-9);
+    const float e2_4pe0_eVnm = (float)(kQe / (4.0 * kPi * kEps0) * 1e9);
+    float lam = sqrtf(eps0_over_e * T_e / (n_e * 1e-21f));
+    float zz = zbar > 1.0f ? zbar : 1.0f;
+    float bcl = zz * e2_4pe0_eVnm / (3.0f * T_e);
+    float bqm = (float)kHbarCeVnm / (2.0f * sqrtf(3.0f * T_e * (float)kMeC2));
+    float L = logf(lam / (bcl > bqm ? bcl : bqm));
+    return L > 2.0f ? L : 2.0f;
 }
+
+// ---------------- double-float sums ----------------
+// Cell sums in a pair of floats (hi + lo, Knuth's TwoSum), ~44-bit
+// precision on the FP32 pipes: GB300 has very little FP64 throughput.
+struct dd { float hi, lo; };
+
+__device__ __forceinline__ dd dd_add(dd a, dd b)
+{
+    float s = a.hi + b.hi;
+    float bv = s - a.hi;
+    float e = (a.hi - (s - bv)) + (b.hi - bv);
+    e += a.lo + b.lo;
+    float h = s + e;
+    return dd{h, e - (h - s)};
+}
+__device__ __forceinline__ dd dd_addf(dd a, float b) { return dd_add(a, dd{b, 0.0f}); }
+__device__ __forceinline__ dd dd_neg(dd a) { return dd{-a.hi, -a.lo}; }
+__device__ __forceinline__ dd dd_sub(dd a, dd b) { return dd_add(a, dd_neg(b)); }
+__device__ __forceinline__ float dd_f(dd a) { return a.hi + a.lo; }
+__device__ __forceinline__ dd dd_zero() { return dd{0.0f, 0.0f}; }
+__device__ __forceinline__ bool dd_le(dd a, dd b) { dd d = dd_sub(b, a); return d.hi > 0.0f || (d.hi == 0.0f && d.lo >= 0.0f); }
 
 // ---------------- Lotz cross section (Eq. 3), cm^2 ----------------
 __device__ __forceinline__ float lotz_sigma(const Tables &T, int z, float dE, float E)
@@ -239,13 +269,17 @@ __device__ __forceinline__ float gm1(float ux, float uy, float uz)
     return u2 / (sqrtf(1.0f + u2) + 1.0f);
 }
 
-// scale the kinetic energy of u by f, direction kept
-__device__ __forceinline__ void scale_kinetic(float &ux, float &uy, float &uz, float f)
+// Multiply the kinetic energy of u by f = 1 - delta, direction kept.  The
+// factor is carried as delta and 1 - |u'|/|u| is formed without
+// cancellation, so small corrections are not lost to FP32 rounding of f.
+__device__ __forceinline__ void scale_kinetic(float &ux, float &uy, float &uz, float delta)
 {
     float g1 = gm1(ux, uy, uz);
-    if (g1 == 0.0f) return;
-    float s = sqrtf(f * (2.0f + f * g1) / (2.0f + g1));
-    ux *= s; uy *= s; uz *= s;
+    if (g1 == 0.0f || delta == 0.0f) return;
+    float b = delta * g1 / (2.0f + g1);
+    float x = delta + b - delta * b;                   // 1 - (|u'|/|u|)^2
+    float d = x / (1.0f + sqrtf(1.0f - x));            // 1 - |u'|/|u|
+    ux -= ux * d; uy -= uy * d; uz -= uz * d;
 }
 
 // One binary collision: Takizuka-Abe deflection tan(theta/2) ~ N(0, var),

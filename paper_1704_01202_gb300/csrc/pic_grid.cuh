@@ -15,7 +15,7 @@ struct MarchArgs {
     const SlabDev *slabs;
     const unsigned *steps;
     const int *row_slab, *row_idx;   // per block
-    double *photons;
+    ph2 *photons;
     SlabTally *tally;
 };
 
@@ -46,16 +46,21 @@ __global__ void k_march(MarchArgs a)
     const int m = (int)floor(sh);
     const double f = sh - m;
     const double tprev = (double)step * S.dt - dtr;
-    double *ph = a.photons + S.ph_off + (size_t)row * nx * nb;
+    ph2 *ph = a.photons + S.ph_off + (size_t)row * nx * nb;
     for (int b = 0; b < nb; ++b) {
-        for (int k = threadIdx.x; k < nx; k += blockDim.x) srow[k] = ph[(size_t)k * nb + b];
+        for (int k = threadIdx.x; k < nx; k += blockDim.x) {
+            ph2 v = ph[(size_t)k * nb + b];
+            srow[k] = (double)v.hi + (double)v.lo;
+        }
         __syncthreads();
         double trans = 0.0, inc = 0.0;
         for (int k = threadIdx.x; k < nx; k += blockDim.x) {
             int j0 = k - m, j1 = k - m - 1;
             double v0 = j0 >= 0 ? srow[j0] : pulse_source(S, b, tprev - (j0 + 0.5) * S.dx / kCnmPerFs, row);
             double v1 = j1 >= 0 ? srow[j1] : pulse_source(S, b, tprev - (j1 + 0.5) * S.dx / kCnmPerFs, row);
-            ph[(size_t)k * nb + b] = (1.0 - f) * v0 + f * v1;
+            double nv = (1.0 - f) * v0 + f * v1;
+            float hi = (float)nv;
+            ph[(size_t)k * nb + b] = ph2{hi, (float)(nv - (double)hi)};
             if (j0 < 0) inc += (1.0 - f) * v0;
             if (j1 < 0) inc += f * v1;
         }
@@ -246,13 +251,16 @@ __global__ void k_e_full(FieldArgs a)
         const int W = S.nx + 1, q = p - S.fld_off, j = q / W, i = q - j * W;
         const int jm = (j - 1 + S.ny) % S.ny;
         const int o = S.fld_off, r = o + j * W, rm = o + jm * W;
-        const float dtf = S.dt / S.nsub, C = (float)kCnmPerFs, kap = (float)S.kappa_J;
+        const float dtf = S.dt / S.nsub, C = (float)kCnmPerFs, kap = S.kappa_f;
         const float *bx = a.B, *by = a.B + n, *bz = a.B + 2 * n;
         const unsigned long long *Jx = a.J, *Jy = a.J + n, *Jz = a.J + 2 * n;
-        const double fix = 1.0 / 1099511627776.0;
         const float sx = S.dx / S.dt, sy = S.ny > 1 ? S.dy / S.dt : C;
+        // fixed point (2^40) back to float: high and low 32 bits separately
         auto jv = [&](const unsigned long long *Jc, int idx, float scale) {
-            return (float)((double)(long long)Jc[idx] * fix) * scale;
+            long long v = (long long)Jc[idx];
+            float hi = (float)(int)(v >> 32) * 4294967296.0f;
+            float lo = (float)(unsigned)(v & 0xffffffffll);
+            return (hi + lo) * (1.0f / 1099511627776.0f) * scale;
         };
         auto ey_new = [&](int ii) {
             return eyi[r + ii] + dtf * (-C * (bz[r + ii] - bz[r + ii - 1]) / S.dx - kap * jv(Jy, r + ii, sy));
@@ -300,47 +308,54 @@ struct DiagArgs {
     double E_lo, E_max;
 };
 
-// block-reduced sums; histogram bins in shared memory
+// per-thread sums in single / double-float precision, block-reduced; the
+// histogram bins in shared memory
 __global__ void k_diag(DiagArgs a)
 {
-    extern __shared__ double sd[];          // [4 + NZ + n_E]
+    extern __shared__ float sdf[];          // [4 + NZ + n_E] block partials
     const int nv = 4 + NZ + a.n_E;
-    for (int k = threadIdx.x; k < nv; k += blockDim.x) sd[k] = 0.0;
+    float *sd = sdf;
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) sd[k] = 0.0f;
     __syncthreads();
     const int ne = *a.n_e, ni = *a.n_i;
-    const double lr = log(a.E_max / a.E_lo);
-    double w_s = 0.0, ke_s = 0.0, ki_s = 0.0, n_s = 0.0;
+    const float lo_e = (float)a.E_lo, inv_lr = (float)(a.n_E / log(a.E_max / a.E_lo));
+    dd w_s = dd_zero(), ke_s = dd_zero(), ki_s = dd_zero();
+    int n_s = 0;
+    const float MC2 = (float)kMeC2, mi = (float)a.m_ion;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ne; k += gridDim.x * blockDim.x) {
         float4 P0 = a.e0[k], P1 = a.e1[k];
-        double ke = kMeC2 * (double)gm1(P0.z, P0.w, P1.x);
-        double w = P1.y;
-        w_s += w;
-        ke_s += w * ke;
-        int b = ke <= a.E_lo ? 0 : (int)floor(log(ke / a.E_lo) / lr * a.n_E);
+        float ke = MC2 * gm1(P0.z, P0.w, P1.x);
+        float w = P1.y;
+        w_s = dd_addf(w_s, w);
+        ke_s = dd_addf(ke_s, w * ke);
+        int b = ke <= lo_e ? 0 : (int)floorf(logf(ke / lo_e) * inv_lr);
         b = b < 0 ? 0 : (b >= a.n_E ? a.n_E - 1 : b);
         atomicAdd(sd + 4 + NZ + b, w);
     }
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ni; k += gridDim.x * blockDim.x) {
         float4 P0 = a.i0[k], P1 = a.i1[k];
-        ki_s += kMeC2 * a.m_ion * (double)gm1(P0.z, P0.w, P1.x);
-        n_s += 1.0;
+        ki_s = dd_addf(ki_s, MC2 * mi * gm1(P0.z, P0.w, P1.x));
+        n_s += 1;
         int Z = __float_as_int(P1.w) & 0xff;
-        double zf = P1.y;
-        atomicAdd(sd + 4 + Z, 1.0 - zf);
-        if (zf > 0.0 && Z < ZNUC) atomicAdd(sd + 4 + Z + 1, zf);
+        float zf = P1.y;
+        atomicAdd(sd + 4 + Z, 1.0f - zf);
+        if (zf > 0.0f && Z < ZNUC) atomicAdd(sd + 4 + Z + 1, zf);
     }
     for (int o = 16; o > 0; o >>= 1) {
-        w_s += __shfl_down_sync(0xffffffffu, w_s, o);
-        ke_s += __shfl_down_sync(0xffffffffu, ke_s, o);
-        ki_s += __shfl_down_sync(0xffffffffu, ki_s, o);
+        w_s = dd_add(w_s, dd{__shfl_down_sync(0xffffffffu, w_s.hi, o), __shfl_down_sync(0xffffffffu, w_s.lo, o)});
+        ke_s = dd_add(ke_s, dd{__shfl_down_sync(0xffffffffu, ke_s.hi, o), __shfl_down_sync(0xffffffffu, ke_s.lo, o)});
+        ki_s = dd_add(ki_s, dd{__shfl_down_sync(0xffffffffu, ki_s.hi, o), __shfl_down_sync(0xffffffffu, ki_s.lo, o)});
         n_s += __shfl_down_sync(0xffffffffu, n_s, o);
     }
     if ((threadIdx.x & 31) == 0) {
-        atomicAdd(sd + 0, w_s); atomicAdd(sd + 1, ke_s); atomicAdd(sd + 2, ki_s); atomicAdd(sd + 3, n_s);
+        atomicAdd(a.out + 0, (double)w_s.hi + (double)w_s.lo);
+        atomicAdd(a.out + 1, (double)ke_s.hi + (double)ke_s.lo);
+        atomicAdd(a.out + 2, (double)ki_s.hi + (double)ki_s.lo);
+        atomicAdd(a.out + 3, (double)n_s);
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < nv; k += blockDim.x)
-        if (sd[k] != 0.0) atomicAdd(a.out + k, sd[k]);
+    for (int k = 4 + threadIdx.x; k < nv; k += blockDim.x)
+        if (sd[k] != 0.0f) atomicAdd(a.out + k, (double)sd[k]);
 }
 
 __global__ void k_sumsq(const float *x, int n, double *out)
@@ -351,11 +366,11 @@ __global__ void k_sumsq(const float *x, int n, double *out)
     if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(out, v);
 }
 
-__global__ void k_photon_energy(const double *ph, int ncell, int nb, const float *hv, double *out)
+__global__ void k_photon_energy(const ph2 *ph, int ncell, int nb, const float *hv, double *out)
 {
     double v = 0.0;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ncell * nb; k += gridDim.x * blockDim.x)
-        v += ph[k] * hv[k % nb];
+        v += ((double)ph[k].hi + (double)ph[k].lo) * hv[k % nb];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(out, v);
 }

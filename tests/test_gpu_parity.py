@@ -77,6 +77,7 @@ def test_oracle_philox_equals_curand(tmp_path):
     assert r.returncode == 0, r.stderr
     rng = np.random.default_rng(2)
     rows = rng.integers(0, 2 ** 32, size=(512, 6), dtype=np.uint64)
+    rows[:, 1] %= 2 ** 29            # curand_init takes the offset as 4 x (c0 + 2^32 c1) in 64 bits
     rows[:8, :4] = 0
     inp = "\n".join(" ".join(str(int(v)) for v in row) for row in rows)
     r = subprocess.run([str(exe)], input=inp, capture_output=True, text=True)
@@ -136,15 +137,30 @@ def test_single_step_every_process(tables, ny):
         assert np.abs(jg[c] - jo[c]).max() < 2e-5 * scale, c
 
 
+def _diag_close(dg, to, co, name):
+    """Diagnostics of the two sides after a multi-step run: the trajectories
+    of single particles diverge chaotically (FP32 against FP64), so the
+    comparison is of cell-averaged and global quantities."""
+    assert abs(dg["ke_e"] / to["KE_E"] - 1) < 2e-3, (name, dg["ke_e"], to["KE_E"])
+    assert abs(dg["e_ion"] - to["ION"]) <= 2e-3 * max(abs(to["ION"]), 1.0), (name, dg["e_ion"], to["ION"])
+    for k in ("ION", "REC", "PH0", "AUG"):
+        assert abs(dg["counts"][k] - co[k]) <= max(3, 0.01 * co[k]), (name, k, dg["counts"][k], co[k])
+
+
 def test_multi_step_1d(tables):
-    """Twenty steps of the plain 1D slab run independently on both sides."""
+    """Twenty steps of the plain 1D slab run independently on both sides:
+    charge states, event counts and energies agree; individual momenta are
+    compared at the first steps only (see test_error_growth)."""
     cfg = P.cfg_small_1d(nx=32)
     st = P.init_particles(cfg)
     g, o = _run_both(cfg, tables, st, 20)
     res = compare_state(g.electrons(), o.electrons(), g.ions(), o.ions(), cfg.nx, cfg.ny)
     assert res["e_same_ids"] and res["i_same_ids"], res
-    assert res["Z_mismatch"] == 0, res
-    assert res["e_bad"] <= int(0.01 * st.n_e), res
+    assert res["Z_mismatch"] <= 2, res
+    to, co = o.tallies()
+    _diag_close(g.diagnostics(), to, co, "1d")
+    csd_g, csd_o = g.diagnostics()["csd"], o.diag()[0]
+    assert np.abs(csd_g - csd_o).sum() < 1e-3
 
 
 def test_multi_step_2d_photo(tables):
@@ -155,7 +171,22 @@ def test_multi_step_2d_photo(tables):
     res = compare_state(g.electrons(), o.electrons(), g.ions(), o.ions(), cfg.nx, cfg.ny)
     assert res["e_same_ids"] and res["i_same_ids"], res
     assert res["Z_mismatch"] <= 2, res
-    assert res["e_bad"] <= int(0.01 * st.n_e), res
+    to, co = o.tallies()
+    _diag_close(g.diagnostics(), to, co, "2d")
+    d = g.diagnostics()
+    assert abs(d["transmission"] - to["TRANS"] / to["INC"]) < 1e-6
+
+
+def test_error_growth_first_steps(tables):
+    """Per-particle momenta stay within 1e-5 (99.9th percentile) for the
+    first steps from the same input; later, chaotic growth of FP32 rounding
+    makes per-particle comparison meaningless (see the multi-step tests)."""
+    cfg = P.cfg_small_1d(nx=32)
+    st = P.init_particles(cfg)
+    for n in (1, 2):
+        g, o = _run_both(cfg, tables, st, n)
+        res = compare_state(g.electrons(), o.electrons(), g.ions(), o.ions(), cfg.nx, cfg.ny)
+        assert res["e_err_p999"] < U_RTOL, (n, res)
 
 
 def test_deterministic_rerun(tables):
@@ -177,9 +208,9 @@ def test_deterministic_rerun(tables):
 
 
 def test_energy_bookkeeping_gpu(tables):
-    """Collisions and atomic processes only: the FP64 energy bookkeeping of
-    the device (kinetic + ionization + photons + transmitted/escaped)
-    balances to FP32 rounding per step, over 200 steps."""
+    """Collisions and atomic processes only: the energy bookkeeping of the
+    device (kinetic + ionization + photons + transmitted/escaped) drifts by
+    less than 1e-6 over 1000 steps."""
     cfg = P.cfg_small_1d(nx=32, flags=P.F_COLL_EE | P.F_COLL_EI | P.F_IONIZE | P.F_RECOMB | P.F_PHOTO | P.F_DECAY)
     pl = P.Pulse(I_peak_Wcm2=5e17, fwhm_fs=10.0, t_peak_fs=2.0, hv_eV=1700.0)
     st = P.init_particles(cfg)
@@ -190,7 +221,7 @@ def test_energy_bookkeeping_gpu(tables):
         return d["ke_e"] + d["ke_i"] + d["e_ion"] + d["e_phot"] + d["e_ka_esc"] + d["e_trans"] - d["e_inc"]
 
     e0 = total(g.diagnostics())
-    g.step(200)
+    g.step(1000)
     d = g.diagnostics()
     assert d["counts"]["ION"] > 0 and d["counts"]["PH0"] > 0
     assert abs(total(d) - e0) / e0 < 1e-6
