@@ -178,11 +178,12 @@ pic_status pic_get_current(pic_ctx *c, double *j3);
 int64_t pic_launch_count(const pic_ctx *c);
 
 /* Device timing of kernel groups with CUDA events on the context stream.
- * enable = 1 starts recording (clearing earlier records), 0 stops.  With
- * ms_out != NULL (5 doubles) the call synchronizes and returns the summed
- * device time of the steps recorded so far: [0] the per-cell kernel (both
- * passes), [1] photon march, [2] counting sort (scan + scatter), [3] field
- * subcycles, [4] whole steps; *nsteps gets the number of steps. */
+ * enable = 1 starts recording (clearing earlier records), 0 stops; -1 keeps
+ * the state.  With ms_out != NULL (6 doubles) the call synchronizes and
+ * returns the summed device time of the steps recorded so far: [0] the
+ * per-cell collision / atomic-process kernel (both passes), [1] photon march,
+ * [2] push + deposit, [3] counting sort (scan + scatter), [4] field
+ * subcycles, [5] whole steps; *nsteps gets the number of steps. */
 pic_status pic_timing(pic_ctx *c, int enable, double *ms_out, int64_t *nsteps);
 
 pic_status pic_free(pic_ctx *c);

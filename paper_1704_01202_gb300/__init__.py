@@ -276,15 +276,15 @@ class Slab:
 
     def timing(self, enable=None):
         """Start (True) / stop (False) event timing; with None return the
-        summed device times {cell, march, sort, field, step} (ms) and the
-        number of recorded steps."""
+        summed device times {cell, march, push, sort, field, step} (ms) and
+        the number of recorded steps."""
         if enable is not None:
             self._check(self.L.pic_timing(self.h, 1 if enable else 0, None, None), "pic_timing")
             return None
-        out = np.zeros(5)
+        out = np.zeros(6)
         n = C.c_int64()
         self._check(self.L.pic_timing(self.h, -1, _p(out), C.byref(n)), "pic_timing")
-        return dict(zip(("cell", "march", "sort", "field", "step"), out)), n.value
+        return dict(zip(("cell", "march", "push", "sort", "field", "step"), out)), n.value
 
     def counts(self):
         ne, ni = C.c_int64(), C.c_int64()

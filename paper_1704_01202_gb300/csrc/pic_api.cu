@@ -12,14 +12,16 @@
 #include "../../include/pic.h"
 #include "pic_dev.cuh"
 #include "pic_cellk.cuh"
+#include "pic_push.cuh"
 #include "pic_grid.cuh"
 
 using namespace pic;
 
 namespace {
 
-constexpr int CNT_APPEND = 0, CNT_WORK = 1, CNT_WORK_BIG = 2, CNT_OVF = 3, CNT_ERR = 4, CNT_MAXE = 5,
-              CNT_MAXI = 6, CNT_NLOAD = 7, NCOUNTERS = 16;
+constexpr int CNT_APPEND = 0, CNT_WORK = 1, CNT_WORK_BIG = 2, CNT_OVF = 3, CNT_WORK_PUSH = 4, CNT_ERR = 5,
+              CNT_MAXE = 6, CNT_MAXI = 7, CNT_NLOAD = 8, NCOUNTERS = 16;
+constexpr int NEV = 6;   // timing events per step
 constexpr int BIG_CE = 2048, BIG_CI = 512;
 
 size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -66,14 +68,14 @@ struct pic_ctx {
 
     int cap_ce = 128, cap_ci = 32, cap_new = 96, wpc = 4;
     size_t smem_main = 0, smem_big = 0;
-    int nsm = 0, grid_main = 0, grid_big = 0;
+    int nsm = 0, grid_main = 0, grid_big = 0, grid_push = 0;
     int64_t launches = 0;
     bool loaded_e = false, loaded_i = false;
     unsigned host_step = 0;
     double fe_factor = 0.0;
     std::vector<double> hv_tab, sigma;   // host copy of the photoionization table
     bool timing = false;
-    std::vector<cudaEvent_t> ev;         // 5 events per recorded step
+    std::vector<cudaEvent_t> ev;         // NEV events per recorded step
     size_t ev_used = 0;
 };
 
@@ -213,15 +215,15 @@ pic_status run_scan(pic_ctx *c, int species_mask, int dst)
 cudaEvent_t *timing_slot(pic_ctx *c)
 {
     if (!c->timing) return nullptr;
-    if (c->ev_used + 5 > c->ev.size()) {
-        for (int k = 0; k < 5; ++k) {
+    if (c->ev_used + NEV > c->ev.size()) {
+        for (int k = 0; k < NEV; ++k) {
             cudaEvent_t e;
             if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
             c->ev.push_back(e);
         }
     }
     cudaEvent_t *p = c->ev.data() + c->ev_used;
-    c->ev_used += 5;
+    c->ev_used += NEV;
     return p;
 }
 
@@ -231,7 +233,7 @@ pic_status launch_step(pic_ctx *c)
     cudaEvent_t *ev = timing_slot(c);
     if (ev) CK(cudaEventRecord(ev[0], st));
     CK(cudaMemsetAsync(c->cnt_e, 0, sizeof(int) * 4 * (size_t)c->ncell, st));   // cnt_e cnt_i fill_e fill_i
-    CK(cudaMemsetAsync(c->counters, 0, sizeof(int) * 4, st));                      // append, work, work_big, ovf
+    CK(cudaMemsetAsync(c->counters, 0, sizeof(int) * 5, st));                      // append, work counters, ovf
     CK(cudaMemsetAsync(c->counters + CNT_MAXE, 0, sizeof(int) * 2, st));
     CK(cudaMemsetAsync(c->J, 0, sizeof(unsigned long long) * 3 * (size_t)c->npts, st));
     if ((c->slab.flags & PIC_F_PHOTO) && c->slab.nb > 0) {
@@ -247,6 +249,18 @@ pic_status launch_step(pic_ctx *c)
     c->launches += 2;
     CK(cudaGetLastError());
     if (ev) CK(cudaEventRecord(ev[2], st));
+    PushArgs pa{};
+    pa.e0 = c->eA0; pa.e1 = c->eA1; pa.ekey = c->ekey; pa.cs_e = c->csE[c->cur];
+    pa.i0 = c->iA0; pa.i1 = c->iA1; pa.ikey = c->ikey; pa.cs_i = c->csI[c->cur];
+    pa.cnt_e = c->cnt_e; pa.cnt_i = c->cnt_i; pa.append = c->counters + CNT_APPEND; pa.cap_e = c->cap_e;
+    pa.ncell = c->ncell; pa.cell_slab = c->cell_slab; pa.slabs = c->d_slab; pa.tally = c->d_tally;
+    pa.fldE = c->E[c->ecur]; pa.fldB = c->B; pa.npts = c->npts; pa.J = c->J;
+    pa.err = c->counters + CNT_ERR; pa.work = c->counters + CNT_WORK_PUSH;
+    k_push<<<c->grid_push, 256, 0, st>>>(pa);
+    k_push_new<<<c->nsm * 2, 256, 0, st>>>(pa);
+    c->launches += 2;
+    CK(cudaGetLastError());
+    if (ev) CK(cudaEventRecord(ev[3], st));
     const int nxt = c->cur ^ 1;
     pic_status r = run_scan(c, 3, nxt);
     if (r != PIC_OK) return r;
@@ -258,7 +272,7 @@ pic_status launch_step(pic_ctx *c)
                    c->cap_i};
     k_scatter<<<sgrid, 256, 0, st>>>(si);
     c->launches += 2;
-    if (ev) CK(cudaEventRecord(ev[3], st));
+    if (ev) CK(cudaEventRecord(ev[4], st));
     if (c->slab.flags & PIC_F_FIELD) {
         FieldArgs f{};
         f.slabs = c->d_slab; f.pt_slab = c->pt_slab; f.npts = c->npts; f.B = c->B; f.J = c->J;
@@ -277,7 +291,7 @@ pic_status launch_step(pic_ctx *c)
     k_advance<<<1, 32, 0, st>>>(c->d_steps, 1);
     ++c->launches;
     CK(cudaGetLastError());
-    if (ev) CK(cudaEventRecord(ev[4], st));
+    if (ev) CK(cudaEventRecord(ev[5], st));
     std::swap(c->eA0, c->eB0); std::swap(c->eA1, c->eB1);
     std::swap(c->iA0, c->iB0); std::swap(c->iA1, c->iB1);
     c->cur = nxt;
@@ -447,6 +461,12 @@ pic_status pic_init(pic_ctx **out, const pic_grid *g, const pic_species *s, cons
     e = cudaFuncSetAttribute(k_march, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8);
     if (e != cudaSuccess) { rs = cuda_fail(c, e, "march attribute"); pic_free(c); return rs; }
     if ((rs = configure_cell_launch(c, 128, 32)) != PIC_OK) { pic_free(c); return rs; }
+    {
+        int occ = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_push, 256, 0);
+        if (e != cudaSuccess) { rs = cuda_fail(c, e, "push occupancy"); pic_free(c); return rs; }
+        c->grid_push = std::max(1, occ) * c->nsm;
+    }
     *out = c;
     return PIC_OK;
 }
@@ -796,19 +816,16 @@ pic_status pic_timing(pic_ctx *c, int enable, double *ms_out, int64_t *nsteps)
     if (!c) return PIC_ERR_ARG;
     if (ms_out) {
         CK(cudaStreamSynchronize(c->stream));
-        for (int k = 0; k < 5; ++k) ms_out[k] = 0.0;
-        for (size_t b = 0; b + 5 <= c->ev_used; b += 5) {
-            float t[4];
-            CK(cudaEventElapsedTime(&t[0], c->ev[b + 1], c->ev[b + 2]));   // cell kernels
-            CK(cudaEventElapsedTime(&t[1], c->ev[b + 0], c->ev[b + 1]));   // march (and memsets)
-            CK(cudaEventElapsedTime(&t[2], c->ev[b + 2], c->ev[b + 3]));   // scan + scatter
-            CK(cudaEventElapsedTime(&t[3], c->ev[b + 3], c->ev[b + 4]));   // fields
-            ms_out[0] += t[0]; ms_out[1] += t[1]; ms_out[2] += t[2]; ms_out[3] += t[3];
-            float all;
-            CK(cudaEventElapsedTime(&all, c->ev[b + 0], c->ev[b + 4]));
-            ms_out[4] += all;
-        }
-        if (nsteps) *nsteps = (int64_t)(c->ev_used / 5);
+        for (int k = 0; k < NEV; ++k) ms_out[k] = 0.0;
+        // groups: cell kernels, march (+ memsets), push, sort, fields, whole step
+        const int from[NEV] = {1, 0, 2, 3, 4, 0}, to[NEV] = {2, 1, 3, 4, 5, 5};
+        for (size_t b = 0; b + NEV <= c->ev_used; b += NEV)
+            for (int k = 0; k < NEV; ++k) {
+                float t;
+                CK(cudaEventElapsedTime(&t, c->ev[b + from[k]], c->ev[b + to[k]]));
+                ms_out[k] += t;
+            }
+        if (nsteps) *nsteps = (int64_t)(c->ev_used / NEV);
     }
     if (enable >= 0) {
         c->timing = enable != 0;

@@ -155,6 +155,8 @@ struct WarpMem {
     NewE *nw;                   // [cap_new]
     float *dE;                  // [16] continuum lowering per charge state
     float *Pz;                  // [16] impact-ionization probability per charge
+    dd *ph;                     // [2 MAXB] photon bin scratch
+    int *phc;                   // [MAXB] events per bin so far
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -166,7 +168,7 @@ __host__ __device__ inline size_t warp_mem_bytes(int ce, int ci, int cn)
     b += align16((size_t)ci * 16) + align16((size_t)ci * 4) + align16((size_t)ci * 8) + align16((size_t)ci * 4)
          + align16((size_t)ci * 2);
     b += align16((size_t)cn * sizeof(NewE));
-    b += 16 * 4 + 16 * 8;
+    b += 16 * 4 + 16 * 4 + 2 * MAXB * 8 + MAXB * 4;
     return b;
 }
 
@@ -185,7 +187,9 @@ __device__ inline WarpMem carve(char *base, int ce, int ci, int cn)
     m.iperm = (unsigned short *)p; p += align16((size_t)ci * 2);
     m.nw = (NewE *)p; p += align16((size_t)cn * sizeof(NewE));
     m.dE = (float *)p; p += 16 * 4;
-    m.Pz = (float *)p;
+    m.Pz = (float *)p; p += 16 * 4;
+    m.ph = (dd *)p; p += 2 * MAXB * 8;
+    m.phc = (int *)p;
     return m;
 }
 
@@ -304,7 +308,7 @@ __device__ __forceinline__ void esirkepov1(float x0, float x1, float qw, float q
 
 // a move of one cell or more: equal sub-cell segments, each deposited
 // straight to global memory around its own start cell
-__device__ void deposit_long(const SlabGrid &g, unsigned long long *J, int npts, int fo, int cx, int cy,
+__device__ __noinline__ void deposit_long(const SlabGrid &g, unsigned long long *J, int npts, int fo, int cx, int cy,
                              float x0, float y0, float x1, float y1, float qw, float qwby, float qwbz)
 {
     float ax = fabsf(x1 - x0), ay = g.ny > 1 ? fabsf(y1 - y0) : 0.0f;

@@ -17,10 +17,9 @@ __device__ __forceinline__ void tally_flush(const CellArgs &a, WarpTally &w, int
 {
     if (w.slab >= 0 && lane == 0) {
         SlabTally *tl = a.tally + w.slab;
-        float v;
-        if ((v = dd_f(w.ion)) != 0.0f) atomicAdd(&tl->ion, (double)w.ion.hi + (double)w.ion.lo);
-        if ((v = dd_f(w.ka)) != 0.0f) atomicAdd(&tl->ka_esc, (double)w.ka.hi + (double)w.ka.lo);
-        if ((v = dd_f(w.esc)) != 0.0f) atomicAdd(&tl->esc, (double)w.esc.hi + (double)w.esc.lo);
+        if (dd_f(w.ion) != 0.0f) atomicAdd(&tl->ion, (double)w.ion.hi + (double)w.ion.lo);
+        if (dd_f(w.ka) != 0.0f) atomicAdd(&tl->ka_esc, (double)w.ka.hi + (double)w.ka.lo);
+        if (dd_f(w.esc) != 0.0f) atomicAdd(&tl->esc, (double)w.esc.hi + (double)w.esc.lo);
         for (int q = 0; q < NCOUNT; ++q)
             if (w.cnt[q]) atomicAdd(tl->cnt + q, (unsigned long long)w.cnt[q]);
     }
@@ -28,163 +27,310 @@ __device__ __forceinline__ void tally_flush(const CellArgs &a, WarpTally &w, int
     for (int q = 0; q < NCOUNT; ++q) w.cnt[q] = 0;
 }
 
-template <int DIM>
-__device__ void cell_push_deposit(const CellArgs &a, const SlabDev &S, const WarpMem &m, int g, int cx, int cy,
-                                  int e0, int ne, int i0, int ni, int nnew, int lane, dd &esc_e_energy,
-                                  int &esc_e, int &esc_i)
+// per-cell scalars shared by the stages of one cell
+struct CellCtx {
+    int s, lc, cx, cy, e0, ne, i0, ni;
+    unsigned step, flags;
+    unsigned long long seed;
+    float wi, mi, n_e, n_i, nref;
+    bool rad;
+};
+
+// ---- EOS-clamped three-body recombination (Sec. IV) ----
+__device__ __noinline__ void stage_recombine(const CellArgs &a, const WarpMem &m, const Tables &T, const SlabDev &S,
+                                             const CellCtx &c, int lane, float Wnew_imp, WarpTally &wt)
 {
-    const unsigned flags = S.flags;
-    const bool do_push = flags & 64u, do_dep = (flags & 128u) != 0;
-    SlabGrid grid;
-    grid.nx = S.nx; grid.ny = S.ny; grid.W = S.nx + 1;
-    grid.fe = a.fldE + S.fld_off; grid.fb = a.fldB + S.fld_off; grid.npts = a.npts; grid.fo = S.fld_off;
-    typename std::conditional<DIM == 2, JAcc2, JAcc1>::type A = {};
-    const int cell0 = S.cell0;
-    const float wi = S.w_ion;
-
-    // electrons present at the start of the step, canonical order
+    const int ne = c.ne, ni = c.ni;
+    const float wi = c.wi, MC2 = (float)kMeC2;
+    float pq = 0.0f;
+    for (int k = lane; k < ni; k += 32) { int sl = m.iperm[k]; pq += (float)(m.ist[sl] & 0xff) + m.iu[sl].w; }
+    const float zb = wsum_f(pq) / ni;
+    dd pkb = dd_zero();
+    float pwb = 0.0f, pwx = 0.0f;
     for (int k = lane; k < ne; k += 32) {
-        int slot = m.eperm[k];
-        float4 uw = m.eu[slot];
-        float4 P0 = a.e0[e0 + slot];
-        float4 P1 = a.e1[e0 + slot];
-        int key;
-        if (uw.w <= 0.0f) {
-            key = -1;
-        } else {
-            float xi = P0.x, eta = P0.y, ux = uw.x, uy = uw.y, uz = uw.z;
-            float ke = (float)kMeC2 * gm1(ux, uy, uz);
-            int nc = push_one<DIM>(S, grid, a.J, a.npts, cx, cy, xi, eta, ux, uy, uz, -1.0f, -uw.w, do_push, do_dep, A);
-            if (nc == -2) { key = -1; atomicOr(a.err, ERR_NUMERIC); }
-            else if (nc < 0) { key = -1; esc_e_energy = dd_addf(esc_e_energy, uw.w * ke); esc_e++; }
-            else key = cell0 + nc;
-            P0 = make_float4(xi, eta, ux, uy);
-            P1.x = uz; P1.y = uw.w;
+        float4 u = m.eu[m.eperm[k]];
+        float ke = MC2 * gm1(u.x, u.y, u.z);
+        pwx += u.w;
+        if (S.E_bulk <= 0.0f || ke < S.E_bulk) { pwb += u.w; pkb = dd_addf(pkb, u.w * ke); }
+    }
+    const float Wb2 = wsum_f(pwb) + Wnew_imp, Kb2 = dd_f(wsum_dd(pkb)), Wex = wsum_f(pwx);
+    const float Te2 = Wb2 > 0.0f ? (2.0f / 3.0f) * Kb2 / Wb2 : 0.0f;
+    const float zeos = eos_lookup(*a.eos, c.n_i, Te2);
+    int Kev = zb > zeos ? (int)floorf((zb - zeos) * ni + 0.5f) : 0;
+    int pel = 0;
+    for (int k = lane; k < ni; k += 32) pel += m.ist[k] & 0xff;
+    const int elig = wsum_i(pel);
+    Kev = min(Kev, elig);
+    Kev = min(Kev, (int)floorf(Wex / wi * (1.0f + 1e-6f)));
+    if (Kev <= 0) return;
+    int *nrec = (int *)m.ikey;            // sort keys are no longer needed
+    float *take = (float *)m.ekey;
+    for (int k = lane; k < ni; k += 32) nrec[k] = 0;
+    __syncwarp();
+    int left = Kev;
+    for (int round = 0; left > 0; ++round) {
+        if (round > ZNUC * 2) {          // cannot happen when Kev <= sum Z
+            if (lane == 0) atomicOr(a.err, ERR_NUMERIC);
+            break;
         }
-        a.e0[e0 + slot] = P0;
-        a.e1[e0 + slot] = P1;
-        a.ekey[e0 + slot] = key;
-        if (key >= 0) atomicAdd(a.cnt_e + key, 1);
-    }
-
-    // electrons created in this cell this step
-    int base = 0;
-    if (nnew > 0) {
-        if (lane == 0) base = atomicAdd(a.append, nnew);
-        base = __shfl_sync(FULL, base, 0);
-        const int sorted = a.cs_e[a.ncell];
-        if (sorted + base + nnew > a.cap_e) {
-            if (lane == 0) atomicOr(a.err, ERR_CAPACITY);
-            for (int k = sorted + base + lane; k < min(a.cap_e, sorted + base + nnew); k += 32) a.ekey[k] = -1;
-            nnew = 0;
+        for (int b0 = 0; b0 < ni && left > 0; b0 += 32) {
+            int t = b0 + lane;
+            bool e = false;
+            if (t < ni) e = (m.ist[m.iperm[t]] & 0xff) - nrec[t] >= 1;
+            unsigned bal = __ballot_sync(FULL, e);
+            int rank = __popc(bal & ((1u << lane) - 1u));
+            if (e && rank < left) nrec[t] += 1;
+            left -= min(left, __popc(bal));
+            __syncwarp();
         }
-        base += sorted;
     }
-    for (int k = lane; k < nnew; k += 32) {
-        NewE q = m.nw[k];
-        int islot = q.meta & 0xffff, kind = q.meta >> 16;
-        float4 I0 = a.i0[i0 + islot];
-        float4 I1 = a.i1[i0 + islot];
-        float xi = I0.x, eta = I0.y, ux = q.ux, uy = q.uy, uz = q.uz;
-        float ke = (float)kMeC2 * gm1(ux, uy, uz);
-        int nc = push_one<DIM>(S, grid, a.J, a.npts, cx, cy, xi, eta, ux, uy, uz, -1.0f, -q.w, do_push, do_dep, A);
-        int key;
-        if (nc == -2) { key = -1; atomicOr(a.err, ERR_NUMERIC); }
-        else if (nc < 0) { key = -1; esc_e_energy = dd_addf(esc_e_energy, q.w * ke); esc_e++; }
-        else key = cell0 + nc;
-        unsigned idhi = ((a.steps[a.cell_slab[g]] + 1u) << 2) | (unsigned)kind;
-        unsigned idlo = __float_as_uint(I1.z);
-        a.e0[base + k] = make_float4(xi, eta, ux, uy);
-        a.e1[base + k] = make_float4(uz, q.w, __uint_as_float(idlo), __uint_as_float(idhi));
-        a.ekey[base + k] = key;
-        if (key >= 0) atomicAdd(a.cnt_e + key, 1);
+    const dd Wrem = dd{(float)Kev * wi, 0.0f};
+    dd carry = dd_zero(), remKE = dd_zero();
+    for (int b0 = 0; b0 < ne; b0 += 32) {
+        int t = b0 + lane;
+        float w = 0.0f, ke = 0.0f;
+        if (t < ne) { float4 u = m.eu[m.eperm[t]]; w = u.w; ke = MC2 * gm1(u.x, u.y, u.z); }
+        dd incl = dd_add(carry, wscan_dd(dd{w, 0.0f}, lane));
+        dd before = dd_sub(incl, dd{w, 0.0f});
+        float tk = fminf(fmaxf(dd_f(dd_sub(Wrem, before)), 0.0f), w);
+        if (t < ne) take[t] = tk;
+        remKE = dd_addf(remKE, tk * ke);
+        carry = wbcast_dd(incl, 31);
     }
-
-    // ions, canonical order
+    __syncwarp();
+    remKE = wsum_dd(remKE);
+    dd pb = dd_zero();
     for (int k = lane; k < ni; k += 32) {
-        int slot = m.iperm[k];
-        float4 iu = m.iu[slot];
-        int st = m.ist[slot];
-        float4 P0 = a.i0[i0 + slot];
-        float4 P1 = a.i1[i0 + slot];
-        float q = (float)(st & 0xff) + iu.w;
-        float xi = P0.x, eta = P0.y, ux = iu.x, uy = iu.y, uz = iu.z;
-        float ke = (float)kMeC2 * S.m_ion * gm1(ux, uy, uz);
-        int nc = push_one<DIM>(S, grid, a.J, a.npts, cx, cy, xi, eta, ux, uy, uz, q / S.m_ion, q * wi, do_push, do_dep, A);
-        int key;
-        if (nc == -2) { key = -1; atomicOr(a.err, ERR_NUMERIC); }
-        else if (nc < 0) { key = -1; esc_e_energy = dd_addf(esc_e_energy, wi * ke); esc_i++; }
-        else key = cell0 + nc;
-        a.i0[i0 + slot] = make_float4(xi, eta, ux, uy);
-        a.i1[i0 + slot] = make_float4(uz, iu.w, P1.z, __int_as_float(st));
-        a.ikey[i0 + slot] = key;
-        if (key >= 0) atomicAdd(a.cnt_i + key, 1);
+        int st = m.ist[m.iperm[k]];
+        int Z = st & 0xff, nK = (st >> 8) & 0xff;
+        for (int r = 1; r <= nrec[k]; ++r) pb = dd_addf(pb, wi * removal_energy(T, Z - r, nK, m.dE[Z - r]));
     }
+    const dd bind = wsum_dd(pb);
+    dd pkr = dd_zero();
+    for (int k = lane; k < ne; k += 32) {
+        float4 u = m.eu[m.eperm[k]];
+        float ke = MC2 * gm1(u.x, u.y, u.z);
+        if (S.E_bulk <= 0.0f || ke < S.E_bulk) pkr = dd_addf(pkr, (u.w - take[k]) * ke);
+    }
+    const float Krem = dd_f(wsum_dd(pkr));
+    if (Krem > 0.0f) {
+        float delta = -dd_f(dd_add(remKE, bind)) / Krem;
+        for (int k = lane; k < ne; k += 32) {
+            int sl = m.eperm[k];
+            float4 u = m.eu[sl];
+            float ke = MC2 * gm1(u.x, u.y, u.z);
+            bool bulk = S.E_bulk <= 0.0f || ke < S.E_bulk;
+            float tk = take[k];
+            float wn = u.w - tk;
+            bool dead = tk > 0.0f && wn <= 0.0f;
+            u.w = dead ? 0.0f : wn;
+            if (bulk && !dead) scale_kinetic(u.x, u.y, u.z, delta);
+            m.eu[sl] = u;
+        }
+        for (int k = lane; k < ni; k += 32) {
+            int sl = m.iperm[k];
+            m.ist[sl] = m.ist[sl] - nrec[k];
+        }
+        wt.ion = dd_sub(wt.ion, bind);
+        if (lane == 0) wt.cnt[C_REC] += Kev;
+    }
+    __syncwarp();
+}
 
-    // the cell's current stencil: fixed reduction tree, then fixed point
-    if (do_dep) {
-        const int fo = S.fld_off, W = S.nx + 1;
-        if constexpr (DIM == 2) {
-#pragma unroll
-            for (int p = 0; p < 3; ++p)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    float v = A.x[p][q];
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
-                    A.x[p][q] = v;
-                    float y = A.y[q][p];
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) y += __shfl_down_sync(FULL, y, o);
-                    A.y[q][p] = y;
+// ---- rad step: subshell photoionization (Eq. 2) ----
+__device__ __noinline__ void stage_photo(const CellArgs &a, const WarpMem &m, const Tables &T, const SlabDev &S,
+                                         const CellCtx &c, int lane, int &nnew, WarpTally &wt)
+{
+    const int ni = c.ni, nb = S.nb;
+    const float wi = c.wi;
+    const float dtr = S.rad_every * S.dt;
+    ph2 *ph = a.photons + S.ph_off + (size_t)c.lc * nb;
+    dd *n0 = m.ph, *used = m.ph + MAXB;
+    int *carry = m.phc;
+    if (lane < nb) { ph2 v = ph[lane]; n0[lane] = dd{v.hi, v.lo}; used[lane] = dd_zero(); carry[lane] = 0; }
+    __syncwarp();
+    const float cph = (float)kCcmPerFs * dtr * c.nref;
+    int c_part = 0, c_ph[NS] = {0, 0, 0, 0, 0};
+    for (int b0 = 0; b0 < ni; b0 += 32) {
+        int t = b0 + lane;
+        int sub = -1, bin = -1, sl = 0, Z = 0, nK = 0;
+        float edge = 0.f, rc = 0.f, rp = 0.f;
+        if (t < ni) {
+            sl = m.iperm[t];
+            int st = m.ist[sl];
+            Z = st & 0xff; nK = (st >> 8) & 0xff;
+            int occ[NS];
+            if (Z < ZNUC && occupancy(ZNUC - Z, nK, occ)) {
+                U4 ra = draw(c.seed, (unsigned long long)m.iid[t], c.step, PU_PHOTO_A);
+                U4 rb = draw(c.seed, (unsigned long long)m.iid[t], c.step, PU_PHOTO_B);
+                float rs[NS] = {u01(ra.x), u01(ra.y), u01(ra.z), u01(ra.w), u01(rb.x)};
+                float Ps = 0.f;
+                for (int q = 0; q < NS; ++q) {
+                    if (!occ[q]) continue;
+                    float ed = lowered_binding(T, Z, q, m.dE[Z]);
+                    float acc = 0.f;
+                    for (int b = 0; b < nb; ++b)
+                        if (S.hv_b[b] > ed) acc += dd_f(n0[b]) * S.sig_b[q][b];
+                    float P = cph * occ[q] * acc;
+                    if (rs[q] < P) { sub = q; Ps = P; edge = ed; break; }
                 }
-#pragma unroll
-            for (int p = 0; p < 4; ++p)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    float v = A.z[p][q];
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
-                    A.z[p][q] = v;
-                }
-            if (lane == 0) {
-                for (int p = 0; p < 4; ++p) {
-                    int i = cx - 1 + p;
-                    for (int q = 0; q < 4; ++q) {
-                        int j = (cy - 1 + q) % S.ny; if (j < 0) j += S.ny;
-                        size_t o = (size_t)fo + (size_t)j * W + i;
-                        if (p < 3 && i >= 0 && i < S.nx) jatomic(a.J + o, A.x[p][q]);
-                        if (q < 3 && i >= 0 && i <= S.nx) jatomic(a.J + a.npts + o, A.y[p][q]);
-                        if (i >= 0 && i <= S.nx) jatomic(a.J + 2 * (size_t)a.npts + o, A.z[p][q]);
+                if (sub >= 0) {
+                    float target = u01(rb.y) * Ps, cum = 0.f;
+                    int lastpos = -1;
+                    for (int b = 0; b < nb; ++b) {
+                        float cb = S.hv_b[b] > edge ? cph * occ[sub] * dd_f(n0[b]) * S.sig_b[sub][b] : 0.f;
+                        if (cb > 0.f) lastpos = b;
+                        cum += cb;
+                        if (cum > target) { bin = b; break; }
                     }
+                    if (bin < 0) bin = lastpos;
+                    rc = u01(rb.z); rp = u01(rb.w);
                 }
             }
-        } else {
-#pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                float x = p < 3 ? A.x[p < 3 ? p : 0] : 0.0f;
-                float y = A.y[p], z = A.z[p];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    x += __shfl_down_sync(FULL, x, o);
-                    y += __shfl_down_sync(FULL, y, o);
-                    z += __shfl_down_sync(FULL, z, o);
-                }
-                if (p < 3) A.x[p] = x;
-                A.y[p] = y; A.z[p] = z;
+        }
+        // the k-th event of a bin gets min(w, max(0, n_bin - k w)) photons
+        float g = 0.0f;
+        bool full = false;
+        for (int b = 0; b < nb; ++b) {
+            bool eb = bin == b && sub >= 0;
+            unsigned bal = __ballot_sync(FULL, eb);
+            if (eb) {
+                int rank = carry[b] + __popc(bal & ((1u << lane) - 1u));
+                dd rest = dd_addf(n0[b], -(float)rank * wi);
+                if (dd_le(dd{wi, 0.0f}, rest)) { g = wi; full = true; }
+                else g = fmaxf(dd_f(rest), 0.0f);
             }
-            if (lane == 0) {
-                for (int p = 0; p < 4; ++p) {
-                    int i = cx - 1 + p;
-                    if (p < 3 && i >= 0 && i < S.nx) jatomic(a.J + fo + i, A.x[p]);
-                    if (i >= 0 && i <= S.nx) {
-                        jatomic(a.J + a.npts + fo + i, A.y[p]);
-                        jatomic(a.J + 2 * (size_t)a.npts + fo + i, A.z[p]);
+            __syncwarp();
+            if (lane == 0) carry[b] += __popc(bal);
+            __syncwarp();
+        }
+        bool ev = sub >= 0 && bin >= 0 && g > 0.0f;
+        if (ev) {
+            if (full) {
+                lose_electron(Z, nK, sub);
+            } else {
+                float zf = m.iu[sl].w + g / wi;
+                if (zf >= 1.0f) {
+                    zf -= 1.0f;
+                    int so = outer_shell(ZNUC - Z, nK);
+                    if (so >= 0) lose_electron(Z, nK, so);
+                }
+                m.iu[sl].w = zf;
+                c_part++;
+            }
+            m.ist[sl] = Z | (nK << 8);
+            c_ph[sub]++;
+        }
+        for (int b = 0; b < nb; ++b) {
+            dd ub = wsum_dd(dd{ev && bin == b ? g : 0.0f, 0.0f});
+            if (lane == 0) used[b] = dd_add(used[b], ub);
+        }
+        wt.ion = dd_add(wt.ion, wsum_dd(dd{ev ? g * edge : 0.0f, 0.0f}));
+        unsigned bal = __ballot_sync(FULL, ev);
+        if (ev) {
+            int pos = nnew + __popc(bal & ((1u << lane) - 1u));
+            if (pos < a.cap_new) {
+                float3 u = iso_momentum(S.hv_b[bin] - edge, rc, rp);
+                NewE q; q.ux = u.x; q.uy = u.y; q.uz = u.z; q.w = g;
+                q.meta = sl | (KIND_PHOTO << 16);
+                m.nw[pos] = q;
+            } else {
+                atomicOr(a.err, ERR_NEW_OVERFLOW);
+            }
+        }
+        nnew = min(nnew + __popc(bal), a.cap_new);
+        __syncwarp();
+    }
+    if (lane < nb) { dd r = dd_sub(n0[lane], used[lane]); ph[lane] = ph2{r.hi, r.lo}; }
+    wt.cnt[C_PART] += wsum_i(c_part);
+    for (int q = 0; q < NS; ++q) wt.cnt[C_PH0 + q] += wsum_i(c_ph[q]);
+    __syncwarp();
+}
+
+// ---- rad step: K-vacancy decay with KLL Auger / K-alpha branching ----
+__device__ __noinline__ void stage_decay(const CellArgs &a, const WarpMem &m, const Tables &T, const SlabDev &S,
+                                         const CellCtx &c, int lane, int &nnew, WarpTally &wt)
+{
+    const int ni = c.ni, nb = S.nb;
+    const float wi = c.wi;
+    const float dtr = S.rad_every * S.dt;
+    dd *addph = m.ph;
+    if (lane < MAXB) addph[lane] = dd_zero();
+    __syncwarp();
+    int c_aug = 0, c_ka = 0;
+    for (int b0 = 0; b0 < ni; b0 += 32) {
+        int t = b0 + lane;
+        int kind = 0, sl = 0, Z = 0;
+        float EA = 0.f, rc = 0.f, rp = 0.f, Eka = 0.f;
+        if (t < ni) {
+            sl = m.iperm[t];
+            int st = m.ist[sl];
+            Z = st & 0xff;
+            int nK = (st >> 8) & 0xff;
+            int nbd = ZNUC - Z, occ[NS];
+            if (nK > 0 && occupancy(nbd, nK, occ)) {
+                float tau = T.tauK[nbd][nK - 1];
+                if (tau > 0.f) {
+                    U4 r = draw(c.seed, (unsigned long long)m.iid[t], c.step, PU_DECAY);
+                    if (u01(r.x) < dtr / tau) {
+                        float om = T.omegaK[nbd][nK - 1];
+                        int nl = occ[1] + occ[2];
+                        if (u01(r.y) < 1.0f - om) {
+                            if (nl >= 2) {
+                                float e2s = lowered_binding(T, Z, 1, m.dE[Z]);
+                                float e2p = lowered_binding(T, Z, 2, m.dE[Z]);
+                                EA = fmaxf(T.E_Ka[Z] - (occ[1] * e2s + occ[2] * e2p) / nl, 0.0f);
+                                int kocc = occ[0] + 1, nb2 = nbd - 1;
+                                int Zn = Z + 1, nKn = (nb2 < 2 ? nb2 : 2) - kocc;
+                                m.ist[sl] = Zn | (nKn << 8);
+                                kind = 1;
+                                rc = u01(r.z); rp = u01(r.w);
+                            }
+                        } else if (occ[2] >= 1) {
+                            Eka = T.E_Ka[Z];
+                            m.ist[sl] = Z | ((nK - 1) << 8);
+                            kind = 2;
+                        }
                     }
                 }
             }
         }
+        unsigned bal = __ballot_sync(FULL, kind == 1);
+        if (kind == 1) {
+            int pos = nnew + __popc(bal & ((1u << lane) - 1u));
+            if (pos < a.cap_new) {
+                float3 u = iso_momentum(EA, rc, rp);
+                NewE q; q.ux = u.x; q.uy = u.y; q.uz = u.z; q.w = wi; q.meta = sl | (KIND_AUGER << 16);
+                m.nw[pos] = q;
+            } else {
+                atomicOr(a.err, ERR_NEW_OVERFLOW);
+            }
+            c_aug++;
+        }
+        nnew = min(nnew + __popc(bal), a.cap_new);
+        int hit = -1;
+        if (kind == 2) {
+            c_ka++;
+            for (int b = 0; b < nb; ++b)
+                if (Eka >= S.hv_b[b] - S.bin_hw && Eka < S.hv_b[b] + S.bin_hw) { hit = b; break; }
+        }
+        for (int b = 0; b < nb; ++b) {
+            dd v = wsum_dd(dd{hit == b ? wi * Eka / S.hv_b[b] : 0.0f, 0.0f});
+            if (lane == 0) addph[b] = dd_add(addph[b], v);
+        }
+        wt.ka = dd_add(wt.ka, wsum_dd(dd{kind == 2 && hit < 0 ? wi * Eka : 0.0f, 0.0f}));
+        wt.ion = dd_sub(wt.ion, wsum_dd(dd{kind == 1 ? wi * EA : (kind == 2 ? wi * Eka : 0.0f), 0.0f}));
+        __syncwarp();
     }
+    if (nb && lane < nb) {
+        ph2 *ph = a.photons + S.ph_off + (size_t)c.lc * nb;
+        ph2 v = ph[lane];
+        dd r = dd_add(dd{v.hi, v.lo}, addph[lane]);
+        ph[lane] = ph2{r.hi, r.lo};
+    }
+    wt.cnt[C_AUG] += wsum_i(c_aug);
+    wt.cnt[C_KA] += wsum_i(c_ka);
+    __syncwarp();
 }
 
 __device__ void process_cell(const CellArgs &a, const WarpMem &m, const Tables &T, int g, int lane, WarpTally &wt)
@@ -205,7 +351,7 @@ __device__ void process_cell(const CellArgs &a, const WarpMem &m, const Tables &
     const bool rad = S.rad_every > 0 && (step % (unsigned)S.rad_every) == 0;
     const float MC2 = (float)kMeC2;
     const float nref = S.nref_f;
-    int c_ee = 0, c_ei = 0, c_ion = 0, c_rej = 0, c_part = 0, c_aug = 0, c_ka = 0, c_ph[NS] = {0, 0, 0, 0, 0};
+    int c_ee = 0, c_ei = 0, c_ion = 0, c_rej = 0;
 
     // ---- stage in shared memory; Philox sort keys ----
     for (int k = lane; k < ne; k += 32) {
@@ -404,317 +550,63 @@ __device__ void process_cell(const CellArgs &a, const WarpMem &m, const Tables &
         __syncwarp();
     }
 
-    // ---- EOS-clamped three-body recombination (Sec. IV) ----
-    if ((flags & 8u) && ni >= 1) {
-        dd pq = dd_zero();
-        for (int k = lane; k < ni; k += 32) { int sl = m.iperm[k]; pq = dd_addf(pq, (float)(m.ist[sl] & 0xff) + m.iu[sl].w); }
-        const float zb = dd_f(wsum_dd(pq)) / ni;
-        dd pwb = dd_zero(), pkb = dd_zero(), pwx = dd_zero();
-        for (int k = lane; k < ne; k += 32) {
-            float4 u = m.eu[m.eperm[k]];
-            float ke = MC2 * gm1(u.x, u.y, u.z);
-            pwx = dd_addf(pwx, u.w);
-            if (S.E_bulk <= 0.0f || ke < S.E_bulk) { pwb = dd_addf(pwb, u.w); pkb = dd_addf(pkb, u.w * ke); }
+    CellCtx cc;
+    cc.s = s; cc.lc = lc; cc.cx = cx; cc.cy = cy; cc.e0 = e0; cc.ne = ne; cc.i0 = i0; cc.ni = ni;
+    cc.step = step; cc.flags = flags; cc.seed = seed; cc.wi = wi; cc.mi = mi; cc.n_e = n_e; cc.n_i = n_i;
+    cc.nref = nref; cc.rad = rad;
+    if ((flags & 8u) && ni >= 1) stage_recombine(a, m, T, S, cc, lane, Wnew_imp, wt);
+    if (rad && (flags & 16u) && S.nb && ni >= 1) stage_photo(a, m, T, S, cc, lane, nnew, wt);
+    if (rad && (flags & 32u) && ni >= 1) stage_decay(a, m, T, S, cc, lane, nnew, wt);
+
+    // ---- write the collided state back (positions unchanged) ----
+    for (int k = lane; k < ne; k += 32) {
+        float4 u = m.eu[k];
+        reinterpret_cast<float2 *>(a.e0 + e0 + k)[1] = make_float2(u.x, u.y);
+        reinterpret_cast<float2 *>(a.e1 + e0 + k)[0] = make_float2(u.z, u.w);
+    }
+    for (int k = lane; k < ni; k += 32) {
+        float4 u = m.iu[k];
+        reinterpret_cast<float2 *>(a.i0 + i0 + k)[1] = make_float2(u.x, u.y);
+        float4 *r1 = a.i1 + i0 + k;
+        reinterpret_cast<float2 *>(r1)[0] = make_float2(u.z, u.w);
+        reinterpret_cast<int *>(r1)[3] = m.ist[k];
+    }
+    // ---- created electrons: after the sorted range, at their ion, with their cell as key ----
+    if (nnew > 0) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(a.append, nnew);
+        base = __shfl_sync(FULL, base, 0);
+        const int sorted = a.cs_e[a.ncell];
+        int n_ok = nnew;
+        if (sorted + base + nnew > a.cap_e) {
+            if (lane == 0) atomicOr(a.err, ERR_CAPACITY);
+            for (int k = sorted + base + lane; k < min(a.cap_e, sorted + base + nnew); k += 32) a.ekey[k] = -1;
+            n_ok = 0;
         }
-        const float Wb2 = dd_f(wsum_dd(pwb)) + Wnew_imp, Kb2 = dd_f(wsum_dd(pkb)), Wex = dd_f(wsum_dd(pwx));
-        const float Te2 = Wb2 > 0.0f ? (2.0f / 3.0f) * Kb2 / Wb2 : 0.0f;
-        const float zeos = eos_lookup(*a.eos, n_i, Te2);
-        int Kev = zb > zeos ? (int)floorf((zb - zeos) * ni + 0.5f) : 0;
-        int pel = 0;
-        for (int k = lane; k < ni; k += 32) pel += m.ist[k] & 0xff;
-        const int elig = wsum_i(pel);
-        Kev = min(Kev, elig);
-        Kev = min(Kev, (int)floorf(Wex / wi * (1.0f + 1e-6f)));
-        if (Kev > 0) {
-            int *nrec = (int *)m.ikey;            // sort keys are no longer needed
-            float *take = (float *)m.ekey;
-            for (int k = lane; k < ni; k += 32) nrec[k] = 0;
-            __syncwarp();
-            int left = Kev;
-            for (int round = 0; left > 0; ++round) {
-                if (round > ZNUC * 2) {          // cannot happen when Kev <= sum Z
-                    if (lane == 0) atomicOr(a.err, ERR_NUMERIC);
-                    break;
-                }
-                for (int b0 = 0; b0 < ni && left > 0; b0 += 32) {
-                    int t = b0 + lane;
-                    bool e = false;
-                    if (t < ni) e = (m.ist[m.iperm[t]] & 0xff) - nrec[t] >= 1;
-                    unsigned bal = __ballot_sync(FULL, e);
-                    int rank = __popc(bal & ((1u << lane) - 1u));
-                    if (e && rank < left) nrec[t] += 1;
-                    left -= min(left, __popc(bal));
-                    __syncwarp();
-                }
-            }
-            const dd Wrem = dd{(float)Kev * wi, 0.0f};
-            dd carry = dd_zero(), remKE = dd_zero();
-            for (int b0 = 0; b0 < ne; b0 += 32) {
-                int t = b0 + lane;
-                float w = 0.0f, ke = 0.0f;
-                if (t < ne) { float4 u = m.eu[m.eperm[t]]; w = u.w; ke = MC2 * gm1(u.x, u.y, u.z); }
-                dd incl = dd_add(carry, wscan_dd(dd{w, 0.0f}, lane));
-                dd before = dd_sub(incl, dd{w, 0.0f});
-                float tk = fminf(fmaxf(dd_f(dd_sub(Wrem, before)), 0.0f), w);
-                if (t < ne) take[t] = tk;
-                remKE = dd_addf(remKE, tk * ke);
-                carry = wbcast_dd(incl, 31);
-            }
-            __syncwarp();
-            remKE = wsum_dd(remKE);
-            dd pb = dd_zero();
-            for (int k = lane; k < ni; k += 32) {
-                int st = m.ist[m.iperm[k]];
-                int Z = st & 0xff, nK = (st >> 8) & 0xff;
-                for (int r = 1; r <= nrec[k]; ++r) pb = dd_addf(pb, wi * removal_energy(T, Z - r, nK, m.dE[Z - r]));
-            }
-            const dd bind = wsum_dd(pb);
-            dd pkr = dd_zero();
-            for (int k = lane; k < ne; k += 32) {
-                float4 u = m.eu[m.eperm[k]];
-                float ke = MC2 * gm1(u.x, u.y, u.z);
-                if (S.E_bulk <= 0.0f || ke < S.E_bulk) pkr = dd_addf(pkr, (u.w - take[k]) * ke);
-            }
-            const float Krem = dd_f(wsum_dd(pkr));
-            if (Krem > 0.0f) {
-                float delta = -dd_f(dd_add(remKE, bind)) / Krem;
-                for (int k = lane; k < ne; k += 32) {
-                    int sl = m.eperm[k];
-                    float4 u = m.eu[sl];
-                    float ke = MC2 * gm1(u.x, u.y, u.z);
-                    bool bulk = S.E_bulk <= 0.0f || ke < S.E_bulk;
-                    float tk = take[k];
-                    float wn = u.w - tk;
-                    bool dead = tk > 0.0f && wn <= 0.0f;
-                    u.w = dead ? 0.0f : wn;
-                    if (bulk && !dead) scale_kinetic(u.x, u.y, u.z, delta);
-                    m.eu[sl] = u;
-                }
-                for (int k = lane; k < ni; k += 32) {
-                    int sl = m.iperm[k];
-                    m.ist[sl] = m.ist[sl] - nrec[k];
-                }
-                wt.ion = dd_sub(wt.ion, bind);
-                if (lane == 0) wt.cnt[C_REC] += Kev;
-            }
-            __syncwarp();
+        for (int k = lane; k < n_ok; k += 32) {
+            NewE q = m.nw[k];
+            int islot = q.meta & 0xffff, kind = q.meta >> 16;
+            float4 I0 = a.i0[i0 + islot];
+            float4 I1 = a.i1[i0 + islot];
+            unsigned idhi = ((step + 1u) << 2) | (unsigned)kind;
+            a.e0[sorted + base + k] = make_float4(I0.x, I0.y, q.ux, q.uy);
+            a.e1[sorted + base + k] = make_float4(q.uz, q.w, I1.z, __uint_as_float(idhi));
+            a.ekey[sorted + base + k] = g;
         }
     }
-
-    // ---- rad step: subshell photoionization (Eq. 2), then K-vacancy decay ----
-    if (rad && (flags & (16u | 32u)) && ni >= 1) {
-        const int nb = S.nb;
-        const float dtr = S.rad_every * S.dt;
-        ph2 *ph = nb ? a.photons + S.ph_off + (size_t)lc * nb : nullptr;
-        if ((flags & 16u) && nb) {
-            dd n0[MAXB], used[MAXB];
-            int carry[MAXB];
-#pragma unroll
-            for (int b = 0; b < MAXB; ++b) {
-                if (b < nb) { ph2 v = ph[b]; n0[b] = dd{v.hi, v.lo}; } else n0[b] = dd_zero();
-                used[b] = dd_zero(); carry[b] = 0;
-            }
-            const float cph = (float)kCcmPerFs * dtr * nref;
-            for (int b0 = 0; b0 < ni; b0 += 32) {
-                int t = b0 + lane;
-                int sub = -1, bin = -1, sl = 0, Z = 0, nK = 0;
-                float edge = 0.f, rc = 0.f, rp = 0.f;
-                if (t < ni) {
-                    sl = m.iperm[t];
-                    int st = m.ist[sl];
-                    Z = st & 0xff; nK = (st >> 8) & 0xff;
-                    int occ[NS];
-                    if (Z < ZNUC && occupancy(ZNUC - Z, nK, occ)) {
-                        U4 ra = draw(seed, (unsigned long long)m.iid[t], step, PU_PHOTO_A);
-                        U4 rb = draw(seed, (unsigned long long)m.iid[t], step, PU_PHOTO_B);
-                        float rs[NS] = {u01(ra.x), u01(ra.y), u01(ra.z), u01(ra.w), u01(rb.x)};
-                        float Ps = 0.f;
-                        for (int q = 0; q < NS; ++q) {
-                            if (!occ[q]) continue;
-                            float ed = lowered_binding(T, Z, q, m.dE[Z]);
-                            float acc = 0.f;
-#pragma unroll
-                            for (int b = 0; b < MAXB; ++b)
-                                if (b < nb && S.hv_b[b] > ed) acc += dd_f(n0[b]) * S.sig_b[q][b];
-                            float P = cph * occ[q] * acc;
-                            if (rs[q] < P) { sub = q; Ps = P; edge = ed; break; }
-                        }
-                        if (sub >= 0) {
-                            float target = u01(rb.y) * Ps, cum = 0.f;
-                            int lastpos = -1;
-#pragma unroll
-                            for (int b = 0; b < MAXB; ++b) {
-                                if (b >= nb || bin >= 0) continue;
-                                float c = S.hv_b[b] > edge ? cph * occ[sub] * dd_f(n0[b]) * S.sig_b[sub][b] : 0.f;
-                                if (c > 0.f) lastpos = b;
-                                cum += c;
-                                if (cum > target) bin = b;
-                            }
-                            if (bin < 0) bin = lastpos;
-                            rc = u01(rb.z); rp = u01(rb.w);
-                        }
-                    }
-                }
-                // k-th event of a bin gets min(w, max(0, n_bin - k w)) photons
-                float g = 0.0f;
-                bool full = false;
-#pragma unroll
-                for (int b = 0; b < MAXB; ++b) {
-                    if (b >= nb) continue;
-                    bool eb = bin == b && sub >= 0;
-                    unsigned bal = __ballot_sync(FULL, eb);
-                    if (eb) {
-                        int rank = carry[b] + __popc(bal & ((1u << lane) - 1u));
-                        dd rest = dd_addf(n0[b], -(float)rank * wi);
-                        if (dd_le(dd{wi, 0.0f}, rest)) { g = wi; full = true; }
-                        else g = fmaxf(dd_f(rest), 0.0f);
-                    }
-                    carry[b] += __popc(bal);
-                }
-                bool ev = sub >= 0 && bin >= 0 && g > 0.0f;
-                if (ev) {
-                    if (full) {
-                        lose_electron(Z, nK, sub);
-                    } else {
-                        float zf = m.iu[sl].w + g / wi;
-                        if (zf >= 1.0f) {
-                            zf -= 1.0f;
-                            int so = outer_shell(ZNUC - Z, nK);
-                            if (so >= 0) lose_electron(Z, nK, so);
-                        }
-                        m.iu[sl].w = zf;
-                        c_part++;
-                    }
-                    m.ist[sl] = Z | (nK << 8);
-                    c_ph[sub]++;
-                }
-#pragma unroll
-                for (int b = 0; b < MAXB; ++b)
-                    if (b < nb) used[b] = dd_add(used[b], wsum_dd(dd{ev && bin == b ? g : 0.0f, 0.0f}));
-                wt.ion = dd_add(wt.ion, wsum_dd(dd{ev ? g * edge : 0.0f, 0.0f}));
-                unsigned bal = __ballot_sync(FULL, ev);
-                if (ev) {
-                    int pos = nnew + __popc(bal & ((1u << lane) - 1u));
-                    if (pos < a.cap_new) {
-                        float3 u = iso_momentum(S.hv_b[bin] - edge, rc, rp);
-                        NewE q; q.ux = u.x; q.uy = u.y; q.uz = u.z; q.w = g;
-                        q.meta = sl | (KIND_PHOTO << 16);
-                        m.nw[pos] = q;
-                    } else {
-                        atomicOr(a.err, ERR_NEW_OVERFLOW);
-                    }
-                }
-                nnew = min(nnew + __popc(bal), a.cap_new);
-            }
-            __syncwarp();
-            if (lane == 0) {
-#pragma unroll
-                for (int b = 0; b < MAXB; ++b)
-                    if (b < nb) { dd r = dd_sub(n0[b], used[b]); ph[b] = ph2{r.hi, r.lo}; }
-            }
-            __syncwarp();
-        }
-        if (flags & 32u) {
-            dd addph[MAXB];
-#pragma unroll
-            for (int b = 0; b < MAXB; ++b) addph[b] = dd_zero();
-            for (int b0 = 0; b0 < ni; b0 += 32) {
-                int t = b0 + lane;
-                int kind = 0, sl = 0, Z = 0;
-                float EA = 0.f, rc = 0.f, rp = 0.f, Eka = 0.f;
-                if (t < ni) {
-                    sl = m.iperm[t];
-                    int st = m.ist[sl];
-                    Z = st & 0xff;
-                    int nK = (st >> 8) & 0xff;
-                    int nbd = ZNUC - Z, occ[NS];
-                    if (nK > 0 && occupancy(nbd, nK, occ)) {
-                        float tau = T.tauK[nbd][nK - 1];
-                        if (tau > 0.f) {
-                            U4 r = draw(seed, (unsigned long long)m.iid[t], step, PU_DECAY);
-                            if (u01(r.x) < dtr / tau) {
-                                float om = T.omegaK[nbd][nK - 1];
-                                int nl = occ[1] + occ[2];
-                                if (u01(r.y) < 1.0f - om) {
-                                    if (nl >= 2) {
-                                        float e2s = lowered_binding(T, Z, 1, m.dE[Z]);
-                                        float e2p = lowered_binding(T, Z, 2, m.dE[Z]);
-                                        EA = fmaxf(T.E_Ka[Z] - (occ[1] * e2s + occ[2] * e2p) / nl, 0.0f);
-                                        int kocc = occ[0] + 1, nb2 = nbd - 1;
-                                        int Zn = Z + 1, nKn = (nb2 < 2 ? nb2 : 2) - kocc;
-                                        m.ist[sl] = Zn | (nKn << 8);
-                                        kind = 1;
-                                        rc = u01(r.z); rp = u01(r.w);
-                                    }
-                                } else if (occ[2] >= 1) {
-                                    Eka = T.E_Ka[Z];
-                                    m.ist[sl] = Z | ((nK - 1) << 8);
-                                    kind = 2;
-                                }
-                            }
-                        }
-                    }
-                }
-                unsigned bal = __ballot_sync(FULL, kind == 1);
-                if (kind == 1) {
-                    int pos = nnew + __popc(bal & ((1u << lane) - 1u));
-                    if (pos < a.cap_new) {
-                        float3 u = iso_momentum(EA, rc, rp);
-                        NewE q; q.ux = u.x; q.uy = u.y; q.uz = u.z; q.w = wi; q.meta = sl | (KIND_AUGER << 16);
-                        m.nw[pos] = q;
-                    } else {
-                        atomicOr(a.err, ERR_NEW_OVERFLOW);
-                    }
-                    c_aug++;
-                }
-                nnew = min(nnew + __popc(bal), a.cap_new);
-                int hit = -1;
-                if (kind == 2) {
-                    c_ka++;
-                    for (int b = 0; b < nb; ++b)
-                        if (Eka >= S.hv_b[b] - S.bin_hw && Eka < S.hv_b[b] + S.bin_hw) { hit = b; break; }
-                }
-#pragma unroll
-                for (int b = 0; b < MAXB; ++b)
-                    if (b < nb) addph[b] = dd_add(addph[b], wsum_dd(dd{hit == b ? wi * Eka / S.hv_b[b] : 0.0f, 0.0f}));
-                wt.ka = dd_add(wt.ka, wsum_dd(dd{kind == 2 && hit < 0 ? wi * Eka : 0.0f, 0.0f}));
-                wt.ion = dd_sub(wt.ion, wsum_dd(dd{kind == 1 ? wi * EA : (kind == 2 ? wi * Eka : 0.0f), 0.0f}));
-            }
-            if (lane == 0 && nb) {
-#pragma unroll
-                for (int b = 0; b < MAXB; ++b)
-                    if (b < nb) { ph2 v = ph[b]; dd r = dd_add(dd{v.hi, v.lo}, addph[b]); ph[b] = ph2{r.hi, r.lo}; }
-            }
-            __syncwarp();
-        }
-    }
-
-    // ---- Boris push + charge-conserving deposit of every particle ----
-    dd esc = dd_zero();
-    int esc_e = 0, esc_i = 0;
-    if (S.ny > 1) cell_push_deposit<2>(a, S, m, g, cx, cy, e0, ne, i0, ni, nnew, lane, esc, esc_e, esc_i);
-    else cell_push_deposit<1>(a, S, m, g, cx, cy, e0, ne, i0, ni, nnew, lane, esc, esc_e, esc_i);
-    wt.esc = dd_add(wt.esc, wsum_dd(esc));
 
     // ---- tallies (lane-uniform) ----
     wt.cnt[C_EE] += wsum_i(c_ee);
     wt.cnt[C_EI] += wsum_i(c_ei);
     wt.cnt[C_ION] += wsum_i(c_ion);
     wt.cnt[C_ION_REJ] += wsum_i(c_rej);
-    wt.cnt[C_PART] += wsum_i(c_part);
-    wt.cnt[C_AUG] += wsum_i(c_aug);
-    wt.cnt[C_KA] += wsum_i(c_ka);
-    wt.cnt[C_ESC_E] += wsum_i(esc_e);
-    wt.cnt[C_ESC_I] += wsum_i(esc_i);
-#pragma unroll
-    for (int q = 0; q < NS; ++q) wt.cnt[C_PH0 + q] += wsum_i(c_ph[q]);
     __syncwarp();
 }
 
 // One warp per cell, cells taken from a shared counter.  Cells whose
 // population exceeds this launch's shared-memory capacity go to a list for
 // the large-cell launch.
-__global__ void __launch_bounds__(256) k_cell(CellArgs a)
+__global__ void __launch_bounds__(256, 2) k_cell(CellArgs a)
 {
     extern __shared__ __align__(16) char smem[];
     __shared__ Tables T;
@@ -743,8 +635,8 @@ __global__ void __launch_bounds__(256) k_cell(CellArgs a)
                 // no larger pass left: report, and drop the cell's particles so
                 // that the next sort stays consistent
                 if (lane == 0) atomicOr(a.err, ERR_CELL_OVERFLOW);
-                for (int k = a.cs_e[g] + lane; k < a.cs_e[g + 1]; k += 32) a.ekey[k] = -1;
-                for (int k = a.cs_i[g] + lane; k < a.cs_i[g + 1]; k += 32) a.ikey[k] = -1;
+                for (int k = a.cs_e[g] + lane; k < a.cs_e[g + 1]; k += 32) reinterpret_cast<float *>(a.e1 + k)[1] = 0.0f;
+                for (int k = a.cs_i[g] + lane; k < a.cs_i[g + 1]; k += 32) reinterpret_cast<int *>(a.i1 + k)[3] = 0xff;
             }
             continue;
         }

@@ -1,0 +1,390 @@
+// Boris push and charge-conserving deposit, one warp per cell.
+//
+// Each particle's contribution to the cell's current stencil is rounded to
+// 32-bit fixed point (2^22 per unit of q w W), summed across the warp with
+// the integer warp reduction, kept in 64-bit running sums and added to the
+// global 2^40 fixed-point grid: integer addition is associative, so the
+// result does not depend on the memory order of the particles, which the
+// atomic scatter of the counting sort leaves unspecified.
+#pragma once
+#include "pic_cell.cuh"
+
+namespace pic {
+
+struct PushArgs {
+    float4 *e0, *e1;
+    int *ekey;
+    const int *cs_e;
+    float4 *i0, *i1;
+    int *ikey;
+    const int *cs_i;
+    int *cnt_e, *cnt_i;
+    const int *append;        // electrons appended this step (after the sorted range)
+    int cap_e;
+    int ncell;
+    const int *cell_slab;
+    const SlabDev *slabs;
+    SlabTally *tally;
+    const float *fldE, *fldB;
+    int npts;
+    unsigned long long *J;
+    int *err;
+    int *work;
+};
+
+constexpr float JI_SCALE = 4194304.0f;        // 2^22 lane fixed point
+constexpr int JI_TO_GLOBAL = 18;              // 2^22 -> 2^40
+
+// CIC weights and indices of one particle on the staggered grid
+struct GatherPt {
+    int xn0, xn1, xh0, xh1;       // node / half-node columns
+    float wn0, wn1, wh0, wh1;
+    int yn0, yn1, yh0, yh1;       // rows (already wrapped)
+    float vn0, vn1, vh0, vh1;
+};
+
+template <int DIM>
+__device__ __forceinline__ GatherPt gather_pt(int nx, int ny, int cx, int cy, float xi, float eta)
+{
+    GatherPt p;
+    p.xn0 = cx; p.xn1 = cx + 1; p.wn0 = 1.0f - xi; p.wn1 = xi;
+    if (xi >= 0.5f) { p.xh0 = cx; p.xh1 = cx + 1; p.wh1 = xi - 0.5f; }
+    else { p.xh0 = cx - 1; p.xh1 = cx; p.wh1 = xi + 0.5f; }
+    p.wh0 = 1.0f - p.wh1;
+    // half nodes exist for 0 <= i <= nx - 1: weight 0 (and a safe index) outside
+    if (p.xh0 < 0) { p.xh0 = 0; p.wh0 = 0.0f; }
+    if (p.xh1 > nx - 1) { p.xh1 = nx - 1; p.wh1 = 0.0f; }
+    if (DIM == 2) {
+        p.yn0 = cy; p.yn1 = cy + 1 == ny ? 0 : cy + 1; p.vn0 = 1.0f - eta; p.vn1 = eta;
+        if (eta >= 0.5f) { p.yh0 = cy; p.yh1 = cy + 1 == ny ? 0 : cy + 1; p.vh1 = eta - 0.5f; }
+        else { p.yh0 = cy == 0 ? ny - 1 : cy - 1; p.yh1 = cy; p.vh1 = eta + 0.5f; }
+        p.vh0 = 1.0f - p.vh1;
+    } else {
+        p.yn0 = p.yn1 = p.yh0 = p.yh1 = 0;
+        p.vn0 = 1.0f; p.vn1 = 0.0f; p.vh0 = 1.0f; p.vh1 = 0.0f;
+    }
+    return p;
+}
+
+__device__ __forceinline__ float interp4(const float *F, int W, int x0, int x1, float w0, float w1, int y0, int y1,
+                                         float v0, float v1)
+{
+    const float *r0 = F + (size_t)y0 * W, *r1 = F + (size_t)y1 * W;
+    return w0 * (v0 * __ldg(r0 + x0) + v1 * __ldg(r1 + x0)) + w1 * (v0 * __ldg(r0 + x1) + v1 * __ldg(r1 + x1));
+}
+
+__device__ __forceinline__ int jq(float v) { return __float2int_rn(v * JI_SCALE); }
+
+// Running sums of a cell's current stencil: sum k is held by lane k % 32
+// in acc[k / 32].  One contribution per lane and node is summed across the
+// warp with the integer warp reduction (all lanes take part; lanes without
+// a particle add 0).
+__device__ __forceinline__ void jadd(long long acc[2], int k, int v, int lane)
+{
+    int s = __reduce_add_sync(FULL, v);
+    if (lane == (k & 31)) acc[k >> 5] += s;
+}
+
+// 2D Esirkepov weights of one sub-cell move (offsets relative to the cell,
+// stencil nodes -1..2); order of the sums: jx[a][b] (12), jy[a][b] (12),
+// jz[a][b] (16)
+__device__ __forceinline__ void esirkepov2_w(float x0, float y0, float x1, float y1, float qw, float qwbz,
+                                             long long acc[2], int lane)
+{
+    float S0x[4], S1x[4], S0y[4], S1y[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        S0x[a] = cic_w(x0, a - 1); S1x[a] = cic_w(x1, a - 1);
+        S0y[a] = cic_w(y0, a - 1); S1y[a] = cic_w(y1, a - 1);
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        float acc_x = 0.0f;
+        float sy = S0y[b] + 0.5f * (S1y[b] - S0y[b]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            acc_x += (S1x[a] - S0x[a]) * sy;
+            jadd(acc, a * 4 + b, jq(-qw * acc_x), lane);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        float acc_y = 0.0f;
+        float dsx = S1x[a] - S0x[a];
+        float sx = S0x[a] + 0.5f * dsx;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            acc_y += (S1y[b] - S0y[b]) * sx;
+            jadd(acc, 12 + a * 3 + b, jq(-qw * acc_y), lane);
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            float dsy = S1y[b] - S0y[b];
+            float wz = S0x[a] * S0y[b] + 0.5f * dsx * S0y[b] + 0.5f * S0x[a] * dsy + dsx * dsy * (1.0f / 3.0f);
+            jadd(acc, 24 + a * 4 + b, jq(qwbz * wz), lane);
+        }
+    }
+}
+
+// 1D: jx at 3 half nodes (0..2), jy (3..6), jz (7..10) at 4 nodes
+__device__ __forceinline__ void esirkepov1_w(float x0, float x1, float qw, float qwby, float qwbz, long long acc[2],
+                                             int lane)
+{
+    float S0x[4], S1x[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) { S0x[a] = cic_w(x0, a - 1); S1x[a] = cic_w(x1, a - 1); }
+    float acc_x = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { acc_x += S1x[a] - S0x[a]; jadd(acc, a, jq(-qw * acc_x), lane); }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        float sv = 0.5f * (S0x[a] + S1x[a]);
+        jadd(acc, 3 + a, jq(qwby * sv), lane);
+        jadd(acc, 7 + a, jq(qwbz * sv), lane);
+    }
+}
+
+__device__ __forceinline__ long long wsum_ll(long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void jglobal(unsigned long long *J, long long v)
+{
+    if (v != 0) atomicAdd(J, (unsigned long long)(v << JI_TO_GLOBAL));
+}
+
+// One particle: gather, Boris, move; returns the next local cell, -1 when
+// it left through an x boundary, -2 when its move is not finite.
+template <int DIM>
+__device__ __forceinline__ int move_particle(const SlabDev &S, const float *fe, const float *fb, int npts,
+                                             int cx, int cy, float &xi, float &eta, float &ux, float &uy,
+                                             float &uz, float qm, float &xn, float &yn)
+{
+    const int W = S.nx + 1;
+    GatherPt p = gather_pt<DIM>(S.nx, S.ny, cx, cy, xi, eta);
+    float ex = interp4(fe, W, p.xh0, p.xh1, p.wh0, p.wh1, p.yn0, p.yn1, p.vn0, p.vn1);
+    float ey = interp4(fe + npts, W, p.xn0, p.xn1, p.wn0, p.wn1, p.yh0, p.yh1, p.vh0, p.vh1);
+    float ez = interp4(fe + 2 * npts, W, p.xn0, p.xn1, p.wn0, p.wn1, p.yn0, p.yn1, p.vn0, p.vn1);
+    float bx = interp4(fb, W, p.xn0, p.xn1, p.wn0, p.wn1, p.yh0, p.yh1, p.vh0, p.vh1);
+    float by = interp4(fb + npts, W, p.xh0, p.xh1, p.wh0, p.wh1, p.yn0, p.yn1, p.vn0, p.vn1);
+    float bz = interp4(fb + 2 * npts, W, p.xh0, p.xh1, p.wh0, p.wh1, p.yh0, p.yh1, p.vh0, p.vh1);
+    boris(ux, uy, uz, ex, ey, ez, bx, by, bz, qm, S.dt);
+    float ig = rsqrtf(1.0f + ux * ux + uy * uy + uz * uz);
+    const float c = (float)kCnmPerFs;
+    xn = xi + ux * ig * c * S.dt / S.dx;
+    yn = DIM == 2 ? eta + uy * ig * c * S.dt / S.dy : eta;
+    if (!(fabsf(xn - xi) < 64.0f && fabsf(yn - eta) < 64.0f)) return -2;
+    float fx = floorf(xn), fy = floorf(yn);
+    int ncx = cx + (int)fx;
+    int ncy = DIM == 2 ? cy + (int)fy : 0;
+    if (DIM == 2) { if (ncy < 0) ncy += S.ny; else if (ncy >= S.ny) ncy -= S.ny; }
+    return (ncx < 0 || ncx >= S.nx) ? -1 : ncy * S.nx + ncx;
+}
+
+__device__ __forceinline__ void wrap_offsets(float xn, float yn, float &xi, float &eta)
+{
+    const float below1 = 0.99999994f;
+    xi = xn - floorf(xn);
+    eta = yn - floorf(yn);
+    if (xi >= 1.0f) xi = below1;
+    if (eta >= 1.0f) eta = below1;
+}
+
+template <int DIM>
+__device__ void push_cell(const PushArgs &a, const SlabDev &S, int s, int g, int lane, dd &esc, int &esc_e,
+                          int &esc_i)
+{
+    const int lc = g - S.cell0;
+    const int cx = lc % S.nx, cy = lc / S.nx;
+    const bool do_push = S.flags & 64u, do_dep = (S.flags & 128u) != 0;
+    const float *fe = a.fldE + S.fld_off, *fb = a.fldB + S.fld_off;
+    const float MC2 = (float)kMeC2;
+    long long acc[2] = {0, 0};
+
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool elec = pass == 0;
+        const int k0 = elec ? a.cs_e[g] : a.cs_i[g], k1 = elec ? a.cs_e[g + 1] : a.cs_i[g + 1];
+        float4 *R0 = elec ? a.e0 : a.i0, *R1 = elec ? a.e1 : a.i1;
+        int *key = elec ? a.ekey : a.ikey;
+        int *cnt = elec ? a.cnt_e : a.cnt_i;
+        // every lane runs the same number of iterations (the warp reductions
+        // of the deposit need all 32 lanes)
+        for (int base = k0; base < k1; base += 32) {
+            const int k = base + lane;
+            const bool have = k < k1;
+            int nk = -1;
+            float x0 = 0.f, y0 = 0.f, x1 = 0.f, y1 = 0.f, qw = 0.f, qwby = 0.f, qwbz = 0.f;
+            bool dep_short = false;
+            if (have) {
+                float4 P0 = R0[k], P1 = R1[k];
+                if (elec ? P1.y <= 0.0f : (__float_as_int(P1.w) & 0xff) == 0xff) {
+                    nk = -1;                                   // recombined away, or dropped
+                } else if (!do_push) {
+                    nk = g;
+                } else {
+                    float q, m, w;
+                    if (elec) { q = -1.0f; m = 1.0f; w = P1.y; }
+                    else { q = (float)(__float_as_int(P1.w) & 0xff) + P1.y; m = S.m_ion; w = S.w_ion; }
+                    float xi = P0.x, eta = P0.y, ux = P0.z, uy = P0.w, uz = P1.x, xn, yn;
+                    float ke = MC2 * m * gm1(ux, uy, uz);
+                    int nc = move_particle<DIM>(S, fe, fb, a.npts, cx, cy, xi, eta, ux, uy, uz, q / m, xn, yn);
+                    if (nc == -2) {
+                        nk = -1;
+                        atomicOr(a.err, ERR_NUMERIC);
+                    } else {
+                        if (do_dep) {
+                            float ig = rsqrtf(1.0f + ux * ux + uy * uy + uz * uz);
+                            qw = q * w; qwby = qw * uy * ig; qwbz = qw * uz * ig;
+                            if (fabsf(xn - xi) < 1.0f && fabsf(yn - eta) < 1.0f) {
+                                dep_short = true;
+                                x0 = xi; y0 = eta; x1 = xn; y1 = yn;
+                            } else {
+                                SlabGrid gr;
+                                gr.nx = S.nx; gr.ny = S.ny; gr.W = S.nx + 1; gr.fe = fe; gr.fb = fb;
+                                gr.npts = a.npts; gr.fo = S.fld_off;
+                                deposit_long(gr, a.J, a.npts, S.fld_off, cx, cy, xi, eta, xn, yn, qw, qwby, qwbz);
+                            }
+                        }
+                        if (nc == -1) {
+                            esc = dd_addf(esc, w * ke);
+                            if (elec) esc_e++; else esc_i++;
+                        } else {
+                            nk = S.cell0 + nc;
+                        }
+                        wrap_offsets(xn, yn, xi, eta);
+                        R0[k] = make_float4(xi, eta, ux, uy);
+                        reinterpret_cast<float *>(R1 + k)[0] = uz;
+                    }
+                }
+                key[k] = nk;
+            }
+            if (do_dep) {
+                if (!dep_short) { qw = qwby = qwbz = 0.0f; x0 = x1 = 0.5f; y0 = y1 = 0.5f; }
+                if constexpr (DIM == 2) esirkepov2_w(x0, y0, x1, y1, qw, qwbz, acc, lane);
+                else esirkepov1_w(x0, x1, qw, qwby, qwbz, acc, lane);
+            }
+            // aggregated count of the next cell
+            unsigned peers = __match_any_sync(FULL, have ? nk : -2);
+            if (have && nk >= 0 && lane == __ffs(peers) - 1) atomicAdd(cnt + nk, __popc(peers));
+        }
+    }
+
+    if (do_dep) {
+        const int fo = S.fld_off, W = S.nx + 1;
+        const int nj = DIM == 2 ? 40 : 11;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = lane + 32 * h;
+            if (k >= nj || acc[h] == 0) continue;
+            if (DIM == 2) {
+                int p, q, comp;
+                if (k < 12) { comp = 0; p = k / 4; q = k % 4; }
+                else if (k < 24) { comp = 1; p = (k - 12) / 3; q = (k - 12) % 3; }
+                else { comp = 2; p = (k - 24) / 4; q = (k - 24) % 4; }
+                const int i = cx - 1 + p;
+                int j = cy - 1 + q;
+                j = j < 0 ? j + S.ny : (j >= S.ny ? j - S.ny : j);
+                const bool ok = comp == 0 ? (i >= 0 && i < S.nx) : (i >= 0 && i <= S.nx);
+                if (ok) jglobal(a.J + (size_t)comp * a.npts + fo + (size_t)j * W + i, acc[h]);
+            } else {
+                int comp, p;
+                if (k < 3) { comp = 0; p = k; } else if (k < 7) { comp = 1; p = k - 3; } else { comp = 2; p = k - 7; }
+                const int i = cx - 1 + p;
+                const bool ok = comp == 0 ? (i >= 0 && i < S.nx) : (i >= 0 && i <= S.nx);
+                if (ok) jglobal(a.J + (size_t)comp * a.npts + fo + i, acc[h]);
+            }
+        }
+    }
+}
+
+__device__ void push_flush(const PushArgs &a, int slab, dd &esc, int &esc_e, int &esc_i, int lane)
+{
+    dd e = wsum_dd(esc);
+    int ce = wsum_i(esc_e), ci = wsum_i(esc_i);
+    if (slab >= 0 && lane == 0) {
+        SlabTally *tl = a.tally + slab;
+        if (dd_f(e) != 0.0f) atomicAdd(&tl->esc, (double)e.hi + (double)e.lo);
+        if (ce) atomicAdd(tl->cnt + C_ESC_E, (unsigned long long)ce);
+        if (ci) atomicAdd(tl->cnt + C_ESC_I, (unsigned long long)ci);
+    }
+    esc = dd_zero();
+    esc_e = esc_i = 0;
+}
+
+__global__ void __launch_bounds__(256) k_push(PushArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    int cur = -1;
+    dd esc = dd_zero();
+    int esc_e = 0, esc_i = 0;
+    for (;;) {
+        int w = 0;
+        if (lane == 0) w = atomicAdd(a.work, 1);
+        w = __shfl_sync(FULL, w, 0);
+        if (w >= a.ncell) break;
+        const int g = w;
+        if (a.cs_e[g + 1] == a.cs_e[g] && a.cs_i[g + 1] == a.cs_i[g]) continue;
+        const int s = __ldg(a.cell_slab + g);
+        if (s != cur) { push_flush(a, cur, esc, esc_e, esc_i, lane); cur = s; }
+        const SlabDev &S = a.slabs[s];
+        if (S.ny > 1) push_cell<2>(a, S, s, g, lane, esc, esc_e, esc_i);
+        else push_cell<1>(a, S, s, g, lane, esc, esc_e, esc_i);
+    }
+    push_flush(a, cur, esc, esc_e, esc_i, lane);
+}
+
+// Electrons created this step sit after the sorted range with their cell in
+// the key; they are pushed one per thread and deposit straight to global
+// memory (integer atomics, so the order does not matter).
+__global__ void k_push_new(PushArgs a)
+{
+    const int sorted = a.cs_e[a.ncell];
+    const int n = min(*a.append, a.cap_e - sorted);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const int k = sorted + t;
+        const int g = a.ekey[k];
+        if (g < 0) continue;
+        const int s = __ldg(a.cell_slab + g);
+        const SlabDev &S = a.slabs[s];
+        const int lc = g - S.cell0, cx = lc % S.nx, cy = lc / S.nx;
+        float4 P0 = a.e0[k], P1 = a.e1[k];
+        int nk = g;
+        if (S.flags & 64u) {
+            const float *fe = a.fldE + S.fld_off, *fb = a.fldB + S.fld_off;
+            float xi = P0.x, eta = P0.y, ux = P0.z, uy = P0.w, uz = P1.x, xn, yn;
+            float ke = (float)kMeC2 * gm1(ux, uy, uz);
+            int nc = S.ny > 1 ? move_particle<2>(S, fe, fb, a.npts, cx, cy, xi, eta, ux, uy, uz, -1.0f, xn, yn)
+                              : move_particle<1>(S, fe, fb, a.npts, cx, cy, xi, eta, ux, uy, uz, -1.0f, xn, yn);
+            if (nc == -2) {
+                nk = -1;
+                atomicOr(a.err, ERR_NUMERIC);
+            } else {
+                if (S.flags & 128u) {
+                    float qw = -P1.y;
+                    float ig = rsqrtf(1.0f + ux * ux + uy * uy + uz * uz);
+                    SlabGrid gr;
+                    gr.nx = S.nx; gr.ny = S.ny; gr.W = S.nx + 1; gr.fe = fe; gr.fb = fb;
+                    gr.npts = a.npts; gr.fo = S.fld_off;
+                    deposit_long(gr, a.J, a.npts, S.fld_off, cx, cy, xi, eta, xn, yn, qw, qw * uy * ig, qw * uz * ig);
+                }
+                if (nc == -1) {
+                    nk = -1;
+                    atomicAdd(&a.tally[s].esc, (double)(P1.y * ke));
+                    atomicAdd(a.tally[s].cnt + C_ESC_E, 1ull);
+                } else {
+                    nk = S.cell0 + nc;
+                }
+                wrap_offsets(xn, yn, xi, eta);
+                a.e0[k] = make_float4(xi, eta, ux, uy);
+                reinterpret_cast<float *>(a.e1 + k)[0] = uz;
+            }
+        }
+        a.ekey[k] = nk;
+        if (nk >= 0) atomicAdd(a.cnt_e + nk, 1);
+    }
+}
+
+}  // namespace pic
