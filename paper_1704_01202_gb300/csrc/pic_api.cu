@@ -50,7 +50,7 @@ struct pic_ctx {
 
     float4 *eA0, *eA1, *eB0, *eB1;
     float4 *iA0, *iA1, *iB0, *iB1;
-    int *ekey, *ikey;
+    int *ekey, *ikey, *eord, *iord;
     int *csE[2], *csI[2];
     int cur = 0;
     int *cnt_e, *cnt_i, *fill_e, *fill_i, *bsum_e, *bsum_i;
@@ -111,8 +111,8 @@ T *carve_arena(pic_ctx *c, size_t count)
 size_t arena_need(int ncell, int npts, int nblk, int cap_e, int cap_i)
 {
     size_t b = 0;
-    b += 4 * al((size_t)cap_e * 16) + al((size_t)cap_e * 4);
-    b += 4 * al((size_t)cap_i * 16) + al((size_t)cap_i * 4);
+    b += 4 * al((size_t)cap_e * 16) + 2 * al((size_t)cap_e * 4);
+    b += 4 * al((size_t)cap_i * 16) + 2 * al((size_t)cap_i * 4);
     b += 4 * al((size_t)(ncell + 1) * 4) + 4 * al((size_t)ncell * 4) + 2 * al((size_t)nblk * 4);
     b += al(NCOUNTERS * 4) + al((size_t)ncell * 4) * 2;
     b += al(sizeof(SlabDev)) + al(4) + al(sizeof(SlabTally)) + al(sizeof(Tables)) + al(sizeof(EosTable));
@@ -164,6 +164,7 @@ CellArgs cell_args(pic_ctx *c, bool big)
 {
     CellArgs a{};
     a.e0 = c->eA0; a.e1 = c->eA1; a.ekey = c->ekey; a.cs_e = c->csE[c->cur];
+    a.eord = c->eord; a.iord = c->iord;
     a.i0 = c->iA0; a.i1 = c->iA1; a.ikey = c->ikey; a.cs_i = c->csI[c->cur];
     a.cnt_e = c->cnt_e; a.cnt_i = c->cnt_i;
     a.append = c->counters + CNT_APPEND;
@@ -251,6 +252,7 @@ pic_status launch_step(pic_ctx *c)
     if (ev) CK(cudaEventRecord(ev[2], st));
     PushArgs pa{};
     pa.e0 = c->eA0; pa.e1 = c->eA1; pa.ekey = c->ekey; pa.cs_e = c->csE[c->cur];
+    pa.eord = c->eord; pa.iord = c->iord;
     pa.i0 = c->iA0; pa.i1 = c->iA1; pa.ikey = c->ikey; pa.cs_i = c->csI[c->cur];
     pa.cnt_e = c->cnt_e; pa.cnt_i = c->cnt_i; pa.append = c->counters + CNT_APPEND; pa.cap_e = c->cap_e;
     pa.ncell = c->ncell; pa.cell_slab = c->cell_slab; pa.slabs = c->d_slab; pa.tally = c->d_tally;
@@ -367,9 +369,11 @@ pic_status pic_init(pic_ctx **out, const pic_grid *g, const pic_species *s, cons
     c->eA0 = carve_arena<float4>(c, c->cap_e); c->eA1 = carve_arena<float4>(c, c->cap_e);
     c->eB0 = carve_arena<float4>(c, c->cap_e); c->eB1 = carve_arena<float4>(c, c->cap_e);
     c->ekey = carve_arena<int>(c, c->cap_e);
+    c->eord = carve_arena<int>(c, c->cap_e);
     c->iA0 = carve_arena<float4>(c, c->cap_i); c->iA1 = carve_arena<float4>(c, c->cap_i);
     c->iB0 = carve_arena<float4>(c, c->cap_i); c->iB1 = carve_arena<float4>(c, c->cap_i);
     c->ikey = carve_arena<int>(c, c->cap_i);
+    c->iord = carve_arena<int>(c, c->cap_i);
     for (int k = 0; k < 2; ++k) { c->csE[k] = carve_arena<int>(c, c->ncell + 1); c->csI[k] = carve_arena<int>(c, c->ncell + 1); }
     c->cnt_e = carve_arena<int>(c, 4 * (size_t)c->ncell);
     c->cnt_i = c->cnt_e + c->ncell; c->fill_e = c->cnt_i + c->ncell; c->fill_i = c->fill_e + c->ncell;

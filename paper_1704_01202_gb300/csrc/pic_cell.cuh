@@ -28,6 +28,7 @@ struct NewE {            // an electron created in this cell this step
 struct CellArgs {
     float4 *e0, *e1;     // electrons (xi, eta, ux, uy), (uz, w, id_lo, id_hi)
     int *ekey;           // next cell of each electron slot (-1: gone)
+    int *eord, *iord;    // canonical order of each cell: slot of position k
     const int *cs_e;     // cell start of electrons [ncell + 1]
     float4 *i0, *i1;     // ions (xi, eta, ux, uy), (uz, zfrac, id, Z | nK << 8)
     int *ikey;

@@ -333,26 +333,42 @@ __device__ __noinline__ void stage_decay(const CellArgs &a, const WarpMem &m, co
     __syncwarp();
 }
 
-__device__ void process_cell(const CellArgs &a, const WarpMem &m, const Tables &T, int g, int lane, WarpTally &wt)
+// One round: every warp of the block takes at most one cell; the stages
+// are separated by block barriers so the warps of an SM fetch the same code
+// at the same time (the stages are long and the instruction cache small).
+__device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables &T, int g, int lane, WarpTally &wt)
 {
-    const int s = __ldg(a.cell_slab + g);
-    if (s != wt.slab) { tally_flush(a, wt, lane); wt.slab = s; }
-    const SlabDev &S = a.slabs[s];
-    const unsigned step = a.steps[s];
-    const unsigned long long seed = S.seed;
-    const unsigned flags = S.flags;
-    const int lc = g - S.cell0;
-    const int cx = lc % S.nx, cy = lc / S.nx;
-    const int e0 = a.cs_e[g], ne = a.cs_e[g + 1] - e0;
-    const int i0 = a.cs_i[g], ni = a.cs_i[g + 1] - i0;
-    if (ne == 0 && ni == 0) return;
+    bool on = g >= 0;
+    int s = 0;
+    const SlabDev *Sp = a.slabs;
+    unsigned step = 0, flags = 0;
+    unsigned long long seed = 0;
+    int lc = 0, cx = 0, cy = 0, e0 = 0, ne = 0, i0 = 0, ni = 0;
+    if (on) {
+        s = __ldg(a.cell_slab + g);
+        if (s != wt.slab) { tally_flush(a, wt, lane); wt.slab = s; }
+        Sp = a.slabs + s;
+        step = a.steps[s];
+        seed = Sp->seed;
+        flags = Sp->flags;
+        lc = g - Sp->cell0;
+        cx = lc % Sp->nx; cy = lc / Sp->nx;
+        e0 = a.cs_e[g]; ne = a.cs_e[g + 1] - e0;
+        i0 = a.cs_i[g]; ni = a.cs_i[g + 1] - i0;
+        on = ne > 0 || ni > 0;
+    }
+    const SlabDev &S = *Sp;
     const float wi = S.w_ion;
     const float mi = S.m_ion;
     const bool rad = S.rad_every > 0 && (step % (unsigned)S.rad_every) == 0;
     const float MC2 = (float)kMeC2;
     const float nref = S.nref_f;
     int c_ee = 0, c_ei = 0, c_ion = 0, c_rej = 0;
+    float n_e = 0.f, n_i = 0.f, Te = 0.f, zbar = 0.f, lnL = 2.f;
+    int nnew = 0;
+    float Wnew_imp = 0.0f;
 
+    if (on) {
     // ---- stage in shared memory; Philox sort keys ----
     for (int k = lane; k < ne; k += 32) {
         float4 P0 = a.e0[e0 + k], P1 = a.e1[e0 + k];
@@ -377,6 +393,10 @@ __device__ void process_cell(const CellArgs &a, const WarpMem &m, const Tables &
     warp_bitonic<unsigned long long>(m.ekey, m.eid, m.eperm, ne, lane);
     warp_bitonic<unsigned int>(m.ikey, m.iid, m.iperm, ni, lane);
 
+    }
+    __syncthreads();
+
+    if (on) {
     // ---- cell moments (Sec. II: T_e = 2/3 E_ave over bulk electrons) ----
     dd We = dd_zero(), Wb = dd_zero(), Kb = dd_zero(), Q = dd_zero();
     for (int k = lane; k < ne; k += 32) {
@@ -390,11 +410,11 @@ __device__ void process_cell(const CellArgs &a, const WarpMem &m, const Tables &
         Q = dd_addf(Q, (float)(m.ist[sl] & 0xff) + m.iu[sl].w);
     }
     We = wsum_dd(We); Wb = wsum_dd(Wb); Kb = wsum_dd(Kb); Q = wsum_dd(Q);
-    const float n_e = dd_f(We) * nref, n_i = (float)ni * wi * nref;
-    const float Te = dd_f(Wb) > 0.0f ? (2.0f / 3.0f) * dd_f(Kb) / dd_f(Wb) : 0.0f;
-    const float zbar = ni > 0 ? dd_f(Q) / ni : 0.0f;
+    n_e = dd_f(We) * nref; n_i = (float)ni * wi * nref;
+    Te = dd_f(Wb) > 0.0f ? (2.0f / 3.0f) * dd_f(Kb) / dd_f(Wb) : 0.0f;
+    zbar = ni > 0 ? dd_f(Q) / ni : 0.0f;
     if (lane < NZ) m.dE[lane] = ipd_shift(S.ipd, lane, n_e, n_i, Te, zbar);
-    const float lnL = S.coulomb_log > 0.0f ? S.coulomb_log : coulomb_log(n_e, Te, zbar);
+    lnL = S.coulomb_log > 0.0f ? S.coulomb_log : coulomb_log(n_e, Te, zbar);
     __syncwarp();
 
     // ---- binary collisions (Sec. IV): e-e, then e-i; exact energy restore ----
@@ -469,9 +489,11 @@ __device__ void process_cell(const CellArgs &a, const WarpMem &m, const Tables &
         __syncwarp();
     }
 
+    }
+    __syncthreads();
+
+    if (on) {
     // ---- Lotz impact ionization, cell-average probability (Eq. 3) ----
-    int nnew = 0;
-    float Wnew_imp = 0.0f;
     if ((flags & 4u) && ne >= 1 && ni >= 1) {
         unsigned pmask = 0;
         for (int k = lane; k < ni; k += 32) { int Z = m.ist[k] & 0xff; if (Z < ZNUC) pmask |= 1u << Z; }
@@ -550,6 +572,10 @@ __device__ void process_cell(const CellArgs &a, const WarpMem &m, const Tables &
         __syncwarp();
     }
 
+    }
+    __syncthreads();
+
+    if (on) {
     CellCtx cc;
     cc.s = s; cc.lc = lc; cc.cx = cx; cc.cy = cy; cc.e0 = e0; cc.ne = ne; cc.i0 = i0; cc.ni = ni;
     cc.step = step; cc.flags = flags; cc.seed = seed; cc.wi = wi; cc.mi = mi; cc.n_e = n_e; cc.n_i = n_i;
@@ -558,7 +584,10 @@ __device__ void process_cell(const CellArgs &a, const WarpMem &m, const Tables &
     if (rad && (flags & 16u) && S.nb && ni >= 1) stage_photo(a, m, T, S, cc, lane, nnew, wt);
     if (rad && (flags & 32u) && ni >= 1) stage_decay(a, m, T, S, cc, lane, nnew, wt);
 
-    // ---- write the collided state back (positions unchanged) ----
+    // ---- write the collided state back (positions unchanged) and the
+    //      canonical order, which the push kernel follows ----
+    for (int k = lane; k < ne; k += 32) a.eord[e0 + k] = m.eperm[k];
+    for (int k = lane; k < ni; k += 32) a.iord[i0 + k] = m.iperm[k];
     for (int k = lane; k < ne; k += 32) {
         float4 u = m.eu[k];
         reinterpret_cast<float2 *>(a.e0 + e0 + k)[1] = make_float2(u.x, u.y);
@@ -601,19 +630,21 @@ __device__ void process_cell(const CellArgs &a, const WarpMem &m, const Tables &
     wt.cnt[C_ION] += wsum_i(c_ion);
     wt.cnt[C_ION_REJ] += wsum_i(c_rej);
     __syncwarp();
+    }
+    __syncthreads();
 }
 
-// One warp per cell, cells taken from a shared counter.  Cells whose
-// population exceeds this launch's shared-memory capacity go to a list for
-// the large-cell launch.
+// Each round the block takes one cell per warp from a shared counter.
+// Cells whose population exceeds this launch's shared-memory capacity go to
+// a list for the large-cell launch.
 __global__ void __launch_bounds__(256, 2) k_cell(CellArgs a)
 {
     extern __shared__ __align__(16) char smem[];
     __shared__ Tables T;
+    __shared__ int round_base;
     for (int k = threadIdx.x; k < (int)(sizeof(Tables) / 4); k += blockDim.x)
         ((float *)&T)[k] = ((const float *)a.tab)[k];
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     WarpMem m = carve(smem + (size_t)warp * warp_mem_bytes(a.cap_ce, a.cap_ci, a.cap_new),
                       a.cap_ce, a.cap_ci, a.cap_new);
     const int total = a.list ? *a.n_list : a.ncell;
@@ -622,25 +653,35 @@ __global__ void __launch_bounds__(256, 2) k_cell(CellArgs a)
     wt.ion = wt.ka = wt.esc = dd_zero();
     for (int q = 0; q < NCOUNT; ++q) wt.cnt[q] = 0;
     for (;;) {
-        int w = 0;
-        if (lane == 0) w = atomicAdd(a.work, 1);
-        w = __shfl_sync(FULL, w, 0);
-        if (w >= total) break;
-        int g = a.list ? a.list[w] : w;
-        int ne = a.cs_e[g + 1] - a.cs_e[g], ni = a.cs_i[g + 1] - a.cs_i[g];
-        if (ne > a.cap_ce || ni > a.cap_ci || 3 * ni > a.cap_new) {
-            if (a.ovf_list) {
-                if (lane == 0) a.ovf_list[atomicAdd(a.ovf_count, 1)] = g;
-            } else {
-                // no larger pass left: report, and drop the cell's particles so
-                // that the next sort stays consistent
-                if (lane == 0) atomicOr(a.err, ERR_CELL_OVERFLOW);
-                for (int k = a.cs_e[g] + lane; k < a.cs_e[g + 1]; k += 32) reinterpret_cast<float *>(a.e1 + k)[1] = 0.0f;
-                for (int k = a.cs_i[g] + lane; k < a.cs_i[g + 1]; k += 32) reinterpret_cast<int *>(a.i1 + k)[3] = 0xff;
+        __syncthreads();
+        if (threadIdx.x == 0) round_base = atomicAdd(a.work, nwarp);
+        __syncthreads();
+        const int base = round_base;
+        if (base >= total) break;
+        int g = -1;
+        if (base + warp < total) {
+            g = a.list ? a.list[base + warp] : base + warp;
+            int ne = a.cs_e[g + 1] - a.cs_e[g], ni = a.cs_i[g + 1] - a.cs_i[g];
+            if (ne > a.cap_ce || ni > a.cap_ci || 3 * ni > a.cap_new) {
+                if (a.ovf_list) {
+                    if (lane == 0) a.ovf_list[atomicAdd(a.ovf_count, 1)] = g;
+                } else {
+                    // no larger pass left: report, and drop the cell's particles so
+                    // that the next sort stays consistent
+                    if (lane == 0) atomicOr(a.err, ERR_CELL_OVERFLOW);
+                    for (int k = a.cs_e[g] + lane; k < a.cs_e[g + 1]; k += 32) {
+                        reinterpret_cast<float *>(a.e1 + k)[1] = 0.0f;
+                        a.eord[k] = k - a.cs_e[g];
+                    }
+                    for (int k = a.cs_i[g] + lane; k < a.cs_i[g + 1]; k += 32) {
+                        reinterpret_cast<int *>(a.i1 + k)[3] = 0xff;
+                        a.iord[k] = k - a.cs_i[g];
+                    }
+                }
+                g = -1;
             }
-            continue;
         }
-        process_cell(a, m, T, g, lane, wt);
+        process_round(a, m, T, g, lane, wt);
     }
     tally_flush(a, wt, lane);
 }

@@ -226,7 +226,7 @@ __device__ __forceinline__ dd dd_zero() { return dd{0.0f, 0.0f}; }
 __device__ __forceinline__ bool dd_le(dd a, dd b) { dd d = dd_sub(b, a); return d.hi > 0.0f || (d.hi == 0.0f && d.lo >= 0.0f); }
 
 // ---------------- Lotz cross section (Eq. 3), cm^2 ----------------
-__device__ __forceinline__ float lotz_sigma(const Tables &T, int z, float dE, float E)
+__device__ __noinline__ float lotz_sigma(const Tables &T, int z, float dE, float E)
 {
     int occ[NS];
     if (z >= ZNUC || !occupancy(ZNUC - z, 0, occ)) return 0.0f;
@@ -286,7 +286,7 @@ __device__ __forceinline__ void scale_kinetic(float &ux, float &uy, float &uz, f
 // var = 2 pi (qa qb)^2 r_e^2 c n lnL dt / (mu^2 beta_rel^3), applied as a
 // rotation of the centre-of-momentum momentum; weighted acceptance
 // min(1, w_other / w_self).  Masses in m_e, u in units of m c of each.
-__device__ __forceinline__ bool binary_collision(float3 &ua, float3 &ub, float ma, float mb, float qa, float qb,
+__device__ __noinline__ bool binary_collision(float3 &ua, float3 &ub, float ma, float mb, float qa, float qb,
                                                  float wa, float wb, float n_l, float lnL, float dtc,
                                                  float r0, float r1, float r2, float r3)
 {

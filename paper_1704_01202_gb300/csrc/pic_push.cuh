@@ -1,11 +1,12 @@
 // Boris push and charge-conserving deposit, one warp per cell.
 //
-// Each particle's contribution to the cell's current stencil is rounded to
-// 32-bit fixed point (2^22 per unit of q w W), summed across the warp with
-// the integer warp reduction, kept in 64-bit running sums and added to the
-// global 2^40 fixed-point grid: integer addition is associative, so the
-// result does not depend on the memory order of the particles, which the
-// atomic scatter of the counting sort leaves unspecified.
+// A cell's particles are visited in the canonical order the collision
+// kernel recorded (the memory order inside a cell, left by the atomic
+// scatter of the counting sort, is unspecified).  Lane L takes canonical
+// positions L, L+32, ...; each stencil contribution is summed across the
+// warp with a fixed butterfly, the running sum of node k is kept by lane
+// k % 32, and the cell's totals go to the global grid as 2^40 fixed point,
+// whose addition is associative.  The current is therefore bit-reproducible.
 #pragma once
 #include "pic_cell.cuh"
 
@@ -14,6 +15,7 @@ namespace pic {
 struct PushArgs {
     float4 *e0, *e1;
     int *ekey;
+    const int *eord, *iord;   // canonical order of each cell (from the collision kernel)
     const int *cs_e;
     float4 *i0, *i1;
     int *ikey;
@@ -32,8 +34,6 @@ struct PushArgs {
     int *work;
 };
 
-constexpr float JI_SCALE = 4194304.0f;        // 2^22 lane fixed point
-constexpr int JI_TO_GLOBAL = 18;              // 2^22 -> 2^40
 
 // CIC weights and indices of one particle on the staggered grid
 struct GatherPt {
@@ -73,23 +73,19 @@ __device__ __forceinline__ float interp4(const float *F, int W, int x0, int x1, 
     return w0 * (v0 * __ldg(r0 + x0) + v1 * __ldg(r1 + x0)) + w1 * (v0 * __ldg(r0 + x1) + v1 * __ldg(r1 + x1));
 }
 
-__device__ __forceinline__ int jq(float v) { return __float2int_rn(v * JI_SCALE); }
-
-// Running sums of a cell's current stencil: sum k is held by lane k % 32
-// in acc[k / 32].  One contribution per lane and node is summed across the
-// warp with the integer warp reduction (all lanes take part; lanes without
-// a particle add 0).
-__device__ __forceinline__ void jadd(long long acc[2], int k, int v, int lane)
+// warp sum of one contribution (fixed butterfly); lane k % 32 keeps it
+__device__ __forceinline__ void jadd(float acc[2], int k, float v, int lane)
 {
-    int s = __reduce_add_sync(FULL, v);
-    if (lane == (k & 31)) acc[k >> 5] += s;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    if (lane == (k & 31)) acc[k >> 5] += v;
 }
 
 // 2D Esirkepov weights of one sub-cell move (offsets relative to the cell,
 // stencil nodes -1..2); order of the sums: jx[a][b] (12), jy[a][b] (12),
 // jz[a][b] (16)
 __device__ __forceinline__ void esirkepov2_w(float x0, float y0, float x1, float y1, float qw, float qwbz,
-                                             long long acc[2], int lane)
+                                             float acc[2], int lane)
 {
     float S0x[4], S1x[4], S0y[4], S1y[4];
 #pragma unroll
@@ -104,7 +100,7 @@ __device__ __forceinline__ void esirkepov2_w(float x0, float y0, float x1, float
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             acc_x += (S1x[a] - S0x[a]) * sy;
-            jadd(acc, a * 4 + b, jq(-qw * acc_x), lane);
+            jadd(acc, a * 4 + b, -qw * acc_x, lane);
         }
     }
 #pragma unroll
@@ -115,19 +111,19 @@ __device__ __forceinline__ void esirkepov2_w(float x0, float y0, float x1, float
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
             acc_y += (S1y[b] - S0y[b]) * sx;
-            jadd(acc, 12 + a * 3 + b, jq(-qw * acc_y), lane);
+            jadd(acc, 12 + a * 3 + b, -qw * acc_y, lane);
         }
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
             float dsy = S1y[b] - S0y[b];
             float wz = S0x[a] * S0y[b] + 0.5f * dsx * S0y[b] + 0.5f * S0x[a] * dsy + dsx * dsy * (1.0f / 3.0f);
-            jadd(acc, 24 + a * 4 + b, jq(qwbz * wz), lane);
+            jadd(acc, 24 + a * 4 + b, qwbz * wz, lane);
         }
     }
 }
 
 // 1D: jx at 3 half nodes (0..2), jy (3..6), jz (7..10) at 4 nodes
-__device__ __forceinline__ void esirkepov1_w(float x0, float x1, float qw, float qwby, float qwbz, long long acc[2],
+__device__ __forceinline__ void esirkepov1_w(float x0, float x1, float qw, float qwby, float qwbz, float acc[2],
                                              int lane)
 {
     float S0x[4], S1x[4];
@@ -135,12 +131,12 @@ __device__ __forceinline__ void esirkepov1_w(float x0, float x1, float qw, float
     for (int a = 0; a < 4; ++a) { S0x[a] = cic_w(x0, a - 1); S1x[a] = cic_w(x1, a - 1); }
     float acc_x = 0.0f;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) { acc_x += S1x[a] - S0x[a]; jadd(acc, a, jq(-qw * acc_x), lane); }
+    for (int a = 0; a < 3; ++a) { acc_x += S1x[a] - S0x[a]; jadd(acc, a, -qw * acc_x, lane); }
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
         float sv = 0.5f * (S0x[a] + S1x[a]);
-        jadd(acc, 3 + a, jq(qwby * sv), lane);
-        jadd(acc, 7 + a, jq(qwbz * sv), lane);
+        jadd(acc, 3 + a, qwby * sv, lane);
+        jadd(acc, 7 + a, qwbz * sv, lane);
     }
 }
 
@@ -151,9 +147,9 @@ __device__ __forceinline__ long long wsum_ll(long long v)
     return v;
 }
 
-__device__ __forceinline__ void jglobal(unsigned long long *J, long long v)
+__device__ __forceinline__ void jglobal(unsigned long long *J, float v)
 {
-    if (v != 0) atomicAdd(J, (unsigned long long)(v << JI_TO_GLOBAL));
+    if (v != 0.0f) atomicAdd(J, (unsigned long long)fix40(v));
 }
 
 // One particle: gather, Boris, move; returns the next local cell, -1 when
@@ -202,7 +198,7 @@ __device__ void push_cell(const PushArgs &a, const SlabDev &S, int s, int g, int
     const bool do_push = S.flags & 64u, do_dep = (S.flags & 128u) != 0;
     const float *fe = a.fldE + S.fld_off, *fb = a.fldB + S.fld_off;
     const float MC2 = (float)kMeC2;
-    long long acc[2] = {0, 0};
+    float acc[2] = {0.0f, 0.0f};
 
     for (int pass = 0; pass < 2; ++pass) {
         const bool elec = pass == 0;
@@ -210,11 +206,13 @@ __device__ void push_cell(const PushArgs &a, const SlabDev &S, int s, int g, int
         float4 *R0 = elec ? a.e0 : a.i0, *R1 = elec ? a.e1 : a.i1;
         int *key = elec ? a.ekey : a.ikey;
         int *cnt = elec ? a.cnt_e : a.cnt_i;
+        const int *ord = elec ? a.eord : a.iord;
+        const int n = k1 - k0;
         // every lane runs the same number of iterations (the warp reductions
         // of the deposit need all 32 lanes)
-        for (int base = k0; base < k1; base += 32) {
-            const int k = base + lane;
-            const bool have = k < k1;
+        for (int base = 0; base < n; base += 32) {
+            const bool have = base + lane < n;
+            const int k = have ? k0 + min(max(ord[k0 + base + lane], 0), n - 1) : k0;
             int nk = -1;
             float x0 = 0.f, y0 = 0.f, x1 = 0.f, y1 = 0.f, qw = 0.f, qwby = 0.f, qwbz = 0.f;
             bool dep_short = false;
@@ -278,7 +276,7 @@ __device__ void push_cell(const PushArgs &a, const SlabDev &S, int s, int g, int
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int k = lane + 32 * h;
-            if (k >= nj || acc[h] == 0) continue;
+            if (k >= nj || acc[h] == 0.0f) continue;
             if (DIM == 2) {
                 int p, q, comp;
                 if (k < 12) { comp = 0; p = k / 4; q = k % 4; }
