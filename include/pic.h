@@ -174,6 +174,58 @@ pic_status pic_get_fields(pic_ctx *c, float *f6);
 /* Current density of the last step, [3][ny][nx+1], units e n_ref nm/fs. */
 pic_status pic_get_current(pic_ctx *c, double *j3);
 
+/* ---------------- batched slabs ----------------
+ * A batch context steps many independent 1D slabs with one launch of each
+ * kernel per step: slot k owns cells [k*slot_cells, (k+1)*slot_cells) of one
+ * global numbering, its own grid points, photons, tallies and step counter.
+ * A slab's random streams are keyed by its own seed, particle ids and its own
+ * step count, and every cross-particle sum is fixed-point or in canonical
+ * order, so a slab evolves bit-identically alone (pic_init) or in a batch,
+ * whatever its neighbours.  Slabs are admitted and retired between steps;
+ * admission copies the particles and re-sorts once, on the next step,
+ * diagnostics or copy call.  pic_step, pic_sync and pic_timing work on batch
+ * contexts; the single-slab calls above return PIC_ERR_STATE.
+ * The paper runs one slab per job; batching is a throughput feature of
+ * this implementation. */
+
+/* Bytes of device memory pic_batch_init needs. 0 on invalid sizes. */
+size_t pic_batch_required_bytes(int max_slabs, int slot_cells, int cap_e, int cap_i);
+
+/* Create an empty batch context of max_slabs slots of slot_cells cells
+ * (2..8192).  cap_e / cap_i: particle capacity summed over all slabs.
+ * arena / stream as in pic_init. */
+pic_status pic_batch_init(pic_ctx **out, int max_slabs, int slot_cells, int cap_e, int cap_i,
+                          const pic_tables *t, void *arena, size_t arena_bytes, void *stream);
+
+/* Admit one 1D slab (g->ny == 1, g->nx <= slot_cells) with its species,
+ * optional pulse (NULL: none) and particles (host arrays as in
+ * pic_load_*).  The host arrays may be freed on return.  *slot_out gets the
+ * slot; PIC_ERR_CAPACITY when no slot is free.  The slab starts at step 0
+ * with zero fields and photons. */
+pic_status pic_batch_admit(pic_ctx *c, const pic_grid *g, const pic_species *s, const pic_pulse *p,
+                           int64_t n_e, const double *eX, const double *eY, const float *eu,
+                           const float *ew, const uint64_t *eid,
+                           int64_t n_i, const double *iX, const double *iY, const float *iu,
+                           const float *izf, const int32_t *iZ, const int32_t *inK,
+                           const uint32_t *iid, int *slot_out);
+
+/* Retire an active slot: its particles are dropped by the next step, after
+ * which the slot is free again. */
+pic_status pic_batch_retire(pic_ctx *c, int slot);
+
+/* Slot state (0 free, 1 active, 2 retired, not yet emptied) and its step
+ * count (synchronizes when step != NULL). */
+pic_status pic_batch_slot(pic_ctx *c, int slot, int *state, uint32_t *step);
+
+/* Per-slot versions of pic_diagnostics, pic_counts, pic_get_electrons and
+ * pic_get_ions (positions in the slab's own cell units). */
+pic_status pic_batch_diagnostics(pic_ctx *c, int slot, pic_diag *out);
+pic_status pic_batch_counts(pic_ctx *c, int slot, int64_t *n_e, int64_t *n_i);
+pic_status pic_batch_get_electrons(pic_ctx *c, int slot, double *X, double *Y, float *u, float *w,
+                                   uint64_t *id);
+pic_status pic_batch_get_ions(pic_ctx *c, int slot, double *X, double *Y, float *u, float *zfrac,
+                              int32_t *Z, int32_t *nK, uint32_t *id);
+
 /* Kernel launches issued by the last pic_step call (for accounting). */
 int64_t pic_launch_count(const pic_ctx *c);
 

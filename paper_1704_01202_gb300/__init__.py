@@ -37,7 +37,9 @@ ABI_FUNCTIONS = ["pic_required_bytes", "pic_init", "pic_source", "pic_load_elect
                  "pic_set_photons", "pic_set_fields", "pic_step", "pic_sync", "pic_diagnostics",
                  "pic_counts", "pic_get_electrons", "pic_get_ions", "pic_get_photons", "pic_get_fields",
                  "pic_get_current", "pic_launch_count", "pic_free", "pic_last_error", "pic_philox_check",
-                 "pic_timing"]
+                 "pic_timing", "pic_batch_required_bytes", "pic_batch_init", "pic_batch_admit",
+                 "pic_batch_retire", "pic_batch_slot", "pic_batch_diagnostics", "pic_batch_counts",
+                 "pic_batch_get_electrons", "pic_batch_get_ions"]
 
 
 def _sources():
@@ -140,8 +142,24 @@ def lib():
             L.pic_philox_check.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
                                            C.POINTER(C.c_uint32), C.c_int]
             L.pic_timing.argtypes = [_P, C.c_int, _D, C.POINTER(C.c_int64)]
+            L.pic_batch_required_bytes.restype = C.c_size_t
+            L.pic_batch_required_bytes.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
+            L.pic_batch_init.argtypes = [C.POINTER(_P), C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(Tables),
+                                         _P, C.c_size_t, _P]
+            L.pic_batch_admit.argtypes = [_P, C.POINTER(Grid), C.POINTER(Species), C.POINTER(Pulse),
+                                          C.c_int64, _D, _D, _F, _F, C.POINTER(C.c_uint64),
+                                          C.c_int64, _D, _D, _F, _F, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                          C.POINTER(C.c_uint32), C.POINTER(C.c_int)]
+            L.pic_batch_retire.argtypes = [_P, C.c_int]
+            L.pic_batch_slot.argtypes = [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_uint32)]
+            L.pic_batch_diagnostics.argtypes = [_P, C.c_int, C.POINTER(Diag)]
+            L.pic_batch_counts.argtypes = [_P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+            L.pic_batch_get_electrons.argtypes = [_P, C.c_int, _D, _D, _F, _F, C.POINTER(C.c_uint64)]
+            L.pic_batch_get_ions.argtypes = [_P, C.c_int, _D, _D, _F, _F, C.POINTER(C.c_int32),
+                                             C.POINTER(C.c_int32), C.POINTER(C.c_uint32)]
             for name in ABI_FUNCTIONS:
-                if name not in ("pic_required_bytes", "pic_launch_count", "pic_last_error"):
+                if name not in ("pic_required_bytes", "pic_launch_count", "pic_last_error",
+                                "pic_batch_required_bytes"):
                     getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -195,15 +213,12 @@ class Slab:
                  use_torch_arena: bool = True, stream=None):
         self.L = lib()
         self.cfg = cfg
-        self.grid = Grid(nx=cfg.nx, ny=cfg.ny, dx_nm=cfg.dx_nm, dy_nm=cfg.dy_nm, dt_fs=cfg.dt_fs,
-                         rad_every=cfg.rad_every, seed=cfg.seed, cfl=cfg.cfl)
+        self.grid = _grid(cfg)
         if cap_e <= 0 or cap_i <= 0:
             ce, ci = default_capacity(cfg.ncell * cfg.ppc_e, cfg.ncell * cfg.ppc_i, cfg.Z_init)
             cap_e = cap_e if cap_e > 0 else ce
             cap_i = cap_i if cap_i > 0 else ci
-        self.species = Species(n_ref_cm3=cfg.n_ref_cm3, w_ion=cfg.w_ion, m_ion_me=cfg.m_ion_me,
-                               E_bulk_eV=cfg.E_bulk_eV, ipd_model=cfg.ipd_model, coulomb_log=cfg.coulomb_log,
-                               flags=cfg.flags, cap_e=cap_e, cap_i=cap_i)
+        self.species = _species(cfg, cap_e, cap_i)
         self._t, self._keep = _tables(tables)
         self.arena = None
         arena_ptr, arena_bytes = None, 0
@@ -247,22 +262,10 @@ class Slab:
         self.n_bins = pl.n_bins
 
     def load(self, st):
-        ex = np.ascontiguousarray(st.eX, dtype=np.float64)
-        ey = np.ascontiguousarray(st.eY, dtype=np.float64)
-        eu = np.ascontiguousarray(st.eu, dtype=np.float32)
-        ew = np.ascontiguousarray(st.ew, dtype=np.float32)
-        eid = np.ascontiguousarray(st.eid, dtype=np.uint64)
-        self._check(self.L.pic_load_electrons(self.h, ex.size, _p(ex), _p(ey), _p(eu, C.c_float), _p(ew, C.c_float),
-                                              _p(eid, C.c_uint64)), "pic_load_electrons")
-        ix = np.ascontiguousarray(st.iX, dtype=np.float64)
-        iy = np.ascontiguousarray(st.iY, dtype=np.float64)
-        iu = np.ascontiguousarray(st.iu, dtype=np.float32)
-        zf = np.ascontiguousarray(st.izf, dtype=np.float32)
-        Z = np.ascontiguousarray(st.iZ, dtype=np.int32)
-        nK = np.ascontiguousarray(st.inK, dtype=np.int32)
-        iid = np.ascontiguousarray(st.iid, dtype=np.uint32)
-        self._check(self.L.pic_load_ions(self.h, ix.size, _p(ix), _p(iy), _p(iu, C.c_float), _p(zf, C.c_float),
-                                         _p(Z, C.c_int32), _p(nK, C.c_int32), _p(iid, C.c_uint32)), "pic_load_ions")
+        _ek, e = _electron_args(st)
+        self._check(self.L.pic_load_electrons(self.h, *e), "pic_load_electrons")
+        _ik, i = _ion_args(st)
+        self._check(self.L.pic_load_ions(self.h, *i), "pic_load_ions")
 
     def step(self, n=1):
         self._check(self.L.pic_step(self.h, n), "pic_step")
@@ -293,25 +296,15 @@ class Slab:
 
     def electrons(self):
         n, _ = self.counts()
-        X, Y = np.zeros(n), np.zeros(n)
-        u = np.zeros((n, 3), dtype=np.float32)
-        w = np.zeros(n, dtype=np.float32)
-        i = np.zeros(n, dtype=np.uint64)
-        self._check(self.L.pic_get_electrons(self.h, _p(X), _p(Y), _p(u, C.c_float), _p(w, C.c_float),
-                                             _p(i, C.c_uint64)), "pic_get_electrons")
-        return dict(X=X, Y=Y, u=u, w=w, id=i)
+        d, args = _electron_out(n)
+        self._check(self.L.pic_get_electrons(self.h, *args), "pic_get_electrons")
+        return d
 
     def ions(self):
         _, n = self.counts()
-        X, Y = np.zeros(n), np.zeros(n)
-        u = np.zeros((n, 3), dtype=np.float32)
-        zf = np.zeros(n, dtype=np.float32)
-        Z = np.zeros(n, dtype=np.int32)
-        nK = np.zeros(n, dtype=np.int32)
-        i = np.zeros(n, dtype=np.uint32)
-        self._check(self.L.pic_get_ions(self.h, _p(X), _p(Y), _p(u, C.c_float), _p(zf, C.c_float),
-                                        _p(Z, C.c_int32), _p(nK, C.c_int32), _p(i, C.c_uint32)), "pic_get_ions")
-        return dict(X=X, Y=Y, u=u, zf=zf, Z=Z, nK=nK, id=i)
+        d, args = _ion_out(n)
+        self._check(self.L.pic_get_ions(self.h, *args), "pic_get_ions")
+        return d
 
     def set_photons(self, ph):
         a = np.ascontiguousarray(ph, dtype=np.float64)
@@ -337,15 +330,139 @@ class Slab:
         return a
 
     def diagnostics(self, n_E=64, E_max=1e4):
-        csd = np.zeros(NZ)
-        eedf = np.zeros(n_E)
-        d = Diag(csd=_p(csd), eedf=_p(eedf), n_E=n_E, E_max_eV=E_max)
+        d, finish = _diag_out(n_E, E_max)
         self._check(self.L.pic_diagnostics(self.h, C.byref(d)), "pic_diagnostics")
+        return finish()
+
+
+def _electron_args(st):
+    """Contiguous copies of a particle state's electrons and the (n, X, Y, u,
+    w, id) arguments pointing into them (keep the copies alive for the call)."""
+    a = [np.ascontiguousarray(st.eX, dtype=np.float64), np.ascontiguousarray(st.eY, dtype=np.float64),
+         np.ascontiguousarray(st.eu, dtype=np.float32), np.ascontiguousarray(st.ew, dtype=np.float32),
+         np.ascontiguousarray(st.eid, dtype=np.uint64)]
+    return a, (a[0].size, _p(a[0]), _p(a[1]), _p(a[2], C.c_float), _p(a[3], C.c_float), _p(a[4], C.c_uint64))
+
+
+def _ion_args(st):
+    a = [np.ascontiguousarray(st.iX, dtype=np.float64), np.ascontiguousarray(st.iY, dtype=np.float64),
+         np.ascontiguousarray(st.iu, dtype=np.float32), np.ascontiguousarray(st.izf, dtype=np.float32),
+         np.ascontiguousarray(st.iZ, dtype=np.int32), np.ascontiguousarray(st.inK, dtype=np.int32),
+         np.ascontiguousarray(st.iid, dtype=np.uint32)]
+    return a, (a[0].size, _p(a[0]), _p(a[1]), _p(a[2], C.c_float), _p(a[3], C.c_float), _p(a[4], C.c_int32),
+            _p(a[5], C.c_int32), _p(a[6], C.c_uint32))
+
+
+def _electron_out(n):
+    d = dict(X=np.zeros(n), Y=np.zeros(n), u=np.zeros((n, 3), dtype=np.float32), w=np.zeros(n, dtype=np.float32),
+             id=np.zeros(n, dtype=np.uint64))
+    return d, (_p(d["X"]), _p(d["Y"]), _p(d["u"], C.c_float), _p(d["w"], C.c_float), _p(d["id"], C.c_uint64))
+
+
+def _ion_out(n):
+    d = dict(X=np.zeros(n), Y=np.zeros(n), u=np.zeros((n, 3), dtype=np.float32), zf=np.zeros(n, dtype=np.float32),
+             Z=np.zeros(n, dtype=np.int32), nK=np.zeros(n, dtype=np.int32), id=np.zeros(n, dtype=np.uint32))
+    return d, (_p(d["X"]), _p(d["Y"]), _p(d["u"], C.c_float), _p(d["zf"], C.c_float), _p(d["Z"], C.c_int32),
+               _p(d["nK"], C.c_int32), _p(d["id"], C.c_uint32))
+
+
+def _diag_out(n_E, E_max):
+    csd = np.zeros(NZ)
+    eedf = np.zeros(n_E)
+    d = Diag(csd=_p(csd), eedf=_p(eedf), n_E=n_E, E_max_eV=E_max)
+
+    def finish():
         out = {k: getattr(d, k) for k, _ in Diag._fields_ if k not in ("csd", "eedf", "counts")}
         out["csd"] = csd
         out["eedf"] = eedf
         out["counts"] = dict(zip(COUNT_NAMES, (int(x) for x in d.counts)))
         return out
+    return d, finish
+
+
+def _grid(cfg) -> Grid:
+    return Grid(nx=cfg.nx, ny=cfg.ny, dx_nm=cfg.dx_nm, dy_nm=cfg.dy_nm, dt_fs=cfg.dt_fs,
+                rad_every=cfg.rad_every, seed=cfg.seed, cfl=cfg.cfl)
+
+
+def _species(cfg, cap_e=0, cap_i=0) -> Species:
+    return Species(n_ref_cm3=cfg.n_ref_cm3, w_ion=cfg.w_ion, m_ion_me=cfg.m_ion_me,
+                   E_bulk_eV=cfg.E_bulk_eV, ipd_model=cfg.ipd_model, coulomb_log=cfg.coulomb_log,
+                   flags=cfg.flags, cap_e=cap_e, cap_i=cap_i)
+
+
+class Batch:
+    """Many independent 1D slabs stepped together (one launch of each kernel
+    per step), admitted and retired between steps."""
+
+    def __init__(self, tables: dict, max_slabs: int, slot_cells: int, cap_e: int, cap_i: int, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise PicError("no CUDA device")
+        self.L = lib()
+        self.max_slabs, self.slot_cells = max_slabs, slot_cells
+        self._t, self._keep = _tables(tables)
+        nbytes = self.L.pic_batch_required_bytes(max_slabs, slot_cells, cap_e, cap_i)
+        if nbytes == 0:
+            raise PicError("pic_batch_required_bytes: invalid sizes")
+        self.arena = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.h = C.c_void_p()
+        st = self.L.pic_batch_init(C.byref(self.h), max_slabs, slot_cells, cap_e, cap_i, C.byref(self._t),
+                                   self.arena.data_ptr(), nbytes, s.cuda_stream)
+        if st != 0:
+            raise PicError(f"pic_batch_init: {STATUS.get(st, st)}")
+        self.cfgs = {}
+
+    _check = Slab._check
+    close = Slab.close
+    __del__ = Slab.__del__
+    step = Slab.step
+    sync = Slab.sync
+    timing = Slab.timing
+    launches = Slab.launches
+
+    def admit(self, cfg, st, pulse=None) -> int:
+        g, sp = _grid(cfg), _species(cfg)
+        pl = C.byref(pulse_struct(pulse)) if pulse is not None else None
+        slot = C.c_int(-1)
+        _ek, e = _electron_args(st)
+        _ik, i = _ion_args(st)
+        self._check(self.L.pic_batch_admit(self.h, C.byref(g), C.byref(sp), pl, *e, *i, C.byref(slot)),
+                    "pic_batch_admit")
+        self.cfgs[slot.value] = cfg
+        return slot.value
+
+    def retire(self, slot: int):
+        self._check(self.L.pic_batch_retire(self.h, slot), "pic_batch_retire")
+        self.cfgs.pop(slot, None)
+
+    def slot(self, slot: int):
+        state, step = C.c_int(), C.c_uint32()
+        self._check(self.L.pic_batch_slot(self.h, slot, C.byref(state), C.byref(step)), "pic_batch_slot")
+        return state.value, step.value
+
+    def counts(self, slot: int):
+        ne, ni = C.c_int64(), C.c_int64()
+        self._check(self.L.pic_batch_counts(self.h, slot, C.byref(ne), C.byref(ni)), "pic_batch_counts")
+        return ne.value, ni.value
+
+    def electrons(self, slot: int):
+        n, _ = self.counts(slot)
+        d, args = _electron_out(n)
+        self._check(self.L.pic_batch_get_electrons(self.h, slot, *args), "pic_batch_get_electrons")
+        return d
+
+    def ions(self, slot: int):
+        _, n = self.counts(slot)
+        d, args = _ion_out(n)
+        self._check(self.L.pic_batch_get_ions(self.h, slot, *args), "pic_batch_get_ions")
+        return d
+
+    def diagnostics(self, slot: int, n_E=64, E_max=1e4):
+        d, finish = _diag_out(n_E, E_max)
+        self._check(self.L.pic_batch_diagnostics(self.h, slot, C.byref(d)), "pic_batch_diagnostics")
+        return finish()
 
 
 def philox_check(ctr: np.ndarray, key) -> np.ndarray:

@@ -1,9 +1,17 @@
 // Host side of the C ABI declared in include/pic.h: the context, its device
 // arena, the per-step launch sequence and the host <-> device copies.
+//
+// A context holds nslot slots.  Slot k owns cells [k*slot_cells,
+// (k+1)*slot_cells) and grid points [k*slot_pts, (k+1)*slot_pts) of one
+// global numbering, so each kernel runs once per step for every slab.
+// pic_init makes a one-slot context (1D or 2D); pic_batch_init a context of
+// 1D slots into which slabs are admitted, and from which they are retired,
+// between steps.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -42,10 +50,18 @@ struct pic_ctx {
     size_t arena_bytes = 0, used = 0;
     std::string err;
 
-    pic_grid grid{};
-    pic_species sp{};
-    SlabDev slab{};
-    int ncell = 0, npts = 0, nblk = 0;
+    bool batch = false;
+    int nslot = 1, slot_cells = 0, slot_pts = 0, slot_rows = 1;
+    std::vector<SlabDev> slabs;          // host copy of every slot's description
+    std::vector<int> slot_state;         // 0 free, 1 active, 2 retired (emptied by the next step)
+    std::vector<pic_grid> grids;         // grid of each slot as given
+    struct Pending {                     // admitted, particles not yet on the device
+        int slot;
+        std::vector<float4> e0, e1, i0, i1;
+        std::vector<int> ek, ik;
+    };
+    std::vector<Pending> pending;
+    int ncell = 0, npts = 0, nblk = 0, nrows = 0, max_row_nx = 0;
     int cap_e = 0, cap_i = 0;
 
     float4 *eA0, *eA1, *eB0, *eB1;
@@ -55,9 +71,9 @@ struct pic_ctx {
     int cur = 0;
     int *cnt_e, *cnt_i, *fill_e, *fill_i, *bsum_e, *bsum_i;
     int *counters, *ovf_list, *cell_slab, *pt_slab, *row_slab, *row_idx;
-    SlabDev *d_slab;
-    unsigned *d_steps;
-    SlabTally *d_tally;
+    SlabDev *d_slab;                     // [nslot]
+    unsigned *d_steps;                   // [nslot]
+    SlabTally *d_tally;                  // [nslot]
     Tables *d_tab;
     EosTable *d_eos;
     float *E[2], *B;
@@ -71,8 +87,6 @@ struct pic_ctx {
     int nsm = 0, grid_main = 0, grid_big = 0, grid_push = 0;
     int64_t launches = 0;
     bool loaded_e = false, loaded_i = false;
-    unsigned host_step = 0;
-    double fe_factor = 0.0;
     std::vector<double> hv_tab, sigma;   // host copy of the photoionization table
     bool timing = false;
     std::vector<cudaEvent_t> ev;         // NEV events per recorded step
@@ -108,17 +122,18 @@ T *carve_arena(pic_ctx *c, size_t count)
     return p;
 }
 
-size_t arena_need(int ncell, int npts, int nblk, int cap_e, int cap_i)
+size_t arena_need(int ncell, int npts, int nblk, int cap_e, int cap_i, int nslot, int nrows)
 {
     size_t b = 0;
     b += 4 * al((size_t)cap_e * 16) + 2 * al((size_t)cap_e * 4);
     b += 4 * al((size_t)cap_i * 16) + 2 * al((size_t)cap_i * 4);
-    b += 4 * al((size_t)(ncell + 1) * 4) + 4 * al((size_t)ncell * 4) + 2 * al((size_t)nblk * 4);
+    b += 4 * al((size_t)(ncell + 1) * 4) + al((size_t)ncell * 16) + 2 * al((size_t)nblk * 4);
     b += al(NCOUNTERS * 4) + al((size_t)ncell * 4) * 2;
-    b += al(sizeof(SlabDev)) + al(4) + al(sizeof(SlabTally)) + al(sizeof(Tables)) + al(sizeof(EosTable));
+    b += al(sizeof(SlabDev) * (size_t)nslot) + al(4 * (size_t)nslot) + al(sizeof(SlabTally) * (size_t)nslot)
+         + al(sizeof(Tables)) + al(sizeof(EosTable));
     b += 3 * al((size_t)npts * 3 * 4) + al((size_t)npts * 3 * 8) + al((size_t)npts * 4);
-    b += 2 * al((size_t)1 << 20);                        // row lists
-    b += al((size_t)ncell * PIC_MAX_BINS * 8);
+    b += 2 * al((size_t)nrows * 4);
+    b += al((size_t)ncell * PIC_MAX_BINS * sizeof(ph2));
     b += al((4 + NZ + 4096 + 8) * 8);
     return b + 4096;
 }
@@ -228,6 +243,16 @@ cudaEvent_t *timing_slot(pic_ctx *c)
     return p;
 }
 
+// does any active slab have this process switched on
+bool any_active(const pic_ctx *c, unsigned flag, bool need_pulse)
+{
+    for (int k = 0; k < c->nslot; ++k) {
+        const SlabDev &S = c->slabs[k];
+        if (S.active && (S.flags & flag) && (!need_pulse || S.nb > 0)) return true;
+    }
+    return false;
+}
+
 pic_status launch_step(pic_ctx *c)
 {
     cudaStream_t st = c->stream;
@@ -237,9 +262,9 @@ pic_status launch_step(pic_ctx *c)
     CK(cudaMemsetAsync(c->counters, 0, sizeof(int) * 5, st));                      // append, work counters, ovf
     CK(cudaMemsetAsync(c->counters + CNT_MAXE, 0, sizeof(int) * 2, st));
     CK(cudaMemsetAsync(c->J, 0, sizeof(unsigned long long) * 3 * (size_t)c->npts, st));
-    if ((c->slab.flags & PIC_F_PHOTO) && c->slab.nb > 0) {
+    if (any_active(c, PIC_F_PHOTO, true)) {
         MarchArgs m{c->d_slab, c->d_steps, c->row_slab, c->row_idx, c->photons, c->d_tally};
-        k_march<<<c->grid.ny, 256, (size_t)c->grid.nx * 8, st>>>(m);
+        k_march<<<c->nrows, 256, (size_t)c->max_row_nx * 8, st>>>(m);
         ++c->launches;
     }
     if (ev) CK(cudaEventRecord(ev[1], st));
@@ -275,11 +300,14 @@ pic_status launch_step(pic_ctx *c)
     k_scatter<<<sgrid, 256, 0, st>>>(si);
     c->launches += 2;
     if (ev) CK(cudaEventRecord(ev[4], st));
-    if (c->slab.flags & PIC_F_FIELD) {
+    if (any_active(c, PIC_F_FIELD, false)) {
+        int nsub = 1;
+        for (int k = 0; k < c->nslot; ++k)
+            if (c->slabs[k].active && (c->slabs[k].flags & PIC_F_FIELD)) nsub = std::max(nsub, c->slabs[k].nsub);
         FieldArgs f{};
         f.slabs = c->d_slab; f.pt_slab = c->pt_slab; f.npts = c->npts; f.B = c->B; f.J = c->J;
         int fg = std::min((c->npts + 255) / 256, c->nsm * 16);
-        for (int sub = 0; sub < c->slab.nsub; ++sub) {
+        for (int sub = 0; sub < nsub; ++sub) {
             f.sub = sub;
             f.Ein = c->E[c->ecur]; f.Eout = c->E[c->ecur ^ 1];
             k_b_half<<<fg, 256, 0, st>>>(f);
@@ -290,14 +318,13 @@ pic_status launch_step(pic_ctx *c)
             c->launches += 3;
         }
     }
-    k_advance<<<1, 32, 0, st>>>(c->d_steps, 1);
+    k_advance<<<(c->nslot + 127) / 128, 128, 0, st>>>(c->d_steps, c->d_slab, c->nslot);
     ++c->launches;
     CK(cudaGetLastError());
     if (ev) CK(cudaEventRecord(ev[5], st));
     std::swap(c->eA0, c->eB0); std::swap(c->eA1, c->eB1);
     std::swap(c->iA0, c->iB0); std::swap(c->iA1, c->iB1);
     c->cur = nxt;
-    ++c->host_step;
     return PIC_OK;
 }
 
@@ -313,41 +340,107 @@ pic_status read_device_error(pic_ctx *c)
     return PIC_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-size_t pic_required_bytes(const pic_grid *g, const pic_species *s, int n_e_cap, int n_i_cap)
+bool valid_grid(const pic_grid *g)
 {
-    if (!g || !s || g->nx <= 0 || g->ny <= 0) return 0;
-    int ncell = g->nx * g->ny, npts = (g->nx + 1) * g->ny;
-    int nblk = (ncell + SCAN_TILE - 1) / SCAN_TILE;
-    int ce = n_e_cap > 0 ? n_e_cap : s->cap_e, ci = n_i_cap > 0 ? n_i_cap : s->cap_i;
-    return arena_need(ncell, npts, nblk, ce, ci);
+    return g && g->nx >= 2 && g->ny >= 1 && g->nx <= 8192 && g->dx_nm > 0 && g->dy_nm > 0 && g->dt_fs > 0 &&
+           g->cfl > 0 && (long long)g->nx * g->ny <= (1LL << 30);
 }
 
-pic_status pic_init(pic_ctx **out, const pic_grid *g, const pic_species *s, const pic_tables *t, void *arena,
-                    size_t arena_bytes, void *stream)
+bool valid_species(const pic_species *s)
 {
-    if (!out || !g || !s || !t) return PIC_ERR_ARG;
-    *out = nullptr;
-    if (g->nx < 2 || g->ny < 1 || g->dx_nm <= 0 || g->dy_nm <= 0 || g->dt_fs <= 0 || g->cfl <= 0)
-        return PIC_ERR_ARG;
-    if ((long long)g->nx * g->ny > (1LL << 30)) return PIC_ERR_ARG;
-    if (s->cap_e <= 0 || s->cap_i <= 0 || s->w_ion <= 0 || s->m_ion_me <= 0 || s->n_ref_cm3 <= 0) return PIC_ERR_ARG;
-    if (g->nx > 8192) return PIC_ERR_ARG;
+    return s && s->w_ion > 0 && s->m_ion_me > 0 && s->n_ref_cm3 > 0 && s->ipd_model >= 0 && s->ipd_model <= 2;
+}
+
+bool valid_pulse(const pic_pulse *p)
+{
+    return p && p->n_bins >= 1 && p->n_bins <= PIC_MAX_BINS && p->hv_eV > 0 && p->fwhm_fs >= 0 &&
+           p->bandwidth_eV >= 0;
+}
+
+// description of the slab of slot k, inactive until it is switched on
+SlabDev make_slab(const pic_ctx *c, int k, const pic_grid *g, const pic_species *s)
+{
+    SlabDev S{};
+    S.active = 0;
+    S.nx = g->nx; S.ny = g->ny;
+    S.cell0 = k * c->slot_cells; S.ncell = g->nx * g->ny;
+    S.fld_off = k * c->slot_pts;
+    S.ph_off = k * c->slot_cells * PIC_MAX_BINS;
+    S.nb = 0;
+    S.rad_every = g->rad_every; S.flags = s->flags; S.ipd = s->ipd_model; S.shape = 0;
+    S.dx = (float)g->dx_nm; S.dy = (float)g->dy_nm; S.dt = (float)g->dt_fs;
+    S.w_ion = (float)s->w_ion; S.m_ion = (float)s->m_ion_me; S.E_bulk = (float)s->E_bulk_eV;
+    S.coulomb_log = (float)s->coulomb_log;
+    S.n_ref = s->n_ref_cm3;
+    const double E0 = kMeKg * kCms / (kQe * 1e-15);
+    S.kappa_J = kQe * s->n_ref_cm3 * 1e6 * 1e-9 / (kEps0 * E0);
+    S.nref_f = (float)S.n_ref;
+    S.kappa_f = (float)S.kappa_J;
+    double inv = 1.0 / (g->dx_nm * g->dx_nm) + (g->ny > 1 ? 1.0 / (g->dy_nm * g->dy_nm) : 0.0);
+    S.nsub = std::max(1, (int)std::ceil(kCnmPerFs * g->dt_fs * std::sqrt(inv) / g->cfl));
+    double dtf = g->dt_fs / S.nsub;
+    S.mur = (float)((kCnmPerFs * dtf - g->dx_nm) / (kCnmPerFs * dtf + g->dx_nm));
+    S.seed = g->seed;
+    return S;
+}
+
+void set_pulse(const pic_ctx *c, SlabDev &S, const pic_pulse *p)
+{
+    S.nb = p->n_bins;
+    S.shape = p->shape;
+    S.I_peak = p->I_peak_Wcm2; S.fwhm = p->fwhm_fs; S.t_peak = p->t_peak_fs; S.spot_sigma = p->spot_sigma_nm;
+    S.bin_hw = (float)(0.5 * p->bandwidth_eV / p->n_bins);
+    for (int b = 0; b < PIC_MAX_BINS; ++b) {
+        double hv = b < p->n_bins ? p->hv_eV + p->bandwidth_eV * ((b + 0.5) / p->n_bins - 0.5) : 0.0;
+        S.hv_b[b] = (float)hv;
+        for (int q = 0; q < NS; ++q) S.sig_b[q][b] = b < p->n_bins ? (float)sigma_table(c, q, hv) : 0.0f;
+    }
+}
+
+// zero the fields, photons, tallies and step counter of slot k and upload
+// its description
+pic_status reset_slot(pic_ctx *c, int k)
+{
+    cudaStream_t st = c->stream;
+    const SlabDev &S = c->slabs[k];
+    for (int comp = 0; comp < 3; ++comp) {
+        size_t o = (size_t)comp * c->npts + S.fld_off;
+        CK(cudaMemsetAsync(c->E[0] + o, 0, sizeof(float) * c->slot_pts, st));
+        CK(cudaMemsetAsync(c->E[1] + o, 0, sizeof(float) * c->slot_pts, st));
+        CK(cudaMemsetAsync(c->B + o, 0, sizeof(float) * c->slot_pts, st));
+    }
+    CK(cudaMemsetAsync(c->photons + S.ph_off, 0, sizeof(ph2) * (size_t)c->slot_cells * PIC_MAX_BINS, st));
+    CK(cudaMemcpyAsync(c->d_slab + k, &S, sizeof(SlabDev), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(c->d_steps + k, 0, sizeof(unsigned), st));
+    CK(cudaMemsetAsync(c->d_tally + k, 0, sizeof(SlabTally), st));
+    CK(cudaStreamSynchronize(st));      // the host copy of S may change after this call
+    return PIC_OK;
+}
+
+// a context of nslot empty slots
+pic_status ctx_create(pic_ctx **out, int nslot, int slot_cells, int slot_pts, int slot_rows, int max_row_nx,
+                      int cap_e, int cap_i, const pic_tables *t, void *arena, size_t arena_bytes, void *stream)
+{
     if (t->n_hv < 2 || !t->hv_tab || !t->sigma_photo || t->n_T < 1 || t->n_n < 1 || t->n_T > EOS_MAX_T ||
         t->n_n > EOS_MAX_N || !t->eos_T || !t->eos_n || !t->eos_Zbar)
         return PIC_ERR_TABLE;
+    if ((long long)nslot * slot_cells > (1LL << 30) || (long long)nslot * slot_pts > (1LL << 30)) return PIC_ERR_ARG;
     pic_ctx *c = new pic_ctx();
     c->stream = (cudaStream_t)stream;
-    c->grid = *g;
-    c->sp = *s;
-    c->ncell = g->nx * g->ny;
-    c->npts = (g->nx + 1) * g->ny;
+    c->nslot = nslot;
+    c->slot_cells = slot_cells;
+    c->slot_pts = slot_pts;
+    c->slot_rows = slot_rows;
+    c->ncell = nslot * slot_cells;
+    c->npts = nslot * slot_pts;
+    c->nrows = nslot * slot_rows;
+    c->max_row_nx = max_row_nx;
     c->nblk = (c->ncell + SCAN_TILE - 1) / SCAN_TILE;
-    c->cap_e = s->cap_e;
-    c->cap_i = s->cap_i;
+    c->cap_e = cap_e;
+    c->cap_i = cap_i;
+    c->slabs.assign(nslot, SlabDev{});
+    c->slot_state.assign(nslot, 0);
+    c->grids.assign(nslot, pic_grid{});
     c->hv_tab.assign(t->hv_tab, t->hv_tab + t->n_hv);
     c->sigma.assign(t->sigma_photo, t->sigma_photo + (size_t)NS * t->n_hv);
     int dev = 0;
@@ -355,7 +448,7 @@ pic_status pic_init(pic_ctx **out, const pic_grid *g, const pic_species *s, cons
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) { pic_status r = cuda_fail(c, e, "device query"); delete c; return r; }
 
-    size_t need = arena_need(c->ncell, c->npts, c->nblk, c->cap_e, c->cap_i);
+    size_t need = arena_need(c->ncell, c->npts, c->nblk, cap_e, cap_i, nslot, c->nrows);
     if (arena) {
         if (arena_bytes < need) { delete c; return PIC_ERR_OOM; }
         c->arena = (char *)arena;
@@ -366,25 +459,24 @@ pic_status pic_init(pic_ctx **out, const pic_grid *g, const pic_species *s, cons
         c->own_arena = true;
         c->arena_bytes = need;
     }
-    c->eA0 = carve_arena<float4>(c, c->cap_e); c->eA1 = carve_arena<float4>(c, c->cap_e);
-    c->eB0 = carve_arena<float4>(c, c->cap_e); c->eB1 = carve_arena<float4>(c, c->cap_e);
-    c->ekey = carve_arena<int>(c, c->cap_e);
-    c->eord = carve_arena<int>(c, c->cap_e);
-    c->iA0 = carve_arena<float4>(c, c->cap_i); c->iA1 = carve_arena<float4>(c, c->cap_i);
-    c->iB0 = carve_arena<float4>(c, c->cap_i); c->iB1 = carve_arena<float4>(c, c->cap_i);
-    c->ikey = carve_arena<int>(c, c->cap_i);
-    c->iord = carve_arena<int>(c, c->cap_i);
+    c->eA0 = carve_arena<float4>(c, cap_e); c->eA1 = carve_arena<float4>(c, cap_e);
+    c->eB0 = carve_arena<float4>(c, cap_e); c->eB1 = carve_arena<float4>(c, cap_e);
+    c->ekey = carve_arena<int>(c, cap_e);
+    c->eord = carve_arena<int>(c, cap_e);
+    c->iA0 = carve_arena<float4>(c, cap_i); c->iA1 = carve_arena<float4>(c, cap_i);
+    c->iB0 = carve_arena<float4>(c, cap_i); c->iB1 = carve_arena<float4>(c, cap_i);
+    c->ikey = carve_arena<int>(c, cap_i);
+    c->iord = carve_arena<int>(c, cap_i);
     for (int k = 0; k < 2; ++k) { c->csE[k] = carve_arena<int>(c, c->ncell + 1); c->csI[k] = carve_arena<int>(c, c->ncell + 1); }
     c->cnt_e = carve_arena<int>(c, 4 * (size_t)c->ncell);
     c->cnt_i = c->cnt_e + c->ncell; c->fill_e = c->cnt_i + c->ncell; c->fill_i = c->fill_e + c->ncell;
-    carve_arena<int>(c, 0);
     c->bsum_e = carve_arena<int>(c, c->nblk); c->bsum_i = carve_arena<int>(c, c->nblk);
     c->counters = carve_arena<int>(c, NCOUNTERS);
     c->ovf_list = carve_arena<int>(c, c->ncell);
     c->cell_slab = carve_arena<int>(c, c->ncell);
-    c->d_slab = carve_arena<SlabDev>(c, 1);
-    c->d_steps = carve_arena<unsigned>(c, 1);
-    c->d_tally = carve_arena<SlabTally>(c, 1);
+    c->d_slab = carve_arena<SlabDev>(c, nslot);
+    c->d_steps = carve_arena<unsigned>(c, nslot);
+    c->d_tally = carve_arena<SlabTally>(c, nslot);
     c->d_tab = carve_arena<Tables>(c, 1);
     c->d_eos = carve_arena<EosTable>(c, 1);
     c->E[0] = carve_arena<float>(c, 3 * (size_t)c->npts);
@@ -392,30 +484,11 @@ pic_status pic_init(pic_ctx **out, const pic_grid *g, const pic_species *s, cons
     c->B = carve_arena<float>(c, 3 * (size_t)c->npts);
     c->J = carve_arena<unsigned long long>(c, 3 * (size_t)c->npts);
     c->pt_slab = carve_arena<int>(c, c->npts);
-    c->row_slab = carve_arena<int>(c, 1 << 18);
-    c->row_idx = carve_arena<int>(c, 1 << 18);
+    c->row_slab = carve_arena<int>(c, c->nrows);
+    c->row_idx = carve_arena<int>(c, c->nrows);
     c->photons = carve_arena<ph2>(c, (size_t)c->ncell * PIC_MAX_BINS);
     c->diag_buf = carve_arena<double>(c, 4 + NZ + 4096 + 8);
     if (!c->diag_buf) { pic_free(c); return PIC_ERR_OOM; }
-
-    // slab description
-    SlabDev &S = c->slab;
-    S.nx = g->nx; S.ny = g->ny; S.cell0 = 0; S.ncell = c->ncell; S.fld_off = 0; S.ph_off = 0; S.nb = 0;
-    S.rad_every = g->rad_every; S.flags = s->flags; S.ipd = s->ipd_model; S.shape = 0;
-    S.dx = (float)g->dx_nm; S.dy = (float)g->dy_nm; S.dt = (float)g->dt_fs;
-    S.w_ion = (float)s->w_ion; S.m_ion = (float)s->m_ion_me; S.E_bulk = (float)s->E_bulk_eV;
-    S.coulomb_log = (float)s->coulomb_log;
-    S.n_ref = s->n_ref_cm3;
-    const double E0 = kMeKg * kCms / (kQe * 1e-15);
-    S.kappa_J = kQe * s->n_ref_cm3 * 1e6 * 1e-9 / (kEps0 * E0);
-    S.nref_f = (float)S.n_ref;
-    S.kappa_f = (float)S.kappa_J;
-    c->fe_factor = kEps0 * E0 * E0 / (2.0 * s->n_ref_cm3 * 1e6 * kQe);
-    double inv = 1.0 / (g->dx_nm * g->dx_nm) + (g->ny > 1 ? 1.0 / (g->dy_nm * g->dy_nm) : 0.0);
-    S.nsub = std::max(1, (int)std::ceil(kCnmPerFs * g->dt_fs * std::sqrt(inv) / g->cfl));
-    double dtf = g->dt_fs / S.nsub;
-    S.mur = (float)((kCnmPerFs * dtf - g->dx_nm) / (kCnmPerFs * dtf + g->dx_nm));
-    S.seed = g->seed;
 
     Tables T{};
     for (int q = 0; q < NS; ++q) { T.lotz_a[q] = (float)t->lotz_a[q]; T.lotz_b[q] = (float)t->lotz_b[q]; T.lotz_c[q] = (float)t->lotz_c[q]; }
@@ -424,81 +497,91 @@ pic_status pic_init(pic_ctx **out, const pic_grid *g, const pic_species *s, cons
         for (int k = 0; k < 2; ++k) { T.tauK[z][k] = (float)t->tauK[z][k]; T.omegaK[z][k] = (float)t->omegaK[z][k]; }
         T.E_Ka[z] = (float)t->E_Kalpha[z];
     }
-    EosTable *eos = new EosTable();
-    eos->n_T = t->n_T; eos->n_n = t->n_n;
-    for (int k = 0; k < t->n_T; ++k) eos->T[k] = (float)t->eos_T[k];
-    for (int k = 0; k < t->n_n; ++k) eos->n[k] = (float)t->eos_n[k];
+    std::vector<EosTable> eos(1);
+    eos[0].n_T = t->n_T; eos[0].n_n = t->n_n;
+    for (int k = 0; k < t->n_T; ++k) eos[0].T[k] = (float)t->eos_T[k];
+    for (int k = 0; k < t->n_n; ++k) eos[0].n[k] = (float)t->eos_n[k];
     for (int a = 0; a < t->n_n; ++a)
-        for (int b = 0; b < t->n_T; ++b) eos->Z[a * t->n_T + b] = (float)t->eos_Zbar[(size_t)a * t->n_T + b];
-    std::vector<int> rows(g->ny);
-    for (int k = 0; k < g->ny; ++k) rows[k] = k;
-    std::vector<int> zeros(g->ny, 0);
-    // the context keeps the table copies alive on the host until the copies finish
-    pic_status rs = PIC_OK;
+        for (int b = 0; b < t->n_T; ++b) eos[0].Z[a * t->n_T + b] = (float)t->eos_Zbar[(size_t)a * t->n_T + b];
+    std::vector<int> cs(c->ncell), ps(c->npts), rs(c->nrows), ri(c->nrows);
+    for (int g = 0; g < c->ncell; ++g) cs[g] = g / slot_cells;
+    for (int p = 0; p < c->npts; ++p) ps[p] = p / slot_pts;
+    for (int q = 0; q < c->nrows; ++q) { rs[q] = q / slot_rows; ri[q] = q % slot_rows; }
+    std::vector<SlabDev> idle(nslot, SlabDev{});
+    cudaStream_t st = c->stream;
     do {
-        cudaStream_t st = c->stream;
         if ((e = cudaMemcpyAsync(c->d_tab, &T, sizeof(Tables), cudaMemcpyHostToDevice, st))) break;
-        if ((e = cudaMemcpyAsync(c->d_eos, eos, sizeof(EosTable), cudaMemcpyHostToDevice, st))) break;
-        if ((e = cudaMemcpyAsync(c->d_slab, &S, sizeof(SlabDev), cudaMemcpyHostToDevice, st))) break;
-        if ((e = cudaMemsetAsync(c->d_steps, 0, sizeof(unsigned), st))) break;
-        if ((e = cudaMemsetAsync(c->d_tally, 0, sizeof(SlabTally), st))) break;
-        if ((e = cudaMemsetAsync(c->cell_slab, 0, sizeof(int) * c->ncell, st))) break;
-        if ((e = cudaMemsetAsync(c->pt_slab, 0, sizeof(int) * c->npts, st))) break;
-        if ((e = cudaMemcpyAsync(c->row_idx, rows.data(), sizeof(int) * g->ny, cudaMemcpyHostToDevice, st))) break;
-        if ((e = cudaMemcpyAsync(c->row_slab, zeros.data(), sizeof(int) * g->ny, cudaMemcpyHostToDevice, st))) break;
+        if ((e = cudaMemcpyAsync(c->d_eos, eos.data(), sizeof(EosTable), cudaMemcpyHostToDevice, st))) break;
+        if ((e = cudaMemcpyAsync(c->d_slab, idle.data(), sizeof(SlabDev) * nslot, cudaMemcpyHostToDevice, st))) break;
+        if ((e = cudaMemsetAsync(c->d_steps, 0, sizeof(unsigned) * nslot, st))) break;
+        if ((e = cudaMemsetAsync(c->d_tally, 0, sizeof(SlabTally) * nslot, st))) break;
+        if ((e = cudaMemcpyAsync(c->cell_slab, cs.data(), sizeof(int) * c->ncell, cudaMemcpyHostToDevice, st))) break;
+        if ((e = cudaMemcpyAsync(c->pt_slab, ps.data(), sizeof(int) * c->npts, cudaMemcpyHostToDevice, st))) break;
+        if ((e = cudaMemcpyAsync(c->row_slab, rs.data(), sizeof(int) * c->nrows, cudaMemcpyHostToDevice, st))) break;
+        if ((e = cudaMemcpyAsync(c->row_idx, ri.data(), sizeof(int) * c->nrows, cudaMemcpyHostToDevice, st))) break;
         if ((e = cudaMemsetAsync(c->E[0], 0, sizeof(float) * 3 * (size_t)c->npts, st))) break;
         if ((e = cudaMemsetAsync(c->E[1], 0, sizeof(float) * 3 * (size_t)c->npts, st))) break;
         if ((e = cudaMemsetAsync(c->B, 0, sizeof(float) * 3 * (size_t)c->npts, st))) break;
+        if ((e = cudaMemsetAsync(c->J, 0, sizeof(unsigned long long) * 3 * (size_t)c->npts, st))) break;
         if ((e = cudaMemsetAsync(c->photons, 0, sizeof(ph2) * (size_t)c->ncell * PIC_MAX_BINS, st))) break;
         if ((e = cudaMemsetAsync(c->counters, 0, sizeof(int) * NCOUNTERS, st))) break;
-        for (int k = 0; k < 2; ++k) {
-            if ((e = cudaMemsetAsync(c->csE[k], 0, sizeof(int) * (c->ncell + 1), st))) break;
-            if ((e = cudaMemsetAsync(c->csI[k], 0, sizeof(int) * (c->ncell + 1), st))) break;
-        }
-        if (e) break;
-        e = cudaStreamSynchronize(st);
+        if ((e = cudaMemsetAsync(c->csE[0], 0, sizeof(int) * (c->ncell + 1), st))) break;
+        if ((e = cudaMemsetAsync(c->csE[1], 0, sizeof(int) * (c->ncell + 1), st))) break;
+        if ((e = cudaMemsetAsync(c->csI[0], 0, sizeof(int) * (c->ncell + 1), st))) break;
+        if ((e = cudaMemsetAsync(c->csI[1], 0, sizeof(int) * (c->ncell + 1), st))) break;
+        e = cudaStreamSynchronize(st);    // the host tables above go out of scope
     } while (0);
-    delete eos;
-    if (e != cudaSuccess) { rs = cuda_fail(c, e, "init copies"); pic_free(c); return rs; }
+    pic_status rc = PIC_OK;
+    if (e != cudaSuccess) { rc = cuda_fail(c, e, "init copies"); pic_free(c); return rc; }
     c->smem_big = warp_mem_bytes(BIG_CE, BIG_CI, 3 * BIG_CI);
     c->grid_big = c->nsm;
     e = cudaFuncSetAttribute(k_march, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8);
-    if (e != cudaSuccess) { rs = cuda_fail(c, e, "march attribute"); pic_free(c); return rs; }
-    if ((rs = configure_cell_launch(c, 128, 32)) != PIC_OK) { pic_free(c); return rs; }
-    {
-        int occ = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_push, 256, 0);
-        if (e != cudaSuccess) { rs = cuda_fail(c, e, "push occupancy"); pic_free(c); return rs; }
-        c->grid_push = std::max(1, occ) * c->nsm;
-    }
+    if (e != cudaSuccess) { rc = cuda_fail(c, e, "march attribute"); pic_free(c); return rc; }
+    if ((rc = configure_cell_launch(c, 128, 32)) != PIC_OK) { pic_free(c); return rc; }
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_push, 256, 0);
+    if (e != cudaSuccess) { rc = cuda_fail(c, e, "push occupancy"); pic_free(c); return rc; }
+    c->grid_push = std::max(1, occ) * c->nsm;
     *out = c;
     return PIC_OK;
 }
 
-pic_status pic_source(pic_ctx *c, const pic_pulse *p)
+// Host records of one slab from positions in cell units of its grid:
+// (xi, eta, ux, uy), (uz, w | zfrac, id, state) and the global cell key.
+pic_status build_records(pic_ctx *c, int slot, const pic_grid *g, bool electrons, int64_t n, const double *X,
+                         const double *Y, const float *u, const float *w_or_zf, const uint64_t *eid,
+                         const int32_t *Z, const int32_t *nK, const uint32_t *iid, std::vector<float4> &p0,
+                         std::vector<float4> &p1, std::vector<int> &key)
 {
-    if (!c || !p) return PIC_ERR_ARG;
-    if (p->n_bins < 1 || p->n_bins > PIC_MAX_BINS || p->hv_eV <= 0 || p->fwhm_fs < 0 || p->bandwidth_eV < 0)
-        return fail(c, PIC_ERR_ARG, "pulse out of range");
-    SlabDev &S = c->slab;
-    S.nb = p->n_bins;
-    S.shape = p->shape;
-    S.I_peak = p->I_peak_Wcm2; S.fwhm = p->fwhm_fs; S.t_peak = p->t_peak_fs; S.spot_sigma = p->spot_sigma_nm;
-    S.bin_hw = (float)(0.5 * p->bandwidth_eV / p->n_bins);
-    for (int b = 0; b < PIC_MAX_BINS; ++b) {
-        double hv = b < p->n_bins ? p->hv_eV + p->bandwidth_eV * ((b + 0.5) / p->n_bins - 0.5) : 0.0;
-        S.hv_b[b] = (float)hv;
-        for (int q = 0; q < NS; ++q) S.sig_b[q][b] = b < p->n_bins ? (float)sigma_table(c, q, hv) : 0.0f;
+    p0.resize(n); p1.resize(n); key.resize(n);
+    const int cell0 = slot * c->slot_cells;
+    for (int64_t k = 0; k < n; ++k) {
+        double fx = std::floor(X[k]), fy = g->ny > 1 ? std::floor(Y[k]) : 0.0;
+        if (!(fx >= 0 && fx < g->nx && fy >= 0 && fy < g->ny))
+            return fail(c, PIC_ERR_ARG, "particle position outside the slab");
+        float xi = (float)(X[k] - fx), eta = g->ny > 1 ? (float)(Y[k] - fy) : (float)Y[k];
+        if (xi >= 1.0f) xi = 0.99999994f;
+        if (g->ny > 1 && eta >= 1.0f) eta = 0.99999994f;
+        key[k] = cell0 + (int)fy * g->nx + (int)fx;
+        p0[k] = make_float4(xi, eta, u[3 * k], u[3 * k + 1]);
+        if (electrons) {
+            uint32_t lo = (uint32_t)eid[k], hi = (uint32_t)(eid[k] >> 32);
+            float flo, fhi;
+            std::memcpy(&flo, &lo, 4); std::memcpy(&fhi, &hi, 4);
+            p1[k] = make_float4(u[3 * k + 2], w_or_zf[k], flo, fhi);
+        } else {
+            if (Z[k] < 0 || Z[k] > ZNUC || nK[k] < 0 || nK[k] > 2) return fail(c, PIC_ERR_ARG, "ion state out of range");
+            int stv = Z[k] | (nK[k] << 8);
+            float fid, fst;
+            std::memcpy(&fid, &iid[k], 4); std::memcpy(&fst, &stv, 4);
+            p1[k] = make_float4(u[3 * k + 2], w_or_zf[k], fid, fst);
+        }
     }
-    CK(cudaMemcpyAsync(c->d_slab, &S, sizeof(SlabDev), cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemsetAsync(c->photons, 0, sizeof(ph2) * (size_t)c->ncell * PIC_MAX_BINS, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
     return PIC_OK;
 }
 
-namespace {
-
-// sort host-built records into the current (A) buffers of one species
+// replace all particles of one species by host records (single-slab load):
+// records into the B buffers, count, scan, scatter into A
 pic_status load_species(pic_ctx *c, bool electrons, int64_t n, const std::vector<float4> &p0,
                         const std::vector<float4> &p1, const std::vector<int> &key)
 {
@@ -527,40 +610,292 @@ pic_status load_species(pic_ctx *c, bool electrons, int64_t n, const std::vector
     return PIC_OK;
 }
 
-pic_status locate(pic_ctx *c, double X, double Y, int &cell, float &xi, float &eta)
+// Admission: host records are appended behind the sorted particles of each
+// species, every sorted particle is keyed by its own cell (-1 when its slab
+// is inactive), and one count / scan / scatter re-sorts all of them.
+pic_status resort_with(pic_ctx *c, const std::vector<float4> &e0, const std::vector<float4> &e1,
+                       const std::vector<int> &ek, const std::vector<float4> &i0, const std::vector<float4> &i1,
+                       const std::vector<int> &ik)
 {
-    double fx = std::floor(X), fy = c->grid.ny > 1 ? std::floor(Y) : 0.0;
-    if (!(fx >= 0 && fx < c->grid.nx && fy >= 0 && fy < c->grid.ny))
-        return fail(c, PIC_ERR_ARG, "particle position outside the slab");
-    cell = (int)fy * c->grid.nx + (int)fx;
-    xi = (float)(X - fx);
-    eta = c->grid.ny > 1 ? (float)(Y - fy) : (float)Y;
-    if (xi >= 1.0f) xi = 0.99999994f;
-    if (c->grid.ny > 1 && eta >= 1.0f) eta = 0.99999994f;
+    cudaStream_t st = c->stream;
+    int ns[2] = {0, 0};
+    CK(cudaMemcpyAsync(&ns[0], c->csE[c->cur] + c->ncell, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&ns[1], c->csI[c->cur] + c->ncell, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const int nxt = c->cur ^ 1;
+    for (int sp = 0; sp < 2; ++sp) {
+        const bool el = sp == 0;
+        const std::vector<float4> &h0 = el ? e0 : i0, &h1 = el ? e1 : i1;
+        const std::vector<int> &hk = el ? ek : ik;
+        const long long n0 = ns[sp], nadd = (long long)hk.size();
+        if (n0 + nadd > (el ? c->cap_e : c->cap_i))
+            return fail(c, PIC_ERR_CAPACITY, "particle capacity exceeded by admission");
+        float4 *A0 = el ? c->eA0 : c->iA0, *A1 = el ? c->eA1 : c->iA1, *B0 = el ? c->eB0 : c->iB0, *B1 = el ? c->eB1 : c->iB1;
+        int *key = el ? c->ekey : c->ikey, *cnt = el ? c->cnt_e : c->cnt_i, *fill = el ? c->fill_e : c->fill_i;
+        const int *cs = el ? c->csE[c->cur] : c->csI[c->cur];
+        k_cell_keys<<<c->nsm * 4, 256, 0, st>>>(cs, c->ncell, c->cell_slab, c->d_slab, key);
+        if (nadd) {
+            CK(cudaMemcpyAsync(A0 + n0, h0.data(), sizeof(float4) * nadd, cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(A1 + n0, h1.data(), sizeof(float4) * nadd, cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(key + n0, hk.data(), sizeof(int) * nadd, cudaMemcpyHostToDevice, st));
+        }
+        const int tot = (int)(n0 + nadd);
+        CK(cudaMemcpyAsync(c->counters + CNT_NLOAD, &tot, sizeof(int), cudaMemcpyHostToDevice, st));
+        CK(cudaMemsetAsync(cnt, 0, sizeof(int) * c->ncell, st));
+        CK(cudaMemsetAsync(fill, 0, sizeof(int) * c->ncell, st));
+        k_count<<<c->nsm * 4, 256, 0, st>>>(key, c->counters + CNT_NLOAD, cnt);
+        pic_status r = run_scan(c, el ? 1 : 2, nxt);
+        if (r != PIC_OK) return r;
+        ScatterArgs sa{A0, A1, key, c->counters + CNT_NLOAD, nullptr, el ? c->csE[nxt] : c->csI[nxt], fill, B0, B1,
+                       el ? c->cap_e : c->cap_i};
+        k_scatter<<<c->nsm * 4, 256, 0, st>>>(sa);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(st));     // tot is read by the device; the next species reuses it
+    }
+    std::swap(c->eA0, c->eB0); std::swap(c->eA1, c->eB1);
+    std::swap(c->iA0, c->iB0); std::swap(c->iA1, c->iB1);
+    c->cur = nxt;
     return PIC_OK;
 }
 
+pic_status apply_pending(pic_ctx *c)
+{
+    if (c->pending.empty()) return PIC_OK;
+    std::vector<float4> e0, e1, i0, i1;
+    std::vector<int> ek, ik;
+    for (auto &p : c->pending) {
+        c->slabs[p.slot].active = 1;
+        pic_status r = reset_slot(c, p.slot);
+        if (r != PIC_OK) return r;
+        e0.insert(e0.end(), p.e0.begin(), p.e0.end()); e1.insert(e1.end(), p.e1.begin(), p.e1.end());
+        ek.insert(ek.end(), p.ek.begin(), p.ek.end());
+        i0.insert(i0.end(), p.i0.begin(), p.i0.end()); i1.insert(i1.end(), p.i1.begin(), p.i1.end());
+        ik.insert(ik.end(), p.ik.begin(), p.ik.end());
+    }
+    c->pending.clear();
+    return resort_with(c, e0, e1, ek, i0, i1, ik);
+}
+
+// particles of one slot back on the host with the slot's cell starts
+pic_status fetch_slot(pic_ctx *c, int slot, bool electrons, std::vector<float4> &p0, std::vector<float4> &p1,
+                      std::vector<int> &cs)
+{
+    cudaStream_t st = c->stream;
+    cs.resize(c->slot_cells + 1);
+    const int *src = (electrons ? c->csE[c->cur] : c->csI[c->cur]) + (size_t)slot * c->slot_cells;
+    CK(cudaMemcpyAsync(cs.data(), src, sizeof(int) * (c->slot_cells + 1), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const int lo = cs[0], n = cs[c->slot_cells] - lo;
+    p0.resize(n); p1.resize(n);
+    if (n) {
+        CK(cudaMemcpyAsync(p0.data(), (electrons ? c->eA0 : c->iA0) + lo, sizeof(float4) * n, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(p1.data(), (electrons ? c->eA1 : c->iA1) + lo, sizeof(float4) * n, cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    for (auto &v : cs) v -= lo;
+    return PIC_OK;
+}
+
+pic_status counts_slot(pic_ctx *c, int slot, int64_t *n_e, int64_t *n_i)
+{
+    int v[4];
+    const size_t a = (size_t)slot * c->slot_cells, b = a + c->slot_cells;
+    CK(cudaMemcpyAsync(&v[0], c->csE[c->cur] + a, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&v[1], c->csE[c->cur] + b, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&v[2], c->csI[c->cur] + a, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&v[3], c->csI[c->cur] + b, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (n_e) *n_e = v[1] - v[0];
+    if (n_i) *n_i = v[3] - v[2];
+    return read_device_error(c);
+}
+
+pic_status get_electrons_slot(pic_ctx *c, int slot, double *X, double *Y, float *u, float *w, uint64_t *id)
+{
+    std::vector<float4> p0, p1;
+    std::vector<int> cs;
+    pic_status r = fetch_slot(c, slot, true, p0, p1, cs);
+    if (r != PIC_OK) return r;
+    const SlabDev &S = c->slabs[slot];
+    for (int cell = 0; cell < c->slot_cells; ++cell) {
+        const int cx = cell % S.nx, cy = cell / S.nx;
+        for (int k = cs[cell]; k < cs[cell + 1]; ++k) {
+            X[k] = cx + (double)p0[k].x;
+            Y[k] = S.ny > 1 ? cy + (double)p0[k].y : (double)p0[k].y;
+            u[3 * k] = p0[k].z; u[3 * k + 1] = p0[k].w; u[3 * k + 2] = p1[k].x;
+            w[k] = p1[k].y;
+            uint32_t lo, hi;
+            std::memcpy(&lo, &p1[k].z, 4); std::memcpy(&hi, &p1[k].w, 4);
+            id[k] = ((uint64_t)hi << 32) | lo;
+        }
+    }
+    return PIC_OK;
+}
+
+pic_status get_ions_slot(pic_ctx *c, int slot, double *X, double *Y, float *u, float *zfrac, int32_t *Z,
+                         int32_t *nK, uint32_t *id)
+{
+    std::vector<float4> p0, p1;
+    std::vector<int> cs;
+    pic_status r = fetch_slot(c, slot, false, p0, p1, cs);
+    if (r != PIC_OK) return r;
+    const SlabDev &S = c->slabs[slot];
+    for (int cell = 0; cell < c->slot_cells; ++cell) {
+        const int cx = cell % S.nx, cy = cell / S.nx;
+        for (int k = cs[cell]; k < cs[cell + 1]; ++k) {
+            X[k] = cx + (double)p0[k].x;
+            Y[k] = S.ny > 1 ? cy + (double)p0[k].y : (double)p0[k].y;
+            u[3 * k] = p0[k].z; u[3 * k + 1] = p0[k].w; u[3 * k + 2] = p1[k].x;
+            zfrac[k] = p1[k].y;
+            uint32_t idv; int stv;
+            std::memcpy(&idv, &p1[k].z, 4); std::memcpy(&stv, &p1[k].w, 4);
+            id[k] = idv;
+            Z[k] = stv & 0xff;
+            nK[k] = (stv >> 8) & 0xff;
+        }
+    }
+    return PIC_OK;
+}
+
+pic_status diag_slot(pic_ctx *c, int slot, pic_diag *out)
+{
+    if (!out || out->n_E < 0 || out->n_E > 4096) return PIC_ERR_ARG;
+    cudaStream_t st = c->stream;
+    const SlabDev &S = c->slabs[slot];
+    const int nE = out->n_E > 0 ? out->n_E : 1;
+    const int nv = 4 + NZ + nE;
+    CK(cudaMemsetAsync(c->diag_buf, 0, sizeof(double) * (nv + 3), st));
+    DiagArgs d{};
+    const size_t a = (size_t)slot * c->slot_cells, b = a + c->slot_cells;
+    d.e0 = c->eA0; d.e1 = c->eA1; d.i0 = c->iA0; d.i1 = c->iA1;
+    d.e_lo = c->csE[c->cur] + a; d.e_hi = c->csE[c->cur] + b;
+    d.i_lo = c->csI[c->cur] + a; d.i_hi = c->csI[c->cur] + b;
+    d.m_ion = S.m_ion; d.out = c->diag_buf; d.n_E = nE; d.E_lo = 0.1;
+    d.E_max = out->E_max_eV > 0.1 ? out->E_max_eV : 1e4;
+    k_diag<<<c->nsm * 4, 256, sizeof(float) * nv, st>>>(d);
+    k_sumsq<<<c->nsm * 2, 256, 0, st>>>(c->E[c->ecur], c->npts, S.fld_off, c->slot_pts, c->diag_buf + nv);
+    k_sumsq<<<c->nsm * 2, 256, 0, st>>>(c->B, c->npts, S.fld_off, c->slot_pts, c->diag_buf + nv);
+    if (S.nb > 0) {
+        const float *hv = reinterpret_cast<const float *>(reinterpret_cast<const char *>(c->d_slab + slot) +
+                                                          offsetof(SlabDev, hv_b));
+        k_photon_energy<<<c->nsm * 2, 256, 0, st>>>(c->photons + S.ph_off, S.ncell, S.nb, hv, c->diag_buf + nv + 1);
+    }
+    CK(cudaGetLastError());
+    std::vector<double> h(nv + 3);
+    SlabTally tl;
+    unsigned step = 0;
+    CK(cudaMemcpyAsync(h.data(), c->diag_buf, sizeof(double) * (nv + 3), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&tl, c->d_tally + slot, sizeof(SlabTally), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&step, c->d_steps + slot, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    int64_t ne = 0, ni = 0;
+    pic_status r = counts_slot(c, slot, &ne, &ni);     // synchronizes the stream
+    if (r != PIC_OK) return r;
+    const double We = h[0], Ke = h[1], Ki = h[2], Ni = h[3];
+    if (out->csd) for (int z = 0; z < NZ; ++z) out->csd[z] = Ni > 0 ? h[4 + z] / Ni : 0.0;
+    double zb = 0.0;
+    for (int z = 0; z < NZ; ++z) zb += z * (Ni > 0 ? h[4 + z] / Ni : 0.0);
+    if (out->eedf && out->n_E > 0) for (int q = 0; q < out->n_E; ++q) out->eedf[q] = We > 0 ? h[4 + NZ + q] / We : 0.0;
+    const double E0 = kMeKg * kCms / (kQe * 1e-15);
+    out->t_fs = step * c->grids[slot].dt_fs;
+    out->transmission = tl.inc > 0 ? tl.trans / tl.inc : 0.0;
+    out->T_e_eV = We > 0 ? (2.0 / 3.0) * Ke / We : 0.0;
+    out->n_e_cm3 = S.ncell > 0 ? We * S.n_ref / S.ncell : 0.0;
+    out->Zbar = zb;
+    out->ke_e = Ke;
+    out->ke_i = Ki * S.w_ion;
+    out->e_ion = tl.ion;
+    out->e_phot = h[nv + 1];
+    out->e_inc = tl.inc;
+    out->e_trans = tl.trans;
+    out->e_ka_esc = tl.ka_esc;
+    out->e_esc = tl.esc;
+    out->e_field = h[nv] * kEps0 * E0 * E0 / (2.0 * S.n_ref * 1e6 * kQe);
+    for (int q = 0; q < 16; ++q) out->counts[q] = tl.cnt[q];
+    out->n_e = ne;
+    out->n_i = ni;
+    return read_device_error(c);
+}
+
+pic_status step_n(pic_ctx *c, int n)
+{
+    pic_status r = apply_pending(c);
+    if (r != PIC_OK) return r;
+    // size the per-warp staging for the largest cells seen so far
+    int mx[2] = {0, 0};
+    CK(cudaMemcpyAsync(mx, c->counters + CNT_MAXE, sizeof(int) * 2, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (mx[0] > 0 || mx[1] > 0) {
+        r = configure_cell_launch(c, mx[0], mx[1]);
+        if (r != PIC_OK) return r;
+    }
+    c->launches = 0;
+    for (int k = 0; k < n; ++k) {
+        r = launch_step(c);
+        if (r != PIC_OK) return r;
+    }
+    // the first step after a retirement dropped the retired slabs' particles
+    if (n > 0)
+        for (int k = 0; k < c->nslot; ++k)
+            if (c->slot_state[k] == 2) c->slot_state[k] = 0;
+    return PIC_OK;
+}
+
+bool batch_slot_ok(const pic_ctx *c, int slot) { return c && c->batch && slot >= 0 && slot < c->nslot; }
+
 }  // namespace
+
+extern "C" {
+
+size_t pic_required_bytes(const pic_grid *g, const pic_species *s, int n_e_cap, int n_i_cap)
+{
+    if (!valid_grid(g) || !s) return 0;
+    int ncell = g->nx * g->ny, npts = (g->nx + 1) * g->ny;
+    int nblk = (ncell + SCAN_TILE - 1) / SCAN_TILE;
+    int ce = n_e_cap > 0 ? n_e_cap : s->cap_e, ci = n_i_cap > 0 ? n_i_cap : s->cap_i;
+    return arena_need(ncell, npts, nblk, ce, ci, 1, g->ny);
+}
+
+pic_status pic_init(pic_ctx **out, const pic_grid *g, const pic_species *s, const pic_tables *t, void *arena,
+                    size_t arena_bytes, void *stream)
+{
+    if (!out || !t) return PIC_ERR_ARG;
+    *out = nullptr;
+    if (!valid_grid(g) || !valid_species(s) || s->cap_e <= 0 || s->cap_i <= 0) return PIC_ERR_ARG;
+    pic_ctx *c = nullptr;
+    pic_status r = ctx_create(&c, 1, g->nx * g->ny, (g->nx + 1) * g->ny, g->ny, g->nx, s->cap_e, s->cap_i, t, arena,
+                              arena_bytes, stream);
+    if (r != PIC_OK) return r;
+    c->grids[0] = *g;
+    c->slabs[0] = make_slab(c, 0, g, s);
+    c->slabs[0].active = 1;
+    c->slot_state[0] = 1;
+    if ((r = reset_slot(c, 0)) != PIC_OK) { pic_free(c); return r; }
+    *out = c;
+    return PIC_OK;
+}
+
+pic_status pic_source(pic_ctx *c, const pic_pulse *p)
+{
+    if (!c || !p) return PIC_ERR_ARG;
+    if (c->batch) return fail(c, PIC_ERR_STATE, "a batch context takes the pulse at admission");
+    if (!valid_pulse(p)) return fail(c, PIC_ERR_ARG, "pulse out of range");
+    set_pulse(c, c->slabs[0], p);
+    CK(cudaMemcpyAsync(c->d_slab, &c->slabs[0], sizeof(SlabDev), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(c->photons, 0, sizeof(ph2) * (size_t)c->ncell * PIC_MAX_BINS, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
 
 pic_status pic_load_electrons(pic_ctx *c, int64_t n, const double *X, const double *Y, const float *u,
                               const float *w, const uint64_t *id)
 {
     if (!c || n < 0 || (n > 0 && (!X || !Y || !u || !w || !id))) return PIC_ERR_ARG;
+    if (c->batch) return fail(c, PIC_ERR_STATE, "a batch context loads particles at admission");
     if (n > c->cap_e) return fail(c, PIC_ERR_CAPACITY, "more electrons than the capacity");
-    std::vector<float4> p0(n), p1(n);
-    std::vector<int> key(n);
-    for (int64_t k = 0; k < n; ++k) {
-        int cell; float xi, eta;
-        pic_status r = locate(c, X[k], Y[k], cell, xi, eta);
-        if (r != PIC_OK) return r;
-        p0[k] = make_float4(xi, eta, u[3 * k], u[3 * k + 1]);
-        uint32_t lo = (uint32_t)id[k], hi = (uint32_t)(id[k] >> 32);
-        float flo, fhi;
-        std::memcpy(&flo, &lo, 4); std::memcpy(&fhi, &hi, 4);
-        p1[k] = make_float4(u[3 * k + 2], w[k], flo, fhi);
-        key[k] = cell;
-    }
-    pic_status r = load_species(c, true, n, p0, p1, key);
+    std::vector<float4> p0, p1;
+    std::vector<int> key;
+    pic_status r = build_records(c, 0, &c->grids[0], true, n, X, Y, u, w, id, nullptr, nullptr, nullptr, p0, p1, key);
+    if (r == PIC_OK) r = load_species(c, true, n, p0, p1, key);
     if (r == PIC_OK) c->loaded_e = true;
     return r;
 }
@@ -569,22 +904,12 @@ pic_status pic_load_ions(pic_ctx *c, int64_t n, const double *X, const double *Y
                          const float *zfrac, const int32_t *Z, const int32_t *nK, const uint32_t *id)
 {
     if (!c || n < 0 || (n > 0 && (!X || !Y || !u || !zfrac || !Z || !nK || !id))) return PIC_ERR_ARG;
+    if (c->batch) return fail(c, PIC_ERR_STATE, "a batch context loads particles at admission");
     if (n > c->cap_i) return fail(c, PIC_ERR_CAPACITY, "more ions than the capacity");
-    std::vector<float4> p0(n), p1(n);
-    std::vector<int> key(n);
-    for (int64_t k = 0; k < n; ++k) {
-        int cell; float xi, eta;
-        pic_status r = locate(c, X[k], Y[k], cell, xi, eta);
-        if (r != PIC_OK) return r;
-        if (Z[k] < 0 || Z[k] > ZNUC || nK[k] < 0 || nK[k] > 2) return fail(c, PIC_ERR_ARG, "ion state out of range");
-        int stv = Z[k] | (nK[k] << 8);
-        float fid, fst;
-        std::memcpy(&fid, &id[k], 4); std::memcpy(&fst, &stv, 4);
-        p0[k] = make_float4(xi, eta, u[3 * k], u[3 * k + 1]);
-        p1[k] = make_float4(u[3 * k + 2], zfrac[k], fid, fst);
-        key[k] = cell;
-    }
-    pic_status r = load_species(c, false, n, p0, p1, key);
+    std::vector<float4> p0, p1;
+    std::vector<int> key;
+    pic_status r = build_records(c, 0, &c->grids[0], false, n, X, Y, u, zfrac, nullptr, Z, nK, id, p0, p1, key);
+    if (r == PIC_OK) r = load_species(c, false, n, p0, p1, key);
     if (r == PIC_OK) c->loaded_i = true;
     return r;
 }
@@ -592,8 +917,10 @@ pic_status pic_load_ions(pic_ctx *c, int64_t n, const double *X, const double *Y
 pic_status pic_set_photons(pic_ctx *c, const double *ph)
 {
     if (!c || !ph) return PIC_ERR_ARG;
-    if (c->slab.nb <= 0) return fail(c, PIC_ERR_STATE, "set a pulse first");
-    size_t n = (size_t)c->ncell * c->slab.nb;
+    if (c->batch) return fail(c, PIC_ERR_STATE, "single-slab call on a batch context");
+    const int nb = c->slabs[0].nb;
+    if (nb <= 0) return fail(c, PIC_ERR_STATE, "set a pulse first");
+    size_t n = (size_t)c->ncell * nb;
     std::vector<ph2> h(n);
     for (size_t k = 0; k < n; ++k) {
         float hi = (float)ph[k];
@@ -607,6 +934,7 @@ pic_status pic_set_photons(pic_ctx *c, const double *ph)
 pic_status pic_set_fields(pic_ctx *c, const float *f6)
 {
     if (!c || !f6) return PIC_ERR_ARG;
+    if (c->batch) return fail(c, PIC_ERR_STATE, "single-slab call on a batch context");
     size_t n = (size_t)c->npts;
     CK(cudaMemcpyAsync(c->E[c->ecur], f6, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->B, f6 + 3 * n, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, c->stream));
@@ -617,21 +945,8 @@ pic_status pic_set_fields(pic_ctx *c, const float *f6)
 pic_status pic_step(pic_ctx *c, int n)
 {
     if (!c || n < 0) return PIC_ERR_ARG;
-    if (!c->loaded_e || !c->loaded_i) return fail(c, PIC_ERR_STATE, "load particles before stepping");
-    // size the per-warp staging for the largest cells seen so far
-    int mx[2] = {0, 0};
-    CK(cudaMemcpyAsync(mx, c->counters + CNT_MAXE, sizeof(int) * 2, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    if (mx[0] > 0 || mx[1] > 0) {
-        pic_status r = configure_cell_launch(c, mx[0], mx[1]);
-        if (r != PIC_OK) return r;
-    }
-    c->launches = 0;
-    for (int k = 0; k < n; ++k) {
-        pic_status r = launch_step(c);
-        if (r != PIC_OK) return r;
-    }
-    return PIC_OK;
+    if (!c->batch && (!c->loaded_e || !c->loaded_i)) return fail(c, PIC_ERR_STATE, "load particles before stepping");
+    return step_n(c, n);
 }
 
 pic_status pic_sync(pic_ctx *c)
@@ -644,86 +959,32 @@ pic_status pic_sync(pic_ctx *c)
 pic_status pic_counts(pic_ctx *c, int64_t *n_e, int64_t *n_i)
 {
     if (!c) return PIC_ERR_ARG;
-    int ne = 0, ni = 0;
-    CK(cudaMemcpyAsync(&ne, c->csE[c->cur] + c->ncell, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(&ni, c->csI[c->cur] + c->ncell, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    if (n_e) *n_e = ne;
-    if (n_i) *n_i = ni;
-    return read_device_error(c);
+    if (c->batch) return fail(c, PIC_ERR_STATE, "single-slab call on a batch context");
+    return counts_slot(c, 0, n_e, n_i);
 }
-
-namespace {
-pic_status fetch(pic_ctx *c, bool electrons, std::vector<float4> &p0, std::vector<float4> &p1, std::vector<int> &cs)
-{
-    int64_t ne, ni;
-    pic_status r = pic_counts(c, &ne, &ni);
-    if (r != PIC_OK) return r;
-    int64_t n = electrons ? ne : ni;
-    p0.resize(n); p1.resize(n); cs.resize(c->ncell + 1);
-    if (n) {
-        CK(cudaMemcpyAsync(p0.data(), electrons ? c->eA0 : c->iA0, sizeof(float4) * n, cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaMemcpyAsync(p1.data(), electrons ? c->eA1 : c->iA1, sizeof(float4) * n, cudaMemcpyDeviceToHost, c->stream));
-    }
-    CK(cudaMemcpyAsync(cs.data(), electrons ? c->csE[c->cur] : c->csI[c->cur], sizeof(int) * (c->ncell + 1),
-                       cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    return PIC_OK;
-}
-}  // namespace
 
 pic_status pic_get_electrons(pic_ctx *c, double *X, double *Y, float *u, float *w, uint64_t *id)
 {
     if (!c) return PIC_ERR_ARG;
-    std::vector<float4> p0, p1;
-    std::vector<int> cs;
-    pic_status r = fetch(c, true, p0, p1, cs);
-    if (r != PIC_OK) return r;
-    for (int cell = 0; cell < c->ncell; ++cell) {
-        int cx = cell % c->grid.nx, cy = cell / c->grid.nx;
-        for (int k = cs[cell]; k < cs[cell + 1]; ++k) {
-            X[k] = cx + (double)p0[k].x;
-            Y[k] = c->grid.ny > 1 ? cy + (double)p0[k].y : (double)p0[k].y;
-            u[3 * k] = p0[k].z; u[3 * k + 1] = p0[k].w; u[3 * k + 2] = p1[k].x;
-            w[k] = p1[k].y;
-            uint32_t lo, hi;
-            std::memcpy(&lo, &p1[k].z, 4); std::memcpy(&hi, &p1[k].w, 4);
-            id[k] = ((uint64_t)hi << 32) | lo;
-        }
-    }
-    return PIC_OK;
+    if (c->batch) return fail(c, PIC_ERR_STATE, "single-slab call on a batch context");
+    return get_electrons_slot(c, 0, X, Y, u, w, id);
 }
 
 pic_status pic_get_ions(pic_ctx *c, double *X, double *Y, float *u, float *zfrac, int32_t *Z, int32_t *nK,
                         uint32_t *id)
 {
     if (!c) return PIC_ERR_ARG;
-    std::vector<float4> p0, p1;
-    std::vector<int> cs;
-    pic_status r = fetch(c, false, p0, p1, cs);
-    if (r != PIC_OK) return r;
-    for (int cell = 0; cell < c->ncell; ++cell) {
-        int cx = cell % c->grid.nx, cy = cell / c->grid.nx;
-        for (int k = cs[cell]; k < cs[cell + 1]; ++k) {
-            X[k] = cx + (double)p0[k].x;
-            Y[k] = c->grid.ny > 1 ? cy + (double)p0[k].y : (double)p0[k].y;
-            u[3 * k] = p0[k].z; u[3 * k + 1] = p0[k].w; u[3 * k + 2] = p1[k].x;
-            zfrac[k] = p1[k].y;
-            uint32_t idv; int stv;
-            std::memcpy(&idv, &p1[k].z, 4); std::memcpy(&stv, &p1[k].w, 4);
-            id[k] = idv;
-            Z[k] = stv & 0xff;
-            nK[k] = (stv >> 8) & 0xff;
-        }
-    }
-    return PIC_OK;
+    if (c->batch) return fail(c, PIC_ERR_STATE, "single-slab call on a batch context");
+    return get_ions_slot(c, 0, X, Y, u, zfrac, Z, nK, id);
 }
 
 pic_status pic_get_photons(pic_ctx *c, double *ph)
 {
     if (!c || !ph) return PIC_ERR_ARG;
-    if (c->slab.nb <= 0) return fail(c, PIC_ERR_STATE, "no pulse set");
-    size_t n = (size_t)c->ncell * c->slab.nb;
+    if (c->batch) return fail(c, PIC_ERR_STATE, "single-slab call on a batch context");
+    const int nb = c->slabs[0].nb;
+    if (nb <= 0) return fail(c, PIC_ERR_STATE, "no pulse set");
+    size_t n = (size_t)c->ncell * nb;
     std::vector<ph2> h(n);
     CK(cudaMemcpyAsync(h.data(), c->photons, sizeof(ph2) * n, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -734,6 +995,7 @@ pic_status pic_get_photons(pic_ctx *c, double *ph)
 pic_status pic_get_fields(pic_ctx *c, float *f6)
 {
     if (!c || !f6) return PIC_ERR_ARG;
+    if (c->batch) return fail(c, PIC_ERR_STATE, "single-slab call on a batch context");
     size_t n = (size_t)c->npts;
     CK(cudaMemcpyAsync(f6, c->E[c->ecur], sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(f6 + 3 * n, c->B, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
@@ -744,13 +1006,15 @@ pic_status pic_get_fields(pic_ctx *c, float *f6)
 pic_status pic_get_current(pic_ctx *c, double *j3)
 {
     if (!c || !j3) return PIC_ERR_ARG;
+    if (c->batch) return fail(c, PIC_ERR_STATE, "single-slab call on a batch context");
     size_t n = (size_t)c->npts;
     std::vector<unsigned long long> raw(3 * n);
     CK(cudaMemcpyAsync(raw.data(), c->J, sizeof(unsigned long long) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    const pic_grid &g = c->grids[0];
     const double fix = 1.0 / 1099511627776.0;
-    const double sx = c->grid.dx_nm / c->grid.dt_fs;
-    const double sy = c->grid.ny > 1 ? c->grid.dy_nm / c->grid.dt_fs : kCnmPerFs;
+    const double sx = g.dx_nm / g.dt_fs;
+    const double sy = g.ny > 1 ? g.dy_nm / g.dt_fs : kCnmPerFs;
     for (size_t k = 0; k < n; ++k) {
         j3[k] = (double)(long long)raw[k] * fix * sx;
         j3[n + k] = (double)(long long)raw[n + k] * fix * sy;
@@ -761,56 +1025,131 @@ pic_status pic_get_current(pic_ctx *c, double *j3)
 
 pic_status pic_diagnostics(pic_ctx *c, pic_diag *out)
 {
-    if (!c || !out || out->n_E < 0 || out->n_E > 4096) return PIC_ERR_ARG;
-    cudaStream_t st = c->stream;
-    const int nE = out->n_E > 0 ? out->n_E : 1;
-    const int nv = 4 + NZ + nE;
-    CK(cudaMemsetAsync(c->diag_buf, 0, sizeof(double) * (nv + 3), st));
-    DiagArgs d{};
-    d.e0 = c->eA0; d.e1 = c->eA1; d.i0 = c->iA0; d.i1 = c->iA1;
-    d.n_e = c->csE[c->cur] + c->ncell; d.n_i = c->csI[c->cur] + c->ncell;
-    d.m_ion = c->sp.m_ion_me; d.out = c->diag_buf; d.n_E = nE; d.E_lo = 0.1;
-    d.E_max = out->E_max_eV > 0.1 ? out->E_max_eV : 1e4;
-    k_diag<<<c->nsm * 4, 256, sizeof(float) * nv, st>>>(d);
-    k_sumsq<<<c->nsm * 4, 256, 0, st>>>(c->E[c->ecur], 3 * c->npts, c->diag_buf + nv);
-    k_sumsq<<<c->nsm * 4, 256, 0, st>>>(c->B, 3 * c->npts, c->diag_buf + nv);
-    if (c->slab.nb > 0) {
-        float *hv = reinterpret_cast<float *>(reinterpret_cast<char *>(c->d_slab) + offsetof(SlabDev, hv_b));
-        k_photon_energy<<<c->nsm * 4, 256, 0, st>>>(c->photons, c->ncell, c->slab.nb, hv, c->diag_buf + nv + 1);
-    }
-    CK(cudaGetLastError());
-    std::vector<double> h(nv + 3);
-    SlabTally tl;
-    unsigned step = 0;
-    int64_t ne = 0, ni = 0;
-    CK(cudaMemcpyAsync(h.data(), c->diag_buf, sizeof(double) * (nv + 3), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&tl, c->d_tally, sizeof(SlabTally), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&step, c->d_steps, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-    pic_status r = pic_counts(c, &ne, &ni);
+    if (!c) return PIC_ERR_ARG;
+    if (c->batch) return fail(c, PIC_ERR_STATE, "single-slab call on a batch context");
+    return diag_slot(c, 0, out);
+}
+
+size_t pic_batch_required_bytes(int max_slabs, int slot_cells, int cap_e, int cap_i)
+{
+    if (max_slabs < 1 || slot_cells < 2 || slot_cells > 8192 || cap_e <= 0 || cap_i <= 0) return 0;
+    long long ncell = (long long)max_slabs * slot_cells, npts = (long long)max_slabs * (slot_cells + 1);
+    if (npts > (1LL << 30)) return 0;
+    int nblk = (int)((ncell + SCAN_TILE - 1) / SCAN_TILE);
+    return arena_need((int)ncell, (int)npts, nblk, cap_e, cap_i, max_slabs, max_slabs);
+}
+
+pic_status pic_batch_init(pic_ctx **out, int max_slabs, int slot_cells, int cap_e, int cap_i, const pic_tables *t,
+                          void *arena, size_t arena_bytes, void *stream)
+{
+    if (!out || !t) return PIC_ERR_ARG;
+    *out = nullptr;
+    if (pic_batch_required_bytes(max_slabs, slot_cells, cap_e, cap_i) == 0) return PIC_ERR_ARG;
+    pic_ctx *c = nullptr;
+    pic_status r = ctx_create(&c, max_slabs, slot_cells, slot_cells + 1, 1, slot_cells, cap_e, cap_i, t, arena,
+                              arena_bytes, stream);
     if (r != PIC_OK) return r;
-    const double We = h[0], Ke = h[1], Ki = h[2], Ni = h[3];
-    if (out->csd) for (int z = 0; z < NZ; ++z) out->csd[z] = Ni > 0 ? h[4 + z] / Ni : 0.0;
-    double zb = 0.0;
-    for (int z = 0; z < NZ; ++z) zb += z * (Ni > 0 ? h[4 + z] / Ni : 0.0);
-    if (out->eedf && out->n_E > 0) for (int b = 0; b < out->n_E; ++b) out->eedf[b] = We > 0 ? h[4 + NZ + b] / We : 0.0;
-    out->t_fs = step * c->grid.dt_fs;
-    out->transmission = tl.inc > 0 ? tl.trans / tl.inc : 0.0;
-    out->T_e_eV = We > 0 ? (2.0 / 3.0) * Ke / We : 0.0;
-    out->n_e_cm3 = We * c->sp.n_ref_cm3 / c->ncell;
-    out->Zbar = zb;
-    out->ke_e = Ke;
-    out->ke_i = Ki * c->sp.w_ion;
-    out->e_ion = tl.ion;
-    out->e_phot = h[nv + 1];
-    out->e_inc = tl.inc;
-    out->e_trans = tl.trans;
-    out->e_ka_esc = tl.ka_esc;
-    out->e_esc = tl.esc;
-    out->e_field = h[nv] * c->fe_factor;
-    for (int q = 0; q < 16; ++q) out->counts[q] = tl.cnt[q];
-    out->n_e = ne;
-    out->n_i = ni;
-    return read_device_error(c);
+    c->batch = true;
+    *out = c;
+    return PIC_OK;
+}
+
+pic_status pic_batch_admit(pic_ctx *c, const pic_grid *g, const pic_species *s, const pic_pulse *p, int64_t n_e,
+                           const double *eX, const double *eY, const float *eu, const float *ew, const uint64_t *eid,
+                           int64_t n_i, const double *iX, const double *iY, const float *iu, const float *izf,
+                           const int32_t *iZ, const int32_t *inK, const uint32_t *iid, int *slot_out)
+{
+    if (!c || !slot_out) return PIC_ERR_ARG;
+    *slot_out = -1;
+    if (!c->batch) return fail(c, PIC_ERR_STATE, "not a batch context");
+    if (!valid_grid(g) || g->ny != 1 || g->nx > c->slot_cells || !valid_species(s))
+        return fail(c, PIC_ERR_ARG, "slab does not fit a slot (1D, nx <= slot cells)");
+    if (p && !valid_pulse(p)) return fail(c, PIC_ERR_ARG, "pulse out of range");
+    if (n_e < 0 || n_i < 0 || (n_e && (!eX || !eY || !eu || !ew || !eid)) ||
+        (n_i && (!iX || !iY || !iu || !izf || !iZ || !inK || !iid)))
+        return fail(c, PIC_ERR_ARG, "particle arrays missing");
+    int k = -1;
+    for (int q = 0; q < c->nslot; ++q)
+        if (c->slot_state[q] == 0) { k = q; break; }
+    if (k < 0) return fail(c, PIC_ERR_CAPACITY, "no free slot");
+    pic_ctx::Pending pd;
+    pd.slot = k;
+    pic_status r = build_records(c, k, g, true, n_e, eX, eY, eu, ew, eid, nullptr, nullptr, nullptr, pd.e0, pd.e1, pd.ek);
+    if (r != PIC_OK) return r;
+    r = build_records(c, k, g, false, n_i, iX, iY, iu, izf, nullptr, iZ, inK, iid, pd.i0, pd.i1, pd.ik);
+    if (r != PIC_OK) return r;
+    c->grids[k] = *g;
+    c->slabs[k] = make_slab(c, k, g, s);
+    if (p) set_pulse(c, c->slabs[k], p);
+    c->slot_state[k] = 1;
+    c->pending.push_back(std::move(pd));
+    *slot_out = k;
+    return PIC_OK;
+}
+
+pic_status pic_batch_retire(pic_ctx *c, int slot)
+{
+    if (!batch_slot_ok(c, slot)) return PIC_ERR_ARG;
+    if (c->slot_state[slot] != 1) return fail(c, PIC_ERR_STATE, "slot is not active");
+    for (size_t q = 0; q < c->pending.size(); ++q)
+        if (c->pending[q].slot == slot) {          // admitted, never on the device
+            c->pending.erase(c->pending.begin() + q);
+            c->slabs[slot].active = 0;
+            c->slot_state[slot] = 0;
+            return PIC_OK;
+        }
+    c->slabs[slot].active = 0;
+    CK(cudaMemcpyAsync(c->d_slab + slot, &c->slabs[slot], sizeof(SlabDev), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->slot_state[slot] = 2;
+    return PIC_OK;
+}
+
+pic_status pic_batch_slot(pic_ctx *c, int slot, int *state, uint32_t *step)
+{
+    if (!batch_slot_ok(c, slot)) return PIC_ERR_ARG;
+    if (state) *state = c->slot_state[slot];
+    if (step) {
+        CK(cudaMemcpyAsync(step, c->d_steps + slot, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    return PIC_OK;
+}
+
+pic_status pic_batch_diagnostics(pic_ctx *c, int slot, pic_diag *out)
+{
+    if (!batch_slot_ok(c, slot)) return PIC_ERR_ARG;
+    if (c->slot_state[slot] != 1) return fail(c, PIC_ERR_STATE, "slot is not active");
+    pic_status r = apply_pending(c);
+    if (r != PIC_OK) return r;
+    return diag_slot(c, slot, out);
+}
+
+pic_status pic_batch_counts(pic_ctx *c, int slot, int64_t *n_e, int64_t *n_i)
+{
+    if (!batch_slot_ok(c, slot)) return PIC_ERR_ARG;
+    pic_status r = apply_pending(c);
+    if (r != PIC_OK) return r;
+    return counts_slot(c, slot, n_e, n_i);
+}
+
+pic_status pic_batch_get_electrons(pic_ctx *c, int slot, double *X, double *Y, float *u, float *w, uint64_t *id)
+{
+    if (!batch_slot_ok(c, slot)) return PIC_ERR_ARG;
+    if (c->slot_state[slot] != 1) return fail(c, PIC_ERR_STATE, "slot is not active");
+    pic_status r = apply_pending(c);
+    if (r != PIC_OK) return r;
+    return get_electrons_slot(c, slot, X, Y, u, w, id);
+}
+
+pic_status pic_batch_get_ions(pic_ctx *c, int slot, double *X, double *Y, float *u, float *zfrac, int32_t *Z,
+                              int32_t *nK, uint32_t *id)
+{
+    if (!batch_slot_ok(c, slot)) return PIC_ERR_ARG;
+    if (c->slot_state[slot] != 1) return fail(c, PIC_ERR_STATE, "slot is not active");
+    pic_status r = apply_pending(c);
+    if (r != PIC_OK) return r;
+    return get_ions_slot(c, slot, X, Y, u, zfrac, Z, nK, id);
 }
 
 int64_t pic_launch_count(const pic_ctx *c) { return c ? c->launches : 0; }

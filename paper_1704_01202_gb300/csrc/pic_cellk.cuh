@@ -355,7 +355,7 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
         cx = lc % Sp->nx; cy = lc / Sp->nx;
         e0 = a.cs_e[g]; ne = a.cs_e[g + 1] - e0;
         i0 = a.cs_i[g]; ni = a.cs_i[g + 1] - i0;
-        on = ne > 0 || ni > 0;
+        on = (ne > 0 || ni > 0) && Sp->active;
     }
     const SlabDev &S = *Sp;
     const float wi = S.w_ion;

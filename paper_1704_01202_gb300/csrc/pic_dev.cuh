@@ -58,6 +58,7 @@ struct EosTable {
 
 // ---------------- per-slab description ----------------
 struct SlabDev {
+    int active;             // 0: retired / never admitted (its particles are dropped)
     int nx, ny, cell0, ncell;
     int fld_off;            // first grid point of this slab in the field arrays
     int ph_off;             // first photon entry (cells * nb)

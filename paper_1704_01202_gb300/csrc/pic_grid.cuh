@@ -39,7 +39,7 @@ __global__ void k_march(MarchArgs a)
     const int s = a.row_slab[blockIdx.x], row = a.row_idx[blockIdx.x];
     const SlabDev &S = a.slabs[s];
     const unsigned step = a.steps[s];
-    if (!(S.flags & 16u) || S.nb == 0 || S.rad_every <= 0 || (step % (unsigned)S.rad_every) != 0) return;
+    if (!S.active || !(S.flags & 16u) || S.nb == 0 || S.rad_every <= 0 || (step % (unsigned)S.rad_every) != 0) return;
     const int nx = S.nx, nb = S.nb;
     const double dtr = (double)S.rad_every * S.dt;
     const double sh = kCnmPerFs * dtr / S.dx;
@@ -220,8 +220,10 @@ __global__ void k_b_half(FieldArgs a)
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < a.npts; p += gridDim.x * blockDim.x) {
         const int s = a.pt_slab[p];
         const SlabDev &S = a.slabs[s];
-        if (!(S.flags & 128u) || a.sub >= S.nsub) continue;
-        const int W = S.nx + 1, q = p - S.fld_off, j = q / W, i = q - j * W;
+        const int W = S.nx + 1, q = p - S.fld_off;
+        // points past the slab's own (a batch slot wider than the slab) stay zero
+        if (!S.active || !(S.flags & 128u) || a.sub >= S.nsub || q >= W * S.ny) continue;
+        const int j = q / W, i = q - j * W;
         const int jp = (j + 1) % S.ny;
         const float h = 0.5f * S.dt / S.nsub * (float)kCnmPerFs;
         const int n = a.npts;
@@ -244,11 +246,12 @@ __global__ void k_e_full(FieldArgs a)
         const int n = a.npts;
         const float *exi = a.Ein, *eyi = a.Ein + n, *ezi = a.Ein + 2 * n;
         float *exo = a.Eout, *eyo = a.Eout + n, *ezo = a.Eout + 2 * n;
-        if (!(S.flags & 128u) || a.sub >= S.nsub) {
+        const int W = S.nx + 1, q = p - S.fld_off;
+        if (!S.active || !(S.flags & 128u) || a.sub >= S.nsub || q >= W * S.ny) {
             exo[p] = exi[p]; eyo[p] = eyi[p]; ezo[p] = ezi[p];
             continue;
         }
-        const int W = S.nx + 1, q = p - S.fld_off, j = q / W, i = q - j * W;
+        const int j = q / W, i = q - j * W;
         const int jm = (j - 1 + S.ny) % S.ny;
         const int o = S.fld_off, r = o + j * W, rm = o + jm * W;
         const float dtf = S.dt / S.nsub, C = (float)kCnmPerFs, kap = S.kappa_f;
@@ -289,10 +292,20 @@ __global__ void k_e_full(FieldArgs a)
     }
 }
 
-__global__ void k_advance(unsigned *steps, int nslab)
+__global__ void k_advance(unsigned *steps, const SlabDev *slabs, int nslab)
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < nslab) steps[s] += 1u;
+    if (s < nslab && slabs[s].active) steps[s] += 1u;
+}
+
+// keys of the sorted particles for a re-sort: their own cell, or -1 when
+// the cell's slab is retired
+__global__ void k_cell_keys(const int *cs, int ncell, const int *cell_slab, const SlabDev *slabs, int *key)
+{
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ncell; g += gridDim.x * blockDim.x) {
+        int k = slabs[cell_slab[g]].active ? g : -1;
+        for (int i = cs[g]; i < cs[g + 1]; ++i) key[i] = k;
+    }
 }
 
 // ---------------------------------------------------------------------
@@ -300,8 +313,7 @@ __global__ void k_advance(unsigned *steps, int nslab)
 // ---------------------------------------------------------------------
 struct DiagArgs {
     const float4 *e0, *e1, *i0, *i1;
-    const int *n_e, *n_i;
-    const int *cs_e, *cs_i;      // to find the slab of a slot: unused when one slab
+    const int *e_lo, *e_hi, *i_lo, *i_hi;   // particle range of the slab (device)
     double m_ion;
     double *out;                 // [0] W_e, [1] KE_e, [2] KE_i, [3] N_i, [4..4+NZ) csd, then eedf
     int n_E;
@@ -317,13 +329,13 @@ __global__ void k_diag(DiagArgs a)
     float *sd = sdf;
     for (int k = threadIdx.x; k < nv; k += blockDim.x) sd[k] = 0.0f;
     __syncthreads();
-    const int ne = *a.n_e, ni = *a.n_i;
+    const int eb = *a.e_lo, ne = *a.e_hi - eb, ib = *a.i_lo, ni = *a.i_hi - ib;
     const float lo_e = (float)a.E_lo, inv_lr = (float)(a.n_E / log(a.E_max / a.E_lo));
     dd w_s = dd_zero(), ke_s = dd_zero(), ki_s = dd_zero();
     int n_s = 0;
     const float MC2 = (float)kMeC2, mi = (float)a.m_ion;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ne; k += gridDim.x * blockDim.x) {
-        float4 P0 = a.e0[k], P1 = a.e1[k];
+        float4 P0 = a.e0[eb + k], P1 = a.e1[eb + k];
         float ke = MC2 * gm1(P0.z, P0.w, P1.x);
         float w = P1.y;
         w_s = dd_addf(w_s, w);
@@ -333,7 +345,7 @@ __global__ void k_diag(DiagArgs a)
         atomicAdd(sd + 4 + NZ + b, w);
     }
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ni; k += gridDim.x * blockDim.x) {
-        float4 P0 = a.i0[k], P1 = a.i1[k];
+        float4 P0 = a.i0[ib + k], P1 = a.i1[ib + k];
         ki_s = dd_addf(ki_s, MC2 * mi * gm1(P0.z, P0.w, P1.x));
         n_s += 1;
         int Z = __float_as_int(P1.w) & 0xff;
@@ -358,10 +370,14 @@ __global__ void k_diag(DiagArgs a)
         if (sd[k] != 0.0f) atomicAdd(a.out + k, (double)sd[k]);
 }
 
-__global__ void k_sumsq(const float *x, int n, double *out)
+// sum of squares of three components of one slab's grid points
+__global__ void k_sumsq(const float *x, int npts, int off, int n, double *out)
 {
     double v = 0.0;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) v += (double)x[k] * x[k];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 3 * n; k += gridDim.x * blockDim.x) {
+        float f = x[(size_t)(k / n) * npts + off + k % n];
+        v += (double)f * f;
+    }
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(out, v);
 }

@@ -328,6 +328,11 @@ __global__ void __launch_bounds__(256) k_push(PushArgs a)
         const int s = __ldg(a.cell_slab + g);
         if (s != cur) { push_flush(a, cur, esc, esc_e, esc_i, lane); cur = s; }
         const SlabDev &S = a.slabs[s];
+        if (!S.active) {              // retired slab: its particles leave
+            for (int k = a.cs_e[g] + lane; k < a.cs_e[g + 1]; k += 32) a.ekey[k] = -1;
+            for (int k = a.cs_i[g] + lane; k < a.cs_i[g + 1]; k += 32) a.ikey[k] = -1;
+            continue;
+        }
         if (S.ny > 1) push_cell<2>(a, S, s, g, lane, esc, esc_e, esc_i);
         else push_cell<1>(a, S, s, g, lane, esc, esc_e, esc_i);
     }
