@@ -245,6 +245,21 @@ const char *pic_last_error(const pic_ctx *c);
  * implementations: out[4*i..] = philox(ctr[4*i..], key) for i < n. */
 pic_status pic_philox_check(const uint32_t *ctr, const uint32_t key[2], uint32_t *out, int n);
 
+/* The same check without any device allocation.  The paper has no
+ * counterpart: this serves callers that must not allocate, e.g. a host
+ * thread of a serving loop whose device memory budget is fixed up front, or
+ * code about to run under stream capture, where cudaMalloc is not allowed.
+ * Scratch is a static device array of PIC_PHILOX_STATIC_MAX counters (four
+ * words each, 128 KiB in all); n above that returns PIC_ERR_ARG.  Nothing in
+ * the scratch needs to start at zero: every word is written before it is
+ * read.  The scratch's address is looked up once per device (the first call
+ * with that device current); make that first call before any stream
+ * capture.  Calls run on the legacy default stream and return when the
+ * result is on the host.  Two calls on the same device at the same time
+ * (two host threads) race on the scratch: serialize them. */
+#define PIC_PHILOX_STATIC_MAX 4096
+pic_status pic_philox_check_static(const uint32_t *ctr, const uint32_t key[2], uint32_t *out, int n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -39,7 +39,7 @@ ABI_FUNCTIONS = ["pic_required_bytes", "pic_init", "pic_source", "pic_load_elect
                  "pic_get_current", "pic_launch_count", "pic_free", "pic_last_error", "pic_philox_check",
                  "pic_timing", "pic_batch_required_bytes", "pic_batch_init", "pic_batch_admit",
                  "pic_batch_retire", "pic_batch_slot", "pic_batch_diagnostics", "pic_batch_counts",
-                 "pic_batch_get_electrons", "pic_batch_get_ions"]
+                 "pic_batch_get_electrons", "pic_batch_get_ions", "pic_philox_check_static"]
 
 
 def _sources():
@@ -141,6 +141,8 @@ def lib():
             L.pic_last_error.argtypes = [_P]
             L.pic_philox_check.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
                                            C.POINTER(C.c_uint32), C.c_int]
+            L.pic_philox_check_static.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
+                                                  C.POINTER(C.c_uint32), C.c_int]
             L.pic_timing.argtypes = [_P, C.c_int, _D, C.POINTER(C.c_int64)]
             L.pic_batch_required_bytes.restype = C.c_size_t
             L.pic_batch_required_bytes.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]

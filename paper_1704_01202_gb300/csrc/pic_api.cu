@@ -14,6 +14,7 @@
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1204,6 +1205,37 @@ pic_status pic_philox_check(const uint32_t *ctr, const uint32_t key[2], uint32_t
     }
     cudaFree(d);
     return st;
+}
+
+// Scratch of pic_philox_check_static: counters then outputs, 4 words each.
+static __device__ __align__(256) uint32_t g_philox_scratch[8 * PIC_PHILOX_STATIC_MAX];
+
+pic_status pic_philox_check_static(const uint32_t *ctr, const uint32_t key[2], uint32_t *out, int n)
+{
+    if (!ctr || !key || !out || n <= 0 || n > PIC_PHILOX_STATIC_MAX) return PIC_ERR_ARG;
+    // address of the scratch on each device, looked up once with that device current
+    constexpr int MAX_DEV = 64;
+    static uint32_t *addr[MAX_DEV] = {};
+    static std::mutex lock;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV) return PIC_ERR_CUDA;
+    uint32_t *d = nullptr;
+    {
+        std::lock_guard<std::mutex> g(lock);
+        if (!addr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_philox_scratch) != cudaSuccess || !p) return PIC_ERR_CUDA;
+            addr[dev] = static_cast<uint32_t *>(p);
+        }
+        d = addr[dev];
+    }
+    if (cudaMemcpy(d, ctr, sizeof(uint32_t) * 4 * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess) return PIC_ERR_CUDA;
+    k_philox_check<<<(n + 127) / 128, 128>>>(d, key[0], key[1], d + 4 * (size_t)PIC_PHILOX_STATIC_MAX, n);
+    if (cudaGetLastError() != cudaSuccess) return PIC_ERR_CUDA;
+    if (cudaMemcpy(out, d + 4 * (size_t)PIC_PHILOX_STATIC_MAX, sizeof(uint32_t) * 4 * (size_t)n,
+                   cudaMemcpyDeviceToHost) != cudaSuccess)
+        return PIC_ERR_CUDA;
+    return PIC_OK;
 }
 
 }  // extern "C"

@@ -1,0 +1,47 @@
+"""The allocation-free Philox check (pic_philox_check_static) against the
+allocating one (pic_philox_check), through the C ABI.  Kept in a file that
+is collected last so it also runs after every other GPU test."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1704_01202_gb300 as pkg  # noqa: E402
+
+MAX = 4096      # PIC_PHILOX_STATIC_MAX in include/pic.h
+
+
+def _call(fn, ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    o = np.zeros_like(c)
+    P = C.POINTER(C.c_uint32)
+    st = fn(c.ctypes.data_as(P), k.ctypes.data_as(P), o.ctypes.data_as(P), c.shape[0])
+    return st, o
+
+
+@pytest.mark.parametrize("n", [1, 1000, MAX])
+def test_static_matches_allocating_twice(n):
+    pkg.build()
+    L = pkg.lib()
+    rng = np.random.default_rng(n)
+    for call in range(2):                   # two calls in a row, new inputs each time
+        ctr = rng.integers(0, 2**32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+        key = rng.integers(0, 2**32, size=2, dtype=np.uint64).astype(np.uint32)
+        st_a, ref = _call(L.pic_philox_check, ctr, key)
+        st_b, got = _call(L.pic_philox_check_static, ctr, key)
+        assert st_a == 0 and st_b == 0, (call, st_a, st_b)
+        assert np.array_equal(got, ref), call
+
+
+def test_static_rejects_oversize():
+    pkg.build()
+    L = pkg.lib()
+    st, _ = _call(L.pic_philox_check_static, np.zeros((MAX + 1, 4), np.uint32), np.zeros(2, np.uint32))
+    assert pkg.STATUS[st] == "PIC_ERR_ARG"
