@@ -3,10 +3,11 @@
 // A cell's particles are visited in the canonical order the collision
 // kernel recorded (the memory order inside a cell, left by the atomic
 // scatter of the counting sort, is unspecified).  Lane L takes canonical
-// positions L, L+32, ...; each stencil contribution is summed across the
-// warp with a fixed butterfly, the running sum of node k is kept by lane
-// k % 32, and the cell's totals go to the global grid as 2^40 fixed point,
-// whose addition is associative.  The current is therefore bit-reproducible.
+// positions L, L+32, ...; each lane stores its stencil contributions in a
+// shared-memory column, lane k % 32 sums row k of each batch in a fixed
+// order and keeps the running total of node k, and the cell's totals go to
+// the global grid as 2^40 fixed point, whose addition is associative.  The
+// current is therefore bit-reproducible.
 #pragma once
 #include "pic_cell.cuh"
 
@@ -73,19 +74,38 @@ __device__ __forceinline__ float interp4(const float *F, int W, int x0, int x1, 
     return w0 * (v0 * __ldg(r0 + x0) + v1 * __ldg(r1 + x0)) + w1 * (v0 * __ldg(r0 + x1) + v1 * __ldg(r1 + x1));
 }
 
-// warp sum of one contribution (fixed butterfly); lane k % 32 keeps it
-__device__ __forceinline__ void jadd(float acc[2], int k, float v, int lane)
+// Per-warp staging of the stencil contributions: row k (node), column
+// lane; the row pitch of 33 words keeps both the column stores and the row
+// sums free of bank conflicts.
+constexpr int JROWS = 40, JPITCH = 33, PUSH_WARPS = 8;
+
+__device__ __forceinline__ void jput(float *col, int k, float v) { col[k * JPITCH] = v; }
+
+// Row sums of one batch (fixed order: four interleaved partial sums, then
+// pairwise), added to the running totals of the rows this lane owns:
+// acc[0] <- row lane, acc[1] <- row lane + 32.
+__device__ __forceinline__ void jrows(const float *sj, int nrows, int lane, float acc[2])
 {
+    __syncwarp();
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-    if (lane == (k & 31)) acc[k >> 5] += v;
+    for (int h = 0; h < 2; ++h) {
+        const int k = lane + 32 * h;
+        if (k < nrows) {
+            const float *r = sj + k * JPITCH;
+            float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) { s0 += r[j]; s1 += r[j + 1]; s2 += r[j + 2]; s3 += r[j + 3]; }
+            acc[h] += (s0 + s1) + (s2 + s3);
+        }
+    }
+    __syncwarp();
 }
 
 // 2D Esirkepov weights of one sub-cell move (offsets relative to the cell,
 // stencil nodes -1..2); order of the sums: jx[a][b] (12), jy[a][b] (12),
 // jz[a][b] (16)
 __device__ __forceinline__ void esirkepov2_w(float x0, float y0, float x1, float y1, float qw, float qwbz,
-                                             float acc[2], int lane)
+                                             float *col)
 {
     float S0x[4], S1x[4], S0y[4], S1y[4];
 #pragma unroll
@@ -100,7 +120,7 @@ __device__ __forceinline__ void esirkepov2_w(float x0, float y0, float x1, float
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             acc_x += (S1x[a] - S0x[a]) * sy;
-            jadd(acc, a * 4 + b, -qw * acc_x, lane);
+            jput(col, a * 4 + b, -qw * acc_x);
         }
     }
 #pragma unroll
@@ -111,32 +131,31 @@ __device__ __forceinline__ void esirkepov2_w(float x0, float y0, float x1, float
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
             acc_y += (S1y[b] - S0y[b]) * sx;
-            jadd(acc, 12 + a * 3 + b, -qw * acc_y, lane);
+            jput(col, 12 + a * 3 + b, -qw * acc_y);
         }
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
             float dsy = S1y[b] - S0y[b];
             float wz = S0x[a] * S0y[b] + 0.5f * dsx * S0y[b] + 0.5f * S0x[a] * dsy + dsx * dsy * (1.0f / 3.0f);
-            jadd(acc, 24 + a * 4 + b, qwbz * wz, lane);
+            jput(col, 24 + a * 4 + b, qwbz * wz);
         }
     }
 }
 
 // 1D: jx at 3 half nodes (0..2), jy (3..6), jz (7..10) at 4 nodes
-__device__ __forceinline__ void esirkepov1_w(float x0, float x1, float qw, float qwby, float qwbz, float acc[2],
-                                             int lane)
+__device__ __forceinline__ void esirkepov1_w(float x0, float x1, float qw, float qwby, float qwbz, float *col)
 {
     float S0x[4], S1x[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) { S0x[a] = cic_w(x0, a - 1); S1x[a] = cic_w(x1, a - 1); }
     float acc_x = 0.0f;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) { acc_x += S1x[a] - S0x[a]; jadd(acc, a, -qw * acc_x, lane); }
+    for (int a = 0; a < 3; ++a) { acc_x += S1x[a] - S0x[a]; jput(col, a, -qw * acc_x); }
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
         float sv = 0.5f * (S0x[a] + S1x[a]);
-        jadd(acc, 3 + a, qwby * sv, lane);
-        jadd(acc, 7 + a, qwbz * sv, lane);
+        jput(col, 3 + a, qwby * sv);
+        jput(col, 7 + a, qwbz * sv);
     }
 }
 
@@ -190,9 +209,10 @@ __device__ __forceinline__ void wrap_offsets(float xn, float yn, float &xi, floa
 }
 
 template <int DIM>
-__device__ void push_cell(const PushArgs &a, const SlabDev &S, int s, int g, int lane, dd &esc, int &esc_e,
-                          int &esc_i)
+__device__ void push_cell(const PushArgs &a, const SlabDev &S, int s, int g, int lane, float *sj, dd &esc,
+                          int &esc_e, int &esc_i)
 {
+    constexpr int NJ = DIM == 2 ? 40 : 11;
     const int lc = g - S.cell0;
     const int cx = lc % S.nx, cy = lc / S.nx;
     const bool do_push = S.flags & 64u, do_dep = (S.flags & 128u) != 0;
@@ -261,8 +281,9 @@ __device__ void push_cell(const PushArgs &a, const SlabDev &S, int s, int g, int
             }
             if (do_dep) {
                 if (!dep_short) { qw = qwby = qwbz = 0.0f; x0 = x1 = 0.5f; y0 = y1 = 0.5f; }
-                if constexpr (DIM == 2) esirkepov2_w(x0, y0, x1, y1, qw, qwbz, acc, lane);
-                else esirkepov1_w(x0, x1, qw, qwby, qwbz, acc, lane);
+                if constexpr (DIM == 2) esirkepov2_w(x0, y0, x1, y1, qw, qwbz, sj + lane);
+                else esirkepov1_w(x0, x1, qw, qwby, qwbz, sj + lane);
+                jrows(sj, NJ, lane, acc);
             }
             // aggregated count of the next cell
             unsigned peers = __match_any_sync(FULL, have ? nk : -2);
@@ -272,11 +293,10 @@ __device__ void push_cell(const PushArgs &a, const SlabDev &S, int s, int g, int
 
     if (do_dep) {
         const int fo = S.fld_off, W = S.nx + 1;
-        const int nj = DIM == 2 ? 40 : 11;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int k = lane + 32 * h;
-            if (k >= nj || acc[h] == 0.0f) continue;
+            if (k >= NJ || acc[h] == 0.0f) continue;
             if (DIM == 2) {
                 int p, q, comp;
                 if (k < 12) { comp = 0; p = k / 4; q = k % 4; }
@@ -312,9 +332,11 @@ __device__ void push_flush(const PushArgs &a, int slab, dd &esc, int &esc_e, int
     esc_e = esc_i = 0;
 }
 
-__global__ void __launch_bounds__(256) k_push(PushArgs a)
+__global__ void __launch_bounds__(32 * PUSH_WARPS, 2) k_push(PushArgs a)
 {
+    __shared__ float s_j[PUSH_WARPS][JROWS * JPITCH];
     const int lane = threadIdx.x & 31;
+    float *sj = s_j[threadIdx.x >> 5];
     int cur = -1;
     dd esc = dd_zero();
     int esc_e = 0, esc_i = 0;
@@ -333,8 +355,8 @@ __global__ void __launch_bounds__(256) k_push(PushArgs a)
             for (int k = a.cs_i[g] + lane; k < a.cs_i[g + 1]; k += 32) a.ikey[k] = -1;
             continue;
         }
-        if (S.ny > 1) push_cell<2>(a, S, s, g, lane, esc, esc_e, esc_i);
-        else push_cell<1>(a, S, s, g, lane, esc, esc_e, esc_i);
+        if (S.ny > 1) push_cell<2>(a, S, s, g, lane, sj, esc, esc_e, esc_i);
+        else push_cell<1>(a, S, s, g, lane, sj, esc, esc_e, esc_i);
     }
     push_flush(a, cur, esc, esc_e, esc_i, lane);
 }
