@@ -221,6 +221,9 @@ def run_gpu(args):
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(pkg, cfg, tab, pl, st, args, world, n0)
+    del st
+    ensemble = run_ensemble(pkg, tab, args, rank) if args.ensemble > 0 else None
+    served = run_served(pkg, tab, args) if args.serve_n > 0 else None
     if dist:
         dist.barrier()
     if rank == 0:
@@ -232,10 +235,72 @@ def run_gpu(args):
                           "ppc": [cfg.ppc_e, cfg.ppc_i], "pulse_keV": pl.hv_eV / 1e3,
                           "l2": "state (1.3 GB) larger than L2; no flush", "parallelism": "replicas"},
                "roofline": roof, "step_hbm_gbs": step_gbs, "cpu_baseline": cb, "e2e": e2e,
-               "gpu_launches": int(launches), "clocks": clk, "kernel_ms": {k: v / max(nrec, 1) for k, v in tms.items()}}
+               "gpu_launches": int(launches), "clocks": clk, "kernel_ms": {k: v / max(nrec, 1) for k, v in tms.items()},
+               "ensemble": ensemble, "served": served}
         print(json.dumps(out))
     if dist:
         dist.destroy_process_group()
+
+
+def run_ensemble(pkg, tab, args, rank):
+    """The batched ensemble: 256 independent 1D slabs (cells log-uniform
+    64-4096, 32-512 particles per cell) stepped together, one launch of each
+    kernel per step for all of them."""
+    import torch
+    ens = P.batched_ensemble(n=args.ensemble, seed=7 + rank)
+    states = [P.init_particles(c) for c, _ in ens]
+    cap_e = cap_i = 0
+    for (c, _), st in zip(ens, states):
+        e, i = pkg.default_capacity(st.n_e, st.n_i, c.Z_init)
+        cap_e, cap_i = cap_e + e, cap_i + i
+    slot_cells = max(c.nx for c, _ in ens)
+    bt = pkg.Batch(tab, len(ens), slot_cells, cap_e, cap_i)
+    for (c, pl), st in zip(ens, states):
+        bt.admit(c, st, pl)
+    bt.step(args.warmup)
+    bt.sync()
+    n0 = sum(sum(bt.counts(k)) for k in range(len(ens)))
+    stream = torch.cuda.current_stream()
+    bt.timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    bt.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = bt.launches
+    tms, nrec = bt.timing(None)
+    n1 = sum(sum(bt.counts(k)) for k in range(len(ens)))
+    bt.close()
+    n_mean = 0.5 * (n0 + n1)
+    return {"workload": f"{len(ens)} 1D Al slabs, cells log-uniform 64-4096 (2 nm), 32-512 particles per cell, "
+                        "I log-uniform 1e15-1e18 W/cm^2, hv U(1.58, 1.90) keV",
+            "slabs": len(ens), "slot_cells": slot_cells, "particles": int(n_mean), "steps": args.steps,
+            "value": n_mean * args.steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / args.steps,
+            "gpu_launches": int(launches), "kernel_ms": {k: v / max(nrec, 1) for k, v in tms.items()}}
+
+
+def run_served(pkg, tab, args):
+    """Served loop: Poisson arrivals of slab requests, continuous batching
+    against the plain one-at-a-time form on the same trace."""
+    from paper_1704_01202_gb300 import serve
+    tr = P.request_trace(n=args.serve_n, rate_hz=200.0, seed=11, horizon_fs=args.serve_horizon_fs)
+    fp = [serve.footprint(r.cfg) for r in tr]
+    slot_cells = max(r.cfg.nx for r in tr)
+    # resident capacity: room for about 64 average requests at once
+    cap_e = max(max(f[0] for f in fp), int(64 * sum(f[0] for f in fp) / len(fp)))
+    cap_i = max(max(f[1] for f in fp), int(64 * sum(f[1] for f in fp) / len(fp)))
+    b = serve.serve_batched(tr, tab, P.init_particles, max_slabs=128, slot_cells=slot_cells,
+                            cap_e=cap_e, cap_i=cap_i, tick_steps=10)
+    o = serve.serve_one_at_a_time(tr, tab, P.init_particles)
+    psteps = sum(r.nsteps * r.cfg.ncell * (r.cfg.ppc_e + r.cfg.ppc_i) for r in tr)
+    keys = ("slabs_per_s", "ttr_p50_s", "ttr_p99_s", "ttr_mean_s", "wall_s")
+    return {"trace": f"{len(tr)} Poisson arrivals at 200/s, ensemble draws + thickness U(0.2, 2) um, "
+                     f"each run {args.serve_horizon_fs:g} fs ({tr[0].nsteps} steps)",
+            "batched": {k: b[k] for k in keys}, "one_at_a_time": {k: o[k] for k in keys},
+            "speedup_slabs_per_s": b["slabs_per_s"] / o["slabs_per_s"],
+            "particle_steps": int(psteps), "max_slabs": 128, "slot_cells": slot_cells}
 
 
 def run_e2e(pkg, cfg, tab, pl, st, args, world, n0):
@@ -268,6 +333,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cells", type=int, nargs=2, default=None, help="smaller foil (profiling)")
+    ap.add_argument("--ensemble", type=int, default=256, help="slabs of the batched ensemble (0: skip)")
+    ap.add_argument("--serve-n", type=int, default=200, help="requests of the served trace (0: skip)")
+    ap.add_argument("--serve-horizon-fs", type=float, default=1.0, help="simulated time per served request")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "gb300" else args.warmup
     if args.impl == "reference":

@@ -209,8 +209,9 @@ pic_status pic_batch_admit(pic_ctx *c, const pic_grid *g, const pic_species *s, 
                            const float *izf, const int32_t *iZ, const int32_t *inK,
                            const uint32_t *iid, int *slot_out);
 
-/* Retire an active slot: its particles are dropped by the next step, after
- * which the slot is free again. */
+/* Retire an active slot: its particles are dropped by the next step, or
+ * earlier by an admission that needs the slot or the space, after which the
+ * slot is free again. */
 pic_status pic_batch_retire(pic_ctx *c, int slot);
 
 /* Slot state (0 free, 1 active, 2 retired, not yet emptied) and its step

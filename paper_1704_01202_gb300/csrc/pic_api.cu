@@ -284,7 +284,7 @@ pic_status launch_step(pic_ctx *c)
     pa.ncell = c->ncell; pa.cell_slab = c->cell_slab; pa.slabs = c->d_slab; pa.tally = c->d_tally;
     pa.fldE = c->E[c->ecur]; pa.fldB = c->B; pa.npts = c->npts; pa.J = c->J;
     pa.err = c->counters + CNT_ERR; pa.work = c->counters + CNT_WORK_PUSH;
-    k_push<<<c->grid_push, 256, 0, st>>>(pa);
+    k_push<<<c->grid_push, 32 * PUSH_WARPS, 0, st>>>(pa);
     k_push_new<<<c->nsm * 2, 256, 0, st>>>(pa);
     c->launches += 2;
     CK(cudaGetLastError());
@@ -540,7 +540,7 @@ pic_status ctx_create(pic_ctx **out, int nslot, int slot_cells, int slot_pts, in
     if (e != cudaSuccess) { rc = cuda_fail(c, e, "march attribute"); pic_free(c); return rc; }
     if ((rc = configure_cell_launch(c, 128, 32)) != PIC_OK) { pic_free(c); return rc; }
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_push, 256, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_push, 32 * PUSH_WARPS, 0);
     if (e != cudaSuccess) { rc = cuda_fail(c, e, "push occupancy"); pic_free(c); return rc; }
     c->grid_push = std::max(1, occ) * c->nsm;
     *out = c;
@@ -659,9 +659,42 @@ pic_status resort_with(pic_ctx *c, const std::vector<float4> &e0, const std::vec
     return PIC_OK;
 }
 
+// drop the particles of retired slabs now (one re-sort) and free their slots
+pic_status compact(pic_ctx *c)
+{
+    const std::vector<float4> no4;
+    const std::vector<int> noi;
+    pic_status r = resort_with(c, no4, no4, noi, no4, no4, noi);
+    if (r != PIC_OK) return r;
+    for (int k = 0; k < c->nslot; ++k)
+        if (c->slot_state[k] == 2) c->slot_state[k] = 0;
+    return PIC_OK;
+}
+
+bool any_retired(const pic_ctx *c)
+{
+    for (int k = 0; k < c->nslot; ++k)
+        if (c->slot_state[k] == 2) return true;
+    return false;
+}
+
 pic_status apply_pending(pic_ctx *c)
 {
     if (c->pending.empty()) return PIC_OK;
+    // the new records are appended behind every sorted particle, retired
+    // ones included: drop those first when the buffers would overflow
+    if (any_retired(c)) {
+        size_t add_e = 0, add_i = 0;
+        for (auto &p : c->pending) { add_e += p.ek.size(); add_i += p.ik.size(); }
+        int ns[2] = {0, 0};
+        CK(cudaMemcpyAsync(&ns[0], c->csE[c->cur] + c->ncell, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(&ns[1], c->csI[c->cur] + c->ncell, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        if (ns[0] + add_e > (size_t)c->cap_e || ns[1] + add_i > (size_t)c->cap_i) {
+            pic_status r = compact(c);
+            if (r != PIC_OK) return r;
+        }
+    }
     std::vector<float4> e0, e1, i0, i1;
     std::vector<int> ek, ik;
     for (auto &p : c->pending) {
@@ -1070,8 +1103,15 @@ pic_status pic_batch_admit(pic_ctx *c, const pic_grid *g, const pic_species *s, 
         (n_i && (!iX || !iY || !iu || !izf || !iZ || !inK || !iid)))
         return fail(c, PIC_ERR_ARG, "particle arrays missing");
     int k = -1;
-    for (int q = 0; q < c->nslot; ++q)
-        if (c->slot_state[q] == 0) { k = q; break; }
+    for (int q = 0; q < c->nslot && k < 0; ++q)
+        if (c->slot_state[q] == 0) k = q;
+    if (k < 0 && any_retired(c)) {               // free the retired slots now
+        pic_status r = apply_pending(c);
+        if (r == PIC_OK) r = compact(c);
+        if (r != PIC_OK) return r;
+        for (int q = 0; q < c->nslot && k < 0; ++q)
+            if (c->slot_state[q] == 0) k = q;
+    }
     if (k < 0) return fail(c, PIC_ERR_CAPACITY, "no free slot");
     pic_ctx::Pending pd;
     pd.slot = k;

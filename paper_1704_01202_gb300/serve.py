@@ -1,0 +1,116 @@
+"""Serving of independent slab simulations on one GPU.
+
+`serve_batched` is continuous batching over the batch context of the C ABI
+(pic_batch_*): requests are admitted as they arrive whenever a slot is free
+and their worst-case particle footprint fits the arena, every kernel of a
+step runs once for all resident slabs, and a slab leaves (diagnostics read,
+slot retired) as soon as it has run its steps.  `serve_one_at_a_time` is
+the plain form: one single-slab context per request, in arrival order.
+
+Both replay the same arrival trace in real time and return per-request
+time-to-result (result ready minus arrival) and the drained slabs/s.  A
+slab's result is the same alone and in the mix (its random streams are
+keyed by its own seed, ids and step count).
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import Batch, Slab, default_capacity
+
+
+def footprint(cfg) -> tuple[int, int]:
+    """Worst-case electron and ion slots of a slab: every ion fully stripped."""
+    n_e, n_i = cfg.ncell * cfg.ppc_e, cfg.ncell * cfg.ppc_i
+    return n_e + n_i * (13 - cfg.Z_init), n_i
+
+
+def _summary(ttr: dict, t0: float, t_end: float, n: int) -> dict:
+    v = np.array([ttr[k] for k in sorted(ttr)])
+    return {"slabs": n, "wall_s": t_end - t0, "slabs_per_s": n / (t_end - t0),
+            "ttr_p50_s": float(np.percentile(v, 50)), "ttr_p99_s": float(np.percentile(v, 99)),
+            "ttr_mean_s": float(v.mean())}
+
+
+def serve_batched(trace, tables, init_state, max_slabs: int, slot_cells: int, cap_e: int, cap_i: int,
+                  tick_steps: int = 25, keep=None, diag_bins: int = 64) -> dict:
+    """Continuous batching of `trace` (requests sorted by arrival).
+
+    init_state(cfg) -> ParticleState builds a request's particles on the
+    host.  keep(rid) -> bool selects requests whose final particles are
+    returned (for tests).  Admission: first come first served, while a slot
+    is free and the reserved worst-case footprints fit cap_e / cap_i."""
+    bt = Batch(tables, max_slabs, slot_cells, cap_e, cap_i)
+    pending = list(trace)
+    active = {}                      # slot -> [request, steps left, footprint]
+    res_e = res_i = 0
+    ttr, results, finals = {}, {}, {}
+    t0 = time.perf_counter()
+    try:
+        while pending or active:
+            now = time.perf_counter() - t0
+            # admit what has arrived, in order, while it fits
+            while pending and pending[0].t_arrive <= now:
+                r = pending[0]
+                fe, fi = footprint(r.cfg)
+                if r.cfg.nx > slot_cells or fe > cap_e or fi > cap_i:
+                    raise ValueError(f"request {r.rid} can never fit the batch")
+                if len(active) >= max_slabs or res_e + fe > cap_e or res_i + fi > cap_i:
+                    break
+                slot = bt.admit(r.cfg, init_state(r.cfg), r.pulse)
+                active[slot] = [r, r.nsteps, (fe, fi)]
+                res_e, res_i = res_e + fe, res_i + fi
+                pending.pop(0)
+            if not active:
+                if pending:
+                    time.sleep(max(0.0, pending[0].t_arrive - (time.perf_counter() - t0)))
+                continue
+            n = min(tick_steps, min(a[1] for a in active.values()))
+            bt.step(n)
+            for slot in list(active):
+                a = active[slot]
+                a[1] -= n
+                if a[1] == 0:
+                    r = a[0]
+                    results[r.rid] = bt.diagnostics(slot, n_E=diag_bins)
+                    if keep is not None and keep(r.rid):
+                        finals[r.rid] = (bt.electrons(slot), bt.ions(slot))
+                    ttr[r.rid] = time.perf_counter() - t0 - r.t_arrive
+                    bt.retire(slot)
+                    res_e, res_i = res_e - a[2][0], res_i - a[2][1]
+                    del active[slot]
+        bt.sync()
+        t_end = time.perf_counter()
+    finally:
+        bt.close()
+    out = _summary(ttr, t0, t_end, len(trace))
+    out.update(results=results, finals=finals, ttr=ttr)
+    return out
+
+
+def serve_one_at_a_time(trace, tables, init_state, keep=None, diag_bins: int = 64) -> dict:
+    """The plain form: each request in arrival order gets its own
+    single-slab context, runs to its horizon, and is freed."""
+    ttr, results, finals = {}, {}, {}
+    t0 = time.perf_counter()
+    for r in trace:
+        wait = r.t_arrive - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        st = init_state(r.cfg)
+        ce, ci = default_capacity(st.n_e, st.n_i, r.cfg.Z_init)
+        s = Slab(r.cfg, tables, r.pulse, cap_e=ce, cap_i=ci)
+        try:
+            s.load(st)
+            s.step(r.nsteps)
+            results[r.rid] = s.diagnostics(n_E=diag_bins)
+            if keep is not None and keep(r.rid):
+                finals[r.rid] = (s.electrons(), s.ions())
+        finally:
+            s.close()
+        ttr[r.rid] = time.perf_counter() - t0 - r.t_arrive
+    out = _summary(ttr, t0, time.perf_counter(), len(trace))
+    out.update(results=results, finals=finals, ttr=ttr)
+    return out

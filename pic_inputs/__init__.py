@@ -405,3 +405,65 @@ def random_fields(cfg: SlabConfig, rng_seed: int, e_amp=1e-4, b_amp=1e-4) -> dic
     for k in ("bx", "by", "bz"):
         out[k] = _f32(rng.standard_normal(shp) * b_amp)
     return out
+
+
+# --------------------------------------------------------------------------
+# batched ensembles and served request traces
+# --------------------------------------------------------------------------
+
+
+def _log_uniform(rng, lo, hi, n=None):
+    return np.exp(rng.uniform(math.log(lo), math.log(hi), n))
+
+
+def ensemble_slab(rng, k: int, seed0: int = 1000, cells=(64, 4096), ppc=(32, 512),
+                  I_Wcm2=(1e15, 1e18), hv_eV=(1580.0, 1900.0), dx_nm: float = 2.0) -> tuple:
+    """One member of the batched ensemble: a 1D Al slab with log-uniform cell
+    count and particles per cell (electrons : ions = 4 : 1), log-uniform
+    peak intensity and uniform photon energy; every process on."""
+    nx = int(round(_log_uniform(rng, *cells)))
+    p = int(round(_log_uniform(rng, *ppc)))
+    ppc_i = max(1, int(round(p / 5)))
+    ppc_e = max(1, p - ppc_i)
+    cfg = SlabConfig(name=f"al_1d_{nx}x{dx_nm:g}nm_{ppc_e}e{ppc_i}i", nx=nx, ny=1, dx_nm=dx_nm, dy_nm=dx_nm,
+                     ppc_e=ppc_e, ppc_i=ppc_i, seed=seed0 + k, flags=F_ALL)
+    pl = Pulse(I_peak_Wcm2=float(_log_uniform(rng, *I_Wcm2)), hv_eV=float(rng.uniform(*hv_eV)))
+    return cfg, pl
+
+
+def batched_ensemble(n: int = 256, seed: int = 7, **kw) -> list:
+    """n independent slabs drawn as in ensemble_slab (dx = 2 nm)."""
+    rng = np.random.default_rng(seed)
+    return [ensemble_slab(rng, k, **kw) for k in range(n)]
+
+
+@dataclass
+class Request:
+    """A served slab simulation: arrival time (s), the slab, its pulse and
+    the number of steps to run (horizon / dt)."""
+    rid: int
+    t_arrive: float
+    cfg: SlabConfig
+    pulse: Pulse
+    nsteps: int
+
+
+def request_trace(n: int = 2000, rate_hz: float = 200.0, seed: int = 11, horizon_fs: float = 150.0,
+                  thickness_um=(0.2, 2.0), min_dx_nm: float = 1.0, **kw) -> list:
+    """Poisson arrivals of slab requests.  Each request is an ensemble draw
+    plus a foil thickness ~ U(0.2, 2) um; the cell size is thickness / cells,
+    with the cell count capped so that cells stay at least min_dx_nm wide
+    (finer cells would only multiply the field subcycles)."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate_hz, n))
+    out = []
+    for k in range(n):
+        cfg, pl = ensemble_slab(rng, k, seed0=20000, **kw)
+        thick_nm = 1e3 * float(rng.uniform(*thickness_um))
+        nx = max(2, min(cfg.nx, int(thick_nm / min_dx_nm)))
+        cfg.nx = nx
+        cfg.dx_nm = cfg.dy_nm = thick_nm / nx
+        cfg.name = f"al_1d_{nx}x{cfg.dx_nm:.3g}nm_{cfg.ppc_e}e{cfg.ppc_i}i"
+        out.append(Request(rid=k, t_arrive=float(t[k]), cfg=cfg, pulse=pl,
+                           nsteps=max(1, int(round(horizon_fs / cfg.dt_fs)))))
+    return out
