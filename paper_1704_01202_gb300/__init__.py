@@ -39,7 +39,8 @@ ABI_FUNCTIONS = ["pic_required_bytes", "pic_init", "pic_source", "pic_load_elect
                  "pic_get_current", "pic_launch_count", "pic_free", "pic_last_error", "pic_philox_check",
                  "pic_timing", "pic_batch_required_bytes", "pic_batch_init", "pic_batch_admit",
                  "pic_batch_retire", "pic_batch_slot", "pic_batch_diagnostics", "pic_batch_counts",
-                 "pic_batch_get_electrons", "pic_batch_get_ions", "pic_philox_check_static"]
+                 "pic_batch_get_electrons", "pic_batch_get_ions", "pic_philox_check_static",
+                 "pic_use_graphs", "pic_autotune"]
 
 
 def _sources():
@@ -143,6 +144,8 @@ def lib():
                                            C.POINTER(C.c_uint32), C.c_int]
             L.pic_philox_check_static.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
                                                   C.POINTER(C.c_uint32), C.c_int]
+            L.pic_use_graphs.argtypes = [_P, C.c_int]
+            L.pic_autotune.argtypes = [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]
             L.pic_timing.argtypes = [_P, C.c_int, _D, C.POINTER(C.c_int64)]
             L.pic_batch_required_bytes.restype = C.c_size_t
             L.pic_batch_required_bytes.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
@@ -278,6 +281,18 @@ class Slab:
     @property
     def launches(self):
         return self.L.pic_launch_count(self.h)
+
+    def use_graphs(self, enable: bool):
+        self._check(self.L.pic_use_graphs(self.h, 1 if enable else 0), "pic_use_graphs")
+
+    def autotune(self, enable=None):
+        """Switch the launch-shape autotuner on / off (None: leave it); returns
+        the warps per CTA in use and the step times measured for 1, 2, 4, 8."""
+        w = C.c_int()
+        ms = np.zeros(4, dtype=np.float32)
+        e = -1 if enable is None else (1 if enable else 0)
+        self._check(self.L.pic_autotune(self.h, e, C.byref(w), _p(ms, C.c_float)), "pic_autotune")
+        return w.value, ms
 
     def timing(self, enable=None):
         """Start (True) / stop (False) event timing; with None return the
@@ -423,6 +438,8 @@ class Batch:
     sync = Slab.sync
     timing = Slab.timing
     launches = Slab.launches
+    use_graphs = Slab.use_graphs
+    autotune = Slab.autotune
 
     def admit(self, cfg, st, pulse=None) -> int:
         g, sp = _grid(cfg), _species(cfg)

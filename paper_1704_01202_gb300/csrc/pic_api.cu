@@ -92,6 +92,28 @@ struct pic_ctx {
     bool timing = false;
     std::vector<cudaEvent_t> ev;         // NEV events per recorded step
     size_t ev_used = 0;
+
+    // CUDA graphs of two steps (the buffer swaps of a step pair cancel, so a
+    // pair replays from the same state); one per buffer parity
+    struct StepShape {
+        const void *eA0, *iA0;
+        int cur, ecur, grid_main, wpc, cap_ce, cap_ci, cap_new, nsub;
+        size_t smem_main;
+        bool march, field;
+    };
+    struct StepGraph {
+        StepShape key{};
+        cudaGraphExec_t exec = nullptr;
+        int64_t launches = 0;
+    };
+    bool use_graphs = true;
+    // autotuner: warps per CTA of the cell kernel, chosen per staging size
+    struct Tuned { int ce, ci, wpc; float ms[4]; };
+    std::vector<Tuned> tuned;
+    bool autotune = false;
+    cudaStream_t cap_stream = nullptr;
+    StepGraph graphs[2];
+    int graph_next = 0;
 };
 
 namespace {
@@ -157,23 +179,39 @@ double sigma_table(const pic_ctx *c, int s, double hv)
     return std::exp(std::log(v[lo]) + f * std::log(v[lo + 1] / v[lo]));
 }
 
+// largest warps per CTA of the cell kernel whose staging fits 200 KB
+int max_wpc(int ce, int ci, int cn)
+{
+    const size_t per = warp_mem_bytes(ce, ci, cn);
+    return std::max(1, (int)std::min<size_t>(8, (200 * 1024) / per));
+}
+
+// warps per CTA of the cell kernel: shared memory, grid of resident CTAs
+pic_status set_wpc(pic_ctx *c, int wpc)
+{
+    c->wpc = wpc;
+    c->smem_main = warp_mem_bytes(c->cap_ce, c->cap_ci, c->cap_new) * wpc;
+    CK(cudaFuncSetAttribute(k_cell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max(c->smem_main, c->smem_big)));
+    int occ = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cell, wpc * 32, c->smem_main));
+    c->grid_main = std::max(1, occ) * c->nsm;
+    return PIC_OK;
+}
+
+// Staging capacities of the main cell pass from the largest cells of the
+// last sort (x1.25, powers of two); warps per CTA from the autotuner's
+// choice for these capacities, else the most that fit.
 pic_status configure_cell_launch(pic_ctx *c, int max_e, int max_i)
 {
     int ce = next_pow2(std::max(64, (int)(max_e * 1.25) + 1));
     int ci = next_pow2(std::max(32, (int)(max_i * 1.25) + 1));
     ce = std::min(ce, 1024);
     ci = std::min(ci, 256);
-    int cn = 3 * ci;
-    size_t per = warp_mem_bytes(ce, ci, cn);
-    int wpc = (int)std::min<size_t>(8, (200 * 1024) / per);
-    if (wpc < 1) wpc = 1;
-    c->cap_ce = ce; c->cap_ci = ci; c->cap_new = cn; c->wpc = wpc;
-    c->smem_main = per * wpc;
-    CK(cudaFuncSetAttribute(k_cell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max(c->smem_main, c->smem_big)));
-    int occ = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cell, wpc * 32, c->smem_main));
-    c->grid_main = std::max(1, occ) * c->nsm;
-    return PIC_OK;
+    c->cap_ce = ce; c->cap_ci = ci; c->cap_new = 3 * ci;
+    int wpc = max_wpc(ce, ci, 3 * ci);
+    for (const auto &t : c->tuned)
+        if (t.ce == ce && t.ci == ci) wpc = t.wpc;
+    return set_wpc(c, wpc);
 }
 
 CellArgs cell_args(pic_ctx *c, bool big)
@@ -254,16 +292,39 @@ bool any_active(const pic_ctx *c, unsigned flag, bool need_pulse)
     return false;
 }
 
+// everything a step's launch sequence depends on besides device memory
+pic_ctx::StepShape step_shape(const pic_ctx *c)
+{
+    pic_ctx::StepShape k{};
+    k.eA0 = c->eA0; k.iA0 = c->iA0; k.cur = c->cur; k.ecur = c->ecur;
+    k.grid_main = c->grid_main; k.wpc = c->wpc; k.smem_main = c->smem_main;
+    k.cap_ce = c->cap_ce; k.cap_ci = c->cap_ci; k.cap_new = c->cap_new;
+    k.march = any_active(c, PIC_F_PHOTO, true);
+    k.field = any_active(c, PIC_F_FIELD, false);
+    k.nsub = 1;
+    for (int q = 0; q < c->nslot; ++q)
+        if (c->slabs[q].active && (c->slabs[q].flags & PIC_F_FIELD)) k.nsub = std::max(k.nsub, c->slabs[q].nsub);
+    return k;
+}
+
+bool same_shape(const pic_ctx::StepShape &a, const pic_ctx::StepShape &b)
+{
+    return a.eA0 == b.eA0 && a.iA0 == b.iA0 && a.cur == b.cur && a.ecur == b.ecur && a.grid_main == b.grid_main &&
+           a.wpc == b.wpc && a.smem_main == b.smem_main && a.cap_ce == b.cap_ce && a.cap_ci == b.cap_ci &&
+           a.cap_new == b.cap_new && a.march == b.march && a.field == b.field && a.nsub == b.nsub;
+}
+
 pic_status launch_step(pic_ctx *c)
 {
     cudaStream_t st = c->stream;
+    const pic_ctx::StepShape shape = step_shape(c);
     cudaEvent_t *ev = timing_slot(c);
     if (ev) CK(cudaEventRecord(ev[0], st));
     CK(cudaMemsetAsync(c->cnt_e, 0, sizeof(int) * 4 * (size_t)c->ncell, st));   // cnt_e cnt_i fill_e fill_i
     CK(cudaMemsetAsync(c->counters, 0, sizeof(int) * 5, st));                      // append, work counters, ovf
     CK(cudaMemsetAsync(c->counters + CNT_MAXE, 0, sizeof(int) * 2, st));
     CK(cudaMemsetAsync(c->J, 0, sizeof(unsigned long long) * 3 * (size_t)c->npts, st));
-    if (any_active(c, PIC_F_PHOTO, true)) {
+    if (shape.march) {
         MarchArgs m{c->d_slab, c->d_steps, c->row_slab, c->row_idx, c->photons, c->d_tally};
         k_march<<<c->nrows, 256, (size_t)c->max_row_nx * 8, st>>>(m);
         ++c->launches;
@@ -301,10 +362,8 @@ pic_status launch_step(pic_ctx *c)
     k_scatter<<<sgrid, 256, 0, st>>>(si);
     c->launches += 2;
     if (ev) CK(cudaEventRecord(ev[4], st));
-    if (any_active(c, PIC_F_FIELD, false)) {
-        int nsub = 1;
-        for (int k = 0; k < c->nslot; ++k)
-            if (c->slabs[k].active && (c->slabs[k].flags & PIC_F_FIELD)) nsub = std::max(nsub, c->slabs[k].nsub);
+    if (shape.field) {
+        const int nsub = shape.nsub;
         FieldArgs f{};
         f.slabs = c->d_slab; f.pt_slab = c->pt_slab; f.npts = c->npts; f.B = c->B; f.J = c->J;
         int fg = std::min((c->npts + 255) / 256, c->nsm * 16);
@@ -850,6 +909,89 @@ pic_status diag_slot(pic_ctx *c, int slot, pic_diag *out)
     return read_device_error(c);
 }
 
+// Capture two steps into a graph (on a private stream: the context stream
+// may be the legacy default stream, which cannot be captured).  The host
+// side of the pair (buffer swaps) is undone, so the context is left as it
+// was; the graph replays the pair.
+pic_status capture_pair(pic_ctx *c, pic_ctx::StepGraph &g)
+{
+    if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    float4 *saved[8] = {c->eA0, c->eA1, c->eB0, c->eB1, c->iA0, c->iA1, c->iB0, c->iB1};
+    const int cur = c->cur, ecur = c->ecur;
+    const int64_t l0 = c->launches;
+    const pic_ctx::StepShape key = step_shape(c);
+    cudaStream_t user = c->stream;
+    c->stream = c->cap_stream;
+    cudaGraph_t graph = nullptr;
+    pic_status r = PIC_OK;
+    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        r = launch_step(c);
+        if (r == PIC_OK) r = launch_step(c);
+        cudaError_t e2 = cudaStreamEndCapture(c->stream, &graph);
+        if (e2 != cudaSuccess && r == PIC_OK) r = cuda_fail(c, e2, "cudaStreamEndCapture");
+    } else {
+        r = cuda_fail(c, e, "cudaStreamBeginCapture");
+    }
+    c->stream = user;
+    c->eA0 = saved[0]; c->eA1 = saved[1]; c->eB0 = saved[2]; c->eB1 = saved[3];
+    c->iA0 = saved[4]; c->iA1 = saved[5]; c->iB0 = saved[6]; c->iB1 = saved[7];
+    c->cur = cur; c->ecur = ecur;
+    const int64_t nl = c->launches - l0;
+    c->launches = l0;
+    if (r == PIC_OK) {
+        if (g.exec) { cudaGraphExecDestroy(g.exec); g.exec = nullptr; }
+        e = cudaGraphInstantiate(&g.exec, graph, 0);
+        if (e != cudaSuccess) { g.exec = nullptr; r = cuda_fail(c, e, "cudaGraphInstantiate"); }
+        g.key = key;
+        g.launches = nl;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    return r;
+}
+
+pic_ctx::StepGraph *pair_graph(pic_ctx *c, pic_status &r)
+{
+    const pic_ctx::StepShape key = step_shape(c);
+    for (auto &g : c->graphs)
+        if (g.exec && same_shape(g.key, key)) return &g;
+    pic_ctx::StepGraph &g = c->graphs[c->graph_next];
+    c->graph_next ^= 1;
+    r = capture_pair(c, g);
+    return r == PIC_OK ? &g : nullptr;
+}
+
+// Autotuner: time real steps with 1, 2, 4 and 8 warps per CTA (as many as
+// fit) for the current staging size and keep the fastest.  The launch shape
+// changes no result (every decision is keyed by particle and cell), so the
+// steps it times are steps of the simulation; it uses up to four of the n
+// steps asked for (fewer when n is smaller: the untried shapes are skipped).
+pic_status tune_step(pic_ctx *c, int n, int &k)
+{
+    pic_ctx::Tuned t{c->cap_ce, c->cap_ci, c->wpc, {0, 0, 0, 0}};
+    const int top = max_wpc(c->cap_ce, c->cap_ci, c->cap_new);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 3.4e38f;
+    pic_status r = PIC_OK;
+    for (int q = 0, w = 1; q < 4 && w <= top && k < n && r == PIC_OK; ++q, w *= 2) {
+        if ((r = set_wpc(c, w)) != PIC_OK) break;
+        cudaEventRecord(e0, c->stream);
+        if ((r = launch_step(c)) != PIC_OK) break;
+        cudaEventRecord(e1, c->stream);
+        ++k;
+        if (cudaEventSynchronize(e1) != cudaSuccess) { r = fail(c, PIC_ERR_CUDA, "autotune timing"); break; }
+        cudaEventElapsedTime(&t.ms[q], e0, e1);
+        if (t.ms[q] < best) { best = t.ms[q]; t.wpc = w; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (r != PIC_OK) return r;
+    if (k > 0 && (1 << k) > top) c->tuned.push_back(t);   // every shape that fits was tried
+    return set_wpc(c, t.wpc);
+}
+
 pic_status step_n(pic_ctx *c, int n)
 {
     pic_status r = apply_pending(c);
@@ -863,7 +1005,24 @@ pic_status step_n(pic_ctx *c, int n)
         if (r != PIC_OK) return r;
     }
     c->launches = 0;
-    for (int k = 0; k < n; ++k) {
+    int k = 0;
+    if (c->autotune) {
+        bool known = false;
+        for (const auto &t : c->tuned) known |= t.ce == c->cap_ce && t.ci == c->cap_ci;
+        if (!known) {
+            r = tune_step(c, n, k);
+            if (r != PIC_OK) return r;
+        }
+    }
+    if (c->use_graphs && !c->timing && n - k >= 2) {
+        pic_ctx::StepGraph *g = pair_graph(c, r);
+        if (!g) return r;
+        for (; k + 2 <= n; k += 2) {   // pairs of the remaining steps
+            CK(cudaGraphLaunch(g->exec, c->stream));
+            c->launches += g->launches;
+        }
+    }
+    for (; k < n; ++k) {
         r = launch_step(c);
         if (r != PIC_OK) return r;
     }
@@ -1195,6 +1354,27 @@ pic_status pic_batch_get_ions(pic_ctx *c, int slot, double *X, double *Y, float 
 
 int64_t pic_launch_count(const pic_ctx *c) { return c ? c->launches : 0; }
 
+pic_status pic_autotune(pic_ctx *c, int enable, int *wpc_out, float *ms_out)
+{
+    if (!c) return PIC_ERR_ARG;
+    if (enable >= 0) c->autotune = enable != 0;
+    if (wpc_out) *wpc_out = c->wpc;
+    if (ms_out) {
+        for (int q = 0; q < 4; ++q) ms_out[q] = 0.0f;
+        for (const auto &t : c->tuned)
+            if (t.ce == c->cap_ce && t.ci == c->cap_ci)
+                for (int q = 0; q < 4; ++q) ms_out[q] = t.ms[q];
+    }
+    return PIC_OK;
+}
+
+pic_status pic_use_graphs(pic_ctx *c, int enable)
+{
+    if (!c) return PIC_ERR_ARG;
+    c->use_graphs = enable != 0;
+    return PIC_OK;
+}
+
 pic_status pic_timing(pic_ctx *c, int enable, double *ms_out, int64_t *nsteps)
 {
     if (!c) return PIC_ERR_ARG;
@@ -1225,6 +1405,9 @@ pic_status pic_free(pic_ctx *c)
     else cudaDeviceSynchronize();
     if (c->own_arena && c->arena) cudaFree(c->arena);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    for (auto &g : c->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
     return PIC_OK;
 }

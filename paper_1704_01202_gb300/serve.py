@@ -38,9 +38,9 @@ def serve_batched(trace, tables, init_state, max_slabs: int, slot_cells: int, ca
                   tick_steps: int = 25, keep=None, diag_bins: int = 64) -> dict:
     """Continuous batching of `trace` (requests sorted by arrival).
 
-    init_state(cfg) -> ParticleState builds a request's particles on the
-    host.  keep(rid) -> bool selects requests whose final particles are
-    returned (for tests).  Admission: first come first served, while a slot
+    init_state(request) -> ParticleState gives a request's particles (the
+    request payload, on the host).  keep(rid) -> bool selects requests whose
+    final particles are returned (for tests).  Admission: first come first served, while a slot
     is free and the reserved worst-case footprints fit cap_e / cap_i."""
     bt = Batch(tables, max_slabs, slot_cells, cap_e, cap_i)
     pending = list(trace)
@@ -59,7 +59,7 @@ def serve_batched(trace, tables, init_state, max_slabs: int, slot_cells: int, ca
                     raise ValueError(f"request {r.rid} can never fit the batch")
                 if len(active) >= max_slabs or res_e + fe > cap_e or res_i + fi > cap_i:
                     break
-                slot = bt.admit(r.cfg, init_state(r.cfg), r.pulse)
+                slot = bt.admit(r.cfg, init_state(r), r.pulse)
                 active[slot] = [r, r.nsteps, (fe, fi)]
                 res_e, res_i = res_e + fe, res_i + fi
                 pending.pop(0)
@@ -99,7 +99,7 @@ def serve_one_at_a_time(trace, tables, init_state, keep=None, diag_bins: int = 6
         wait = r.t_arrive - (time.perf_counter() - t0)
         if wait > 0:
             time.sleep(wait)
-        st = init_state(r.cfg)
+        st = init_state(r)
         ce, ci = default_capacity(st.n_e, st.n_i, r.cfg.Z_init)
         s = Slab(r.cfg, tables, r.pulse, cap_e=ce, cap_i=ci)
         try:

@@ -37,9 +37,10 @@ def test_served_results_equal_alone():
     # three slots and room for about half the trace: requests queue, slots
     # and space are reused
     cap_e, cap_i = (max(int(fp[:, q].sum() // 2), int(fp[:, q].max())) for q in (0, 1))
-    out = serve.serve_batched(tr, tab, P.init_particles, max_slabs=3, slot_cells=96,
+    init = lambda r: P.init_particles(r.cfg)  # noqa: E731
+    out = serve.serve_batched(tr, tab, init, max_slabs=3, slot_cells=96,
                               cap_e=cap_e, cap_i=cap_i, tick_steps=4, keep=lambda rid: True)
-    ref = serve.serve_one_at_a_time(tr, tab, P.init_particles, keep=lambda rid: True)
+    ref = serve.serve_one_at_a_time(tr, tab, init, keep=lambda rid: True)
     assert sorted(out["results"]) == [r.rid for r in tr]
     for r in tr:
         a, b = out["results"][r.rid], ref["results"][r.rid]
