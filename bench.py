@@ -180,9 +180,14 @@ def run_gpu(args):
     slab.load(st)
     stream = torch.cuda.current_stream()
 
+    # launch-shape autotuning on the first steps (real steps of the run)
+    slab.autotune(True)
+    slab.step(4)
     for _ in range(args.warmup):
         slab.step(1)
+    slab.autotune(False)
     slab.sync()
+    tuned = slab.autotune()
     ne0, ni0 = slab.counts()
     if dist:
         dist.barrier()
@@ -242,6 +247,7 @@ def run_gpu(args):
                           "l2": "state (1.3 GB) larger than L2; no flush", "parallelism": "replicas"},
                "roofline": roof, "step_hbm_gbs": step_gbs, "cpu_baseline": cb, "e2e": e2e,
                "gpu_launches": int(launches), "clocks": clk, "kernel_ms": {k: v / max(nrec, 1) for k, v in tms.items()},
+               "autotune": {"cell_warps_per_cta": tuned[0], "step_ms_1_2_4_8": [float(x) for x in tuned[1]]},
                "ensemble": ensemble, "served": served}
         print(json.dumps(out))
     if dist:
@@ -263,8 +269,11 @@ def run_ensemble(pkg, tab, args, rank):
     bt = pkg.Batch(tab, len(ens), slot_cells, cap_e, cap_i)
     for (c, pl), st in zip(ens, states):
         bt.admit(c, st, pl)
-    bt.step(args.warmup)
+    bt.autotune(True)
+    bt.step(4 + args.warmup)
+    bt.autotune(False)
     bt.sync()
+    tuned = bt.autotune()
     n0 = sum(sum(bt.counts(k)) for k in range(len(ens)))
     stream = torch.cuda.current_stream()
     bt.timing(True)
@@ -284,7 +293,8 @@ def run_ensemble(pkg, tab, args, rank):
                         "I log-uniform 1e15-1e18 W/cm^2, hv U(1.58, 1.90) keV",
             "slabs": len(ens), "slot_cells": slot_cells, "particles": int(n_mean), "steps": args.steps,
             "value": n_mean * args.steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / args.steps,
-            "gpu_launches": int(launches), "kernel_ms": {k: v / max(nrec, 1) for k, v in tms.items()}}
+            "gpu_launches": int(launches), "kernel_ms": {k: v / max(nrec, 1) for k, v in tms.items()},
+            "autotune": {"cell_warps_per_cta": tuned[0], "step_ms_1_2_4_8": [float(x) for x in tuned[1]]}}
 
 
 def run_served(pkg, tab, args):

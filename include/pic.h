@@ -238,10 +238,11 @@ int64_t pic_launch_count(const pic_ctx *c);
 pic_status pic_use_graphs(pic_ctx *c, int enable);
 
 /* Launch-shape autotuner (default off).  enable = 1: whenever a pic_step
- * call meets staging sizes not tuned before, its first steps run the cell
- * kernel with 1, 2, 4 and 8 warps per CTA (as many as fit in shared memory),
- * timed with CUDA events, and the fastest is kept for those sizes.  These are
- * steps of the simulation: the launch shape changes no result.  enable = 0
+ * call meets staging sizes whose tuning is not finished, its first steps run
+ * the cell kernel with the untried ones of 1, 2, 4 and 8 warps per CTA (as
+ * many as fit in shared memory), one step each, timed with CUDA events; once
+ * all are timed the fastest is kept for those sizes.  These are steps of the
+ * simulation: the launch shape changes no result.  enable = 0
  * stops tuning (choices made are kept); -1 leaves it as is.  wpc_out (may be
  * NULL) gets the warps per CTA in use; ms_out (4 floats, may be NULL) the
  * step times measured for 1, 2, 4, 8 warps at the current sizes (0: not

@@ -108,7 +108,7 @@ struct pic_ctx {
     };
     bool use_graphs = true;
     // autotuner: warps per CTA of the cell kernel, chosen per staging size
-    struct Tuned { int ce, ci, wpc; float ms[4]; };
+    struct Tuned { int ce, ci, wpc; float ms[4]; unsigned tried; bool done = false; };
     std::vector<Tuned> tuned;
     bool autotune = false;
     cudaStream_t cap_stream = nullptr;
@@ -210,7 +210,7 @@ pic_status configure_cell_launch(pic_ctx *c, int max_e, int max_i)
     c->cap_ce = ce; c->cap_ci = ci; c->cap_new = 3 * ci;
     int wpc = max_wpc(ce, ci, 3 * ci);
     for (const auto &t : c->tuned)
-        if (t.ce == ce && t.ci == ci) wpc = t.wpc;
+        if (t.ce == ce && t.ci == ci && t.done) wpc = t.wpc;
     return set_wpc(c, wpc);
 }
 
@@ -964,32 +964,48 @@ pic_ctx::StepGraph *pair_graph(pic_ctx *c, pic_status &r)
 // Autotuner: time real steps with 1, 2, 4 and 8 warps per CTA (as many as
 // fit) for the current staging size and keep the fastest.  The launch shape
 // changes no result (every decision is keyed by particle and cell), so the
-// steps it times are steps of the simulation; it uses up to four of the n
-// steps asked for (fewer when n is smaller: the untried shapes are skipped).
+// steps it times are steps of the simulation.  Shapes not yet tried are
+// tried on the first steps of this call (one step each, as many as the call
+// has); the search goes on in later calls until every shape has been timed.
+pic_ctx::Tuned *tuned_entry(pic_ctx *c)
+{
+    for (auto &t : c->tuned)
+        if (t.ce == c->cap_ce && t.ci == c->cap_ci) return &t;
+    return nullptr;
+}
+
 pic_status tune_step(pic_ctx *c, int n, int &k)
 {
-    pic_ctx::Tuned t{c->cap_ce, c->cap_ci, c->wpc, {0, 0, 0, 0}};
+    pic_ctx::Tuned *t = tuned_entry(c);
+    if (!t) {
+        c->tuned.push_back(pic_ctx::Tuned{c->cap_ce, c->cap_ci, c->wpc, {0, 0, 0, 0}, 0});
+        t = &c->tuned.back();
+    }
     const int top = max_wpc(c->cap_ce, c->cap_ci, c->cap_new);
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    float best = 3.4e38f;
     pic_status r = PIC_OK;
     for (int q = 0, w = 1; q < 4 && w <= top && k < n && r == PIC_OK; ++q, w *= 2) {
+        if (t->tried & (1 << q)) continue;
         if ((r = set_wpc(c, w)) != PIC_OK) break;
         cudaEventRecord(e0, c->stream);
         if ((r = launch_step(c)) != PIC_OK) break;
         cudaEventRecord(e1, c->stream);
         ++k;
         if (cudaEventSynchronize(e1) != cudaSuccess) { r = fail(c, PIC_ERR_CUDA, "autotune timing"); break; }
-        cudaEventElapsedTime(&t.ms[q], e0, e1);
-        if (t.ms[q] < best) { best = t.ms[q]; t.wpc = w; }
+        cudaEventElapsedTime(&t->ms[q], e0, e1);
+        t->tried |= 1 << q;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (r != PIC_OK) return r;
-    if (k > 0 && (1 << k) > top) c->tuned.push_back(t);   // every shape that fits was tried
-    return set_wpc(c, t.wpc);
+    float best = 3.4e38f;
+    for (int q = 0, w = 1; q < 4; ++q, w *= 2)
+        if ((t->tried & (1 << q)) && t->ms[q] < best) { best = t->ms[q]; t->wpc = w; }
+    t->done = true;
+    for (int q = 0, w = 1; q < 4 && w <= top; ++q, w *= 2) t->done &= (t->tried >> q) & 1;
+    return set_wpc(c, t->wpc);
 }
 
 pic_status step_n(pic_ctx *c, int n)
@@ -1007,9 +1023,8 @@ pic_status step_n(pic_ctx *c, int n)
     c->launches = 0;
     int k = 0;
     if (c->autotune) {
-        bool known = false;
-        for (const auto &t : c->tuned) known |= t.ce == c->cap_ce && t.ci == c->cap_ci;
-        if (!known) {
+        const pic_ctx::Tuned *t = tuned_entry(c);
+        if (!t || !t->done) {
             r = tune_step(c, n, k);
             if (r != PIC_OK) return r;
         }
