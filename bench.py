@@ -182,7 +182,7 @@ def run_gpu(args):
 
     # launch-shape autotuning on the first steps (real steps of the run)
     slab.autotune(True)
-    slab.step(4)
+    slab.step(9)
     for _ in range(args.warmup):
         slab.step(1)
     slab.autotune(False)
@@ -247,7 +247,7 @@ def run_gpu(args):
                           "l2": "state (1.3 GB) larger than L2; no flush", "parallelism": "replicas"},
                "roofline": roof, "step_hbm_gbs": step_gbs, "cpu_baseline": cb, "e2e": e2e,
                "gpu_launches": int(launches), "clocks": clk, "kernel_ms": {k: v / max(nrec, 1) for k, v in tms.items()},
-               "autotune": {"cell_warps_per_cta": tuned[0], "step_ms_1_2_4_8": [float(x) for x in tuned[1]]},
+               "autotune": {"cell_warps_per_cta": tuned[0], "cell_ms_1_2_4_8": [float(x) for x in tuned[1]]},
                "ensemble": ensemble, "served": served}
         print(json.dumps(out))
     if dist:
@@ -270,7 +270,7 @@ def run_ensemble(pkg, tab, args, rank):
     for (c, pl), st in zip(ens, states):
         bt.admit(c, st, pl)
     bt.autotune(True)
-    bt.step(4 + args.warmup)
+    bt.step(9 + args.warmup)
     bt.autotune(False)
     bt.sync()
     tuned = bt.autotune()
@@ -294,7 +294,7 @@ def run_ensemble(pkg, tab, args, rank):
             "slabs": len(ens), "slot_cells": slot_cells, "particles": int(n_mean), "steps": args.steps,
             "value": n_mean * args.steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / args.steps,
             "gpu_launches": int(launches), "kernel_ms": {k: v / max(nrec, 1) for k, v in tms.items()},
-            "autotune": {"cell_warps_per_cta": tuned[0], "step_ms_1_2_4_8": [float(x) for x in tuned[1]]}}
+            "autotune": {"cell_warps_per_cta": tuned[0], "cell_ms_1_2_4_8": [float(x) for x in tuned[1]]}}
 
 
 def run_served(pkg, tab, args):

@@ -238,14 +238,15 @@ int64_t pic_launch_count(const pic_ctx *c);
 pic_status pic_use_graphs(pic_ctx *c, int enable);
 
 /* Launch-shape autotuner (default off).  enable = 1: whenever a pic_step
- * call meets staging sizes whose tuning is not finished, its first steps run
- * the cell kernel with the untried ones of 1, 2, 4 and 8 warps per CTA (as
- * many as fit in shared memory), one step each, timed with CUDA events; once
- * all are timed the fastest is kept for those sizes.  These are steps of the
- * simulation: the launch shape changes no result.  enable = 0
- * stops tuning (choices made are kept); -1 leaves it as is.  wpc_out (may be
- * NULL) gets the warps per CTA in use; ms_out (4 floats, may be NULL) the
- * step times measured for 1, 2, 4, 8 warps at the current sizes (0: not
+ * call meets tier-0 staging sizes whose tuning is not finished, its first
+ * steps run the cell kernel with 1, 2, 4 and 8 warps per CTA (as many as fit
+ * in shared memory), each twice in the order 1 2 4 8 8 4 2 1, timing the
+ * cell kernels with CUDA events; the fastest mean is kept for those sizes.
+ * The context's first step is not timed.  These are steps of the
+ * simulation: the launch shape changes no result.  enable = 0 stops tuning
+ * (choices made are kept); -1 leaves it as is.  wpc_out (may be NULL) gets
+ * the warps per CTA in use; ms_out (4 floats, may be NULL) the mean cell
+ * kernel times measured for 1, 2, 4, 8 warps at the current sizes (0: not
  * tried). */
 pic_status pic_autotune(pic_ctx *c, int enable, int *wpc_out, float *ms_out);
 

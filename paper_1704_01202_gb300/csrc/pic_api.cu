@@ -28,8 +28,10 @@ using namespace pic;
 
 namespace {
 
-constexpr int CNT_APPEND = 0, CNT_WORK = 1, CNT_WORK_BIG = 2, CNT_OVF = 3, CNT_WORK_PUSH = 4, CNT_ERR = 5,
-              CNT_MAXE = 6, CNT_MAXI = 7, CNT_NLOAD = 8, NCOUNTERS = 16;
+// device counters; [0, CNT_STEP_ZERO) are cleared at the start of a step
+constexpr int CNT_APPEND = 0, CNT_WORK = 1, CNT_WORK_T1 = 2, CNT_WORK_BIG = 3, CNT_OVF = 4, CNT_OVF2 = 5,
+              CNT_WORK_PUSH = 6, CNT_STEP_ZERO = 7, CNT_ERR = 8, CNT_MAXE = 9, CNT_MAXI = 10, CNT_NLOAD = 11,
+              CNT_HIST_E = 16, CNT_HIST_I = CNT_HIST_E + NHIST, NCOUNTERS = CNT_HIST_I + NHIST;
 constexpr int NEV = 6;   // timing events per step
 constexpr int BIG_CE = 2048, BIG_CI = 512;
 
@@ -71,7 +73,7 @@ struct pic_ctx {
     int *csE[2], *csI[2];
     int cur = 0;
     int *cnt_e, *cnt_i, *fill_e, *fill_i, *bsum_e, *bsum_i;
-    int *counters, *ovf_list, *cell_slab, *pt_slab, *row_slab, *row_idx;
+    int *counters, *ovf_list, *ovf_list2, *cell_slab, *pt_slab, *row_slab, *row_idx;
     SlabDev *d_slab;                     // [nslot]
     unsigned *d_steps;                   // [nslot]
     SlabTally *d_tally;                  // [nslot]
@@ -83,9 +85,13 @@ struct pic_ctx {
     ph2 *photons;
     double *diag_buf;
 
+    // cell-kernel tiers: tier 0 takes every cell with the staging sizes
+    // below; cells that do not fit go to tier 1 (sized for the largest
+    // cells, when that is larger), then to the one-warp large-cell pass
     int cap_ce = 128, cap_ci = 32, cap_new = 96, wpc = 4;
-    size_t smem_main = 0, smem_big = 0;
-    int nsm = 0, grid_main = 0, grid_big = 0, grid_push = 0;
+    int t1_ce = 0, t1_ci = 0, t1_wpc = 1;    // t1_ce == 0: no tier 1
+    size_t smem_main = 0, smem_t1 = 0, smem_big = 0;
+    int nsm = 0, grid_main = 0, grid_t1 = 0, grid_big = 0, grid_push = 0;
     int64_t launches = 0;
     bool loaded_e = false, loaded_i = false;
     std::vector<double> hv_tab, sigma;   // host copy of the photoionization table
@@ -97,7 +103,7 @@ struct pic_ctx {
     // pair replays from the same state); one per buffer parity
     struct StepShape {
         const void *eA0, *iA0;
-        int cur, ecur, grid_main, wpc, cap_ce, cap_ci, cap_new, nsub;
+        int cur, ecur, grid_main, wpc, cap_ce, cap_ci, cap_new, nsub, t1_ce, t1_ci, t1_wpc, grid_t1;
         size_t smem_main;
         bool march, field;
     };
@@ -108,7 +114,10 @@ struct pic_ctx {
     };
     bool use_graphs = true;
     // autotuner: warps per CTA of the cell kernel, chosen per staging size
-    struct Tuned { int ce, ci, wpc; float ms[4]; unsigned tried; bool done = false; };
+    struct Tuned { int ce, ci, wpc; float ms[4]; unsigned tried; bool done = false; };  // ms: mean of two
+    cudaEvent_t cell_ev[2] = {nullptr, nullptr};    // around the cell kernels while tuning
+    bool cell_ev_on = false;
+    int64_t steps_done = 0;
     std::vector<Tuned> tuned;
     bool autotune = false;
     cudaStream_t cap_stream = nullptr;
@@ -151,7 +160,7 @@ size_t arena_need(int ncell, int npts, int nblk, int cap_e, int cap_i, int nslot
     b += 4 * al((size_t)cap_e * 16) + 2 * al((size_t)cap_e * 4);
     b += 4 * al((size_t)cap_i * 16) + 2 * al((size_t)cap_i * 4);
     b += 4 * al((size_t)(ncell + 1) * 4) + al((size_t)ncell * 16) + 2 * al((size_t)nblk * 4);
-    b += al(NCOUNTERS * 4) + al((size_t)ncell * 4) * 2;
+    b += al(NCOUNTERS * 4) + al((size_t)ncell * 4) * 3;
     b += al(sizeof(SlabDev) * (size_t)nslot) + al(4 * (size_t)nslot) + al(sizeof(SlabTally) * (size_t)nslot)
          + al(sizeof(Tables)) + al(sizeof(EosTable));
     b += 3 * al((size_t)npts * 3 * 4) + al((size_t)npts * 3 * 8) + al((size_t)npts * 4);
@@ -186,35 +195,79 @@ int max_wpc(int ce, int ci, int cn)
     return std::max(1, (int)std::min<size_t>(8, (200 * 1024) / per));
 }
 
-// warps per CTA of the cell kernel: shared memory, grid of resident CTAs
+pic_status cell_smem_attr(pic_ctx *c)
+{
+    const size_t m = std::max(std::max(c->smem_main, c->smem_t1), c->smem_big);
+    CK(cudaFuncSetAttribute(k_cell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m));
+    return PIC_OK;
+}
+
+// warps per CTA of the tier-0 cell launch: shared memory, grid of resident CTAs
 pic_status set_wpc(pic_ctx *c, int wpc)
 {
     c->wpc = wpc;
     c->smem_main = warp_mem_bytes(c->cap_ce, c->cap_ci, c->cap_new) * wpc;
-    CK(cudaFuncSetAttribute(k_cell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max(c->smem_main, c->smem_big)));
+    pic_status r = cell_smem_attr(c);
+    if (r != PIC_OK) return r;
     int occ = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cell, wpc * 32, c->smem_main));
     c->grid_main = std::max(1, occ) * c->nsm;
     return PIC_OK;
 }
 
-// Staging capacities of the main cell pass from the largest cells of the
-// last sort (x1.25, powers of two); warps per CTA from the autotuner's
-// choice for these capacities, else the most that fit.
-pic_status configure_cell_launch(pic_ctx *c, int max_e, int max_i)
+// smallest power-of-two capacity (>= lo) that holds `share` of the non-empty
+// cells of a histogram (bins of bit length)
+int cap_for_share(const int *hist, double share, int lo)
 {
-    int ce = next_pow2(std::max(64, (int)(max_e * 1.25) + 1));
-    int ci = next_pow2(std::max(32, (int)(max_i * 1.25) + 1));
-    ce = std::min(ce, 1024);
-    ci = std::min(ci, 256);
+    long long tot = 0;
+    for (int b = 1; b < NHIST; ++b) tot += hist[b];
+    if (tot == 0) return lo;
+    long long acc = 0;
+    for (int b = 1; b < NHIST; ++b) {
+        acc += hist[b];
+        if (acc >= share * tot) return std::max(lo, 1 << b);   // bin b holds n < 2^b
+    }
+    return std::max(lo, 1 << (NHIST - 1));
+}
+
+// Staging sizes of the cell tiers from the last sort's cell populations:
+// tier 0 holds 90 % of the cells of each species (powers of two, at least
+// 64 electrons / 32 ions); tier 1 the largest cells x 1.25 (at most 1024 /
+// 256), launched only when larger than tier 0.  Warps per CTA of tier 0 from
+// the autotuner's choice for its sizes, else the most that fit.
+pic_status configure_cell_launch(pic_ctx *c, const int *hist_e, const int *hist_i, int max_e, int max_i)
+{
+    int ce = std::min(cap_for_share(hist_e, 0.9, 64), 1024);
+    int ci = std::min(cap_for_share(hist_i, 0.9, 32), 256);
+    int ce1 = std::min(next_pow2(std::max(64, (int)(max_e * 1.25) + 1)), 1024);
+    int ci1 = std::min(next_pow2(std::max(32, (int)(max_i * 1.25) + 1)), 256);
+    ce = std::min(ce, ce1);
+    ci = std::min(ci, ci1);
     c->cap_ce = ce; c->cap_ci = ci; c->cap_new = 3 * ci;
+    if (ce1 > ce || ci1 > ci) {
+        c->t1_ce = ce1; c->t1_ci = ci1;
+        c->t1_wpc = max_wpc(ce1, ci1, 3 * ci1);
+        c->smem_t1 = warp_mem_bytes(ce1, ci1, 3 * ci1) * c->t1_wpc;
+    } else {
+        c->t1_ce = c->t1_ci = 0;
+        c->smem_t1 = 0;
+    }
     int wpc = max_wpc(ce, ci, 3 * ci);
     for (const auto &t : c->tuned)
         if (t.ce == ce && t.ci == ci && t.done) wpc = t.wpc;
-    return set_wpc(c, wpc);
+    pic_status r = set_wpc(c, wpc);
+    if (r != PIC_OK || !c->t1_ce) return r;
+    int occ = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cell, c->t1_wpc * 32, c->smem_t1));
+    c->grid_t1 = std::max(1, occ) * c->nsm;
+    return PIC_OK;
 }
 
-CellArgs cell_args(pic_ctx *c, bool big)
+// arguments of one cell-kernel launch: tier 0 (all cells), tier 1 (the
+// cells tier 0 could not stage) or the large-cell pass (the rest)
+enum CellTier { TIER0, TIER1, TIER_BIG };
+
+CellArgs cell_args(pic_ctx *c, CellTier tier)
 {
     CellArgs a{};
     a.e0 = c->eA0; a.e1 = c->eA1; a.ekey = c->ekey; a.cs_e = c->csE[c->cur];
@@ -236,14 +289,21 @@ CellArgs cell_args(pic_ctx *c, bool big)
     a.tab = c->d_tab;
     a.eos = c->d_eos;
     a.err = c->counters + CNT_ERR;
-    if (!big) {
+    const bool t1 = c->t1_ce > 0;
+    if (tier == TIER0) {
         a.work = c->counters + CNT_WORK;
         a.list = nullptr; a.n_list = nullptr;
         a.ovf_list = c->ovf_list; a.ovf_count = c->counters + CNT_OVF;
         a.cap_ce = c->cap_ce; a.cap_ci = c->cap_ci; a.cap_new = c->cap_new;
+    } else if (tier == TIER1) {
+        a.work = c->counters + CNT_WORK_T1;
+        a.list = c->ovf_list; a.n_list = c->counters + CNT_OVF;
+        a.ovf_list = c->ovf_list2; a.ovf_count = c->counters + CNT_OVF2;
+        a.cap_ce = c->t1_ce; a.cap_ci = c->t1_ci; a.cap_new = 3 * c->t1_ci;
     } else {
         a.work = c->counters + CNT_WORK_BIG;
-        a.list = c->ovf_list; a.n_list = c->counters + CNT_OVF;
+        a.list = t1 ? c->ovf_list2 : c->ovf_list;
+        a.n_list = c->counters + (t1 ? CNT_OVF2 : CNT_OVF);
         a.ovf_list = nullptr; a.ovf_count = nullptr;
         a.cap_ce = BIG_CE; a.cap_ci = BIG_CI; a.cap_new = 3 * BIG_CI;
     }
@@ -254,8 +314,18 @@ pic_status run_scan(pic_ctx *c, int species_mask, int dst)
 {
     ScanArgs s{};
     int k = 0;
-    if (species_mask & 1) { s.cnt[k] = c->cnt_e; s.cs[k] = c->csE[dst]; s.bsum[k] = c->bsum_e; s.maxc[k] = c->counters + CNT_MAXE; ++k; }
-    if (species_mask & 2) { s.cnt[k] = c->cnt_i; s.cs[k] = c->csI[dst]; s.bsum[k] = c->bsum_i; s.maxc[k] = c->counters + CNT_MAXI; ++k; }
+    if (species_mask & 1) {
+        s.cnt[k] = c->cnt_e; s.cs[k] = c->csE[dst]; s.bsum[k] = c->bsum_e;
+        s.maxc[k] = c->counters + CNT_MAXE; s.hist[k] = c->counters + CNT_HIST_E; ++k;
+    }
+    if (species_mask & 2) {
+        s.cnt[k] = c->cnt_i; s.cs[k] = c->csI[dst]; s.bsum[k] = c->bsum_i;
+        s.maxc[k] = c->counters + CNT_MAXI; s.hist[k] = c->counters + CNT_HIST_I; ++k;
+    }
+    for (int q = 0; q < k; ++q) {
+        CK(cudaMemsetAsync(s.maxc[q], 0, sizeof(int), c->stream));
+        CK(cudaMemsetAsync(s.hist[q], 0, sizeof(int) * NHIST, c->stream));
+    }
     s.n = c->ncell;
     s.nblk = c->nblk;
     dim3 g1(c->nblk, k);
@@ -299,6 +369,7 @@ pic_ctx::StepShape step_shape(const pic_ctx *c)
     k.eA0 = c->eA0; k.iA0 = c->iA0; k.cur = c->cur; k.ecur = c->ecur;
     k.grid_main = c->grid_main; k.wpc = c->wpc; k.smem_main = c->smem_main;
     k.cap_ce = c->cap_ce; k.cap_ci = c->cap_ci; k.cap_new = c->cap_new;
+    k.t1_ce = c->t1_ce; k.t1_ci = c->t1_ci; k.t1_wpc = c->t1_wpc; k.grid_t1 = c->grid_t1;
     k.march = any_active(c, PIC_F_PHOTO, true);
     k.field = any_active(c, PIC_F_FIELD, false);
     k.nsub = 1;
@@ -311,7 +382,8 @@ bool same_shape(const pic_ctx::StepShape &a, const pic_ctx::StepShape &b)
 {
     return a.eA0 == b.eA0 && a.iA0 == b.iA0 && a.cur == b.cur && a.ecur == b.ecur && a.grid_main == b.grid_main &&
            a.wpc == b.wpc && a.smem_main == b.smem_main && a.cap_ce == b.cap_ce && a.cap_ci == b.cap_ci &&
-           a.cap_new == b.cap_new && a.march == b.march && a.field == b.field && a.nsub == b.nsub;
+           a.cap_new == b.cap_new && a.march == b.march && a.field == b.field && a.nsub == b.nsub &&
+           a.t1_ce == b.t1_ce && a.t1_ci == b.t1_ci && a.t1_wpc == b.t1_wpc && a.grid_t1 == b.grid_t1;
 }
 
 pic_status launch_step(pic_ctx *c)
@@ -321,8 +393,7 @@ pic_status launch_step(pic_ctx *c)
     cudaEvent_t *ev = timing_slot(c);
     if (ev) CK(cudaEventRecord(ev[0], st));
     CK(cudaMemsetAsync(c->cnt_e, 0, sizeof(int) * 4 * (size_t)c->ncell, st));   // cnt_e cnt_i fill_e fill_i
-    CK(cudaMemsetAsync(c->counters, 0, sizeof(int) * 5, st));                      // append, work counters, ovf
-    CK(cudaMemsetAsync(c->counters + CNT_MAXE, 0, sizeof(int) * 2, st));
+    CK(cudaMemsetAsync(c->counters, 0, sizeof(int) * CNT_STEP_ZERO, st));          // append, work counters, lists
     CK(cudaMemsetAsync(c->J, 0, sizeof(unsigned long long) * 3 * (size_t)c->npts, st));
     if (shape.march) {
         MarchArgs m{c->d_slab, c->d_steps, c->row_slab, c->row_idx, c->photons, c->d_tally};
@@ -330,11 +401,18 @@ pic_status launch_step(pic_ctx *c)
         ++c->launches;
     }
     if (ev) CK(cudaEventRecord(ev[1], st));
-    CellArgs am = cell_args(c, false);
-    k_cell<<<c->grid_main, c->wpc * 32, c->smem_main, st>>>(am);
-    CellArgs ab = cell_args(c, true);
+    if (c->cell_ev_on) CK(cudaEventRecord(c->cell_ev[0], st));
+    CellArgs a0 = cell_args(c, TIER0);
+    k_cell<<<c->grid_main, c->wpc * 32, c->smem_main, st>>>(a0);
+    if (c->t1_ce) {
+        CellArgs a1 = cell_args(c, TIER1);
+        k_cell<<<c->grid_t1, c->t1_wpc * 32, c->smem_t1, st>>>(a1);
+        ++c->launches;
+    }
+    CellArgs ab = cell_args(c, TIER_BIG);
     k_cell<<<c->grid_big, 32, c->smem_big, st>>>(ab);
     c->launches += 2;
+    if (c->cell_ev_on) CK(cudaEventRecord(c->cell_ev[1], st));
     CK(cudaGetLastError());
     if (ev) CK(cudaEventRecord(ev[2], st));
     PushArgs pa{};
@@ -533,6 +611,7 @@ pic_status ctx_create(pic_ctx **out, int nslot, int slot_cells, int slot_pts, in
     c->bsum_e = carve_arena<int>(c, c->nblk); c->bsum_i = carve_arena<int>(c, c->nblk);
     c->counters = carve_arena<int>(c, NCOUNTERS);
     c->ovf_list = carve_arena<int>(c, c->ncell);
+    c->ovf_list2 = carve_arena<int>(c, c->ncell);
     c->cell_slab = carve_arena<int>(c, c->ncell);
     c->d_slab = carve_arena<SlabDev>(c, nslot);
     c->d_steps = carve_arena<unsigned>(c, nslot);
@@ -597,7 +676,10 @@ pic_status ctx_create(pic_ctx **out, int nslot, int slot_cells, int slot_pts, in
     c->grid_big = c->nsm;
     e = cudaFuncSetAttribute(k_march, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8);
     if (e != cudaSuccess) { rc = cuda_fail(c, e, "march attribute"); pic_free(c); return rc; }
-    if ((rc = configure_cell_launch(c, 128, 32)) != PIC_OK) { pic_free(c); return rc; }
+    {
+        int he[NHIST] = {}, hi[NHIST] = {};
+        if ((rc = configure_cell_launch(c, he, hi, 100, 25)) != PIC_OK) { pic_free(c); return rc; }
+    }
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_push, 32 * PUSH_WARPS, 0);
     if (e != cudaSuccess) { rc = cuda_fail(c, e, "push occupancy"); pic_free(c); return rc; }
@@ -961,12 +1043,14 @@ pic_ctx::StepGraph *pair_graph(pic_ctx *c, pic_status &r)
     return r == PIC_OK ? &g : nullptr;
 }
 
-// Autotuner: time real steps with 1, 2, 4 and 8 warps per CTA (as many as
-// fit) for the current staging size and keep the fastest.  The launch shape
-// changes no result (every decision is keyed by particle and cell), so the
-// steps it times are steps of the simulation.  Shapes not yet tried are
-// tried on the first steps of this call (one step each, as many as the call
-// has); the search goes on in later calls until every shape has been timed.
+// Autotuner: time the cell kernels of real steps with 1, 2, 4 and 8 warps
+// per CTA (as many as fit) for the current staging sizes and keep the
+// fastest.  The launch shape changes no result (every decision is keyed by
+// particle and cell), so the steps it times are steps of the simulation.
+// Each shape is timed twice, in the order 1 2 4 8 8 4 2 1, so that a slow
+// drift of the step cost (cells filling up as the slab ionizes) cancels;
+// the context's first step is not timed.  A call tunes with as many of its
+// steps as it has; the search goes on in later calls until it is complete.
 pic_ctx::Tuned *tuned_entry(pic_ctx *c)
 {
     for (auto &t : c->tuned)
@@ -982,29 +1066,45 @@ pic_status tune_step(pic_ctx *c, int n, int &k)
         t = &c->tuned.back();
     }
     const int top = max_wpc(c->cap_ce, c->cap_ci, c->cap_new);
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
-    pic_status r = PIC_OK;
-    for (int q = 0, w = 1; q < 4 && w <= top && k < n && r == PIC_OK; ++q, w *= 2) {
-        if (t->tried & (1 << q)) continue;
-        if ((r = set_wpc(c, w)) != PIC_OK) break;
-        cudaEventRecord(e0, c->stream);
-        if ((r = launch_step(c)) != PIC_OK) break;
-        cudaEventRecord(e1, c->stream);
+    int shapes = 0;
+    while (shapes < 4 && (1 << shapes) <= top) ++shapes;
+    if (c->steps_done == 0 && k < n) {          // untimed first step of the context
+        pic_status r = launch_step(c);
+        if (r != PIC_OK) return r;
         ++k;
-        if (cudaEventSynchronize(e1) != cudaSuccess) { r = fail(c, PIC_ERR_CUDA, "autotune timing"); break; }
-        cudaEventElapsedTime(&t->ms[q], e0, e1);
-        t->tried |= 1 << q;
+        ++c->steps_done;
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    if (!c->cell_ev[0]) {
+        CK(cudaEventCreate(&c->cell_ev[0]));
+        CK(cudaEventCreate(&c->cell_ev[1]));
+    }
+    pic_status r = PIC_OK;
+    while (t->tried < (unsigned)(2 * shapes) && k < n && r == PIC_OK) {
+        const int idx = t->tried < (unsigned)shapes ? (int)t->tried : 2 * shapes - 1 - (int)t->tried;
+        if ((r = set_wpc(c, 1 << idx)) != PIC_OK) break;
+        c->cell_ev_on = true;
+        r = launch_step(c);
+        c->cell_ev_on = false;
+        if (r != PIC_OK) break;
+        ++k;
+        ++c->steps_done;
+        float ms = 0.0f;
+        if (cudaEventSynchronize(c->cell_ev[1]) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, c->cell_ev[0], c->cell_ev[1]) != cudaSuccess) {
+            r = fail(c, PIC_ERR_CUDA, "autotune timing");
+            break;
+        }
+        t->ms[idx] += 0.5f * ms;
+        ++t->tried;
+    }
     if (r != PIC_OK) return r;
-    float best = 3.4e38f;
-    for (int q = 0, w = 1; q < 4; ++q, w *= 2)
-        if ((t->tried & (1 << q)) && t->ms[q] < best) { best = t->ms[q]; t->wpc = w; }
-    t->done = true;
-    for (int q = 0, w = 1; q < 4 && w <= top; ++q, w *= 2) t->done &= (t->tried >> q) & 1;
+    t->done = t->tried >= (unsigned)(2 * shapes);
+    t->wpc = max_wpc(c->cap_ce, c->cap_ci, c->cap_new);      // undecided: the default
+    if (t->done) {
+        float best = 3.4e38f;
+        for (int q = 0; q < shapes; ++q)
+            if (t->ms[q] < best) { best = t->ms[q]; t->wpc = 1 << q; }
+    }
     return set_wpc(c, t->wpc);
 }
 
@@ -1013,11 +1113,11 @@ pic_status step_n(pic_ctx *c, int n)
     pic_status r = apply_pending(c);
     if (r != PIC_OK) return r;
     // size the per-warp staging for the largest cells seen so far
-    int mx[2] = {0, 0};
-    CK(cudaMemcpyAsync(mx, c->counters + CNT_MAXE, sizeof(int) * 2, cudaMemcpyDeviceToHost, c->stream));
+    int cn[NCOUNTERS];
+    CK(cudaMemcpyAsync(cn, c->counters, sizeof(int) * NCOUNTERS, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    if (mx[0] > 0 || mx[1] > 0) {
-        r = configure_cell_launch(c, mx[0], mx[1]);
+    if (cn[CNT_MAXE] > 0 || cn[CNT_MAXI] > 0) {
+        r = configure_cell_launch(c, cn + CNT_HIST_E, cn + CNT_HIST_I, cn[CNT_MAXE], cn[CNT_MAXI]);
         if (r != PIC_OK) return r;
     }
     c->launches = 0;
@@ -1029,6 +1129,7 @@ pic_status step_n(pic_ctx *c, int n)
             if (r != PIC_OK) return r;
         }
     }
+    const int tuned_steps = k;        // counted by tune_step
     if (c->use_graphs && !c->timing && n - k >= 2) {
         pic_ctx::StepGraph *g = pair_graph(c, r);
         if (!g) return r;
@@ -1041,6 +1142,7 @@ pic_status step_n(pic_ctx *c, int n)
         r = launch_step(c);
         if (r != PIC_OK) return r;
     }
+    c->steps_done += n - tuned_steps;
     // the first step after a retirement dropped the retired slabs' particles
     if (n > 0)
         for (int k = 0; k < c->nslot; ++k)
@@ -1423,6 +1525,8 @@ pic_status pic_free(pic_ctx *c)
     for (auto &g : c->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    for (cudaEvent_t e : c->cell_ev)
+        if (e) cudaEventDestroy(e);
     delete c;
     return PIC_OK;
 }

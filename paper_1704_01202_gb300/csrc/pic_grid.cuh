@@ -113,7 +113,10 @@ __device__ __forceinline__ int block_excl_scan(int v, int *sh, int &total)
     return pre + x - v;
 }
 
-struct ScanArgs { const int *cnt[2]; int *cs[2]; int *bsum[2]; int *maxc[2]; int n; int nblk; };
+// hist[sp][b]: cells whose count n has b = bit length of n (0 for empty,
+// b in 1..15 for n in [2^(b-1), 2^b), 15 also for anything larger)
+constexpr int NHIST = 16;
+struct ScanArgs { const int *cnt[2]; int *cs[2]; int *bsum[2]; int *maxc[2]; int *hist[2]; int n; int nblk; };
 
 __global__ void __launch_bounds__(SCAN_T) k_scan_reduce(ScanArgs a)
 {
@@ -146,16 +149,22 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_blocks(ScanArgs a)
 __global__ void __launch_bounds__(SCAN_T) k_scan_final(ScanArgs a)
 {
     __shared__ int sh[32];
+    __shared__ int hs[NHIST];
     const int sp = blockIdx.y;
     const int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+    if (threadIdx.x < NHIST) hs[threadIdx.x] = 0;
+    __syncthreads();
     int v[SCAN_ITEMS], sum = 0, mx = 0;
     for (int k = 0; k < SCAN_ITEMS; ++k) {
         v[k] = base + k < a.n ? a.cnt[sp][base + k] : 0;
         sum += v[k];
         mx = max(mx, v[k]);
+        if (v[k] > 0) atomicAdd(hs + min(32 - __clz(v[k]), NHIST - 1), 1);
     }
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0 && mx > 0) atomicMax(a.maxc[sp], mx);
+    __syncthreads();
+    if (threadIdx.x < NHIST && hs[threadIdx.x]) atomicAdd(a.hist[sp] + threadIdx.x, hs[threadIdx.x]);
     int tot;
     int ex = block_excl_scan(sum, sh, tot) + a.bsum[sp][blockIdx.x];
     for (int k = 0; k < SCAN_ITEMS; ++k) {

@@ -82,7 +82,8 @@ def test_autotune_keeps_results():
         s = pkg.Slab(cfg, P.standin_tables(), pl)
         s.autotune(tune)
         s.load(st)
-        s.step(6)
+        s.step(5)           # tuning goes on across calls
+        s.step(7)
         s.sync()
         w, ms = s.autotune()
         runs.append((s.electrons(), s.ions()))

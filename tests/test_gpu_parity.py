@@ -274,3 +274,36 @@ def test_full_size_sampled_cells(tables):
     q0e = st.ew.sum()
     q0i = cfg.w_ion * (st.iZ + st.izf).sum()
     assert abs((qe - qi) - (q0e - q0i)) < 1e-6 * qi
+
+
+def test_uneven_cells_all_tiers(tables):
+    """Cells of very different populations in one slab: most cells are
+    staged by the first cell-kernel tier, a few need the second (larger
+    staging, fewer warps per CTA) and one the large-cell pass.  One step
+    against the oracle."""
+    cfg = P.cfg_small_1d(nx=64, ppc_e=24, ppc_i=6, T_e_eV=30.0, flags=P.F_ALL & ~P.F_PHOTO)
+    st = P.init_particles(cfg)
+    rng = np.random.default_rng(9)
+    extra = {5: (300, 90), 17: (500, 40), 40: (1500, 400)}     # cell: (electrons, ions)
+    eX, eu, ew, iX, iu = [st.eX], [st.eu], [st.ew], [st.iX], [st.iu]
+    for c, (ne, ni) in extra.items():
+        eX.append(c + P._f32(rng.random(ne) * 0.999))
+        eu.append(P._f32(rng.standard_normal((ne, 3)) * 0.01))
+        ew.append(np.full(ne, st.ew[0]))
+        iX.append(c + P._f32(rng.random(ni) * 0.999))
+        iu.append(P._f32(rng.standard_normal((ni, 3)) * 1e-5))
+    ne_x = sum(v[0] for v in extra.values())
+    ni_x = sum(v[1] for v in extra.values())
+    st = P.ParticleState(
+        eX=np.concatenate(eX), eY=np.full(st.n_e + ne_x, 0.5), eu=np.concatenate(eu), ew=np.concatenate(ew),
+        eid=np.arange(st.n_e + ne_x, dtype=np.uint64),
+        iX=np.concatenate(iX), iY=np.full(st.n_i + ni_x, 0.5), iu=np.concatenate(iu),
+        izf=np.zeros(st.n_i + ni_x), iZ=np.full(st.n_i + ni_x, cfg.Z_init, dtype=np.int32),
+        inK=np.zeros(st.n_i + ni_x, dtype=np.int32), iid=np.arange(st.n_i + ni_x, dtype=np.uint32))
+    g, o = _run_both(cfg, tables, st, 1)
+    res = compare_state(g.electrons(), o.electrons(), g.ions(), o.ions(), cfg.nx, cfg.ny)
+    _assert_parity(res, st.n_e)
+    dg = g.diagnostics()
+    _, co = o.tallies()
+    for k in ("ION", "REC", "EE", "EI"):
+        assert abs(dg["counts"][k] - co[k]) <= max(1, int(1e-3 * co[k])), (k, dg["counts"][k], co[k])
