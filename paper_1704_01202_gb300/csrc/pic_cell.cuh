@@ -156,6 +156,7 @@ struct WarpMem {
     NewE *nw;                   // [cap_new]
     float *dE;                  // [16] continuum lowering per charge state
     float *Pz;                  // [16] impact-ionization probability per charge
+    float4 *lz;                 // [NS] Lotz constants of one charge state: P, 1/P, ln P, a q
     dd *ph;                     // [2 MAXB] photon bin scratch
     int *phc;                   // [MAXB] events per bin so far
 };
@@ -169,7 +170,7 @@ __host__ __device__ inline size_t warp_mem_bytes(int ce, int ci, int cn)
     b += align16((size_t)ci * 16) + align16((size_t)ci * 4) + align16((size_t)ci * 8) + align16((size_t)ci * 4)
          + align16((size_t)ci * 2);
     b += align16((size_t)cn * sizeof(NewE));
-    b += 16 * 4 + 16 * 4 + 2 * MAXB * 8 + MAXB * 4;
+    b += 16 * 4 + 16 * 4 + NS * 16 + 2 * MAXB * 8 + MAXB * 4;
     return b;
 }
 
@@ -189,6 +190,7 @@ __device__ inline WarpMem carve(char *base, int ce, int ci, int cn)
     m.nw = (NewE *)p; p += align16((size_t)cn * sizeof(NewE));
     m.dE = (float *)p; p += 16 * 4;
     m.Pz = (float *)p; p += 16 * 4;
+    m.lz = (float4 *)p; p += NS * 16;
     m.ph = (dd *)p; p += 2 * MAXB * 8;
     m.phc = (int *)p;
     return m;

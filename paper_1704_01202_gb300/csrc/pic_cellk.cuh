@@ -498,24 +498,53 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
         unsigned pmask = 0;
         for (int k = lane; k < ni; k += 32) { int Z = m.ist[k] & 0xff; if (Z < ZNUC) pmask |= 1u << Z; }
         for (int o = 16; o > 0; o >>= 1) pmask |= __shfl_xor_sync(FULL, pmask, o);
+        // kinetic energy and w * beta of each electron (canonical order), kept
+        // in the sort-key storage, which is free until recombination
+        float2 *ew = reinterpret_cast<float2 *>(m.ekey);
         dd pk = dd_zero();
-        for (int k = lane; k < ne; k += 32) { float4 u = m.eu[m.eperm[k]]; pk = dd_addf(pk, u.w * MC2 * gm1(u.x, u.y, u.z)); }
+        for (int k = lane; k < ne; k += 32) {
+            float4 u = m.eu[m.eperm[k]];
+            float u2 = u.x * u.x + u.y * u.y + u.z * u.z;
+            float g1 = u2 / (sqrtf(1.0f + u2) + 1.0f);
+            pk = dd_addf(pk, u.w * MC2 * g1);
+            ew[k] = make_float2(MC2 * g1, u.w * (sqrtf(u2) / (1.0f + g1)));
+        }
         const dd Kt = wsum_dd(pk);
         const float cfac = (float)(kCcmPerFs) * S.dt * nref;
         for (int z = 0; z < ZNUC; ++z) {
             if (!(pmask & (1u << z))) continue;
+            // Lotz constants of charge state z (lowest-energy configuration):
+            // lowered binding P, 1/P, ln P, a * occupation (0: empty subshell)
+            if (lane < NS) {
+                const int o = subshell_occ(ZNUC - z, lane);
+                float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if (o > 0) {
+                    const float P = lowered_binding(T, z, lane, m.dE[z]);
+                    v = make_float4(P, 1.0f / P, logf(P), T.lotz_a[lane] * (float)o);
+                }
+                m.lz[lane] = v;
+            }
+            __syncwarp();
             dd pr = dd_zero();
-            const float dEz = m.dE[z];
             for (int k = lane; k < ne; k += 32) {
-                float4 u = m.eu[m.eperm[k]];
-                float u2 = u.x * u.x + u.y * u.y + u.z * u.z;
-                float g1 = u2 / (sqrtf(1.0f + u2) + 1.0f);
-                float beta = sqrtf(u2) / (1.0f + g1);
-                pr = dd_addf(pr, u.w * beta * lotz_sigma(T, z, dEz, MC2 * g1));
+                const float2 q = ew[k];
+                const float E = q.x, lnE = logf(E), invE = 1.0f / E;
+                float sig = 0.0f;
+#pragma unroll
+                for (int sh = 0; sh < NS; ++sh) {
+                    const float4 L = m.lz[sh];
+                    if (L.w > 0.0f && E > L.x) {
+                        const float x = E * L.y;
+                        sig += L.w * (lnE - L.z) * (invE * L.y) *
+                               (1.0f - T.lotz_b[sh] * expf(-T.lotz_c[sh] * (x - 1.0f)));
+                    }
+                }
+                pr = dd_addf(pr, q.y * sig);
             }
             float P = cfac * dd_f(wsum_dd(pr));
             if (lane == 0) m.Pz[z] = P;
             if (P > 1.0f && lane == 0) wt.cnt[C_PGT1]++;
+            __syncwarp();
         }
         __syncwarp();
         dd carry = dd_zero(), paid = dd_zero();

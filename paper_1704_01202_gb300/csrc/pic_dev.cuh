@@ -226,21 +226,17 @@ __device__ __forceinline__ float dd_f(dd a) { return a.hi + a.lo; }
 __device__ __forceinline__ dd dd_zero() { return dd{0.0f, 0.0f}; }
 __device__ __forceinline__ bool dd_le(dd a, dd b) { dd d = dd_sub(b, a); return d.hi > 0.0f || (d.hi == 0.0f && d.lo >= 0.0f); }
 
-// ---------------- Lotz cross section (Eq. 3), cm^2 ----------------
-__device__ __noinline__ float lotz_sigma(const Tables &T, int z, float dE, float E)
+// ---------------- Lotz cross section (Eq. 3) ----------------
+// sigma(E) = sum_s a_s q_s ln(E / P_s) / (E P_s) [1 - b_s exp(-c_s (E / P_s - 1))]
+// over the occupied subshells s with E > P_s (q_s electrons, P_s the lowered
+// binding); the sum runs in the cell kernel with per-cell constants of P_s.
+__device__ __forceinline__ int subshell_occ(int nb, int s)
 {
-    int occ[NS];
-    if (z >= ZNUC || !occupancy(ZNUC - z, 0, occ)) return 0.0f;
-    float sig = 0.0f;
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-        if (!occ[s]) continue;
-        float P = lowered_binding(T, z, s, dE);
-        if (E <= P) continue;
-        float x = E / P;
-        sig += T.lotz_a[s] * occ[s] * logf(x) / (E * P) * (1.0f - T.lotz_b[s] * expf(-T.lotz_c[s] * (x - 1.0f)));
-    }
-    return sig;
+    // electrons of subshell s in the lowest-energy configuration of nb bound
+    // electrons (no K vacancy): 1s 2s 2p 3s 3p filled in order
+    const int start = s == 0 ? 0 : s == 1 ? 2 : s == 2 ? 4 : s == 3 ? 10 : 12;
+    const int t = nb - start;
+    return t <= 0 ? 0 : (t < cap_of(s) ? t : cap_of(s));
 }
 
 // EOS table, bilinear, clamped
