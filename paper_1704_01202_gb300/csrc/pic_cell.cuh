@@ -108,13 +108,18 @@ __device__ __forceinline__ dd wbcast_dd(dd v, int src)
     return dd{__shfl_sync(FULL, v.hi, src), __shfl_sync(FULL, v.lo, src)};
 }
 
-// ascending sort on (key, id) of n entries, padded to a power of two
+// Ascending sort of n entries on (key, id), padded to a power of two.  Only
+// the 64-bit keys and the 16-bit slots move; ids stay in slot order and are
+// read only when two keys tie.  Afterwards id[] is rewritten into the sorted
+// order (through tmp, n entries of scratch).  Padding entries (slot 0xffff)
+// order after everything.
 template <class IdT>
-__device__ void warp_bitonic(unsigned long long *key, IdT *id, unsigned short *slot, int n, int lane)
+__device__ void warp_bitonic(unsigned long long *key, IdT *id, unsigned short *slot, unsigned long long *tmp, int n,
+                             int lane)
 {
     int np = 1;
     while (np < n) np <<= 1;
-    for (int k = n + lane; k < np; k += 32) { key[k] = ~0ull; id[k] = (IdT)~(IdT)0; slot[k] = 0xffff; }
+    for (int k = n + lane; k < np; k += 32) { key[k] = ~0ull; slot[k] = 0xffff; }
     __syncwarp();
     for (int size = 2; size <= np; size <<= 1) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
@@ -123,17 +128,24 @@ __device__ void warp_bitonic(unsigned long long *key, IdT *id, unsigned short *s
                 int hi = lo + stride;
                 bool asc = (lo & size) == 0;
                 unsigned long long kl = key[lo], kh = key[hi];
-                IdT il = id[lo], ih = id[hi];
-                bool gt = kl > kh || (kl == kh && il > ih);
+                unsigned short sl = slot[lo], sh = slot[hi];
+                bool gt = kl > kh;
+                if (kl == kh) {
+                    const bool pl = sl == 0xffff, ph = sh == 0xffff;
+                    gt = pl || ph ? (pl && !ph) : id[sl] > id[sh];
+                }
                 if (gt == asc) {
                     key[lo] = kh; key[hi] = kl;
-                    id[lo] = ih; id[hi] = il;
-                    unsigned short s = slot[lo]; slot[lo] = slot[hi]; slot[hi] = s;
+                    slot[lo] = sh; slot[hi] = sl;
                 }
             }
             __syncwarp();
         }
     }
+    for (int k = lane; k < n; k += 32) tmp[k] = (unsigned long long)id[slot[k]];
+    __syncwarp();
+    for (int k = lane; k < n; k += 32) id[k] = (IdT)tmp[k];
+    __syncwarp();
 }
 
 __device__ __forceinline__ float cic_w(float x, int node)

@@ -390,8 +390,9 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
         m.iperm[k] = (unsigned short)k;
     }
     __syncwarp();
-    warp_bitonic<unsigned long long>(m.ekey, m.eid, m.eperm, ne, lane);
-    warp_bitonic<unsigned int>(m.ikey, m.iid, m.iperm, ni, lane);
+    // the sorted keys are not needed after the sort: they serve as scratch
+    warp_bitonic<unsigned long long>(m.ekey, m.eid, m.eperm, m.ekey, ne, lane);
+    warp_bitonic<unsigned int>(m.ikey, m.iid, m.iperm, m.ikey, ni, lane);
 
     }
     __syncthreads();

@@ -288,9 +288,11 @@ __device__ __noinline__ bool binary_collision(float3 &ua, float3 &ub, float ma, 
                                                  float r0, float r1, float r2, float r3)
 {
     if (qa == 0.0f || qb == 0.0f) return false;
+    // divisions by the same quantity are done once, as a reciprocal
     float ga = sqrtf(1.0f + ua.x * ua.x + ua.y * ua.y + ua.z * ua.z);
     float gb = sqrtf(1.0f + ub.x * ub.x + ub.y * ub.y + ub.z * ub.z);
-    float dvx = ua.x / ga - ub.x / gb, dvy = ua.y / ga - ub.y / gb, dvz = ua.z / ga - ub.z / gb;
+    const float iga = 1.0f / ga, igb = 1.0f / gb;
+    float dvx = ua.x * iga - ub.x * igb, dvy = ua.y * iga - ub.y * igb, dvz = ua.z * iga - ub.z * igb;
     float vrel = sqrtf(dvx * dvx + dvy * dvy + dvz * dvz);
     if (vrel < 1e-10f) return false;
     float mu = ma * mb / (ma + mb);
@@ -304,7 +306,8 @@ __device__ __noinline__ bool binary_collision(float3 &ua, float3 &ub, float ma, 
 
     float pax = ma * ua.x, pay = ma * ua.y, paz = ma * ua.z;
     float Ea = ma * ga, Eb = mb * gb, E = Ea + Eb;
-    float bx = (pax + mb * ub.x) / E, by = (pay + mb * ub.y) / E, bz = (paz + mb * ub.z) / E;
+    const float iE = 1.0f / E;
+    float bx = (pax + mb * ub.x) * iE, by = (pay + mb * ub.y) * iE, bz = (paz + mb * ub.z) * iE;
     float b2 = bx * bx + by * by + bz * bz;
     float gc = rsqrtf(1.0f - b2);
     float h = gc * gc / (gc + 1.0f);
@@ -313,14 +316,17 @@ __device__ __noinline__ bool binary_collision(float3 &ua, float3 &ub, float ma, 
     float sx = pax + c1 * bx, sy = pay + c1 * by, sz = paz + c1 * bz;
     float p = sqrtf(sx * sx + sy * sy + sz * sz);
     if (p == 0.0f) return false;
-    float nx = sx / p, ny = sy / p, nz = sz / p;
+    const float ip = 1.0f / p;
+    float nx = sx * ip, ny = sy * ip, nz = sz * ip;
     float d2 = delta * delta;
-    float st = 2.0f * delta / (1.0f + d2), ct = (1.0f - d2) / (1.0f + d2);
+    const float id2 = 1.0f / (1.0f + d2);
+    float st = 2.0f * delta * id2, ct = (1.0f - d2) * id2;
     float e1x, e1y, e1z, e2x, e2y, e2z;
     float np = sqrtf(nx * nx + ny * ny);
     if (np > 0.0f) {
-        e1x = nx * nz / np; e1y = ny * nz / np; e1z = -np;
-        e2x = -ny / np; e2y = nx / np; e2z = 0.0f;
+        const float inp = 1.0f / np;
+        e1x = nx * nz * inp; e1y = ny * nz * inp; e1z = -np;
+        e2x = -ny * inp; e2y = nx * inp; e2z = 0.0f;
     } else {
         e1x = 1.0f; e1y = 0.0f; e1z = 0.0f;
         e2x = 0.0f; e2y = 1.0f; e2z = 0.0f;
@@ -332,8 +338,14 @@ __device__ __noinline__ bool binary_collision(float3 &ua, float3 &ub, float ma, 
     float bq = bx * qx + by * qy + bz * qz;
     float ca = h * bq + gc * Eas, cb = -h * bq + gc * Ebs;
     float wm = wa > wb ? wa : wb;
-    if (r3 < wb / wm) { ua.x = (qx + ca * bx) / ma; ua.y = (qy + ca * by) / ma; ua.z = (qz + ca * bz) / ma; }
-    if (r3 < wa / wm) { ub.x = (-qx + cb * bx) / mb; ub.y = (-qy + cb * by) / mb; ub.z = (-qz + cb * bz) / mb; }
+    if (r3 < wb / wm) {
+        const float ima = 1.0f / ma;
+        ua.x = (qx + ca * bx) * ima; ua.y = (qy + ca * by) * ima; ua.z = (qz + ca * bz) * ima;
+    }
+    if (r3 < wa / wm) {
+        const float imb = 1.0f / mb;
+        ub.x = (-qx + cb * bx) * imb; ub.y = (-qy + cb * by) * imb; ub.z = (-qz + cb * bz) * imb;
+    }
     return true;
 }
 
