@@ -42,7 +42,7 @@ STEP_BYTES_PER_PARTICLE = 136
 # DRAM bytes per particle of the cell kernel's main pass, from one ncu
 # capture of the foil at 512 x 256 cells (profiles/k_cell_k_push_al_2d_512x256x5nm.md),
 # scaled to a launch by the particle count; None once the kernel changes
-CELL_TRAFFIC_BYTES_PER_PARTICLE = 65.7
+CELL_TRAFFIC_BYTES_PER_PARTICLE = None
 
 
 def measured_peaks():
@@ -115,20 +115,21 @@ def workload(cells=None):
     return cfg, pl
 
 
-def cpu_baseline(steps=3, patch=64):
-    """The oracle as it stands on a 64 x 64-cell patch of the foil."""
+def cpu_baseline(steps=32, patch=128):
+    """The oracle as it stands on a patch of the foil (default 128 x 128
+    cells, 1.3 M particles, 32 steps: about 10 s on 16 host cores)."""
     import oracle
     cfg, pl = workload()
     sub = P.SlabConfig(**{**cfg.to_dict(), "nx": patch, "ny": patch})
     st = P.init_particles(sub)
     o = oracle.OracleSlab(sub, P.standin_tables(), pl)
     o.load(st)
-    o.step(1)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    o.step(1, threads=cores)
     n = st.n_e + st.n_i
     t0 = time.perf_counter()
-    o.step(steps)
+    o.step(steps, threads=cores)
     dt = time.perf_counter() - t0
-    cores = os.cpu_count()
     return {"value": n * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{patch}x{patch}-cell patch of the foil ({n} particles), {steps} steps after 1 warm-up, "
                       f"OpenMP over cells"}
@@ -141,10 +142,10 @@ def run_reference(args):
     cfg, _ = workload()
     vals = []
     for _ in range(max(1, args.warmup)):
-        cpu_baseline(steps=1)
+        cpu_baseline(steps=1, patch=64)
     cb = None
     for _ in range(args.steps):
-        cb = cpu_baseline(steps=2)
+        cb = cpu_baseline(steps=2, patch=64)
         vals.append(cb["value"])
     v = statistics.median(vals)
     cb["value"] = v
@@ -235,6 +236,7 @@ def run_gpu(args):
     del st
     ensemble = run_ensemble(pkg, tab, args, rank) if args.ensemble > 0 else None
     served = run_served(pkg, tab, args) if args.serve_n > 0 else None
+    kedge_scan = run_kedge(pkg, tab, args) if args.kedge_points > 0 else None
     if dist:
         dist.barrier()
     if rank == 0:
@@ -248,7 +250,7 @@ def run_gpu(args):
                "roofline": roof, "step_hbm_gbs": step_gbs, "cpu_baseline": cb, "e2e": e2e,
                "gpu_launches": int(launches), "clocks": clk, "kernel_ms": {k: v / max(nrec, 1) for k, v in tms.items()},
                "autotune": {"cell_warps_per_cta": tuned[0], "cell_ms_1_2_4_8": [float(x) for x in tuned[1]]},
-               "ensemble": ensemble, "served": served}
+               "ensemble": ensemble, "served": served, "kedge_scan": kedge_scan}
         print(json.dumps(out))
     if dist:
         dist.destroy_process_group()
@@ -323,6 +325,22 @@ def run_served(pkg, tab, args):
             "particle_steps": int(psteps), "max_slabs": 128, "slot_cells": slot_cells}
 
 
+def run_kedge(pkg, tab, args):
+    """K-edge transmission sweep (photon energy x continuum-lowering model),
+    every point a slab of one batch."""
+    from paper_1704_01202_gb300 import kedge
+    hv = np.linspace(1540.0, 1870.0, args.kedge_points)
+    slabs = kedge.scan_slabs(P, hv)
+    nsteps = int(round(args.kedge_horizon_fs / slabs[0][0].dt_fs))
+    res = kedge.run_scan(tab, slabs, P.init_particles, nsteps)
+    curve = {}
+    for r in res["points"]:
+        curve.setdefault({1: "EK", 2: "SP"}.get(r["ipd"], str(r["ipd"])), []).append(round(r["transmission"], 5))
+    return {"workload": f"{len(slabs)} 1D foils of 250 x 2 nm, 64 e + 16 i per cell, 10 fs / 1e17 W/cm^2 pulse, "
+                        f"{args.kedge_horizon_fs:g} fs", "hv_eV": [float(x) for x in hv], "transmission": curve,
+            "steps": nsteps, "wall_s": res["wall_s"], "particle_steps_per_s": res["particle_steps_per_s"]}
+
+
 def run_e2e(pkg, cfg, tab, pl, st, args, world, n0):
     """Public API with host buffers: context, H2D load, steps with a D2H
     diagnostics read after each."""
@@ -356,6 +374,8 @@ def main():
     ap.add_argument("--ensemble", type=int, default=256, help="slabs of the batched ensemble (0: skip)")
     ap.add_argument("--serve-n", type=int, default=200, help="requests of the served trace (0: skip)")
     ap.add_argument("--serve-horizon-fs", type=float, default=5.0, help="simulated time per served request")
+    ap.add_argument("--kedge-points", type=int, default=12, help="photon energies of the K-edge sweep (0: skip)")
+    ap.add_argument("--kedge-horizon-fs", type=float, default=30.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "gb300" else args.warmup
     if args.impl == "reference":

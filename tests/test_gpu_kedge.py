@@ -1,0 +1,45 @@
+"""K-edge transmission scan (batched photon-energy sweep, two continuum-
+lowering models) against the oracle run point by point."""
+import numpy as np
+import pytest
+
+import pic_inputs as P
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle  # noqa: E402
+import paper_1704_01202_gb300 as pkg  # noqa: E402
+from paper_1704_01202_gb300 import kedge  # noqa: E402
+
+
+def test_kedge_scan_matches_oracle():
+    pkg.build()
+    oracle.build()
+    tab = P.standin_tables()
+    # a thin foil the photons cross in a few steps; energies below and
+    # above the cold edge, both models
+    slabs = kedge.scan_slabs(P, [1520.0, 1660.0], models=(P.IPD_EK, P.IPD_SP), nx=16, dx_nm=2.0, ppc=(32, 8),
+                             I_Wcm2=5e17, fwhm_fs=2.0, t_peak_fs=0.3)
+    nsteps = 14
+    res = kedge.run_scan(tab, slabs, P.init_particles, nsteps)
+    assert res["slabs"] == 4 and len(res["points"]) == 4
+    for (cfg, pl, hv, ipd), row in zip(slabs, res["points"]):
+        o = oracle.OracleSlab(cfg, tab, pl)
+        o.load(P.init_particles(cfg))
+        o.step(nsteps)
+        to, co = o.tallies()
+        t_o = to["TRANS"] / to["INC"]
+        assert 0.0 < row["transmission"] < 1.0
+        # photon absorption follows the same random events on both sides;
+        # FP32 against FP64 leaves a small statistical difference
+        assert abs(row["transmission"] - t_o) < 5e-3 * max(t_o, 1e-3) + 1e-4, (hv, ipd, row["transmission"], t_o)
+        ph_o = sum(int(co[f"PH{q}"]) for q in range(5))
+        assert abs(row["photoionizations"] - ph_o) <= max(2, int(0.01 * ph_o)), (hv, ipd, row, ph_o)
+    # above the edge the foil absorbs more than below it (K shell opens)
+    t = {(r["hv_eV"], r["ipd"]): r["transmission"] for r in res["points"]}
+    for ipd in (P.IPD_EK, P.IPD_SP):
+        assert t[(1660.0, ipd)] < t[(1520.0, ipd)]

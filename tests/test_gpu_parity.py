@@ -307,3 +307,24 @@ def test_uneven_cells_all_tiers(tables):
     _, co = o.tallies()
     for k in ("ION", "REC", "EE", "EI"):
         assert abs(dg["counts"][k] - co[k]) <= max(1, int(1e-3 * co[k])), (k, dg["counts"][k], co[k])
+
+
+@pytest.mark.parametrize("ipd", [P.IPD_NONE, P.IPD_SP])
+def test_single_step_ipd_models(tables, ipd):
+    """Continuum lowering switched to Stewart-Pyatt (Eq. 5) or off: one rad
+    step with every process against the oracle (Ecker-Kroell, Eq. 4, is the
+    default of the other tests)."""
+    cfg = P.cfg_small_1d(nx=40, ppc_e=64, ppc_i=16, T_e_eV=40.0, flags=P.F_ALL, rad_every=1, ipd_model=ipd)
+    pl = P.Pulse(I_peak_Wcm2=3e17, fwhm_fs=30.0, t_peak_fs=0.0, hv_eV=1600.0, n_bins=2, bandwidth_eV=60.0)
+    tab = dict(tables)
+    tab["sigma_photo"] = tables["sigma_photo"] * 50.0
+    st = _busy(cfg, seed=8)
+    ph = P.photons_uniform(cfg, pl, 1.0)
+    g, o = _run_both(cfg, tab, st, 1, pulse=pl, photons=ph)
+    res = compare_state(g.electrons(), o.electrons(), g.ions(), o.ions(), cfg.nx, cfg.ny)
+    _assert_parity(res, st.n_e)
+    dg = g.diagnostics()
+    _, co = o.tallies()
+    for k in ("ION", "REC", "PH0", "PH1", "PH2", "AUG"):
+        assert abs(dg["counts"][k] - co[k]) <= max(1, int(1e-3 * co[k])), (k, dg["counts"][k], co[k])
+    assert co["PH0"] > 0 and co["ION"] > 0
