@@ -237,6 +237,7 @@ def run_gpu(args):
     ensemble = run_ensemble(pkg, tab, args, rank) if args.ensemble > 0 else None
     served = run_served(pkg, tab, args) if args.serve_n > 0 else None
     kedge_scan = run_kedge(pkg, tab, args) if args.kedge_points > 0 else None
+    thermal = run_thermal(pkg, tab, args) if args.thermal_horizon_fs > 0 else None
     if dist:
         dist.barrier()
     if rank == 0:
@@ -250,7 +251,7 @@ def run_gpu(args):
                "roofline": roof, "step_hbm_gbs": step_gbs, "cpu_baseline": cb, "e2e": e2e,
                "gpu_launches": int(launches), "clocks": clk, "kernel_ms": {k: v / max(nrec, 1) for k, v in tms.items()},
                "autotune": {"cell_warps_per_cta": tuned[0], "cell_ms_1_2_4_8": [float(x) for x in tuned[1]]},
-               "ensemble": ensemble, "served": served, "kedge_scan": kedge_scan}
+               "ensemble": ensemble, "served": served, "kedge_scan": kedge_scan, "thermalization": thermal}
         print(json.dumps(out))
     if dist:
         dist.destroy_process_group()
@@ -341,6 +342,20 @@ def run_kedge(pkg, tab, args):
             "steps": nsteps, "wall_s": res["wall_s"], "particle_steps_per_s": res["particle_steps_per_s"]}
 
 
+def run_thermal(pkg, tab, args):
+    """Non-thermal against force-thermalized electrons: the small 1D slab
+    under a 1.7 keV, 80 fs, 1.36e17 W/cm^2 pulse, both variants in one batch."""
+    from paper_1704_01202_gb300 import thermal
+    cfg = P.cfg_small_1d(nx=128, flags=P.F_ALL)
+    pulse = P.Pulse(I_peak_Wcm2=1.36e17, fwhm_fs=80.0, t_peak_fs=80.0, hv_eV=1700.0)
+    r = thermal.compare(tab, cfg, pulse, P.init_particles, args.thermal_horizon_fs, 10.0, P.F_THERM)
+    r["workload"] = (f"al_1d_128x2nm_256e64i, 1.7 keV / 80 fs / 1.36e17 W/cm^2, {args.thermal_horizon_fs:g} fs, "
+                     "with and without forced thermalization")
+    for k in ("Zbar", "Zbar_therm", "T_e_eV", "T_e_eV_therm"):
+        r[k] = [round(x, 4) for x in r[k]]
+    return r
+
+
 def run_e2e(pkg, cfg, tab, pl, st, args, world, n0):
     """Public API with host buffers: context, H2D load, steps with a D2H
     diagnostics read after each."""
@@ -376,6 +391,7 @@ def main():
     ap.add_argument("--serve-horizon-fs", type=float, default=5.0, help="simulated time per served request")
     ap.add_argument("--kedge-points", type=int, default=12, help="photon energies of the K-edge sweep (0: skip)")
     ap.add_argument("--kedge-horizon-fs", type=float, default=30.0)
+    ap.add_argument("--thermal-horizon-fs", type=float, default=60.0, help="0: skip")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "gb300" else args.warmup
     if args.impl == "reference":

@@ -51,7 +51,11 @@ typedef enum {
 /* process switches (bit flags) */
 enum {
     PIC_F_COLL_EE = 1, PIC_F_COLL_EI = 2, PIC_F_IONIZE = 4, PIC_F_RECOMB = 8,
-    PIC_F_PHOTO = 16, PIC_F_DECAY = 32, PIC_F_PUSH = 64, PIC_F_FIELD = 128
+    PIC_F_PHOTO = 16, PIC_F_DECAY = 32, PIC_F_PUSH = 64, PIC_F_FIELD = 128,
+    /* forced-thermalization variant (Sec. VI C): on rad steps each cell's
+     * free electrons are redrawn from a Maxwellian at (2/3) E_ave, with the
+     * cell's electron momentum and kinetic energy kept */
+    PIC_F_THERM = 256
 };
 enum { PIC_IPD_NONE = 0, PIC_IPD_EK = 1, PIC_IPD_SP = 2 };
 

@@ -22,9 +22,12 @@
  *   6. rad steps: subshell photoionization (Sec. III, Eq. 2, partial
  *      ionization) then K-vacancy decay with Auger/K-alpha branching
  *      (Sec. III)
+ *   7. rad steps, only in the forced-thermalization variant (Sec. VI C):
+ *      the cell's free electrons resampled from a Maxwellian at (2/3) E_ave,
+ *      momentum and kinetic energy restored exactly
  *   then over all particles:
- *   7. relativistic Boris push, charge-conserving (Esirkepov) deposit
- *   8. Yee field update, subcycled, periodic in y, first-order Mur in x
+ *   8. relativistic Boris push, charge-conserving (Esirkepov) deposit
+ *   9. Yee field update, subcycled, periodic in y, first-order Mur in x
  */
 #include "oracle.h"
 
@@ -50,7 +53,8 @@ static const double P_MIN = 1.0;                 /* eV, floor of lowered binding
 
 /* Philox stream purposes (counter word 3) */
 enum { PU_PAIR_E = 1, PU_PAIR_I = 2, PU_COLL_EE = 3, PU_COLL_EI = 4,
-       PU_COLL_IE = 5, PU_ION = 6, PU_PHOTO_A = 7, PU_PHOTO_B = 8, PU_DECAY = 9 };
+       PU_COLL_IE = 5, PU_ION = 6, PU_PHOTO_A = 7, PU_PHOTO_B = 8, PU_DECAY = 9,
+       PU_THERM = 10 };
 /* kinds of created electrons (high id word = ((step+1) << 2) | kind) */
 enum { K_IMPACT = 1, K_PHOTO = 2, K_AUGER = 3 };
 
@@ -741,6 +745,79 @@ static void iso_u(double ke, double rc, double rp, double u[3])
     u[0] = um * st * cos(ph); u[1] = um * st * sin(ph); u[2] = um * ct;
 }
 
+/* Forced thermalization (Sec. VI C, the variant that thermalizes the photo-
+ * and Auger electrons instantly): after the rad-step processes, the free
+ * electrons of the cell, those created in this step included, get momenta
+ * drawn from a Maxwellian at kT = (2/3) E_ave (E_ave the weighted mean
+ * kinetic energy), each component normal with standard deviation
+ * sqrt(kT / m c^2).  The draw's small excess of momentum and energy is then
+ * removed: the mean momentum is shifted back to the cell's, and the
+ * momenta relative to it are scaled by the one factor that restores the
+ * cell's kinetic energy (Newton on the relativistic energy), so both are
+ * conserved exactly. */
+typedef struct { double *u; double w; uint64_t id; } eref;
+
+static double therm_energy(const eref *r, int n, const double V[3], const double *d, double a, double *slope)
+{
+    double K = 0.0, dK = 0.0;
+    for (int k = 0; k < n; ++k) {
+        double u[3] = {V[0] + a * d[3 * k], V[1] + a * d[3 * k + 1], V[2] + a * d[3 * k + 2]};
+        K += r[k].w * kin(u, 1.0);
+        dK += r[k].w * ME_C2 * (u[0] * d[3 * k] + u[1] * d[3 * k + 1] + u[2] * d[3 * k + 2]) / gam(u);
+    }
+    *slope = dK;
+    return K;
+}
+
+static void thermalize(orc_slab *S, const int *pe, int ne, cellout *o, uint64_t seed, uint32_t step)
+{
+    eref *r = malloc(sizeof(eref) * (ne + o->n + 1));
+    int n = 0;
+    for (int k = 0; k < ne; ++k) {
+        elec *e = &S->e[pe[k]];
+        if (e->alive && e->w > 0.0) { r[n].u = e->u; r[n].w = e->w; r[n].id = e->id; ++n; }
+    }
+    for (int k = 0; k < o->n; ++k)
+        if (o->ne[k].w > 0.0) { r[n].u = o->ne[k].u; r[n].w = o->ne[k].w; r[n].id = o->ne[k].id; ++n; }
+    double W = 0.0, K = 0.0, P[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < n; ++k) {
+        W += r[k].w;
+        K += r[k].w * kin(r[k].u, 1.0);
+        for (int c = 0; c < 3; ++c) P[c] += r[k].w * r[k].u[c];
+    }
+    if (n < 2 || W <= 0.0 || K <= 0.0) { free(r); return; }
+    const double T = (2.0 / 3.0) * K / W, sig = sqrt(T / ME_C2);
+    double Pn[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < n; ++k) {
+        double q[4];
+        draw4(seed, r[k].id, step, PU_THERM, q);
+        double a0 = sqrt(-2.0 * log(q[0])), a1 = sqrt(-2.0 * log(q[2]));
+        r[k].u[0] = sig * a0 * cos(2.0 * PI * q[1]);
+        r[k].u[1] = sig * a0 * sin(2.0 * PI * q[1]);
+        r[k].u[2] = sig * a1 * cos(2.0 * PI * q[3]);
+        for (int c = 0; c < 3; ++c) Pn[c] += r[k].w * r[k].u[c];
+    }
+    /* mean momentum back to the cell's; peculiar momenta d about it */
+    double V[3], *d = malloc(sizeof(double) * 3 * n);
+    for (int c = 0; c < 3; ++c) V[c] = P[c] / W;
+    for (int k = 0; k < n; ++k)
+        for (int c = 0; c < 3; ++c) d[3 * k + c] = r[k].u[c] - Pn[c] / W;
+    /* scale d by a so that the kinetic energy is K (convex in a, root >= 0) */
+    double a = 1.0;
+    for (int it = 0; it < 60; ++it) {
+        double slope, Ka = therm_energy(r, n, V, d, a, &slope);
+        if (slope <= 0.0) break;
+        double da = (Ka - K) / slope;
+        a -= da;
+        if (a < 0.0) a = 0.0;
+        if (fabs(da) < 1e-15 * (a > 1e-300 ? a : 1.0)) break;
+    }
+    for (int k = 0; k < n; ++k)
+        for (int c = 0; c < 3; ++c) r[k].u[c] = V[c] + a * d[3 * k + c];
+    free(d);
+    free(r);
+}
+
 static void cell_physics(orc_slab *S, int cell, int *eidx, int ne, int *iidx, int ni, cellout *o)
 {
     const orc_params *p = &S->p;
@@ -1067,6 +1144,8 @@ static void cell_physics(orc_slab *S, int cell, int *eidx, int ne, int *iidx, in
             }
         }
     }
+    /* 7. rad step, forced-thermalization variant */
+    if (rad && (p->flags & ORC_F_THERM)) thermalize(S, pe, ne, o, seed, step);
     free(pe); free(pi);
 }
 

@@ -19,7 +19,8 @@
 
 enum {
     ORC_F_COLL_EE = 1, ORC_F_COLL_EI = 2, ORC_F_IONIZE = 4, ORC_F_RECOMB = 8,
-    ORC_F_PHOTO = 16, ORC_F_DECAY = 32, ORC_F_PUSH = 64, ORC_F_FIELD = 128
+    ORC_F_PHOTO = 16, ORC_F_DECAY = 32, ORC_F_PUSH = 64, ORC_F_FIELD = 128,
+    ORC_F_THERM = 256     /* forced thermalization on rad steps (Sec. VI C variant) */
 };
 
 typedef struct {

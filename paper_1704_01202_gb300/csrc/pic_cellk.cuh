@@ -36,6 +36,112 @@ struct CellCtx {
     bool rad;
 };
 
+// ---- forced-thermalization variant (Sec. VI C), rad steps ----
+// The cell's free electrons, those created in this step included, are
+// redrawn from a Maxwellian at kT = (2/3) E_ave (components normal with
+// standard deviation sqrt(kT / m c^2), Box-Muller on the electron's Philox
+// draw); the mean momentum is shifted back to the cell's and the momenta
+// about it scaled by one factor (Newton) so that the cell's kinetic energy
+// is kept.  Sums are double-float.
+struct ThermSums { dd W, K, Px, Py, Pz; int n; };
+
+__device__ __forceinline__ void therm_add(ThermSums &t, float4 u)
+{
+    t.W = dd_addf(t.W, u.w);
+    t.K = dd_addf(t.K, u.w * (float)kMeC2 * gm1(u.x, u.y, u.z));
+    t.Px = dd_addf(t.Px, u.w * u.x); t.Py = dd_addf(t.Py, u.w * u.y); t.Pz = dd_addf(t.Pz, u.w * u.z);
+    t.n += 1;
+}
+
+__device__ __noinline__ void stage_therm(const CellArgs &a, const WarpMem &m, const CellCtx &c, int lane, int nnew)
+{
+    const int ne = c.ne;
+    const float MC2 = (float)kMeC2;
+    ThermSums t0{dd_zero(), dd_zero(), dd_zero(), dd_zero(), dd_zero(), 0};
+    for (int k = lane; k < ne; k += 32) { float4 u = m.eu[m.eperm[k]]; if (u.w > 0.0f) therm_add(t0, u); }
+    for (int k = lane; k < nnew; k += 32) {
+        NewE q = m.nw[k];
+        if (q.w > 0.0f) therm_add(t0, make_float4(q.ux, q.uy, q.uz, q.w));
+    }
+    const dd W = wsum_dd(t0.W), K = wsum_dd(t0.K);
+    const float P[3] = {dd_f(wsum_dd(t0.Px)), dd_f(wsum_dd(t0.Py)), dd_f(wsum_dd(t0.Pz))};
+    const int n = wsum_i(t0.n);
+    const float Wf = dd_f(W), Kf = dd_f(K);
+    if (n < 2 || !(Wf > 0.0f) || !(Kf > 0.0f)) return;
+    const float sig = sqrtf((2.0f / 3.0f) * Kf / Wf / MC2);
+    // redraw; the new momenta replace the old ones in shared memory
+    auto redraw = [&](unsigned long long id) {
+        U4 r = draw(c.seed, id, c.step, PU_THERM);
+        const float a0 = sqrtf(-2.0f * logf(u01(r.x))), a1 = sqrtf(-2.0f * logf(u01(r.z)));
+        float sn, cs;
+        sincosf(2.0f * kPiF * u01(r.y), &sn, &cs);
+        return make_float3(sig * a0 * cs, sig * a0 * sn, sig * a1 * cosf(2.0f * kPiF * u01(r.w)));
+    };
+    dd Qx = dd_zero(), Qy = dd_zero(), Qz = dd_zero();
+    for (int k = lane; k < ne; k += 32) {
+        const int sl = m.eperm[k];
+        float4 u = m.eu[sl];
+        if (!(u.w > 0.0f)) continue;
+        float3 v = redraw(m.eid[k]);
+        m.eu[sl] = make_float4(v.x, v.y, v.z, u.w);
+        Qx = dd_addf(Qx, u.w * v.x); Qy = dd_addf(Qy, u.w * v.y); Qz = dd_addf(Qz, u.w * v.z);
+    }
+    for (int k = lane; k < nnew; k += 32) {
+        NewE q = m.nw[k];
+        if (!(q.w > 0.0f)) continue;
+        const int islot = q.meta & 0xffff, kind = q.meta >> 16;
+        const unsigned ion_id = __float_as_uint(a.i1[c.i0 + islot].z);
+        const unsigned long long id = ((unsigned long long)(((c.step + 1u) << 2) | (unsigned)kind) << 32) | ion_id;
+        float3 v = redraw(id);
+        q.ux = v.x; q.uy = v.y; q.uz = v.z;
+        m.nw[k] = q;
+        Qx = dd_addf(Qx, q.w * v.x); Qy = dd_addf(Qy, q.w * v.y); Qz = dd_addf(Qz, q.w * v.z);
+    }
+    __syncwarp();
+    const float iW = 1.0f / Wf;
+    const float V[3] = {P[0] * iW, P[1] * iW, P[2] * iW};
+    const float M[3] = {dd_f(wsum_dd(Qx)) * iW, dd_f(wsum_dd(Qy)) * iW, dd_f(wsum_dd(Qz)) * iW};
+    // kinetic energy of the cell with the peculiar momenta d = u - M scaled by s
+    auto energy = [&](float s, float &slope) {
+        dd e = dd_zero(), de = dd_zero();
+        auto one = [&](float4 u) {
+            float dx = u.x - M[0], dy = u.y - M[1], dz = u.z - M[2];
+            float ux = V[0] + s * dx, uy = V[1] + s * dy, uz = V[2] + s * dz;
+            e = dd_addf(e, u.w * MC2 * gm1(ux, uy, uz));
+            de = dd_addf(de, u.w * MC2 * (ux * dx + uy * dy + uz * dz) * rsqrtf(1.0f + ux * ux + uy * uy + uz * uz));
+        };
+        for (int k = lane; k < ne; k += 32) { float4 u = m.eu[m.eperm[k]]; if (u.w > 0.0f) one(u); }
+        for (int k = lane; k < nnew; k += 32) {
+            NewE q = m.nw[k];
+            if (q.w > 0.0f) one(make_float4(q.ux, q.uy, q.uz, q.w));
+        }
+        slope = dd_f(wsum_dd(de));
+        return wsum_dd(e);
+    };
+    float s = 1.0f;
+    for (int it = 0; it < 8; ++it) {
+        float slope;
+        const dd e = energy(s, slope);
+        if (!(slope > 0.0f)) break;
+        const float ds = dd_f(dd_sub(e, K)) / slope;
+        s = fmaxf(s - ds, 0.0f);
+        if (fabsf(ds) <= 1e-7f * s) break;
+    }
+    for (int k = lane; k < ne; k += 32) {
+        const int sl = m.eperm[k];
+        float4 u = m.eu[sl];
+        if (!(u.w > 0.0f)) continue;
+        m.eu[sl] = make_float4(V[0] + s * (u.x - M[0]), V[1] + s * (u.y - M[1]), V[2] + s * (u.z - M[2]), u.w);
+    }
+    for (int k = lane; k < nnew; k += 32) {
+        NewE q = m.nw[k];
+        if (!(q.w > 0.0f)) continue;
+        q.ux = V[0] + s * (q.ux - M[0]); q.uy = V[1] + s * (q.uy - M[1]); q.uz = V[2] + s * (q.uz - M[2]);
+        m.nw[k] = q;
+    }
+    __syncwarp();
+}
+
 // ---- EOS-clamped three-body recombination (Sec. IV) ----
 __device__ __noinline__ void stage_recombine(const CellArgs &a, const WarpMem &m, const Tables &T, const SlabDev &S,
                                              const CellCtx &c, int lane, float Wnew_imp, WarpTally &wt)
@@ -613,6 +719,7 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
     if ((flags & 8u) && ni >= 1) stage_recombine(a, m, T, S, cc, lane, Wnew_imp, wt);
     if (rad && (flags & 16u) && S.nb && ni >= 1) stage_photo(a, m, T, S, cc, lane, nnew, wt);
     if (rad && (flags & 32u) && ni >= 1) stage_decay(a, m, T, S, cc, lane, nnew, wt);
+    if (rad && (flags & 256u)) stage_therm(a, m, cc, lane, nnew);
 
     // ---- write the collided state back (positions unchanged) and the
     //      canonical order, which the push kernel follows ----

@@ -186,6 +186,7 @@ F_DECAY = 32
 F_PUSH = 64
 F_FIELD = 128
 F_ALL = 255
+F_THERM = 256      # forced-thermalization variant (Sec. VI C), off in F_ALL
 
 IPD_NONE, IPD_EK, IPD_SP = 0, 1, 2
 

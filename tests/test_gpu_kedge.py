@@ -43,3 +43,17 @@ def test_kedge_scan_matches_oracle():
     t = {(r["hv_eV"], r["ipd"]): r["transmission"] for r in res["points"]}
     for ipd in (P.IPD_EK, P.IPD_SP):
         assert t[(1660.0, ipd)] < t[(1520.0, ipd)]
+
+
+def test_thermal_comparison_runs():
+    """The non-thermal / force-thermalized pair in one batch: same initial
+    state, histories recorded every 5 fs; the variants differ in their
+    electrons but keep the same energy bookkeeping trend."""
+    from paper_1704_01202_gb300 import thermal
+    pkg.build()
+    cfg = P.cfg_small_1d(nx=16, ppc_e=64, ppc_i=16, rad_every=1, flags=P.F_ALL)
+    pulse = P.Pulse(I_peak_Wcm2=5e17, fwhm_fs=5.0, t_peak_fs=2.0, hv_eV=1700.0)
+    r = thermal.compare(P.standin_tables(), cfg, pulse, P.init_particles, 10.0, 5.0, P.F_THERM)
+    assert r["steps"] == 500 and len(r["t_fs"]) == 2
+    assert r["Zbar"][-1] >= 3.0 and r["Zbar_therm"][-1] >= 3.0
+    assert r["T_e_eV"][-1] > 0 and r["T_e_eV_therm"][-1] > 0

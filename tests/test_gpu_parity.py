@@ -328,3 +328,50 @@ def test_single_step_ipd_models(tables, ipd):
     for k in ("ION", "REC", "PH0", "PH1", "PH2", "AUG"):
         assert abs(dg["counts"][k] - co[k]) <= max(1, int(1e-3 * co[k])), (k, dg["counts"][k], co[k])
     assert co["PH0"] > 0 and co["ION"] > 0
+
+
+def test_single_step_forced_thermalization(tables):
+    """The forced-thermalization variant (Sec. VI C) on a rad step with every
+    process: electrons created by photoionization, Auger decay and impact
+    ionization are redrawn with the rest; per-particle parity with the
+    oracle."""
+    cfg = P.cfg_small_1d(nx=40, ppc_e=64, ppc_i=16, T_e_eV=25.0, flags=P.F_ALL | P.F_THERM, rad_every=1)
+    pl = P.Pulse(I_peak_Wcm2=3e17, fwhm_fs=30.0, t_peak_fs=0.0, hv_eV=1700.0, n_bins=3, bandwidth_eV=400.0)
+    tab = dict(tables)
+    tab["sigma_photo"] = tables["sigma_photo"] * 50.0
+    st = _busy(cfg, seed=6)
+    ph = P.photons_uniform(cfg, pl, 1.0)
+    g, o = _run_both(cfg, tab, st, 1, pulse=pl, photons=ph)
+    res = compare_state(g.electrons(), o.electrons(), g.ions(), o.ions(), cfg.nx, cfg.ny)
+    _assert_parity(res, st.n_e)
+    _, co = o.tallies()
+    assert co["PH0"] > 0 and co["AUG"] > 0 and co["ION"] > 0
+
+
+def test_thermalization_conserves_cell_momentum_energy_gpu(tables):
+    """Thermalization alone (no push): each cell's weighted electron
+    momentum and kinetic energy are kept to FP32 rounding."""
+    cfg = P.cfg_small_1d(nx=24, ppc_e=256, ppc_i=64, beam_frac=0.2, rad_every=1, flags=P.F_THERM)
+    st = P.init_particles(cfg)
+    st.eu[:, 0] += 0.005
+    g = pkg.Slab(cfg, tables)
+    g.load(st)
+    g.step(1)
+    e = g.electrons()
+
+    def kin(u):
+        u = u.astype(np.float64)
+        u2 = (u * u).sum(axis=1)
+        return 510998.95 * u2 / (np.sqrt(1 + u2) + 1)
+
+    c0, c1 = np.floor(st.eX).astype(int), np.floor(e["X"]).astype(int)
+    for c in range(cfg.nx):
+        m0, m1 = c0 == c, c1 == c
+        w0, w1 = st.ew[m0].astype(np.float64), e["w"][m1].astype(np.float64)
+        p0 = (w0[:, None] * st.eu[m0]).sum(axis=0)
+        p1 = (w1[:, None] * e["u"][m1].astype(np.float64)).sum(axis=0)
+        scale = (w0[:, None] * np.abs(st.eu[m0])).sum(axis=0)
+        assert np.all(np.abs(p1 - p0) < 2e-6 * scale), (c, p0, p1)
+        k0, k1 = (w0 * kin(st.eu[m0])).sum(), (w1 * kin(e["u"][m1])).sum()
+        assert abs(k1 / k0 - 1) < 2e-6, (c, k0, k1)
+    g.close()
