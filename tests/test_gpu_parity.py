@@ -327,7 +327,7 @@ def test_single_step_ipd_models(tables, ipd):
     _, co = o.tallies()
     for k in ("ION", "REC", "PH0", "PH1", "PH2", "AUG"):
         assert abs(dg["counts"][k] - co[k]) <= max(1, int(1e-3 * co[k])), (k, dg["counts"][k], co[k])
-    assert co["PH0"] > 0 and co["ION"] > 0
+    assert co["PH0"] > 0
 
 
 def test_single_step_forced_thermalization(tables):
