@@ -107,6 +107,20 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons)}
 
 
+def aggregate(ms, particle_steps, dist=None, device="cpu"):
+    """Whole-job throughput over the ranks: the slowest rank's time and the
+    particle-steps of all ranks (replicas: no data-path collective, only
+    this reduction of two numbers)."""
+    if dist is None:
+        return ms, particle_steps / (ms * 1e-3)
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    n = torch.tensor([particle_steps], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(n.item()) / (float(t.item()) * 1e-3)
+
+
 def workload(cells=None):
     cfg = P.cfg_foil_2d()
     if cells:
@@ -208,11 +222,7 @@ def run_gpu(args):
     slab.timing(False)
     ne1, ni1 = slab.counts()
     n_mean = 0.5 * (ne0 + ni0 + ne1 + ni1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n_mean * args.steps / (ms * 1e-3)
+    ms, value = aggregate(ms, n_mean * args.steps, dist, "cuda")
 
     # dominant kernel roofline: the per-cell kernel
     peak, peak_kind = measured_peaks()
