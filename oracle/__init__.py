@@ -109,6 +109,8 @@ def lib():
             L.orc_lotz.argtypes = [C.POINTER(Tables), C.c_int, C.c_double, C.c_double]
             L.orc_coulomb_log.restype = C.c_double
             L.orc_coulomb_log.argtypes = [C.c_double, C.c_double, C.c_double]
+            L.orc_field_speed.restype = C.c_double
+            L.orc_field_speed.argtypes = [C.c_void_p]
             L.orc_collide.restype = C.c_int
             L.orc_collide.argtypes = [_D, _D] + [C.c_double] * 9 + [_D]
             L.orc_boris.argtypes = [_D, _D, _D, C.c_double, C.c_double]
@@ -298,6 +300,14 @@ def ipd(model, z, n_e, n_i, T_e, zbar):
 
 def coulomb_log(n_e, T_e, zbar):
     return lib().orc_coulomb_log(n_e, T_e, zbar)
+
+
+def field_speed(cfg):
+    """Speed (nm/fs) of the oracle's Yee update for a slab configuration."""
+    p = Params(nx=cfg.nx, ny=cfg.ny, dx=cfg.dx_nm, dy=cfg.dy_nm, dt=cfg.dt_fs, rad_every=cfg.rad_every,
+               seed=cfg.seed, cfl=cfg.cfl, n_ref=cfg.n_ref_cm3, w_ion=cfg.w_ion, m_ion=cfg.m_ion_me,
+               E_bulk=cfg.E_bulk_eV, ipd_model=cfg.ipd_model, coulomb_log=cfg.coulomb_log, flags=cfg.flags)
+    return lib().orc_field_speed(C.byref(p))
 
 
 class TableHandle:

@@ -27,7 +27,8 @@
  *      momentum and kinetic energy restored exactly
  *   then over all particles:
  *   8. relativistic Boris push, charge-conserving (Esirkepov) deposit
- *   9. Yee field update, subcycled, periodic in y, first-order Mur in x
+ *   9. Yee field update at the field speed the step resolves (see
+ *      orc_field_speed), periodic in y, first-order Mur in x
  */
 #include "oracle.h"
 
@@ -1157,8 +1158,8 @@ static double kappa_J(const orc_slab *s)
 }
 
 #define IX(j, i) ((size_t)(j) * W + (i))
-/* B half step: dB/dt = -c curl E */
-static void b_half(double *f, int nx, int ny, double dx, double dy, double h)
+/* B half step: dB/dt = -curl E, times the field speed cf */
+static void b_half(double *f, int nx, int ny, double dx, double dy, double h, double cf)
 {
     int W = nx + 1;
     size_t ng = (size_t)ny * W;
@@ -1166,33 +1167,33 @@ static void b_half(double *f, int nx, int ny, double dx, double dy, double h)
     for (int j = 0; j < ny; ++j) {
         int jp = (j + 1) % ny;
         for (int i = 0; i <= nx; ++i)
-            bx[IX(j, i)] -= h * C_NM_FS * (ez[IX(jp, i)] - ez[IX(j, i)]) / dy;
+            bx[IX(j, i)] -= h * cf * (ez[IX(jp, i)] - ez[IX(j, i)]) / dy;
         for (int i = 0; i < nx; ++i) {
-            by[IX(j, i)] += h * C_NM_FS * (ez[IX(j, i + 1)] - ez[IX(j, i)]) / dx;
-            bz[IX(j, i)] -= h * C_NM_FS * ((ey[IX(j, i + 1)] - ey[IX(j, i)]) / dx
+            by[IX(j, i)] += h * cf * (ez[IX(j, i + 1)] - ez[IX(j, i)]) / dx;
+            bz[IX(j, i)] -= h * cf * ((ey[IX(j, i + 1)] - ey[IX(j, i)]) / dx
                                            - (ex[IX(jp, i)] - ex[IX(j, i)]) / dy);
         }
     }
 }
 
-/* E full step: dE/dt = c curl B - kappa J; first-order Mur at x = 0, L */
+/* E full step: dE/dt = cf curl B - kappa J; first-order Mur at x = 0, L */
 static void e_full(double *f, const double *jc, int nx, int ny, double dx, double dy,
-                   double dtf, double kap)
+                   double dtf, double kap, double cf)
 {
     int W = nx + 1;
     size_t ng = (size_t)ny * W;
     double *ex = f, *ey = f + ng, *ez = f + 2 * ng, *bx = f + 3 * ng, *by = f + 4 * ng, *bz = f + 5 * ng;
     const double *jx = jc, *jy = jc + ng, *jz = jc + 2 * ng;
-    double mur = (C_NM_FS * dtf - dx) / (C_NM_FS * dtf + dx);
+    double mur = (cf * dtf - dx) / (cf * dtf + dx);
     for (int j = 0; j < ny; ++j) {
         int jm = (j - 1 + ny) % ny;
         double y0 = ey[IX(j, 0)], y1 = ey[IX(j, 1)], yn1 = ey[IX(j, nx - 1)], yn = ey[IX(j, nx)];
         double z0 = ez[IX(j, 0)], z1 = ez[IX(j, 1)], zn1 = ez[IX(j, nx - 1)], zn = ez[IX(j, nx)];
         for (int i = 0; i < nx; ++i)
-            ex[IX(j, i)] += dtf * (C_NM_FS * (bz[IX(j, i)] - bz[IX(jm, i)]) / dy - kap * jx[IX(j, i)]);
+            ex[IX(j, i)] += dtf * (cf * (bz[IX(j, i)] - bz[IX(jm, i)]) / dy - kap * jx[IX(j, i)]);
         for (int i = 1; i < nx; ++i) {
-            ey[IX(j, i)] += dtf * (-C_NM_FS * (bz[IX(j, i)] - bz[IX(j, i - 1)]) / dx - kap * jy[IX(j, i)]);
-            ez[IX(j, i)] += dtf * (C_NM_FS * ((by[IX(j, i)] - by[IX(j, i - 1)]) / dx
+            ey[IX(j, i)] += dtf * (-cf * (bz[IX(j, i)] - bz[IX(j, i - 1)]) / dx - kap * jy[IX(j, i)]);
+            ez[IX(j, i)] += dtf * (cf * ((by[IX(j, i)] - by[IX(j, i - 1)]) / dx
                                               - (bx[IX(j, i)] - bx[IX(jm, i)]) / dy)
                                    - kap * jz[IX(j, i)]);
         }
@@ -1204,25 +1205,30 @@ static void e_full(double *f, const double *jc, int nx, int ny, double dx, doubl
 }
 #undef IX
 
-/* number of field subcycles per particle step: Yee stability with margin
- * cfl (the particle step c*dt exceeds the cell size) */
-static int n_subcycles(const orc_params *p)
+/* Field speed of the Yee update: c where the particle step resolves it
+ * (c dt within cfl times the Yee limit), otherwise the largest speed that
+ * the step resolves.  The particle step c dt = 6 nm exceeds the 2-5 nm cells
+ * of the workloads; subcycling the fields with the current held fixed let
+ * the particles see the transverse waves only every dt, and the transverse
+ * fields then grew exponentially once e-i collisions fed them noise (both
+ * sides, within a few fs).  Gauss's law goes through the continuity of the
+ * deposited current and does not involve cf, so the electrostatic and
+ * sheath fields are unchanged; only light waves and magnetic induction are
+ * slowed. */
+double orc_field_speed(const orc_params *p)
 {
     double inv = 1.0 / (p->dx * p->dx) + (p->ny > 1 ? 1.0 / (p->dy * p->dy) : 0.0);
-    int n = (int)ceil(C_NM_FS * p->dt * sqrt(inv) / p->cfl);
-    return n < 1 ? 1 : n;
+    double cmax = p->cfl / (p->dt * sqrt(inv));
+    return C_NM_FS < cmax ? C_NM_FS : cmax;
 }
 
 static void field_step(orc_slab *s)
 {
     const orc_params *p = &s->p;
-    int nsub = n_subcycles(p);
-    double dtf = p->dt / nsub, kap = kappa_J(s);
-    for (int it = 0; it < nsub; ++it) {
-        b_half(s->f, p->nx, p->ny, p->dx, p->dy, 0.5 * dtf);
-        e_full(s->f, s->j, p->nx, p->ny, p->dx, p->dy, dtf, kap);
-        b_half(s->f, p->nx, p->ny, p->dx, p->dy, 0.5 * dtf);
-    }
+    const double cf = orc_field_speed(p), dt = p->dt, kap = kappa_J(s);
+    b_half(s->f, p->nx, p->ny, p->dx, p->dy, 0.5 * dt, cf);
+    e_full(s->f, s->j, p->nx, p->ny, p->dx, p->dy, dt, kap, cf);
+    b_half(s->f, p->nx, p->ny, p->dx, p->dy, 0.5 * dt, cf);
 }
 
 /* field at (X, Y): CIC from the staggered grid, zero outside [0, nx] */

@@ -97,6 +97,7 @@ int orc_occ(int nb, int nk, int occ[ORC_NS]);
 double orc_ipd(int model, int z, double n_e, double n_i, double T_e, double zbar);
 double orc_lotz(const orc_tables *t, int z, double dE, double E);
 double orc_coulomb_log(double n_e, double T_e, double zbar);
+double orc_field_speed(const orc_params *p);   /* nm/fs, speed of the Yee update */
 int orc_collide(double ua[3], double ub[3], double ma, double mb, double qa,
                 double qb, double wa, double wb, double n_l, double lnL,
                 double dtc, const double r[4]);

@@ -514,10 +514,19 @@ SlabDev make_slab(const pic_ctx *c, int k, const pic_grid *g, const pic_species 
     S.kappa_J = kQe * s->n_ref_cm3 * 1e6 * 1e-9 / (kEps0 * E0);
     S.nref_f = (float)S.n_ref;
     S.kappa_f = (float)S.kappa_J;
+    // Field speed: c where the step resolves it (c dt within cfl of the Yee
+    // limit), else the largest speed it resolves.  With c dt beyond the cell
+    // size, fields subcycled at c with the current held fixed are seen by
+    // the particles only every dt, and the transverse fields grow without
+    // bound once collisions feed them noise; the continuity of the deposited
+    // current, hence Gauss's law and the electrostatic fields, does not
+    // depend on this speed.  One field update per step.
     double inv = 1.0 / (g->dx_nm * g->dx_nm) + (g->ny > 1 ? 1.0 / (g->dy_nm * g->dy_nm) : 0.0);
-    S.nsub = std::max(1, (int)std::ceil(kCnmPerFs * g->dt_fs * std::sqrt(inv) / g->cfl));
-    double dtf = g->dt_fs / S.nsub;
-    S.mur = (float)((kCnmPerFs * dtf - g->dx_nm) / (kCnmPerFs * dtf + g->dx_nm));
+    const double cmax = g->cfl / (g->dt_fs * std::sqrt(inv));
+    const double cf = kCnmPerFs < cmax ? kCnmPerFs : cmax;
+    S.nsub = 1;
+    S.cf = (float)cf;
+    S.mur = (float)((cf * g->dt_fs - g->dx_nm) / (cf * g->dt_fs + g->dx_nm));
     S.seed = g->seed;
     return S;
 }

@@ -67,11 +67,12 @@ struct SlabDev {
     int rad_every;
     unsigned flags;
     int ipd;
-    int nsub;               // field subcycles per step
+    int nsub;               // field updates per step (1: the field speed below is resolved by dt)
     int shape;
     float dx, dy, dt;
     float w_ion, m_ion, E_bulk, coulomb_log;
     float mur;              // first-order Mur coefficient
+    float cf;               // speed of the Yee update, nm/fs (c, or the largest speed dt resolves)
     double n_ref;           // cm^-3
     double kappa_J;         // J coupling of the normalized field equations
     float nref_f, kappa_f;  // the same in single precision for the kernels

@@ -234,7 +234,7 @@ __global__ void k_b_half(FieldArgs a)
         if (!S.active || !(S.flags & 128u) || a.sub >= S.nsub || q >= W * S.ny) continue;
         const int j = q / W, i = q - j * W;
         const int jp = (j + 1) % S.ny;
-        const float h = 0.5f * S.dt / S.nsub * (float)kCnmPerFs;
+        const float h = 0.5f * S.dt / S.nsub * S.cf;
         const int n = a.npts;
         const float *ex = a.Ein, *ey = a.Ein + n, *ez = a.Ein + 2 * n;
         float *bx = a.B, *by = a.B + n, *bz = a.B + 2 * n;
@@ -263,7 +263,8 @@ __global__ void k_e_full(FieldArgs a)
         const int j = q / W, i = q - j * W;
         const int jm = (j - 1 + S.ny) % S.ny;
         const int o = S.fld_off, r = o + j * W, rm = o + jm * W;
-        const float dtf = S.dt / S.nsub, C = (float)kCnmPerFs, kap = S.kappa_f;
+        // Cf: speed of the curl terms; C: c, the velocity unit of J
+        const float dtf = S.dt / S.nsub, C = (float)kCnmPerFs, Cf = S.cf, kap = S.kappa_f;
         const float *bx = a.B, *by = a.B + n, *bz = a.B + 2 * n;
         const unsigned long long *Jx = a.J, *Jy = a.J + n, *Jz = a.J + 2 * n;
         const float sx = S.dx / S.dt, sy = S.ny > 1 ? S.dy / S.dt : C;
@@ -275,14 +276,14 @@ __global__ void k_e_full(FieldArgs a)
             return (hi + lo) * (1.0f / 1099511627776.0f) * scale;
         };
         auto ey_new = [&](int ii) {
-            return eyi[r + ii] + dtf * (-C * (bz[r + ii] - bz[r + ii - 1]) / S.dx - kap * jv(Jy, r + ii, sy));
+            return eyi[r + ii] + dtf * (-Cf * (bz[r + ii] - bz[r + ii - 1]) / S.dx - kap * jv(Jy, r + ii, sy));
         };
         auto ez_new = [&](int ii) {
-            return ezi[r + ii] + dtf * (C * ((by[r + ii] - by[r + ii - 1]) / S.dx - (bx[r + ii] - bx[rm + ii]) / S.dy)
+            return ezi[r + ii] + dtf * (Cf * ((by[r + ii] - by[r + ii - 1]) / S.dx - (bx[r + ii] - bx[rm + ii]) / S.dy)
                                         - kap * jv(Jz, r + ii, C));
         };
         if (i < S.nx)
-            exo[p] = exi[p] + dtf * (C * (bz[r + i] - bz[rm + i]) / S.dy - kap * jv(Jx, p, sx));
+            exo[p] = exi[p] + dtf * (Cf * (bz[r + i] - bz[rm + i]) / S.dy - kap * jv(Jx, p, sx));
         else
             exo[p] = exi[p];
         if (i >= 1 && i < S.nx) {

@@ -121,13 +121,16 @@ def test_cold_plasma_frequency():
     assert abs(w_meas / w_pe - 1) < 0.02
 
 
-def test_vacuum_pulse_magic_step_and_mur():
-    """1D vacuum: at c dt_f = dx the Yee scheme moves a pulse by exactly one
-    cell per subcycle, and first-order Mur lets it leave without
-    reflection."""
+@pytest.mark.parametrize("dt_cells", [1.0, 2.0])
+def test_vacuum_pulse_magic_step_and_mur(dt_cells):
+    """1D vacuum: with the field speed at the Yee limit (cf dt = dx) the
+    scheme moves a pulse by exactly one cell per step, and first-order Mur
+    lets it leave without reflection.  dt_cells = c dt / dx: at 1 the field
+    speed is c, at 2 the step does not resolve c and the field runs at c/2."""
     dx = 2.0
-    cfg = P.cfg_small_1d(flags=P.F_FIELD, nx=200, dx_nm=dx, dt_fs=2 * dx / C_NM_FS, cfl=1.0,
+    cfg = P.cfg_small_1d(flags=P.F_FIELD, nx=200, dx_nm=dx, dt_fs=dt_cells * dx / C_NM_FS, cfl=1.0,
                          ppc_e=1, ppc_i=1, beam_frac=0.0)
+    assert oracle.field_speed(cfg) == pytest.approx(C_NM_FS / dt_cells, rel=1e-12)
     o = oracle.OracleSlab(cfg, P.standin_tables())
     st = P.init_particles(cfg)
     st.eX = st.eX[:0]; st.eY = st.eY[:0]; st.eu = st.eu[:0]; st.ew = st.ew[:0]; st.eid = st.eid[:0]
@@ -139,15 +142,15 @@ def test_vacuum_pulse_magic_step_and_mur():
     f = {k: np.zeros((1, cfg.nx + 1)) for k in ("ex", "ey", "ez", "bx", "by", "bz")}
     x0, w = 60.0, 6.0
     f["ey"][0] = np.exp(-((x_node - x0) / w) ** 2)
-    # Bz one half cell ahead in space and half a subcycle in time
+    # Bz one half cell ahead in space and half a step in time
     f["bz"][0] = np.exp(-((x_half - 0.5 - x0) / w) ** 2)
     f["bz"][0, -1] = 0.0
     o.set_fields(f)
     e0 = (f["ey"] ** 2).sum()
-    o.step(30)                      # 60 subcycles: 60 cells
+    o.step(60)                      # one cell per step
     ey = o.fields()["ey"][0]
     assert abs(np.argmax(ey) - (x0 + 60)) <= 1
-    o.step(100)
+    o.step(200)
     f1 = o.fields()
     left = sum((f1[k] ** 2).sum() for k in f1)
     assert left < 1e-6 * e0
@@ -167,3 +170,23 @@ def test_oracle_deterministic_across_threads(tables):
     assert np.array_equal(outs[0][0], outs[1][0])
     assert np.array_equal(outs[0][1], outs[1][1])
     assert np.array_equal(outs[0][2], outs[1][2])
+
+
+def test_field_energy_stays_bounded_with_collisions(tables):
+    """The small 1D slab with every process under the 1.7 keV pulse: the
+    field energy stays at the level of grid noise over 6 fs (with the
+    fields subcycled at the physical c it grew by orders of magnitude in
+    that time, through the transverse components, once e-i collisions were
+    on)."""
+    cfg = P.cfg_small_1d(nx=64, flags=P.F_ALL)
+    pl = P.Pulse(I_peak_Wcm2=1.36e17, fwhm_fs=80.0, t_peak_fs=80.0, hv_eV=1700.0)
+    o = oracle.OracleSlab(cfg, tables, pl)
+    o.load(P.init_particles(cfg))
+    fe = []
+    for _ in range(6):
+        o.step(50)
+        t, _ = o.tallies()
+        fe.append(t["FIELD"])
+    assert max(fe) < 10 * fe[0], fe
+    t, _ = o.tallies()
+    assert t["FIELD"] < 0.05 * t["KE_E"]
