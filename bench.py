@@ -196,8 +196,9 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
 
     # launch-shape autotuning on the first steps (real steps of the run)
-    slab.autotune(True)
-    slab.step(9)
+    if not args.no_autotune:
+        slab.autotune(True)
+        slab.step(9)
     for _ in range(args.warmup):
         slab.step(1)
     slab.autotune(False)
@@ -402,6 +403,8 @@ def main():
     ap.add_argument("--kedge-points", type=int, default=12, help="photon energies of the K-edge sweep (0: skip)")
     ap.add_argument("--kedge-horizon-fs", type=float, default=30.0)
     ap.add_argument("--thermal-horizon-fs", type=float, default=60.0, help="0: skip")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="default launch shapes (profiling: timings under a profiler mislead the tuner)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "gb300" else args.warmup
     if args.impl == "reference":
