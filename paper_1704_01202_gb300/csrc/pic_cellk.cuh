@@ -471,6 +471,8 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
     const float nref = S.nref_f;
     int c_ee = 0, c_ei = 0, c_ion = 0, c_rej = 0;
     float n_e = 0.f, n_i = 0.f, Te = 0.f, zbar = 0.f, lnL = 2.f;
+    const bool coll = (flags & 3u) != 0;
+    dd Kpre = dd_zero();
     int nnew = 0;
     float Wnew_imp = 0.0f;
 
@@ -525,8 +527,6 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
     __syncwarp();
 
     // ---- binary collisions (Sec. IV): e-e, then e-i; exact energy restore ----
-    const bool coll = (flags & 3u) != 0;
-    dd Kpre = dd_zero();
     if (coll) {
         dd pk = dd_zero(), pki = dd_zero();
         for (int k = lane; k < ne; k += 32) { float4 u = m.eu[m.eperm[k]]; pk = dd_addf(pk, u.w * MC2 * gm1(u.x, u.y, u.z)); }
@@ -554,6 +554,11 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
         for (int p = lane; p < npairs; p += 32) ee(start + 2 * p, start + 2 * p + 1, S.dt);
         __syncwarp();
     }
+
+    }
+    __syncthreads();     // the e-i code next: warps in step, as elsewhere
+
+    if (on) {
     if ((flags & 2u) && ne >= 1 && ni >= 1) {
         const bool e_long = ne >= ni;
         const int nlong = e_long ? ne : ni, nshort = e_long ? ni : ne;

@@ -171,21 +171,65 @@ __device__ __forceinline__ void jglobal(unsigned long long *J, float v)
     if (v != 0.0f) atomicAdd(J, (unsigned long long)fix40(v));
 }
 
+// The 3 x 3 grid points around cell (cx, cy) (columns cx-1..cx+1, rows
+// cy-1..cy+1 wrapped in y; one row repeated in 1D) of the six field
+// components, [component][row][column]: every CIC gather of a particle in
+// the cell reads inside it.  Columns outside [0, nx] hold 0 (their weight is
+// 0).  One warp fills it, 54 loads per cell instead of 24 per particle.
+constexpr int TILE = 54;
+
+template <int DIM>
+__device__ __forceinline__ void load_tile(float *tile, const SlabDev &S, const float *fe, const float *fb, int npts,
+                                          int cx, int cy, int lane)
+{
+    const int W = S.nx + 1;
+    for (int t = lane; t < TILE; t += 32) {
+        const int comp = t / 9, r = (t % 9) / 3, l = t % 3;
+        const int gx = cx - 1 + l;
+        int gy = 0;
+        if (DIM == 2) { gy = cy - 1 + r; gy = gy < 0 ? gy + S.ny : (gy >= S.ny ? gy - S.ny : gy); }
+        const float *F = comp < 3 ? fe + (size_t)comp * npts : fb + (size_t)(comp - 3) * npts;
+        tile[t] = (gx >= 0 && gx <= S.nx) ? __ldg(F + (size_t)gy * W + gx) : 0.0f;
+    }
+}
+
+// interp4 on a tile component: columns / rows are tile-local
+__device__ __forceinline__ float tinterp(const float *T, int x0, int x1, float w0, float w1, int y0, int y1,
+                                         float v0, float v1)
+{
+    return w0 * (v0 * T[y0 * 3 + x0] + v1 * T[y1 * 3 + x0]) + w1 * (v0 * T[y0 * 3 + x1] + v1 * T[y1 * 3 + x1]);
+}
+
 // One particle: gather, Boris, move; returns the next local cell, -1 when
-// it left through an x boundary, -2 when its move is not finite.
+// it left through an x boundary, -2 when its move is not finite.  The
+// fields come from global memory, or from the cell's tile when tile != NULL
+// (the same values and the same arithmetic).
 template <int DIM>
 __device__ __forceinline__ int move_particle(const SlabDev &S, const float *fe, const float *fb, int npts,
-                                             int cx, int cy, float &xi, float &eta, float &ux, float &uy,
-                                             float &uz, float qm, float &xn, float &yn)
+                                             const float *tile, int cx, int cy, float &xi, float &eta, float &ux,
+                                             float &uy, float &uz, float qm, float &xn, float &yn)
 {
     const int W = S.nx + 1;
     GatherPt p = gather_pt<DIM>(S.nx, S.ny, cx, cy, xi, eta);
-    float ex = interp4(fe, W, p.xh0, p.xh1, p.wh0, p.wh1, p.yn0, p.yn1, p.vn0, p.vn1);
-    float ey = interp4(fe + npts, W, p.xn0, p.xn1, p.wn0, p.wn1, p.yh0, p.yh1, p.vh0, p.vh1);
-    float ez = interp4(fe + 2 * npts, W, p.xn0, p.xn1, p.wn0, p.wn1, p.yn0, p.yn1, p.vn0, p.vn1);
-    float bx = interp4(fb, W, p.xn0, p.xn1, p.wn0, p.wn1, p.yh0, p.yh1, p.vh0, p.vh1);
-    float by = interp4(fb + npts, W, p.xh0, p.xh1, p.wh0, p.wh1, p.yn0, p.yn1, p.vn0, p.vn1);
-    float bz = interp4(fb + 2 * npts, W, p.xh0, p.xh1, p.wh0, p.wh1, p.yh0, p.yh1, p.vh0, p.vh1);
+    float ex, ey, ez, bx, by, bz;
+    if (tile) {
+        // tile columns: nodes cx, cx+1 -> 1, 2; half nodes (cx-1, cx) or (cx, cx+1)
+        const int hx0 = xi >= 0.5f ? 1 : 0, hy0 = DIM == 2 ? (eta >= 0.5f ? 1 : 0) : 1;
+        const int ny0 = DIM == 2 ? 1 : 1, ny1 = DIM == 2 ? 2 : 1, hy1 = DIM == 2 ? hy0 + 1 : 1;
+        ex = tinterp(tile + 0, hx0, hx0 + 1, p.wh0, p.wh1, ny0, ny1, p.vn0, p.vn1);
+        ey = tinterp(tile + 9, 1, 2, p.wn0, p.wn1, hy0, hy1, p.vh0, p.vh1);
+        ez = tinterp(tile + 18, 1, 2, p.wn0, p.wn1, ny0, ny1, p.vn0, p.vn1);
+        bx = tinterp(tile + 27, 1, 2, p.wn0, p.wn1, hy0, hy1, p.vh0, p.vh1);
+        by = tinterp(tile + 36, hx0, hx0 + 1, p.wh0, p.wh1, ny0, ny1, p.vn0, p.vn1);
+        bz = tinterp(tile + 45, hx0, hx0 + 1, p.wh0, p.wh1, hy0, hy1, p.vh0, p.vh1);
+    } else {
+        ex = interp4(fe, W, p.xh0, p.xh1, p.wh0, p.wh1, p.yn0, p.yn1, p.vn0, p.vn1);
+        ey = interp4(fe + npts, W, p.xn0, p.xn1, p.wn0, p.wn1, p.yh0, p.yh1, p.vh0, p.vh1);
+        ez = interp4(fe + 2 * npts, W, p.xn0, p.xn1, p.wn0, p.wn1, p.yn0, p.yn1, p.vn0, p.vn1);
+        bx = interp4(fb, W, p.xn0, p.xn1, p.wn0, p.wn1, p.yh0, p.yh1, p.vh0, p.vh1);
+        by = interp4(fb + npts, W, p.xh0, p.xh1, p.wh0, p.wh1, p.yn0, p.yn1, p.vn0, p.vn1);
+        bz = interp4(fb + 2 * npts, W, p.xh0, p.xh1, p.wh0, p.wh1, p.yh0, p.yh1, p.vh0, p.vh1);
+    }
     boris(ux, uy, uz, ex, ey, ez, bx, by, bz, qm, S.dt);
     float ig = rsqrtf(1.0f + ux * ux + uy * uy + uz * uz);
     const float c = (float)kCnmPerFs;
@@ -209,8 +253,8 @@ __device__ __forceinline__ void wrap_offsets(float xn, float yn, float &xi, floa
 }
 
 template <int DIM>
-__device__ void push_cell(const PushArgs &a, const SlabDev &S, int s, int g, int lane, float *sj, dd &esc,
-                          int &esc_e, int &esc_i)
+__device__ void push_cell(const PushArgs &a, const SlabDev &S, int s, int g, int lane, float *sj, float *tile,
+                          dd &esc, int &esc_e, int &esc_i)
 {
     constexpr int NJ = DIM == 2 ? 40 : 11;
     const int lc = g - S.cell0;
@@ -219,6 +263,11 @@ __device__ void push_cell(const PushArgs &a, const SlabDev &S, int s, int g, int
     const float *fe = a.fldE + S.fld_off, *fb = a.fldB + S.fld_off;
     const float MC2 = (float)kMeC2;
     float acc[2] = {0.0f, 0.0f};
+    if (do_push) {
+        __syncwarp();
+        load_tile<DIM>(tile, S, fe, fb, a.npts, cx, cy, lane);
+        __syncwarp();
+    }
 
     for (int pass = 0; pass < 2; ++pass) {
         const bool elec = pass == 0;
@@ -248,7 +297,7 @@ __device__ void push_cell(const PushArgs &a, const SlabDev &S, int s, int g, int
                     else { q = (float)(__float_as_int(P1.w) & 0xff) + P1.y; m = S.m_ion; w = S.w_ion; }
                     float xi = P0.x, eta = P0.y, ux = P0.z, uy = P0.w, uz = P1.x, xn, yn;
                     float ke = MC2 * m * gm1(ux, uy, uz);
-                    int nc = move_particle<DIM>(S, fe, fb, a.npts, cx, cy, xi, eta, ux, uy, uz, q / m, xn, yn);
+                    int nc = move_particle<DIM>(S, fe, fb, a.npts, tile, cx, cy, xi, eta, ux, uy, uz, q / m, xn, yn);
                     if (nc == -2) {
                         nk = -1;
                         atomicOr(a.err, ERR_NUMERIC);
@@ -335,8 +384,10 @@ __device__ void push_flush(const PushArgs &a, int slab, dd &esc, int &esc_e, int
 __global__ void __launch_bounds__(32 * PUSH_WARPS, 2) k_push(PushArgs a)
 {
     __shared__ float s_j[PUSH_WARPS][JROWS * JPITCH];
+    __shared__ float s_t[PUSH_WARPS][TILE];
     const int lane = threadIdx.x & 31;
     float *sj = s_j[threadIdx.x >> 5];
+    float *tile = s_t[threadIdx.x >> 5];
     int cur = -1;
     dd esc = dd_zero();
     int esc_e = 0, esc_i = 0;
@@ -355,8 +406,8 @@ __global__ void __launch_bounds__(32 * PUSH_WARPS, 2) k_push(PushArgs a)
             for (int k = a.cs_i[g] + lane; k < a.cs_i[g + 1]; k += 32) a.ikey[k] = -1;
             continue;
         }
-        if (S.ny > 1) push_cell<2>(a, S, s, g, lane, sj, esc, esc_e, esc_i);
-        else push_cell<1>(a, S, s, g, lane, sj, esc, esc_e, esc_i);
+        if (S.ny > 1) push_cell<2>(a, S, s, g, lane, sj, tile, esc, esc_e, esc_i);
+        else push_cell<1>(a, S, s, g, lane, sj, tile, esc, esc_e, esc_i);
     }
     push_flush(a, cur, esc, esc_e, esc_i, lane);
 }
@@ -381,8 +432,8 @@ __global__ void k_push_new(PushArgs a)
             const float *fe = a.fldE + S.fld_off, *fb = a.fldB + S.fld_off;
             float xi = P0.x, eta = P0.y, ux = P0.z, uy = P0.w, uz = P1.x, xn, yn;
             float ke = (float)kMeC2 * gm1(ux, uy, uz);
-            int nc = S.ny > 1 ? move_particle<2>(S, fe, fb, a.npts, cx, cy, xi, eta, ux, uy, uz, -1.0f, xn, yn)
-                              : move_particle<1>(S, fe, fb, a.npts, cx, cy, xi, eta, ux, uy, uz, -1.0f, xn, yn);
+            int nc = S.ny > 1 ? move_particle<2>(S, fe, fb, a.npts, nullptr, cx, cy, xi, eta, ux, uy, uz, -1.0f, xn, yn)
+                              : move_particle<1>(S, fe, fb, a.npts, nullptr, cx, cy, xi, eta, ux, uy, uz, -1.0f, xn, yn);
             if (nc == -2) {
                 nk = -1;
                 atomicOr(a.err, ERR_NUMERIC);
