@@ -270,6 +270,13 @@ const char *pic_last_error(const pic_ctx *c);
  * implementations: out[4*i..] = philox(ctr[4*i..], key) for i < n. */
 pic_status pic_philox_check(const uint32_t *ctr, const uint32_t key[2], uint32_t *out, int n);
 
+/* The in-cell ordering of the device (ascending key, ties by id; the
+ * canonical order every per-cell rule follows), run on n <= 1024 given
+ * entries by one warp with the algorithm a cell of that size uses:
+ * order[k] = index of the entry at position k.  For checking it against
+ * other implementations. */
+pic_status pic_order_check(const uint64_t *key, const uint64_t *id, int n, uint16_t *order);
+
 /* The same check without any device allocation.  The paper has no
  * counterpart: this serves callers that must not allocate, e.g. a host
  * thread of a serving loop whose device memory budget is fixed up front, or

@@ -40,7 +40,7 @@ ABI_FUNCTIONS = ["pic_required_bytes", "pic_init", "pic_source", "pic_load_elect
                  "pic_timing", "pic_batch_required_bytes", "pic_batch_init", "pic_batch_admit",
                  "pic_batch_retire", "pic_batch_slot", "pic_batch_diagnostics", "pic_batch_counts",
                  "pic_batch_get_electrons", "pic_batch_get_ions", "pic_philox_check_static",
-                 "pic_use_graphs", "pic_autotune"]
+                 "pic_use_graphs", "pic_autotune", "pic_order_check"]
 
 
 def _sources():
@@ -145,6 +145,8 @@ def lib():
             L.pic_philox_check_static.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
                                                   C.POINTER(C.c_uint32), C.c_int]
             L.pic_use_graphs.argtypes = [_P, C.c_int]
+            L.pic_order_check.argtypes = [C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.c_int,
+                                          C.POINTER(C.c_uint16)]
             L.pic_autotune.argtypes = [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]
             L.pic_timing.argtypes = [_P, C.c_int, _D, C.POINTER(C.c_int64)]
             L.pic_batch_required_bytes.restype = C.c_size_t
@@ -493,3 +495,14 @@ def philox_check(ctr: np.ndarray, key) -> np.ndarray:
     if st != 0:
         raise PicError(f"pic_philox_check: {STATUS.get(st, st)}")
     return o
+
+
+def order_check(key: np.ndarray, ids: np.ndarray) -> np.ndarray:
+    """Device in-cell ordering of (key, id) entries: positions -> entry index."""
+    k = np.ascontiguousarray(key, dtype=np.uint64)
+    i = np.ascontiguousarray(ids, dtype=np.uint64)
+    o = np.zeros(k.size, dtype=np.uint16)
+    st = lib().pic_order_check(_p(k, C.c_uint64), _p(i, C.c_uint64), k.size, _p(o, C.c_uint16))
+    if st != 0:
+        raise PicError(f"pic_order_check: {STATUS.get(st, st)}")
+    return o.astype(np.int64)

@@ -1558,6 +1558,31 @@ pic_status pic_philox_check(const uint32_t *ctr, const uint32_t key[2], uint32_t
     return st;
 }
 
+pic_status pic_order_check(const uint64_t *key, const uint64_t *id, int n, uint16_t *order)
+{
+    if (!key || !id || !order || n <= 0 || n > 1024) return PIC_ERR_ARG;
+    int np = 1;
+    while (np < n) np <<= 1;
+    const size_t smem = (size_t)np * 16 + (size_t)n * 16 + 256 * 4 + (size_t)np * 2;
+    char *d = nullptr;
+    const size_t bytes = (size_t)n * 16 + (size_t)n * 2;
+    if (cudaMalloc(&d, bytes) != cudaSuccess) return PIC_ERR_OOM;
+    pic_status st = PIC_OK;
+    unsigned long long *dk = (unsigned long long *)d, *di = dk + n;
+    unsigned short *dout = (unsigned short *)(di + n);
+    if (cudaMemcpy(dk, key, sizeof(uint64_t) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(di, id, sizeof(uint64_t) * n, cudaMemcpyHostToDevice) != cudaSuccess)
+        st = PIC_ERR_CUDA;
+    if (st == PIC_OK) {
+        k_order_check<<<1, 32, smem>>>(dk, di, n, dout);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpy(order, dout, sizeof(uint16_t) * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+            st = PIC_ERR_CUDA;
+    }
+    cudaFree(d);
+    return st;
+}
+
 // Scratch of pic_philox_check_static: counters then outputs, 4 words each.
 static __device__ __align__(256) uint32_t g_philox_scratch[8 * PIC_PHILOX_STATIC_MAX];
 

@@ -148,6 +148,81 @@ __device__ void warp_bitonic(unsigned long long *key, IdT *id, unsigned short *s
     __syncwarp();
 }
 
+// Sort of larger cells (n > kRadixMin), same result as warp_bitonic: a
+// stable LSD radix sort (four 8-bit digits) of the keys' high 32 bits packed
+// with the slot, then the rare runs of equal high words reordered by (low
+// word, id) by one lane.  buf holds 2 n packed entries, hist 256 counters.
+constexpr int kRadixMin = 128;
+
+template <class IdT>
+__device__ void warp_radix(const unsigned long long *key, IdT *id, unsigned short *slot, unsigned long long *tmp,
+                           unsigned long long *buf, int *hist, int n, int lane)
+{
+    unsigned long long *A = buf, *B = buf + n;
+    for (int k = lane; k < n; k += 32) A[k] = (key[k] & 0xffffffff00000000ull) | (unsigned long long)k;
+    for (int pass = 0; pass < 4; ++pass) {
+        const int shift = 32 + 8 * pass;
+        for (int b = lane; b < 256; b += 32) hist[b] = 0;
+        __syncwarp();
+        for (int k = lane; k < n; k += 32) atomicAdd(hist + (int)((A[k] >> shift) & 255u), 1);
+        __syncwarp();
+        // exclusive scan of the 256 counts: eight per lane, then across lanes
+        int c[8], run = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) { c[q] = hist[lane * 8 + q]; run += c[q]; }
+        int incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += t;
+        }
+        int off = incl - run;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) { hist[lane * 8 + q] = off; off += c[q]; }
+        __syncwarp();
+        // stable scatter, 32 entries at a time in order
+        for (int base = 0; base < n; base += 32) {
+            const int k = base + lane;
+            const bool act = k < n;
+            const unsigned long long v = act ? A[k] : 0ull;
+            const int d = act ? (int)((v >> shift) & 255u) : -1;
+            const unsigned peers = __match_any_sync(FULL, d);
+            const int at = act ? hist[d] + __popc(peers & ((1u << lane) - 1u)) : 0;
+            __syncwarp();
+            if (act) {
+                B[at] = v;
+                if (lane == __ffs(peers) - 1) hist[d] += __popc(peers);
+            }
+            __syncwarp();
+        }
+        unsigned long long *t = A; A = B; B = t;
+    }
+    // equal high words (rare): order those runs by (low word, id)
+    bool tie = false;
+    for (int k = lane; k + 1 < n; k += 32) tie |= (A[k] >> 32) == (A[k + 1] >> 32);
+    if (__any_sync(FULL, tie) && lane == 0) {
+        for (int k = 1; k < n; ++k) {
+            unsigned long long v = A[k];
+            int j = k - 1;
+            while (j >= 0 && (A[j] >> 32) == (v >> 32)) {
+                const int sa = (int)(A[j] & 0xffffu), sb = (int)(v & 0xffffu);
+                const bool gt = key[sa] > key[sb] || (key[sa] == key[sb] && id[sa] > id[sb]);
+                if (!gt) break;
+                A[j + 1] = A[j];
+                --j;
+            }
+            A[j + 1] = v;
+        }
+    }
+    __syncwarp();
+    for (int k = lane; k < n; k += 32) slot[k] = (unsigned short)(A[k] & 0xffffu);
+    __syncwarp();
+    for (int k = lane; k < n; k += 32) tmp[k] = (unsigned long long)id[slot[k]];
+    __syncwarp();
+    for (int k = lane; k < n; k += 32) id[k] = (IdT)tmp[k];
+    __syncwarp();
+}
+
 __device__ __forceinline__ float cic_w(float x, int node)
 {
     float d = fabsf(x - (float)node);
@@ -169,6 +244,8 @@ struct WarpMem {
     float *dE;                  // [16] continuum lowering per charge state
     float *Pz;                  // [16] impact-ionization probability per charge
     float4 *lz;                 // [NS] Lotz constants of one charge state: P, 1/P, ln P, a q
+    unsigned long long *rbuf;   // [2 max(cap_ce, cap_ci)] radix sort (only when a cell can exceed kRadixMin)
+    int *rhist;                 // [256]
     dd *ph;                     // [2 MAXB] photon bin scratch
     int *phc;                   // [MAXB] events per bin so far
 };
@@ -183,6 +260,8 @@ __host__ __device__ inline size_t warp_mem_bytes(int ce, int ci, int cn)
          + align16((size_t)ci * 2);
     b += align16((size_t)cn * sizeof(NewE));
     b += 16 * 4 + 16 * 4 + NS * 16 + 2 * MAXB * 8 + MAXB * 4;
+    const int cm = ce > ci ? ce : ci;
+    if (cm > kRadixMin) b += align16((size_t)cm * 16) + 256 * 4;
     return b;
 }
 
@@ -204,7 +283,14 @@ __device__ inline WarpMem carve(char *base, int ce, int ci, int cn)
     m.Pz = (float *)p; p += 16 * 4;
     m.lz = (float4 *)p; p += NS * 16;
     m.ph = (dd *)p; p += 2 * MAXB * 8;
-    m.phc = (int *)p;
+    m.phc = (int *)p; p += MAXB * 4;
+    const int cm = ce > ci ? ce : ci;
+    m.rbuf = nullptr; m.rhist = nullptr;
+    if (cm > kRadixMin) {
+        p = (char *)(((size_t)p + 15) & ~(size_t)15);
+        m.rbuf = (unsigned long long *)p; p += align16((size_t)cm * 16);
+        m.rhist = (int *)p;
+    }
     return m;
 }
 

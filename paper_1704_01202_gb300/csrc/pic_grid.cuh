@@ -401,6 +401,27 @@ __global__ void k_photon_energy(const ph2 *ph, int ncell, int nb, const float *h
     if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(out, v);
 }
 
+// the in-cell ordering of one cell (bitonic up to kRadixMin entries, radix
+// above), run by one warp on given keys and ids: order[k] = slot at position k
+__global__ void k_order_check(const unsigned long long *key_in, const unsigned long long *id_in, int n,
+                              unsigned short *order)
+{
+    extern __shared__ __align__(16) char sm[];
+    int np = 1;
+    while (np < n) np <<= 1;
+    unsigned long long *key = (unsigned long long *)sm;                  // [np]
+    unsigned long long *id = key + np;                                    // [np]
+    unsigned long long *buf = id + np;                                    // [2 n]
+    int *hist = (int *)(buf + 2 * n);                                     // [256]
+    unsigned short *slot = (unsigned short *)(hist + 256);               // [np]
+    const int lane = threadIdx.x;
+    for (int k = lane; k < n; k += 32) { key[k] = key_in[k]; id[k] = id_in[k]; slot[k] = (unsigned short)k; }
+    __syncwarp();
+    if (n > kRadixMin) warp_radix<unsigned long long>(key, id, slot, key, buf, hist, n, lane);
+    else warp_bitonic<unsigned long long>(key, id, slot, key, n, lane);
+    for (int k = lane; k < n; k += 32) order[k] = slot[k];
+}
+
 __global__ void k_philox_check(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, int n)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;

@@ -375,3 +375,19 @@ def test_thermalization_conserves_cell_momentum_energy_gpu(tables):
         k0, k1 = (w0 * kin(st.eu[m0])).sum(), (w1 * kin(e["u"][m1])).sum()
         assert abs(k1 / k0 - 1) < 2e-6, (c, k0, k1)
     g.close()
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 64, 100, 128, 129, 300, 512, 1000])
+def test_cell_order_matches_lexsort(n):
+    """The device's in-cell ordering (bitonic up to 128 entries, radix sort
+    above) is the ascending (key, id) order: random keys, keys whose high
+    words collide, and fully equal keys broken by id."""
+    rng = np.random.default_rng(n)
+    ids = rng.permutation(np.arange(10 * n, dtype=np.uint64))[:n]
+    cases = [rng.integers(0, 2**63, n, dtype=np.uint64) * np.uint64(2) + rng.integers(0, 2, n, dtype=np.uint64),
+             (rng.integers(0, 4, n, dtype=np.uint64) << np.uint64(32)) | rng.integers(0, 2**32, n, dtype=np.uint64),
+             (rng.integers(0, 3, n, dtype=np.uint64) << np.uint64(40)) | rng.integers(0, 3, n, dtype=np.uint64)]
+    for key in cases:
+        got = pkg.order_check(key, ids)
+        ref = np.lexsort((ids, key))
+        assert np.array_equal(got, ref)
