@@ -152,7 +152,7 @@ __device__ void warp_bitonic(unsigned long long *key, IdT *id, unsigned short *s
 // stable LSD radix sort (four 8-bit digits) of the keys' high 32 bits packed
 // with the slot, then the rare runs of equal high words reordered by (low
 // word, id) by one lane.  buf holds 2 n packed entries, hist 256 counters.
-constexpr int kRadixMin = 128;
+constexpr int kRadixMin = 512;
 
 template <class IdT>
 __device__ void warp_radix(const unsigned long long *key, IdT *id, unsigned short *slot, unsigned long long *tmp,

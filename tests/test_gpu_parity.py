@@ -377,9 +377,9 @@ def test_thermalization_conserves_cell_momentum_energy_gpu(tables):
     g.close()
 
 
-@pytest.mark.parametrize("n", [1, 2, 31, 64, 100, 128, 129, 300, 512, 1000])
+@pytest.mark.parametrize("n", [1, 2, 31, 64, 100, 128, 129, 300, 512, 513, 1000])
 def test_cell_order_matches_lexsort(n):
-    """The device's in-cell ordering (bitonic up to 128 entries, radix sort
+    """The device's in-cell ordering (bitonic up to 512 entries, radix sort
     above) is the ascending (key, id) order: random keys, keys whose high
     words collide, and fully equal keys broken by id."""
     rng = np.random.default_rng(n)
