@@ -391,3 +391,27 @@ def test_cell_order_matches_lexsort(n):
         got = pkg.order_check(key, ids)
         ref = np.lexsort((ids, key))
         assert np.array_equal(got, ref)
+
+
+def test_small_slab_full_500_steps(tables):
+    """The plain 1D slab at its full size and length (128 x 2 nm cells,
+    256 e + 64 i per cell, collisions, Lotz ionization and recombination,
+    500 steps of 0.02 fs): FP32 device against the FP64 oracle, run
+    independently.  Single trajectories decorrelate (chaos), so the charge
+    state, temperature, density and event counts are compared."""
+    cfg = P.cfg_small_1d()
+    st = P.init_particles(cfg)
+    g, o = _run_both(cfg, tables, st, 500)
+    dg = g.diagnostics()
+    to, co = o.tallies()
+    csd_o, _ = o.diag()
+    zbar_o = float((np.arange(len(csd_o)) * csd_o).sum())
+    e = o.electrons()
+    ke = 510998.95 * (e["u"] ** 2).sum(1) / (np.sqrt(1 + (e["u"] ** 2).sum(1)) + 1)
+    te_o = (2.0 / 3.0) * (e["w"] * ke).sum() / e["w"].sum()
+    assert abs(dg["Zbar"] / zbar_o - 1) < 0.01, (dg["Zbar"], zbar_o)
+    assert abs(dg["T_e_eV"] / te_o - 1) < 0.02, (dg["T_e_eV"], te_o)
+    assert abs(dg["n_e"] / len(e["id"]) - 1) < 0.02
+    for k in ("ION", "REC", "EE", "EI"):
+        assert abs(dg["counts"][k] / max(co[k], 1) - 1) < 0.03, (k, dg["counts"][k], co[k])
+    assert np.abs(dg["csd"] - csd_o).sum() < 0.02
