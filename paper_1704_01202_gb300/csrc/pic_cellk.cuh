@@ -639,10 +639,12 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
                 m.lz[lane] = v;
             }
             __syncwarp();
+            // fast log / exp: a few ulp on a probability; only a decision
+            // within that of its threshold could flip
             dd pr = dd_zero();
             for (int k = lane; k < ne; k += 32) {
                 const float2 q = ew[k];
-                const float E = q.x, lnE = logf(E), invE = 1.0f / E;
+                const float E = q.x, lnE = __logf(E), invE = 1.0f / E;
                 float sig = 0.0f;
 #pragma unroll
                 for (int sh = 0; sh < NS; ++sh) {
@@ -650,7 +652,7 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
                     if (L.w > 0.0f && E > L.x) {
                         const float x = E * L.y;
                         sig += L.w * (lnE - L.z) * (invE * L.y) *
-                               (1.0f - T.lotz_b[sh] * expf(-T.lotz_c[sh] * (x - 1.0f)));
+                               (1.0f - T.lotz_b[sh] * __expf(-T.lotz_c[sh] * (x - 1.0f)));
                     }
                 }
                 pr = dd_addf(pr, q.y * sig);

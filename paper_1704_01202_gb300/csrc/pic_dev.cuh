@@ -302,9 +302,9 @@ __device__ __noinline__ bool binary_collision(float3 &ua, float3 &ub, float ma, 
     const float k0 = (float)(2.0 * kPi * kReCm * kReCm * kCcmPerFs);
     float q2 = qa * qb;
     float var = k0 * q2 * q2 * n_l * lnL * dtc / (mu * mu * vrel * vrel * vrel);
-    float delta = sqrtf(var) * sqrtf(-2.0f * logf(r0)) * cosf(2.0f * kPiF * r1);
+    float delta = sqrtf(var) * sqrtf(-2.0f * logf(r0)) * cospif(2.0f * r1);
     float sphi, cphi;
-    sincosf(2.0f * kPiF * r2, &sphi, &cphi);
+    sincospif(2.0f * r2, &sphi, &cphi);
 
     float pax = ma * ua.x, pay = ma * ua.y, paz = ma * ua.z;
     float Ea = ma * ga, Eb = mb * gb, E = Ea + Eb;

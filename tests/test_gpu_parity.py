@@ -414,4 +414,6 @@ def test_small_slab_full_500_steps(tables):
     assert abs(dg["n_e"] / len(e["id"]) - 1) < 0.02
     for k in ("ION", "REC", "EE", "EI"):
         assert abs(dg["counts"][k] / max(co[k], 1) - 1) < 0.03, (k, dg["counts"][k], co[k])
-    assert np.abs(dg["csd"] - csd_o).sum() < 0.02
+    # independent samples of ~8200 ions once the trajectories decorrelate:
+    # the L1 distance of two such histograms is ~0.02 on average
+    assert np.abs(dg["csd"] - csd_o).sum() < 0.06
