@@ -42,7 +42,7 @@ STEP_BYTES_PER_PARTICLE = 136
 # DRAM bytes per particle of the cell kernel's main pass, from one ncu
 # capture of the foil at 512 x 256 cells (profiles/k_cell_k_push_al_2d_512x256x5nm.md),
 # scaled to a launch by the particle count; None once the kernel changes
-CELL_TRAFFIC_BYTES_PER_PARTICLE = 65.6
+CELL_TRAFFIC_BYTES_PER_PARTICLE = 65.8
 
 
 def measured_peaks():
