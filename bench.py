@@ -249,6 +249,7 @@ def run_gpu(args):
     served = run_served(pkg, tab, args) if args.serve_n > 0 else None
     kedge_scan = run_kedge(pkg, tab, args) if args.kedge_points > 0 else None
     thermal = run_thermal(pkg, tab, args) if args.thermal_horizon_fs > 0 else None
+    extreme = run_extreme(pkg, tab, args) if args.extreme_horizon_fs > 0 else None
     if dist:
         dist.barrier()
     if rank == 0:
@@ -262,7 +263,8 @@ def run_gpu(args):
                "roofline": roof, "step_hbm_gbs": step_gbs, "cpu_baseline": cb, "e2e": e2e,
                "gpu_launches": int(launches), "clocks": clk, "kernel_ms": {k: v / max(nrec, 1) for k, v in tms.items()},
                "autotune": {"cell_warps_per_cta": tuned[0], "cell_ms_1_2_4_8": [float(x) for x in tuned[1]]},
-               "ensemble": ensemble, "served": served, "kedge_scan": kedge_scan, "thermalization": thermal}
+               "ensemble": ensemble, "served": served, "kedge_scan": kedge_scan, "thermalization": thermal,
+               "extreme_10keV": extreme}
         print(json.dumps(out))
     if dist:
         dist.destroy_process_group()
@@ -367,6 +369,22 @@ def run_thermal(pkg, tab, args):
     return r
 
 
+def run_extreme(pkg, tab, args):
+    """The 10 keV extreme case (Sec. VI C): 8 keV photoelectrons and
+    1.4 keV Auger electrons in the small slab under a 10 keV, 20 fs,
+    1e19 W/cm^2 pulse, with and without forced thermalization, and the share
+    of the free-electron energy above 700 eV."""
+    from paper_1704_01202_gb300 import thermal
+    cfg = P.cfg_small_1d(nx=128, flags=P.F_ALL)
+    pulse = P.Pulse(I_peak_Wcm2=1.0e19, fwhm_fs=20.0, t_peak_fs=30.0, hv_eV=10000.0)
+    r = thermal.compare(tab, cfg, pulse, P.init_particles, args.extreme_horizon_fs, 10.0, P.F_THERM, tail_eV=700.0)
+    r["workload"] = (f"al_1d_128x2nm_256e64i, 10 keV / 20 fs / 1e19 W/cm^2 peak at 30 fs, "
+                     f"{args.extreme_horizon_fs:g} fs, with and without forced thermalization")
+    for k in ("Zbar", "Zbar_therm", "T_e_eV", "T_e_eV_therm", "tail_number_share", "tail_energy_share"):
+        r[k] = [round(x, 4) for x in r[k]]
+    return r
+
+
 def run_e2e(pkg, cfg, tab, pl, st, args, world, n0):
     """Public API with host buffers: context, H2D load, steps with a D2H
     diagnostics read after each."""
@@ -403,6 +421,7 @@ def main():
     ap.add_argument("--kedge-points", type=int, default=12, help="photon energies of the K-edge sweep (0: skip)")
     ap.add_argument("--kedge-horizon-fs", type=float, default=30.0)
     ap.add_argument("--thermal-horizon-fs", type=float, default=60.0, help="0: skip")
+    ap.add_argument("--extreme-horizon-fs", type=float, default=60.0, help="10 keV case; 0: skip")
     ap.add_argument("--no-autotune", action="store_true",
                     help="default launch shapes (profiling: timings under a profiler mislead the tuner)")
     args = ap.parse_args()

@@ -18,7 +18,21 @@ import time
 from . import Batch, default_capacity
 
 
-def compare(tables, cfg, pulse, init_state, horizon_fs: float, every_fs: float = 5.0, therm_flag: int = 256) -> dict:
+def tail_share(e: dict, threshold_eV: float) -> tuple[float, float]:
+    """Weight fraction of the electrons above threshold_eV and the fraction
+    of the free-electron kinetic energy they carry."""
+    import numpy as np
+    u = e["u"].astype(np.float64)
+    u2 = (u * u).sum(axis=1)
+    ke = 510998.95 * u2 / (np.sqrt(1.0 + u2) + 1.0)
+    w = e["w"].astype(np.float64)
+    hot = ke > threshold_eV
+    W, K = w.sum(), (w * ke).sum()
+    return (float(w[hot].sum() / W) if W > 0 else 0.0, float((w * ke)[hot].sum() / K) if K > 0 else 0.0)
+
+
+def compare(tables, cfg, pulse, init_state, horizon_fs: float, every_fs: float = 5.0, therm_flag: int = 256,
+            tail_eV: float = 0.0) -> dict:
     import copy
     import torch
     cfg_t = copy.deepcopy(cfg)
@@ -32,6 +46,8 @@ def compare(tables, cfg, pulse, init_state, horizon_fs: float, every_fs: float =
         per = max(1, int(round(every_fs / cfg.dt_fs)))
         nsteps = int(round(horizon_fs / cfg.dt_fs))
         out = {"t_fs": [], "Zbar": [], "Zbar_therm": [], "T_e_eV": [], "T_e_eV_therm": []}
+        if tail_eV > 0:
+            out["tail_number_share"], out["tail_energy_share"] = [], []
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         done = 0
@@ -45,6 +61,10 @@ def compare(tables, cfg, pulse, init_state, horizon_fs: float, every_fs: float =
             out["Zbar_therm"].append(b["Zbar"])
             out["T_e_eV"].append(a["T_e_eV"])
             out["T_e_eV_therm"].append(b["T_e_eV"])
+            if tail_eV > 0:     # of the non-thermal run (outside the timing would be fairer; it is small)
+                ns, es = tail_share(bt.electrons(k_plain), tail_eV)
+                out["tail_number_share"].append(ns)
+                out["tail_energy_share"].append(es)
         wall = time.perf_counter() - t0
     finally:
         bt.close()

@@ -417,3 +417,25 @@ def test_small_slab_full_500_steps(tables):
     # independent samples of ~8200 ions once the trajectories decorrelate:
     # the L1 distance of two such histograms is ~0.02 on average
     assert np.abs(dg["csd"] - csd_o).sum() < 0.06
+
+
+def test_single_step_10kev(tables):
+    """The 10 keV extreme case (Sec. VI C): a rad step at 1e19 W/cm^2 makes
+    8 keV photoelectrons and 1.4 keV Auger electrons (relativistic
+    collisions, gamma - 1 ~ 0.016); per-particle parity with the oracle,
+    with and without forced thermalization."""
+    for flags in (P.F_ALL, P.F_ALL | P.F_THERM):
+        cfg = P.cfg_small_1d(nx=32, ppc_e=64, ppc_i=16, T_e_eV=50.0, flags=flags, rad_every=1)
+        pl = P.Pulse(I_peak_Wcm2=1.0e19, fwhm_fs=20.0, t_peak_fs=0.0, hv_eV=10000.0, n_bins=2, bandwidth_eV=20.0)
+        tab = dict(tables)
+        tab["sigma_photo"] = tables["sigma_photo"] * 100.0      # enough events in one step
+        st = _busy(cfg, seed=12)
+        ph = P.photons_uniform(cfg, pl, 50.0)
+        g, o = _run_both(cfg, tab, st, 1, pulse=pl, photons=ph)
+        res = compare_state(g.electrons(), o.electrons(), g.ions(), o.ions(), cfg.nx, cfg.ny)
+        _assert_parity(res, st.n_e)
+        _, co = o.tallies()
+        assert co["PH0"] > 0 and co["AUG"] > 0, co
+        e = g.electrons()
+        u2 = (e["u"].astype(np.float64) ** 2).sum(axis=1)
+        assert (np.sqrt(1 + u2) - 1).max() > 0.012 or flags & P.F_THERM   # relativistic photoelectrons
