@@ -231,14 +231,14 @@ int cap_for_share(const int *hist, double share, int lo)
 }
 
 // Staging sizes of the cell tiers from the last sort's cell populations:
-// tier 0 holds 90 % of the cells of each species (powers of two, at least
+// tier 0 holds 75 % of the cells of each species (powers of two, at least
 // 64 electrons / 32 ions); tier 1 the largest cells x 1.25 (at most 1024 /
 // 256), launched only when larger than tier 0.  Warps per CTA of tier 0 from
 // the autotuner's choice for its sizes, else the most that fit.
 pic_status configure_cell_launch(pic_ctx *c, const int *hist_e, const int *hist_i, int max_e, int max_i)
 {
-    int ce = std::min(cap_for_share(hist_e, 0.9, 64), 1024);
-    int ci = std::min(cap_for_share(hist_i, 0.9, 32), 256);
+    int ce = std::min(cap_for_share(hist_e, 0.75, 64), 1024);
+    int ci = std::min(cap_for_share(hist_i, 0.75, 32), 256);
     int ce1 = std::min(next_pow2(std::max(64, (int)(max_e * 1.25) + 1)), 1024);
     int ci1 = std::min(next_pow2(std::max(32, (int)(max_i * 1.25) + 1)), 256);
     ce = std::min(ce, ce1);
