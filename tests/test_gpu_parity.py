@@ -439,3 +439,42 @@ def test_single_step_10kev(tables):
         e = g.electrons()
         u2 = (e["u"].astype(np.float64) ** 2).sum(axis=1)
         assert (np.sqrt(1 + u2) - 1).max() > 0.012 or flags & P.F_THERM   # relativistic photoelectrons
+
+
+def test_k_vacancy_history_over_a_pulse(tables):
+    """A 64 x 2 cell slice of the 2D foil through 200 steps (4 fs) of a
+    1.6 keV pulse peaking at 5 fs: K-shell photoionization fills K
+    vacancies that then decay by KLL Auger or K-alpha over many rad steps
+    (Sec. III).  The two sides run independently; their event histories
+    agree within the statistics of decorrelated trajectories."""
+    cfg = P.cfg_foil_2d(nx=64, ny=2)
+    st = P.init_particles(cfg)
+    g, o = _run_both(cfg, tables, st, 200, pulse=P.pulse_foil_2d(t_peak_fs=5.0))
+    cg = g.diagnostics()["counts"]
+    _, co = o.tallies()
+    assert co["AUG"] > 100 and co["KA"] > 0, co
+    for k, rel, floor in (("PH0", 0.03, 4), ("AUG", 0.03, 4), ("PART", 0.2, 4), ("KA", 0.3, 3),
+                          ("ION", 0.05, 10), ("REC", 0.12, 20)):
+        assert abs(cg[k] - co[k]) <= max(floor, rel * co[k]), (k, cg[k], co[k])
+    nk_g = int((g.ions()["nK"] > 0).sum())
+    nk_o = int((o.ions()["nK"] > 0).sum())
+    assert abs(nk_g - nk_o) <= max(4, 0.1 * nk_o), (nk_g, nk_o)
+
+
+def test_partial_events_only_below_one_ion_weight(tables):
+    """The same slice early in the pulse (peak at 80 fs, first 5 fs): the
+    photon number of a bin in a cell stays below one ion's weight, so every
+    absorption is a partial event (the fraction moves the ion's outer
+    electron, Sec. III) and no K vacancy, Auger or K-alpha appears on
+    either side."""
+    cfg = P.cfg_foil_2d(nx=64, ny=2)
+    st = P.init_particles(cfg)
+    g, o = _run_both(cfg, tables, st, 250, pulse=P.pulse_foil_2d(t_peak_fs=80.0))
+    ph = g.photons()
+    assert ph.max() < cfg.w_ion
+    cg = g.diagnostics()["counts"]
+    _, co = o.tallies()
+    for cnt in (cg, co):
+        assert cnt["PART"] > 0 and cnt["PH0"] > 0 and cnt["AUG"] == 0 and cnt["KA"] == 0, cnt
+    assert int((g.ions()["nK"] > 0).sum()) == 0 and int((o.ions()["nK"] > 0).sum()) == 0
+    assert abs(cg["PART"] - co["PART"]) <= max(4, 0.1 * co["PART"]), (cg["PART"], co["PART"])
