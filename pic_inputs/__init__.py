@@ -223,7 +223,8 @@ class SlabConfig:
 
     @property
     def w_ion(self) -> float:
-        return 1.0 / self.ppc_i
+        # rounded to FP32 so that both precisions see the same ion weight
+        return float(np.float32(1.0 / self.ppc_i))
 
     @property
     def w_e(self) -> float:
@@ -265,6 +266,24 @@ def cfg_foil_2d(**kw) -> SlabConfig:
 
 def pulse_foil_2d(**kw) -> Pulse:
     p = Pulse(I_peak_Wcm2=1.0e17, fwhm_fs=80.0, t_peak_fs=80.0, hv_eV=1600.0)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def cfg_large_2d(**kw) -> SlabConfig:
+    """Large 2D precision study: 8192 x 1024 cells of 5 nm (40.96 x 5.12 um),
+    80 e + 20 Al3+ per cell (0.84e9 particles), every process on."""
+    base = dict(name="al_2d_8192x1024x5nm_80e20i", nx=8192, ny=1024, dx_nm=5.0,
+                dy_nm=5.0, ppc_e=80, ppc_i=20, flags=F_ALL)
+    base.update(kw)
+    return SlabConfig(**base)
+
+
+def pulse_large_2d(**kw) -> Pulse:
+    """1.8 keV, 5e17 W/cm^2, 80 fs FWHM, peaking at 40 fs (two thirds into
+    the study's 3000 steps of 0.02 fs)."""
+    p = Pulse(I_peak_Wcm2=5.0e17, fwhm_fs=80.0, t_peak_fs=40.0, hv_eV=1800.0)
     for k, v in kw.items():
         setattr(p, k, v)
     return p

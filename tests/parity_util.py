@@ -43,3 +43,34 @@ def compare_state(g_e, o_e, g_i, o_i, nx, ny):
         out["i_bad"] = int((erri > U_RTOL).sum())
         out["i_err_max"] = float(erri.max()) if erri.size else 0.0
     return out
+
+
+def _cells_of(cfg, X, Y):
+    return np.floor(Y).astype(np.int64) * cfg.nx + np.floor(X).astype(np.int64)
+
+
+def sampled_cell_state(cfg, st, cells):
+    """The particles of `cells` (sorted cell indices of a large slab) as a
+    len(cells) x 1 slab of their own, cell k of the list becoming cell k,
+    with the in-cell offsets, momenta, weights and ids kept."""
+    import pic_inputs as P
+    rank = np.full(cfg.ncell, -1, dtype=np.int64)
+    rank[cells] = np.arange(len(cells))
+    ce, ci = _cells_of(cfg, st.eX, st.eY), _cells_of(cfg, st.iX, st.iY)
+    me, mi = rank[ce] >= 0, rank[ci] >= 0
+    sub_cfg = P.SlabConfig(**{**cfg.to_dict(), "nx": len(cells), "ny": 1})
+    sub = P.ParticleState(
+        eX=rank[ce[me]] + (st.eX[me] - np.floor(st.eX[me])), eY=np.full(me.sum(), 0.5),
+        eu=st.eu[me], ew=st.ew[me], eid=st.eid[me],
+        iX=rank[ci[mi]] + (st.iX[mi] - np.floor(st.iX[mi])), iY=np.full(mi.sum(), 0.5),
+        iu=st.iu[mi], izf=st.izf[mi], iZ=st.iZ[mi], inK=st.inK[mi], iid=st.iid[mi])
+    return sub_cfg, sub
+
+
+def select_cells(cfg, e, i, cells):
+    """The electrons and ions of a device read-back that sit in `cells`."""
+    keep = np.zeros(cfg.ncell, dtype=bool)
+    keep[cells] = True
+    se = keep[_cells_of(cfg, e["X"], e["Y"])]
+    si = keep[_cells_of(cfg, i["X"], i["Y"])]
+    return {k: v[se] for k, v in e.items()}, {k: v[si] for k, v in i.items()}

@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 import pic_inputs as P
-from parity_util import compare_state, match, momentum_errors, U_RTOL
+from parity_util import compare_state, match, momentum_errors, sampled_cell_state, select_cells, U_RTOL
 
 pytestmark = pytest.mark.gpu
 
@@ -242,32 +242,17 @@ def test_full_size_sampled_cells(tables):
     g.load(st)
     g.step(1)
     g.sync()
-    rng = np.random.default_rng(0)
-    cells = np.sort(rng.choice(cfg.ncell, 64, replace=False))
-    ce = (np.floor(st.eY).astype(np.int64) * cfg.nx + np.floor(st.eX).astype(np.int64))
-    ci = (np.floor(st.iY).astype(np.int64) * cfg.nx + np.floor(st.iX).astype(np.int64))
-    sub_cfg = P.SlabConfig(**{**cfg.to_dict(), "nx": 64, "ny": 1})
-    rank = {c: k for k, c in enumerate(cells)}
-    me = np.isin(ce, cells)
-    mi = np.isin(ci, cells)
-    sub = P.ParticleState(
-        eX=np.array([rank[c] for c in ce[me]]) + (st.eX[me] - np.floor(st.eX[me])), eY=np.full(me.sum(), 0.5),
-        eu=st.eu[me], ew=st.ew[me], eid=st.eid[me],
-        iX=np.array([rank[c] for c in ci[mi]]) + (st.iX[mi] - np.floor(st.iX[mi])), iY=np.full(mi.sum(), 0.5),
-        iu=st.iu[mi], izf=st.izf[mi], iZ=st.iZ[mi], inK=st.inK[mi], iid=st.iid[mi])
+    cells = np.sort(np.random.default_rng(0).choice(cfg.ncell, 64, replace=False))
+    sub_cfg, sub = sampled_cell_state(cfg, st, cells)
+    me_sum = len(sub.eid)
     o = oracle.OracleSlab(sub_cfg, tables)
     o.load(sub)
     o.step(1)
     oe, oi = o.electrons(), o.ions()
     ge, gi = g.electrons(), g.ions()
-    gce = (np.floor(ge["Y"]).astype(np.int64) * cfg.nx + np.floor(ge["X"]).astype(np.int64))
-    gci = (np.floor(gi["Y"]).astype(np.int64) * cfg.nx + np.floor(gi["X"]).astype(np.int64))
-    sel_e = np.isin(gce, cells)
-    sel_i = np.isin(gci, cells)
-    ge_s = {k: v[sel_e] for k, v in ge.items()}
-    gi_s = {k: v[sel_i] for k, v in gi.items()}
+    ge_s, gi_s = select_cells(cfg, ge, gi, cells)
     res = compare_state(ge_s, oe, gi_s, oi, 64, 1)
-    _assert_parity(res, me.sum())
+    _assert_parity(res, me_sum)
     # properties over the whole slab: charge neutrality kept to FP32 rounding
     qe = ge["w"].astype(np.float64).sum()
     qi = cfg.w_ion * (gi["Z"] + gi["zf"].astype(np.float64)).sum()
