@@ -173,6 +173,17 @@ pic_status pic_counts(pic_ctx *c, int64_t *n_e, int64_t *n_i);
 pic_status pic_get_electrons(pic_ctx *c, double *X, double *Y, float *u, float *w, uint64_t *id);
 pic_status pic_get_ions(pic_ctx *c, double *X, double *Y, float *u, float *zfrac,
                         int32_t *Z, int32_t *nK, uint32_t *id);
+/* The same read-back with momenta, weights and fractional charges in
+ * double precision: the FP64 build's state without rounding to float (the
+ * FP32 build returns its values widened).  Same layout and errors. */
+pic_status pic_get_electrons64(pic_ctx *c, double *X, double *Y, double *u, double *w, uint64_t *id);
+pic_status pic_get_ions64(pic_ctx *c, double *X, double *Y, double *u, double *zfrac,
+                          int32_t *Z, int32_t *nK, uint32_t *id);
+/* Bytes of the arithmetic type of the loaded build: 4 for the production
+ * library (FP32 state and arithmetic), 8 for the FP64 build of the same
+ * kernels (a check of the device logic free of single-precision rounding;
+ * no counterpart in the paper, which runs in double precision). */
+int pic_real_bytes(void);
 pic_status pic_get_photons(pic_ctx *c, double *ph);
 pic_status pic_get_fields(pic_ctx *c, float *f6);
 /* Current density of the last step, [3][ny][nx+1], units e n_ref nm/fs. */

@@ -3,8 +3,11 @@
 Thin Python binding of the C ABI in include/pic.h: argument marshalling
 only.  Every step of the simulation runs in the CUDA kernels of
 paper_1704_01202_gb300/csrc, compiled for sm_103a into
-paper_1704_01202_gb300/_build/libpicgb.so.  There is no CPU path: if the
-library or a GPU is missing, the calls raise.
+paper_1704_01202_gb300/_build/libpicgb.so (FP32 state and arithmetic) and,
+from the same sources, libpicgb64.so (the same kernels in FP64, used to
+check the device logic against the FP64 oracle without single-precision
+rounding).  There is no CPU path: if the library or a GPU is missing, the
+calls raise.
 
 PyTorch provides the device memory (one uint8 arena tensor per context)
 and the CUDA stream.
@@ -22,11 +25,13 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libpicgb.so")
+LIB64_PATH = os.path.join(_BUILD, "libpicgb64.so")
 _INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 _lock = threading.Lock()
 _lib = None
+_lib64 = None
 
 NSUB, NZ, MAX_BINS = 5, 14, 8
 STATUS = {0: "PIC_OK", 1: "PIC_ERR_ARG", 2: "PIC_ERR_OOM", 3: "PIC_ERR_TABLE", 4: "PIC_ERR_CUDA",
@@ -40,7 +45,8 @@ ABI_FUNCTIONS = ["pic_required_bytes", "pic_init", "pic_source", "pic_load_elect
                  "pic_timing", "pic_batch_required_bytes", "pic_batch_init", "pic_batch_admit",
                  "pic_batch_retire", "pic_batch_slot", "pic_batch_diagnostics", "pic_batch_counts",
                  "pic_batch_get_electrons", "pic_batch_get_ions", "pic_philox_check_static",
-                 "pic_use_graphs", "pic_autotune", "pic_order_check"]
+                 "pic_use_graphs", "pic_autotune", "pic_order_check",
+                 "pic_get_electrons64", "pic_get_ions64", "pic_real_bytes"]
 
 
 def _sources():
@@ -48,21 +54,33 @@ def _sources():
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile the CUDA library for sm_103a (nvcc cross-compiles without a GPU)."""
+    """Compile the CUDA library for sm_103a (nvcc cross-compiles without a
+    GPU): the FP32 build and the FP64 build, in parallel.  Returns the FP32
+    library's path."""
     srcs = _sources() + [os.path.join(_INCLUDE, "pic.h")]
-    if not force and os.path.exists(LIB_PATH) and \
-            os.path.getmtime(LIB_PATH) >= max(os.path.getmtime(s) for s in srcs):
+    newest = max(os.path.getmtime(s) for s in srcs)
+    todo = [(path, flags) for path, flags in ((LIB_PATH, []), (LIB64_PATH, ["-DPIC_FP64"]))
+            if force or not os.path.exists(path) or os.path.getmtime(path) < newest]
+    if not todo:
         return LIB_PATH
     os.makedirs(_BUILD, exist_ok=True)
-    tmp = LIB_PATH + f".{os.getpid()}.tmp"
-    cmd = ["nvcc", ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "-o", tmp, os.path.join(_SRC, "pic_api.cu")]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError("nvcc failed:\n" + r.stderr[-4000:])
-    if verbose:
-        print(r.stderr)
-    os.replace(tmp, LIB_PATH)
+    procs = []
+    for path, flags in todo:
+        tmp = path + f".{os.getpid()}.tmp"
+        cmd = ["nvcc", ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", *flags,
+               "-o", tmp, os.path.join(_SRC, "pic_api.cu")]
+        procs.append((path, tmp, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)))
+    errors = []
+    for path, tmp, pr in procs:
+        _, err = pr.communicate()
+        if pr.returncode != 0:
+            errors.append(f"nvcc failed for {os.path.basename(path)}:\n" + err[-4000:])
+            continue
+        if verbose:
+            print(err)
+        os.replace(tmp, path)
+    if errors:
+        raise RuntimeError("\n".join(errors))
     return LIB_PATH
 
 
@@ -107,14 +125,16 @@ _D = C.POINTER(C.c_double)
 _F = C.POINTER(C.c_float)
 
 
-def lib():
-    """Load the compiled library (raises if it has not been built)."""
-    global _lib
+def lib(fp64: bool = False):
+    """Load the compiled library, the FP32 build or (fp64) the FP64 build
+    (raises if it has not been built)."""
+    global _lib, _lib64
     with _lock:
-        if _lib is None:
-            if not os.path.exists(LIB_PATH):
-                raise RuntimeError(f"CUDA library missing: {LIB_PATH} (run __graft_entry__.build())")
-            L = C.CDLL(LIB_PATH)
+        if (_lib64 if fp64 else _lib) is None:
+            path = LIB64_PATH if fp64 else LIB_PATH
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library missing: {path} (run __graft_entry__.build())")
+            L = C.CDLL(path)
             L.pic_required_bytes.restype = C.c_size_t
             L.pic_required_bytes.argtypes = [C.POINTER(Grid), C.POINTER(Species), C.c_int, C.c_int]
             L.pic_init.argtypes = [C.POINTER(_P), C.POINTER(Grid), C.POINTER(Species), C.POINTER(Tables),
@@ -132,6 +152,9 @@ def lib():
             L.pic_get_electrons.argtypes = [_P, _D, _D, _F, _F, C.POINTER(C.c_uint64)]
             L.pic_get_ions.argtypes = [_P, _D, _D, _F, _F, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                        C.POINTER(C.c_uint32)]
+            L.pic_get_electrons64.argtypes = [_P, _D, _D, _D, _D, C.POINTER(C.c_uint64)]
+            L.pic_get_ions64.argtypes = [_P, _D, _D, _D, _D, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                         C.POINTER(C.c_uint32)]
             L.pic_get_photons.argtypes = [_P, _D]
             L.pic_get_fields.argtypes = [_P, _F]
             L.pic_get_current.argtypes = [_P, _D]
@@ -168,8 +191,13 @@ def lib():
                 if name not in ("pic_required_bytes", "pic_launch_count", "pic_last_error",
                                 "pic_batch_required_bytes"):
                     getattr(L, name).restype = C.c_int
-            _lib = L
-    return _lib
+            if L.pic_real_bytes() != (8 if fp64 else 4):
+                raise RuntimeError(f"{path} is not the {'FP64' if fp64 else 'FP32'} build")
+            if fp64:
+                _lib64 = L
+            else:
+                _lib = L
+    return _lib64 if fp64 else _lib
 
 
 class PicError(RuntimeError):
@@ -217,8 +245,8 @@ class Slab:
     """One slab on the GPU, driven through the C ABI."""
 
     def __init__(self, cfg, tables: dict, pulse=None, cap_e: int = 0, cap_i: int = 0,
-                 use_torch_arena: bool = True, stream=None):
-        self.L = lib()
+                 use_torch_arena: bool = True, stream=None, fp64: bool = False):
+        self.L = lib(fp64)
         self.cfg = cfg
         self.grid = _grid(cfg)
         if cap_e <= 0 or cap_i <= 0:
@@ -313,16 +341,20 @@ class Slab:
         self._check(self.L.pic_counts(self.h, C.byref(ne), C.byref(ni)), "pic_counts")
         return ne.value, ni.value
 
-    def electrons(self):
+    def electrons(self, full: bool = False):
+        """Electrons on the host; full: momenta and weights in double
+        precision (the FP64 build's state as it is)."""
         n, _ = self.counts()
-        d, args = _electron_out(n)
-        self._check(self.L.pic_get_electrons(self.h, *args), "pic_get_electrons")
+        d, args = _electron_out(n, full)
+        f = self.L.pic_get_electrons64 if full else self.L.pic_get_electrons
+        self._check(f(self.h, *args), "pic_get_electrons")
         return d
 
-    def ions(self):
+    def ions(self, full: bool = False):
         _, n = self.counts()
-        d, args = _ion_out(n)
-        self._check(self.L.pic_get_ions(self.h, *args), "pic_get_ions")
+        d, args = _ion_out(n, full)
+        f = self.L.pic_get_ions64 if full else self.L.pic_get_ions
+        self._check(f(self.h, *args), "pic_get_ions")
         return d
 
     def set_photons(self, ph):
@@ -372,16 +404,18 @@ def _ion_args(st):
             _p(a[5], C.c_int32), _p(a[6], C.c_uint32))
 
 
-def _electron_out(n):
-    d = dict(X=np.zeros(n), Y=np.zeros(n), u=np.zeros((n, 3), dtype=np.float32), w=np.zeros(n, dtype=np.float32),
+def _electron_out(n, full=False):
+    ft, ct = (np.float64, C.c_double) if full else (np.float32, C.c_float)
+    d = dict(X=np.zeros(n), Y=np.zeros(n), u=np.zeros((n, 3), dtype=ft), w=np.zeros(n, dtype=ft),
              id=np.zeros(n, dtype=np.uint64))
-    return d, (_p(d["X"]), _p(d["Y"]), _p(d["u"], C.c_float), _p(d["w"], C.c_float), _p(d["id"], C.c_uint64))
+    return d, (_p(d["X"]), _p(d["Y"]), _p(d["u"], ct), _p(d["w"], ct), _p(d["id"], C.c_uint64))
 
 
-def _ion_out(n):
-    d = dict(X=np.zeros(n), Y=np.zeros(n), u=np.zeros((n, 3), dtype=np.float32), zf=np.zeros(n, dtype=np.float32),
+def _ion_out(n, full=False):
+    ft, ct = (np.float64, C.c_double) if full else (np.float32, C.c_float)
+    d = dict(X=np.zeros(n), Y=np.zeros(n), u=np.zeros((n, 3), dtype=ft), zf=np.zeros(n, dtype=ft),
              Z=np.zeros(n, dtype=np.int32), nK=np.zeros(n, dtype=np.int32), id=np.zeros(n, dtype=np.uint32))
-    return d, (_p(d["X"]), _p(d["Y"]), _p(d["u"], C.c_float), _p(d["zf"], C.c_float), _p(d["Z"], C.c_int32),
+    return d, (_p(d["X"]), _p(d["Y"]), _p(d["u"], ct), _p(d["zf"], ct), _p(d["Z"], C.c_int32),
                _p(d["nK"], C.c_int32), _p(d["id"], C.c_uint32))
 
 

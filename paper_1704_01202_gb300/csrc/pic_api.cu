@@ -33,7 +33,9 @@ constexpr int CNT_APPEND = 0, CNT_WORK = 1, CNT_WORK_T1 = 2, CNT_WORK_BIG = 3, C
               CNT_WORK_PUSH = 6, CNT_STEP_ZERO = 7, CNT_ERR = 8, CNT_MAXE = 9, CNT_MAXI = 10, CNT_NLOAD = 11,
               CNT_HIST_E = 16, CNT_HIST_I = CNT_HIST_E + NHIST, NCOUNTERS = CNT_HIST_I + NHIST;
 constexpr int NEV = 6;   // timing events per step
-constexpr int BIG_CE = 2048, BIG_CI = 512;
+// largest cell of the one-warp pass (the FP64 build's staging is twice as
+// wide and takes half the populations into the same shared memory)
+constexpr int BIG_CE = sizeof(real) == 8 ? 1024 : 2048, BIG_CI = sizeof(real) == 8 ? 256 : 512;
 
 size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -60,15 +62,15 @@ struct pic_ctx {
     std::vector<pic_grid> grids;         // grid of each slot as given
     struct Pending {                     // admitted, particles not yet on the device
         int slot;
-        std::vector<float4> e0, e1, i0, i1;
+        std::vector<real4> e0, e1, i0, i1;
         std::vector<int> ek, ik;
     };
     std::vector<Pending> pending;
     int ncell = 0, npts = 0, nblk = 0, nrows = 0, max_row_nx = 0;
     int cap_e = 0, cap_i = 0;
 
-    float4 *eA0, *eA1, *eB0, *eB1;
-    float4 *iA0, *iA1, *iB0, *iB1;
+    real4 *eA0, *eA1, *eB0, *eB1;
+    real4 *iA0, *iA1, *iB0, *iB1;
     int *ekey, *ikey, *eord, *iord;
     int *csE[2], *csI[2];
     int cur = 0;
@@ -79,7 +81,7 @@ struct pic_ctx {
     SlabTally *d_tally;                  // [nslot]
     Tables *d_tab;
     EosTable *d_eos;
-    float *E[2], *B;
+    real *E[2], *B;
     int ecur = 0;
     unsigned long long *J;
     ph2 *photons;
@@ -157,13 +159,13 @@ T *carve_arena(pic_ctx *c, size_t count)
 size_t arena_need(int ncell, int npts, int nblk, int cap_e, int cap_i, int nslot, int nrows)
 {
     size_t b = 0;
-    b += 4 * al((size_t)cap_e * 16) + 2 * al((size_t)cap_e * 4);
-    b += 4 * al((size_t)cap_i * 16) + 2 * al((size_t)cap_i * 4);
+    b += 4 * al((size_t)cap_e * sizeof(real4)) + 2 * al((size_t)cap_e * 4);
+    b += 4 * al((size_t)cap_i * sizeof(real4)) + 2 * al((size_t)cap_i * 4);
     b += 4 * al((size_t)(ncell + 1) * 4) + al((size_t)ncell * 16) + 2 * al((size_t)nblk * 4);
     b += al(NCOUNTERS * 4) + al((size_t)ncell * 4) * 3;
     b += al(sizeof(SlabDev) * (size_t)nslot) + al(4 * (size_t)nslot) + al(sizeof(SlabTally) * (size_t)nslot)
          + al(sizeof(Tables)) + al(sizeof(EosTable));
-    b += 3 * al((size_t)npts * 3 * 4) + al((size_t)npts * 3 * 8) + al((size_t)npts * 4);
+    b += 3 * al((size_t)npts * 3 * sizeof(real)) + al((size_t)npts * 3 * 8) + al((size_t)npts * 4);
     b += 2 * al((size_t)nrows * 4);
     b += al((size_t)ncell * PIC_MAX_BINS * sizeof(ph2));
     b += al((4 + NZ + 4096 + 8) * 8);
@@ -506,14 +508,14 @@ SlabDev make_slab(const pic_ctx *c, int k, const pic_grid *g, const pic_species 
     S.ph_off = k * c->slot_cells * PIC_MAX_BINS;
     S.nb = 0;
     S.rad_every = g->rad_every; S.flags = s->flags; S.ipd = s->ipd_model; S.shape = 0;
-    S.dx = (float)g->dx_nm; S.dy = (float)g->dy_nm; S.dt = (float)g->dt_fs;
-    S.w_ion = (float)s->w_ion; S.m_ion = (float)s->m_ion_me; S.E_bulk = (float)s->E_bulk_eV;
-    S.coulomb_log = (float)s->coulomb_log;
+    S.dx = (real)g->dx_nm; S.dy = (real)g->dy_nm; S.dt = (real)g->dt_fs;
+    S.w_ion = (real)s->w_ion; S.m_ion = (real)s->m_ion_me; S.E_bulk = (real)s->E_bulk_eV;
+    S.coulomb_log = (real)s->coulomb_log;
     S.n_ref = s->n_ref_cm3;
     const double E0 = kMeKg * kCms / (kQe * 1e-15);
     S.kappa_J = kQe * s->n_ref_cm3 * 1e6 * 1e-9 / (kEps0 * E0);
-    S.nref_f = (float)S.n_ref;
-    S.kappa_f = (float)S.kappa_J;
+    S.nref_f = (real)S.n_ref;
+    S.kappa_f = (real)S.kappa_J;
     // Field speed: c where the step resolves it (c dt within cfl of the Yee
     // limit), else the largest speed it resolves.  With c dt beyond the cell
     // size, fields subcycled at c with the current held fixed are seen by
@@ -525,8 +527,8 @@ SlabDev make_slab(const pic_ctx *c, int k, const pic_grid *g, const pic_species 
     const double cmax = g->cfl / (g->dt_fs * std::sqrt(inv));
     const double cf = kCnmPerFs < cmax ? kCnmPerFs : cmax;
     S.nsub = 1;
-    S.cf = (float)cf;
-    S.mur = (float)((cf * g->dt_fs - g->dx_nm) / (cf * g->dt_fs + g->dx_nm));
+    S.cf = (real)cf;
+    S.mur = (real)((cf * g->dt_fs - g->dx_nm) / (cf * g->dt_fs + g->dx_nm));
     S.seed = g->seed;
     return S;
 }
@@ -536,11 +538,11 @@ void set_pulse(const pic_ctx *c, SlabDev &S, const pic_pulse *p)
     S.nb = p->n_bins;
     S.shape = p->shape;
     S.I_peak = p->I_peak_Wcm2; S.fwhm = p->fwhm_fs; S.t_peak = p->t_peak_fs; S.spot_sigma = p->spot_sigma_nm;
-    S.bin_hw = (float)(0.5 * p->bandwidth_eV / p->n_bins);
+    S.bin_hw = (real)(0.5 * p->bandwidth_eV / p->n_bins);
     for (int b = 0; b < PIC_MAX_BINS; ++b) {
         double hv = b < p->n_bins ? p->hv_eV + p->bandwidth_eV * ((b + 0.5) / p->n_bins - 0.5) : 0.0;
-        S.hv_b[b] = (float)hv;
-        for (int q = 0; q < NS; ++q) S.sig_b[q][b] = b < p->n_bins ? (float)sigma_table(c, q, hv) : 0.0f;
+        S.hv_b[b] = (real)hv;
+        for (int q = 0; q < NS; ++q) S.sig_b[q][b] = b < p->n_bins ? (real)sigma_table(c, q, hv) : (real)0;
     }
 }
 
@@ -552,9 +554,9 @@ pic_status reset_slot(pic_ctx *c, int k)
     const SlabDev &S = c->slabs[k];
     for (int comp = 0; comp < 3; ++comp) {
         size_t o = (size_t)comp * c->npts + S.fld_off;
-        CK(cudaMemsetAsync(c->E[0] + o, 0, sizeof(float) * c->slot_pts, st));
-        CK(cudaMemsetAsync(c->E[1] + o, 0, sizeof(float) * c->slot_pts, st));
-        CK(cudaMemsetAsync(c->B + o, 0, sizeof(float) * c->slot_pts, st));
+        CK(cudaMemsetAsync(c->E[0] + o, 0, sizeof(real) * c->slot_pts, st));
+        CK(cudaMemsetAsync(c->E[1] + o, 0, sizeof(real) * c->slot_pts, st));
+        CK(cudaMemsetAsync(c->B + o, 0, sizeof(real) * c->slot_pts, st));
     }
     CK(cudaMemsetAsync(c->photons + S.ph_off, 0, sizeof(ph2) * (size_t)c->slot_cells * PIC_MAX_BINS, st));
     CK(cudaMemcpyAsync(c->d_slab + k, &S, sizeof(SlabDev), cudaMemcpyHostToDevice, st));
@@ -606,12 +608,12 @@ pic_status ctx_create(pic_ctx **out, int nslot, int slot_cells, int slot_pts, in
         c->own_arena = true;
         c->arena_bytes = need;
     }
-    c->eA0 = carve_arena<float4>(c, cap_e); c->eA1 = carve_arena<float4>(c, cap_e);
-    c->eB0 = carve_arena<float4>(c, cap_e); c->eB1 = carve_arena<float4>(c, cap_e);
+    c->eA0 = carve_arena<real4>(c, cap_e); c->eA1 = carve_arena<real4>(c, cap_e);
+    c->eB0 = carve_arena<real4>(c, cap_e); c->eB1 = carve_arena<real4>(c, cap_e);
     c->ekey = carve_arena<int>(c, cap_e);
     c->eord = carve_arena<int>(c, cap_e);
-    c->iA0 = carve_arena<float4>(c, cap_i); c->iA1 = carve_arena<float4>(c, cap_i);
-    c->iB0 = carve_arena<float4>(c, cap_i); c->iB1 = carve_arena<float4>(c, cap_i);
+    c->iA0 = carve_arena<real4>(c, cap_i); c->iA1 = carve_arena<real4>(c, cap_i);
+    c->iB0 = carve_arena<real4>(c, cap_i); c->iB1 = carve_arena<real4>(c, cap_i);
     c->ikey = carve_arena<int>(c, cap_i);
     c->iord = carve_arena<int>(c, cap_i);
     for (int k = 0; k < 2; ++k) { c->csE[k] = carve_arena<int>(c, c->ncell + 1); c->csI[k] = carve_arena<int>(c, c->ncell + 1); }
@@ -627,9 +629,9 @@ pic_status ctx_create(pic_ctx **out, int nslot, int slot_cells, int slot_pts, in
     c->d_tally = carve_arena<SlabTally>(c, nslot);
     c->d_tab = carve_arena<Tables>(c, 1);
     c->d_eos = carve_arena<EosTable>(c, 1);
-    c->E[0] = carve_arena<float>(c, 3 * (size_t)c->npts);
-    c->E[1] = carve_arena<float>(c, 3 * (size_t)c->npts);
-    c->B = carve_arena<float>(c, 3 * (size_t)c->npts);
+    c->E[0] = carve_arena<real>(c, 3 * (size_t)c->npts);
+    c->E[1] = carve_arena<real>(c, 3 * (size_t)c->npts);
+    c->B = carve_arena<real>(c, 3 * (size_t)c->npts);
     c->J = carve_arena<unsigned long long>(c, 3 * (size_t)c->npts);
     c->pt_slab = carve_arena<int>(c, c->npts);
     c->row_slab = carve_arena<int>(c, c->nrows);
@@ -639,18 +641,18 @@ pic_status ctx_create(pic_ctx **out, int nslot, int slot_cells, int slot_pts, in
     if (!c->diag_buf) { pic_free(c); return PIC_ERR_OOM; }
 
     Tables T{};
-    for (int q = 0; q < NS; ++q) { T.lotz_a[q] = (float)t->lotz_a[q]; T.lotz_b[q] = (float)t->lotz_b[q]; T.lotz_c[q] = (float)t->lotz_c[q]; }
+    for (int q = 0; q < NS; ++q) { T.lotz_a[q] = (real)t->lotz_a[q]; T.lotz_b[q] = (real)t->lotz_b[q]; T.lotz_c[q] = (real)t->lotz_c[q]; }
     for (int z = 0; z < NZ; ++z) {
-        for (int q = 0; q < NS; ++q) T.E_bind[z][q] = (float)t->E_bind[z][q];
-        for (int k = 0; k < 2; ++k) { T.tauK[z][k] = (float)t->tauK[z][k]; T.omegaK[z][k] = (float)t->omegaK[z][k]; }
-        T.E_Ka[z] = (float)t->E_Kalpha[z];
+        for (int q = 0; q < NS; ++q) T.E_bind[z][q] = (real)t->E_bind[z][q];
+        for (int k = 0; k < 2; ++k) { T.tauK[z][k] = (real)t->tauK[z][k]; T.omegaK[z][k] = (real)t->omegaK[z][k]; }
+        T.E_Ka[z] = (real)t->E_Kalpha[z];
     }
     std::vector<EosTable> eos(1);
     eos[0].n_T = t->n_T; eos[0].n_n = t->n_n;
-    for (int k = 0; k < t->n_T; ++k) eos[0].T[k] = (float)t->eos_T[k];
-    for (int k = 0; k < t->n_n; ++k) eos[0].n[k] = (float)t->eos_n[k];
+    for (int k = 0; k < t->n_T; ++k) eos[0].T[k] = (real)t->eos_T[k];
+    for (int k = 0; k < t->n_n; ++k) eos[0].n[k] = (real)t->eos_n[k];
     for (int a = 0; a < t->n_n; ++a)
-        for (int b = 0; b < t->n_T; ++b) eos[0].Z[a * t->n_T + b] = (float)t->eos_Zbar[(size_t)a * t->n_T + b];
+        for (int b = 0; b < t->n_T; ++b) eos[0].Z[a * t->n_T + b] = (real)t->eos_Zbar[(size_t)a * t->n_T + b];
     std::vector<int> cs(c->ncell), ps(c->npts), rs(c->nrows), ri(c->nrows);
     for (int g = 0; g < c->ncell; ++g) cs[g] = g / slot_cells;
     for (int p = 0; p < c->npts; ++p) ps[p] = p / slot_pts;
@@ -667,9 +669,9 @@ pic_status ctx_create(pic_ctx **out, int nslot, int slot_cells, int slot_pts, in
         if ((e = cudaMemcpyAsync(c->pt_slab, ps.data(), sizeof(int) * c->npts, cudaMemcpyHostToDevice, st))) break;
         if ((e = cudaMemcpyAsync(c->row_slab, rs.data(), sizeof(int) * c->nrows, cudaMemcpyHostToDevice, st))) break;
         if ((e = cudaMemcpyAsync(c->row_idx, ri.data(), sizeof(int) * c->nrows, cudaMemcpyHostToDevice, st))) break;
-        if ((e = cudaMemsetAsync(c->E[0], 0, sizeof(float) * 3 * (size_t)c->npts, st))) break;
-        if ((e = cudaMemsetAsync(c->E[1], 0, sizeof(float) * 3 * (size_t)c->npts, st))) break;
-        if ((e = cudaMemsetAsync(c->B, 0, sizeof(float) * 3 * (size_t)c->npts, st))) break;
+        if ((e = cudaMemsetAsync(c->E[0], 0, sizeof(real) * 3 * (size_t)c->npts, st))) break;
+        if ((e = cudaMemsetAsync(c->E[1], 0, sizeof(real) * 3 * (size_t)c->npts, st))) break;
+        if ((e = cudaMemsetAsync(c->B, 0, sizeof(real) * 3 * (size_t)c->npts, st))) break;
         if ((e = cudaMemsetAsync(c->J, 0, sizeof(unsigned long long) * 3 * (size_t)c->npts, st))) break;
         if ((e = cudaMemsetAsync(c->photons, 0, sizeof(ph2) * (size_t)c->ncell * PIC_MAX_BINS, st))) break;
         if ((e = cudaMemsetAsync(c->counters, 0, sizeof(int) * NCOUNTERS, st))) break;
@@ -701,8 +703,8 @@ pic_status ctx_create(pic_ctx **out, int nslot, int slot_cells, int slot_pts, in
 // (xi, eta, ux, uy), (uz, w | zfrac, id, state) and the global cell key.
 pic_status build_records(pic_ctx *c, int slot, const pic_grid *g, bool electrons, int64_t n, const double *X,
                          const double *Y, const float *u, const float *w_or_zf, const uint64_t *eid,
-                         const int32_t *Z, const int32_t *nK, const uint32_t *iid, std::vector<float4> &p0,
-                         std::vector<float4> &p1, std::vector<int> &key)
+                         const int32_t *Z, const int32_t *nK, const uint32_t *iid, std::vector<real4> &p0,
+                         std::vector<real4> &p1, std::vector<int> &key)
 {
     p0.resize(n); p1.resize(n); key.resize(n);
     const int cell0 = slot * c->slot_cells;
@@ -710,22 +712,17 @@ pic_status build_records(pic_ctx *c, int slot, const pic_grid *g, bool electrons
         double fx = std::floor(X[k]), fy = g->ny > 1 ? std::floor(Y[k]) : 0.0;
         if (!(fx >= 0 && fx < g->nx && fy >= 0 && fy < g->ny))
             return fail(c, PIC_ERR_ARG, "particle position outside the slab");
-        float xi = (float)(X[k] - fx), eta = g->ny > 1 ? (float)(Y[k] - fy) : (float)Y[k];
-        if (xi >= 1.0f) xi = 0.99999994f;
-        if (g->ny > 1 && eta >= 1.0f) eta = 0.99999994f;
+        real xi = (real)(X[k] - fx), eta = g->ny > 1 ? (real)(Y[k] - fy) : (real)Y[k];
+        if (xi >= (real)1) xi = kBelow1;
+        if (g->ny > 1 && eta >= (real)1) eta = kBelow1;
         key[k] = cell0 + (int)fy * g->nx + (int)fx;
-        p0[k] = make_float4(xi, eta, u[3 * k], u[3 * k + 1]);
+        p0[k] = make_real4(xi, eta, u[3 * k], u[3 * k + 1]);
         if (electrons) {
-            uint32_t lo = (uint32_t)eid[k], hi = (uint32_t)(eid[k] >> 32);
-            float flo, fhi;
-            std::memcpy(&flo, &lo, 4); std::memcpy(&fhi, &hi, 4);
-            p1[k] = make_float4(u[3 * k + 2], w_or_zf[k], flo, fhi);
+            p1[k] = rec_e1(u[3 * k + 2], w_or_zf[k], eid[k]);
         } else {
             if (Z[k] < 0 || Z[k] > ZNUC || nK[k] < 0 || nK[k] > 2) return fail(c, PIC_ERR_ARG, "ion state out of range");
             int stv = Z[k] | (nK[k] << 8);
-            float fid, fst;
-            std::memcpy(&fid, &iid[k], 4); std::memcpy(&fst, &stv, 4);
-            p1[k] = make_float4(u[3 * k + 2], w_or_zf[k], fid, fst);
+            p1[k] = rec_i1(u[3 * k + 2], w_or_zf[k], iid[k], stv);
         }
     }
     return PIC_OK;
@@ -733,18 +730,18 @@ pic_status build_records(pic_ctx *c, int slot, const pic_grid *g, bool electrons
 
 // replace all particles of one species by host records (single-slab load):
 // records into the B buffers, count, scan, scatter into A
-pic_status load_species(pic_ctx *c, bool electrons, int64_t n, const std::vector<float4> &p0,
-                        const std::vector<float4> &p1, const std::vector<int> &key)
+pic_status load_species(pic_ctx *c, bool electrons, int64_t n, const std::vector<real4> &p0,
+                        const std::vector<real4> &p1, const std::vector<int> &key)
 {
     cudaStream_t st = c->stream;
-    float4 *s0 = electrons ? c->eB0 : c->iB0, *s1 = electrons ? c->eB1 : c->iB1;
-    float4 *d0 = electrons ? c->eA0 : c->iA0, *d1 = electrons ? c->eA1 : c->iA1;
+    real4 *s0 = electrons ? c->eB0 : c->iB0, *s1 = electrons ? c->eB1 : c->iB1;
+    real4 *d0 = electrons ? c->eA0 : c->iA0, *d1 = electrons ? c->eA1 : c->iA1;
     int *k = electrons ? c->ekey : c->ikey;
     int *cnt = electrons ? c->cnt_e : c->cnt_i, *fill = electrons ? c->fill_e : c->fill_i;
     int nn = (int)n;
     if (n > 0) {
-        CK(cudaMemcpyAsync(s0, p0.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(s1, p1.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(s0, p0.data(), sizeof(real4) * n, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(s1, p1.data(), sizeof(real4) * n, cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(k, key.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
     }
     CK(cudaMemcpyAsync(c->counters + CNT_NLOAD, &nn, sizeof(int), cudaMemcpyHostToDevice, st));
@@ -764,8 +761,8 @@ pic_status load_species(pic_ctx *c, bool electrons, int64_t n, const std::vector
 // Admission: host records are appended behind the sorted particles of each
 // species, every sorted particle is keyed by its own cell (-1 when its slab
 // is inactive), and one count / scan / scatter re-sorts all of them.
-pic_status resort_with(pic_ctx *c, const std::vector<float4> &e0, const std::vector<float4> &e1,
-                       const std::vector<int> &ek, const std::vector<float4> &i0, const std::vector<float4> &i1,
+pic_status resort_with(pic_ctx *c, const std::vector<real4> &e0, const std::vector<real4> &e1,
+                       const std::vector<int> &ek, const std::vector<real4> &i0, const std::vector<real4> &i1,
                        const std::vector<int> &ik)
 {
     cudaStream_t st = c->stream;
@@ -776,18 +773,18 @@ pic_status resort_with(pic_ctx *c, const std::vector<float4> &e0, const std::vec
     const int nxt = c->cur ^ 1;
     for (int sp = 0; sp < 2; ++sp) {
         const bool el = sp == 0;
-        const std::vector<float4> &h0 = el ? e0 : i0, &h1 = el ? e1 : i1;
+        const std::vector<real4> &h0 = el ? e0 : i0, &h1 = el ? e1 : i1;
         const std::vector<int> &hk = el ? ek : ik;
         const long long n0 = ns[sp], nadd = (long long)hk.size();
         if (n0 + nadd > (el ? c->cap_e : c->cap_i))
             return fail(c, PIC_ERR_CAPACITY, "particle capacity exceeded by admission");
-        float4 *A0 = el ? c->eA0 : c->iA0, *A1 = el ? c->eA1 : c->iA1, *B0 = el ? c->eB0 : c->iB0, *B1 = el ? c->eB1 : c->iB1;
+        real4 *A0 = el ? c->eA0 : c->iA0, *A1 = el ? c->eA1 : c->iA1, *B0 = el ? c->eB0 : c->iB0, *B1 = el ? c->eB1 : c->iB1;
         int *key = el ? c->ekey : c->ikey, *cnt = el ? c->cnt_e : c->cnt_i, *fill = el ? c->fill_e : c->fill_i;
         const int *cs = el ? c->csE[c->cur] : c->csI[c->cur];
         k_cell_keys<<<c->nsm * 4, 256, 0, st>>>(cs, c->ncell, c->cell_slab, c->d_slab, key);
         if (nadd) {
-            CK(cudaMemcpyAsync(A0 + n0, h0.data(), sizeof(float4) * nadd, cudaMemcpyHostToDevice, st));
-            CK(cudaMemcpyAsync(A1 + n0, h1.data(), sizeof(float4) * nadd, cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(A0 + n0, h0.data(), sizeof(real4) * nadd, cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(A1 + n0, h1.data(), sizeof(real4) * nadd, cudaMemcpyHostToDevice, st));
             CK(cudaMemcpyAsync(key + n0, hk.data(), sizeof(int) * nadd, cudaMemcpyHostToDevice, st));
         }
         const int tot = (int)(n0 + nadd);
@@ -812,7 +809,7 @@ pic_status resort_with(pic_ctx *c, const std::vector<float4> &e0, const std::vec
 // drop the particles of retired slabs now (one re-sort) and free their slots
 pic_status compact(pic_ctx *c)
 {
-    const std::vector<float4> no4;
+    const std::vector<real4> no4;
     const std::vector<int> noi;
     pic_status r = resort_with(c, no4, no4, noi, no4, no4, noi);
     if (r != PIC_OK) return r;
@@ -845,7 +842,7 @@ pic_status apply_pending(pic_ctx *c)
             if (r != PIC_OK) return r;
         }
     }
-    std::vector<float4> e0, e1, i0, i1;
+    std::vector<real4> e0, e1, i0, i1;
     std::vector<int> ek, ik;
     for (auto &p : c->pending) {
         c->slabs[p.slot].active = 1;
@@ -861,7 +858,7 @@ pic_status apply_pending(pic_ctx *c)
 }
 
 // particles of one slot back on the host with the slot's cell starts
-pic_status fetch_slot(pic_ctx *c, int slot, bool electrons, std::vector<float4> &p0, std::vector<float4> &p1,
+pic_status fetch_slot(pic_ctx *c, int slot, bool electrons, std::vector<real4> &p0, std::vector<real4> &p1,
                       std::vector<int> &cs)
 {
     cudaStream_t st = c->stream;
@@ -872,8 +869,8 @@ pic_status fetch_slot(pic_ctx *c, int slot, bool electrons, std::vector<float4> 
     const int lo = cs[0], n = cs[c->slot_cells] - lo;
     p0.resize(n); p1.resize(n);
     if (n) {
-        CK(cudaMemcpyAsync(p0.data(), (electrons ? c->eA0 : c->iA0) + lo, sizeof(float4) * n, cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(p1.data(), (electrons ? c->eA1 : c->iA1) + lo, sizeof(float4) * n, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(p0.data(), (electrons ? c->eA0 : c->iA0) + lo, sizeof(real4) * n, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(p1.data(), (electrons ? c->eA1 : c->iA1) + lo, sizeof(real4) * n, cudaMemcpyDeviceToHost, st));
     }
     CK(cudaStreamSynchronize(st));
     for (auto &v : cs) v -= lo;
@@ -894,9 +891,11 @@ pic_status counts_slot(pic_ctx *c, int slot, int64_t *n_e, int64_t *n_i)
     return read_device_error(c);
 }
 
-pic_status get_electrons_slot(pic_ctx *c, int slot, double *X, double *Y, float *u, float *w, uint64_t *id)
+// U is float (the ABI's particle arrays) or double (the full-precision read-back)
+template <class U>
+pic_status get_electrons_slot(pic_ctx *c, int slot, double *X, double *Y, U *u, U *w, uint64_t *id)
 {
-    std::vector<float4> p0, p1;
+    std::vector<real4> p0, p1;
     std::vector<int> cs;
     pic_status r = fetch_slot(c, slot, true, p0, p1, cs);
     if (r != PIC_OK) return r;
@@ -906,20 +905,19 @@ pic_status get_electrons_slot(pic_ctx *c, int slot, double *X, double *Y, float 
         for (int k = cs[cell]; k < cs[cell + 1]; ++k) {
             X[k] = cx + (double)p0[k].x;
             Y[k] = S.ny > 1 ? cy + (double)p0[k].y : (double)p0[k].y;
-            u[3 * k] = p0[k].z; u[3 * k + 1] = p0[k].w; u[3 * k + 2] = p1[k].x;
-            w[k] = p1[k].y;
-            uint32_t lo, hi;
-            std::memcpy(&lo, &p1[k].z, 4); std::memcpy(&hi, &p1[k].w, 4);
-            id[k] = ((uint64_t)hi << 32) | lo;
+            u[3 * k] = (U)p0[k].z; u[3 * k + 1] = (U)p0[k].w; u[3 * k + 2] = (U)p1[k].x;
+            w[k] = (U)p1[k].y;
+            id[k] = rec_eid(p1[k]);
         }
     }
     return PIC_OK;
 }
 
-pic_status get_ions_slot(pic_ctx *c, int slot, double *X, double *Y, float *u, float *zfrac, int32_t *Z,
+template <class U>
+pic_status get_ions_slot(pic_ctx *c, int slot, double *X, double *Y, U *u, U *zfrac, int32_t *Z,
                          int32_t *nK, uint32_t *id)
 {
-    std::vector<float4> p0, p1;
+    std::vector<real4> p0, p1;
     std::vector<int> cs;
     pic_status r = fetch_slot(c, slot, false, p0, p1, cs);
     if (r != PIC_OK) return r;
@@ -929,11 +927,10 @@ pic_status get_ions_slot(pic_ctx *c, int slot, double *X, double *Y, float *u, f
         for (int k = cs[cell]; k < cs[cell + 1]; ++k) {
             X[k] = cx + (double)p0[k].x;
             Y[k] = S.ny > 1 ? cy + (double)p0[k].y : (double)p0[k].y;
-            u[3 * k] = p0[k].z; u[3 * k + 1] = p0[k].w; u[3 * k + 2] = p1[k].x;
-            zfrac[k] = p1[k].y;
-            uint32_t idv; int stv;
-            std::memcpy(&idv, &p1[k].z, 4); std::memcpy(&stv, &p1[k].w, 4);
-            id[k] = idv;
+            u[3 * k] = (U)p0[k].z; u[3 * k + 1] = (U)p0[k].w; u[3 * k + 2] = (U)p1[k].x;
+            zfrac[k] = (U)p1[k].y;
+            const int stv = rec_ist(p1[k]);
+            id[k] = rec_iid(p1[k]);
             Z[k] = stv & 0xff;
             nK[k] = (stv >> 8) & 0xff;
         }
@@ -956,11 +953,11 @@ pic_status diag_slot(pic_ctx *c, int slot, pic_diag *out)
     d.i_lo = c->csI[c->cur] + a; d.i_hi = c->csI[c->cur] + b;
     d.m_ion = S.m_ion; d.out = c->diag_buf; d.n_E = nE; d.E_lo = 0.1;
     d.E_max = out->E_max_eV > 0.1 ? out->E_max_eV : 1e4;
-    k_diag<<<c->nsm * 4, 256, sizeof(float) * nv, st>>>(d);
+    k_diag<<<c->nsm * 4, 256, sizeof(real) * nv, st>>>(d);
     k_sumsq<<<c->nsm * 2, 256, 0, st>>>(c->E[c->ecur], c->npts, S.fld_off, c->slot_pts, c->diag_buf + nv);
     k_sumsq<<<c->nsm * 2, 256, 0, st>>>(c->B, c->npts, S.fld_off, c->slot_pts, c->diag_buf + nv);
     if (S.nb > 0) {
-        const float *hv = reinterpret_cast<const float *>(reinterpret_cast<const char *>(c->d_slab + slot) +
+        const real *hv = reinterpret_cast<const real *>(reinterpret_cast<const char *>(c->d_slab + slot) +
                                                           offsetof(SlabDev, hv_b));
         k_photon_energy<<<c->nsm * 2, 256, 0, st>>>(c->photons + S.ph_off, S.ncell, S.nb, hv, c->diag_buf + nv + 1);
     }
@@ -1007,7 +1004,7 @@ pic_status diag_slot(pic_ctx *c, int slot, pic_diag *out)
 pic_status capture_pair(pic_ctx *c, pic_ctx::StepGraph &g)
 {
     if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
-    float4 *saved[8] = {c->eA0, c->eA1, c->eB0, c->eB1, c->iA0, c->iA1, c->iB0, c->iB1};
+    real4 *saved[8] = {c->eA0, c->eA1, c->eB0, c->eB1, c->iA0, c->iA1, c->iB0, c->iB1};
     const int cur = c->cur, ecur = c->ecur;
     const int64_t l0 = c->launches;
     const pic_ctx::StepShape key = step_shape(c);
@@ -1211,7 +1208,7 @@ pic_status pic_load_electrons(pic_ctx *c, int64_t n, const double *X, const doub
     if (!c || n < 0 || (n > 0 && (!X || !Y || !u || !w || !id))) return PIC_ERR_ARG;
     if (c->batch) return fail(c, PIC_ERR_STATE, "a batch context loads particles at admission");
     if (n > c->cap_e) return fail(c, PIC_ERR_CAPACITY, "more electrons than the capacity");
-    std::vector<float4> p0, p1;
+    std::vector<real4> p0, p1;
     std::vector<int> key;
     pic_status r = build_records(c, 0, &c->grids[0], true, n, X, Y, u, w, id, nullptr, nullptr, nullptr, p0, p1, key);
     if (r == PIC_OK) r = load_species(c, true, n, p0, p1, key);
@@ -1225,7 +1222,7 @@ pic_status pic_load_ions(pic_ctx *c, int64_t n, const double *X, const double *Y
     if (!c || n < 0 || (n > 0 && (!X || !Y || !u || !zfrac || !Z || !nK || !id))) return PIC_ERR_ARG;
     if (c->batch) return fail(c, PIC_ERR_STATE, "a batch context loads particles at admission");
     if (n > c->cap_i) return fail(c, PIC_ERR_CAPACITY, "more ions than the capacity");
-    std::vector<float4> p0, p1;
+    std::vector<real4> p0, p1;
     std::vector<int> key;
     pic_status r = build_records(c, 0, &c->grids[0], false, n, X, Y, u, zfrac, nullptr, Z, nK, id, p0, p1, key);
     if (r == PIC_OK) r = load_species(c, false, n, p0, p1, key);
@@ -1242,8 +1239,8 @@ pic_status pic_set_photons(pic_ctx *c, const double *ph)
     size_t n = (size_t)c->ncell * nb;
     std::vector<ph2> h(n);
     for (size_t k = 0; k < n; ++k) {
-        float hi = (float)ph[k];
-        h[k] = ph2{hi, (float)(ph[k] - (double)hi)};
+        real hi = (real)ph[k];
+        h[k] = ph2{hi, (real)(ph[k] - (double)hi)};
     }
     CK(cudaMemcpyAsync(c->photons, h.data(), sizeof(ph2) * n, cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -1255,8 +1252,9 @@ pic_status pic_set_fields(pic_ctx *c, const float *f6)
     if (!c || !f6) return PIC_ERR_ARG;
     if (c->batch) return fail(c, PIC_ERR_STATE, "single-slab call on a batch context");
     size_t n = (size_t)c->npts;
-    CK(cudaMemcpyAsync(c->E[c->ecur], f6, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->B, f6 + 3 * n, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, c->stream));
+    std::vector<real> h(f6, f6 + 6 * n);
+    CK(cudaMemcpyAsync(c->E[c->ecur], h.data(), sizeof(real) * 3 * n, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->B, h.data() + 3 * n, sizeof(real) * 3 * n, cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return PIC_OK;
 }
@@ -1297,6 +1295,23 @@ pic_status pic_get_ions(pic_ctx *c, double *X, double *Y, float *u, float *zfrac
     return get_ions_slot(c, 0, X, Y, u, zfrac, Z, nK, id);
 }
 
+pic_status pic_get_electrons64(pic_ctx *c, double *X, double *Y, double *u, double *w, uint64_t *id)
+{
+    if (!c) return PIC_ERR_ARG;
+    if (c->batch) return fail(c, PIC_ERR_STATE, "single-slab call on a batch context");
+    return get_electrons_slot(c, 0, X, Y, u, w, id);
+}
+
+pic_status pic_get_ions64(pic_ctx *c, double *X, double *Y, double *u, double *zfrac, int32_t *Z, int32_t *nK,
+                          uint32_t *id)
+{
+    if (!c) return PIC_ERR_ARG;
+    if (c->batch) return fail(c, PIC_ERR_STATE, "single-slab call on a batch context");
+    return get_ions_slot(c, 0, X, Y, u, zfrac, Z, nK, id);
+}
+
+int pic_real_bytes(void) { return (int)sizeof(real); }
+
 pic_status pic_get_photons(pic_ctx *c, double *ph)
 {
     if (!c || !ph) return PIC_ERR_ARG;
@@ -1316,9 +1331,11 @@ pic_status pic_get_fields(pic_ctx *c, float *f6)
     if (!c || !f6) return PIC_ERR_ARG;
     if (c->batch) return fail(c, PIC_ERR_STATE, "single-slab call on a batch context");
     size_t n = (size_t)c->npts;
-    CK(cudaMemcpyAsync(f6, c->E[c->ecur], sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(f6 + 3 * n, c->B, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
+    std::vector<real> h(6 * n);
+    CK(cudaMemcpyAsync(h.data(), c->E[c->ecur], sizeof(real) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(h.data() + 3 * n, c->B, sizeof(real) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    for (size_t k = 0; k < 6 * n; ++k) f6[k] = (float)h[k];
     return read_device_error(c);
 }
 
@@ -1331,7 +1348,7 @@ pic_status pic_get_current(pic_ctx *c, double *j3)
     CK(cudaMemcpyAsync(raw.data(), c->J, sizeof(unsigned long long) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     const pic_grid &g = c->grids[0];
-    const double fix = 1.0 / 1099511627776.0;
+    const double fix = 1.0 / JFIX;
     const double sx = g.dx_nm / g.dt_fs;
     const double sy = g.ny > 1 ? g.dy_nm / g.dt_fs : kCnmPerFs;
     for (size_t k = 0; k < n; ++k) {

@@ -18,19 +18,21 @@
 namespace pic {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr double JFIX = 1099511627776.0;        // 2^40 fixed-point scale of J
+// fixed-point scale of J: 2^40 (|J| < 2^22 per node); the FP64 build keeps
+// 2^48 (|J| < 2^14), eight more bits for its 1e-12 comparison
+constexpr double JFIX = sizeof(real) == 8 ? 281474976710656.0 : 1099511627776.0;
 
 struct NewE {            // an electron created in this cell this step
-    float ux, uy, uz, w;
+    real ux, uy, uz, w;
     int meta;            // ion slot | kind << 16
 };
 
 struct CellArgs {
-    float4 *e0, *e1;     // electrons (xi, eta, ux, uy), (uz, w, id_lo, id_hi)
+    real4 *e0, *e1;     // electrons (xi, eta, ux, uy), (uz, w, id_lo, id_hi)
     int *ekey;           // next cell of each electron slot (-1: gone)
     int *eord, *iord;    // canonical order of each cell: slot of position k
     const int *cs_e;     // cell start of electrons [ncell + 1]
-    float4 *i0, *i1;     // ions (xi, eta, ux, uy), (uz, zfrac, id, Z | nK << 8)
+    real4 *i0, *i1;     // ions (xi, eta, ux, uy), (uz, zfrac, id, Z | nK << 8)
     int *ikey;
     const int *cs_i;
     int *cnt_e, *cnt_i;  // per-cell counts of the next sort
@@ -42,8 +44,8 @@ struct CellArgs {
     const unsigned *steps;
     SlabTally *tally;
     ph2 *photons;
-    const float *fldE;   // [3][npts] ex ey ez
-    const float *fldB;   // [3][npts] bx by bz
+    const real *fldE;   // [3][npts] ex ey ez
+    const real *fldB;   // [3][npts] bx by bz
     int npts;
     unsigned long long *J;   // [3][npts] fixed point
     const Tables *tab;
@@ -58,7 +60,7 @@ struct CellArgs {
 
 // warp reductions: a fixed tree, result broadcast from lane 0 so every lane
 // holds the same bits
-__device__ __forceinline__ float wsum_f(float v)
+__device__ __forceinline__ real wsum_f(real v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
@@ -83,11 +85,11 @@ __device__ __forceinline__ int wsum_i(int v)
 }
 
 // inclusive prefix over the lanes (fixed order)
-__device__ __forceinline__ float wscan_f(float v, int lane)
+__device__ __forceinline__ real wscan_f(real v, int lane)
 {
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        float t = __shfl_up_sync(FULL, v, o);
+        real t = __shfl_up_sync(FULL, v, o);
         if (lane >= o) v += t;
     }
     return v;
@@ -223,45 +225,49 @@ __device__ void warp_radix(const unsigned long long *key, IdT *id, unsigned shor
     __syncwarp();
 }
 
-__device__ __forceinline__ float cic_w(float x, int node)
+__device__ __forceinline__ real cic_w(real x, int node)
 {
-    float d = fabsf(x - (float)node);
-    return d < 1.0f ? 1.0f - d : 0.0f;
+    real d = r_fabs(x - (real)node);
+    return d < RF(1.0) ? RF(1.0) - d : RF(0.0);
 }
 
 // per-warp shared memory carve-up
 struct WarpMem {
-    float4 *eu;                 // [cap_ce] ux uy uz w (slot order)
-    unsigned long long *ekey;   // [cap_ce] sort key, later reused as float take
+    real4 *eu;                 // [cap_ce] ux uy uz w (slot order)
+    unsigned long long *ekey;   // [cap_ce] sort key, later reused as real take
     unsigned long long *eid;    // [cap_ce] ids in canonical order
     unsigned short *eperm;      // [cap_ce] canonical position -> slot
-    float4 *iu;                 // [cap_ci] ux uy uz zfrac (slot order)
+    real4 *iu;                 // [cap_ci] ux uy uz zfrac (slot order)
     int *ist;                   // [cap_ci] Z | nK << 8 (slot order)
     unsigned long long *ikey;   // [cap_ci] sort key, later reused as nrec
     unsigned int *iid;          // [cap_ci] ids in canonical order
     unsigned short *iperm;      // [cap_ci]
     NewE *nw;                   // [cap_new]
-    float *dE;                  // [16] continuum lowering per charge state
-    float *Pz;                  // [16] impact-ionization probability per charge
-    float4 *lz;                 // [NS] Lotz constants of one charge state: P, 1/P, ln P, a q
+    real *dE;                  // [16] continuum lowering per charge state
+    real *Pz;                  // [16] impact-ionization probability per charge
+    real4 *lz;                 // [NS] Lotz constants of one charge state: P, 1/P, ln P, a q
     unsigned long long *rbuf;   // [2 max(cap_ce, cap_ci)] radix sort (only when a cell can exceed kRadixMin)
     int *rhist;                 // [256]
     dd *ph;                     // [2 MAXB] photon bin scratch
     int *phc;                   // [MAXB] events per bin so far
 };
 
-__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+// shared-memory pieces start on 16 B (FP32) or 32 B (FP64: real4 is 32 B);
+// the sort-key storage later holds a real2 per electron
+constexpr size_t kSmAlign = sizeof(real4) > 16 ? 32 : 16;
+constexpr size_t kKeyBytes = sizeof(real2) > 8 ? sizeof(real2) : 8;
+__host__ __device__ inline size_t amem(size_t x) { return (x + kSmAlign - 1) & ~(kSmAlign - 1); }
 
 __host__ __device__ inline size_t warp_mem_bytes(int ce, int ci, int cn)
 {
     size_t b = 0;
-    b += align16((size_t)ce * 16) + align16((size_t)ce * 8) * 2 + align16((size_t)ce * 2);
-    b += align16((size_t)ci * 16) + align16((size_t)ci * 4) + align16((size_t)ci * 8) + align16((size_t)ci * 4)
-         + align16((size_t)ci * 2);
-    b += align16((size_t)cn * sizeof(NewE));
-    b += 16 * 4 + 16 * 4 + NS * 16 + 2 * MAXB * 8 + MAXB * 4;
+    b += amem((size_t)ce * sizeof(real4)) + amem((size_t)ce * kKeyBytes) + amem((size_t)ce * 8) + amem((size_t)ce * 2);
+    b += amem((size_t)ci * sizeof(real4)) + amem((size_t)ci * 4) + amem((size_t)ci * 8) + amem((size_t)ci * 4)
+         + amem((size_t)ci * 2);
+    b += amem((size_t)cn * sizeof(NewE));
+    b += amem(16 * sizeof(real)) * 2 + amem(NS * sizeof(real4)) + amem(2 * MAXB * sizeof(dd)) + amem(MAXB * 4);
     const int cm = ce > ci ? ce : ci;
-    if (cm > kRadixMin) b += align16((size_t)cm * 16) + 256 * 4;
+    if (cm > kRadixMin) b += amem((size_t)cm * 16) + 256 * 4;
     return b;
 }
 
@@ -269,26 +275,25 @@ __device__ inline WarpMem carve(char *base, int ce, int ci, int cn)
 {
     WarpMem m;
     char *p = base;
-    m.eu = (float4 *)p; p += align16((size_t)ce * 16);
-    m.ekey = (unsigned long long *)p; p += align16((size_t)ce * 8);
-    m.eid = (unsigned long long *)p; p += align16((size_t)ce * 8);
-    m.eperm = (unsigned short *)p; p += align16((size_t)ce * 2);
-    m.iu = (float4 *)p; p += align16((size_t)ci * 16);
-    m.ist = (int *)p; p += align16((size_t)ci * 4);
-    m.ikey = (unsigned long long *)p; p += align16((size_t)ci * 8);
-    m.iid = (unsigned int *)p; p += align16((size_t)ci * 4);
-    m.iperm = (unsigned short *)p; p += align16((size_t)ci * 2);
-    m.nw = (NewE *)p; p += align16((size_t)cn * sizeof(NewE));
-    m.dE = (float *)p; p += 16 * 4;
-    m.Pz = (float *)p; p += 16 * 4;
-    m.lz = (float4 *)p; p += NS * 16;
-    m.ph = (dd *)p; p += 2 * MAXB * 8;
-    m.phc = (int *)p; p += MAXB * 4;
+    m.eu = (real4 *)p; p += amem((size_t)ce * sizeof(real4));
+    m.ekey = (unsigned long long *)p; p += amem((size_t)ce * kKeyBytes);
+    m.eid = (unsigned long long *)p; p += amem((size_t)ce * 8);
+    m.eperm = (unsigned short *)p; p += amem((size_t)ce * 2);
+    m.iu = (real4 *)p; p += amem((size_t)ci * sizeof(real4));
+    m.ist = (int *)p; p += amem((size_t)ci * 4);
+    m.ikey = (unsigned long long *)p; p += amem((size_t)ci * 8);
+    m.iid = (unsigned int *)p; p += amem((size_t)ci * 4);
+    m.iperm = (unsigned short *)p; p += amem((size_t)ci * 2);
+    m.nw = (NewE *)p; p += amem((size_t)cn * sizeof(NewE));
+    m.dE = (real *)p; p += amem(16 * sizeof(real));
+    m.Pz = (real *)p; p += amem(16 * sizeof(real));
+    m.lz = (real4 *)p; p += amem(NS * sizeof(real4));
+    m.ph = (dd *)p; p += amem(2 * MAXB * sizeof(dd));
+    m.phc = (int *)p; p += amem(MAXB * 4);
     const int cm = ce > ci ? ce : ci;
     m.rbuf = nullptr; m.rhist = nullptr;
     if (cm > kRadixMin) {
-        p = (char *)(((size_t)p + 15) & ~(size_t)15);
-        m.rbuf = (unsigned long long *)p; p += align16((size_t)cm * 16);
+        m.rbuf = (unsigned long long *)p; p += amem((size_t)cm * 16);
         m.rhist = (int *)p;
     }
     return m;
@@ -299,30 +304,30 @@ __device__ inline WarpMem carve(char *base, int ce, int ci, int cn)
 // ---------------------------------------------------------------------
 struct SlabGrid {
     int nx, ny, W;       // W = nx + 1 points per row
-    const float *fe;     // ex of this slab (ey, ez follow with stride npts)
-    const float *fb;     // bx of this slab
+    const real *fe;     // ex of this slab (ey, ez follow with stride npts)
+    const real *fb;     // bx of this slab
     int npts;            // stride between components
     int fo;              // first grid point of the slab
 };
 
-__device__ __forceinline__ float grid_interp(const float *F, const SlabGrid &g, int cx, int cy,
-                                             float xi, float eta, bool hx, bool hy)
+__device__ __forceinline__ real grid_interp(const real *F, const SlabGrid &g, int cx, int cy,
+                                             real xi, real eta, bool hx, bool hy)
 {
-    float xs = xi - (hx ? 0.5f : 0.0f), ys = eta - (hy ? 0.5f : 0.0f);
-    int ax = (int)floorf(xs), ay = (int)floorf(ys);
-    float fx = xs - (float)ax, fy = ys - (float)ay;
+    real xs = xi - (hx ? RF(0.5) : RF(0.0)), ys = eta - (hy ? RF(0.5) : RF(0.0));
+    int ax = (int)r_floor(xs), ay = (int)r_floor(ys);
+    real fx = xs - (real)ax, fy = ys - (real)ay;
     int imax = hx ? g.nx - 1 : g.nx;
-    float v = 0.0f;
+    real v = RF(0.0);
 #pragma unroll
     for (int a = 0; a < 2; ++a) {
         int i = cx + ax + a;
         if (i < 0 || i > imax) continue;
-        float wx = a ? fx : 1.0f - fx;
+        real wx = a ? fx : RF(1.0) - fx;
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
             int j = cy + ay + b;
             j %= g.ny; if (j < 0) j += g.ny;
-            float wy = b ? fy : 1.0f - fy;
+            real wy = b ? fy : RF(1.0) - fy;
             v += wx * wy * __ldg(F + (size_t)j * g.W + i);
         }
     }
@@ -332,31 +337,36 @@ __device__ __forceinline__ float grid_interp(const float *F, const SlabGrid &g, 
 // ---------------------------------------------------------------------
 // current deposit
 // ---------------------------------------------------------------------
-struct JAcc2 { float x[3][4], y[4][3], z[4][4]; };
-struct JAcc1 { float x[3], y[4], z[4]; };
+struct JAcc2 { real x[3][4], y[4][3], z[4][4]; };
+struct JAcc1 { real x[3], y[4], z[4]; };
 
 // v * 2^40 rounded to a 64-bit integer with FP32 and integer instructions
-// only (|v| < 2^22): the high part is split off exactly at 2^31
-__device__ __forceinline__ long long fix40(float v)
+// only (|v| < 2^22): the high part is split off exactly at 2^31 (the
+// FP64 build rounds v * JFIX directly)
+__device__ __forceinline__ long long fix40(real v)
 {
+#ifdef PIC_FP64
+    return __double2ll_rn(v * JFIX);
+#else
     float x = v * 1099511627776.0f;                     // exact: power-of-two scale
     float qh = truncf(x * 4.656612873077393e-10f);      // x / 2^31, integer part
     float r = fmaf(-qh, 2147483648.0f, x);               // exact remainder, |r| < 2^31
     long long lo = (long long)__float2int_rn(fminf(fmaxf(r, -2147483520.0f), 2147483520.0f));
     return ((long long)(int)qh << 31) + lo;
+#endif
 }
 
-__device__ __forceinline__ void jatomic(unsigned long long *J, float v)
+__device__ __forceinline__ void jatomic(unsigned long long *J, real v)
 {
-    if (v != 0.0f) atomicAdd(J, (unsigned long long)fix40(v));
+    if (v != RF(0.0)) atomicAdd(J, (unsigned long long)fix40(v));
 }
 
 // Esirkepov weights of one sub-cell move, stencil anchored at cell (ax, ay)
 // offsets -1..2; start (x0, y0), end (x1, y1) relative to the anchor cell
-__device__ __forceinline__ void esirkepov2(float x0, float y0, float x1, float y1, float qw, float qwbz,
-                                           float frac, JAcc2 &A)
+__device__ __forceinline__ void esirkepov2(real x0, real y0, real x1, real y1, real qw, real qwbz,
+                                           real frac, JAcc2 &A)
 {
-    float S0x[4], S1x[4], S0y[4], S1y[4];
+    real S0x[4], S1x[4], S0y[4], S1y[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
         S0x[a] = cic_w(x0, a - 1); S1x[a] = cic_w(x1, a - 1);
@@ -364,8 +374,8 @@ __device__ __forceinline__ void esirkepov2(float x0, float y0, float x1, float y
     }
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-        float acc = 0.0f;
-        float sy = S0y[b] + 0.5f * (S1y[b] - S0y[b]);
+        real acc = RF(0.0);
+        real sy = S0y[b] + RF(0.5) * (S1y[b] - S0y[b]);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             acc += (S1x[a] - S0x[a]) * sy;
@@ -374,9 +384,9 @@ __device__ __forceinline__ void esirkepov2(float x0, float y0, float x1, float y
     }
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-        float acc = 0.0f;
-        float dsx = S1x[a] - S0x[a];
-        float sx = S0x[a] + 0.5f * dsx;
+        real acc = RF(0.0);
+        real dsx = S1x[a] - S0x[a];
+        real sx = S0x[a] + RF(0.5) * dsx;
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
             acc += (S1y[b] - S0y[b]) * sx;
@@ -384,24 +394,24 @@ __device__ __forceinline__ void esirkepov2(float x0, float y0, float x1, float y
         }
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-            float dsy = S1y[b] - S0y[b];
-            float wz = S0x[a] * S0y[b] + 0.5f * dsx * S0y[b] + 0.5f * S0x[a] * dsy + dsx * dsy * (1.0f / 3.0f);
+            real dsy = S1y[b] - S0y[b];
+            real wz = S0x[a] * S0y[b] + RF(0.5) * dsx * S0y[b] + RF(0.5) * S0x[a] * dsy + dsx * dsy * (RF(1.0) / RF(3.0));
             A.z[a][b] += qwbz * wz * frac;
         }
     }
 }
 
-__device__ __forceinline__ void esirkepov1(float x0, float x1, float qw, float qwby, float qwbz, float frac, JAcc1 &A)
+__device__ __forceinline__ void esirkepov1(real x0, real x1, real qw, real qwby, real qwbz, real frac, JAcc1 &A)
 {
-    float S0x[4], S1x[4];
+    real S0x[4], S1x[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) { S0x[a] = cic_w(x0, a - 1); S1x[a] = cic_w(x1, a - 1); }
-    float acc = 0.0f;
+    real acc = RF(0.0);
 #pragma unroll
     for (int a = 0; a < 3; ++a) { acc += S1x[a] - S0x[a]; A.x[a] -= qw * acc; }
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-        float s = 0.5f * (S0x[a] + S1x[a]);
+        real s = RF(0.5) * (S0x[a] + S1x[a]);
         A.y[a] += qwby * s * frac;
         A.z[a] += qwbz * s * frac;
     }
@@ -410,16 +420,16 @@ __device__ __forceinline__ void esirkepov1(float x0, float x1, float qw, float q
 // a move of one cell or more: equal sub-cell segments, each deposited
 // straight to global memory around its own start cell
 __device__ __noinline__ void deposit_long(const SlabGrid &g, unsigned long long *J, int npts, int fo, int cx, int cy,
-                             float x0, float y0, float x1, float y1, float qw, float qwby, float qwbz)
+                             real x0, real y0, real x1, real y1, real qw, real qwby, real qwbz)
 {
-    float ax = fabsf(x1 - x0), ay = g.ny > 1 ? fabsf(y1 - y0) : 0.0f;
-    int nseg = (int)floorf(fmaxf(ax, ay)) + 1;
+    real ax = r_fabs(x1 - x0), ay = g.ny > 1 ? r_fabs(y1 - y0) : RF(0.0);
+    int nseg = (int)r_floor(r_fmax(ax, ay)) + 1;
     for (int k = 0; k < nseg; ++k) {
-        float a0 = (float)k / nseg, a1 = (float)(k + 1) / nseg;
-        float xa = x0 + a0 * (x1 - x0), xb = x0 + a1 * (x1 - x0);
-        float ya = y0 + a0 * (y1 - y0), yb = y0 + a1 * (y1 - y0);
-        int sx = (int)floorf(xa), sy = g.ny > 1 ? (int)floorf(ya) : 0;
-        float f = 1.0f / nseg;
+        real a0 = (real)k / nseg, a1 = (real)(k + 1) / nseg;
+        real xa = x0 + a0 * (x1 - x0), xb = x0 + a1 * (x1 - x0);
+        real ya = y0 + a0 * (y1 - y0), yb = y0 + a1 * (y1 - y0);
+        int sx = (int)r_floor(xa), sy = g.ny > 1 ? (int)r_floor(ya) : 0;
+        real f = RF(1.0) / nseg;
         if (g.ny == 1) {
             JAcc1 A = {};
             esirkepov1(xa - sx, xb - sx, qw, qwby, qwbz, f, A);
@@ -454,39 +464,39 @@ __device__ __noinline__ void deposit_long(const SlabGrid &g, unsigned long long 
 // ---------------------------------------------------------------------
 template <int DIM, class Acc>
 __device__ __forceinline__ int push_one(const SlabDev &S, const SlabGrid &g, unsigned long long *J, int npts,
-                                        int cx, int cy, float &xi, float &eta, float &ux, float &uy, float &uz,
-                                        float qm, float qw, bool do_push, bool do_dep, Acc &A)
+                                        int cx, int cy, real &xi, real &eta, real &ux, real &uy, real &uz,
+                                        real qm, real qw, bool do_push, bool do_dep, Acc &A)
 {
     if (!do_push) return cy * S.nx + cx;
-    float ex = grid_interp(g.fe, g, cx, cy, xi, eta, true, false);
-    float ey = grid_interp(g.fe + g.npts, g, cx, cy, xi, eta, false, true);
-    float ez = grid_interp(g.fe + 2 * g.npts, g, cx, cy, xi, eta, false, false);
-    float bx = grid_interp(g.fb, g, cx, cy, xi, eta, false, true);
-    float by = grid_interp(g.fb + g.npts, g, cx, cy, xi, eta, true, false);
-    float bz = grid_interp(g.fb + 2 * g.npts, g, cx, cy, xi, eta, true, true);
+    real ex = grid_interp(g.fe, g, cx, cy, xi, eta, true, false);
+    real ey = grid_interp(g.fe + g.npts, g, cx, cy, xi, eta, false, true);
+    real ez = grid_interp(g.fe + 2 * g.npts, g, cx, cy, xi, eta, false, false);
+    real bx = grid_interp(g.fb, g, cx, cy, xi, eta, false, true);
+    real by = grid_interp(g.fb + g.npts, g, cx, cy, xi, eta, true, false);
+    real bz = grid_interp(g.fb + 2 * g.npts, g, cx, cy, xi, eta, true, true);
     boris(ux, uy, uz, ex, ey, ez, bx, by, bz, qm, S.dt);
-    float ig = rsqrtf(1.0f + ux * ux + uy * uy + uz * uz);
-    float bxv = ux * ig, byv = uy * ig, bzv = uz * ig;
-    const float c = (float)kCnmPerFs;
-    float xn = xi + bxv * c * S.dt / S.dx;
-    float yn = DIM == 2 ? eta + byv * c * S.dt / S.dy : eta;
-    if (!(fabsf(xn - xi) < 64.0f && fabsf(yn - eta) < 64.0f)) return -2;   // not finite: dropped
+    real ig = r_rsqrt(RF(1.0) + ux * ux + uy * uy + uz * uz);
+    real bxv = ux * ig, byv = uy * ig, bzv = uz * ig;
+    const real c = (real)kCnmPerFs;
+    real xn = xi + bxv * c * S.dt / S.dx;
+    real yn = DIM == 2 ? eta + byv * c * S.dt / S.dy : eta;
+    if (!(r_fabs(xn - xi) < RF(64.0) && r_fabs(yn - eta) < RF(64.0))) return -2;   // not finite: dropped
     if (do_dep) {
-        if (fabsf(xn - xi) < 1.0f && fabsf(yn - eta) < 1.0f) {
-            if constexpr (DIM == 2) esirkepov2(xi, eta, xn, yn, qw, qw * bzv, 1.0f, A);
-            else esirkepov1(xi, xn, qw, qw * byv, qw * bzv, 1.0f, A);
+        if (r_fabs(xn - xi) < RF(1.0) && r_fabs(yn - eta) < RF(1.0)) {
+            if constexpr (DIM == 2) esirkepov2(xi, eta, xn, yn, qw, qw * bzv, RF(1.0), A);
+            else esirkepov1(xi, xn, qw, qw * byv, qw * bzv, RF(1.0), A);
         } else {
             deposit_long(g, J, npts, g.fo, cx, cy, xi, eta, xn, yn, qw, qw * byv, qw * bzv);
         }
     }
-    float fx = floorf(xn), fy = floorf(yn);
+    real fx = r_floor(xn), fy = r_floor(yn);
     int ncx = cx + (int)fx;
     int ncy = cy + (int)fy;
     xi = xn - fx;
     eta = yn - fy;
-    const float below1 = 0.99999994f;
-    if (xi >= 1.0f) xi = below1;
-    if (eta >= 1.0f) eta = below1;
+    const real below1 = kBelow1;
+    if (xi >= RF(1.0)) xi = below1;
+    if (eta >= RF(1.0)) eta = below1;
     if (DIM == 1) { ncy = 0; }
     else { ncy %= S.ny; if (ncy < 0) ncy += S.ny; }
     if (ncx < 0 || ncx >= S.nx) return -1;

@@ -17,9 +17,9 @@ __device__ __forceinline__ void tally_flush(const CellArgs &a, WarpTally &w, int
 {
     if (w.slab >= 0 && lane == 0) {
         SlabTally *tl = a.tally + w.slab;
-        if (dd_f(w.ion) != 0.0f) atomicAdd(&tl->ion, (double)w.ion.hi + (double)w.ion.lo);
-        if (dd_f(w.ka) != 0.0f) atomicAdd(&tl->ka_esc, (double)w.ka.hi + (double)w.ka.lo);
-        if (dd_f(w.esc) != 0.0f) atomicAdd(&tl->esc, (double)w.esc.hi + (double)w.esc.lo);
+        if (dd_f(w.ion) != RF(0.0)) atomicAdd(&tl->ion, (double)w.ion.hi + (double)w.ion.lo);
+        if (dd_f(w.ka) != RF(0.0)) atomicAdd(&tl->ka_esc, (double)w.ka.hi + (double)w.ka.lo);
+        if (dd_f(w.esc) != RF(0.0)) atomicAdd(&tl->esc, (double)w.esc.hi + (double)w.esc.lo);
         for (int q = 0; q < NCOUNT; ++q)
             if (w.cnt[q]) atomicAdd(tl->cnt + q, (unsigned long long)w.cnt[q]);
     }
@@ -32,7 +32,7 @@ struct CellCtx {
     int s, lc, cx, cy, e0, ne, i0, ni;
     unsigned step, flags;
     unsigned long long seed;
-    float wi, mi, n_e, n_i, nref;
+    real wi, mi, n_e, n_i, nref;
     bool rad;
 };
 
@@ -42,13 +42,13 @@ struct CellCtx {
 // standard deviation sqrt(kT / m c^2), Box-Muller on the electron's Philox
 // draw); the mean momentum is shifted back to the cell's and the momenta
 // about it scaled by one factor (Newton) so that the cell's kinetic energy
-// is kept.  Sums are double-float.
+// is kept.  Sums are double-float (double-double in the FP64 build).
 struct ThermSums { dd W, K, Px, Py, Pz; int n; };
 
-__device__ __forceinline__ void therm_add(ThermSums &t, float4 u)
+__device__ __forceinline__ void therm_add(ThermSums &t, real4 u)
 {
     t.W = dd_addf(t.W, u.w);
-    t.K = dd_addf(t.K, u.w * (float)kMeC2 * gm1(u.x, u.y, u.z));
+    t.K = dd_addf(t.K, u.w * (real)kMeC2 * gm1(u.x, u.y, u.z));
     t.Px = dd_addf(t.Px, u.w * u.x); t.Py = dd_addf(t.Py, u.w * u.y); t.Pz = dd_addf(t.Pz, u.w * u.z);
     t.n += 1;
 }
@@ -56,86 +56,86 @@ __device__ __forceinline__ void therm_add(ThermSums &t, float4 u)
 __device__ __noinline__ void stage_therm(const CellArgs &a, const WarpMem &m, const CellCtx &c, int lane, int nnew)
 {
     const int ne = c.ne;
-    const float MC2 = (float)kMeC2;
+    const real MC2 = (real)kMeC2;
     ThermSums t0{dd_zero(), dd_zero(), dd_zero(), dd_zero(), dd_zero(), 0};
-    for (int k = lane; k < ne; k += 32) { float4 u = m.eu[m.eperm[k]]; if (u.w > 0.0f) therm_add(t0, u); }
+    for (int k = lane; k < ne; k += 32) { real4 u = m.eu[m.eperm[k]]; if (u.w > RF(0.0)) therm_add(t0, u); }
     for (int k = lane; k < nnew; k += 32) {
         NewE q = m.nw[k];
-        if (q.w > 0.0f) therm_add(t0, make_float4(q.ux, q.uy, q.uz, q.w));
+        if (q.w > RF(0.0)) therm_add(t0, make_real4(q.ux, q.uy, q.uz, q.w));
     }
     const dd W = wsum_dd(t0.W), K = wsum_dd(t0.K);
-    const float P[3] = {dd_f(wsum_dd(t0.Px)), dd_f(wsum_dd(t0.Py)), dd_f(wsum_dd(t0.Pz))};
+    const real P[3] = {dd_f(wsum_dd(t0.Px)), dd_f(wsum_dd(t0.Py)), dd_f(wsum_dd(t0.Pz))};
     const int n = wsum_i(t0.n);
-    const float Wf = dd_f(W), Kf = dd_f(K);
-    if (n < 2 || !(Wf > 0.0f) || !(Kf > 0.0f)) return;
-    const float sig = sqrtf((2.0f / 3.0f) * Kf / Wf / MC2);
+    const real Wf = dd_f(W), Kf = dd_f(K);
+    if (n < 2 || !(Wf > RF(0.0)) || !(Kf > RF(0.0))) return;
+    const real sig = r_sqrt((RF(2.0) / RF(3.0)) * Kf / Wf / MC2);
     // redraw; the new momenta replace the old ones in shared memory
     auto redraw = [&](unsigned long long id) {
         U4 r = draw(c.seed, id, c.step, PU_THERM);
-        const float a0 = sqrtf(-2.0f * logf(u01(r.x))), a1 = sqrtf(-2.0f * logf(u01(r.z)));
-        float sn, cs;
-        sincosf(2.0f * kPiF * u01(r.y), &sn, &cs);
-        return make_float3(sig * a0 * cs, sig * a0 * sn, sig * a1 * cosf(2.0f * kPiF * u01(r.w)));
+        const real a0 = r_sqrt(-RF(2.0) * r_log(u01(r.x))), a1 = r_sqrt(-RF(2.0) * r_log(u01(r.z)));
+        real sn, cs;
+        r_sincos(RF(2.0) * kPiR * u01(r.y), &sn, &cs);
+        return make_real3(sig * a0 * cs, sig * a0 * sn, sig * a1 * r_cos(RF(2.0) * kPiR * u01(r.w)));
     };
     dd Qx = dd_zero(), Qy = dd_zero(), Qz = dd_zero();
     for (int k = lane; k < ne; k += 32) {
         const int sl = m.eperm[k];
-        float4 u = m.eu[sl];
-        if (!(u.w > 0.0f)) continue;
-        float3 v = redraw(m.eid[k]);
-        m.eu[sl] = make_float4(v.x, v.y, v.z, u.w);
+        real4 u = m.eu[sl];
+        if (!(u.w > RF(0.0))) continue;
+        real3 v = redraw(m.eid[k]);
+        m.eu[sl] = make_real4(v.x, v.y, v.z, u.w);
         Qx = dd_addf(Qx, u.w * v.x); Qy = dd_addf(Qy, u.w * v.y); Qz = dd_addf(Qz, u.w * v.z);
     }
     for (int k = lane; k < nnew; k += 32) {
         NewE q = m.nw[k];
-        if (!(q.w > 0.0f)) continue;
+        if (!(q.w > RF(0.0))) continue;
         const int islot = q.meta & 0xffff, kind = q.meta >> 16;
-        const unsigned ion_id = __float_as_uint(a.i1[c.i0 + islot].z);
+        const unsigned ion_id = rec_iid(a.i1[c.i0 + islot]);
         const unsigned long long id = ((unsigned long long)(((c.step + 1u) << 2) | (unsigned)kind) << 32) | ion_id;
-        float3 v = redraw(id);
+        real3 v = redraw(id);
         q.ux = v.x; q.uy = v.y; q.uz = v.z;
         m.nw[k] = q;
         Qx = dd_addf(Qx, q.w * v.x); Qy = dd_addf(Qy, q.w * v.y); Qz = dd_addf(Qz, q.w * v.z);
     }
     __syncwarp();
-    const float iW = 1.0f / Wf;
-    const float V[3] = {P[0] * iW, P[1] * iW, P[2] * iW};
-    const float M[3] = {dd_f(wsum_dd(Qx)) * iW, dd_f(wsum_dd(Qy)) * iW, dd_f(wsum_dd(Qz)) * iW};
+    const real iW = RF(1.0) / Wf;
+    const real V[3] = {P[0] * iW, P[1] * iW, P[2] * iW};
+    const real M[3] = {dd_f(wsum_dd(Qx)) * iW, dd_f(wsum_dd(Qy)) * iW, dd_f(wsum_dd(Qz)) * iW};
     // kinetic energy of the cell with the peculiar momenta d = u - M scaled by s
-    auto energy = [&](float s, float &slope) {
+    auto energy = [&](real s, real &slope) {
         dd e = dd_zero(), de = dd_zero();
-        auto one = [&](float4 u) {
-            float dx = u.x - M[0], dy = u.y - M[1], dz = u.z - M[2];
-            float ux = V[0] + s * dx, uy = V[1] + s * dy, uz = V[2] + s * dz;
+        auto one = [&](real4 u) {
+            real dx = u.x - M[0], dy = u.y - M[1], dz = u.z - M[2];
+            real ux = V[0] + s * dx, uy = V[1] + s * dy, uz = V[2] + s * dz;
             e = dd_addf(e, u.w * MC2 * gm1(ux, uy, uz));
-            de = dd_addf(de, u.w * MC2 * (ux * dx + uy * dy + uz * dz) * rsqrtf(1.0f + ux * ux + uy * uy + uz * uz));
+            de = dd_addf(de, u.w * MC2 * (ux * dx + uy * dy + uz * dz) * r_rsqrt(RF(1.0) + ux * ux + uy * uy + uz * uz));
         };
-        for (int k = lane; k < ne; k += 32) { float4 u = m.eu[m.eperm[k]]; if (u.w > 0.0f) one(u); }
+        for (int k = lane; k < ne; k += 32) { real4 u = m.eu[m.eperm[k]]; if (u.w > RF(0.0)) one(u); }
         for (int k = lane; k < nnew; k += 32) {
             NewE q = m.nw[k];
-            if (q.w > 0.0f) one(make_float4(q.ux, q.uy, q.uz, q.w));
+            if (q.w > RF(0.0)) one(make_real4(q.ux, q.uy, q.uz, q.w));
         }
         slope = dd_f(wsum_dd(de));
         return wsum_dd(e);
     };
-    float s = 1.0f;
+    real s = RF(1.0);
     for (int it = 0; it < 8; ++it) {
-        float slope;
+        real slope;
         const dd e = energy(s, slope);
-        if (!(slope > 0.0f)) break;
-        const float ds = dd_f(dd_sub(e, K)) / slope;
-        s = fmaxf(s - ds, 0.0f);
-        if (fabsf(ds) <= 1e-7f * s) break;
+        if (!(slope > RF(0.0))) break;
+        const real ds = dd_f(dd_sub(e, K)) / slope;
+        s = r_fmax(s - ds, RF(0.0));
+        if (r_fabs(ds) <= RF(1e-7) * s) break;
     }
     for (int k = lane; k < ne; k += 32) {
         const int sl = m.eperm[k];
-        float4 u = m.eu[sl];
-        if (!(u.w > 0.0f)) continue;
-        m.eu[sl] = make_float4(V[0] + s * (u.x - M[0]), V[1] + s * (u.y - M[1]), V[2] + s * (u.z - M[2]), u.w);
+        real4 u = m.eu[sl];
+        if (!(u.w > RF(0.0))) continue;
+        m.eu[sl] = make_real4(V[0] + s * (u.x - M[0]), V[1] + s * (u.y - M[1]), V[2] + s * (u.z - M[2]), u.w);
     }
     for (int k = lane; k < nnew; k += 32) {
         NewE q = m.nw[k];
-        if (!(q.w > 0.0f)) continue;
+        if (!(q.w > RF(0.0))) continue;
         q.ux = V[0] + s * (q.ux - M[0]); q.uy = V[1] + s * (q.uy - M[1]); q.uz = V[2] + s * (q.uz - M[2]);
         m.nw[k] = q;
     }
@@ -144,33 +144,33 @@ __device__ __noinline__ void stage_therm(const CellArgs &a, const WarpMem &m, co
 
 // ---- EOS-clamped three-body recombination (Sec. IV) ----
 __device__ __noinline__ void stage_recombine(const CellArgs &a, const WarpMem &m, const Tables &T, const SlabDev &S,
-                                             const CellCtx &c, int lane, float Wnew_imp, WarpTally &wt)
+                                             const CellCtx &c, int lane, real Wnew_imp, WarpTally &wt)
 {
     const int ne = c.ne, ni = c.ni;
-    const float wi = c.wi, MC2 = (float)kMeC2;
-    float pq = 0.0f;
-    for (int k = lane; k < ni; k += 32) { int sl = m.iperm[k]; pq += (float)(m.ist[sl] & 0xff) + m.iu[sl].w; }
-    const float zb = wsum_f(pq) / ni;
+    const real wi = c.wi, MC2 = (real)kMeC2;
+    real pq = RF(0.0);
+    for (int k = lane; k < ni; k += 32) { int sl = m.iperm[k]; pq += (real)(m.ist[sl] & 0xff) + m.iu[sl].w; }
+    const real zb = wsum_f(pq) / ni;
     dd pkb = dd_zero();
-    float pwb = 0.0f, pwx = 0.0f;
+    real pwb = RF(0.0), pwx = RF(0.0);
     for (int k = lane; k < ne; k += 32) {
-        float4 u = m.eu[m.eperm[k]];
-        float ke = MC2 * gm1(u.x, u.y, u.z);
+        real4 u = m.eu[m.eperm[k]];
+        real ke = MC2 * gm1(u.x, u.y, u.z);
         pwx += u.w;
-        if (S.E_bulk <= 0.0f || ke < S.E_bulk) { pwb += u.w; pkb = dd_addf(pkb, u.w * ke); }
+        if (S.E_bulk <= RF(0.0) || ke < S.E_bulk) { pwb += u.w; pkb = dd_addf(pkb, u.w * ke); }
     }
-    const float Wb2 = wsum_f(pwb) + Wnew_imp, Kb2 = dd_f(wsum_dd(pkb)), Wex = wsum_f(pwx);
-    const float Te2 = Wb2 > 0.0f ? (2.0f / 3.0f) * Kb2 / Wb2 : 0.0f;
-    const float zeos = eos_lookup(*a.eos, c.n_i, Te2);
-    int Kev = zb > zeos ? (int)floorf((zb - zeos) * ni + 0.5f) : 0;
+    const real Wb2 = wsum_f(pwb) + Wnew_imp, Kb2 = dd_f(wsum_dd(pkb)), Wex = wsum_f(pwx);
+    const real Te2 = Wb2 > RF(0.0) ? (RF(2.0) / RF(3.0)) * Kb2 / Wb2 : RF(0.0);
+    const real zeos = eos_lookup(*a.eos, c.n_i, Te2);
+    int Kev = zb > zeos ? (int)r_floor((zb - zeos) * ni + RF(0.5)) : 0;
     int pel = 0;
     for (int k = lane; k < ni; k += 32) pel += m.ist[k] & 0xff;
     const int elig = wsum_i(pel);
     Kev = min(Kev, elig);
-    Kev = min(Kev, (int)floorf(Wex / wi * (1.0f + 1e-6f)));
+    Kev = min(Kev, (int)r_floor(Wex / wi * (RF(1.0) + RF(1e-6))));
     if (Kev <= 0) return;
     int *nrec = (int *)m.ikey;            // sort keys are no longer needed
-    float *take = (float *)m.ekey;
+    real *take = (real *)m.ekey;
     for (int k = lane; k < ni; k += 32) nrec[k] = 0;
     __syncwarp();
     int left = Kev;
@@ -190,15 +190,15 @@ __device__ __noinline__ void stage_recombine(const CellArgs &a, const WarpMem &m
             __syncwarp();
         }
     }
-    const dd Wrem = dd{(float)Kev * wi, 0.0f};
+    const dd Wrem = dd{(real)Kev * wi, RF(0.0)};
     dd carry = dd_zero(), remKE = dd_zero();
     for (int b0 = 0; b0 < ne; b0 += 32) {
         int t = b0 + lane;
-        float w = 0.0f, ke = 0.0f;
-        if (t < ne) { float4 u = m.eu[m.eperm[t]]; w = u.w; ke = MC2 * gm1(u.x, u.y, u.z); }
-        dd incl = dd_add(carry, wscan_dd(dd{w, 0.0f}, lane));
-        dd before = dd_sub(incl, dd{w, 0.0f});
-        float tk = fminf(fmaxf(dd_f(dd_sub(Wrem, before)), 0.0f), w);
+        real w = RF(0.0), ke = RF(0.0);
+        if (t < ne) { real4 u = m.eu[m.eperm[t]]; w = u.w; ke = MC2 * gm1(u.x, u.y, u.z); }
+        dd incl = dd_add(carry, wscan_dd(dd{w, RF(0.0)}, lane));
+        dd before = dd_sub(incl, dd{w, RF(0.0)});
+        real tk = r_fmin(r_fmax(dd_f(dd_sub(Wrem, before)), RF(0.0)), w);
         if (t < ne) take[t] = tk;
         remKE = dd_addf(remKE, tk * ke);
         carry = wbcast_dd(incl, 31);
@@ -214,22 +214,22 @@ __device__ __noinline__ void stage_recombine(const CellArgs &a, const WarpMem &m
     const dd bind = wsum_dd(pb);
     dd pkr = dd_zero();
     for (int k = lane; k < ne; k += 32) {
-        float4 u = m.eu[m.eperm[k]];
-        float ke = MC2 * gm1(u.x, u.y, u.z);
-        if (S.E_bulk <= 0.0f || ke < S.E_bulk) pkr = dd_addf(pkr, (u.w - take[k]) * ke);
+        real4 u = m.eu[m.eperm[k]];
+        real ke = MC2 * gm1(u.x, u.y, u.z);
+        if (S.E_bulk <= RF(0.0) || ke < S.E_bulk) pkr = dd_addf(pkr, (u.w - take[k]) * ke);
     }
-    const float Krem = dd_f(wsum_dd(pkr));
-    if (Krem > 0.0f) {
-        float delta = -dd_f(dd_add(remKE, bind)) / Krem;
+    const real Krem = dd_f(wsum_dd(pkr));
+    if (Krem > RF(0.0)) {
+        real delta = -dd_f(dd_add(remKE, bind)) / Krem;
         for (int k = lane; k < ne; k += 32) {
             int sl = m.eperm[k];
-            float4 u = m.eu[sl];
-            float ke = MC2 * gm1(u.x, u.y, u.z);
-            bool bulk = S.E_bulk <= 0.0f || ke < S.E_bulk;
-            float tk = take[k];
-            float wn = u.w - tk;
-            bool dead = tk > 0.0f && wn <= 0.0f;
-            u.w = dead ? 0.0f : wn;
+            real4 u = m.eu[sl];
+            real ke = MC2 * gm1(u.x, u.y, u.z);
+            bool bulk = S.E_bulk <= RF(0.0) || ke < S.E_bulk;
+            real tk = take[k];
+            real wn = u.w - tk;
+            bool dead = tk > RF(0.0) && wn <= RF(0.0);
+            u.w = dead ? RF(0.0) : wn;
             if (bulk && !dead) scale_kinetic(u.x, u.y, u.z, delta);
             m.eu[sl] = u;
         }
@@ -248,19 +248,19 @@ __device__ __noinline__ void stage_photo(const CellArgs &a, const WarpMem &m, co
                                          const CellCtx &c, int lane, int &nnew, WarpTally &wt)
 {
     const int ni = c.ni, nb = S.nb;
-    const float wi = c.wi;
-    const float dtr = S.rad_every * S.dt;
+    const real wi = c.wi;
+    const real dtr = S.rad_every * S.dt;
     ph2 *ph = a.photons + S.ph_off + (size_t)c.lc * nb;
     dd *n0 = m.ph, *used = m.ph + MAXB;
     int *carry = m.phc;
     if (lane < nb) { ph2 v = ph[lane]; n0[lane] = dd{v.hi, v.lo}; used[lane] = dd_zero(); carry[lane] = 0; }
     __syncwarp();
-    const float cph = (float)kCcmPerFs * dtr * c.nref;
+    const real cph = (real)kCcmPerFs * dtr * c.nref;
     int c_part = 0, c_ph[NS] = {0, 0, 0, 0, 0};
     for (int b0 = 0; b0 < ni; b0 += 32) {
         int t = b0 + lane;
         int sub = -1, bin = -1, sl = 0, Z = 0, nK = 0;
-        float edge = 0.f, rc = 0.f, rp = 0.f;
+        real edge = RF(0.), rc = RF(0.), rp = RF(0.);
         if (t < ni) {
             sl = m.iperm[t];
             int st = m.ist[sl];
@@ -269,23 +269,23 @@ __device__ __noinline__ void stage_photo(const CellArgs &a, const WarpMem &m, co
             if (Z < ZNUC && occupancy(ZNUC - Z, nK, occ)) {
                 U4 ra = draw(c.seed, (unsigned long long)m.iid[t], c.step, PU_PHOTO_A);
                 U4 rb = draw(c.seed, (unsigned long long)m.iid[t], c.step, PU_PHOTO_B);
-                float rs[NS] = {u01(ra.x), u01(ra.y), u01(ra.z), u01(ra.w), u01(rb.x)};
-                float Ps = 0.f;
+                real rs[NS] = {u01(ra.x), u01(ra.y), u01(ra.z), u01(ra.w), u01(rb.x)};
+                real Ps = RF(0.);
                 for (int q = 0; q < NS; ++q) {
                     if (!occ[q]) continue;
-                    float ed = lowered_binding(T, Z, q, m.dE[Z]);
-                    float acc = 0.f;
+                    real ed = lowered_binding(T, Z, q, m.dE[Z]);
+                    real acc = RF(0.);
                     for (int b = 0; b < nb; ++b)
                         if (S.hv_b[b] > ed) acc += dd_f(n0[b]) * S.sig_b[q][b];
-                    float P = cph * occ[q] * acc;
+                    real P = cph * occ[q] * acc;
                     if (rs[q] < P) { sub = q; Ps = P; edge = ed; break; }
                 }
                 if (sub >= 0) {
-                    float target = u01(rb.y) * Ps, cum = 0.f;
+                    real target = u01(rb.y) * Ps, cum = RF(0.);
                     int lastpos = -1;
                     for (int b = 0; b < nb; ++b) {
-                        float cb = S.hv_b[b] > edge ? cph * occ[sub] * dd_f(n0[b]) * S.sig_b[sub][b] : 0.f;
-                        if (cb > 0.f) lastpos = b;
+                        real cb = S.hv_b[b] > edge ? cph * occ[sub] * dd_f(n0[b]) * S.sig_b[sub][b] : RF(0.);
+                        if (cb > RF(0.)) lastpos = b;
                         cum += cb;
                         if (cum > target) { bin = b; break; }
                     }
@@ -295,29 +295,29 @@ __device__ __noinline__ void stage_photo(const CellArgs &a, const WarpMem &m, co
             }
         }
         // the k-th event of a bin gets min(w, max(0, n_bin - k w)) photons
-        float g = 0.0f;
+        real g = RF(0.0);
         bool full = false;
         for (int b = 0; b < nb; ++b) {
             bool eb = bin == b && sub >= 0;
             unsigned bal = __ballot_sync(FULL, eb);
             if (eb) {
                 int rank = carry[b] + __popc(bal & ((1u << lane) - 1u));
-                dd rest = dd_addf(n0[b], -(float)rank * wi);
-                if (dd_le(dd{wi, 0.0f}, rest)) { g = wi; full = true; }
-                else g = fmaxf(dd_f(rest), 0.0f);
+                dd rest = dd_addf(n0[b], -(real)rank * wi);
+                if (dd_le(dd{wi, RF(0.0)}, rest)) { g = wi; full = true; }
+                else g = r_fmax(dd_f(rest), RF(0.0));
             }
             __syncwarp();
             if (lane == 0) carry[b] += __popc(bal);
             __syncwarp();
         }
-        bool ev = sub >= 0 && bin >= 0 && g > 0.0f;
+        bool ev = sub >= 0 && bin >= 0 && g > RF(0.0);
         if (ev) {
             if (full) {
                 lose_electron(Z, nK, sub);
             } else {
-                float zf = m.iu[sl].w + g / wi;
-                if (zf >= 1.0f) {
-                    zf -= 1.0f;
+                real zf = m.iu[sl].w + g / wi;
+                if (zf >= RF(1.0)) {
+                    zf -= RF(1.0);
                     int so = outer_shell(ZNUC - Z, nK);
                     if (so >= 0) lose_electron(Z, nK, so);
                 }
@@ -328,15 +328,15 @@ __device__ __noinline__ void stage_photo(const CellArgs &a, const WarpMem &m, co
             c_ph[sub]++;
         }
         for (int b = 0; b < nb; ++b) {
-            dd ub = wsum_dd(dd{ev && bin == b ? g : 0.0f, 0.0f});
+            dd ub = wsum_dd(dd{ev && bin == b ? g : RF(0.0), RF(0.0)});
             if (lane == 0) used[b] = dd_add(used[b], ub);
         }
-        wt.ion = dd_add(wt.ion, wsum_dd(dd{ev ? g * edge : 0.0f, 0.0f}));
+        wt.ion = dd_add(wt.ion, wsum_dd(dd{ev ? g * edge : RF(0.0), RF(0.0)}));
         unsigned bal = __ballot_sync(FULL, ev);
         if (ev) {
             int pos = nnew + __popc(bal & ((1u << lane) - 1u));
             if (pos < a.cap_new) {
-                float3 u = iso_momentum(S.hv_b[bin] - edge, rc, rp);
+                real3 u = iso_momentum(S.hv_b[bin] - edge, rc, rp);
                 NewE q; q.ux = u.x; q.uy = u.y; q.uz = u.z; q.w = g;
                 q.meta = sl | (KIND_PHOTO << 16);
                 m.nw[pos] = q;
@@ -358,8 +358,8 @@ __device__ __noinline__ void stage_decay(const CellArgs &a, const WarpMem &m, co
                                          const CellCtx &c, int lane, int &nnew, WarpTally &wt)
 {
     const int ni = c.ni, nb = S.nb;
-    const float wi = c.wi;
-    const float dtr = S.rad_every * S.dt;
+    const real wi = c.wi;
+    const real dtr = S.rad_every * S.dt;
     dd *addph = m.ph;
     if (lane < MAXB) addph[lane] = dd_zero();
     __syncwarp();
@@ -367,7 +367,7 @@ __device__ __noinline__ void stage_decay(const CellArgs &a, const WarpMem &m, co
     for (int b0 = 0; b0 < ni; b0 += 32) {
         int t = b0 + lane;
         int kind = 0, sl = 0, Z = 0;
-        float EA = 0.f, rc = 0.f, rp = 0.f, Eka = 0.f;
+        real EA = RF(0.), rc = RF(0.), rp = RF(0.), Eka = RF(0.);
         if (t < ni) {
             sl = m.iperm[t];
             int st = m.ist[sl];
@@ -375,17 +375,17 @@ __device__ __noinline__ void stage_decay(const CellArgs &a, const WarpMem &m, co
             int nK = (st >> 8) & 0xff;
             int nbd = ZNUC - Z, occ[NS];
             if (nK > 0 && occupancy(nbd, nK, occ)) {
-                float tau = T.tauK[nbd][nK - 1];
-                if (tau > 0.f) {
+                real tau = T.tauK[nbd][nK - 1];
+                if (tau > RF(0.)) {
                     U4 r = draw(c.seed, (unsigned long long)m.iid[t], c.step, PU_DECAY);
                     if (u01(r.x) < dtr / tau) {
-                        float om = T.omegaK[nbd][nK - 1];
+                        real om = T.omegaK[nbd][nK - 1];
                         int nl = occ[1] + occ[2];
-                        if (u01(r.y) < 1.0f - om) {
+                        if (u01(r.y) < RF(1.0) - om) {
                             if (nl >= 2) {
-                                float e2s = lowered_binding(T, Z, 1, m.dE[Z]);
-                                float e2p = lowered_binding(T, Z, 2, m.dE[Z]);
-                                EA = fmaxf(T.E_Ka[Z] - (occ[1] * e2s + occ[2] * e2p) / nl, 0.0f);
+                                real e2s = lowered_binding(T, Z, 1, m.dE[Z]);
+                                real e2p = lowered_binding(T, Z, 2, m.dE[Z]);
+                                EA = r_fmax(T.E_Ka[Z] - (occ[1] * e2s + occ[2] * e2p) / nl, RF(0.0));
                                 int kocc = occ[0] + 1, nb2 = nbd - 1;
                                 int Zn = Z + 1, nKn = (nb2 < 2 ? nb2 : 2) - kocc;
                                 m.ist[sl] = Zn | (nKn << 8);
@@ -405,7 +405,7 @@ __device__ __noinline__ void stage_decay(const CellArgs &a, const WarpMem &m, co
         if (kind == 1) {
             int pos = nnew + __popc(bal & ((1u << lane) - 1u));
             if (pos < a.cap_new) {
-                float3 u = iso_momentum(EA, rc, rp);
+                real3 u = iso_momentum(EA, rc, rp);
                 NewE q; q.ux = u.x; q.uy = u.y; q.uz = u.z; q.w = wi; q.meta = sl | (KIND_AUGER << 16);
                 m.nw[pos] = q;
             } else {
@@ -421,11 +421,11 @@ __device__ __noinline__ void stage_decay(const CellArgs &a, const WarpMem &m, co
                 if (Eka >= S.hv_b[b] - S.bin_hw && Eka < S.hv_b[b] + S.bin_hw) { hit = b; break; }
         }
         for (int b = 0; b < nb; ++b) {
-            dd v = wsum_dd(dd{hit == b ? wi * Eka / S.hv_b[b] : 0.0f, 0.0f});
+            dd v = wsum_dd(dd{hit == b ? wi * Eka / S.hv_b[b] : RF(0.0), RF(0.0)});
             if (lane == 0) addph[b] = dd_add(addph[b], v);
         }
-        wt.ka = dd_add(wt.ka, wsum_dd(dd{kind == 2 && hit < 0 ? wi * Eka : 0.0f, 0.0f}));
-        wt.ion = dd_sub(wt.ion, wsum_dd(dd{kind == 1 ? wi * EA : (kind == 2 ? wi * Eka : 0.0f), 0.0f}));
+        wt.ka = dd_add(wt.ka, wsum_dd(dd{kind == 2 && hit < 0 ? wi * Eka : RF(0.0), RF(0.0)}));
+        wt.ion = dd_sub(wt.ion, wsum_dd(dd{kind == 1 ? wi * EA : (kind == 2 ? wi * Eka : RF(0.0)), RF(0.0)}));
         __syncwarp();
     }
     if (nb && lane < nb) {
@@ -464,34 +464,34 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
         on = (ne > 0 || ni > 0) && Sp->active;
     }
     const SlabDev &S = *Sp;
-    const float wi = S.w_ion;
-    const float mi = S.m_ion;
+    const real wi = S.w_ion;
+    const real mi = S.m_ion;
     const bool rad = S.rad_every > 0 && (step % (unsigned)S.rad_every) == 0;
-    const float MC2 = (float)kMeC2;
-    const float nref = S.nref_f;
+    const real MC2 = (real)kMeC2;
+    const real nref = S.nref_f;
     int c_ee = 0, c_ei = 0, c_ion = 0, c_rej = 0;
-    float n_e = 0.f, n_i = 0.f, Te = 0.f, zbar = 0.f, lnL = 2.f;
+    real n_e = RF(0.), n_i = RF(0.), Te = RF(0.), zbar = RF(0.), lnL = RF(2.);
     const bool coll = (flags & 3u) != 0;
     dd Kpre = dd_zero();
     int nnew = 0;
-    float Wnew_imp = 0.0f;
+    real Wnew_imp = RF(0.0);
 
     if (on) {
     // ---- stage in shared memory; Philox sort keys ----
     for (int k = lane; k < ne; k += 32) {
-        float4 P0 = a.e0[e0 + k], P1 = a.e1[e0 + k];
-        m.eu[k] = make_float4(P0.z, P0.w, P1.x, P1.y);
-        unsigned long long id = ((unsigned long long)__float_as_uint(P1.w) << 32) | __float_as_uint(P1.z);
+        real4 P0 = a.e0[e0 + k], P1 = a.e1[e0 + k];
+        m.eu[k] = make_real4(P0.z, P0.w, P1.x, P1.y);
+        unsigned long long id = rec_eid(P1);
         U4 r = draw(seed, id, step, PU_PAIR_E);
         m.ekey[k] = ((unsigned long long)r.x << 32) | r.y;
         m.eid[k] = id;
         m.eperm[k] = (unsigned short)k;
     }
     for (int k = lane; k < ni; k += 32) {
-        float4 P0 = a.i0[i0 + k], P1 = a.i1[i0 + k];
-        m.iu[k] = make_float4(P0.z, P0.w, P1.x, P1.y);
-        m.ist[k] = __float_as_int(P1.w);
-        unsigned id = __float_as_uint(P1.z);
+        real4 P0 = a.i0[i0 + k], P1 = a.i1[i0 + k];
+        m.iu[k] = make_real4(P0.z, P0.w, P1.x, P1.y);
+        m.ist[k] = rec_ist(P1);
+        unsigned id = rec_iid(P1);
         U4 r = draw(seed, (unsigned long long)id, step, PU_PAIR_I);
         m.ikey[k] = ((unsigned long long)r.x << 32) | r.y;
         m.iid[k] = id;
@@ -511,46 +511,46 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
     // ---- cell moments (Sec. II: T_e = 2/3 E_ave over bulk electrons) ----
     dd We = dd_zero(), Wb = dd_zero(), Kb = dd_zero(), Q = dd_zero();
     for (int k = lane; k < ne; k += 32) {
-        float4 u = m.eu[m.eperm[k]];
-        float ke = MC2 * gm1(u.x, u.y, u.z);
+        real4 u = m.eu[m.eperm[k]];
+        real ke = MC2 * gm1(u.x, u.y, u.z);
         We = dd_addf(We, u.w);
-        if (S.E_bulk <= 0.0f || ke < S.E_bulk) { Wb = dd_addf(Wb, u.w); Kb = dd_addf(Kb, u.w * ke); }
+        if (S.E_bulk <= RF(0.0) || ke < S.E_bulk) { Wb = dd_addf(Wb, u.w); Kb = dd_addf(Kb, u.w * ke); }
     }
     for (int k = lane; k < ni; k += 32) {
         int sl = m.iperm[k];
-        Q = dd_addf(Q, (float)(m.ist[sl] & 0xff) + m.iu[sl].w);
+        Q = dd_addf(Q, (real)(m.ist[sl] & 0xff) + m.iu[sl].w);
     }
     We = wsum_dd(We); Wb = wsum_dd(Wb); Kb = wsum_dd(Kb); Q = wsum_dd(Q);
-    n_e = dd_f(We) * nref; n_i = (float)ni * wi * nref;
-    Te = dd_f(Wb) > 0.0f ? (2.0f / 3.0f) * dd_f(Kb) / dd_f(Wb) : 0.0f;
-    zbar = ni > 0 ? dd_f(Q) / ni : 0.0f;
+    n_e = dd_f(We) * nref; n_i = (real)ni * wi * nref;
+    Te = dd_f(Wb) > RF(0.0) ? (RF(2.0) / RF(3.0)) * dd_f(Kb) / dd_f(Wb) : RF(0.0);
+    zbar = ni > 0 ? dd_f(Q) / ni : RF(0.0);
     if (lane < NZ) m.dE[lane] = ipd_shift(S.ipd, lane, n_e, n_i, Te, zbar);
-    lnL = S.coulomb_log > 0.0f ? S.coulomb_log : coulomb_log(n_e, Te, zbar);
+    lnL = S.coulomb_log > RF(0.0) ? S.coulomb_log : coulomb_log(n_e, Te, zbar);
     __syncwarp();
 
     // ---- binary collisions (Sec. IV): e-e, then e-i; exact energy restore ----
     if (coll) {
         dd pk = dd_zero(), pki = dd_zero();
-        for (int k = lane; k < ne; k += 32) { float4 u = m.eu[m.eperm[k]]; pk = dd_addf(pk, u.w * MC2 * gm1(u.x, u.y, u.z)); }
-        for (int k = lane; k < ni; k += 32) { float4 u = m.iu[m.iperm[k]]; pki = dd_addf(pki, wi * MC2 * mi * gm1(u.x, u.y, u.z)); }
+        for (int k = lane; k < ne; k += 32) { real4 u = m.eu[m.eperm[k]]; pk = dd_addf(pk, u.w * MC2 * gm1(u.x, u.y, u.z)); }
+        for (int k = lane; k < ni; k += 32) { real4 u = m.iu[m.iperm[k]]; pki = dd_addf(pki, wi * MC2 * mi * gm1(u.x, u.y, u.z)); }
         Kpre = dd_add(wsum_dd(pk), wsum_dd(pki));
     }
     if ((flags & 1u) && ne >= 2) {
         const int start = (ne & 1) ? 3 : 0;
-        auto ee = [&](int pa, int pb, float dtc) {
+        auto ee = [&](int pa, int pb, real dtc) {
             int sa = m.eperm[pa], sb = m.eperm[pb];
-            float4 A = m.eu[sa], B = m.eu[sb];
-            float3 ua = make_float3(A.x, A.y, A.z), ub = make_float3(B.x, B.y, B.z);
+            real4 A = m.eu[sa], B = m.eu[sb];
+            real3 ua = make_real3(A.x, A.y, A.z), ub = make_real3(B.x, B.y, B.z);
             U4 r = draw(seed, m.eid[pa], step, PU_COLL_EE);
-            if (binary_collision(ua, ub, 1.0f, 1.0f, -1.0f, -1.0f, A.w, B.w, n_e, lnL, dtc,
+            if (binary_collision(ua, ub, RF(1.0), RF(1.0), -RF(1.0), -RF(1.0), A.w, B.w, n_e, lnL, dtc,
                                  u01(r.x), u01(r.y), u01(r.z), u01(r.w))) c_ee++;
-            m.eu[sa] = make_float4(ua.x, ua.y, ua.z, A.w);
-            m.eu[sb] = make_float4(ub.x, ub.y, ub.z, B.w);
+            m.eu[sa] = make_real4(ua.x, ua.y, ua.z, A.w);
+            m.eu[sb] = make_real4(ub.x, ub.y, ub.z, B.w);
         };
         if ((ne & 1) && lane == 0) {
-            ee(0, 1, 0.5f * S.dt);
-            ee(1, 2, 0.5f * S.dt);
-            ee(2, 0, 0.5f * S.dt);
+            ee(0, 1, RF(0.5) * S.dt);
+            ee(1, 2, RF(0.5) * S.dt);
+            ee(2, 0, RF(0.5) * S.dt);
         }
         const int npairs = (ne - start) >> 1;
         for (int p = lane; p < npairs; p += 32) ee(start + 2 * p, start + 2 * p + 1, S.dt);
@@ -570,31 +570,31 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
                 int pe = e_long ? base + t : t;
                 int pi = e_long ? t : base + t;
                 int se = m.eperm[pe], si = m.iperm[pi];
-                float4 A = m.eu[se], B = m.iu[si];
-                float q = (float)(m.ist[si] & 0xff) + B.w;
-                float npair = e_long ? n_i * fmaxf(A.w, wi) / wi : n_e * fmaxf(A.w, wi) / A.w;
+                real4 A = m.eu[se], B = m.iu[si];
+                real q = (real)(m.ist[si] & 0xff) + B.w;
+                real npair = e_long ? n_i * r_fmax(A.w, wi) / wi : n_e * r_fmax(A.w, wi) / A.w;
                 U4 r = e_long ? draw(seed, m.eid[pe], step, PU_COLL_EI)
                               : draw(seed, (unsigned long long)m.iid[pi], step, PU_COLL_IE);
-                float3 ua = make_float3(A.x, A.y, A.z), ub = make_float3(B.x, B.y, B.z);
-                if (binary_collision(ua, ub, 1.0f, mi, -1.0f, q, A.w, wi, npair, lnL, S.dt,
+                real3 ua = make_real3(A.x, A.y, A.z), ub = make_real3(B.x, B.y, B.z);
+                if (binary_collision(ua, ub, RF(1.0), mi, -RF(1.0), q, A.w, wi, npair, lnL, S.dt,
                                      u01(r.x), u01(r.y), u01(r.z), u01(r.w))) c_ei++;
-                m.eu[se] = make_float4(ua.x, ua.y, ua.z, A.w);
-                m.iu[si] = make_float4(ub.x, ub.y, ub.z, B.w);
+                m.eu[se] = make_real4(ua.x, ua.y, ua.z, A.w);
+                m.iu[si] = make_real4(ub.x, ub.y, ub.z, B.w);
             }
             __syncwarp();
         }
     }
     if (coll && ne >= 1) {
         dd pk = dd_zero(), pki = dd_zero();
-        for (int k = lane; k < ne; k += 32) { float4 u = m.eu[m.eperm[k]]; pk = dd_addf(pk, u.w * MC2 * gm1(u.x, u.y, u.z)); }
-        for (int k = lane; k < ni; k += 32) { float4 u = m.iu[m.iperm[k]]; pki = dd_addf(pki, wi * MC2 * mi * gm1(u.x, u.y, u.z)); }
+        for (int k = lane; k < ne; k += 32) { real4 u = m.eu[m.eperm[k]]; pk = dd_addf(pk, u.w * MC2 * gm1(u.x, u.y, u.z)); }
+        for (int k = lane; k < ni; k += 32) { real4 u = m.iu[m.iperm[k]]; pki = dd_addf(pki, wi * MC2 * mi * gm1(u.x, u.y, u.z)); }
         dd Ke = wsum_dd(pk), Ki = wsum_dd(pki);
-        float ke = dd_f(Ke);
-        if (ke > 0.0f) {
-            float delta = -dd_f(dd_sub(dd_sub(Kpre, Ke), Ki)) / ke;     // f = 1 - delta
-            if (delta < 1.0f) {
+        real ke = dd_f(Ke);
+        if (ke > RF(0.0)) {
+            real delta = -dd_f(dd_sub(dd_sub(Kpre, Ke), Ki)) / ke;     // f = 1 - delta
+            if (delta < RF(1.0)) {
                 for (int k = lane; k < ne; k += 32) {
-                    float4 u = m.eu[k];
+                    real4 u = m.eu[k];
                     scale_kinetic(u.x, u.y, u.z, delta);
                     m.eu[k] = u;
                 }
@@ -614,27 +614,27 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
         for (int o = 16; o > 0; o >>= 1) pmask |= __shfl_xor_sync(FULL, pmask, o);
         // kinetic energy and w * beta of each electron (canonical order), kept
         // in the sort-key storage, which is free until recombination
-        float2 *ew = reinterpret_cast<float2 *>(m.ekey);
+        real2 *ew = reinterpret_cast<real2 *>(m.ekey);
         dd pk = dd_zero();
         for (int k = lane; k < ne; k += 32) {
-            float4 u = m.eu[m.eperm[k]];
-            float u2 = u.x * u.x + u.y * u.y + u.z * u.z;
-            float g1 = u2 / (sqrtf(1.0f + u2) + 1.0f);
+            real4 u = m.eu[m.eperm[k]];
+            real u2 = u.x * u.x + u.y * u.y + u.z * u.z;
+            real g1 = u2 / (r_sqrt(RF(1.0) + u2) + RF(1.0));
             pk = dd_addf(pk, u.w * MC2 * g1);
-            ew[k] = make_float2(MC2 * g1, u.w * (sqrtf(u2) / (1.0f + g1)));
+            ew[k] = make_real2(MC2 * g1, u.w * (r_sqrt(u2) / (RF(1.0) + g1)));
         }
         const dd Kt = wsum_dd(pk);
-        const float cfac = (float)(kCcmPerFs) * S.dt * nref;
+        const real cfac = (real)(kCcmPerFs) * S.dt * nref;
         for (int z = 0; z < ZNUC; ++z) {
             if (!(pmask & (1u << z))) continue;
             // Lotz constants of charge state z (lowest-energy configuration):
             // lowered binding P, 1/P, ln P, a * occupation (0: empty subshell)
             if (lane < NS) {
                 const int o = subshell_occ(ZNUC - z, lane);
-                float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                real4 v = make_real4(RF(0.0), RF(0.0), RF(0.0), RF(0.0));
                 if (o > 0) {
-                    const float P = lowered_binding(T, z, lane, m.dE[z]);
-                    v = make_float4(P, 1.0f / P, logf(P), T.lotz_a[lane] * (float)o);
+                    const real P = lowered_binding(T, z, lane, m.dE[z]);
+                    v = make_real4(P, RF(1.0) / P, r_log(P), T.lotz_a[lane] * (real)o);
                 }
                 m.lz[lane] = v;
             }
@@ -643,23 +643,23 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
             // within that of its threshold could flip
             dd pr = dd_zero();
             for (int k = lane; k < ne; k += 32) {
-                const float2 q = ew[k];
-                const float E = q.x, lnE = __logf(E), invE = 1.0f / E;
-                float sig = 0.0f;
+                const real2 q = ew[k];
+                const real E = q.x, lnE = r_flog(E), invE = RF(1.0) / E;
+                real sig = RF(0.0);
 #pragma unroll
                 for (int sh = 0; sh < NS; ++sh) {
-                    const float4 L = m.lz[sh];
-                    if (L.w > 0.0f && E > L.x) {
-                        const float x = E * L.y;
+                    const real4 L = m.lz[sh];
+                    if (L.w > RF(0.0) && E > L.x) {
+                        const real x = E * L.y;
                         sig += L.w * (lnE - L.z) * (invE * L.y) *
-                               (1.0f - T.lotz_b[sh] * __expf(-T.lotz_c[sh] * (x - 1.0f)));
+                               (RF(1.0) - T.lotz_b[sh] * r_fexp(-T.lotz_c[sh] * (x - RF(1.0))));
                     }
                 }
                 pr = dd_addf(pr, q.y * sig);
             }
-            float P = cfac * dd_f(wsum_dd(pr));
+            real P = cfac * dd_f(wsum_dd(pr));
             if (lane == 0) m.Pz[z] = P;
-            if (P > 1.0f && lane == 0) wt.cnt[C_PGT1]++;
+            if (P > RF(1.0) && lane == 0) wt.cnt[C_PGT1]++;
             __syncwarp();
         }
         __syncwarp();
@@ -667,7 +667,7 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
         for (int b0 = 0; b0 < ni; b0 += 32) {
             int t = b0 + lane;
             bool cand = false;
-            float cost = 0.0f;
+            real cost = RF(0.0);
             int sl = 0, Z = 0, nK = 0;
             if (t < ni) {
                 sl = m.iperm[t];
@@ -681,7 +681,7 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
                     }
                 }
             }
-            dd incl = dd_add(carry, wscan_dd(dd{cost, 0.0f}, lane));
+            dd incl = dd_add(carry, wscan_dd(dd{cost, RF(0.0)}, lane));
             bool acc = cand && dd_le(incl, Kt);
             if (cand && !acc) c_rej++;
             unsigned bal = __ballot_sync(FULL, acc);
@@ -691,24 +691,24 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
                 m.ist[sl] = Z | (nK << 8);
                 int pos = nnew + __popc(bal & ((1u << lane) - 1u));
                 if (pos < a.cap_new) {
-                    NewE q; q.ux = q.uy = q.uz = 0.0f; q.w = wi; q.meta = sl | (KIND_IMPACT << 16);
+                    NewE q; q.ux = q.uy = q.uz = RF(0.0); q.w = wi; q.meta = sl | (KIND_IMPACT << 16);
                     m.nw[pos] = q;
                 } else {
                     atomicOr(a.err, ERR_NEW_OVERFLOW);
                 }
                 c_ion++;
             }
-            paid = dd_add(paid, wsum_dd(dd{acc ? cost : 0.0f, 0.0f}));
+            paid = dd_add(paid, wsum_dd(dd{acc ? cost : RF(0.0), RF(0.0)}));
             nnew += __popc(bal);
             carry = wbcast_dd(incl, 31);
         }
         nnew = min(nnew, a.cap_new);
         Wnew_imp = nnew * wi;
-        float pf = dd_f(paid);
-        if (pf > 0.0f) {
-            float delta = pf / dd_f(Kt);
+        real pf = dd_f(paid);
+        if (pf > RF(0.0)) {
+            real delta = pf / dd_f(Kt);
             for (int k = lane; k < ne; k += 32) {
-                float4 u = m.eu[k];
+                real4 u = m.eu[k];
                 scale_kinetic(u.x, u.y, u.z, delta);
                 m.eu[k] = u;
             }
@@ -735,16 +735,16 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
     for (int k = lane; k < ne; k += 32) a.eord[e0 + k] = m.eperm[k];
     for (int k = lane; k < ni; k += 32) a.iord[i0 + k] = m.iperm[k];
     for (int k = lane; k < ne; k += 32) {
-        float4 u = m.eu[k];
-        reinterpret_cast<float2 *>(a.e0 + e0 + k)[1] = make_float2(u.x, u.y);
-        reinterpret_cast<float2 *>(a.e1 + e0 + k)[0] = make_float2(u.z, u.w);
+        real4 u = m.eu[k];
+        reinterpret_cast<real2 *>(a.e0 + e0 + k)[1] = make_real2(u.x, u.y);
+        reinterpret_cast<real2 *>(a.e1 + e0 + k)[0] = make_real2(u.z, u.w);
     }
     for (int k = lane; k < ni; k += 32) {
-        float4 u = m.iu[k];
-        reinterpret_cast<float2 *>(a.i0 + i0 + k)[1] = make_float2(u.x, u.y);
-        float4 *r1 = a.i1 + i0 + k;
-        reinterpret_cast<float2 *>(r1)[0] = make_float2(u.z, u.w);
-        reinterpret_cast<int *>(r1)[3] = m.ist[k];
+        real4 u = m.iu[k];
+        reinterpret_cast<real2 *>(a.i0 + i0 + k)[1] = make_real2(u.x, u.y);
+        real4 *r1 = a.i1 + i0 + k;
+        reinterpret_cast<real2 *>(r1)[0] = make_real2(u.z, u.w);
+        r1->w = bits_real((uint32_t)m.ist[k]);
     }
     // ---- created electrons: after the sorted range, at their ion, with their cell as key ----
     if (nnew > 0) {
@@ -761,11 +761,11 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
         for (int k = lane; k < n_ok; k += 32) {
             NewE q = m.nw[k];
             int islot = q.meta & 0xffff, kind = q.meta >> 16;
-            float4 I0 = a.i0[i0 + islot];
-            float4 I1 = a.i1[i0 + islot];
+            real4 I0 = a.i0[i0 + islot];
+            real4 I1 = a.i1[i0 + islot];
             unsigned idhi = ((step + 1u) << 2) | (unsigned)kind;
-            a.e0[sorted + base + k] = make_float4(I0.x, I0.y, q.ux, q.uy);
-            a.e1[sorted + base + k] = make_float4(q.uz, q.w, I1.z, __uint_as_float(idhi));
+            a.e0[sorted + base + k] = make_real4(I0.x, I0.y, q.ux, q.uy);
+            a.e1[sorted + base + k] = rec_e1(q.uz, q.w, ((unsigned long long)idhi << 32) | rec_iid(I1));
             a.ekey[sorted + base + k] = g;
         }
     }
@@ -785,11 +785,11 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
 // a list for the large-cell launch.
 __global__ void __launch_bounds__(256, 2) k_cell(CellArgs a)
 {
-    extern __shared__ __align__(16) char smem[];
+    extern __shared__ __align__(kSmAlign) char smem[];
     __shared__ Tables T;
     __shared__ int round_base;
-    for (int k = threadIdx.x; k < (int)(sizeof(Tables) / 4); k += blockDim.x)
-        ((float *)&T)[k] = ((const float *)a.tab)[k];
+    for (int k = threadIdx.x; k < (int)(sizeof(Tables) / sizeof(real)); k += blockDim.x)
+        ((real *)&T)[k] = ((const real *)a.tab)[k];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     WarpMem m = carve(smem + (size_t)warp * warp_mem_bytes(a.cap_ce, a.cap_ci, a.cap_new),
                       a.cap_ce, a.cap_ci, a.cap_new);
@@ -816,11 +816,11 @@ __global__ void __launch_bounds__(256, 2) k_cell(CellArgs a)
                     // that the next sort stays consistent
                     if (lane == 0) atomicOr(a.err, ERR_CELL_OVERFLOW);
                     for (int k = a.cs_e[g] + lane; k < a.cs_e[g + 1]; k += 32) {
-                        reinterpret_cast<float *>(a.e1 + k)[1] = 0.0f;
+                        reinterpret_cast<real *>(a.e1 + k)[1] = RF(0.0);
                         a.eord[k] = k - a.cs_e[g];
                     }
                     for (int k = a.cs_i[g] + lane; k < a.cs_i[g + 1]; k += 32) {
-                        reinterpret_cast<int *>(a.i1 + k)[3] = 0xff;
+                        a.i1[k].w = bits_real(0xffu);
                         a.iord[k] = k - a.cs_i[g];
                     }
                 }

@@ -59,8 +59,8 @@ __global__ void k_march(MarchArgs a)
             double v0 = j0 >= 0 ? srow[j0] : pulse_source(S, b, tprev - (j0 + 0.5) * S.dx / kCnmPerFs, row);
             double v1 = j1 >= 0 ? srow[j1] : pulse_source(S, b, tprev - (j1 + 0.5) * S.dx / kCnmPerFs, row);
             double nv = (1.0 - f) * v0 + f * v1;
-            float hi = (float)nv;
-            ph[(size_t)k * nb + b] = ph2{hi, (float)(nv - (double)hi)};
+            real hi = (real)nv;
+            ph[(size_t)k * nb + b] = ph2{hi, (real)(nv - (double)hi)};
             if (j0 < 0) inc += (1.0 - f) * v0;
             if (j1 < 0) inc += f * v1;
         }
@@ -178,13 +178,13 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_final(ScanArgs a)
 // decision is keyed by particle id)
 // ---------------------------------------------------------------------
 struct ScatterArgs {
-    const float4 *s0, *s1;
+    const real4 *s0, *s1;
     const int *key;
     const int *n_sorted;     // cs_old[ncell]
     const int *n_extra;      // appended this step (NULL: none)
     const int *cs_new;
     int *fill;
-    float4 *d0, *d1;
+    real4 *d0, *d1;
     int cap;                 // slots beyond the capacity never hold particles
 };
 
@@ -217,9 +217,9 @@ struct FieldArgs {
     const SlabDev *slabs;
     const int *pt_slab;      // slab of every grid point
     int npts;
-    const float *Ein;        // [3][npts]
-    float *Eout;             // [3][npts]
-    float *B;                // [3][npts]
+    const real *Ein;        // [3][npts]
+    real *Eout;             // [3][npts]
+    real *B;                // [3][npts]
     const unsigned long long *J;   // [3][npts] fixed point
     int sub;                 // subcycle index
 };
@@ -234,10 +234,10 @@ __global__ void k_b_half(FieldArgs a)
         if (!S.active || !(S.flags & 128u) || a.sub >= S.nsub || q >= W * S.ny) continue;
         const int j = q / W, i = q - j * W;
         const int jp = (j + 1) % S.ny;
-        const float h = 0.5f * S.dt / S.nsub * S.cf;
+        const real h = RF(0.5) * S.dt / S.nsub * S.cf;
         const int n = a.npts;
-        const float *ex = a.Ein, *ey = a.Ein + n, *ez = a.Ein + 2 * n;
-        float *bx = a.B, *by = a.B + n, *bz = a.B + 2 * n;
+        const real *ex = a.Ein, *ey = a.Ein + n, *ez = a.Ein + 2 * n;
+        real *bx = a.B, *by = a.B + n, *bz = a.B + 2 * n;
         const int o = S.fld_off, r = o + j * W, rp = o + jp * W;
         bx[p] -= h * (ez[rp + i] - ez[r + i]) / S.dy;
         if (i < S.nx) {
@@ -253,8 +253,8 @@ __global__ void k_e_full(FieldArgs a)
         const int s = a.pt_slab[p];
         const SlabDev &S = a.slabs[s];
         const int n = a.npts;
-        const float *exi = a.Ein, *eyi = a.Ein + n, *ezi = a.Ein + 2 * n;
-        float *exo = a.Eout, *eyo = a.Eout + n, *ezo = a.Eout + 2 * n;
+        const real *exi = a.Ein, *eyi = a.Ein + n, *ezi = a.Ein + 2 * n;
+        real *exo = a.Eout, *eyo = a.Eout + n, *ezo = a.Eout + 2 * n;
         const int W = S.nx + 1, q = p - S.fld_off;
         if (!S.active || !(S.flags & 128u) || a.sub >= S.nsub || q >= W * S.ny) {
             exo[p] = exi[p]; eyo[p] = eyi[p]; ezo[p] = ezi[p];
@@ -264,16 +264,16 @@ __global__ void k_e_full(FieldArgs a)
         const int jm = (j - 1 + S.ny) % S.ny;
         const int o = S.fld_off, r = o + j * W, rm = o + jm * W;
         // Cf: speed of the curl terms; C: c, the velocity unit of J
-        const float dtf = S.dt / S.nsub, C = (float)kCnmPerFs, Cf = S.cf, kap = S.kappa_f;
-        const float *bx = a.B, *by = a.B + n, *bz = a.B + 2 * n;
+        const real dtf = S.dt / S.nsub, C = (real)kCnmPerFs, Cf = S.cf, kap = S.kappa_f;
+        const real *bx = a.B, *by = a.B + n, *bz = a.B + 2 * n;
         const unsigned long long *Jx = a.J, *Jy = a.J + n, *Jz = a.J + 2 * n;
-        const float sx = S.dx / S.dt, sy = S.ny > 1 ? S.dy / S.dt : C;
-        // fixed point (2^40) back to float: high and low 32 bits separately
-        auto jv = [&](const unsigned long long *Jc, int idx, float scale) {
+        const real sx = S.dx / S.dt, sy = S.ny > 1 ? S.dy / S.dt : C;
+        // fixed point (JFIX) back to real: high and low 32 bits separately
+        auto jv = [&](const unsigned long long *Jc, int idx, real scale) {
             long long v = (long long)Jc[idx];
-            float hi = (float)(int)(v >> 32) * 4294967296.0f;
-            float lo = (float)(unsigned)(v & 0xffffffffll);
-            return (hi + lo) * (1.0f / 1099511627776.0f) * scale;
+            real hi = (real)(int)(v >> 32) * RF(4294967296.0);
+            real lo = (real)(unsigned)(v & 0xffffffffll);
+            return (hi + lo) * (real)(1.0 / JFIX) * scale;
         };
         auto ey_new = [&](int ii) {
             return eyi[r + ii] + dtf * (-Cf * (bz[r + ii] - bz[r + ii - 1]) / S.dx - kap * jv(Jy, r + ii, sy));
@@ -290,12 +290,12 @@ __global__ void k_e_full(FieldArgs a)
             eyo[p] = ey_new(i);
             ezo[p] = ez_new(i);
         } else if (i == 0) {
-            float y1 = S.nx > 1 ? ey_new(1) : eyi[r + 1], z1 = S.nx > 1 ? ez_new(1) : ezi[r + 1];
+            real y1 = S.nx > 1 ? ey_new(1) : eyi[r + 1], z1 = S.nx > 1 ? ez_new(1) : ezi[r + 1];
             eyo[p] = eyi[r + 1] + S.mur * (y1 - eyi[r]);
             ezo[p] = ezi[r + 1] + S.mur * (z1 - ezi[r]);
         } else {
             const int l = S.nx - 1;
-            float yl = l >= 1 ? ey_new(l) : eyi[r + l], zl = l >= 1 ? ez_new(l) : ezi[r + l];
+            real yl = l >= 1 ? ey_new(l) : eyi[r + l], zl = l >= 1 ? ez_new(l) : ezi[r + l];
             eyo[p] = eyi[r + l] + S.mur * (yl - eyi[r + S.nx]);
             ezo[p] = ezi[r + l] + S.mur * (zl - ezi[r + S.nx]);
         }
@@ -322,7 +322,7 @@ __global__ void k_cell_keys(const int *cs, int ncell, const int *cell_slab, cons
 // diagnostics
 // ---------------------------------------------------------------------
 struct DiagArgs {
-    const float4 *e0, *e1, *i0, *i1;
+    const real4 *e0, *e1, *i0, *i1;
     const int *e_lo, *e_hi, *i_lo, *i_hi;   // particle range of the slab (device)
     double m_ion;
     double *out;                 // [0] W_e, [1] KE_e, [2] KE_i, [3] N_i, [4..4+NZ) csd, then eedf
@@ -334,34 +334,34 @@ struct DiagArgs {
 // histogram bins in shared memory
 __global__ void k_diag(DiagArgs a)
 {
-    extern __shared__ float sdf[];          // [4 + NZ + n_E] block partials
+    extern __shared__ real sdf[];          // [4 + NZ + n_E] block partials
     const int nv = 4 + NZ + a.n_E;
-    float *sd = sdf;
-    for (int k = threadIdx.x; k < nv; k += blockDim.x) sd[k] = 0.0f;
+    real *sd = sdf;
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) sd[k] = RF(0.0);
     __syncthreads();
     const int eb = *a.e_lo, ne = *a.e_hi - eb, ib = *a.i_lo, ni = *a.i_hi - ib;
-    const float lo_e = (float)a.E_lo, inv_lr = (float)(a.n_E / log(a.E_max / a.E_lo));
+    const real lo_e = (real)a.E_lo, inv_lr = (real)(a.n_E / log(a.E_max / a.E_lo));
     dd w_s = dd_zero(), ke_s = dd_zero(), ki_s = dd_zero();
     int n_s = 0;
-    const float MC2 = (float)kMeC2, mi = (float)a.m_ion;
+    const real MC2 = (real)kMeC2, mi = (real)a.m_ion;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ne; k += gridDim.x * blockDim.x) {
-        float4 P0 = a.e0[eb + k], P1 = a.e1[eb + k];
-        float ke = MC2 * gm1(P0.z, P0.w, P1.x);
-        float w = P1.y;
+        real4 P0 = a.e0[eb + k], P1 = a.e1[eb + k];
+        real ke = MC2 * gm1(P0.z, P0.w, P1.x);
+        real w = P1.y;
         w_s = dd_addf(w_s, w);
         ke_s = dd_addf(ke_s, w * ke);
-        int b = ke <= lo_e ? 0 : (int)floorf(logf(ke / lo_e) * inv_lr);
+        int b = ke <= lo_e ? 0 : (int)r_floor(r_log(ke / lo_e) * inv_lr);
         b = b < 0 ? 0 : (b >= a.n_E ? a.n_E - 1 : b);
         atomicAdd(sd + 4 + NZ + b, w);
     }
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ni; k += gridDim.x * blockDim.x) {
-        float4 P0 = a.i0[ib + k], P1 = a.i1[ib + k];
+        real4 P0 = a.i0[ib + k], P1 = a.i1[ib + k];
         ki_s = dd_addf(ki_s, MC2 * mi * gm1(P0.z, P0.w, P1.x));
         n_s += 1;
-        int Z = __float_as_int(P1.w) & 0xff;
-        float zf = P1.y;
-        atomicAdd(sd + 4 + Z, 1.0f - zf);
-        if (zf > 0.0f && Z < ZNUC) atomicAdd(sd + 4 + Z + 1, zf);
+        int Z = rec_ist(P1) & 0xff;
+        real zf = P1.y;
+        atomicAdd(sd + 4 + Z, RF(1.0) - zf);
+        if (zf > RF(0.0) && Z < ZNUC) atomicAdd(sd + 4 + Z + 1, zf);
     }
     for (int o = 16; o > 0; o >>= 1) {
         w_s = dd_add(w_s, dd{__shfl_down_sync(0xffffffffu, w_s.hi, o), __shfl_down_sync(0xffffffffu, w_s.lo, o)});
@@ -377,22 +377,22 @@ __global__ void k_diag(DiagArgs a)
     }
     __syncthreads();
     for (int k = 4 + threadIdx.x; k < nv; k += blockDim.x)
-        if (sd[k] != 0.0f) atomicAdd(a.out + k, (double)sd[k]);
+        if (sd[k] != RF(0.0)) atomicAdd(a.out + k, (double)sd[k]);
 }
 
 // sum of squares of three components of one slab's grid points
-__global__ void k_sumsq(const float *x, int npts, int off, int n, double *out)
+__global__ void k_sumsq(const real *x, int npts, int off, int n, double *out)
 {
     double v = 0.0;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 3 * n; k += gridDim.x * blockDim.x) {
-        float f = x[(size_t)(k / n) * npts + off + k % n];
+        real f = x[(size_t)(k / n) * npts + off + k % n];
         v += (double)f * f;
     }
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(out, v);
 }
 
-__global__ void k_photon_energy(const ph2 *ph, int ncell, int nb, const float *hv, double *out)
+__global__ void k_photon_energy(const ph2 *ph, int ncell, int nb, const real *hv, double *out)
 {
     double v = 0.0;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ncell * nb; k += gridDim.x * blockDim.x)

@@ -16,12 +16,16 @@ def _declared():
 
 
 def test_library_exports_every_declared_symbol():
-    path = pkg.build()
-    lib = ctypes.CDLL(path)
+    """Both builds (FP32 and FP64 arithmetic) export the whole ABI and say
+    which arithmetic type they were built with."""
+    pkg.build()
     names = _declared()
     assert len(names) >= 15
-    missing = [n for n in names if not hasattr(lib, n)]
-    assert not missing, missing
+    for path, nbytes in ((pkg.LIB_PATH, 4), (pkg.LIB64_PATH, 8)):
+        lib = ctypes.CDLL(path)
+        missing = [n for n in names if not hasattr(lib, n)]
+        assert not missing, (path, missing)
+        assert lib.pic_real_bytes() == nbytes
     assert sorted(pkg.ABI_FUNCTIONS) == names
 
 

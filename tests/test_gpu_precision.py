@@ -91,28 +91,32 @@ def test_subdomain_diagnostics_within_method_spread(tables):
     the method is taken from two oracle runs beside the reference one: the
     next seed, and the same seed with 0.1 % of the electron momenta changed
     by 1e-6 (which decorrelates the run the way FP32 rounding does).  Every
-    diagnostic of the FP32 device run lies within three times that spread.
+    diagnostic of the FP32 device run, and of the FP64 build of the same
+    kernels, lies within three times that spread.
     The recombination count is the small residual of ionization against the
     EOS clamp (6 % of the ionizations here): realizations differ by 4-8 %,
     hence its floor of 10 %."""
     pulse = P.pulse_large_2d(t_peak_fs=1.5)
     nsteps = 150
     cfg = P.cfg_large_2d(nx=64, ny=64)
-    g = pkg.Slab(cfg, tables, pulse)
-    g.load(P.init_particles(cfg))
-    g.step(nsteps)
-    g.sync()
-    dg = _gpu_diag(g)
-    g.close()
+    dev = {}
+    for name, fp64 in (("FP32", False), ("FP64", True)):
+        g = pkg.Slab(cfg, tables, pulse, fp64=fp64)
+        g.load(P.init_particles(cfg))
+        g.step(nsteps)
+        g.sync()
+        dev[name] = _gpu_diag(g)
+        g.close()
     ref = _oracle_run(tables, pulse, nsteps)
     others = [_oracle_run(tables, pulse, nsteps, seed=1), _oracle_run(tables, pulse, nsteps, perturb=1e-6)]
     assert ref["counts"]["AUG"] > 0 and 0.05 < ref["transmission"] < 0.95, ref
-    err = _distances(dg, ref)
-    spread = {k: max(_distances(o, ref)[k] for o in others) for k in err}
-    print("\ndiagnostic        FP32 device vs oracle   oracle spread")
-    for k in err:
-        print(f"{k:18s} {err[k]:22.3e} {spread[k]:15.3e}")
-    bad = {k: (err[k], spread[k]) for k in err if err[k] > max(3.0 * spread[k], FLOORS[k])}
+    err = {name: _distances(d, ref) for name, d in dev.items()}
+    spread = {k: max(_distances(o, ref)[k] for o in others) for k in err["FP32"]}
+    print("\ndiagnostic         FP32 device   FP64 device   oracle spread   (distance from the oracle)")
+    for k in spread:
+        print(f"{k:18s} {err['FP32'][k]:12.3e} {err['FP64'][k]:13.3e} {spread[k]:15.3e}")
+    bad = {(name, k): (e[k], spread[k]) for name, e in err.items() for k in e
+           if e[k] > max(3.0 * spread[k], FLOORS[k])}
     assert not bad, bad
 
 
