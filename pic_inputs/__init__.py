@@ -202,7 +202,7 @@ class SlabConfig:
     dt_fs: float = 0.02
     rad_every: int = 5
     seed: int = 0
-    cfl: float = 0.95
+    cfl: float = 0.5                # Courant number of the field update (see the field reading)
     n_ref_cm3: float = 6.0e22       # ion density; weight unit is n_ref*V_cell
     Z_init: int = 3
     T_e_eV: float = 10.0
