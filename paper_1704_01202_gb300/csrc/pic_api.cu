@@ -199,9 +199,34 @@ int max_wpc(int ce, int ci, int cn)
 
 pic_status cell_smem_attr(pic_ctx *c)
 {
+    // the opt-in maximum (less the kernel's static shared memory), so that
+    // occupancy can be asked for any staging size
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa{};
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    CK(cudaFuncGetAttributes(&fa, k_cell));
     const size_t m = std::max(std::max(c->smem_main, c->smem_t1), c->smem_big);
-    CK(cudaFuncSetAttribute(k_cell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m));
+    const size_t lim = optin > (int)fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : m;
+    CK(cudaFuncSetAttribute(k_cell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max(m, lim)));
     return PIC_OK;
+}
+
+// Warps per CTA (up to max_wpc) that keep the most warps of the cell kernel
+// resident per SM: with large cells the staging, not the registers, limits
+// residency, and fewer warps per CTA can let more CTAs share an SM.  Ties
+// go to the larger CTA.
+int best_wpc(pic_ctx *c, int ce, int ci, int cn)
+{
+    if (cell_smem_attr(c) != PIC_OK) return max_wpc(ce, ci, cn);
+    const size_t per = warp_mem_bytes(ce, ci, cn);
+    int best = 1, best_warps = 0;
+    for (int w = 1; w <= max_wpc(ce, ci, cn); ++w) {
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cell, 32 * w, per * w) != cudaSuccess) continue;
+        if (occ * w >= best_warps) { best_warps = occ * w; best = w; }
+    }
+    return best;
 }
 
 // warps per CTA of the tier-0 cell launch: shared memory, grid of resident CTAs
@@ -248,13 +273,13 @@ pic_status configure_cell_launch(pic_ctx *c, const int *hist_e, const int *hist_
     c->cap_ce = ce; c->cap_ci = ci; c->cap_new = 3 * ci;
     if (ce1 > ce || ci1 > ci) {
         c->t1_ce = ce1; c->t1_ci = ci1;
-        c->t1_wpc = max_wpc(ce1, ci1, 3 * ci1);
+        c->t1_wpc = best_wpc(c, ce1, ci1, 3 * ci1);
         c->smem_t1 = warp_mem_bytes(ce1, ci1, 3 * ci1) * c->t1_wpc;
     } else {
         c->t1_ce = c->t1_ci = 0;
         c->smem_t1 = 0;
     }
-    int wpc = max_wpc(ce, ci, 3 * ci);
+    int wpc = best_wpc(c, ce, ci, 3 * ci);
     for (const auto &t : c->tuned)
         if (t.ce == ce && t.ci == ci && t.done) wpc = t.wpc;
     pic_status r = set_wpc(c, wpc);
@@ -1105,7 +1130,7 @@ pic_status tune_step(pic_ctx *c, int n, int &k)
     }
     if (r != PIC_OK) return r;
     t->done = t->tried >= (unsigned)(2 * shapes);
-    t->wpc = max_wpc(c->cap_ce, c->cap_ci, c->cap_new);      // undecided: the default
+    t->wpc = best_wpc(c, c->cap_ce, c->cap_ci, c->cap_new);  // undecided: the default
     if (t->done) {
         float best = 3.4e38f;
         for (int q = 0; q < shapes; ++q)
