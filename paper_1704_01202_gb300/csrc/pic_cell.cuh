@@ -225,6 +225,99 @@ __device__ void warp_radix(const unsigned long long *key, IdT *id, unsigned shor
     __syncwarp();
 }
 
+// Sort of up to 32 E entries in registers, E per lane (entry lane * E + j):
+// the bitonic network over (key high 48 bits | slot) words, compare-exchange
+// through warp shuffles across lanes and in place within a lane.  Gives the
+// (key, slot) order, which is the (key, id) order unless two keys share
+// their high 48 bits (probability ~n^2 / 2^49 per cell): then it returns
+// false and leaves key[], id[] and slot[] untouched for the exact sort.
+template <int E, int S>
+__device__ __forceinline__ void reg_cmpx_in_lane(unsigned long long (&v)[E], int lane, int size)
+{
+    if constexpr (S < E) {
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            if ((j & S) != 0) continue;
+            const bool asc = ((lane * E + j) & size) == 0;
+            const unsigned long long a = v[j], b = v[j ^ S];
+            if ((a > b) == asc) { v[j] = b; v[j ^ S] = a; }
+        }
+    }
+}
+
+template <int E, class IdT>
+__device__ __forceinline__ bool warp_sort_reg(const unsigned long long *key, IdT *id, unsigned short *slot,
+                                           unsigned long long *tmp, int n, int lane)
+{
+    unsigned long long v[E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+        const int k = lane * E + j;
+        v[j] = k < n ? (key[k] & ~0xffffull) | (unsigned long long)k : ~0ull;
+    }
+    for (int size = 2; size <= 32 * E; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= E) {
+                const int lm = stride / E;
+#pragma unroll
+                for (int j = 0; j < E; ++j) {
+                    const int e = lane * E + j;
+                    const unsigned long long o = __shfl_xor_sync(FULL, v[j], lm);
+                    const bool keep_min = ((e & stride) == 0) == ((e & size) == 0);
+                    v[j] = keep_min ? (o < v[j] ? o : v[j]) : (o > v[j] ? o : v[j]);
+                }
+            } else if (stride == 1) {
+                reg_cmpx_in_lane<E, 1>(v, lane, size);
+            } else if (stride == 2) {
+                reg_cmpx_in_lane<E, 2>(v, lane, size);
+            } else if (stride == 4) {
+                reg_cmpx_in_lane<E, 4>(v, lane, size);
+            } else {
+                reg_cmpx_in_lane<E, 8>(v, lane, size);
+            }
+        }
+    }
+    // neighbours with equal high words (the padding never compares: its
+    // positions are >= n)
+    bool tie = false;
+#pragma unroll
+    for (int j = 0; j + 1 < E; ++j)
+        tie |= lane * E + j + 1 < n && (v[j] >> 16) == (v[j + 1] >> 16);
+    const unsigned long long nx = __shfl_down_sync(FULL, v[0], 1);
+    tie |= lane < 31 && lane * E + E < n && (v[E - 1] >> 16) == (nx >> 16);
+    if (__any_sync(FULL, tie)) return false;
+    IdT idv[E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+        const int k = lane * E + j;
+        idv[j] = k < n ? id[(int)(v[j] & 0xffffu)] : (IdT)0;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+        const int k = lane * E + j;
+        if (k < n) { slot[k] = (unsigned short)(v[j] & 0xffffu); id[k] = idv[j]; }
+    }
+    __syncwarp();
+    (void)tmp;
+    return true;
+}
+
+// The in-cell canonical order, ascending (key, id): registers up to
+// kRadixMin entries (the shared-memory network when high words tie), the
+// radix sort above.  slot[] must hold 0..n-1 on entry.
+template <class IdT>
+__device__ void warp_sort(unsigned long long *key, IdT *id, unsigned short *slot, unsigned long long *tmp,
+                          unsigned long long *rbuf, int *rhist, int n, int lane)
+{
+    if (n > kRadixMin) { warp_radix<IdT>(key, id, slot, tmp, rbuf, rhist, n, lane); return; }
+    bool done = false;
+    if (n <= 32) done = warp_sort_reg<1, IdT>(key, id, slot, tmp, n, lane);
+    else if (n <= 64) done = warp_sort_reg<2, IdT>(key, id, slot, tmp, n, lane);
+    else if (n <= 128) done = warp_sort_reg<4, IdT>(key, id, slot, tmp, n, lane);
+    if (!done) warp_bitonic<IdT>(key, id, slot, tmp, n, lane);
+}
+
 __device__ __forceinline__ real cic_w(real x, int node)
 {
     real d = r_fabs(x - (real)node);

@@ -499,10 +499,8 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
     }
     __syncwarp();
     // the sorted keys are not needed after the sort: they serve as scratch
-    if (ne > kRadixMin) warp_radix<unsigned long long>(m.ekey, m.eid, m.eperm, m.ekey, m.rbuf, m.rhist, ne, lane);
-    else warp_bitonic<unsigned long long>(m.ekey, m.eid, m.eperm, m.ekey, ne, lane);
-    if (ni > kRadixMin) warp_radix<unsigned int>(m.ikey, m.iid, m.iperm, m.ikey, m.rbuf, m.rhist, ni, lane);
-    else warp_bitonic<unsigned int>(m.ikey, m.iid, m.iperm, m.ikey, ni, lane);
+    warp_sort<unsigned long long>(m.ekey, m.eid, m.eperm, m.ekey, m.rbuf, m.rhist, ne, lane);
+    warp_sort<unsigned int>(m.ikey, m.iid, m.iperm, m.ikey, m.rbuf, m.rhist, ni, lane);
 
     }
     __syncthreads();

@@ -401,8 +401,8 @@ __global__ void k_photon_energy(const ph2 *ph, int ncell, int nb, const real *hv
     if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(out, v);
 }
 
-// the in-cell ordering of one cell (bitonic up to kRadixMin entries, radix
-// above), run by one warp on given keys and ids: order[k] = slot at position k
+// the in-cell ordering of one cell (the cell kernel's warp_sort), run by
+// one warp on given keys and ids: order[k] = slot at position k
 __global__ void k_order_check(const unsigned long long *key_in, const unsigned long long *id_in, int n,
                               unsigned short *order)
 {
@@ -417,8 +417,7 @@ __global__ void k_order_check(const unsigned long long *key_in, const unsigned l
     const int lane = threadIdx.x;
     for (int k = lane; k < n; k += 32) { key[k] = key_in[k]; id[k] = id_in[k]; slot[k] = (unsigned short)k; }
     __syncwarp();
-    if (n > kRadixMin) warp_radix<unsigned long long>(key, id, slot, key, buf, hist, n, lane);
-    else warp_bitonic<unsigned long long>(key, id, slot, key, n, lane);
+    warp_sort<unsigned long long>(key, id, slot, key, buf, hist, n, lane);
     for (int k = lane; k < n; k += 32) order[k] = slot[k];
 }
 
