@@ -190,6 +190,11 @@ double sigma_table(const pic_ctx *c, int s, double hv)
     return std::exp(std::log(v[lo]) + f * std::log(v[lo + 1] / v[lo]));
 }
 
+// the cell-kernel instance for a launch staging up to ce electrons and ci
+// ions per cell: in-register sorts up to 128 entries, or up to 512
+typedef void (*CellKernel)(CellArgs);
+CellKernel cell_kernel(int ce, int ci) { return ce <= 128 && ci <= 128 ? k_cell<128> : k_cell<512>; }
+
 // largest warps per CTA of the cell kernel whose staging fits 200 KB
 int max_wpc(int ce, int ci, int cn)
 {
@@ -205,10 +210,11 @@ pic_status cell_smem_attr(pic_ctx *c)
     cudaFuncAttributes fa{};
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    CK(cudaFuncGetAttributes(&fa, k_cell));
+    CK(cudaFuncGetAttributes(&fa, k_cell<512>));
     const size_t m = std::max(std::max(c->smem_main, c->smem_t1), c->smem_big);
     const size_t lim = optin > (int)fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : m;
-    CK(cudaFuncSetAttribute(k_cell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max(m, lim)));
+    CK(cudaFuncSetAttribute(k_cell<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max(m, lim)));
+    CK(cudaFuncSetAttribute(k_cell<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max(m, lim)));
     return PIC_OK;
 }
 
@@ -223,7 +229,8 @@ int best_wpc(pic_ctx *c, int ce, int ci, int cn)
     int best = 1, best_warps = 0;
     for (int w = 1; w <= max_wpc(ce, ci, cn); ++w) {
         int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cell, 32 * w, per * w) != cudaSuccess) continue;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cell_kernel(ce, ci), 32 * w, per * w) != cudaSuccess)
+            continue;
         if (occ * w >= best_warps) { best_warps = occ * w; best = w; }
     }
     return best;
@@ -237,7 +244,7 @@ pic_status set_wpc(pic_ctx *c, int wpc)
     pic_status r = cell_smem_attr(c);
     if (r != PIC_OK) return r;
     int occ = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cell, wpc * 32, c->smem_main));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cell_kernel(c->cap_ce, c->cap_ci), wpc * 32, c->smem_main));
     c->grid_main = std::max(1, occ) * c->nsm;
     return PIC_OK;
 }
@@ -285,7 +292,8 @@ pic_status configure_cell_launch(pic_ctx *c, const int *hist_e, const int *hist_
     pic_status r = set_wpc(c, wpc);
     if (r != PIC_OK || !c->t1_ce) return r;
     int occ = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cell, c->t1_wpc * 32, c->smem_t1));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cell_kernel(c->t1_ce, c->t1_ci), c->t1_wpc * 32,
+                                                     c->smem_t1));
     c->grid_t1 = std::max(1, occ) * c->nsm;
     return PIC_OK;
 }
@@ -430,14 +438,14 @@ pic_status launch_step(pic_ctx *c)
     if (ev) CK(cudaEventRecord(ev[1], st));
     if (c->cell_ev_on) CK(cudaEventRecord(c->cell_ev[0], st));
     CellArgs a0 = cell_args(c, TIER0);
-    k_cell<<<c->grid_main, c->wpc * 32, c->smem_main, st>>>(a0);
+    cell_kernel(c->cap_ce, c->cap_ci)<<<c->grid_main, c->wpc * 32, c->smem_main, st>>>(a0);
     if (c->t1_ce) {
         CellArgs a1 = cell_args(c, TIER1);
-        k_cell<<<c->grid_t1, c->t1_wpc * 32, c->smem_t1, st>>>(a1);
+        cell_kernel(c->t1_ce, c->t1_ci)<<<c->grid_t1, c->t1_wpc * 32, c->smem_t1, st>>>(a1);
         ++c->launches;
     }
     CellArgs ab = cell_args(c, TIER_BIG);
-    k_cell<<<c->grid_big, 32, c->smem_big, st>>>(ab);
+    k_cell<512><<<c->grid_big, 32, c->smem_big, st>>>(ab);
     c->launches += 2;
     if (c->cell_ev_on) CK(cudaEventRecord(c->cell_ev[1], st));
     CK(cudaGetLastError());

@@ -303,10 +303,20 @@ __device__ __forceinline__ bool warp_sort_reg(const unsigned long long *key, IdT
     return true;
 }
 
-// The in-cell canonical order, ascending (key, id): registers up to
-// kRadixMin entries (the shared-memory network when high words tie), the
-// radix sort above.  slot[] must hold 0..n-1 on entry.
-template <class IdT>
+// the larger register sorts out of line: their 16-32 key registers would
+// otherwise raise the register pressure of the whole cell kernel
+template <int E, class IdT>
+__device__ __noinline__ bool warp_sort_reg_call(const unsigned long long *key, IdT *id, unsigned short *slot,
+                                                unsigned long long *tmp, int n, int lane)
+{
+    return warp_sort_reg<E, IdT>(key, id, slot, tmp, n, lane);
+}
+
+// The in-cell canonical order, ascending (key, id): registers up to RMAX
+// entries (128 or 512; the shared-memory network when high words tie or
+// the cell is larger), the radix sort above kRadixMin.  slot[] must hold
+// 0..n-1 on entry.
+template <class IdT, int RMAX = 512>
 __device__ void warp_sort(unsigned long long *key, IdT *id, unsigned short *slot, unsigned long long *tmp,
                           unsigned long long *rbuf, int *rhist, int n, int lane)
 {
@@ -315,6 +325,10 @@ __device__ void warp_sort(unsigned long long *key, IdT *id, unsigned short *slot
     if (n <= 32) done = warp_sort_reg<1, IdT>(key, id, slot, tmp, n, lane);
     else if (n <= 64) done = warp_sort_reg<2, IdT>(key, id, slot, tmp, n, lane);
     else if (n <= 128) done = warp_sort_reg<4, IdT>(key, id, slot, tmp, n, lane);
+    else if constexpr (RMAX > 128) {
+        if (n <= 256) done = warp_sort_reg_call<8, IdT>(key, id, slot, tmp, n, lane);
+        else done = warp_sort_reg_call<16, IdT>(key, id, slot, tmp, n, lane);
+    }
     if (!done) warp_bitonic<IdT>(key, id, slot, tmp, n, lane);
 }
 

@@ -442,6 +442,7 @@ __device__ __noinline__ void stage_decay(const CellArgs &a, const WarpMem &m, co
 // One round: every warp of the block takes at most one cell; the stages
 // are separated by block barriers so the warps of an SM fetch the same code
 // at the same time (the stages are long and the instruction cache small).
+template <int RMAX>
 __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables &T, int g, int lane, WarpTally &wt)
 {
     bool on = g >= 0;
@@ -499,8 +500,8 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
     }
     __syncwarp();
     // the sorted keys are not needed after the sort: they serve as scratch
-    warp_sort<unsigned long long>(m.ekey, m.eid, m.eperm, m.ekey, m.rbuf, m.rhist, ne, lane);
-    warp_sort<unsigned int>(m.ikey, m.iid, m.iperm, m.ikey, m.rbuf, m.rhist, ni, lane);
+    warp_sort<unsigned long long, RMAX>(m.ekey, m.eid, m.eperm, m.ekey, m.rbuf, m.rhist, ne, lane);
+    warp_sort<unsigned int, RMAX>(m.ikey, m.iid, m.iperm, m.ikey, m.rbuf, m.rhist, ni, lane);
 
     }
     __syncthreads();
@@ -781,6 +782,9 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
 // Each round the block takes one cell per warp from a shared counter.
 // Cells whose population exceeds this launch's shared-memory capacity go to
 // a list for the large-cell launch.
+// RMAX: the largest cell sorted in registers (128: launches whose staging
+// holds at most 128 entries per species; 512: the launches for larger cells)
+template <int RMAX>
 __global__ void __launch_bounds__(256, 2) k_cell(CellArgs a)
 {
     extern __shared__ __align__(kSmAlign) char smem[];
@@ -825,7 +829,7 @@ __global__ void __launch_bounds__(256, 2) k_cell(CellArgs a)
                 g = -1;
             }
         }
-        process_round(a, m, T, g, lane, wt);
+        process_round<RMAX>(a, m, T, g, lane, wt);
     }
     tally_flush(a, wt, lane);
 }
