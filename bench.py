@@ -328,7 +328,7 @@ def run_served(pkg, tab, args):
     cap_e = max(max(f[0] for f in fp), int(64 * sum(f[0] for f in fp) / len(fp)))
     cap_i = max(max(f[1] for f in fp), int(64 * sum(f[1] for f in fp) / len(fp)))
     b = serve.serve_batched(tr, tab, init, max_slabs=128, slot_cells=slot_cells,
-                            cap_e=cap_e, cap_i=cap_i, tick_steps=10)
+                            cap_e=cap_e, cap_i=cap_i, tick_steps=25)
     o = serve.serve_one_at_a_time(tr, tab, init)
     psteps = sum(r.nsteps * r.cfg.ncell * (r.cfg.ppc_e + r.cfg.ppc_i) for r in tr)
     keys = ("slabs_per_s", "ttr_p50_s", "ttr_p99_s", "ttr_mean_s", "wall_s")
@@ -416,8 +416,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cells", type=int, nargs=2, default=None, help="smaller foil (profiling)")
     ap.add_argument("--ensemble", type=int, default=256, help="slabs of the batched ensemble (0: skip)")
-    ap.add_argument("--serve-n", type=int, default=200, help="requests of the served trace (0: skip)")
-    ap.add_argument("--serve-horizon-fs", type=float, default=5.0, help="simulated time per served request")
+    ap.add_argument("--serve-n", type=int, default=40, help="requests of the served trace (0: skip)")
+    ap.add_argument("--serve-horizon-fs", type=float, default=150.0,
+                    help="simulated time per served request (the workload's 150 fs)")
     ap.add_argument("--kedge-points", type=int, default=12, help="photon energies of the K-edge sweep (0: skip)")
     ap.add_argument("--kedge-horizon-fs", type=float, default=30.0)
     ap.add_argument("--thermal-horizon-fs", type=float, default=60.0, help="0: skip")
