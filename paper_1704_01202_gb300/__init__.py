@@ -476,6 +476,7 @@ class Batch:
     launches = Slab.launches
     use_graphs = Slab.use_graphs
     autotune = Slab.autotune
+    autotune = Slab.autotune
 
     def admit(self, cfg, st, pulse=None) -> int:
         g, sp = _grid(cfg), _species(cfg)

@@ -35,14 +35,18 @@ def _summary(ttr: dict, t0: float, t_end: float, n: int) -> dict:
 
 
 def serve_batched(trace, tables, init_state, max_slabs: int, slot_cells: int, cap_e: int, cap_i: int,
-                  tick_steps: int = 25, keep=None, diag_bins: int = 64) -> dict:
+                  tick_steps: int = 25, keep=None, diag_bins: int = 64, autotune: bool = False) -> dict:
     """Continuous batching of `trace` (requests sorted by arrival).
 
     init_state(request) -> ParticleState gives a request's particles (the
     request payload, on the host).  keep(rid) -> bool selects requests whose
     final particles are returned (for tests).  Admission: first come first served, while a slot
-    is free and the reserved worst-case footprints fit cap_e / cap_i."""
+    is free and the reserved worst-case footprints fit cap_e / cap_i.
+    autotune: let the launch-shape autotuner time the cell kernel's warps
+    per CTA for each new staging size (results do not depend on it)."""
     bt = Batch(tables, max_slabs, slot_cells, cap_e, cap_i)
+    if autotune:
+        bt.autotune(True)
     pending = list(trace)
     active = {}                      # slot -> [request, steps left, footprint]
     res_e = res_i = 0
