@@ -1,0 +1,102 @@
+"""Pins against values the paper states in its text (tests/golden/
+paper_facts.json, each with its section): the cold K edge, how far K-shell
+photoionization reaches at three photon energies under Ecker-Kroell
+lowering (Sec. V, Eq. 4; Sec. VI B), the KLL Auger energy (Sec. VI B), the
+photoelectron energy of the 10 keV case (Sec. VI C), the time steps and
+the free-electron room per cell (Sec. VI).  The atomic data are stand-ins,
+so these check that the stand-ins and the oracle's continuum lowering,
+Auger and photoelectron energies land where the paper says the method
+lands."""
+import json
+import os
+
+import numpy as np
+
+import oracle
+import pic_inputs as P
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+MC2 = 510998.95
+FACTS = json.load(open(os.path.join(HERE, "golden", "paper_facts.json")))
+
+
+def _ke(u):
+    u2 = (u * u).sum(axis=1)
+    return MC2 * u2 / (np.sqrt(1.0 + u2) + 1.0)
+
+
+def _kind(ids):
+    return (ids >> np.uint64(32)) & np.uint64(3)
+
+
+def test_cold_k_edge(tables):
+    f = FACTS["cold_k_edge_eV"]
+    assert abs(tables["E_bind"][0][0] / f["value"] - 1) < f["rel_tol"]
+
+
+def test_k_photoionization_reach_under_ecker_kroell(tables):
+    """The highest charge state whose lowered K edge lies below hv, plus the
+    one electron the photon removes, is the product charge the paper gives
+    for each photon energy."""
+    f = FACTS["k_photoionization_reach"]
+    c = f["conditions"]
+    n_i = c["n_i_cm3"]
+    n_e = c["Zbar"] * n_i
+    edge = [tables["E_bind"][z][0] - oracle.ipd(P.IPD_EK, z, n_e, n_i, c["T_eV"], c["Zbar"]) for z in range(13)]
+    for hv, top in zip(f["hv_eV"], f["highest_product_charge"]):
+        z_max = max(z for z in range(13) if edge[z] < hv)
+        assert abs((z_max + 1) - top) <= f["tol_charge"], (hv, z_max + 1, top, np.round(edge, 1))
+
+
+def test_kll_auger_energy(tables):
+    """Al ions just K-photoionized from the solid's Al3+ (Z = 4, one K
+    vacancy) decay by KLL Auger in one rad step: the Auger electrons carry
+    about 1.4 keV."""
+    f = FACTS["kll_auger_energy_keV"]
+    cfg = P.cfg_small_1d(flags=P.F_DECAY, nx=2, ppc_e=4, ppc_i=64, beam_frac=0.0, rad_every=1)
+    st = P.init_particles(cfg)
+    st.iZ[:] = 4
+    st.inK[:] = 1
+    tab = dict(tables)
+    tab["tauK"] = np.asarray(tables["tauK"]) * 1e-3       # every vacancy decays within the step
+    tab["omegaK"] = np.zeros_like(np.asarray(tables["omegaK"]))
+    o = oracle.OracleSlab(cfg, tab, P.Pulse(I_peak_Wcm2=0.0, n_bins=1))
+    o.load(st)
+    o.step(1)
+    e = o.electrons()
+    aug = _kind(e["id"]) == 3
+    assert aug.sum() == st.n_i
+    ke = _ke(e["u"][aug]) / 1e3
+    assert np.all(np.abs(ke / f["value"] - 1) < f["rel_tol"]), (ke.min(), ke.max())
+
+
+def test_photoelectrons_of_the_10kev_case(tables):
+    """10 keV photons on Al3+: the K-shell photoelectrons (most of the
+    events at this energy) carry about 8 keV."""
+    f = FACTS["photoelectron_10keV_keV"]
+    cfg = P.cfg_small_1d(flags=P.F_PHOTO, nx=32, ppc_e=4, ppc_i=64, beam_frac=0.0, rad_every=1)
+    pl = P.Pulse(I_peak_Wcm2=1.0e19, fwhm_fs=20.0, t_peak_fs=0.0, hv_eV=10000.0, n_bins=2, bandwidth_eV=20.0)
+    tab = dict(tables)
+    tab["sigma_photo"] = np.asarray(tables["sigma_photo"]) * 100.0
+    st = P.init_particles(cfg)
+    o = oracle.OracleSlab(cfg, tab, pl)
+    o.load(st)
+    o.set_photons(P.photons_uniform(cfg, pl, 50.0))
+    o.step(1)
+    e = o.electrons()
+    ph = _kind(e["id"]) == 2
+    assert ph.sum() > 20
+    ke = _ke(e["u"][ph]) / 1e3
+    k_shell = ke < 9.0                      # L-shell photoelectrons sit near 9.9 keV
+    assert k_shell.mean() > 0.5
+    assert abs(np.median(ke[k_shell]) / f["value"] - 1) < f["rel_tol"], np.median(ke[k_shell])
+
+
+def test_time_steps_and_electron_room():
+    f = FACTS["time_steps_fs"]
+    cfg = P.cfg_small_1d()
+    assert cfg.dt_fs == f["dt_pic"] and abs(cfg.rad_every * cfg.dt_fs - f["dt_rad"]) < 1e-12
+    g = FACTS["free_electrons_per_cell_max"]
+    from paper_1704_01202_gb300.serve import footprint
+    one = P.cfg_small_1d(nx=1, ppc_i=g["ions_per_cell"], ppc_e=3 * g["ions_per_cell"])
+    assert footprint(one)[0] == g["value"]
