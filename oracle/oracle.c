@@ -28,7 +28,8 @@
  *   then over all particles:
  *   8. relativistic Boris push, charge-conserving (Esirkepov) deposit
  *   9. Yee field update at the field speed the step resolves (see
- *      orc_field_speed), periodic in y, first-order Mur in x
+ *      orc_field_speed) with the binomially smoothed current (see
+ *      smooth_current), periodic in y, first-order Mur in x
  */
 #include "oracle.h"
 
@@ -1222,13 +1223,53 @@ double orc_field_speed(const orc_params *p)
     return C_NM_FS < cmax ? C_NM_FS : cmax;
 }
 
+/* The current the field update sees: the deposited current smoothed by the
+ * binomial (1/4, 1/2, 1/4) filter along x, and along y (periodic) in 2D,
+ * each component over its own points (Jx on the nx faces of a row, Jy and
+ * Jz on its nx + 1 nodes; nothing beyond the slab).  A linear filter of
+ * constant weights commutes with the discrete divergence away from the x
+ * boundaries, so Gauss's law holds there for the equally smoothed charge;
+ * the smoothing damps the grid-scale modes through which cells many Debye
+ * lengths wide heat numerically. */
+static void smooth_current(const double *jc, double *out, int nx, int ny)
+{
+    const int W = nx + 1;
+    const size_t ng = (size_t)ny * W;
+    for (int c = 0; c < 3; ++c) {
+        const double *src = jc + c * ng;
+        double *dst = out + c * ng;
+        const int imax = c == 0 ? nx - 1 : nx;
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < W; ++i) {
+                if (i > imax) { dst[(size_t)j * W + i] = 0.0; continue; }
+                double acc = 0.0;
+                for (int b = -1; b <= 1; ++b) {
+                    if (ny == 1 && b != 0) continue;
+                    const int jj = (j + b + ny) % ny;
+                    const double wy = ny == 1 ? 1.0 : (b == 0 ? 0.5 : 0.25);
+                    for (int a = -1; a <= 1; ++a) {
+                        const int ii = i + a;
+                        if (ii < 0 || ii > imax) continue;
+                        acc += wy * (a == 0 ? 0.5 : 0.25) * src[(size_t)jj * W + ii];
+                    }
+                }
+                dst[(size_t)j * W + i] = acc;
+            }
+    }
+}
+
 static void field_step(orc_slab *s)
 {
     const orc_params *p = &s->p;
     const double cf = orc_field_speed(p), dt = p->dt, kap = kappa_J(s);
+    const size_t ng = (size_t)p->ny * (p->nx + 1);
+    double *js = (double *)malloc(sizeof(double) * 3 * ng);
+    if (!js) abort();
+    smooth_current(s->j, js, p->nx, p->ny);
     b_half(s->f, p->nx, p->ny, p->dx, p->dy, 0.5 * dt, cf);
-    e_full(s->f, s->j, p->nx, p->ny, p->dx, p->dy, dt, kap, cf);
+    e_full(s->f, js, p->nx, p->ny, p->dx, p->dy, dt, kap, cf);
     b_half(s->f, p->nx, p->ny, p->dx, p->dy, 0.5 * dt, cf);
+    free(js);
 }
 
 /* field at (X, Y): CIC from the staggered grid, zero outside [0, nx] */

@@ -275,15 +275,33 @@ __global__ void k_e_full(FieldArgs a)
             real lo = (real)(unsigned)(v & 0xffffffffll);
             return (hi + lo) * (real)(1.0 / JFIX) * scale;
         };
+        // the current the update sees: (1/4, 1/2, 1/4) along x over the
+        // component's own points (nx faces for Jx, nx + 1 nodes for Jy, Jz;
+        // nothing beyond the slab) and along y (periodic) in 2D
+        const int rp1 = o + ((j + 1) % S.ny) * W;
+        auto js = [&](const unsigned long long *Jc, int ii, int imax, real scale) {
+            real acc = RF(0.0);
+            for (int b = 0; b < 3; ++b) {
+                if (S.ny == 1 && b != 1) continue;
+                const int rr = b == 0 ? rm : (b == 1 ? r : rp1);
+                const real wy = S.ny == 1 ? RF(1.0) : (b == 1 ? RF(0.5) : RF(0.25));
+                for (int d = -1; d <= 1; ++d) {
+                    const int ix = ii + d;
+                    if (ix < 0 || ix > imax) continue;
+                    acc += wy * (d == 0 ? RF(0.5) : RF(0.25)) * jv(Jc, rr + ix, scale);
+                }
+            }
+            return acc;
+        };
         auto ey_new = [&](int ii) {
-            return eyi[r + ii] + dtf * (-Cf * (bz[r + ii] - bz[r + ii - 1]) / S.dx - kap * jv(Jy, r + ii, sy));
+            return eyi[r + ii] + dtf * (-Cf * (bz[r + ii] - bz[r + ii - 1]) / S.dx - kap * js(Jy, ii, S.nx, sy));
         };
         auto ez_new = [&](int ii) {
             return ezi[r + ii] + dtf * (Cf * ((by[r + ii] - by[r + ii - 1]) / S.dx - (bx[r + ii] - bx[rm + ii]) / S.dy)
-                                        - kap * jv(Jz, r + ii, C));
+                                        - kap * js(Jz, ii, S.nx, C));
         };
         if (i < S.nx)
-            exo[p] = exi[p] + dtf * (Cf * (bz[r + i] - bz[rm + i]) / S.dy - kap * jv(Jx, p, sx));
+            exo[p] = exi[p] + dtf * (Cf * (bz[r + i] - bz[rm + i]) / S.dy - kap * js(Jx, i, S.nx - 1, sx));
         else
             exo[p] = exi[p];
         if (i >= 1 && i < S.nx) {

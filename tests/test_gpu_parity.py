@@ -233,13 +233,13 @@ def test_energy_bookkeeping_gpu(tables):
 
 def test_full_step_energy_drift_matches_oracle(tables):
     """With the push, the deposit and the fields on, the total energy of the
-    small 1D slab is not conserved by the explicit PIC step: it first dips
-    (field energy radiated through the absorbing boundaries is not tallied)
-    and then grows through the numerical heating of cells ~50 Debye lengths
-    wide, +2.4 % of itself over the 500 steps of the workload.  That drift
-    belongs to the scheme, so the device reproduces the oracle's: the two
-    independent (decorrelating) runs' drifts agree within 10 % (measured
-    4 % apart)."""
+    small 1D slab is not conserved by the explicit PIC step: it dips (field
+    energy radiated through the absorbing boundaries is not tallied) and
+    then rises through the residual numerical heating of cells ~50 Debye
+    lengths wide (-0.7 % after 200 steps, +0.3 % after 500 with the
+    smoothed current).  That drift belongs to the scheme, so the device's
+    drift curve follows the oracle's: within 0.1 % of the initial energy at
+    every 100 steps (two oracle seeds differ by 0.07 %)."""
     cfg = P.cfg_small_1d()
     st = P.init_particles(cfg)
     g = pkg.Slab(cfg, tables)
@@ -256,12 +256,14 @@ def test_full_step_energy_drift_matches_oracle(tables):
 
     e0g, e0o = tot_g(g.diagnostics()), tot_o(o.tallies()[0])
     assert abs(e0g / e0o - 1) < 1e-6
-    g.step(500)
-    o.step(500)
-    dg = tot_g(g.diagnostics()) - e0g
-    do = tot_o(o.tallies()[0]) - e0o
-    print(f"\nenergy drift over 500 steps: device {dg / e0g:.4e}, oracle {do / e0o:.4e} of the initial energy")
-    assert do > 0 and abs(dg - do) <= 0.10 * abs(do), (dg / e0g, do / e0o)
+    rows = []
+    for _ in range(5):
+        g.step(100)
+        o.step(100)
+        rows.append(((tot_g(g.diagnostics()) - e0g) / e0g, (tot_o(o.tallies()[0]) - e0o) / e0o))
+    print("\nenergy drift every 100 steps (device, oracle):", [(round(a, 5), round(b, 5)) for a, b in rows])
+    assert max(abs(a - b) for a, b in rows) < 1e-3, rows
+    assert max(abs(b) for _, b in rows) < 0.02, rows
 
 
 def test_full_size_sampled_cells(tables):
