@@ -67,7 +67,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     procs = []
     for path, flags in todo:
         tmp = path + f".{os.getpid()}.tmp"
-        cmd = ["nvcc", ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", *flags,
+        cmd = ["nvcc", ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC,-pthread", *flags,
                "-o", tmp, os.path.join(_SRC, "pic_api.cu")]
         procs.append((path, tmp, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)))
     errors = []

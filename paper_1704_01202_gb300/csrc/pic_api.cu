@@ -16,6 +16,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/pic.h"
@@ -741,22 +742,41 @@ pic_status build_records(pic_ctx *c, int slot, const pic_grid *g, bool electrons
 {
     p0.resize(n); p1.resize(n); key.resize(n);
     const int cell0 = slot * c->slot_cells;
-    for (int64_t k = 0; k < n; ++k) {
-        double fx = std::floor(X[k]), fy = g->ny > 1 ? std::floor(Y[k]) : 0.0;
-        if (!(fx >= 0 && fx < g->nx && fy >= 0 && fy < g->ny))
-            return fail(c, PIC_ERR_ARG, "particle position outside the slab");
-        real xi = (real)(X[k] - fx), eta = g->ny > 1 ? (real)(Y[k] - fy) : (real)Y[k];
-        if (xi >= (real)1) xi = kBelow1;
-        if (g->ny > 1 && eta >= (real)1) eta = kBelow1;
-        key[k] = cell0 + (int)fy * g->nx + (int)fx;
-        p0[k] = make_real4(xi, eta, u[3 * k], u[3 * k + 1]);
-        if (electrons) {
-            p1[k] = rec_e1(u[3 * k + 2], w_or_zf[k], eid[k]);
-        } else {
-            if (Z[k] < 0 || Z[k] > ZNUC || nK[k] < 0 || nK[k] > 2) return fail(c, PIC_ERR_ARG, "ion state out of range");
-            int stv = Z[k] | (nK[k] << 8);
-            p1[k] = rec_i1(u[3 * k + 2], w_or_zf[k], iid[k], stv);
+    // 0 ok, 1 position outside the slab, 2 ion state out of range
+    auto fill = [&](int64_t lo, int64_t hi) -> int {
+        for (int64_t k = lo; k < hi; ++k) {
+            double fx = std::floor(X[k]), fy = g->ny > 1 ? std::floor(Y[k]) : 0.0;
+            if (!(fx >= 0 && fx < g->nx && fy >= 0 && fy < g->ny)) return 1;
+            real xi = (real)(X[k] - fx), eta = g->ny > 1 ? (real)(Y[k] - fy) : (real)Y[k];
+            if (xi >= (real)1) xi = kBelow1;
+            if (g->ny > 1 && eta >= (real)1) eta = kBelow1;
+            key[k] = cell0 + (int)fy * g->nx + (int)fx;
+            p0[k] = make_real4(xi, eta, u[3 * k], u[3 * k + 1]);
+            if (electrons) {
+                p1[k] = rec_e1(u[3 * k + 2], w_or_zf[k], eid[k]);
+            } else {
+                if (Z[k] < 0 || Z[k] > ZNUC || nK[k] < 0 || nK[k] > 2) return 2;
+                int stv = Z[k] | (nK[k] << 8);
+                p1[k] = rec_i1(u[3 * k + 2], w_or_zf[k], iid[k], stv);
+            }
         }
+        return 0;
+    };
+    // large loads are split over host threads (disjoint ranges, same records)
+    const int64_t per = 1 << 20;
+    const int nt = (int)std::min<int64_t>(std::max(1u, std::thread::hardware_concurrency()), (n + per - 1) / per);
+    std::vector<int> rc(std::max(nt, 1), 0);
+    if (nt <= 1) {
+        rc[0] = fill(0, n);
+    } else {
+        std::vector<std::thread> th;
+        for (int t = 0; t < nt; ++t)
+            th.emplace_back([&, t] { rc[t] = fill(n * t / nt, n * (t + 1) / nt); });
+        for (auto &x : th) x.join();
+    }
+    for (int r : rc) {
+        if (r == 1) return fail(c, PIC_ERR_ARG, "particle position outside the slab");
+        if (r == 2) return fail(c, PIC_ERR_ARG, "ion state out of range");
     }
     return PIC_OK;
 }
