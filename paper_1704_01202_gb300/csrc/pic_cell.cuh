@@ -246,8 +246,8 @@ __device__ __forceinline__ void reg_cmpx_in_lane(unsigned long long (&v)[E], int
 }
 
 template <int E, class IdT>
-__device__ __forceinline__ bool warp_sort_reg(const unsigned long long *key, IdT *id, unsigned short *slot,
-                                           unsigned long long *tmp, int n, int lane)
+__device__ __forceinline__ bool warp_sort_reg(const unsigned long long *key, IdT *id, unsigned short *slot, int n,
+                                              int lane)
 {
     unsigned long long v[E];
 #pragma unroll
@@ -299,17 +299,16 @@ __device__ __forceinline__ bool warp_sort_reg(const unsigned long long *key, IdT
         if (k < n) { slot[k] = (unsigned short)(v[j] & 0xffffu); id[k] = idv[j]; }
     }
     __syncwarp();
-    (void)tmp;
     return true;
 }
 
 // the larger register sorts out of line: their 16-32 key registers would
 // otherwise raise the register pressure of the whole cell kernel
 template <int E, class IdT>
-__device__ __noinline__ bool warp_sort_reg_call(const unsigned long long *key, IdT *id, unsigned short *slot,
-                                                unsigned long long *tmp, int n, int lane)
+__device__ __noinline__ bool warp_sort_reg_call(const unsigned long long *key, IdT *id, unsigned short *slot, int n,
+                                                int lane)
 {
-    return warp_sort_reg<E, IdT>(key, id, slot, tmp, n, lane);
+    return warp_sort_reg<E, IdT>(key, id, slot, n, lane);
 }
 
 // The in-cell canonical order, ascending (key, id): registers up to RMAX
@@ -322,12 +321,12 @@ __device__ void warp_sort(unsigned long long *key, IdT *id, unsigned short *slot
 {
     if (n > kRadixMin) { warp_radix<IdT>(key, id, slot, tmp, rbuf, rhist, n, lane); return; }
     bool done = false;
-    if (n <= 32) done = warp_sort_reg<1, IdT>(key, id, slot, tmp, n, lane);
-    else if (n <= 64) done = warp_sort_reg<2, IdT>(key, id, slot, tmp, n, lane);
-    else if (n <= 128) done = warp_sort_reg<4, IdT>(key, id, slot, tmp, n, lane);
+    if (n <= 32) done = warp_sort_reg<1, IdT>(key, id, slot, n, lane);
+    else if (n <= 64) done = warp_sort_reg<2, IdT>(key, id, slot, n, lane);
+    else if (n <= 128) done = warp_sort_reg<4, IdT>(key, id, slot, n, lane);
     else if constexpr (RMAX > 128) {
-        if (n <= 256) done = warp_sort_reg_call<8, IdT>(key, id, slot, tmp, n, lane);
-        else done = warp_sort_reg_call<16, IdT>(key, id, slot, tmp, n, lane);
+        if (n <= 256) done = warp_sort_reg_call<8, IdT>(key, id, slot, n, lane);
+        else done = warp_sort_reg_call<16, IdT>(key, id, slot, n, lane);
     }
     if (!done) warp_bitonic<IdT>(key, id, slot, tmp, n, lane);
 }
