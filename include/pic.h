@@ -291,7 +291,7 @@ pic_status pic_order_check(const uint64_t *key, const uint64_t *id, int n, uint1
 /* The same check without any device allocation.  The paper has no
  * counterpart: this serves callers that must not allocate, e.g. a host
  * thread of a serving loop whose device memory budget is fixed up front, or
- * code about to run under stream capture, where cudaMalloc is not allowed.
+ * code that is not allowed to enter the device allocator at all.
  * Scratch is a static device array of PIC_PHILOX_STATIC_MAX counters (four
  * words each, 128 KiB in all); n above that returns PIC_ERR_ARG.  Nothing in
  * the scratch needs to start at zero: every word is written before it is
