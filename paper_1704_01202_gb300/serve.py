@@ -11,6 +11,9 @@ Both replay the same arrival trace in real time and return per-request
 time-to-result (result ready minus arrival) and the drained slabs/s.  A
 slab's result is the same alone and in the mix (its random streams are
 keyed by its own seed, ids and step count).
+
+    python -m paper_1704_01202_gb300.serve --requests 40 --horizon-fs 150
+    python -m paper_1704_01202_gb300.serve --static 48 --steps 4
 """
 from __future__ import annotations
 
@@ -118,3 +121,50 @@ def serve_one_at_a_time(trace, tables, init_state, keep=None, diag_bins: int = 6
     out = _summary(ttr, t0, time.perf_counter(), len(trace))
     out.update(results=results, finals=finals, ttr=ttr)
     return out
+
+
+def main():
+    """Replay the seeded request trace (continuous batching against one at a
+    time), or with --static N admit the first N requests at once and run K
+    steps of the batch (a fixed batch for profiling the batched kernels)."""
+    import argparse
+    import json
+    import pic_inputs as P
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--requests", type=int, default=40)
+    ap.add_argument("--horizon-fs", type=float, default=150.0)
+    ap.add_argument("--static", type=int, default=0, help="admit this many requests at once and step")
+    ap.add_argument("--steps", type=int, default=4)
+    args = ap.parse_args()
+    tab = P.standin_tables()
+    if args.static:
+        tr = P.request_trace(n=args.static, rate_hz=200.0, seed=11, horizon_fs=args.horizon_fs)
+        fp = [footprint(r.cfg) for r in tr]
+        bt = Batch(tab, len(tr), max(r.cfg.nx for r in tr), sum(f[0] for f in fp) + 1024, sum(f[1] for f in fp) + 1024)
+        try:
+            bt.use_graphs(False)
+            for r in tr:
+                bt.admit(r.cfg, P.init_particles(r.cfg), r.pulse)
+            t0 = time.perf_counter()
+            bt.step(args.steps)
+            bt.sync()
+            wall = time.perf_counter() - t0
+        finally:
+            bt.close()
+        print(json.dumps({"requests": len(tr), "steps": args.steps, "wall_s": wall,
+                          "particles": int(sum(r.cfg.ncell * (r.cfg.ppc_e + r.cfg.ppc_i) for r in tr))}))
+        return
+    tr = P.request_trace(n=args.requests, rate_hz=200.0, seed=11, horizon_fs=args.horizon_fs)
+    payload = {r.rid: P.init_particles(r.cfg) for r in tr}
+    fp = [footprint(r.cfg) for r in tr]
+    cap_e = max(max(f[0] for f in fp), int(64 * sum(f[0] for f in fp) / len(fp)))
+    cap_i = max(max(f[1] for f in fp), int(64 * sum(f[1] for f in fp) / len(fp)))
+    b = serve_batched(tr, tab, lambda r: payload[r.rid], 128, max(r.cfg.nx for r in tr), cap_e, cap_i)
+    o = serve_one_at_a_time(tr, tab, lambda r: payload[r.rid])
+    keys = ("slabs_per_s", "ttr_p50_s", "ttr_p99_s", "wall_s")
+    print(json.dumps({"batched": {k: b[k] for k in keys}, "one_at_a_time": {k: o[k] for k in keys},
+                      "speedup": b["slabs_per_s"] / o["slabs_per_s"]}))
+
+
+if __name__ == "__main__":
+    main()
