@@ -1,10 +1,11 @@
-// The per-cell hot path: one warp owns one cell and runs, in order, the
-// canonical random ordering of its particles, the FP64 cell moments, binary
-// e-e and e-i collisions, Lotz impact ionization, EOS-clamped
-// recombination, (rad steps) subshell photoionization and K-vacancy decay,
-// then the Boris push and the charge-conserving deposit of every particle of
-// the cell.  Particles are staged in shared memory; their positions stay in
-// global memory until the push.
+// Building blocks of the per-cell hot path: one warp owns one cell and runs,
+// in order, the canonical random ordering of its particles, the cell
+// moments (double-float sums), binary e-e and e-i collisions, Lotz impact
+// ionization, EOS-clamped recombination and, on rad steps, subshell
+// photoionization and K-vacancy decay (k_cell); the Boris push and the
+// charge-conserving deposit of the cell's particles follow in a second
+// kernel in the same canonical order (k_push).  Particles are staged in
+// shared memory; their positions stay in global memory until the push.
 //
 // Determinism: every random number is keyed by (slab seed, particle id,
 // step, purpose) and every ordering comes from a sort on Philox keys, so

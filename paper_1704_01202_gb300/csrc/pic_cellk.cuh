@@ -1,4 +1,6 @@
-// The fused per-cell kernel (see pic_cell.cuh for the building blocks).
+// The per-cell collision and atomic-process kernel k_cell: one warp per
+// cell, phase-synchronous rounds (see pic_cell.cuh for the building blocks;
+// the push and deposit follow in pic_push.cuh).
 #pragma once
 #include <type_traits>
 #include "pic_cell.cuh"
