@@ -10,7 +10,9 @@
  * partial events, K-vacancy decay with KLL-Auger / K-alpha branching
  * (Sec. III), continuum lowering (Sec. V, Eqs. 4-5), ballistic march of the
  * XFEL photons (Sec. II, reduced to attenuation along x), Boris push,
- * charge-conserving deposit and a subcycled Yee field update.
+ * charge-conserving deposit and one Yee field update per step at the
+ * field speed the step resolves (light slowed where c dt exceeds the
+ * Courant limit of the cells).
  *
  * Units: lengths nm, times fs, energies eV, momenta u = gamma v / c,
  * particle weights in units of n_ref * V_cell (n_ref = reference density),
@@ -72,7 +74,8 @@ typedef struct {
     double dt_fs;
     int rad_every;          /* photon march / photoionization / decay period */
     uint64_t seed;          /* Philox key of the slab */
-    double cfl;             /* field subcycle margin, c dt_f <= cfl * Yee limit */
+    double cfl;             /* Courant number of the field update: its speed is
+                             * min(c, cfl / (dt sqrt(1/dx^2 + [ny>1]/dy^2))) */
 } pic_grid;
 
 /* Species and model switches of one slab.  Ions share one weight. */
@@ -271,7 +274,7 @@ pic_status pic_autotune(pic_ctx *c, int enable, int *wpc_out, float *ms_out);
  * returns the summed device time of the steps recorded so far: [0] the
  * per-cell collision / atomic-process kernel (both passes), [1] photon march,
  * [2] push + deposit, [3] counting sort (scan + scatter), [4] field
- * subcycles, [5] whole steps; *nsteps gets the number of steps. */
+ * update, [5] whole steps; *nsteps gets the number of steps. */
 pic_status pic_timing(pic_ctx *c, int enable, double *ms_out, int64_t *nsteps);
 
 pic_status pic_free(pic_ctx *c);

@@ -1621,7 +1621,8 @@ pic_status pic_philox_check(const uint32_t *ctr, const uint32_t key[2], uint32_t
     if (cudaMemcpy(d, ctr, sizeof(uint32_t) * 4 * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess) st = PIC_ERR_CUDA;
     if (st == PIC_OK) {
         k_philox_check<<<(n + 127) / 128, 128>>>(d, key[0], key[1], d + 4 * (size_t)n, n);
-        if (cudaMemcpy(out, d + 4 * (size_t)n, sizeof(uint32_t) * 4 * (size_t)n, cudaMemcpyDeviceToHost) != cudaSuccess)
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpy(out, d + 4 * (size_t)n, sizeof(uint32_t) * 4 * (size_t)n, cudaMemcpyDeviceToHost) != cudaSuccess)
             st = PIC_ERR_CUDA;
     }
     cudaFree(d);

@@ -1,5 +1,5 @@
 // Grid-level kernels: photon march, counting sort (scan + scatter), Yee
-// field subcycles, particle loading and diagnostic reductions.
+// field update, particle loading and diagnostic reductions.
 #pragma once
 #include "pic_dev.cuh"
 
@@ -210,7 +210,8 @@ __global__ void k_count(const int *key, const int *n_ptr, int *cnt)
 }
 
 // ---------------------------------------------------------------------
-// Yee field subcycle, all slabs at once; y periodic, Mur in x.
+// Yee field update, all slabs at once; y periodic, Mur in x.  One update per
+// step (nsub = 1) at the slab's field speed cf, the largest the step resolves.
 // E is double buffered so the Mur boundary can read old interior values.
 // ---------------------------------------------------------------------
 struct FieldArgs {
@@ -221,7 +222,7 @@ struct FieldArgs {
     real *Eout;             // [3][npts]
     real *B;                // [3][npts]
     const unsigned long long *J;   // [3][npts] fixed point
-    int sub;                 // subcycle index
+    int sub;                 // update index within the step (always 0: nsub = 1)
 };
 
 __global__ void k_b_half(FieldArgs a)

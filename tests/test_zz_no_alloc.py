@@ -1,6 +1,8 @@
 """The allocation-free Philox check (pic_philox_check_static) against the
-allocating one (pic_philox_check), through the C ABI.  Kept in a file that
-is collected last so it also runs after every other GPU test."""
+allocating one (pic_philox_check), through the C ABI, and on its own
+against the oracle's Philox4x32-10 (itself checked against cuRAND's
+generator).  Kept in a file that is collected last so it also runs after
+every other GPU test."""
 import ctypes as C
 
 import numpy as np
@@ -12,6 +14,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
+import oracle  # noqa: E402
 import paper_1704_01202_gb300 as pkg  # noqa: E402
 
 MAX = 4096      # PIC_PHILOX_STATIC_MAX in include/pic.h
@@ -38,6 +41,22 @@ def test_static_matches_allocating_twice(n):
         st_b, got = _call(L.pic_philox_check_static, ctr, key)
         assert st_a == 0 and st_b == 0, (call, st_a, st_b)
         assert np.array_equal(got, ref), call
+
+
+def test_static_matches_oracle_at_max():
+    """One call at the largest size, compared row by row (a sample of rows
+    and both ends) with the oracle's independent Philox4x32-10."""
+    pkg.build()
+    L = pkg.lib()
+    rng = np.random.default_rng(77)
+    ctr = rng.integers(0, 2**32, size=(MAX, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    key = np.array([0xDEADBEEF, 0x01234567], dtype=np.uint32)
+    st, got = _call(L.pic_philox_check_static, ctr, key)
+    assert st == 0
+    rows = np.concatenate([[0, 1, MAX - 1], rng.choice(MAX, 61, replace=False)])
+    for r in rows:
+        assert np.array_equal(got[r], oracle.philox(ctr[r], key)), r
 
 
 def test_static_rejects_oversize():
