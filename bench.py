@@ -1,19 +1,27 @@
 """Benchmark: collided particle-steps/s of the GB300 collisional-PIC step.
 
-Workload: the 2D XFEL-driven Al foil, 2048 x 256 cells of 5 nm, 64
-electrons + 16 Al3+ per cell (41.9 M macroparticles), 1.6 keV / 80 fs /
-1e17 W/cm^2 pulse, every process on, FP32 particle state with FP64 cell
-sums.  A step is one pass of the whole hot path (march, sort, collisions,
-atomic processes, push, deposit, fields) over the slab.
+Workload: the large 2D slab of solid Al, 8192 x 1024 cells of 5 nm, 80
+electrons + 20 Al3+ per cell (0.84e9 macroparticles at the start), 1.8
+keV / 80 fs / 5e17 W/cm^2 pulse peaking at 40 fs, every process on, FP32
+particle state with FP64-grade (double-float) cell sums: the largest
+workload that fits one GPU.  A step is one pass of the whole hot path
+(march, sort, collisions, atomic processes, push, deposit, fields) over
+the slab.
+
+The slab is first advanced --advance-fs (10 fs, 500 steps) outside the
+clock, so that the timed steps run on a plasma that the beam electrons and
+the pulse have already ionized (several charge states per cell, more
+electrons than at the start), not on the cold Al3+ of step 0; the mean
+rate over the advance is reported beside the timed value.
 
 value: particle-steps/s with the state resident in HBM (device-timed with
 CUDA events on the context stream, K steps between a synchronize on each
 side).  e2e: the same metric through the public API with host buffers:
 the H2D load of the initial state and a D2H diagnostics read every step
-inside the timed region.  The state (1.3 GB) is far larger than L2.
+inside the timed region.  The state (27 GB) is far larger than L2.
 
 --impl reference: the FP64 oracle on the host cores, on a bounded sample
-of the same workload (a 64 x 64-cell patch of the foil).
+of the same workload (a 64 x 64-cell patch of the slab).
 """
 import argparse
 import json
@@ -39,10 +47,10 @@ UNIT = "particle-steps/s"
 CELL_BYTES_PER_PARTICLE = 68
 # whole step: cell kernel 68 B + scatter (36 B read, 32 B written)
 STEP_BYTES_PER_PARTICLE = 136
-# DRAM bytes per particle of the cell kernel's main pass, from one ncu
-# capture of the foil at 512 x 256 cells (profiles/k_cell_k_push_al_2d_512x256x5nm.md),
-# scaled to a launch by the particle count; None once the kernel changes
-CELL_TRAFFIC_BYTES_PER_PARTICLE = 65.8
+# DRAM bytes per particle of the cell kernel, from one ncu capture of a
+# smaller slab of the same make-up (profiles/), scaled to a launch by the
+# particle count; None when no capture of the current kernel exists
+CELL_TRAFFIC_BYTES_PER_PARTICLE = None
 
 
 def measured_peaks():
@@ -121,19 +129,25 @@ def aggregate(ms, particle_steps, dist=None, device="cpu"):
     return float(t.item()), float(n.item()) / (float(t.item()) * 1e-3)
 
 
-def workload(cells=None):
-    cfg = P.cfg_foil_2d()
+def workload(cells=None, which="large"):
+    """The timed workload: the large 2D slab (8192 x 1024 cells, 80 e + 20 i)
+    or, with which="foil", the 2D foil (2048 x 256 cells, 64 e + 16 i);
+    cells: a smaller slab of the same make-up (profiling)."""
+    if which == "foil":
+        cfg, pl = P.cfg_foil_2d(), P.pulse_foil_2d()
+    else:
+        cfg, pl = P.cfg_large_2d(), P.pulse_large_2d()
     if cells:
-        cfg = P.cfg_foil_2d(nx=cells[0], ny=cells[1], name=f"al_2d_{cells[0]}x{cells[1]}x5nm_64e16i")
-    pl = P.pulse_foil_2d()
+        cfg.nx, cfg.ny = cells
+        cfg.name = f"al_2d_{cells[0]}x{cells[1]}x5nm_{cfg.ppc_e}e{cfg.ppc_i}i"
     return cfg, pl
 
 
-def cpu_baseline(steps=32, patch=128):
-    """The oracle as it stands on a patch of the foil (default 128 x 128
-    cells, 1.3 M particles, 32 steps: about 10 s on 16 host cores)."""
+def cpu_baseline(steps=32, patch=128, which="large"):
+    """The oracle as it stands on a patch of the workload (default 128 x 128
+    cells, 1.6 M particles, 32 steps: about 10 s on 16 host cores)."""
     import oracle
-    cfg, pl = workload()
+    cfg, pl = workload(which=which)
     sub = P.SlabConfig(**{**cfg.to_dict(), "nx": patch, "ny": patch})
     st = P.init_particles(sub)
     o = oracle.OracleSlab(sub, P.standin_tables(), pl)
@@ -145,21 +159,21 @@ def cpu_baseline(steps=32, patch=128):
     o.step(steps, threads=cores)
     dt = time.perf_counter() - t0
     return {"value": n * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{patch}x{patch}-cell patch of the foil ({n} particles), {steps} steps after 1 warm-up, "
-                      f"OpenMP over cells"}
+            "sample": f"{patch}x{patch}-cell patch of {cfg.name} ({n} particles), {steps} steps after "
+                      f"1 warm-up, OpenMP over cells"}
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    cfg, _ = workload()
+    cfg, _ = workload(which=args.workload)
     vals = []
     for _ in range(max(1, args.warmup)):
-        cpu_baseline(steps=1, patch=64)
+        cpu_baseline(steps=1, patch=64, which=args.workload)
     cb = None
     for _ in range(args.steps):
-        cb = cpu_baseline(steps=2, patch=64)
+        cb = cpu_baseline(steps=2, patch=64, which=args.workload)
         vals.append(cb["value"])
     v = statistics.median(vals)
     cb["value"] = v
@@ -170,6 +184,20 @@ def run_reference(args):
            "cpu_baseline": cb,
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
+
+
+def capacity(cfg, n_e, n_i):
+    """Particle capacity of the timed slab: electrons for a mean charge up to
+    9.5 on the large slab (the precision study's figure), for full
+    stripping otherwise (below 2^31 slots)."""
+    import paper_1704_01202_gb300 as pkg
+    ce, ci = pkg.default_capacity(n_e, n_i, cfg.Z_init)
+    return min(ce, int(9.5 * n_i) + 1024, (1 << 31) - (1 << 28)), ci
+
+
+def charge_states(csd, share=0.01):
+    """Charge states holding more than `share` of the ions."""
+    return [z for z, f in enumerate(csd) if f > share]
 
 
 def run_gpu(args):
@@ -185,25 +213,49 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     pkg.build()
-    cfg, pl = workload(args.cells)
-    # replicas: every rank runs its own foil with its own seed
+    cfg, pl = workload(args.cells, args.workload)
+    # replicas: every rank runs its own slab with its own seed
     cfg.seed = cfg.seed + rank
     tab = P.standin_tables()
+    t_gen = time.perf_counter()
     st = P.init_particles(cfg)
+    t_gen = time.perf_counter() - t_gen
     n0 = st.n_e + st.n_i
-    slab = pkg.Slab(cfg, tab, pl)
+    cap_e, cap_i = capacity(cfg, st.n_e, st.n_i)
+    slab = pkg.Slab(cfg, tab, pl, cap_e=cap_e, cap_i=cap_i)
     slab.load(st)
     stream = torch.cuda.current_stream()
 
-    # launch-shape autotuning on the first steps (real steps of the run)
-    if not args.no_autotune:
+    # advance outside the clock (autotuning the launch shapes on its first
+    # steps; these are real steps of the run), timed as a whole for the mean
+    n_adv = int(round(args.advance_fs / cfg.dt_fs))
+    tune_steps = 0 if args.no_autotune else min(9, n_adv)
+    adv = {"steps": n_adv, "fs": n_adv * cfg.dt_fs}
+    ne_a, ni_a = slab.counts()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a0.record(stream)
+    if tune_steps:
         slab.autotune(True)
-        slab.step(9)
+        slab.step(tune_steps)
+        slab.autotune(False)
+    if n_adv > tune_steps:
+        slab.step(n_adv - tune_steps)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    ne_b, ni_b = slab.counts()
+    if n_adv:
+        adv_ms = a0.elapsed_time(a1)
+        adv["value"] = 0.5 * (ne_a + ni_a + ne_b + ni_b) * n_adv / (adv_ms * 1e-3)
+        adv["ms_per_step"] = adv_ms / n_adv
     for _ in range(args.warmup):
         slab.step(1)
-    slab.autotune(False)
     slab.sync()
     tuned = slab.autotune()
+    dw = slab.diagnostics()
+    window = {"t_fs": [dw["t_fs"], dw["t_fs"] + args.steps * cfg.dt_fs], "Zbar": dw["Zbar"],
+              "charge_states_over_1pct": charge_states(dw["csd"]), "T_e_eV": dw["T_e_eV"],
+              "electrons_per_ion": dw["n_e"] / max(dw["n_i"], 1)}
     ne0, ni0 = slab.counts()
     if dist:
         dist.barrier()
@@ -231,7 +283,8 @@ def run_gpu(args):
     achieved = CELL_BYTES_PER_PARTICLE * n_mean / (cell_ms * 1e-3) / 1e9
     traffic = CELL_TRAFFIC_BYTES_PER_PARTICLE * n_mean if CELL_TRAFFIC_BYTES_PER_PARTICLE else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "traffic_note": "ncu capture at 512x256 cells scaled by particles",
+            "traffic": traffic, "traffic_note": "ncu DRAM bytes of a smaller slab of the same make-up, "
+                                                "scaled by particles (profiles/)",
             "kernel": "k_cell", "peak_source": peak_kind,
             "bytes_per_particle": CELL_BYTES_PER_PARTICLE, "kernel_ms_per_step": cell_ms,
             "share_of_step": tms["cell"] / max(tms["step"], 1e-9)}
@@ -241,10 +294,13 @@ def run_gpu(args):
     slab.close()
     del slab
     torch.cuda.synchronize()
+    torch.cuda.empty_cache()
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(pkg, cfg, tab, pl, st, args, world, n0)
+        e2e = run_e2e(pkg, cfg, tab, pl, st, args, world, n0, (cap_e, cap_i))
     del st
+    torch.cuda.empty_cache()
+    foil = run_foil(pkg, tab, args) if args.foil_steps > 0 and args.workload != "foil" else None
     ensemble = run_ensemble(pkg, tab, args, rank) if args.ensemble > 0 else None
     served = run_served(pkg, tab, args) if args.serve_n > 0 else None
     kedge_scan = run_kedge(pkg, tab, args) if args.kedge_points > 0 else None
@@ -253,21 +309,58 @@ def run_gpu(args):
     if dist:
         dist.barrier()
     if rank == 0:
-        cb = cpu_baseline() if world == 1 and not args.no_cpu else None
+        cb = cpu_baseline(which=args.workload) if world == 1 and not args.no_cpu else None
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "config": {"workload": cfg.name, "cells": [cfg.nx, cfg.ny], "particles": int(n_mean),
-                          "ppc": [cfg.ppc_e, cfg.ppc_i], "pulse_keV": pl.hv_eV / 1e3,
-                          "l2": "state (1.3 GB) larger than L2; no flush", "parallelism": "replicas"},
+                          "particles_start": int(n0), "ppc": [cfg.ppc_e, cfg.ppc_i], "pulse_keV": pl.hv_eV / 1e3,
+                          "pulse_Wcm2": pl.I_peak_Wcm2, "pulse_peak_fs": pl.t_peak_fs,
+                          "l2": f"state ({n_mean * 32 / 1e9:.0f} GB) larger than L2; no flush",
+                          "parallelism": "replicas", "host_generation_s": round(t_gen, 1)},
+               "timed_window": window, "advance": adv,
                "roofline": roof, "step_hbm_gbs": step_gbs, "cpu_baseline": cb, "e2e": e2e,
                "gpu_launches": int(launches), "clocks": clk, "kernel_ms": {k: v / max(nrec, 1) for k, v in tms.items()},
                "autotune": {"cell_warps_per_cta": tuned[0], "cell_ms_1_2_4_8": [float(x) for x in tuned[1]]},
-               "ensemble": ensemble, "served": served, "kedge_scan": kedge_scan, "thermalization": thermal,
-               "extreme_10keV": extreme}
+               "foil_2048x256": foil, "ensemble": ensemble, "served": served, "kedge_scan": kedge_scan,
+               "thermalization": thermal, "extreme_10keV": extreme}
         print(json.dumps(out))
     if dist:
         dist.destroy_process_group()
+
+
+def run_foil(pkg, tab, args):
+    """The 2D foil (2048 x 256 cells of 5 nm, 64 e + 16 i per cell, 1.6 keV /
+    1e17 W/cm^2), timed the same way from its first steps (autotuning,
+    warm-up, then --foil-steps steps)."""
+    import torch
+    cfg, pl = workload(None, "foil")
+    st = P.init_particles(cfg)
+    slab = pkg.Slab(cfg, tab, pl)
+    slab.load(st)
+    del st
+    stream = torch.cuda.current_stream()
+    slab.autotune(True)
+    slab.step(9)
+    slab.autotune(False)
+    slab.step(max(args.warmup, 3))
+    slab.sync()
+    ne0, ni0 = slab.counts()
+    slab.timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    slab.step(args.foil_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    tms, nrec = slab.timing(None)
+    ne1, ni1 = slab.counts()
+    slab.close()
+    n_mean = 0.5 * (ne0 + ni0 + ne1 + ni1)
+    return {"workload": cfg.name, "particles": int(n_mean), "steps": args.foil_steps,
+            "value": n_mean * args.foil_steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / args.foil_steps,
+            "kernel_ms": {k: v / max(nrec, 1) for k, v in tms.items()}}
 
 
 def run_ensemble(pkg, tab, args, rank):
@@ -385,13 +478,13 @@ def run_extreme(pkg, tab, args):
     return r
 
 
-def run_e2e(pkg, cfg, tab, pl, st, args, world, n0):
+def run_e2e(pkg, cfg, tab, pl, st, args, world, n0, caps):
     """Public API with host buffers: context, H2D load, steps with a D2H
-    diagnostics read after each; 100 steps (2 fs) of the foil's 2000, so
-    that the one-time set-up weighs as it would in a run."""
+    diagnostics read after each; 100 steps (2 fs), so that the one-time
+    set-up weighs as it would in a run."""
     e2e_steps = 100
     t0 = time.perf_counter()
-    s2 = pkg.Slab(cfg, tab, pl)
+    s2 = pkg.Slab(cfg, tab, pl, cap_e=caps[0], cap_i=caps[1])
     s2.load(st)
     d2h = 0
     for _ in range(e2e_steps):
@@ -415,7 +508,12 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cells", type=int, nargs=2, default=None, help="smaller foil (profiling)")
+    ap.add_argument("--workload", default="large", choices=["large", "foil"],
+                    help="timed slab: the large 2D slab (8192 x 1024) or the 2D foil (2048 x 256)")
+    ap.add_argument("--cells", type=int, nargs=2, default=None, help="smaller slab of the same make-up (profiling)")
+    ap.add_argument("--advance-fs", type=float, default=10.0,
+                    help="simulated time run before the timed steps, outside the clock")
+    ap.add_argument("--foil-steps", type=int, default=20, help="timed steps of the 2D foil leg (0: skip)")
     ap.add_argument("--ensemble", type=int, default=256, help="slabs of the batched ensemble (0: skip)")
     ap.add_argument("--serve-n", type=int, default=40, help="requests of the served trace (0: skip)")
     ap.add_argument("--serve-horizon-fs", type=float, default=150.0,

@@ -121,6 +121,11 @@ def lib():
             L.orc_rho.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, _D]
             L.orc_eos.restype = C.c_double
             L.orc_eos.argtypes = [C.POINTER(Tables), C.c_double, C.c_double]
+            L.orc_trace.argtypes = [C.c_void_p, C.c_double]
+            L.orc_trace_count.restype = C.c_int
+            L.orc_trace_count.argtypes = [C.c_void_p]
+            L.orc_trace_decisions.argtypes = [C.c_void_p, _U64]
+            L.orc_trace_get.argtypes = [C.c_void_p, C.c_void_p]
             _lib = L
     return _lib
 
@@ -156,6 +161,16 @@ def make_tables(tab: dict):
 
 
 M_AL_ME = 26.9815385 * 1822.888486
+
+# one record of the decision trace (orc_near)
+NEAR_DTYPE = np.dtype([("step", np.uint32), ("cell", np.int32), ("kind", np.int32), ("species", np.int32),
+                       ("id", np.uint64), ("x", np.float64), ("thr", np.float64)])
+NEAR_KINDS = {1: "COLL_ACC", 2: "ION_DRAW", 3: "ION_PAY", 4: "REC_K", 5: "REC_CAP", 6: "PH_EDGE",
+              7: "PH_DRAW", 8: "PH_BIN", 9: "PH_PART", 10: "PH_ZF", 11: "DECAY", 12: "BRANCH",
+              13: "REC_TAKE", 14: "EBULK"}
+# relative distance from a threshold within which an FP32 evaluation of a
+# decision may differ from the FP64 one (a threshold flip)
+FLIP_REL = 2.0 ** -20
 
 
 class OracleSlab:
@@ -269,6 +284,23 @@ class OracleSlab:
         c = np.zeros(len(C_NAMES), dtype=np.uint64)
         self.L.orc_tallies(self.h, _p(t), _p(c, C.c_uint64))
         return dict(zip(T_NAMES, t)), dict(zip(C_NAMES, (int(x) for x in c)))
+
+    def trace(self, rel=FLIP_REL):
+        """Start the decision trace (rel <= 0 stops it): every threshold
+        decision of the following steps is counted, and recorded when it
+        lies within rel (relative) of its threshold."""
+        self.L.orc_trace(self.h, rel)
+
+    def near(self):
+        """Recorded near-threshold decisions (NEAR_DTYPE records) and the
+        counts of Monte-Carlo draws and of other decisions."""
+        n = self.L.orc_trace_count(self.h)
+        out = np.zeros(n, dtype=NEAR_DTYPE)
+        if n:
+            self.L.orc_trace_get(self.h, out.ctypes.data_as(C.c_void_p))
+        d = np.zeros(2, dtype=np.uint64)
+        self.L.orc_trace_decisions(self.h, _p(d, C.c_uint64))
+        return out, int(d[0]), int(d[1])
 
     def diag(self, n_E=64, E_max=1e4):
         csd = np.zeros(NZ)

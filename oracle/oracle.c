@@ -503,6 +503,9 @@ struct orc_slab {
     uint32_t step;
     double tally[ORC_NT];
     uint64_t cnt[ORC_NC];
+    double trace_rel;           /* > 0: decision trace on */
+    orc_near *near; int nnear, capnear;
+    uint64_t ndraw, ndec;
 };
 
 static double *dupd(const double *a, size_t n)
@@ -535,6 +538,7 @@ void orc_destroy(orc_slab *s)
     if (!s) return;
     free(s->hv_tab); free(s->sigma); free(s->eos_T); free(s->eos_n); free(s->eos_Z);
     free(s->hv_b); free(s->sig_b); free(s->e); free(s->ion); free(s->f); free(s->j); free(s->ph);
+    free(s->near);
     free(s);
 }
 
@@ -725,7 +729,27 @@ typedef struct {
     newe *ne; int n, cap;
     double tally_ion, ka_esc;
     uint64_t cnt[ORC_NC];
+    /* decision trace of the cell (see orc_trace) */
+    double rel; uint32_t step; int cell;
+    orc_near *nr; int nn, ncap;
+    uint64_t ndraw, ndec;
 } cellout;
+
+/* a decision x < thr (or x > thr): counted; recorded when within rel of
+ * the threshold.  draw != 0 for Monte-Carlo draws. */
+static void decide(cellout *o, int draw, int kind, int species, uint64_t id, double x, double thr)
+{
+    if (!(o->rel > 0.0)) return;
+    if (draw) o->ndraw++; else o->ndec++;
+    if (!(fabs(x - thr) <= o->rel * fabs(thr))) return;
+    if (o->nn == o->ncap) {
+        o->ncap = o->ncap ? 2 * o->ncap : 8;
+        o->nr = realloc(o->nr, sizeof(orc_near) * o->ncap);
+    }
+    orc_near *q = &o->nr[o->nn++];
+    q->step = o->step; q->cell = o->cell; q->kind = kind; q->species = species; q->id = id;
+    q->x = x; q->thr = thr;
+}
 
 static void push_new(cellout *o, double X, double Y, const double u[3], double w, uint64_t id)
 {
@@ -849,6 +873,7 @@ static void cell_physics(orc_slab *S, int cell, int *eidx, int ne, int *iidx, in
         elec *e = &S->e[pe[k]];
         double ke = kin(e->u, 1.0);
         We += e->w;
+        if (p->E_bulk > 0.0) decide(o, 0, ORC_N_EBULK, 0, e->id, ke, p->E_bulk);
         if (p->E_bulk <= 0.0 || ke < p->E_bulk) { Wb += e->w; Kb += e->w * ke; }
     }
     for (int k = 0; k < ni; ++k) Q += S->ion[pi[k]].Z + S->ion[pi[k]].zf;
@@ -876,6 +901,10 @@ static void cell_physics(orc_slab *S, int cell, int *eidx, int ne, int *iidx, in
             elec *a = &S->e[pe[pa[k]]], *b = &S->e[pe[pb[k]]];
             double r[4];
             draw4(seed, a->id, step, PU_COLL_EE, r);
+            if (a->w != b->w) {
+                double wm = a->w > b->w ? a->w : b->w;
+                decide(o, 1, ORC_N_COLL_ACC, 0, a->id, r[3], (a->w < wm ? a->w : b->w) / wm);
+            }
             o->cnt[ORC_C_EE] += orc_collide(a->u, b->u, 1.0, 1.0, -1.0, -1.0, a->w, b->w,
                                             n_e, lnL, p->dt * fr[k], r);
         }
@@ -898,6 +927,10 @@ static void cell_physics(orc_slab *S, int cell, int *eidx, int ne, int *iidx, in
                 b = &S->ion[pi[k]]; a = &S->e[pe[k % ne]];
                 draw4(seed, b->id, step, PU_COLL_IE, r);
                 npair = n_e * (a->w > wi ? a->w : wi) / a->w;
+            }
+            if (a->w != wi) {
+                double wm = a->w > wi ? a->w : wi;
+                decide(o, 1, ORC_N_COLL_ACC, 0, a->id, r[3], (a->w < wm ? a->w : wi) / wm);
             }
             o->cnt[ORC_C_EI] += orc_collide(a->u, b->u, 1.0, p->m_ion, -1.0, b->Z + b->zf,
                                             a->w, wi, npair, lnL, p->dt, r);
@@ -945,8 +978,10 @@ static void cell_physics(orc_slab *S, int cell, int *eidx, int ne, int *iidx, in
             if (q->Z >= 13) continue;
             double r[4];
             draw4(seed, q->id, step, PU_ION, r);
+            decide(o, 1, ORC_N_ION_DRAW, 1, q->id, r[0], Pz[q->Z]);
             if (!(r[0] < Pz[q->Z])) continue;
             double I = ion_energy(t, q->Z, q->nK, dE);
+            if (!stop) decide(o, 0, ORC_N_ION_PAY, -1, 0, paid + wi * I, Kt);
             if (stop || paid + wi * I > Kt) { stop = 1; o->cnt[ORC_C_ION_REJ]++; continue; }
             paid += wi * I;
             int s = outermost(13 - q->Z, q->nK);
@@ -981,7 +1016,11 @@ static void cell_physics(orc_slab *S, int cell, int *eidx, int ne, int *iidx, in
         double Te2 = Wb2 > 0 ? (2.0 / 3.0) * Kb2 / Wb2 : 0.0;
         double zeos = orc_eos(t, n_i, Te2);
         int Kev = 0;
-        if (zb > zeos) Kev = (int)floor((zb - zeos) * ni + 0.5);
+        if (zb > zeos) {
+            const double xk = (zb - zeos) * ni + 0.5;
+            decide(o, 0, ORC_N_REC_K, -1, 0, xk, floor(xk + 0.5));
+            Kev = (int)floor(xk);
+        }
         /* events are dealt round-robin over the ions in canonical order; an
          * ion can take several in one step (no limit on the instantaneous
          * rate), at most as many as its charge */
@@ -989,6 +1028,7 @@ static void cell_physics(orc_slab *S, int cell, int *eidx, int ne, int *iidx, in
         for (int k = 0; k < ni; ++k) elig += S->ion[pi[k]].Z;
         if (Kev > elig) Kev = elig;
         int wcap = (int)floor(Wex / wi + 1e-9);
+        if (Kev >= wcap) decide(o, 0, ORC_N_REC_CAP, -1, 0, Wex / wi, floor(Wex / wi + 0.5));
         if (Kev > wcap) Kev = wcap;
         if (Kev > 0) {
             int *nrec = calloc(ni, sizeof(int));
@@ -1004,6 +1044,7 @@ static void cell_physics(orc_slab *S, int cell, int *eidx, int ne, int *iidx, in
             for (int k = 0; k < ne; ++k) {
                 elec *e = &S->e[pe[k]];
                 double tk = Wrem - before;
+                decide(o, 0, ORC_N_REC_TAKE, -1, 0, before + e->w, Wrem);
                 if (tk > e->w) tk = e->w;
                 if (tk < 0.0) tk = 0.0;
                 take[k] = tk;
@@ -1064,9 +1105,12 @@ static void cell_physics(orc_slab *S, int cell, int *eidx, int ne, int *iidx, in
                     if (!occ[q2]) continue;
                     double ed = lowered(t, q->Z, q2, dE[q->Z]);
                     double acc = 0.0;
-                    for (int b = 0; b < nb; ++b)
+                    for (int b = 0; b < nb; ++b) {
+                        decide(o, 0, ORC_N_PH_EDGE, 1, q->id, S->hv_b[b], ed);
                         if (S->hv_b[b] > ed) acc += n0[b] * S->sig_b[q2 * nb + b];
+                    }
                     double P = cph * occ[q2] * acc;
+                    if (P > 0.0) decide(o, 1, ORC_N_PH_DRAW, 1, q->id, rs[q2], P);
                     if (rs[q2] < P) { sub = q2; Ps = P; edge = ed; break; }
                 }
                 if (sub < 0) continue;
@@ -1076,10 +1120,12 @@ static void cell_physics(orc_slab *S, int cell, int *eidx, int ne, int *iidx, in
                     double c = (S->hv_b[b] > edge) ? cph * occ[sub] * n0[b] * S->sig_b[sub * nb + b] : 0.0;
                     if (c > 0.0) lastpos = b;
                     cum += c;
+                    if (c > 0.0) decide(o, 0, ORC_N_PH_BIN, 1, q->id, cum, target);
                     if (cum > target) { bin = b; break; }
                 }
                 if (bin < 0) bin = lastpos;
                 if (bin < 0) continue;
+                decide(o, 0, ORC_N_PH_PART, -1, 0, ph[bin], wi);
                 double g = ph[bin] < wi ? ph[bin] : wi;
                 if (g <= 0.0) continue;
                 ph[bin] -= g;
@@ -1088,6 +1134,7 @@ static void cell_physics(orc_slab *S, int cell, int *eidx, int ne, int *iidx, in
                 } else {
                     q->zf += g / wi;
                     o->cnt[ORC_C_PART]++;
+                    decide(o, 0, ORC_N_PH_ZF, 1, q->id, q->zf, 1.0);
                     if (q->zf >= 1.0) {
                         q->zf -= 1.0;
                         int so = outermost(13 - q->Z, q->nK);
@@ -1112,9 +1159,11 @@ static void cell_physics(orc_slab *S, int cell, int *eidx, int ne, int *iidx, in
                 if (tau <= 0.0) continue;
                 double r[4];
                 draw4(seed, q->id, step, PU_DECAY, r);
+                decide(o, 1, ORC_N_DECAY, 1, q->id, r[0], dtr / tau);
                 if (!(r[0] < dtr / tau)) continue;
                 double om = t->omegaK[nbd][q->nK - 1];
                 int nl = occ[1] + occ[2];
+                decide(o, 1, ORC_N_BRANCH, 1, q->id, r[1], 1.0 - om);
                 if (r[1] < 1.0 - om) {
                     if (nl < 2) continue;
                     double e2s = lowered(t, q->Z, 1, dE[q->Z]), e2p = lowered(t, q->Z, 2, dE[q->Z]);
@@ -1361,6 +1410,7 @@ void orc_step(orc_slab *s, int nsteps, int nthreads)
             free(fe); free(fi);
         }
         cellout *co = calloc(ncell, sizeof(cellout));
+        for (int c = 0; c < ncell; ++c) { co[c].rel = s->trace_rel; co[c].step = s->step; co[c].cell = c; }
 #pragma omp parallel for schedule(dynamic, 16)
         for (int c = 0; c < ncell; ++c)
             cell_physics(s, c, oe + cse[c], cse[c + 1] - cse[c], oi + csi[c], csi[c + 1] - csi[c], &co[c]);
@@ -1379,6 +1429,16 @@ void orc_step(orc_slab *s, int nsteps, int nthreads)
             s->tally[ORC_T_ION] += co[c].tally_ion;
             s->tally[ORC_T_KA_ESC] += co[c].ka_esc;
             for (int q = 0; q < ORC_NC; ++q) s->cnt[q] += co[c].cnt[q];
+            s->ndraw += co[c].ndraw;
+            s->ndec += co[c].ndec;
+            for (int k = 0; k < co[c].nn; ++k) {
+                if (s->nnear == s->capnear) {
+                    s->capnear = s->capnear ? 2 * s->capnear : 64;
+                    s->near = realloc(s->near, sizeof(orc_near) * s->capnear);
+                }
+                s->near[s->nnear++] = co[c].nr[k];
+            }
+            free(co[c].nr);
             free(co[c].ne);
         }
         (void)ne_old;
@@ -1437,6 +1497,20 @@ void orc_tallies(orc_slab *s, double *t, uint64_t *c)
     for (int q = 0; q < ORC_NT; ++q) t[q] = s->tally[q];
     t[ORC_T_KE_E] = kee; t[ORC_T_KE_I] = kei; t[ORC_T_PHOT] = ph; t[ORC_T_FIELD] = fe;
     for (int q = 0; q < ORC_NC; ++q) c[q] = s->cnt[q];
+}
+
+/* ---------------- decision trace ---------------- */
+void orc_trace(orc_slab *s, double rel)
+{
+    s->trace_rel = rel;
+    s->nnear = 0;
+    s->ndraw = s->ndec = 0;
+}
+int orc_trace_count(const orc_slab *s) { return s->nnear; }
+void orc_trace_decisions(const orc_slab *s, uint64_t out[2]) { out[0] = s->ndraw; out[1] = s->ndec; }
+void orc_trace_get(const orc_slab *s, orc_near *out)
+{
+    if (s->nnear) memcpy(out, s->near, sizeof(orc_near) * s->nnear);
 }
 
 /* charge-state distribution (fractional charges split between Z and Z+1)

@@ -65,6 +65,34 @@ enum { ORC_C_ION, ORC_C_ION_REJ, ORC_C_REC, ORC_C_PH0, ORC_C_PH1, ORC_C_PH2,
 
 typedef struct orc_slab orc_slab;
 
+/* Decision trace (for classifying FP32-against-FP64 mismatches): every
+ * comparison of a number x with a threshold thr that decides an integer
+ * outcome of the step (r < P of a Monte-Carlo draw, a rounding of an event
+ * count, an energy or photon budget, an edge) is counted, and recorded when
+ * |x - thr| <= rel * |thr|.  Recording changes nothing in the step. */
+enum { ORC_N_COLL_ACC = 1,   /* weighted acceptance r < w_other / w_max (particle) */
+       ORC_N_ION_DRAW = 2,   /* impact ionization r < P_z (ion) */
+       ORC_N_ION_PAY = 3,    /* payment budget: paid + w I > K (cell) */
+       ORC_N_REC_K = 4,      /* recombination count rounding (cell) */
+       ORC_N_REC_CAP = 5,    /* recombination electron-weight cap (cell) */
+       ORC_N_PH_EDGE = 6,    /* photon energy against a lowered edge (ion) */
+       ORC_N_PH_DRAW = 7,    /* photoionization r < P_s (ion) */
+       ORC_N_PH_BIN = 8,     /* bin choice: cumulative > r P_s (ion) */
+       ORC_N_PH_PART = 9,    /* photons left in the bin < w_i (cell) */
+       ORC_N_PH_ZF = 10,     /* fractional charge reaching 1 (ion) */
+       ORC_N_DECAY = 11,     /* K-vacancy decay r < dt_rad / tau (ion) */
+       ORC_N_BRANCH = 12,    /* Auger / K-alpha branch r < 1 - omega (ion) */
+       ORC_N_REC_TAKE = 13,  /* recombination weight reaching an electron's whole weight (cell) */
+       ORC_N_EBULK = 14 };   /* kinetic energy against E_bulk (electron) */
+typedef struct {
+    uint32_t step;
+    int32_t cell;        /* cell of the slab */
+    int32_t kind;        /* ORC_N_* */
+    int32_t species;     /* 0 electron, 1 ion, -1 the cell as a whole */
+    uint64_t id;         /* particle id (0 for the cell) */
+    double x, thr;
+} orc_near;
+
 orc_slab *orc_create(const orc_params *p, const orc_tables *t);
 void orc_destroy(orc_slab *s);
 void orc_set_pulse(orc_slab *s, const orc_pulse *pl);
@@ -89,6 +117,14 @@ void orc_get_photons(const orc_slab *s, double *ph);
 void orc_step(orc_slab *s, int nsteps, int nthreads);
 void orc_tallies(orc_slab *s, double *t, uint64_t *c);
 void orc_diag(const orc_slab *s, double *csd, int n_E, double E_max, double *eedf);
+/* decision trace: rel <= 0 switches it off (the default); records of
+ * earlier steps are kept until orc_trace is called again */
+void orc_trace(orc_slab *s, double rel);
+int orc_trace_count(const orc_slab *s);
+/* decisions counted since orc_trace: [0] Monte-Carlo draws (r < P),
+ * [1] every other threshold decision */
+void orc_trace_decisions(const orc_slab *s, uint64_t out[2]);
+void orc_trace_get(const orc_slab *s, orc_near *out);
 
 /* building blocks exposed for the closed-form and invariant pins */
 void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

@@ -74,3 +74,163 @@ def select_cells(cfg, e, i, cells):
     se = keep[_cells_of(cfg, e["X"], e["Y"])]
     si = keep[_cells_of(cfg, i["X"], i["Y"])]
     return {k: v[se] for k, v in e.items()}, {k: v[si] for k, v in i.items()}
+
+
+# ---- classification of mismatches as threshold flips ----
+
+def _cell_of_ids(cfg, X, Y):
+    return (np.floor(Y).astype(np.int64) * cfg.nx + np.floor(X).astype(np.int64)) if cfg.ny > 1 \
+        else np.floor(X).astype(np.int64)
+
+
+def classify(cfg, st, g_e, o_e, g_i, o_i, near, n_draw, n_dec):
+    """Every difference between the device's state after one step and the
+    oracle's, classified against the oracle's decision trace of that step.
+
+    A decision that lies within 2^-20 of its threshold (|x - thr| <= 2^-20
+    |thr|, the survey's definition of a threshold flip) may go the other
+    way in FP32; its consequences stay inside its cell but spread there (the
+    impact-ionization payment and the collision energy restore scale every
+    electron of the cell, an extra or missing ionization moves the
+    recombination count, photons taken from a bin change what later ions
+    see).  So a difference is explained when the cell its particle sat in at
+    the start of the step holds a near-threshold decision, and the flips
+    counted are the near decisions of the cells that differ.  st is the
+    state both sides started from (positions name the cells).
+    Returns a dict: draws, decisions, near, flip_cells, flips, unexplained
+    (a list of descriptions; empty when every difference is a flip)."""
+    ecell = dict(zip(st.eid.tolist(), _cell_of_ids(cfg, st.eX, st.eY).tolist()))
+    icell = dict(zip(st.iid.astype(np.uint64).tolist(), _cell_of_ids(cfg, st.iX, st.iY).tolist()))
+
+    def cell_of_e(eid):
+        eid = int(eid)
+        if eid in ecell:
+            return ecell[eid]
+        return icell.get(eid & 0xffffffff, -1)         # created: at its parent ion
+
+    near_cells = {}
+    for r in near:
+        near_cells.setdefault(int(r["cell"]), []).append(r)
+    unexplained, diff_cells = [], set()
+
+    def note(what, cell):
+        if cell in near_cells:
+            diff_cells.add(cell)
+        else:
+            unexplained.append(f"{what} (cell {cell})")
+
+    ge_ids, oe_ids = set(g_e["id"].tolist()), set(o_e["id"].tolist())
+    for eid in ge_ids ^ oe_ids:
+        note(f"electron {eid} on one side only", cell_of_e(eid))
+    gi_ids, oi_ids = set(g_i["id"].tolist()), set(o_i["id"].tolist())
+    for iid in gi_ids ^ oi_ids:
+        note(f"ion {iid} on one side only", icell.get(int(iid), -1))
+    # common electrons: momentum and weight
+    ce = np.array(sorted(ge_ids & oe_ids), dtype=np.uint64)
+    if ce.size:
+        ga, oa = np.argsort(g_e["id"]), np.argsort(o_e["id"])
+        gk = ga[np.searchsorted(g_e["id"][ga], ce)]
+        ok = oa[np.searchsorted(o_e["id"][oa], ce)]
+        err = momentum_errors(g_e["u"][gk], o_e["u"][ok])
+        wg, wo = g_e["w"][gk].astype(np.float64), o_e["w"][ok]
+        werr = np.abs(wg - wo) / np.maximum(np.abs(wo), 1e-30)
+        for k in np.nonzero((err > U_RTOL) | (werr > U_RTOL))[0]:
+            note(f"electron {int(ce[k])} momentum {err[k]:.2e} weight {werr[k]:.2e}", cell_of_e(ce[k]))
+    ci = np.array(sorted(gi_ids & oi_ids), dtype=np.uint64)
+    if ci.size:
+        ga, oa = np.argsort(g_i["id"]), np.argsort(o_i["id"])
+        gk = ga[np.searchsorted(g_i["id"][ga].astype(np.uint64), ci)]
+        ok = oa[np.searchsorted(o_i["id"][oa].astype(np.uint64), ci)]
+        err = momentum_errors(g_i["u"][gk], o_i["u"][ok])
+        bad = (g_i["Z"][gk] != o_i["Z"][ok]) | (g_i["nK"][gk] != o_i["nK"][ok]) | \
+              (np.abs(g_i["zf"][gk].astype(np.float64) - o_i["zf"][ok]) > U_RTOL) | (err > U_RTOL)
+        for k in np.nonzero(bad)[0]:
+            note(f"ion {int(ci[k])} Z {g_i['Z'][gk[k]]}/{o_i['Z'][ok[k]]} nK {g_i['nK'][gk[k]]}/{o_i['nK'][ok[k]]} "
+                 f"momentum {err[k]:.2e}", icell.get(int(ci[k]), -1))
+    flips = sum(len(near_cells[c]) for c in diff_cells)
+    return {"draws": n_draw, "decisions": n_dec, "near": len(near), "flip_cells": sorted(diff_cells),
+            "flips": flips, "unexplained": unexplained}
+
+
+def flip_summary(cls):
+    return (f"flips: {cls['flips']} of {cls['draws']} draws ({cls['decisions']} other decisions), "
+            f"{cls['near']} near-threshold decisions, cells with differences {cls['flip_cells'][:8]}")
+
+
+# the north star's bound on threshold flips: fewer than 1e-5 of the draws
+FLIP_SHARE = 1e-5
+
+
+def assert_flip_parity(cfg, st, g_e, g_i, o, counts=None, o_counts=None, keys=()):
+    """One step of both sides from the same state `st`, the oracle run with
+    its decision trace on (OracleSlab.trace before the step): every
+    difference must be a threshold flip, and flips must stay below 1e-5 of
+    the step's Monte-Carlo draws.  With the device's and the oracle's event
+    counters given, the counts of `keys` must be equal, or differ by no more
+    than the ions of the cells that flipped.  Returns the classification."""
+    near, n_draw, n_dec = o.near()
+    o_e, o_i = o.electrons(), o.ions()
+    cls = classify(cfg, st, g_e, o_e, g_i, o_i, near, n_draw, n_dec)
+    print("\n" + flip_summary(cls))
+    assert not cls["unexplained"], (flip_summary(cls), cls["unexplained"][:20])
+    assert cls["flips"] <= FLIP_SHARE * cls["draws"], flip_summary(cls)
+    if counts is not None:
+        ci = _cell_of_ids(cfg, st.iX, st.iY)
+        slack = int(np.isin(ci, np.array(cls["flip_cells"], dtype=np.int64)).sum())
+        for k in keys:
+            assert abs(int(counts[k]) - int(o_counts[k])) <= slack, (k, counts[k], o_counts[k], flip_summary(cls))
+    return cls
+
+
+# ---- multi-step runs against the oracle's own spread ----
+
+# |device - mean| <= SPREAD_K sd sqrt(1 + 1/n) + floor, with mean and sd of n
+# oracle realizations: 4.0 is about the 99.5 % two-sided quantile of
+# Student's t with 7 degrees of freedom (n = 8), so a device run that is one
+# more realization of the method fails a given diagnostic by chance about
+# once in 200
+SPREAD_K = 4.0
+
+
+def oracle_spread(case):
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_spread.json")
+    return json.load(open(path))[case]
+
+
+def spread_violations(case, values, floors=None, default_floor=0.0):
+    """Diagnostics of a device run (dict name -> value) outside the spread
+    of the oracle's realizations of `case` (tests/golden/oracle_spread.json);
+    floors: absolute floor per name (default_floor otherwise).  Returns
+    {name: (value, mean, bound)} of the violations and prints the table."""
+    g = oracle_spread(case)["diagnostics"]
+    floors = floors or {}
+    bad = {}
+    print(f"\n{case}: diagnostic, device, oracle mean, oracle sd, |z|")
+    for name, v in values.items():
+        d = g[name]
+        n = len(d["values"])
+        scale = d["sd"] * (1.0 + 1.0 / n) ** 0.5
+        bound = SPREAD_K * scale + floors.get(name, default_floor)
+        z = abs(v - d["mean"]) / scale if scale > 0 else float("inf") if v != d["mean"] else 0.0
+        print(f"  {name:14s} {v:14.6g} {d['mean']:14.6g} {d['sd']:11.3g} {z:7.2f}")
+        if abs(v - d["mean"]) > bound:
+            bad[name] = (v, d["mean"], bound)
+    return bad
+
+
+def spread_hist_l1(case, prefix, hist):
+    """L1 distance of a device histogram (csd_* or eedf_* bins of `case`)
+    from the mean of the oracle's realizations, and the bound it must stay
+    within: 1.5 times the largest distance of one realization from the mean
+    of the other seven (the realizations' own scatter).  Returns (d, bound)."""
+    g = oracle_spread(case)["diagnostics"]
+    names = sorted((k for k in g if k.startswith(prefix + "_")), key=lambda k: int(k.split("_")[1]))
+    V = np.array([g[k]["values"] for k in names])          # bins x realizations
+    mean = V.mean(axis=1)
+    n = V.shape[1]
+    loo = [np.abs(V[:, j] - (V.sum(axis=1) - V[:, j]) / (n - 1)).sum() for j in range(n)]
+    d = float(np.abs(np.asarray(hist, dtype=np.float64)[:len(names)] - mean).sum())
+    print(f"  {prefix} L1 from the oracle mean {d:.3e}; realizations' own {min(loo):.3e} .. {max(loo):.3e}")
+    return d, 1.5 * max(loo)

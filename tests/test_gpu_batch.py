@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import pic_inputs as P
-from parity_util import compare_state
+from parity_util import assert_flip_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -157,11 +157,9 @@ def test_batch_slot_against_oracle():
     bt.step(1)
     o = oracle.OracleSlab(a, P.standin_tables(), pa)
     o.load(sa)
+    o.trace()
     o.step(1)
-    res = compare_state(bt.electrons(k), o.electrons(), bt.ions(k), o.ions(), a.nx, a.ny)
-    n_e = sa.n_e
-    assert res["e_same_ids"] and res["i_same_ids"], res
-    assert res["Z_mismatch"] <= max(1, int(1e-3 * n_e)), res
-    assert res["e_bad"] <= max(2, int(1e-3 * n_e)), res
-    assert res["i_bad"] <= max(2, int(1e-3 * n_e)), res
+    _, co = o.tallies()
+    assert_flip_parity(a, sa, bt.electrons(k), bt.ions(k), o, bt.diagnostics(k)["counts"], co,
+                       ("ION", "ION_REJ", "REC", "PH0", "PART", "AUG", "KA", "EE", "EI"))
     bt.close()

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import pic_inputs as P
-from parity_util import compare_state
+from parity_util import assert_flip_parity, compare_state
 
 pytestmark = pytest.mark.gpu
 
@@ -71,10 +71,9 @@ def test_smallest_grids(tables):
         g.step(1)
         o = oracle.OracleSlab(cfg, tables)
         o.load(st)
+        o.trace()
         o.step(1)
-        res = compare_state(g.electrons(), o.electrons(), g.ions(), o.ions(), cfg.nx, cfg.ny)
-        assert res["e_same_ids"] and res["i_same_ids"], (nx, ny, res)
-        assert res["e_bad"] <= 2 and res["Z_mismatch"] == 0, (nx, ny, res)
+        assert_flip_parity(cfg, st, g.electrons(), g.ions(), o)
         g.close()
 
 

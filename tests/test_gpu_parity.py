@@ -2,9 +2,11 @@
 
 Same seeded inputs on both sides; particles are matched by id.  Tolerances:
 per-particle momenta within 1e-5 relative (FP32 state against FP64),
-charge states, K vacancies and created-particle ids exact, except for
-threshold flips (a decision r < P taken differently because P differs in
-the last FP32 bits), which are counted and bounded.
+charge states, K vacancies, weights, created-particle ids and event counts
+exact, except for threshold flips: a decision that the oracle takes within
+2^-20 of its threshold (its decision trace records them) may go the other
+way in FP32, and only the cells holding such a decision may differ; flips
+must stay below 1e-5 of the step's Monte-Carlo draws.
 """
 import os
 import subprocess
@@ -13,7 +15,8 @@ import numpy as np
 import pytest
 
 import pic_inputs as P
-from parity_util import compare_state, match, momentum_errors, sampled_cell_state, select_cells, U_RTOL
+from parity_util import (assert_flip_parity, compare_state, match, momentum_errors, oracle_spread,
+                         sampled_cell_state, select_cells, spread_hist_l1, spread_violations, U_RTOL)
 
 pytestmark = pytest.mark.gpu
 
@@ -38,6 +41,7 @@ def _run_both(cfg, tables, st, nsteps, pulse=None, photons=None, fields=None, st
     g.load(st)
     o = oracle.OracleSlab(cfg, tables, pulse)
     o.load(st)
+    o.trace()
     if photons is not None:
         g.set_photons(photons)
         o.set_photons(photons)
@@ -50,13 +54,12 @@ def _run_both(cfg, tables, st, nsteps, pulse=None, photons=None, fields=None, st
     return g, o
 
 
-def _assert_parity(res, n_e, max_bad_frac=1e-3):
-    assert res["e_same_ids"], res
-    assert res["i_same_ids"], res
-    assert res["Z_mismatch"] <= max(1, int(1e-3 * n_e)), res
-    assert res["nK_mismatch"] <= max(1, int(1e-3 * n_e)), res
-    assert res["e_bad"] <= max(2, int(max_bad_frac * n_e)), res
-    assert res["i_bad"] <= max(2, int(max_bad_frac * n_e)), res
+def _assert_parity(cfg, st, g, o, keys=("ION", "ION_REJ", "REC", "PH0", "PH1", "PH2", "PH3", "PH4", "PART",
+                                         "AUG", "KA", "EE", "EI")):
+    """One step's parity: every difference a threshold flip (see
+    parity_util.classify), event counts equal up to the flipped cells."""
+    _, co = o.tallies()
+    return assert_flip_parity(cfg, st, g.electrons(), g.ions(), o, g.diagnostics()["counts"], co, keys)
 
 
 def test_philox_device_equals_oracle():
@@ -92,9 +95,7 @@ def test_single_step_1d(tables):
     cfg = P.cfg_small_1d(nx=48)
     st = P.init_particles(cfg)
     g, o = _run_both(cfg, tables, st, 1)
-    res = compare_state(g.electrons(), o.electrons(), g.ions(), o.ions(), cfg.nx, cfg.ny)
-    _assert_parity(res, st.n_e)
-    assert res["e_err_p999"] < U_RTOL, res
+    _assert_parity(cfg, st, g, o)
 
 
 def _busy(cfg, seed=5):
@@ -117,12 +118,8 @@ def test_single_step_every_process(tables, ny):
     ph[:, cfg.nx // 2:, :] = 0.3 * cfg.w_ion
     f = P.random_fields(cfg, 3, e_amp=2e-3, b_amp=2e-3)
     g, o = _run_both(cfg, tab, st, 1, pulse=pl, photons=ph, fields=f)
-    res = compare_state(g.electrons(), o.electrons(), g.ions(), o.ions(), cfg.nx, cfg.ny)
-    _assert_parity(res, st.n_e)
-    dg = g.diagnostics()
+    _assert_parity(cfg, st, g, o)
     _, co = o.tallies()
-    for k in ("ION", "REC", "PH0", "PH2", "PART", "AUG", "KA"):
-        assert abs(dg["counts"][k] - co[k]) <= max(1, int(1e-3 * co[k])), (k, dg["counts"][k], co[k])
     assert co["ION"] > 0 and co["REC"] > 0 and co["PH0"] > 0 and co["AUG"] > 0 and co["PART"] > 0
     # photon field, fields and current of the step
     # photon numbers: FP64-grade sums of FP32 event weights (6e-8 relative)
@@ -236,36 +233,34 @@ def test_full_step_energy_drift_matches_oracle(tables):
     small 1D slab is not conserved by the explicit PIC step: it dips (field
     energy radiated through the absorbing boundaries is not tallied) and
     then rises through the residual numerical heating of cells ~50 Debye
-    lengths wide (-0.7 % after 200 steps, +0.3 % after 500 with the
-    smoothed current).  That drift belongs to the scheme, so the device's
-    drift curve follows the oracle's: within 0.3 % of the initial energy at
-    every 100 steps.  The residual heating is driven by particle noise, so
-    the two decorrelating runs differ like two realizations (measured 0.15 %
-    apart at most; two oracle seeds 0.07 % apart at the end)."""
+    lengths wide.  That drift belongs to the scheme, so the device's drift
+    curve (every 100 steps) must lie within the spread of the oracle's own
+    realizations of it (eight Philox keys from the same initial state,
+    tests/golden/oracle_spread.json), with a floor of 1e-4 of the initial
+    energy; the oracle's drift itself stays below 2 %."""
     cfg = P.cfg_small_1d()
     st = P.init_particles(cfg)
     g = pkg.Slab(cfg, tables)
     g.load(st)
-    o = oracle.OracleSlab(cfg, tables)
-    o.load(st)
 
     def tot_g(d):
         return sum(d[k] for k in ("ke_e", "ke_i", "e_ion", "e_phot", "e_field", "e_esc", "e_trans", "e_ka_esc")) \
             - d["e_inc"]
 
-    def tot_o(t):
-        return sum(t[k] for k in ("KE_E", "KE_I", "ION", "PHOT", "FIELD", "ESC", "TRANS", "KA_ESC")) - t["INC"]
-
-    e0g, e0o = tot_g(g.diagnostics()), tot_o(o.tallies()[0])
+    o = oracle.OracleSlab(cfg, tables)
+    o.load(st)
+    t0, _ = o.tallies()
+    e0o = sum(t0[k] for k in ("KE_E", "KE_I", "ION", "PHOT", "FIELD", "ESC", "TRANS", "KA_ESC")) - t0["INC"]
+    e0g = tot_g(g.diagnostics())
     assert abs(e0g / e0o - 1) < 1e-6
-    rows = []
-    for _ in range(5):
+    drift = {}
+    for k in range(5):
         g.step(100)
-        o.step(100)
-        rows.append(((tot_g(g.diagnostics()) - e0g) / e0g, (tot_o(o.tallies()[0]) - e0o) / e0o))
-    print("\nenergy drift every 100 steps (device, oracle):", [(round(a, 5), round(b, 5)) for a, b in rows])
-    assert max(abs(a - b) for a, b in rows) < 3e-3, rows
-    assert max(abs(b) for _, b in rows) < 0.02, rows
+        drift[f"drift_{100 * (k + 1)}"] = (tot_g(g.diagnostics()) - e0g) / e0g
+    bad = spread_violations("small_slab_500", drift, default_floor=1e-4)
+    assert not bad, bad
+    assert max(abs(v["mean"]) for k, v in oracle_spread("small_slab_500")["diagnostics"].items()
+               if k.startswith("drift")) < 0.02
 
 
 def test_full_size_sampled_cells(tables):
@@ -284,12 +279,12 @@ def test_full_size_sampled_cells(tables):
     me_sum = len(sub.eid)
     o = oracle.OracleSlab(sub_cfg, tables)
     o.load(sub)
+    o.trace()
     o.step(1)
-    oe, oi = o.electrons(), o.ions()
     ge, gi = g.electrons(), g.ions()
     ge_s, gi_s = select_cells(cfg, ge, gi, cells)
-    res = compare_state(ge_s, oe, gi_s, oi, 64, 1)
-    _assert_parity(res, me_sum)
+    assert len(ge_s["id"]) >= me_sum
+    assert_flip_parity(sub_cfg, sub, ge_s, gi_s, o)
     # properties over the whole slab: charge neutrality kept to FP32 rounding
     qe = ge["w"].astype(np.float64).sum()
     qi = cfg.w_ion * (gi["Z"] + gi["zf"].astype(np.float64)).sum()
@@ -323,12 +318,7 @@ def test_uneven_cells_all_tiers(tables):
         izf=np.zeros(st.n_i + ni_x), iZ=np.full(st.n_i + ni_x, cfg.Z_init, dtype=np.int32),
         inK=np.zeros(st.n_i + ni_x, dtype=np.int32), iid=np.arange(st.n_i + ni_x, dtype=np.uint32))
     g, o = _run_both(cfg, tables, st, 1)
-    res = compare_state(g.electrons(), o.electrons(), g.ions(), o.ions(), cfg.nx, cfg.ny)
-    _assert_parity(res, st.n_e)
-    dg = g.diagnostics()
-    _, co = o.tallies()
-    for k in ("ION", "REC", "EE", "EI"):
-        assert abs(dg["counts"][k] - co[k]) <= max(1, int(1e-3 * co[k])), (k, dg["counts"][k], co[k])
+    _assert_parity(cfg, st, g, o)
 
 
 @pytest.mark.parametrize("ipd", [P.IPD_NONE, P.IPD_SP])
@@ -343,12 +333,8 @@ def test_single_step_ipd_models(tables, ipd):
     st = _busy(cfg, seed=8)
     ph = P.photons_uniform(cfg, pl, 1.0)
     g, o = _run_both(cfg, tab, st, 1, pulse=pl, photons=ph)
-    res = compare_state(g.electrons(), o.electrons(), g.ions(), o.ions(), cfg.nx, cfg.ny)
-    _assert_parity(res, st.n_e)
-    dg = g.diagnostics()
+    _assert_parity(cfg, st, g, o)
     _, co = o.tallies()
-    for k in ("ION", "REC", "PH0", "PH1", "PH2", "AUG"):
-        assert abs(dg["counts"][k] - co[k]) <= max(1, int(1e-3 * co[k])), (k, dg["counts"][k], co[k])
     assert co["PH0"] > 0
 
 
@@ -364,8 +350,7 @@ def test_single_step_forced_thermalization(tables):
     st = _busy(cfg, seed=6)
     ph = P.photons_uniform(cfg, pl, 1.0)
     g, o = _run_both(cfg, tab, st, 1, pulse=pl, photons=ph)
-    res = compare_state(g.electrons(), o.electrons(), g.ions(), o.ions(), cfg.nx, cfg.ny)
-    _assert_parity(res, st.n_e)
+    _assert_parity(cfg, st, g, o)
     _, co = o.tallies()
     assert co["PH0"] > 0 and co["AUG"] > 0 and co["ION"] > 0
 
@@ -418,27 +403,27 @@ def test_cell_order_matches_lexsort(n):
 def test_small_slab_full_500_steps(tables):
     """The plain 1D slab at its full size and length (128 x 2 nm cells,
     256 e + 64 i per cell, collisions, Lotz ionization and recombination,
-    500 steps of 0.02 fs): FP32 device against the FP64 oracle, run
-    independently.  Single trajectories decorrelate (chaos), so the charge
-    state, temperature, density and event counts are compared."""
+    push and fields, 500 steps of 0.02 fs): single trajectories decorrelate
+    (chaos), so the device's mean charge, temperature, electron count and
+    event counts must lie within the spread of eight oracle realizations
+    (tests/golden/oracle_spread.json; floor: 3 events), and its
+    charge-state histogram no farther from their mean (L1) than 1.5 times
+    the farthest realization from the mean of the others."""
     cfg = P.cfg_small_1d()
     st = P.init_particles(cfg)
-    g, o = _run_both(cfg, tables, st, 500)
-    dg = g.diagnostics()
-    to, co = o.tallies()
-    csd_o, _ = o.diag()
-    zbar_o = float((np.arange(len(csd_o)) * csd_o).sum())
-    e = o.electrons()
-    ke = 510998.95 * (e["u"] ** 2).sum(1) / (np.sqrt(1 + (e["u"] ** 2).sum(1)) + 1)
-    te_o = (2.0 / 3.0) * (e["w"] * ke).sum() / e["w"].sum()
-    assert abs(dg["Zbar"] / zbar_o - 1) < 0.01, (dg["Zbar"], zbar_o)
-    assert abs(dg["T_e_eV"] / te_o - 1) < 0.02, (dg["T_e_eV"], te_o)
-    assert abs(dg["n_e"] / len(e["id"]) - 1) < 0.02
+    g = pkg.Slab(cfg, tables)
+    g.load(st)
+    g.step(500)
+    d = g.diagnostics()
+    vals = {"Zbar": d["Zbar"], "T_e_eV": d["T_e_eV"], "n_e": float(d["n_e"])}
     for k in ("ION", "REC", "EE", "EI"):
-        assert abs(dg["counts"][k] / max(co[k], 1) - 1) < 0.03, (k, dg["counts"][k], co[k])
-    # independent samples of ~8200 ions once the trajectories decorrelate:
-    # the L1 distance of two such histograms is ~0.02 on average
-    assert np.abs(dg["csd"] - csd_o).sum() < 0.06
+        vals["count_" + k] = float(d["counts"][k])
+    floors = {f"count_{k}": 3.0 for k in ("ION", "REC", "EE", "EI")}
+    floors["n_e"] = 3.0
+    bad = spread_violations("small_slab_500", vals, floors)
+    assert not bad, bad
+    l1, bound = spread_hist_l1("small_slab_500", "csd", d["csd"])
+    assert l1 <= bound, (l1, bound)
 
 
 def test_single_step_10kev(tables):
@@ -454,8 +439,7 @@ def test_single_step_10kev(tables):
         st = _busy(cfg, seed=12)
         ph = P.photons_uniform(cfg, pl, 50.0)
         g, o = _run_both(cfg, tab, st, 1, pulse=pl, photons=ph)
-        res = compare_state(g.electrons(), o.electrons(), g.ions(), o.ions(), cfg.nx, cfg.ny)
-        _assert_parity(res, st.n_e)
+        _assert_parity(cfg, st, g, o)
         _, co = o.tallies()
         assert co["PH0"] > 0 and co["AUG"] > 0, co
         e = g.electrons()
@@ -467,38 +451,47 @@ def test_k_vacancy_history_over_a_pulse(tables):
     """A 64 x 2 cell slice of the 2D foil through 200 steps (4 fs) of a
     1.6 keV pulse peaking at 5 fs: K-shell photoionization fills K
     vacancies that then decay by KLL Auger or K-alpha over many rad steps
-    (Sec. III).  The two sides run independently; their event histories
-    agree within the statistics of decorrelated trajectories."""
+    (Sec. III).  The device's event history must lie within the spread of
+    eight oracle realizations (tests/golden/oracle_spread.json; floor: 3
+    events, 3 hollow ions, 1e-3 of transmission)."""
     cfg = P.cfg_foil_2d(nx=64, ny=2)
     st = P.init_particles(cfg)
-    g, o = _run_both(cfg, tables, st, 200, pulse=P.pulse_foil_2d(t_peak_fs=5.0))
-    cg = g.diagnostics()["counts"]
-    _, co = o.tallies()
-    assert co["AUG"] > 100 and co["KA"] > 0, co
-    # counts of decorrelated trajectories (the photon absorption follows the
-    # ion states, which the chaotic collisions reshuffle): a few per cent
-    for k, rel, floor in (("PH0", 0.06, 4), ("AUG", 0.06, 4), ("PART", 0.2, 4), ("KA", 0.3, 3),
-                          ("ION", 0.05, 10), ("REC", 0.12, 20)):
-        assert abs(cg[k] - co[k]) <= max(floor, rel * co[k]), (k, cg[k], co[k])
-    nk_g = int((g.ions()["nK"] > 0).sum())
-    nk_o = int((o.ions()["nK"] > 0).sum())
-    assert abs(nk_g - nk_o) <= max(4, 0.1 * nk_o), (nk_g, nk_o)
+    g = pkg.Slab(cfg, tables, P.pulse_foil_2d(t_peak_fs=5.0))
+    g.load(st)
+    g.step(200)
+    d = g.diagnostics()
+    assert d["counts"]["AUG"] > 100 and d["counts"]["KA"] > 0, d["counts"]
+    vals = {"count_" + k: float(d["counts"][k]) for k in ("PH0", "AUG", "PART", "KA", "ION", "REC")}
+    vals["n_hollow"] = float((g.ions()["nK"] > 0).sum())
+    vals["transmission"] = d["transmission"]
+    floors = {k: 3.0 for k in vals}
+    floors["transmission"] = 1e-3
+    bad = spread_violations("kvac_history", vals, floors)
+    assert not bad, bad
 
 
 def test_partial_events_only_below_one_ion_weight(tables):
     """The same slice early in the pulse (peak at 80 fs, first 5 fs): the
     photon number of a bin in a cell stays below one ion's weight, so every
     absorption is a partial event (the fraction moves the ion's outer
-    electron, Sec. III) and no K vacancy, Auger or K-alpha appears on
-    either side."""
+    electron, Sec. III) and no K vacancy, Auger or K-alpha appears, on the
+    device as in every oracle realization; the device's counts lie within
+    the oracle's spread (tests/golden/oracle_spread.json; floor 3 events)."""
     cfg = P.cfg_foil_2d(nx=64, ny=2)
     st = P.init_particles(cfg)
-    g, o = _run_both(cfg, tables, st, 250, pulse=P.pulse_foil_2d(t_peak_fs=80.0))
+    g = pkg.Slab(cfg, tables, P.pulse_foil_2d(t_peak_fs=80.0))
+    g.load(st)
+    g.step(250)
     ph = g.photons()
     assert ph.max() < cfg.w_ion
     cg = g.diagnostics()["counts"]
-    _, co = o.tallies()
-    for cnt in (cg, co):
-        assert cnt["PART"] > 0 and cnt["PH0"] > 0 and cnt["AUG"] == 0 and cnt["KA"] == 0, cnt
-    assert int((g.ions()["nK"] > 0).sum()) == 0 and int((o.ions()["nK"] > 0).sum()) == 0
-    assert abs(cg["PART"] - co["PART"]) <= max(4, 0.1 * co["PART"]), (cg["PART"], co["PART"])
+    assert cg["PART"] > 0 and cg["PH0"] > 0 and cg["AUG"] == 0 and cg["KA"] == 0, cg
+    assert int((g.ions()["nK"] > 0).sum()) == 0
+    gold = oracle_spread("partial_early")["diagnostics"]
+    assert max(gold["count_AUG"]["values"]) == 0 and max(gold["count_KA"]["values"]) == 0
+    vals = {"count_" + k: float(cg[k]) for k in ("PART", "PH0", "ION", "REC")}
+    vals["transmission"] = g.diagnostics()["transmission"]
+    floors = {k: 3.0 for k in vals}
+    floors["transmission"] = 1e-3
+    bad = spread_violations("partial_early", vals, floors)
+    assert not bad, bad
