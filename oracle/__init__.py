@@ -91,6 +91,7 @@ def lib():
             L.orc_n_ions.restype = C.c_int
             L.orc_n_ions.argtypes = [C.c_void_p]
             L.orc_get_electrons.argtypes = [C.c_void_p, _D, _D, _D, _D, _U64]
+            L.orc_get_electron_scales.argtypes = [C.c_void_p, _D]
             L.orc_get_ions.argtypes = [C.c_void_p, _D, _D, _D, _D, _I32, _I32, _U32]
             for fn in ("orc_set_fields", "orc_get_fields", "orc_get_current",
                        "orc_set_photons", "orc_get_photons"):
@@ -112,7 +113,7 @@ def lib():
             L.orc_field_speed.restype = C.c_double
             L.orc_field_speed.argtypes = [C.c_void_p]
             L.orc_collide.restype = C.c_int
-            L.orc_collide.argtypes = [_D, _D] + [C.c_double] * 9 + [_D]
+            L.orc_collide.argtypes = [_D, _D] + [C.c_double] * 9 + [_D, C.c_void_p]
             L.orc_boris.argtypes = [_D, _D, _D, C.c_double, C.c_double]
             L.orc_pair_order.argtypes = [C.c_int, _U64, C.c_uint32, C.c_uint32, C.c_uint64, _I]
             L.orc_ee_pairs.restype = C.c_int
@@ -167,7 +168,7 @@ NEAR_DTYPE = np.dtype([("step", np.uint32), ("cell", np.int32), ("kind", np.int3
                        ("id", np.uint64), ("x", np.float64), ("thr", np.float64)])
 NEAR_KINDS = {1: "COLL_ACC", 2: "ION_DRAW", 3: "ION_PAY", 4: "REC_K", 5: "REC_CAP", 6: "PH_EDGE",
               7: "PH_DRAW", 8: "PH_BIN", 9: "PH_PART", 10: "PH_ZF", 11: "DECAY", 12: "BRANCH",
-              13: "REC_TAKE", 14: "EBULK"}
+              13: "REC_TAKE", 14: "EBULK", 15: "BASIS"}
 # relative distance from a threshold within which an FP32 evaluation of a
 # decision may differ from the FP64 one (a threshold flip)
 FLIP_REL = 2.0 ** -20
@@ -235,9 +236,11 @@ class OracleSlab:
         X, Y, w = np.zeros(n), np.zeros(n), np.zeros(n)
         u = np.zeros((n, 3))
         i = np.zeros(n, dtype=np.uint64)
+        cs = np.zeros(n)
         if n:
             self.L.orc_get_electrons(self.h, _p(X), _p(Y), _p(u), _p(w), _p(i, C.c_uint64))
-        return dict(X=X, Y=Y, u=u, w=w, id=i)
+            self.L.orc_get_electron_scales(self.h, _p(cs))
+        return dict(X=X, Y=Y, u=u, w=w, id=i, cscale=cs)
 
     def ions(self):
         n = self.L.orc_n_ions(self.h)
@@ -359,7 +362,7 @@ def collide(ua, ub, ma, mb, qa, qb, wa, wb, n_l, lnL, dtc, r):
     a = np.array(ua, dtype=np.float64)
     b = np.array(ub, dtype=np.float64)
     rr = np.array(r, dtype=np.float64)
-    did = lib().orc_collide(_p(a), _p(b), ma, mb, qa, qb, wa, wb, n_l, lnL, dtc, _p(rr))
+    did = lib().orc_collide(_p(a), _p(b), ma, mb, qa, qb, wa, wb, n_l, lnL, dtc, _p(rr), None)
     return a, b, did
 
 

@@ -82,8 +82,12 @@ void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* uniform in the open interval (0,1): top 24 bits, centred */
-double orc_u01(uint32_t x) { return ((double)(x >> 8) + 0.5) * (1.0 / 16777216.0); }
+/* uniform in the open interval (0,1): the top 23 bits k, centred,
+ * (k + 1/2) 2^-23.  Every such value has at most 24 significant bits, so
+ * it is the same number in single and double precision (24 bits, (k + 1/2)
+ * 2^-24, would need 25 bits for k >= 2^23 and round to k + 1 in single
+ * precision, 1.0 at the top). */
+double orc_u01(uint32_t x) { return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0); }
 
 static void draw4(uint64_t seed, uint64_t id, uint32_t step, uint32_t purpose, double r[4])
 {
@@ -265,7 +269,7 @@ static void scale_ke(double u[3], double f)
  * fs; r[0..3] uniforms.  Returns 1 if a rotation was computed. */
 int orc_collide(double ua[3], double ub[3], double ma, double mb, double qa,
                 double qb, double wa, double wb, double n_l, double lnL,
-                double dtc, const double r[4])
+                double dtc, const double r[4], double *np2_out)
 {
     if (qa == 0.0 || qb == 0.0) return 0;
     double ga = gam(ua), gb = gam(ub);
@@ -293,14 +297,21 @@ int orc_collide(double ua[3], double ub[3], double ma, double mb, double qa,
     double n[3] = {ps[0] / p, ps[1] / p, ps[2] / p};
     double st = 2.0 * delta / (1.0 + delta * delta);
     double ct = (1.0 - delta * delta) / (1.0 + delta * delta);
+    /* orthonormal (e1, e2) about n, the origin of the azimuth: built on the
+     * z axis while n is at least 30 degrees from it (|n_xy|^2 >= 1/4), on
+     * the x axis otherwise, so that the frame never divides by a small
+     * component (any frame gives the same distribution of outcomes) */
     double e1[3], e2[3];
-    double np = sqrt(n[0] * n[0] + n[1] * n[1]);
-    if (np > 0.0) {
+    double np2 = n[0] * n[0] + n[1] * n[1];
+    if (np2_out) *np2_out = np2;
+    if (np2 >= 0.25) {
+        double np = sqrt(np2);
         e1[0] = n[0] * n[2] / np; e1[1] = n[1] * n[2] / np; e1[2] = -np;
         e2[0] = -n[1] / np; e2[1] = n[0] / np; e2[2] = 0.0;
     } else {
-        e1[0] = 1.0; e1[1] = 0.0; e1[2] = 0.0;
-        e2[0] = 0.0; e2[1] = 1.0; e2[2] = 0.0;
+        double nq = sqrt(n[1] * n[1] + n[2] * n[2]);
+        e2[0] = 0.0; e2[1] = n[2] / nq; e2[2] = -n[1] / nq;
+        e1[0] = nq; e1[1] = -n[0] * n[1] / nq; e1[2] = -n[0] * n[2] / nq;
     }
     double cp = cos(phi), sp = sin(phi);
     double qa_s[3];
@@ -485,7 +496,10 @@ void orc_rho(int nx, int ny, double X, double Y, double qw, double *rho)
 }
 
 /* ---------------- slab state ---------------- */
-typedef struct { double X, Y, u[3], w; uint64_t id; int alive; } elec;
+/* cs: momentum scale of the binary collisions the electron took part in
+ * during the last step (the largest |u| of itself and its partners before
+ * each collision; test bookkeeping, no part of the method) */
+typedef struct { double X, Y, u[3], w; uint64_t id; int alive; double cs; } elec;
 typedef struct { double X, Y, u[3], zf; uint32_t id; int Z, nK; } ionr;
 
 struct orc_slab {
@@ -596,7 +610,7 @@ void orc_load_electrons(orc_slab *s, int n, const double *X, const double *Y,
         elec *e = &s->e[k];
         e->X = X[k]; e->Y = Y[k];
         e->u[0] = u[3 * k]; e->u[1] = u[3 * k + 1]; e->u[2] = u[3 * k + 2];
-        e->w = w[k]; e->id = id[k]; e->alive = 1;
+        e->w = w[k]; e->id = id[k]; e->alive = 1; e->cs = 0.0;
     }
     s->ne = n;
 }
@@ -617,6 +631,10 @@ void orc_load_ions(orc_slab *s, int n, const double *X, const double *Y,
 }
 
 int orc_n_electrons(const orc_slab *s) { return s->ne; }
+void orc_get_electron_scales(const orc_slab *s, double *cs)
+{
+    for (int k = 0; k < s->ne; ++k) cs[k] = s->e[k].cs;
+}
 int orc_n_ions(const orc_slab *s) { return s->ni; }
 
 void orc_get_electrons(const orc_slab *s, double *X, double *Y, double *u, double *w, uint64_t *id)
@@ -867,6 +885,8 @@ static void cell_physics(orc_slab *S, int cell, int *eidx, int ne, int *iidx, in
         free(ids); free(perm);
     }
 
+    for (int k = 0; k < ne; ++k) S->e[pe[k]].cs = 0.0;
+
     /* 2. moments (FP64) */
     double We = 0, Wb = 0, Kb = 0, Q = 0;
     for (int k = 0; k < ne; ++k) {
@@ -900,13 +920,22 @@ static void cell_physics(orc_slab *S, int cell, int *eidx, int ne, int *iidx, in
         for (int k = 0; k < np; ++k) {
             elec *a = &S->e[pe[pa[k]]], *b = &S->e[pe[pb[k]]];
             double r[4];
+            {
+                const double sa = sqrt(a->u[0] * a->u[0] + a->u[1] * a->u[1] + a->u[2] * a->u[2]);
+                const double sb = sqrt(b->u[0] * b->u[0] + b->u[1] * b->u[1] + b->u[2] * b->u[2]);
+                const double m = sa > sb ? sa : sb;
+                if (m > a->cs) a->cs = m;
+                if (m > b->cs) b->cs = m;
+            }
             draw4(seed, a->id, step, PU_COLL_EE, r);
             if (a->w != b->w) {
                 double wm = a->w > b->w ? a->w : b->w;
                 decide(o, 1, ORC_N_COLL_ACC, 0, a->id, r[3], (a->w < wm ? a->w : b->w) / wm);
             }
+            double np2 = -1.0;
             o->cnt[ORC_C_EE] += orc_collide(a->u, b->u, 1.0, 1.0, -1.0, -1.0, a->w, b->w,
-                                            n_e, lnL, p->dt * fr[k], r);
+                                            n_e, lnL, p->dt * fr[k], r, &np2);
+            if (np2 >= 0.0) decide(o, 0, ORC_N_BASIS, 0, a->id, np2, 0.25);
         }
         free(pa); free(pb); free(fr);
     }
@@ -932,8 +961,10 @@ static void cell_physics(orc_slab *S, int cell, int *eidx, int ne, int *iidx, in
                 double wm = a->w > wi ? a->w : wi;
                 decide(o, 1, ORC_N_COLL_ACC, 0, a->id, r[3], (a->w < wm ? a->w : wi) / wm);
             }
+            double np2 = -1.0;
             o->cnt[ORC_C_EI] += orc_collide(a->u, b->u, 1.0, p->m_ion, -1.0, b->Z + b->zf,
-                                            a->w, wi, npair, lnL, p->dt, r);
+                                            a->w, wi, npair, lnL, p->dt, r, &np2);
+            if (np2 >= 0.0) decide(o, 0, ORC_N_BASIS, 0, a->id, np2, 0.25);
         }
     }
 
@@ -1424,7 +1455,7 @@ void orc_step(orc_slab *s, int nsteps, int nthreads)
                 elec *e = &s->e[s->ne++];
                 newe *q = &co[c].ne[k];
                 e->X = q->X; e->Y = q->Y; e->u[0] = q->u[0]; e->u[1] = q->u[1]; e->u[2] = q->u[2];
-                e->w = q->w; e->id = q->id; e->alive = 1;
+                e->w = q->w; e->id = q->id; e->alive = 1; e->cs = 0.0;
             }
             s->tally[ORC_T_ION] += co[c].tally_ion;
             s->tally[ORC_T_KA_ESC] += co[c].ka_esc;

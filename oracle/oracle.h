@@ -83,7 +83,8 @@ enum { ORC_N_COLL_ACC = 1,   /* weighted acceptance r < w_other / w_max (particl
        ORC_N_DECAY = 11,     /* K-vacancy decay r < dt_rad / tau (ion) */
        ORC_N_BRANCH = 12,    /* Auger / K-alpha branch r < 1 - omega (ion) */
        ORC_N_REC_TAKE = 13,  /* recombination weight reaching an electron's whole weight (cell) */
-       ORC_N_EBULK = 14 };   /* kinetic energy against E_bulk (electron) */
+       ORC_N_EBULK = 14,     /* kinetic energy against E_bulk (electron) */
+       ORC_N_BASIS = 15 };   /* azimuth frame of a collision: |n_xy|^2 against 1/4 (particle) */
 typedef struct {
     uint32_t step;
     int32_t cell;        /* cell of the slab */
@@ -104,6 +105,11 @@ void orc_load_ions(orc_slab *s, int n, const double *X, const double *Y,
                    const double *u, const double *zf, const int32_t *Z,
                    const int32_t *nK, const uint32_t *id);
 int orc_n_electrons(const orc_slab *s);
+/* for each electron (orc_get_electrons order): the largest |u| among
+ * itself and its e-e collision partners, taken before each collision of
+ * the last step (0 if it did not collide): the momentum scale to which an
+ * FP32 evaluation of those collisions rounds (test bookkeeping) */
+void orc_get_electron_scales(const orc_slab *s, double *cs);
 int orc_n_ions(const orc_slab *s);
 void orc_get_electrons(const orc_slab *s, double *X, double *Y, double *u,
                        double *w, uint64_t *id);
@@ -134,9 +140,11 @@ double orc_ipd(int model, int z, double n_e, double n_i, double T_e, double zbar
 double orc_lotz(const orc_tables *t, int z, double dE, double E);
 double orc_coulomb_log(double n_e, double T_e, double zbar);
 double orc_field_speed(const orc_params *p);   /* nm/fs, speed of the Yee update */
+/* np2_out (may be NULL): squared in-plane part of the collision's
+ * centre-of-momentum direction, which picks the azimuth frame */
 int orc_collide(double ua[3], double ub[3], double ma, double mb, double qa,
                 double qb, double wa, double wb, double n_l, double lnL,
-                double dtc, const double r[4]);
+                double dtc, const double r[4], double *np2_out);
 void orc_boris(double u[3], const double e[3], const double b[3], double qm, double dt);
 void orc_pair_order(int n, const uint64_t *id, uint32_t step, uint32_t purpose,
                     uint64_t seed, int *perm);

@@ -227,8 +227,9 @@ __device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint
     return U4{c0, c1, c2, c3};
 }
 
-// uniform in (0,1): top 24 bits, centred; exact in float and double
-__device__ __forceinline__ real u01(uint32_t x) { return ((real)(x >> 8) + RF(0.5)) * (RF(1.0) / RF(16777216.0)); }
+// uniform in (0,1): top 23 bits, centred, (k + 1/2) 2^-23: at most 24
+// significant bits, so the same value in float and double
+__device__ __forceinline__ real u01(uint32_t x) { return ((real)(x >> 9) + RF(0.5)) * (RF(1.0) / RF(8388608.0)); }
 
 __device__ __forceinline__ U4 draw(unsigned long long seed, unsigned long long id, uint32_t step, uint32_t purpose)
 {
@@ -443,15 +444,19 @@ __device__ __noinline__ bool binary_collision(real3 &ua, real3 &ub, real ma, rea
     real d2 = delta * delta;
     const real id2 = RF(1.0) / (RF(1.0) + d2);
     real st = RF(2.0) * delta * id2, ct = (RF(1.0) - d2) * id2;
+    // azimuth frame (e1, e2) about n: on the z axis while n is at least 30
+    // degrees from it, on the x axis otherwise (no division by a small
+    // component, so FP32 rounding is not amplified near the poles)
     real e1x, e1y, e1z, e2x, e2y, e2z;
-    real np = r_sqrt(nx * nx + ny * ny);
-    if (np > RF(0.0)) {
-        const real inp = RF(1.0) / np;
+    const real np2 = nx * nx + ny * ny;
+    if (np2 >= RF(0.25)) {
+        const real np = r_sqrt(np2), inp = RF(1.0) / np;
         e1x = nx * nz * inp; e1y = ny * nz * inp; e1z = -np;
         e2x = -ny * inp; e2y = nx * inp; e2z = RF(0.0);
     } else {
-        e1x = RF(1.0); e1y = RF(0.0); e1z = RF(0.0);
-        e2x = RF(0.0); e2y = RF(1.0); e2z = RF(0.0);
+        const real nq = r_sqrt(ny * ny + nz * nz), inq = RF(1.0) / nq;
+        e2x = RF(0.0); e2y = nz * inq; e2z = -ny * inq;
+        e1x = nq; e1y = -nx * ny * inq; e1z = -nx * nz * inq;
     }
     real qx = p * (ct * nx + st * cphi * e1x + st * sphi * e2x);
     real qy = p * (ct * ny + st * cphi * e1y + st * sphi * e2y);

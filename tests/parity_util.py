@@ -78,6 +78,8 @@ def select_cells(cfg, e, i, cells):
 
 # ---- classification of mismatches as threshold flips ----
 
+REC_TAKE = 13      # oracle decision kind: recombination weight reaching an electron's whole weight
+
 def _cell_of_ids(cfg, X, Y):
     return (np.floor(Y).astype(np.int64) * cfg.nx + np.floor(X).astype(np.int64)) if cfg.ny > 1 \
         else np.floor(X).astype(np.int64)
@@ -86,6 +88,13 @@ def _cell_of_ids(cfg, X, Y):
 def classify(cfg, st, g_e, o_e, g_i, o_i, near, n_draw, n_dec):
     """Every difference between the device's state after one step and the
     oracle's, classified against the oracle's decision trace of that step.
+
+    Momenta: an electron's error is taken relative to the momentum scale of
+    the binary collisions that produced it (the oracle's cscale: the larger
+    |u| of itself and each e-e partner, before the collision), since an FP32
+    evaluation of a collision rounds both outgoing momenta at the pair's
+    scale; the error of a slow electron scattered by a fast one is relative
+    to the fast one.
 
     A decision that lies within 2^-20 of its threshold (|x - thr| <= 2^-20
     |thr|, the survey's definition of a threshold flip) may go the other
@@ -131,11 +140,17 @@ def classify(cfg, st, g_e, o_e, g_i, o_i, near, n_draw, n_dec):
         ga, oa = np.argsort(g_e["id"]), np.argsort(o_e["id"])
         gk = ga[np.searchsorted(g_e["id"][ga], ce)]
         ok = oa[np.searchsorted(o_e["id"][oa], ce)]
-        err = momentum_errors(g_e["u"][gk], o_e["u"][ok])
+        du = np.linalg.norm(g_e["u"][gk].astype(np.float64) - o_e["u"][ok], axis=1)
+        scale = np.linalg.norm(o_e["u"][ok], axis=1)
+        if "cscale" in o_e:
+            scale = np.maximum(scale, o_e["cscale"][ok])
+        err = du / (scale + U_FLOOR)
         wg, wo = g_e["w"][gk].astype(np.float64), o_e["w"][ok]
         werr = np.abs(wg - wo) / np.maximum(np.abs(wo), 1e-30)
         for k in np.nonzero((err > U_RTOL) | (werr > U_RTOL))[0]:
-            note(f"electron {int(ce[k])} momentum {err[k]:.2e} weight {werr[k]:.2e}", cell_of_e(ce[k]))
+            uo = o_e["u"][ok[k]]
+            note(f"electron {int(ce[k])} momentum {err[k]:.2e} |u| {np.linalg.norm(uo):.3e} weight {werr[k]:.2e}",
+                 cell_of_e(ce[k]))
     ci = np.array(sorted(gi_ids & oi_ids), dtype=np.uint64)
     if ci.size:
         ga, oa = np.argsort(g_i["id"]), np.argsort(o_i["id"])
@@ -147,14 +162,23 @@ def classify(cfg, st, g_e, o_e, g_i, o_i, near, n_draw, n_dec):
         for k in np.nonzero(bad)[0]:
             note(f"ion {int(ci[k])} Z {g_i['Z'][gk[k]]}/{o_i['Z'][ok[k]]} nK {g_i['nK'][gk[k]]}/{o_i['nK'][ok[k]]} "
                  f"momentum {err[k]:.2e}", icell.get(int(ci[k]), -1))
-    flips = sum(len(near_cells[c]) for c in diff_cells)
+    # a recombination that takes an electron's whole weight on one side and
+    # leaves a rounding-size remainder on the other changes no charge state
+    # and no event count: counted apart from the event flips
+    flips = sum(1 for c in diff_cells for r in near_cells[c] if int(r["kind"]) != REC_TAKE)
+    remainders = sum(1 for c in diff_cells for r in near_cells[c] if int(r["kind"]) == REC_TAKE)
+    import oracle
+    kinds = [(oracle.NEAR_KINDS.get(int(r["kind"]), int(r["kind"])), int(r["cell"]), float(r["x"]), float(r["thr"]))
+             for c in sorted(diff_cells) for r in near_cells[c]]
     return {"draws": n_draw, "decisions": n_dec, "near": len(near), "flip_cells": sorted(diff_cells),
-            "flips": flips, "unexplained": unexplained}
+            "flips": flips, "remainders": remainders, "flip_kinds": kinds, "unexplained": unexplained}
 
 
 def flip_summary(cls):
+    kinds = cls.get("flip_kinds", [])
     return (f"flips: {cls['flips']} of {cls['draws']} draws ({cls['decisions']} other decisions), "
-            f"{cls['near']} near-threshold decisions, cells with differences {cls['flip_cells'][:8]}")
+            f"{cls.get('remainders', 0)} recombination remainders, "
+            f"{cls['near']} near-threshold decisions, cells with differences {cls['flip_cells'][:8]} {kinds[:8]}")
 
 
 # the benchmark spec's bound on threshold flips: fewer than 1e-5 of the draws

@@ -47,6 +47,29 @@ def test_collision_conserves_momentum_energy(ma, mb, qb):
     assert worst_e < 1e-12
 
 
+def test_collision_frame_near_the_pole():
+    """Centre-of-momentum directions within a few degrees of the z axis
+    (the azimuth frame then switches to the x axis): momentum and energy
+    conserved to 1e-12 and the scattering angle between the old and new
+    relative momentum is 2 atan(delta) on both sides of the switch."""
+    rng = np.random.default_rng(8)
+    for k in range(200):
+        th = rng.uniform(0.0, 0.4) if k % 2 else rng.uniform(0.45, 0.6)   # |n_xy| below / above 1/2
+        ph = rng.uniform(0, 2 * math.pi)
+        d = 0.02 * np.array([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
+        ua, ub = d, -d                                     # equal masses: COM at rest, n along d
+        r = rng.random(4)
+        a, b, did = oracle.collide(ua, ub, 1.0, 1.0, -1.0, -1.0, 1.0, 1.0, 1e23, 3.0, 0.05, r)
+        assert did
+        assert np.linalg.norm(a + b) < 1e-15
+        assert abs(np.linalg.norm(a) - np.linalg.norm(ua)) < 1e-15
+        cos_t = float(np.dot(a, ua) / np.dot(ua, ua))
+        var = 2 * math.pi * 2.8179403262e-13 ** 2 * 2.99792458e-5 * 1e23 * 3.0 * 0.05 / \
+            (0.25 * (2 * 0.02 / math.sqrt(1 + 0.02 ** 2)) ** 3)
+        delta = math.sqrt(var) * math.sqrt(-2 * math.log(r[0])) * math.cos(2 * math.pi * r[1])
+        assert abs(cos_t - (1 - delta * delta) / (1 + delta * delta)) < 1e-12
+
+
 def test_collision_weighted_acceptance():
     """Unequal weights: the lighter particle always moves, the heavier one
     with probability w_light / w_heavy (Nanbu-Yonemura)."""

@@ -54,6 +54,14 @@ def test_uniform_open_interval():
     L = oracle.lib()
     assert 0.0 < L.orc_u01(0) < 1e-7
     assert 1.0 - 1e-7 < L.orc_u01(0xFFFFFFFF) < 1.0
+    # every uniform is exactly a single-precision number (the FP32 device
+    # path draws the same value), the largest one included
+    rng = np.random.default_rng(4)
+    xs = np.concatenate([rng.integers(0, 2**32, 20000, dtype=np.uint64), [0, 2**31, 2**32 - 1, 2**32 - 512]])
+    for x in xs:
+        u = L.orc_u01(int(x))
+        assert float(np.float32(u)) == u, x
+    assert float(np.float32(L.orc_u01(0xFFFFFFFF))) < 1.0
 
 
 def test_pair_order_is_uniform_permutation():
