@@ -57,9 +57,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
     """Compile the CUDA library for sm_103a (nvcc cross-compiles without a
     GPU): the FP32 build and the FP64 build, in parallel.  Returns the FP32
     library's path."""
-    srcs = _sources() + [os.path.join(_INCLUDE, "pic.h")]
+    srcs = _sources() + [os.path.join(_INCLUDE, "pic.h"), os.path.abspath(__file__)]
     newest = max(os.path.getmtime(s) for s in srcs)
-    todo = [(path, flags) for path, flags in ((LIB_PATH, []), (LIB64_PATH, ["-DPIC_FP64"]))
+    # FP32 build: approximate single-precision division and square root
+    # (within 2-3 ulp) and denormals flushed to zero; the FP64 build's double
+    # arithmetic is IEEE either way
+    fast32 = ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]
+    todo = [(path, flags) for path, flags in ((LIB_PATH, fast32), (LIB64_PATH, ["-DPIC_FP64"]))
             if force or not os.path.exists(path) or os.path.getmtime(path) < newest]
     if not todo:
         return LIB_PATH

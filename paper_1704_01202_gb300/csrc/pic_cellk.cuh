@@ -36,6 +36,13 @@ struct CellCtx {
     unsigned long long seed;
     real wi, mi, n_e, n_i, nref;
     bool rad;
+    // sums the recombination stage needs, when the earlier stages already
+    // hold them (every electron bulk, impact ionization run): kinetic
+    // energy of the electrons after the ionization payment, their weight,
+    // and the ion charge after ionization
+    bool have_sums;
+    dd K_after;
+    real W_e, Q_after;
 };
 
 // ---- forced-thermalization variant (Sec. VI C), rad steps ----
@@ -150,18 +157,30 @@ __device__ __noinline__ void stage_recombine(const CellArgs &a, const WarpMem &m
 {
     const int ne = c.ne, ni = c.ni;
     const real wi = c.wi, MC2 = (real)kMeC2;
-    real pq = RF(0.0);
-    for (int k = lane; k < ni; k += 32) { int sl = m.iperm[k]; pq += (real)(m.ist[sl] & 0xff) + m.iu[sl].w; }
-    const real zb = wsum_f(pq) / ni;
-    dd pkb = dd_zero();
-    real pwb = RF(0.0), pwx = RF(0.0);
-    for (int k = lane; k < ne; k += 32) {
-        real4 u = m.eu[m.eperm[k]];
-        real ke = MC2 * gm1(u.x, u.y, u.z);
-        pwx += u.w;
-        if (S.E_bulk <= RF(0.0) || ke < S.E_bulk) { pwb += u.w; pkb = dd_addf(pkb, u.w * ke); }
+    real zb, Wb2, Kb2, Wex;
+    if (c.have_sums) {
+        // every electron is bulk: the sums of the moments and ionization
+        // stages, which the ionization payment changed by a known amount
+        zb = c.Q_after / ni;
+        Wb2 = c.W_e + Wnew_imp;
+        Kb2 = dd_f(c.K_after);
+        Wex = c.W_e;
+    } else {
+        real pq = RF(0.0);
+        for (int k = lane; k < ni; k += 32) { int sl = m.iperm[k]; pq += (real)(m.ist[sl] & 0xff) + m.iu[sl].w; }
+        zb = wsum_f(pq) / ni;
+        dd pkb = dd_zero();
+        real pwb = RF(0.0), pwx = RF(0.0);
+        for (int k = lane; k < ne; k += 32) {
+            real4 u = m.eu[m.eperm[k]];
+            real ke = MC2 * gm1(u.x, u.y, u.z);
+            pwx += u.w;
+            if (S.E_bulk <= RF(0.0) || ke < S.E_bulk) { pwb += u.w; pkb = dd_addf(pkb, u.w * ke); }
+        }
+        Wb2 = wsum_f(pwb) + Wnew_imp;
+        Kb2 = dd_f(wsum_dd(pkb));
+        Wex = wsum_f(pwx);
     }
-    const real Wb2 = wsum_f(pwb) + Wnew_imp, Kb2 = dd_f(wsum_dd(pkb)), Wex = wsum_f(pwx);
     const real Te2 = Wb2 > RF(0.0) ? (RF(2.0) / RF(3.0)) * Kb2 / Wb2 : RF(0.0);
     const real zeos = eos_lookup(*a.eos, c.n_i, Te2);
     int Kev = zb > zeos ? (int)r_floor((zb - zeos) * ni + RF(0.5)) : 0;
@@ -475,9 +494,15 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
     int c_ee = 0, c_ei = 0, c_ion = 0, c_rej = 0;
     real n_e = RF(0.), n_i = RF(0.), Te = RF(0.), zbar = RF(0.), lnL = RF(2.);
     const bool coll = (flags & 3u) != 0;
+    const bool all_bulk = S.E_bulk <= RF(0.0);
     dd Kpre = dd_zero();
     int nnew = 0;
     real Wnew_imp = RF(0.0);
+    // sums carried from stage to stage (see CellCtx)
+    dd Qcell = dd_zero(), Kall = dd_zero(), Kt = dd_zero(), paid_cell = dd_zero();
+    real We_cell = RF(0.0);
+    int n_imp = 0;
+    bool ew_ready = false, ionized = false;
 
     if (on) {
     // ---- stage in shared memory; Philox sort keys ----
@@ -510,18 +535,22 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
 
     if (on) {
     // ---- cell moments (Sec. II: T_e = 2/3 E_ave over bulk electrons) ----
-    dd We = dd_zero(), Wb = dd_zero(), Kb = dd_zero(), Q = dd_zero();
+    dd We = dd_zero(), Wb = dd_zero(), Kb = dd_zero(), Q = dd_zero(), Ka = dd_zero();
     for (int k = lane; k < ne; k += 32) {
         real4 u = m.eu[m.eperm[k]];
         real ke = MC2 * gm1(u.x, u.y, u.z);
         We = dd_addf(We, u.w);
-        if (S.E_bulk <= RF(0.0) || ke < S.E_bulk) { Wb = dd_addf(Wb, u.w); Kb = dd_addf(Kb, u.w * ke); }
+        if (all_bulk || ke < S.E_bulk) { Wb = dd_addf(Wb, u.w); Kb = dd_addf(Kb, u.w * ke); }
+        if (!all_bulk) Ka = dd_addf(Ka, u.w * ke);
     }
     for (int k = lane; k < ni; k += 32) {
         int sl = m.iperm[k];
         Q = dd_addf(Q, (real)(m.ist[sl] & 0xff) + m.iu[sl].w);
     }
     We = wsum_dd(We); Wb = wsum_dd(Wb); Kb = wsum_dd(Kb); Q = wsum_dd(Q);
+    Kall = all_bulk ? Kb : wsum_dd(Ka);
+    Qcell = Q;
+    We_cell = dd_f(We);
     n_e = dd_f(We) * nref; n_i = (real)ni * wi * nref;
     Te = dd_f(Wb) > RF(0.0) ? (RF(2.0) / RF(3.0)) * dd_f(Kb) / dd_f(Wb) : RF(0.0);
     zbar = ni > 0 ? dd_f(Q) / ni : RF(0.0);
@@ -531,10 +560,10 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
 
     // ---- binary collisions (Sec. IV): e-e, then e-i; exact energy restore ----
     if (coll) {
-        dd pk = dd_zero(), pki = dd_zero();
-        for (int k = lane; k < ne; k += 32) { real4 u = m.eu[m.eperm[k]]; pk = dd_addf(pk, u.w * MC2 * gm1(u.x, u.y, u.z)); }
+        // electron part from the moments above; the ions' own pass
+        dd pki = dd_zero();
         for (int k = lane; k < ni; k += 32) { real4 u = m.iu[m.iperm[k]]; pki = dd_addf(pki, wi * MC2 * mi * gm1(u.x, u.y, u.z)); }
-        Kpre = dd_add(wsum_dd(pk), wsum_dd(pki));
+        Kpre = dd_add(Kall, wsum_dd(pki));
     }
     if ((flags & 1u) && ne >= 2) {
         const int start = (ne & 1) ? 3 : 0;
@@ -591,14 +620,34 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
         for (int k = lane; k < ni; k += 32) { real4 u = m.iu[m.iperm[k]]; pki = dd_addf(pki, wi * MC2 * mi * gm1(u.x, u.y, u.z)); }
         dd Ke = wsum_dd(pk), Ki = wsum_dd(pki);
         real ke = dd_f(Ke);
+        real delta = RF(0.0);
         if (ke > RF(0.0)) {
-            real delta = -dd_f(dd_sub(dd_sub(Kpre, Ke), Ki)) / ke;     // f = 1 - delta
-            if (delta < RF(1.0)) {
-                for (int k = lane; k < ne; k += 32) {
-                    real4 u = m.eu[k];
-                    scale_kinetic(u.x, u.y, u.z, delta);
-                    m.eu[k] = u;
-                }
+            delta = -dd_f(dd_sub(dd_sub(Kpre, Ke), Ki)) / ke;     // f = 1 - delta
+            if (!(delta < RF(1.0))) delta = RF(0.0);
+        }
+        if ((flags & 4u) && ni >= 1) {
+            // the restore and the ionization stage's per-electron inputs in
+            // one pass: kinetic energy and w * beta after the restore, in
+            // the sort-key storage (free until recombination), and their sum
+            real2 *ew = reinterpret_cast<real2 *>(m.ekey);
+            dd pt = dd_zero();
+            for (int k = lane; k < ne; k += 32) {
+                const int sl = m.eperm[k];
+                real4 u = m.eu[sl];
+                scale_kinetic(u.x, u.y, u.z, delta);
+                m.eu[sl] = u;
+                real u2 = u.x * u.x + u.y * u.y + u.z * u.z;
+                real g1 = u2 / (r_sqrt(RF(1.0) + u2) + RF(1.0));
+                pt = dd_addf(pt, u.w * MC2 * g1);
+                ew[k] = make_real2(MC2 * g1, u.w * (r_sqrt(u2) / (RF(1.0) + g1)));
+            }
+            Kt = wsum_dd(pt);
+            ew_ready = true;
+        } else if (delta != RF(0.0)) {
+            for (int k = lane; k < ne; k += 32) {
+                real4 u = m.eu[k];
+                scale_kinetic(u.x, u.y, u.z, delta);
+                m.eu[k] = u;
             }
         }
         __syncwarp();
@@ -616,15 +665,18 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
         // kinetic energy and w * beta of each electron (canonical order), kept
         // in the sort-key storage, which is free until recombination
         real2 *ew = reinterpret_cast<real2 *>(m.ekey);
-        dd pk = dd_zero();
-        for (int k = lane; k < ne; k += 32) {
-            real4 u = m.eu[m.eperm[k]];
-            real u2 = u.x * u.x + u.y * u.y + u.z * u.z;
-            real g1 = u2 / (r_sqrt(RF(1.0) + u2) + RF(1.0));
-            pk = dd_addf(pk, u.w * MC2 * g1);
-            ew[k] = make_real2(MC2 * g1, u.w * (r_sqrt(u2) / (RF(1.0) + g1)));
+        if (!ew_ready) {
+            dd pk = dd_zero();
+            for (int k = lane; k < ne; k += 32) {
+                real4 u = m.eu[m.eperm[k]];
+                real u2 = u.x * u.x + u.y * u.y + u.z * u.z;
+                real g1 = u2 / (r_sqrt(RF(1.0) + u2) + RF(1.0));
+                pk = dd_addf(pk, u.w * MC2 * g1);
+                ew[k] = make_real2(MC2 * g1, u.w * (r_sqrt(u2) / (RF(1.0) + g1)));
+            }
+            Kt = wsum_dd(pk);
         }
-        const dd Kt = wsum_dd(pk);
+        __syncwarp();
         const real cfac = (real)(kCcmPerFs) * S.dt * nref;
         for (int z = 0; z < ZNUC; ++z) {
             if (!(pmask & (1u << z))) continue;
@@ -701,10 +753,13 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
             }
             paid = dd_add(paid, wsum_dd(dd{acc ? cost : RF(0.0), RF(0.0)}));
             nnew += __popc(bal);
+            n_imp += __popc(bal);
             carry = wbcast_dd(incl, 31);
         }
         nnew = min(nnew, a.cap_new);
         Wnew_imp = nnew * wi;
+        paid_cell = paid;
+        ionized = true;
         real pf = dd_f(paid);
         if (pf > RF(0.0)) {
             real delta = pf / dd_f(Kt);
@@ -726,6 +781,10 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
     cc.s = s; cc.lc = lc; cc.cx = cx; cc.cy = cy; cc.e0 = e0; cc.ne = ne; cc.i0 = i0; cc.ni = ni;
     cc.step = step; cc.flags = flags; cc.seed = seed; cc.wi = wi; cc.mi = mi; cc.n_e = n_e; cc.n_i = n_i;
     cc.nref = nref; cc.rad = rad;
+    cc.have_sums = all_bulk && ionized;
+    cc.K_after = dd_sub(Kt, paid_cell);
+    cc.W_e = We_cell;
+    cc.Q_after = dd_f(Qcell) + (real)n_imp;
     if ((flags & 8u) && ni >= 1) stage_recombine(a, m, T, S, cc, lane, Wnew_imp, wt);
     if (rad && (flags & 16u) && S.nb && ni >= 1) stage_photo(a, m, T, S, cc, lane, nnew, wt);
     if (rad && (flags & 32u) && ni >= 1) stage_decay(a, m, T, S, cc, lane, nnew, wt);
