@@ -538,10 +538,15 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
     dd We = dd_zero(), Wb = dd_zero(), Kb = dd_zero(), Q = dd_zero(), Ka = dd_zero();
     for (int k = lane; k < ne; k += 32) {
         real4 u = m.eu[m.eperm[k]];
-        real ke = MC2 * gm1(u.x, u.y, u.z);
+        const real g1 = gm1(u.x, u.y, u.z);
+        const real ke = MC2 * g1;
+        // w * MC2 * g1: the same rounding as the kernel's other kinetic-energy
+        // sums, so that the collision energy restore does not see a bias
+        // between two formulas of the same energy
+        const real wk = u.w * MC2 * g1;
         We = dd_addf(We, u.w);
-        if (all_bulk || ke < S.E_bulk) { Wb = dd_addf(Wb, u.w); Kb = dd_addf(Kb, u.w * ke); }
-        if (!all_bulk) Ka = dd_addf(Ka, u.w * ke);
+        if (all_bulk || ke < S.E_bulk) { Wb = dd_addf(Wb, u.w); Kb = dd_addf(Kb, wk); }
+        if (!all_bulk) Ka = dd_addf(Ka, wk);
     }
     for (int k = lane; k < ni; k += 32) {
         int sl = m.iperm[k];
