@@ -1167,11 +1167,35 @@ pic_status tune_step(pic_ctx *c, int n, int &k)
     return set_wpc(c, t->wpc);
 }
 
+// Steps between two re-sizings of the cell tiers inside one pic_step call:
+// ionization grows the cells, and cells that outgrow the tiers fall through
+// to the one-warp large-cell pass.  Even, so that step pairs replay whole.
+constexpr int RESIZE_EVERY = 32;
+
+pic_status step_chunk(pic_ctx *c, int n);
+
 pic_status step_n(pic_ctx *c, int n)
 {
     pic_status r = apply_pending(c);
     if (r != PIC_OK) return r;
-    // size the per-warp staging for the largest cells seen so far
+    c->launches = 0;
+    for (int done = 0; done < n;) {
+        const int m = std::min(n - done, RESIZE_EVERY);
+        r = step_chunk(c, m);
+        if (r != PIC_OK) return r;
+        done += m;
+    }
+    // the first step after a retirement dropped the retired slabs' particles
+    if (n > 0)
+        for (int k = 0; k < c->nslot; ++k)
+            if (c->slot_state[k] == 2) c->slot_state[k] = 0;
+    return PIC_OK;
+}
+
+pic_status step_chunk(pic_ctx *c, int n)
+{
+    pic_status r = PIC_OK;
+    // size the per-warp staging for the cells of the last sort
     int cn[NCOUNTERS];
     CK(cudaMemcpyAsync(cn, c->counters, sizeof(int) * NCOUNTERS, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -1179,7 +1203,6 @@ pic_status step_n(pic_ctx *c, int n)
         r = configure_cell_launch(c, cn + CNT_HIST_E, cn + CNT_HIST_I, cn[CNT_MAXE], cn[CNT_MAXI]);
         if (r != PIC_OK) return r;
     }
-    c->launches = 0;
     int k = 0;
     if (c->autotune) {
         const pic_ctx::Tuned *t = tuned_entry(c);
@@ -1202,10 +1225,6 @@ pic_status step_n(pic_ctx *c, int n)
         if (r != PIC_OK) return r;
     }
     c->steps_done += n - tuned_steps;
-    // the first step after a retirement dropped the retired slabs' particles
-    if (n > 0)
-        for (int k = 0; k < c->nslot; ++k)
-            if (c->slot_state[k] == 2) c->slot_state[k] = 0;
     return PIC_OK;
 }
 

@@ -258,3 +258,52 @@ def spread_hist_l1(case, prefix, hist):
     d = float(np.abs(np.asarray(hist, dtype=np.float64)[:len(names)] - mean).sum())
     print(f"  {prefix} L1 from the oracle mean {d:.3e}; realizations' own {min(loo):.3e} .. {max(loo):.3e}")
     return d, 1.5 * max(loo)
+
+
+def welch_violations(case, dev_rows, floors=None, default_floor=0.0):
+    """Eight device realizations (dev_rows: one dict of diagnostics per
+    Philox key 1..8) against the oracle's eight of `case`: for every
+    diagnostic |mean_dev - mean_oracle| <= SPREAD_K * s + floor with
+    s = sqrt(sd_dev^2 / n_dev + sd_oracle^2 / n_oracle) (Welch's standard
+    error of the difference of two means; a systematic difference between
+    the two implementations shows here at a fraction of one realization's
+    scatter).  Returns {name: (mean_dev, mean_oracle, bound)} of the
+    violations and prints the table."""
+    g = oracle_spread(case)["diagnostics"]
+    floors = floors or {}
+    bad = {}
+    print(f"\n{case}: diagnostic, device mean, oracle mean, standard error, |t|")
+    for name in dev_rows[0]:
+        v = np.array([r[name] for r in dev_rows], dtype=np.float64)
+        o = g[name]
+        se = float(np.sqrt(v.var(ddof=1) / v.size + o["sd"] ** 2 / len(o["values"])))
+        diff = abs(v.mean() - o["mean"])
+        t = diff / se if se > 0 else (0.0 if diff == 0 else float("inf"))
+        print(f"  {name:14s} {v.mean():14.6g} {o['mean']:14.6g} {se:11.3g} {t:7.2f}")
+        if diff > SPREAD_K * se + floors.get(name, default_floor):
+            bad[name] = (float(v.mean()), o["mean"], SPREAD_K * se + floors.get(name, default_floor))
+    return bad
+
+
+def welch_hist_l1(case, prefix, dev_hists):
+    """L1 distance between the mean histogram (csd_* or eedf_* bins) of
+    eight device realizations and the oracle's eight, and its bound: 1.5
+    times the largest distance of one oracle realization from the mean of
+    the other seven, scaled to a difference of two eight-run means
+    (sqrt(2 / 8) / sqrt(1 + 1/7)).  Returns (d, bound)."""
+    g = oracle_spread(case)["diagnostics"]
+    names = sorted((k for k in g if k.startswith(prefix + "_")), key=lambda k: int(k.split("_")[1]))
+    V = np.array([g[k]["values"] for k in names])
+    n = V.shape[1]
+    loo = [np.abs(V[:, j] - (V.sum(axis=1) - V[:, j]) / (n - 1)).sum() for j in range(n)]
+    dm = np.mean(np.asarray(dev_hists, dtype=np.float64)[:, :len(names)], axis=0)
+    d = float(np.abs(dm - V.mean(axis=1)).sum())
+    bound = 1.5 * max(loo) * np.sqrt(2.0 / n) / np.sqrt(1.0 + 1.0 / (n - 1))
+    print(f"  {prefix} L1 between the mean histograms {d:.3e} (bound {bound:.3e})")
+    return d, bound
+
+
+def key_realizations(run, keys=range(1, 9)):
+    """run(key) -> dict of diagnostics, for the Philox keys of the oracle's
+    spread (the same initial state, seed 0 of the input generator)."""
+    return [run(k) for k in keys]
