@@ -21,7 +21,7 @@ _lock = threading.Lock()
 _lib = None
 
 NS, NZ = 5, 14
-T_NAMES = ["KE_E", "KE_I", "ION", "PHOT", "INC", "TRANS", "KA_ESC", "ESC", "FIELD"]
+T_NAMES = ["KE_E", "KE_I", "ION", "PHOT", "INC", "TRANS", "KA_ESC", "ESC", "FIELD", "BACK", "RT_NUM", "RT_PEND"]
 C_NAMES = ["ION", "ION_REJ", "REC", "PH0", "PH1", "PH2", "PH3", "PH4", "PART",
            "AUG", "KA", "PGT1", "ESC_E", "ESC_I", "EE", "EI"]
 
@@ -57,6 +57,10 @@ class Tables(C.Structure):
                 ("n_hv", C.c_int), ("hv_tab", C.POINTER(C.c_double)), ("sigma", C.POINTER(C.c_double)),
                 ("n_T", C.c_int), ("n_n", C.c_int), ("eos_T", C.POINTER(C.c_double)),
                 ("eos_n", C.POINTER(C.c_double)), ("eos_Z", C.POINTER(C.c_double))]
+
+
+class RT(C.Structure):
+    _fields_ = [("coarsen", C.c_int), ("n_polar", C.c_int), ("n_azimuth", C.c_int), ("scheme", C.c_int)]
 
 
 class Pulse(C.Structure):
@@ -123,6 +127,15 @@ def lib():
             L.orc_eos.restype = C.c_double
             L.orc_eos.argtypes = [C.POINTER(Tables), C.c_double, C.c_double]
             L.orc_trace.argtypes = [C.c_void_p, C.c_double]
+            L.orc_set_rt.restype = C.c_int
+            L.orc_set_rt.argtypes = [C.c_void_p, C.POINTER(RT)]
+            L.orc_rt_ordinates.restype = C.c_int
+            L.orc_rt_ordinates.argtypes = [C.c_void_p, _D, _D, _D]
+            L.orc_rt_get.argtypes = [C.c_void_p, _D, _D, _D]
+            L.orc_rt_set.argtypes = [C.c_void_p, _D, _D, _D]
+            L.orc_rt_cells.argtypes = [C.c_void_p, _D, _D, _D, _D]
+            L.orc_rt_line.argtypes = [_D, _D, C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_int,
+                                      C.c_void_p, C.c_void_p, C.c_int, _D, _D]
             L.orc_trace_count.restype = C.c_int
             L.orc_trace_count.argtypes = [C.c_void_p]
             L.orc_trace_decisions.argtypes = [C.c_void_p, _U64]
@@ -288,6 +301,38 @@ class OracleSlab:
         self.L.orc_tallies(self.h, _p(t), _p(c, C.c_uint64))
         return dict(zip(T_NAMES, t)), dict(zip(C_NAMES, (int(x) for x in c)))
 
+    def set_rt(self, coarsen=5, n_polar=4, n_azimuth=2, scheme=0):
+        """Switch on radiation transport (see orc_set_rt in oracle.h)."""
+        if self.n_bins == 0:
+            raise ValueError("radiation transport needs a pulse")
+        r = RT(coarsen=coarsen, n_polar=n_polar, n_azimuth=n_azimuth, scheme=scheme)
+        if self.L.orc_set_rt(self.h, C.byref(r)) != 0:
+            raise ValueError("invalid radiation transport setting")
+        self.rt = r
+        self.nrx = self.cfg.nx // coarsen
+        self.nry = self.cfg.ny // coarsen if self.cfg.ny > 1 else 1
+        mu, vy, w = np.zeros(1 + 16 * 16), np.zeros(1 + 16 * 16), np.zeros(1 + 16 * 16)
+        self.nord = self.L.orc_rt_ordinates(self.h, _p(mu), _p(vy), _p(w))
+        self.ordinates = (mu[:self.nord], vy[:self.nord], w[:self.nord])
+
+    def rt_field(self):
+        shp = (self.nord, self.n_bins, self.nry, self.nrx)
+        F, Gx, Gy = np.zeros(shp), np.zeros(shp), np.zeros(shp)
+        self.L.orc_rt_get(self.h, _p(F), _p(Gx), _p(Gy))
+        return F, Gx, Gy
+
+    def set_rt_field(self, F, Gx=None, Gy=None):
+        F = np.ascontiguousarray(F, dtype=np.float64)
+        Gx = np.zeros_like(F) if Gx is None else np.ascontiguousarray(Gx, dtype=np.float64)
+        Gy = np.zeros_like(F) if Gy is None else np.ascontiguousarray(Gy, dtype=np.float64)
+        self.L.orc_rt_set(self.h, _p(F), _p(Gx), _p(Gy))
+
+    def rt_cells(self):
+        nc = self.cfg.nx * self.cfg.ny
+        chi, emc, w, dE = np.zeros((nc, self.n_bins)), np.zeros(nc), np.zeros(nc), np.zeros(nc)
+        self.L.orc_rt_cells(self.h, _p(chi), _p(emc), _p(w), _p(dE))
+        return dict(chi=chi, emc=emc, w=w, dE=dE)
+
     def trace(self, rel=FLIP_REL):
         """Start the decision trace (rel <= 0 stops it): every threshold
         decision of the following steps is counted, and recorded when it
@@ -387,6 +432,21 @@ def ee_pairs(n):
     fr = np.zeros(n + 3)
     m = lib().orc_ee_pairs(n, _p(pa, C.c_int), _p(pb, C.c_int), _p(fr))
     return pa[:m], pb[:m], fr[:m]
+
+
+def rt_line(f, g, nu, scheme=0, periodic=False, fin=None, gin=None, gt=None):
+    """One advection of a line (orc_rt_line): returns (f, g, gt, inflow, outflow)."""
+    f = np.array(f, dtype=np.float64)
+    g = np.array(g, dtype=np.float64)
+    gt = None if gt is None else np.array(gt, dtype=np.float64)
+    fin = None if fin is None else np.ascontiguousarray(fin, dtype=np.float64)
+    gin = None if gin is None else np.ascontiguousarray(gin, dtype=np.float64)
+    i, o = np.zeros(1), np.zeros(1)
+    lib().orc_rt_line(_p(f), _p(g), None if gt is None else gt.ctypes.data_as(C.c_void_p), f.size, nu, scheme,
+                      1 if periodic else 0, None if fin is None else fin.ctypes.data_as(C.c_void_p),
+                      None if gin is None else gin.ctypes.data_as(C.c_void_p), 0 if fin is None else fin.size,
+                      _p(i), _p(o))
+    return f, g, gt, float(i[0]), float(o[0])
 
 
 def deposit(nx, ny, dx, dy, dt, X0, Y0, X1, Y1, vz, vy, qw, j3=None):

@@ -514,6 +514,14 @@ struct orc_slab {
     double *f;                  /* [6][ny][nx+1] ex ey ez bx by bz */
     double *j;                  /* [3][ny][nx+1] */
     double *ph;                 /* [ny][nx][nb] */
+    /* radiation transport mode (orc_set_rt) */
+    int rt_on;
+    orc_rt rt;
+    int nrx, nry, nrc, ncd, nord;
+    double *o_mu, *o_vy, *o_w;  /* [nord] direction cosines in the plane, share of isotropic emission */
+    double *F, *Gx, *Gy;        /* [nord][nb][nry][nrx] */
+    double *n_pub;              /* [nrc][nb] densities published to the cells */
+    double *c_chi, *c_emc, *c_w, *c_dE;   /* per PIC cell ([ncell][nb], [ncell] x 3) */
     uint32_t step;
     double tally[ORC_NT];
     uint64_t cnt[ORC_NC];
@@ -553,6 +561,8 @@ void orc_destroy(orc_slab *s)
     free(s->hv_tab); free(s->sigma); free(s->eos_T); free(s->eos_n); free(s->eos_Z);
     free(s->hv_b); free(s->sig_b); free(s->e); free(s->ion); free(s->f); free(s->j); free(s->ph);
     free(s->near);
+    free(s->o_mu); free(s->o_vy); free(s->o_w); free(s->F); free(s->Gx); free(s->Gy); free(s->n_pub);
+    free(s->c_chi); free(s->c_emc); free(s->c_w); free(s->c_dE);
     free(s);
 }
 
@@ -738,6 +748,397 @@ static void march(orc_slab *s)
     free(col);
 }
 
+/* ---------------- radiation transport (Sec. II, Eqs. 1a and 1b) ---------------- */
+/* Gauss-Legendre nodes and weights on (-1, 1) (Newton on the Legendre
+ * recurrence), nodes in descending order */
+static void gauss_legendre(int n, double *x, double *w)
+{
+    for (int i = 0; i < n; ++i) {
+        double z = cos(PI * (i + 0.75) / (n + 0.5)), pp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1; p1 = p2;
+            }
+            if (n == 1) { p1 = z; p0 = 1.0; }
+            pp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / pp;
+            z -= dz;
+            if (fabs(dz) < 1e-15) break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * pp * pp);
+    }
+}
+
+int orc_set_rt(orc_slab *s, const orc_rt *rt)
+{
+    const orc_params *p = &s->p;
+    const int R = rt->coarsen, d2 = p->ny > 1;
+    if (!s->have_pulse || R < 1 || p->nx % R || (d2 && p->ny % R) || rt->n_polar < 0 || rt->n_polar > 16 ||
+        (d2 && (rt->n_azimuth < 1 || rt->n_azimuth > 16)) || (rt->scheme != 0 && rt->scheme != 1))
+        return 1;
+    s->rt = *rt;
+    s->rt_on = 1;
+    s->nrx = p->nx / R;
+    s->nry = d2 ? p->ny / R : 1;
+    s->nrc = s->nrx * s->nry;
+    s->ncd = d2 ? R * R : R;
+    const int naz = d2 ? rt->n_azimuth : 1;
+    s->nord = 1 + rt->n_polar * naz;
+    const int nb = s->pulse.n_bins;
+    free(s->o_mu); free(s->o_vy); free(s->o_w);
+    s->o_mu = calloc(s->nord, sizeof(double));
+    s->o_vy = calloc(s->nord, sizeof(double));
+    s->o_w = calloc(s->nord, sizeof(double));
+    s->o_mu[0] = 1.0;                 /* the XFEL beam along +x: no share of isotropic emission */
+    if (rt->n_polar > 0) {
+        double *x = malloc(sizeof(double) * rt->n_polar), *a = malloc(sizeof(double) * rt->n_polar);
+        gauss_legendre(rt->n_polar, x, a);
+        for (int k = 0; k < rt->n_polar; ++k)
+            for (int j = 0; j < naz; ++j) {
+                const int o = 1 + k * naz + j;
+                s->o_mu[o] = x[k];
+                /* azimuth phi in (0, pi) about +x: n_z = sin(theta) sin(phi) >= 0,
+                 * the lower hemisphere is its mirror image */
+                s->o_vy[o] = d2 ? sqrt(1.0 - x[k] * x[k]) * cos(PI * (j + 0.5) / naz) : 0.0;
+                s->o_w[o] = 0.5 * a[k] / naz;
+            }
+        free(x); free(a);
+    }
+    const size_t nf = (size_t)s->nord * nb * s->nrc, nc = (size_t)p->nx * p->ny;
+    free(s->F); free(s->Gx); free(s->Gy); free(s->n_pub);
+    free(s->c_chi); free(s->c_emc); free(s->c_w); free(s->c_dE);
+    s->F = calloc(nf, sizeof(double));
+    s->Gx = calloc(nf, sizeof(double));
+    s->Gy = calloc(nf, sizeof(double));
+    s->n_pub = calloc((size_t)s->nrc * nb, sizeof(double));
+    s->c_chi = calloc(nc * nb, sizeof(double));
+    s->c_emc = calloc(nc, sizeof(double));
+    s->c_w = calloc(nc, sizeof(double));
+    s->c_dE = calloc(nc, sizeof(double));
+    return 0;
+}
+
+int orc_rt_ordinates(const orc_slab *s, double *mu, double *vy, double *w)
+{
+    for (int o = 0; o < s->nord; ++o) { mu[o] = s->o_mu[o]; vy[o] = s->o_vy[o]; w[o] = s->o_w[o]; }
+    return s->nord;
+}
+
+void orc_rt_get(const orc_slab *s, double *F, double *Gx, double *Gy)
+{
+    const size_t nf = (size_t)s->nord * s->pulse.n_bins * s->nrc;
+    memcpy(F, s->F, sizeof(double) * nf);
+    memcpy(Gx, s->Gx, sizeof(double) * nf);
+    memcpy(Gy, s->Gy, sizeof(double) * nf);
+}
+
+void orc_rt_set(orc_slab *s, const double *F, const double *Gx, const double *Gy)
+{
+    const size_t nf = (size_t)s->nord * s->pulse.n_bins * s->nrc;
+    memcpy(s->F, F, sizeof(double) * nf);
+    memcpy(s->Gx, Gx, sizeof(double) * nf);
+    memcpy(s->Gy, Gy, sizeof(double) * nf);
+}
+
+void orc_rt_cells(const orc_slab *s, double *chi, double *emc, double *wcell, double *dEc)
+{
+    const size_t nc = (size_t)s->p.nx * s->p.ny;
+    memcpy(chi, s->c_chi, sizeof(double) * nc * s->pulse.n_bins);
+    memcpy(emc, s->c_emc, sizeof(double) * nc);
+    memcpy(wcell, s->c_w, sizeof(double) * nc);
+    memcpy(dEc, s->c_dE, sizeof(double) * nc);
+}
+
+/* cubic Hermite pieces on one node interval, unit spacing, t in [0, 1]:
+ * value, slope, and integral from 0 to t */
+static double herm(double f0, double g0, double f1, double g1, double t)
+{
+    const double t2 = t * t, t3 = t2 * t;
+    return (2 * t3 - 3 * t2 + 1) * f0 + (t3 - 2 * t2 + t) * g0 + (-2 * t3 + 3 * t2) * f1 + (t3 - t2) * g1;
+}
+static double herm_d(double f0, double g0, double f1, double g1, double t)
+{
+    const double t2 = t * t;
+    return (6 * t2 - 6 * t) * f0 + (3 * t2 - 4 * t + 1) * g0 + (-6 * t2 + 6 * t) * f1 + (3 * t2 - 2 * t) * g1;
+}
+static double herm_i(double f0, double g0, double f1, double g1, double t)
+{
+    const double t2 = t * t, t3 = t2 * t, t4 = t3 * t;
+    return (0.5 * t4 - t3 + t) * f0 + (0.25 * t4 - 2.0 * t3 / 3.0 + 0.5 * t2) * g0 + (-0.5 * t4 + t3) * f1 +
+           (0.25 * t4 - t3 / 3.0) * g1;
+}
+
+typedef struct {
+    const double *f, *g;
+    int n, periodic, ng;
+    double nu;
+    const double *fin, *gin;
+} rtline;
+
+/* value and slope of node j of a line (ghosts outside [0, n)) */
+static void rt_node(const rtline *L, int j, double *fj, double *gj)
+{
+    if (L->periodic) { j %= L->n; if (j < 0) j += L->n; *fj = L->f[j]; *gj = L->g[j]; return; }
+    if (j >= 0 && j < L->n) { *fj = L->f[j]; *gj = L->g[j]; return; }
+    const int in_side = L->nu > 0 ? j < 0 : j >= L->n;
+    if (in_side) {
+        const int q = L->nu > 0 ? -j - 1 : j - L->n;
+        if (q < L->ng && L->fin) { *fj = L->fin[q]; *gj = L->gin ? L->gin[q] : 0.0; }
+        else { *fj = 0.0; *gj = 0.0; }
+        return;
+    }
+    *fj = 0.0;                          /* beyond the outflow face: empty */
+    *gj = 0.0;
+}
+
+/* integral of the Hermite reconstruction over [a, b] (node coordinates) */
+static double rt_integral(const rtline *L, double a, double b)
+{
+    double acc = 0.0;
+    int k = (int)floor(a);
+    while (k < b) {
+        const double lo = a > k ? a - k : 0.0, hi = b < k + 1 ? b - k : 1.0;
+        if (hi > lo) {
+            double f0, g0, f1, g1;
+            rt_node(L, k, &f0, &g0);
+            rt_node(L, k + 1, &f1, &g1);
+            acc += herm_i(f0, g0, f1, g1, hi) - herm_i(f0, g0, f1, g1, lo);
+        }
+        ++k;
+    }
+    return acc;
+}
+
+/* contents crossing the two faces of a line in one shift by nu nodes, as
+ * the linear split moves them (node j's content goes (1 - fr) to j + m and
+ * fr to j + m + 1, mirrored for nu < 0): the inflow ghosts' parts that land
+ * inside or beyond entered, every part that lands beyond the far face left */
+static void split_flows(const rtline *L, int n, double nu, double *in, double *out)
+{
+    const double a = fabs(nu);
+    const int m = (int)floor(a), sgn = nu >= 0 ? 1 : -1;
+    const double fr = a - m;
+    for (int j = -(m + 1); j < n + m + 1; ++j) {
+        if ((sgn > 0 && j >= n) || (sgn < 0 && j < 0)) continue;
+        double v, dummy;
+        rt_node(L, j, &v, &dummy);
+        if (v == 0.0) continue;
+        const int in_src = j < 0 || j >= n;
+        const int d[2] = {j + sgn * m, j + sgn * (m + 1)};
+        const double part[2] = {(1.0 - fr) * v, fr * v};
+        for (int q = 0; q < 2; ++q) {
+            const int inside = d[q] >= 0 && d[q] < n, far = sgn > 0 ? d[q] >= n : d[q] < 0;
+            if (in_src && (inside || far)) *in += part[q];
+            if (far) *out += part[q];
+        }
+    }
+}
+
+void orc_rt_line(double *f, double *g, double *gt, int n, double nu, int scheme, int periodic,
+                 const double *fin, const double *gin, int ng, double *in, double *out)
+{
+    double *f0 = malloc(sizeof(double) * n), *g0 = malloc(sizeof(double) * n), *t0 = malloc(sizeof(double) * n);
+    memcpy(f0, f, sizeof(double) * n);
+    memcpy(g0, g, sizeof(double) * n);
+    if (gt) memcpy(t0, gt, sizeof(double) * n);
+    else memset(t0, 0, sizeof(double) * n);
+    rtline L = {f0, g0, n, periodic, ng, nu, fin, gin};
+    rtline T = {t0, t0, n, periodic, ng, nu, NULL, NULL};   /* transverse slope: zero inflow */
+    *in = *out = 0.0;
+    if (scheme == 1) {
+        /* the ballistic march's split: node j's content goes (1 - fr) to
+         * j + m and fr to j + m + 1 (mirrored for nu < 0) */
+        const double a = fabs(nu);
+        const int m = (int)floor(a), sgn = nu >= 0 ? 1 : -1;
+        const double fr = a - m;
+        for (int i = 0; i < n; ++i) {
+            double v0, v1, dummy;
+            rt_node(&L, i - sgn * m, &v0, &dummy);
+            rt_node(&L, i - sgn * (m + 1), &v1, &dummy);
+            f[i] = (1.0 - fr) * v0 + fr * v1;
+        }
+        if (!periodic) split_flows(&L, n, nu, in, out);
+        if (gt) memset(gt, 0, sizeof(double) * n);
+        memset(g, 0, sizeof(double) * n);
+    } else {
+        for (int i = 0; i < n; ++i) {
+            const double xd = i - nu;
+            const int k = (int)floor(xd);
+            const double t = xd - k;
+            double fa, ga, fb, gb;
+            rt_node(&L, k, &fa, &ga);
+            rt_node(&L, k + 1, &fb, &gb);
+            f[i] = herm(fa, ga, fb, gb, t);
+            g[i] = herm_d(fa, ga, fb, gb, t);
+            if (gt) {
+                double ta, tb, dummy;
+                rt_node(&T, k, &ta, &dummy);
+                rt_node(&T, k + 1, &tb, &dummy);
+                gt[i] = (1.0 - t) * ta + t * tb;
+            }
+        }
+        /* faces crossed: the contents the shift carries across them, as the
+         * linear split moves them (exact at integer Courant numbers, where
+         * CIP is an exact shift too); what CIP's cubic update of the
+         * interior adds to or removes from that is the scheme's own gain */
+        if (!periodic) split_flows(&L, n, nu, in, out);
+    }
+    free(f0); free(g0); free(t0);
+}
+
+/* photon density (n_ref units) of bin b entering x = 0 at time tau, at height y (nm) */
+static double rt_source(const orc_slab *s, int b, double tau, double y)
+{
+    double I = pulse_I(&s->pulse, tau);
+    double n = I / (C_CM_FS * 1e15 * s->hv_b[b] * Q_E) / s->pulse.n_bins;
+    if (s->pulse.spot_sigma > 0.0 && s->p.ny > 1) {
+        double yc = y - 0.5 * s->p.ny * s->p.dy;
+        n *= exp(-0.5 * yc * yc / (s->pulse.spot_sigma * s->pulse.spot_sigma));
+    }
+    return n / s->p.n_ref;
+}
+
+static int rt_cell(const orc_slab *s, int c)
+{
+    const int R = s->rt.coarsen, i = c % s->p.nx, j = c / s->p.nx;
+    return (s->p.ny > 1 ? (j / R) * s->nrx : 0) + i / R;
+}
+
+/* One rad step of the radiation field, before the cells' physics of the
+ * step: (1) gather what the cells recorded at the last rad step (opacity,
+ * photon energy taken by photoionization, electron weight, K-alpha photons
+ * added to their photon numbers); (2) absorb the field over dt_rad with
+ * that opacity; (3) the energy absorbed beyond what the photoionization
+ * events took is given to the bulk electrons of the rad cell (negative:
+ * taken), shared among its PIC cells by electron weight, at their next
+ * rad step; (4) K-alpha photons join the diffuse ordinates isotropically;
+ * (5) advect every ordinate and bin (x, then y in 2D); (6) publish the
+ * photon densities to the PIC cells. */
+static void rt_step(orc_slab *s)
+{
+    const orc_params *p = &s->p;
+    const int nb = s->pulse.n_bins, nrc = s->nrc, nord = s->nord, ncell = p->nx * p->ny, ncd = s->ncd;
+    const double dtr = p->rad_every * p->dt;
+    const double dxr = p->dx * s->rt.coarsen, dyr = p->dy * s->rt.coarsen;
+    double *chi = calloc((size_t)nrc * nb, sizeof(double)), *ka = calloc((size_t)nrc * nb, sizeof(double));
+    double *emc = calloc(nrc, sizeof(double)), *W = calloc(nrc, sizeof(double));
+    /* (1) */
+    for (int c = 0; c < ncell; ++c) {
+        const int r = rt_cell(s, c);
+        emc[r] += s->c_emc[c];
+        W[r] += s->c_w[c];
+        for (int b = 0; b < nb; ++b) {
+            chi[(size_t)r * nb + b] += s->c_chi[(size_t)c * nb + b] / ncd;
+            ka[(size_t)r * nb + b] += (s->ph[(size_t)c * nb + b] - s->n_pub[(size_t)r * nb + b]) / ncd;
+        }
+    }
+    /* (2), (3) */
+    for (int r = 0; r < nrc; ++r) {
+        double A = 0.0;
+        for (int b = 0; b < nb; ++b) {
+            const double e = exp(-chi[(size_t)r * nb + b] * C_CM_FS * dtr);
+            for (int o = 0; o < nord; ++o) {
+                const size_t q = ((size_t)o * nb + b) * nrc + r;
+                A += s->F[q] * (1.0 - e) * ncd * s->hv_b[b];
+                s->F[q] *= e; s->Gx[q] *= e; s->Gy[q] *= e;
+            }
+        }
+        const double dE = A - emc[r];
+        s->tally[ORC_T_RT_PEND] += A;      /* the events' photons were owed (see cell_physics) */
+        if (dE == 0.0) continue;
+        for (int c = 0; c < ncell; ++c) {
+            if (rt_cell(s, c) != r) continue;
+            s->c_dE[c] += W[r] > 0.0 ? dE * s->c_w[c] / W[r] : dE / ncd;
+        }
+    }
+    /* (4) */
+    for (int r = 0; r < nrc; ++r)
+        for (int b = 0; b < nb; ++b) {
+            const double k = ka[(size_t)r * nb + b];
+            if (k == 0.0) continue;
+            if (nord > 1) {
+                for (int o = 1; o < nord; ++o) s->F[((size_t)o * nb + b) * nrc + r] += k * s->o_w[o];
+            } else {
+                s->tally[ORC_T_KA_ESC] += k * ncd * s->hv_b[b];
+            }
+        }
+    /* (5) */
+    const double tprev = (double)s->step * p->dt - dtr;
+    const int mx = s->nrx > s->nry ? s->nrx : s->nry;
+    double *f = malloc(sizeof(double) * mx), *g = malloc(sizeof(double) * mx), *gt = malloc(sizeof(double) * mx);
+    for (int o = 0; o < nord; ++o)
+        for (int b = 0; b < nb; ++b) {
+            double *F = s->F + ((size_t)o * nb + b) * nrc, *Gx = s->Gx + ((size_t)o * nb + b) * nrc;
+            double *Gy = s->Gy + ((size_t)o * nb + b) * nrc;
+            double before = 0.0, after = 0.0, inflow = 0.0, outflow = 0.0;
+            for (int r = 0; r < nrc; ++r) before += F[r];
+            const double nux = C_NM_FS * dtr * s->o_mu[o] / dxr;
+            for (int ry = 0; ry < s->nry; ++ry) {
+                int ng = 0;
+                double fin[64], gin[64];
+                if (o == 0 && nux > 0) {
+                    const double y = (ry + 0.5) * dyr;
+                    ng = (int)floor(nux) + 3;
+                    if (ng > 62) ng = 62;
+                    for (int q = 0; q < ng; ++q) {
+                        const int j = -1 - q;
+                        const double xa = (j + 0.5) * dxr, xm = (j - 0.5) * dxr, xp = (j + 1.5) * dxr;
+                        fin[q] = rt_source(s, b, tprev - xa / C_NM_FS, y);
+                        gin[q] = 0.5 * (rt_source(s, b, tprev - xp / C_NM_FS, y) - rt_source(s, b, tprev - xm / C_NM_FS, y));
+                    }
+                }
+                for (int rx = 0; rx < s->nrx; ++rx) {
+                    f[rx] = F[(size_t)ry * s->nrx + rx]; g[rx] = Gx[(size_t)ry * s->nrx + rx];
+                    gt[rx] = Gy[(size_t)ry * s->nrx + rx];
+                }
+                double in, out;
+                orc_rt_line(f, g, gt, s->nrx, nux, s->rt.scheme, 0, ng ? fin : NULL, ng ? gin : NULL, ng, &in, &out);
+                for (int rx = 0; rx < s->nrx; ++rx) {
+                    F[(size_t)ry * s->nrx + rx] = f[rx]; Gx[(size_t)ry * s->nrx + rx] = g[rx];
+                    Gy[(size_t)ry * s->nrx + rx] = gt[rx];
+                }
+                inflow += in;
+                outflow += out;
+                if (nux > 0) s->tally[ORC_T_TRANS] += out * ncd * s->hv_b[b];
+                else s->tally[ORC_T_BACK] += out * ncd * s->hv_b[b];
+            }
+            s->tally[ORC_T_INC] += inflow * ncd * s->hv_b[b];
+            if (s->nry > 1 && s->o_vy[o] != 0.0) {
+                const double nuy = C_NM_FS * dtr * s->o_vy[o] / dyr;
+                for (int rx = 0; rx < s->nrx; ++rx) {
+                    for (int ry = 0; ry < s->nry; ++ry) {
+                        f[ry] = F[(size_t)ry * s->nrx + rx]; g[ry] = Gy[(size_t)ry * s->nrx + rx];
+                        gt[ry] = Gx[(size_t)ry * s->nrx + rx];
+                    }
+                    double in, out;
+                    orc_rt_line(f, g, gt, s->nry, nuy, s->rt.scheme, 1, NULL, NULL, 0, &in, &out);
+                    for (int ry = 0; ry < s->nry; ++ry) {
+                        F[(size_t)ry * s->nrx + rx] = f[ry]; Gy[(size_t)ry * s->nrx + rx] = g[ry];
+                        Gx[(size_t)ry * s->nrx + rx] = gt[ry];
+                    }
+                }
+            }
+            for (int r = 0; r < nrc; ++r) after += F[r];
+            s->tally[ORC_T_RT_NUM] += (after - before - inflow + outflow) * ncd * s->hv_b[b];
+        }
+    free(f); free(g); free(gt);
+    /* (6) */
+    for (int r = 0; r < nrc; ++r)
+        for (int b = 0; b < nb; ++b) {
+            double n = 0.0;
+            for (int o = 0; o < nord; ++o) n += s->F[((size_t)o * nb + b) * nrc + r];
+            s->n_pub[(size_t)r * nb + b] = n;
+        }
+    for (int c = 0; c < ncell; ++c) {
+        const int r = rt_cell(s, c);
+        for (int b = 0; b < nb; ++b) s->ph[(size_t)c * nb + b] = s->n_pub[(size_t)r * nb + b];
+    }
+    free(chi); free(ka); free(emc); free(W);
+}
+
 /* ---------------- per-cell physics ---------------- */
 typedef struct {
     double X, Y, u[3], w; uint64_t id;
@@ -745,7 +1146,7 @@ typedef struct {
 
 typedef struct {
     newe *ne; int n, cap;
-    double tally_ion, ka_esc;
+    double tally_ion, ka_esc, rt_applied;
     uint64_t cnt[ORC_NC];
     /* decision trace of the cell (see orc_trace) */
     double rel; uint32_t step; int cell;
@@ -886,6 +1287,37 @@ static void cell_physics(orc_slab *S, int cell, int *eidx, int ne, int *iidx, in
     }
 
     for (int k = 0; k < ne; ++k) S->e[pe[k]].cs = 0.0;
+
+    /* 1b. radiation transport mode, rad steps: the energy the radiation
+     * field gave up to (or took from) this cell's share of its rad cell
+     * goes to the bulk electrons by one factor on their kinetic energy
+     * (Sec. II: uniform heating or cooling); at most 90 % of their energy
+     * is taken, the rest waits for the next rad step */
+    const int rtmode = S->rt_on && rad;
+    if (rtmode) {
+        const int nbr = S->pulse.n_bins;
+        for (int b = 0; b < nbr; ++b) S->c_chi[(size_t)cell * nbr + b] = 0.0;
+        S->c_emc[cell] = 0.0;
+        const double dE = S->c_dE[cell];
+        if (dE != 0.0) {
+            double K = 0.0;
+            for (int k = 0; k < ne; ++k) {
+                const elec *e = &S->e[pe[k]];
+                const double ke = kin(e->u, 1.0);
+                if (p->E_bulk <= 0.0 || ke < p->E_bulk) K += e->w * ke;
+            }
+            if (K > 0.0) {
+                const double dEa = dE < -0.9 * K ? -0.9 * K : dE;
+                const double f = 1.0 + dEa / K;
+                for (int k = 0; k < ne; ++k) {
+                    elec *e = &S->e[pe[k]];
+                    if (p->E_bulk <= 0.0 || kin(e->u, 1.0) < p->E_bulk) scale_ke(e->u, f);
+                }
+                S->c_dE[cell] = dE - dEa;
+                o->rt_applied += dEa;
+            }
+        }
+    }
 
     /* 2. moments (FP64) */
     double We = 0, Wb = 0, Kb = 0, Q = 0;
@@ -1123,10 +1555,27 @@ static void cell_physics(orc_slab *S, int cell, int *eidx, int ne, int *iidx, in
             double cph = C_CM_FS * dtr * p->n_ref;
             double *n0 = malloc(sizeof(double) * nb);
             memcpy(n0, ph, sizeof(double) * nb);
+            /* photons left in the bins for the events of this cell: the
+             * cell's own photon numbers, or in transport mode a copy (the
+             * field loses the absorbed photons through the opacity instead) */
+            double *avail = rtmode ? malloc(sizeof(double) * nb) : ph;
+            if (rtmode) memcpy(avail, ph, sizeof(double) * nb);
+            double *chi = rtmode ? S->c_chi + (size_t)cell * nb : NULL;
             for (int k = 0; k < ni; ++k) {
                 ionr *q = &S->ion[pi[k]];
                 int nbd = 13 - q->Z, occ[ORC_NS];
                 if (nbd <= 0 || !orc_occ(nbd, q->nK, occ)) continue;
+                if (chi) {
+                    /* opacity of the cell in each bin: sum over subshells
+                     * of N_s sigma_s above the lowered edge (Eq. 2's
+                     * absorption), for the radiation transport */
+                    for (int q2 = 0; q2 < ORC_NS; ++q2) {
+                        if (!occ[q2]) continue;
+                        const double ed = lowered(t, q->Z, q2, dE[q->Z]);
+                        for (int b = 0; b < nb; ++b)
+                            if (S->hv_b[b] > ed) chi[b] += p->n_ref * wi * occ[q2] * S->sig_b[q2 * nb + b];
+                    }
+                }
                 double ra[4], rb[4];
                 draw4(seed, q->id, step, PU_PHOTO_A, ra);
                 draw4(seed, q->id, step, PU_PHOTO_B, rb);
@@ -1156,10 +1605,17 @@ static void cell_physics(orc_slab *S, int cell, int *eidx, int ne, int *iidx, in
                 }
                 if (bin < 0) bin = lastpos;
                 if (bin < 0) continue;
-                decide(o, 0, ORC_N_PH_PART, -1, 0, ph[bin], wi);
-                double g = ph[bin] < wi ? ph[bin] : wi;
+                decide(o, 0, ORC_N_PH_PART, -1, 0, avail[bin], wi);
+                double g = avail[bin] < wi ? avail[bin] : wi;
                 if (g <= 0.0) continue;
-                ph[bin] -= g;
+                avail[bin] -= g;
+                if (rtmode) {
+                    /* the plasma takes these photons' energy now; the field
+                     * gives it up through its opacity at the next transport
+                     * step: owed until then */
+                    S->c_emc[cell] += g * S->hv_b[bin];
+                    o->rt_applied += g * S->hv_b[bin];
+                }
                 if (g == wi) {
                     remove_electron(&q->Z, &q->nK, sub);
                 } else {
@@ -1179,6 +1635,7 @@ static void cell_physics(orc_slab *S, int cell, int *eidx, int ne, int *iidx, in
                 o->cnt[ORC_C_PH0 + sub]++;
             }
             free(n0);
+            if (rtmode) free(avail);
         }
         if (p->flags & ORC_F_DECAY) {
             for (int k = 0; k < ni; ++k) {
@@ -1228,6 +1685,14 @@ static void cell_physics(orc_slab *S, int cell, int *eidx, int ne, int *iidx, in
     }
     /* 7. rad step, forced-thermalization variant */
     if (rad && (p->flags & ORC_F_THERM)) thermalize(S, pe, ne, o, seed, step);
+    /* 8. transport mode: the cell's electron weight, its share of the next
+     * heating of its rad cell */
+    if (rtmode) {
+        double W = 0.0;
+        for (int k = 0; k < ne; ++k) if (S->e[pe[k]].alive) W += S->e[pe[k]].w;
+        for (int k = 0; k < o->n; ++k) W += o->ne[k].w;
+        S->c_w[cell] = W;
+    }
     free(pe); free(pi);
 }
 
@@ -1426,7 +1891,8 @@ void orc_step(orc_slab *s, int nsteps, int nthreads)
 #endif
     for (int it = 0; it < nsteps; ++it) {
         int rad = p->rad_every > 0 && (s->step % (uint32_t)p->rad_every) == 0;
-        if (rad && (p->flags & ORC_F_PHOTO) && s->have_pulse) march(s);
+        if (rad && s->rt_on) rt_step(s);
+        else if (rad && (p->flags & ORC_F_PHOTO) && s->have_pulse) march(s);
 
         /* bucket by cell (counting sort) */
         int *cse = calloc(ncell + 1, sizeof(int)), *csi = calloc(ncell + 1, sizeof(int));
@@ -1459,6 +1925,7 @@ void orc_step(orc_slab *s, int nsteps, int nthreads)
             }
             s->tally[ORC_T_ION] += co[c].tally_ion;
             s->tally[ORC_T_KA_ESC] += co[c].ka_esc;
+            s->tally[ORC_T_RT_PEND] -= co[c].rt_applied;
             for (int q = 0; q < ORC_NC; ++q) s->cnt[q] += co[c].cnt[q];
             s->ndraw += co[c].ndraw;
             s->ndec += co[c].ndec;
@@ -1517,7 +1984,18 @@ void orc_tallies(orc_slab *s, double *t, uint64_t *c)
     double kee = 0.0, kei = 0.0, ph = 0.0, fe = 0.0;
     for (int k = 0; k < s->ne; ++k) kee += s->e[k].w * kin(s->e[k].u, 1.0);
     for (int k = 0; k < s->ni; ++k) kei += p->w_ion * kin(s->ion[k].u, p->m_ion);
-    if (s->have_pulse) {
+    if (s->have_pulse && s->rt_on) {
+        /* the rad field, plus the K-alpha photons the cells added since it
+         * was published */
+        const int nb = s->pulse.n_bins;
+        for (int o = 0; o < s->nord; ++o)
+            for (int b = 0; b < nb; ++b)
+                for (int r = 0; r < s->nrc; ++r)
+                    ph += s->F[((size_t)o * nb + b) * s->nrc + r] * s->ncd * s->hv_b[b];
+        for (int c = 0; c < p->nx * p->ny; ++c)
+            for (int b = 0; b < nb; ++b)
+                ph += (s->ph[(size_t)c * nb + b] - s->n_pub[(size_t)rt_cell(s, c) * nb + b]) * s->hv_b[b];
+    } else if (s->have_pulse) {
         int nb = s->pulse.n_bins;
         for (size_t q = 0; q < (size_t)p->ny * p->nx * nb; ++q) ph += s->ph[q] * s->hv_b[q % nb];
     }

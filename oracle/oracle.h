@@ -58,7 +58,11 @@ typedef struct {
 
 /* energy tallies (weighted eV, units n_ref*V_cell) and event counters */
 enum { ORC_T_KE_E, ORC_T_KE_I, ORC_T_ION, ORC_T_PHOT, ORC_T_INC, ORC_T_TRANS,
-       ORC_T_KA_ESC, ORC_T_ESC, ORC_T_FIELD, ORC_NT };
+       ORC_T_KA_ESC, ORC_T_ESC, ORC_T_FIELD,
+       ORC_T_BACK,        /* radiation leaving through x = 0 (transport mode) */
+       ORC_T_RT_NUM,      /* field energy the transport scheme itself gained (CIP is not conservative) */
+       ORC_T_RT_PEND,     /* energy on its way from the radiation field to the bulk electrons */
+       ORC_NT };
 enum { ORC_C_ION, ORC_C_ION_REJ, ORC_C_REC, ORC_C_PH0, ORC_C_PH1, ORC_C_PH2,
        ORC_C_PH3, ORC_C_PH4, ORC_C_PART, ORC_C_AUG, ORC_C_KA, ORC_C_PGT1,
        ORC_C_ESC_E, ORC_C_ESC_I, ORC_C_EE, ORC_C_EI, ORC_NC };
@@ -98,6 +102,43 @@ orc_slab *orc_create(const orc_params *p, const orc_tables *t);
 void orc_destroy(orc_slab *s);
 void orc_set_pulse(orc_slab *s, const orc_pulse *pl);
 void orc_set_step(orc_slab *s, uint32_t n);
+
+/* Radiation transport mode (Sec. II, Eqs. 1a and 1b): the photon field is
+ * the specific intensity on a rad grid `coarsen` times coarser than the PIC
+ * grid, in discrete ordinates (the XFEL beam along +x and Gauss-Legendre
+ * polar nodes x azimuths of the upper hemisphere, the lower one folded in
+ * by symmetry), advected every rad step by the CIP scheme (scheme 0) or by
+ * the conservative linear split of the ballistic march (scheme 1);
+ * absorbed with the opacity of subshell photoionization, fed by K-alpha
+ * emission; the energy the field loses to absorption beyond what the
+ * Monte-Carlo photoionization events took heats (or cools) the bulk
+ * electrons of the rad cell uniformly at the next rad step.  Set after
+ * orc_set_pulse and before the first step; nx (and ny in 2D) must be
+ * multiples of coarsen. */
+typedef struct {
+    int coarsen;       /* PIC cells per rad cell along x (and y) */
+    int n_polar;       /* Gauss-Legendre nodes of mu = cos(theta) from +x (0: the beam only) */
+    int n_azimuth;     /* azimuths in (0, pi) per polar node (2D; ignored in 1D) */
+    int scheme;        /* 0 CIP, 1 linear split */
+} orc_rt;
+int orc_set_rt(orc_slab *s, const orc_rt *rt);   /* 0 on success */
+int orc_rt_ordinates(const orc_slab *s, double *mu, double *vy, double *w);   /* returns the count */
+/* rad field: photon density (n_ref units) per ordinate, bin and rad cell,
+ * [nord][nb][nry][nrx]; the CIP derivatives along x and y the same */
+void orc_rt_get(const orc_slab *s, double *F, double *Gx, double *Gy);
+void orc_rt_set(orc_slab *s, const double *F, const double *Gx, const double *Gy);
+/* one CIP (scheme 0) or linear (scheme 1) advection of a line of n nodes by
+ * nu nodes: f, g in place; fin/gin: values of the inflow ghost nodes
+ * j = -1, -2, ... (nu > 0) or n, n+1, ... (nu < 0), ng of them; outflow
+ * ghosts repeat the edge value with zero slope.  in/out: content (node
+ * units) that crossed the inflow and outflow faces.  periodic: wrap, no
+ * ghosts. */
+void orc_rt_line(double *f, double *g, double *gt, int n, double nu, int scheme, int periodic,
+                 const double *fin, const double *gin, int ng, double *in, double *out);
+/* per PIC cell after the last rad step (transport mode): opacity per bin
+ * (cm^-1), photon energy taken by photoionization events, electron weight,
+ * and the energy still to be given to the cell's bulk electrons */
+void orc_rt_cells(const orc_slab *s, double *chi, double *emc, double *wcell, double *dEc);
 uint32_t orc_get_step(const orc_slab *s);
 void orc_load_electrons(orc_slab *s, int n, const double *X, const double *Y,
                         const double *u, const double *w, const uint64_t *id);
