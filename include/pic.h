@@ -133,6 +133,16 @@ typedef struct {
      * K-alpha, P > 1 warnings, escaped e / i, e-e and e-i collisions */
     uint64_t counts[16];
     int64_t n_e, n_i;
+    /* radiation transport mode (pic_rt; 0 otherwise): radiation energy
+     * that left through x = 0, field energy the transport scheme itself
+     * gained (CIP is not conservative; the contents crossing the faces are
+     * counted by the linear split), and energy owed between the field and
+     * the electrons (photons taken by photoionization events before the
+     * field's opacity removed them, absorption beyond the events not yet
+     * given to the bulk electrons).  Conserved: ke_e + ke_i + e_ion +
+     * e_phot + e_ka_esc + e_trans + e_back + e_esc + e_field - e_inc -
+     * e_rt_num + e_rt_pend (up to the field solver's own drift). */
+    double e_back, e_rt_num, e_rt_pend;
 } pic_diag;
 
 /* Bytes of device memory pic_init needs for this slab. */
@@ -148,6 +158,44 @@ pic_status pic_init(pic_ctx **out, const pic_grid *g, const pic_species *s,
 /* Set the XFEL pulse (Sec. III Eq. 2 inputs); may be called before any
  * step.  Without a pulse photoionization sees no photons. */
 pic_status pic_source(pic_ctx *c, const pic_pulse *p);
+
+/* Radiation transport (Sec. II, Eqs. 1a and 1b), instead of the ballistic
+ * march of the pulse: the photon field is the photon density per discrete
+ * ordinate and bin on a rad grid `coarsen` times coarser than the PIC grid
+ * (the rad cell of the paper), advanced once per rad step: absorbed with
+ * the opacity of subshell photoionization that the ions of each rad cell
+ * present (Eq. 2's cross sections above the lowered edges), fed by the
+ * K-alpha photons of the decays (isotropic, into the diffuse ordinates),
+ * and advected by the CIP scheme (the intensity with its derivative,
+ * cubic Hermite at the departure point; scheme 0) or by the march's linear
+ * split (scheme 1).  The energy the field loses to its opacity beyond what
+ * the Monte-Carlo photoionization events took (Eq. 1b's dE_ij) heats the
+ * rad cell's bulk electrons uniformly at the next rad step (cools them when
+ * negative), shared among its PIC cells by electron weight.  Ordinates:
+ * the XFEL beam along +x, then n_polar Gauss-Legendre nodes of mu =
+ * cos(theta) times n_azimuth azimuths in (0, pi) (2D; the lower hemisphere
+ * is the mirror image).  Single-slab contexts only, after pic_source; nx
+ * (and ny in 2D) multiples of coarsen, at most 4096 rad cells along each
+ * axis, n_polar 0..16, n_azimuth 1..16.  The context allocates the field
+ * (cudaMalloc) and frees it in pic_free.  PIC_ERR_STATE without a pulse,
+ * on a batch context or when already on; PIC_ERR_ARG for invalid sizes. */
+typedef struct {
+    int coarsen;       /* PIC cells per rad cell along x (and along y in 2D) */
+    int n_polar;       /* diffuse polar nodes (0: the beam alone) */
+    int n_azimuth;     /* azimuths per polar node (2D) */
+    int scheme;        /* 0 CIP, 1 linear split */
+} pic_rt_config;
+pic_status pic_rt(pic_ctx *c, const pic_rt_config *rt);
+/* The rad field and its CIP slopes along x and y, [nord][n_bins][nry][nrx]
+ * (nord = 1 + n_polar * n_azimuth, n_azimuth = 1 in 1D), photon densities
+ * in units of n_ref; caller-allocated.  Synchronizes. */
+pic_status pic_rt_get(pic_ctx *c, double *F, double *Gx, double *Gy);
+pic_status pic_rt_set(pic_ctx *c, const double *F, const double *Gx, const double *Gy);
+/* What each PIC cell recorded at the last rad step for the transport:
+ * opacity per bin (cm^-1, [ncell][n_bins]), photon energy its
+ * photoionization events took, its electron weight, and the energy still
+ * due to its bulk electrons ([ncell] each).  Synchronizes. */
+pic_status pic_rt_cells(pic_ctx *c, double *chi, double *emc, double *w, double *dE);
 
 /* Load particles from host memory (absolute positions in cell units).
  * u is [n][3]; ids must be unique per species.  Replaces any particles. */

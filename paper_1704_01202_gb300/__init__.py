@@ -46,7 +46,8 @@ ABI_FUNCTIONS = ["pic_required_bytes", "pic_init", "pic_source", "pic_load_elect
                  "pic_batch_retire", "pic_batch_slot", "pic_batch_diagnostics", "pic_batch_counts",
                  "pic_batch_get_electrons", "pic_batch_get_ions", "pic_philox_check_static",
                  "pic_use_graphs", "pic_autotune", "pic_order_check",
-                 "pic_get_electrons64", "pic_get_ions64", "pic_real_bytes"]
+                 "pic_get_electrons64", "pic_get_ions64", "pic_real_bytes",
+                 "pic_rt", "pic_rt_get", "pic_rt_set", "pic_rt_cells"]
 
 
 def _sources():
@@ -121,7 +122,12 @@ class Diag(C.Structure):
                 ("ke_e", C.c_double), ("ke_i", C.c_double), ("e_ion", C.c_double), ("e_phot", C.c_double),
                 ("e_inc", C.c_double), ("e_trans", C.c_double), ("e_ka_esc", C.c_double),
                 ("e_esc", C.c_double), ("e_field", C.c_double), ("counts", C.c_uint64 * 16),
-                ("n_e", C.c_int64), ("n_i", C.c_int64)]
+                ("n_e", C.c_int64), ("n_i", C.c_int64),
+                ("e_back", C.c_double), ("e_rt_num", C.c_double), ("e_rt_pend", C.c_double)]
+
+
+class RTConfig(C.Structure):
+    _fields_ = [("coarsen", C.c_int), ("n_polar", C.c_int), ("n_azimuth", C.c_int), ("scheme", C.c_int)]
 
 
 _P = C.c_void_p
@@ -176,6 +182,10 @@ def lib(fp64: bool = False):
                                           C.POINTER(C.c_uint16)]
             L.pic_autotune.argtypes = [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]
             L.pic_timing.argtypes = [_P, C.c_int, _D, C.POINTER(C.c_int64)]
+            L.pic_rt.argtypes = [_P, C.POINTER(RTConfig)]
+            L.pic_rt_get.argtypes = [_P, _D, _D, _D]
+            L.pic_rt_set.argtypes = [_P, _D, _D, _D]
+            L.pic_rt_cells.argtypes = [_P, _D, _D, _D, _D]
             L.pic_batch_required_bytes.restype = C.c_size_t
             L.pic_batch_required_bytes.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
             L.pic_batch_init.argtypes = [C.POINTER(_P), C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(Tables),
@@ -299,6 +309,33 @@ class Slab:
     def set_pulse(self, pl):
         self._check(self.L.pic_source(self.h, C.byref(pulse_struct(pl))), "pic_source")
         self.n_bins = pl.n_bins
+
+    def set_rt(self, coarsen=5, n_polar=4, n_azimuth=2, scheme=0):
+        """Radiation transport instead of the ballistic march (pic_rt)."""
+        r = RTConfig(coarsen=coarsen, n_polar=n_polar, n_azimuth=n_azimuth, scheme=scheme)
+        self._check(self.L.pic_rt(self.h, C.byref(r)), "pic_rt")
+        self.rt = r
+        self.nrx = self.cfg.nx // coarsen
+        self.nry = self.cfg.ny // coarsen if self.cfg.ny > 1 else 1
+        self.nord = 1 + n_polar * (n_azimuth if self.cfg.ny > 1 else 1)
+
+    def rt_field(self):
+        shp = (self.nord, self.n_bins, self.nry, self.nrx)
+        F, Gx, Gy = np.zeros(shp), np.zeros(shp), np.zeros(shp)
+        self._check(self.L.pic_rt_get(self.h, _p(F), _p(Gx), _p(Gy)), "pic_rt_get")
+        return F, Gx, Gy
+
+    def set_rt_field(self, F, Gx=None, Gy=None):
+        F = np.ascontiguousarray(F, dtype=np.float64)
+        Gx = np.zeros_like(F) if Gx is None else np.ascontiguousarray(Gx, dtype=np.float64)
+        Gy = np.zeros_like(F) if Gy is None else np.ascontiguousarray(Gy, dtype=np.float64)
+        self._check(self.L.pic_rt_set(self.h, _p(F), _p(Gx), _p(Gy)), "pic_rt_set")
+
+    def rt_cells(self):
+        nc = self.cfg.nx * self.cfg.ny
+        chi, emc, w, dE = np.zeros((nc, self.n_bins)), np.zeros(nc), np.zeros(nc), np.zeros(nc)
+        self._check(self.L.pic_rt_cells(self.h, _p(chi), _p(emc), _p(w), _p(dE)), "pic_rt_cells")
+        return dict(chi=chi, emc=emc, w=w, dE=dE)
 
     def load(self, st):
         _ek, e = _electron_args(st)

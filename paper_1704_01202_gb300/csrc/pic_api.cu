@@ -24,6 +24,7 @@
 #include "pic_cellk.cuh"
 #include "pic_push.cuh"
 #include "pic_grid.cuh"
+#include "pic_rt.cuh"
 
 using namespace pic;
 
@@ -108,7 +109,7 @@ struct pic_ctx {
         const void *eA0, *iA0;
         int cur, ecur, grid_main, wpc, cap_ce, cap_ci, cap_new, nsub, t1_ce, t1_ci, t1_wpc, grid_t1;
         size_t smem_main;
-        bool march, field;
+        bool march, field, rt;
     };
     struct StepGraph {
         StepShape key{};
@@ -126,6 +127,9 @@ struct pic_ctx {
     cudaStream_t cap_stream = nullptr;
     StepGraph graphs[2];
     int graph_next = 0;
+    // radiation transport mode (pic_rt): device memory the context owns
+    void *rt_mem = nullptr;
+    int rt_nord = 0;
 };
 
 namespace {
@@ -406,7 +410,8 @@ pic_ctx::StepShape step_shape(const pic_ctx *c)
     k.grid_main = c->grid_main; k.wpc = c->wpc; k.smem_main = c->smem_main;
     k.cap_ce = c->cap_ce; k.cap_ci = c->cap_ci; k.cap_new = c->cap_new;
     k.t1_ce = c->t1_ce; k.t1_ci = c->t1_ci; k.t1_wpc = c->t1_wpc; k.grid_t1 = c->grid_t1;
-    k.march = any_active(c, PIC_F_PHOTO, true);
+    k.rt = c->slabs[0].rt != 0;
+    k.march = !k.rt && any_active(c, PIC_F_PHOTO, true);
     k.field = any_active(c, PIC_F_FIELD, false);
     k.nsub = 1;
     for (int q = 0; q < c->nslot; ++q)
@@ -418,7 +423,7 @@ bool same_shape(const pic_ctx::StepShape &a, const pic_ctx::StepShape &b)
 {
     return a.eA0 == b.eA0 && a.iA0 == b.iA0 && a.cur == b.cur && a.ecur == b.ecur && a.grid_main == b.grid_main &&
            a.wpc == b.wpc && a.smem_main == b.smem_main && a.cap_ce == b.cap_ce && a.cap_ci == b.cap_ci &&
-           a.cap_new == b.cap_new && a.march == b.march && a.field == b.field && a.nsub == b.nsub &&
+           a.cap_new == b.cap_new && a.march == b.march && a.field == b.field && a.nsub == b.nsub && a.rt == b.rt &&
            a.t1_ce == b.t1_ce && a.t1_ci == b.t1_ci && a.t1_wpc == b.t1_wpc && a.grid_t1 == b.grid_t1;
 }
 
@@ -431,7 +436,24 @@ pic_status launch_step(pic_ctx *c)
     CK(cudaMemsetAsync(c->cnt_e, 0, sizeof(int) * 4 * (size_t)c->ncell, st));   // cnt_e cnt_i fill_e fill_i
     CK(cudaMemsetAsync(c->counters, 0, sizeof(int) * CNT_STEP_ZERO, st));          // append, work counters, lists
     CK(cudaMemsetAsync(c->J, 0, sizeof(unsigned long long) * 3 * (size_t)c->npts, st));
-    if (shape.march) {
+    if (shape.rt) {
+        // radiation transport (single-slab contexts): the kernels return at
+        // once on steps that are not rad steps
+        const SlabDev &S = c->slabs[0];
+        RtArgs ra{c->d_slab, c->d_steps, c->photons, c->d_tally};
+        const int nrc = S.rt_nrx * S.rt_nry;
+        k_rt_cells<<<(nrc + 127) / 128, 128, 0, st>>>(ra);
+        const size_t smx = 3 * sizeof(double) * (RT_GHOST + S.rt_nrx);
+        k_rt_sweep<<<S.rt_nord * S.nb * S.rt_nry, RT_THREADS, smx, st>>>(ra, 0);
+        c->launches += 2;
+        if (S.ny > 1) {
+            const size_t smy = 3 * sizeof(double) * (RT_GHOST + S.rt_nry);
+            k_rt_sweep<<<S.rt_nord * S.nb * S.rt_nrx, RT_THREADS, smy, st>>>(ra, 1);
+            ++c->launches;
+        }
+        k_rt_publish<<<std::min((S.ncell + 255) / 256, c->nsm * 8), 256, 0, st>>>(ra);
+        ++c->launches;
+    } else if (shape.march) {
         MarchArgs m{c->d_slab, c->d_steps, c->row_slab, c->row_idx, c->photons, c->d_tally};
         k_march<<<c->nrows, 256, (size_t)c->max_row_nx * 8, st>>>(m);
         ++c->launches;
@@ -1009,7 +1031,9 @@ pic_status diag_slot(pic_ctx *c, int slot, pic_diag *out)
     k_diag<<<c->nsm * 4, 256, sizeof(real) * nv, st>>>(d);
     k_sumsq<<<c->nsm * 2, 256, 0, st>>>(c->E[c->ecur], c->npts, S.fld_off, c->slot_pts, c->diag_buf + nv);
     k_sumsq<<<c->nsm * 2, 256, 0, st>>>(c->B, c->npts, S.fld_off, c->slot_pts, c->diag_buf + nv);
-    if (S.nb > 0) {
+    if (S.nb > 0 && S.rt) {
+        k_rt_energy<<<c->nsm * 2, 256, 0, st>>>(c->d_slab + slot, c->photons, c->diag_buf + nv + 1);
+    } else if (S.nb > 0) {
         const real *hv = reinterpret_cast<const real *>(reinterpret_cast<const char *>(c->d_slab + slot) +
                                                           offsetof(SlabDev, hv_b));
         k_photon_energy<<<c->nsm * 2, 256, 0, st>>>(c->photons + S.ph_off, S.ncell, S.nb, hv, c->diag_buf + nv + 1);
@@ -1044,6 +1068,9 @@ pic_status diag_slot(pic_ctx *c, int slot, pic_diag *out)
     out->e_ka_esc = tl.ka_esc;
     out->e_esc = tl.esc;
     out->e_field = h[nv] * kEps0 * E0 * E0 / (2.0 * S.n_ref * 1e6 * kQe);
+    out->e_back = tl.back;
+    out->e_rt_num = tl.rt_num;
+    out->e_rt_pend = tl.rt_pend;
     for (int q = 0; q < 16; ++q) out->counts[q] = tl.cnt[q];
     out->n_e = ne;
     out->n_i = ni;
@@ -1625,8 +1652,122 @@ pic_status pic_free(pic_ctx *c)
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (cudaEvent_t e : c->cell_ev)
         if (e) cudaEventDestroy(e);
+    if (c->rt_mem) cudaFree(c->rt_mem);
     delete c;
     return PIC_OK;
+}
+
+pic_status pic_rt(pic_ctx *c, const pic_rt_config *rt)
+{
+    if (!c || !rt) return PIC_ERR_ARG;
+    if (c->batch) return fail(c, PIC_ERR_STATE, "radiation transport runs on single-slab contexts");
+    SlabDev &S = c->slabs[0];
+    const int R = rt->coarsen, d2 = S.ny > 1;
+    if (S.nb <= 0) return fail(c, PIC_ERR_STATE, "pic_rt needs a pulse (pic_source) first");
+    if (R < 1 || S.nx % R || (d2 && S.ny % R) || S.nx / R > 4096 || (d2 && S.ny / R > 4096) || rt->n_polar < 0 ||
+        rt->n_polar > 16 || (d2 && (rt->n_azimuth < 1 || rt->n_azimuth > 16)) || (rt->scheme != 0 && rt->scheme != 1))
+        return fail(c, PIC_ERR_ARG, "invalid radiation transport setting");
+    if (c->rt_mem) return fail(c, PIC_ERR_STATE, "radiation transport already on");
+    const int nb = S.nb, nrx = S.nx / R, nry = d2 ? S.ny / R : 1, nrc = nrx * nry;
+    const int naz = d2 ? rt->n_azimuth : 1, nord = 1 + rt->n_polar * naz;
+    // ordinates: the beam along +x, then Gauss-Legendre nodes of mu =
+    // cos(theta) (Newton on the Legendre recurrence) times azimuths in
+    // (0, pi); weights: share of the sphere (the lower half folded in)
+    std::vector<double> ord(3 * (size_t)nord, 0.0);
+    ord[0] = 1.0;
+    for (int k = 0; k < rt->n_polar; ++k) {
+        const int n = rt->n_polar;
+        double z = std::cos(kPi * (4.0 * k + 3.0) / (4.0 * n + 2.0)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double pm = 1.0, pc = z;                 // P_{j-1}, P_j
+            for (int j = 2; j <= n; ++j) {
+                const double pn = ((2.0 * j - 1.0) * z * pc - (j - 1.0) * pm) / j;
+                pm = pc; pc = pn;
+            }
+            dp = n * (z * pc - pm) / (z * z - 1.0);   // P_n'
+            const double step = pc / dp;
+            z -= step;
+            if (std::fabs(step) < 1e-15) break;
+        }
+        const double a = 2.0 / ((1.0 - z * z) * dp * dp);
+        for (int j = 0; j < naz; ++j) {
+            const int o = 1 + k * naz + j;
+            ord[o] = z;
+            ord[nord + o] = d2 ? std::sqrt(1.0 - z * z) * std::cos(kPi * (j + 0.5) / naz) : 0.0;
+            ord[2 * (size_t)nord + o] = 0.5 * a / naz;
+        }
+    }
+    const size_t nf = (size_t)nord * nb * nrc, ncell = (size_t)S.ncell;
+    // the sum of the pieces carved below, each rounded up to 256 bytes
+    const size_t bytes = 3 * al(nf * 8) + al((size_t)nrc * nb * 8) + al(ord.size() * 8) + al(ncell * nb * 4) +
+                         2 * al(ncell * 8) + al(ncell * 4);
+    char *mem = nullptr;
+    CK(cudaMalloc(&mem, bytes));
+    c->rt_mem = mem;
+    CK(cudaMemsetAsync(mem, 0, bytes, c->stream));
+    char *q = mem;
+    S.rt_F = (double *)q; q += al(nf * 8);
+    S.rt_Gx = (double *)q; q += al(nf * 8);
+    S.rt_Gy = (double *)q; q += al(nf * 8);
+    S.rt_npub = (double *)q; q += al((size_t)nrc * nb * 8);
+    double *d_ord = (double *)q; q += al(ord.size() * 8);
+    S.rt_ord = d_ord;
+    S.rt_chi = (float *)q; q += al(ncell * nb * 4);
+    S.rt_emc = (double *)q; q += al(ncell * 8);
+    S.rt_dE = (double *)q; q += al(ncell * 8);
+    S.rt_w = (float *)q;
+    S.rt = 1; S.rt_R = R; S.rt_nrx = nrx; S.rt_nry = nry; S.rt_nord = nord; S.rt_scheme = rt->scheme;
+    S.rt_ncd = d2 ? R * R : R;
+    c->rt_nord = nord;
+    CK(cudaMemcpyAsync(d_ord, ord.data(), ord.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_slab, &S, sizeof(SlabDev), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaFuncSetAttribute(k_rt_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)(3 * sizeof(double) * (RT_GHOST + std::max(nrx, nry)))));
+    CK(cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
+pic_status pic_rt_get(pic_ctx *c, double *F, double *Gx, double *Gy)
+{
+    if (!c || !F || !Gx || !Gy) return PIC_ERR_ARG;
+    if (!c->rt_mem) return fail(c, PIC_ERR_STATE, "radiation transport is off");
+    const SlabDev &S = c->slabs[0];
+    const size_t nf = (size_t)S.rt_nord * S.nb * S.rt_nrx * S.rt_nry;
+    CK(cudaMemcpyAsync(F, S.rt_F, nf * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(Gx, S.rt_Gx, nf * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(Gy, S.rt_Gy, nf * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return read_device_error(c);
+}
+
+pic_status pic_rt_set(pic_ctx *c, const double *F, const double *Gx, const double *Gy)
+{
+    if (!c || !F || !Gx || !Gy) return PIC_ERR_ARG;
+    if (!c->rt_mem) return fail(c, PIC_ERR_STATE, "radiation transport is off");
+    const SlabDev &S = c->slabs[0];
+    const size_t nf = (size_t)S.rt_nord * S.nb * S.rt_nrx * S.rt_nry;
+    CK(cudaMemcpyAsync(S.rt_F, F, nf * 8, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(S.rt_Gx, Gx, nf * 8, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(S.rt_Gy, Gy, nf * 8, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
+pic_status pic_rt_cells(pic_ctx *c, double *chi, double *emc, double *w, double *dE)
+{
+    if (!c || !chi || !emc || !w || !dE) return PIC_ERR_ARG;
+    if (!c->rt_mem) return fail(c, PIC_ERR_STATE, "radiation transport is off");
+    const SlabDev &S = c->slabs[0];
+    const size_t n = (size_t)S.ncell;
+    std::vector<float> hc(n * S.nb), hw(n);
+    CK(cudaMemcpyAsync(hc.data(), S.rt_chi, hc.size() * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(hw.data(), S.rt_w, n * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(emc, S.rt_emc, n * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(dE, S.rt_dE, n * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (size_t k = 0; k < hc.size(); ++k) chi[k] = hc[k];
+    for (size_t k = 0; k < n; ++k) w[k] = hw[k];
+    return read_device_error(c);
 }
 
 const char *pic_last_error(const pic_ctx *c) { return c ? c->err.c_str() : "no context"; }

@@ -12,6 +12,7 @@ namespace pic {
 struct WarpTally {
     int slab;
     dd ion, ka, esc;
+    dd rt;          // energy the electrons took from the radiation field (transport mode)
     int cnt[NCOUNT];
 };
 
@@ -22,10 +23,11 @@ __device__ __forceinline__ void tally_flush(const CellArgs &a, WarpTally &w, int
         if (dd_f(w.ion) != RF(0.0)) atomicAdd(&tl->ion, (double)w.ion.hi + (double)w.ion.lo);
         if (dd_f(w.ka) != RF(0.0)) atomicAdd(&tl->ka_esc, (double)w.ka.hi + (double)w.ka.lo);
         if (dd_f(w.esc) != RF(0.0)) atomicAdd(&tl->esc, (double)w.esc.hi + (double)w.esc.lo);
+        if (dd_f(w.rt) != RF(0.0)) atomicAdd(&tl->rt_pend, -((double)w.rt.hi + (double)w.rt.lo));
         for (int q = 0; q < NCOUNT; ++q)
             if (w.cnt[q]) atomicAdd(tl->cnt + q, (unsigned long long)w.cnt[q]);
     }
-    w.ion = w.ka = w.esc = dd_zero();
+    w.ion = w.ka = w.esc = w.rt = dd_zero();
     for (int q = 0; q < NCOUNT; ++q) w.cnt[q] = 0;
 }
 
@@ -278,6 +280,13 @@ __device__ __noinline__ void stage_photo(const CellArgs &a, const WarpMem &m, co
     __syncwarp();
     const real cph = (real)kCcmPerFs * dtr * c.nref;
     int c_part = 0, c_ph[NS] = {0, 0, 0, 0, 0};
+    // transport mode: the ions' opacity per bin (sum over occupied subshells
+    // of N_s sigma_s above the lowered edge) and the photon energy the
+    // events take; the field is not depleted here (its opacity does that)
+    const bool rtm = S.rt != 0;
+    real chi_l[MAXB];
+    for (int b = 0; b < MAXB; ++b) chi_l[b] = RF(0.0);
+    dd emc = dd_zero();
     for (int b0 = 0; b0 < ni; b0 += 32) {
         int t = b0 + lane;
         int sub = -1, bin = -1, sl = 0, Z = 0, nK = 0;
@@ -288,6 +297,13 @@ __device__ __noinline__ void stage_photo(const CellArgs &a, const WarpMem &m, co
             Z = st & 0xff; nK = (st >> 8) & 0xff;
             int occ[NS];
             if (Z < ZNUC && occupancy(ZNUC - Z, nK, occ)) {
+                if (rtm)
+                    for (int q = 0; q < NS; ++q) {
+                        if (!occ[q]) continue;
+                        const real ed = lowered_binding(T, Z, q, m.dE[Z]);
+                        for (int b = 0; b < nb; ++b)
+                            if (S.hv_b[b] > ed) chi_l[b] += (real)occ[q] * S.sig_b[q][b];
+                    }
                 U4 ra = draw(c.seed, (unsigned long long)m.iid[t], c.step, PU_PHOTO_A);
                 U4 rb = draw(c.seed, (unsigned long long)m.iid[t], c.step, PU_PHOTO_B);
                 real rs[NS] = {u01(ra.x), u01(ra.y), u01(ra.z), u01(ra.w), u01(rb.x)};
@@ -353,6 +369,7 @@ __device__ __noinline__ void stage_photo(const CellArgs &a, const WarpMem &m, co
             if (lane == 0) used[b] = dd_add(used[b], ub);
         }
         wt.ion = dd_add(wt.ion, wsum_dd(dd{ev ? g * edge : RF(0.0), RF(0.0)}));
+        if (rtm) emc = dd_add(emc, wsum_dd(dd{ev ? g * S.hv_b[bin] : RF(0.0), RF(0.0)}));
         unsigned bal = __ballot_sync(FULL, ev);
         if (ev) {
             int pos = nnew + __popc(bal & ((1u << lane) - 1u));
@@ -368,7 +385,19 @@ __device__ __noinline__ void stage_photo(const CellArgs &a, const WarpMem &m, co
         nnew = min(nnew + __popc(bal), a.cap_new);
         __syncwarp();
     }
-    if (lane < nb) { dd r = dd_sub(n0[lane], used[lane]); ph[lane] = ph2{r.hi, r.lo}; }
+    if (rtm) {
+        // opacity (cm^-1) and the events' photon energy, owed to the field
+        // until its opacity takes it at the next transport step
+        for (int b = 0; b < nb; ++b) {
+            const real v = wsum_f(chi_l[b]);
+            if (lane == 0) S.rt_chi[(size_t)c.lc * nb + b] = (float)(v * c.nref * c.wi);
+        }
+        if (lane == 0) S.rt_emc[c.lc] = (double)emc.hi + (double)emc.lo;
+        wt.rt = dd_add(wt.rt, emc);
+    } else if (lane < nb) {
+        dd r = dd_sub(n0[lane], used[lane]);
+        ph[lane] = ph2{r.hi, r.lo};
+    }
     wt.cnt[C_PART] += wsum_i(c_part);
     for (int q = 0; q < NS; ++q) wt.cnt[C_PH0 + q] += wsum_i(c_ph[q]);
     __syncwarp();
@@ -532,6 +561,38 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
 
     }
     __syncthreads();
+
+    if (on && rad && S.rt) {
+    // ---- transport mode: the energy the radiation field gave up to (or
+    //      took from) this cell goes to its bulk electrons by one factor on
+    //      their kinetic energy (Sec. II), at most 90 % of it taken; the rest
+    //      waits for the next rad step ----
+    if (lane < S.nb) S.rt_chi[(size_t)lc * S.nb + lane] = 0.0f;
+    if (lane == 0) S.rt_emc[lc] = 0.0;
+    const double dEc = S.rt_dE[lc];
+    if (dEc != 0.0) {
+        dd pk = dd_zero();
+        for (int k = lane; k < ne; k += 32) {
+            const real4 u = m.eu[m.eperm[k]];
+            const real ke = MC2 * gm1(u.x, u.y, u.z);
+            if (S.E_bulk <= RF(0.0) || ke < S.E_bulk) pk = dd_addf(pk, u.w * ke);
+        }
+        const real K = dd_f(wsum_dd(pk));
+        if (K > RF(0.0)) {
+            const real dEa = (real)dEc < -RF(0.9) * K ? -RF(0.9) * K : (real)dEc;
+            const real delta = -dEa / K;
+            for (int k = lane; k < ne; k += 32) {
+                const int sl = m.eperm[k];
+                real4 u = m.eu[sl];
+                const real ke = MC2 * gm1(u.x, u.y, u.z);
+                if (S.E_bulk <= RF(0.0) || ke < S.E_bulk) { scale_kinetic(u.x, u.y, u.z, delta); m.eu[sl] = u; }
+            }
+            if (lane == 0) S.rt_dE[lc] = dEc - (double)dEa;
+            wt.rt = dd_addf(wt.rt, dEa);
+        }
+    }
+    __syncwarp();
+    }
 
     if (on) {
     // ---- cell moments (Sec. II: T_e = 2/3 E_ave over bulk electrons) ----
@@ -799,10 +860,19 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
     //      canonical order, which the push kernel follows ----
     for (int k = lane; k < ne; k += 32) a.eord[e0 + k] = m.eperm[k];
     for (int k = lane; k < ni; k += 32) a.iord[i0 + k] = m.iperm[k];
+    real wsum = RF(0.0);
     for (int k = lane; k < ne; k += 32) {
         real4 u = m.eu[k];
         reinterpret_cast<real2 *>(a.e0 + e0 + k)[1] = make_real2(u.x, u.y);
         reinterpret_cast<real2 *>(a.e1 + e0 + k)[0] = make_real2(u.z, u.w);
+        wsum += u.w > RF(0.0) ? u.w : RF(0.0);
+    }
+    if (rad && S.rt) {
+        // transport mode: the cell's electron weight after the step, created
+        // electrons included: its share of the next heating of its rad cell
+        for (int k = lane; k < nnew; k += 32) wsum += m.nw[k].w;
+        wsum = wsum_f(wsum);
+        if (lane == 0) S.rt_w[lc] = (float)wsum;
     }
     for (int k = lane; k < ni; k += 32) {
         real4 u = m.iu[k];
@@ -864,7 +934,7 @@ __global__ void __launch_bounds__(256, 2) k_cell(CellArgs a)
     const int total = a.list ? *a.n_list : a.ncell;
     WarpTally wt;
     wt.slab = -1;
-    wt.ion = wt.ka = wt.esc = dd_zero();
+    wt.ion = wt.ka = wt.esc = wt.rt = dd_zero();
     for (int q = 0; q < NCOUNT; ++q) wt.cnt[q] = 0;
     for (;;) {
         __syncthreads();

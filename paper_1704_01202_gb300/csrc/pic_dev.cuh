@@ -200,10 +200,22 @@ struct SlabDev {
     real hv_b[MAXB];
     real sig_b[NS][MAXB];
     real bin_hw;
+    // radiation transport mode (single-slab contexts; rt = 0: the ballistic
+    // march): discrete ordinates on a rad grid rt_R times coarser
+    int rt, rt_R, rt_nrx, rt_nry, rt_nord, rt_scheme, rt_ncd;
+    double *rt_F, *rt_Gx, *rt_Gy;    // [nord][nb][nry][nrx] photon density (n_ref units), CIP slopes
+    double *rt_npub;                 // [nrc][nb] densities published to the cells
+    const double *rt_ord;            // [3][nord]: x and y direction cosines, share of isotropic emission
+    float *rt_chi;                   // [ncell][nb] opacity (cm^-1), written on rad steps by the cell kernel
+    double *rt_emc, *rt_dE;          // [ncell] photon energy the events took; energy due to the bulk electrons
+    float *rt_w;                     // [ncell] electron weight after the cell's rad step
 };
 
 struct SlabTally {
     double ion, ka_esc, esc, inc, trans;
+    // radiation transport: energy leaving through x = 0, the transport
+    // scheme's own gain, energy owed between the field and the electrons
+    double back, rt_num, rt_pend;
     unsigned long long cnt[NCOUNT];
 };
 
