@@ -302,6 +302,7 @@ def run_gpu(args):
     del st
     torch.cuda.empty_cache()
     foil = run_foil(pkg, tab, args) if args.foil_steps > 0 and args.workload != "foil" else None
+    rt = run_rt(pkg, tab, args) if args.rt_steps > 0 else None
     ensemble = run_ensemble(pkg, tab, args, rank) if args.ensemble > 0 else None
     served = run_served(pkg, tab, args) if args.serve_n > 0 else None
     kedge_scan = run_kedge(pkg, tab, args) if args.kedge_points > 0 else None
@@ -323,11 +324,51 @@ def run_gpu(args):
                "roofline": roof, "step_hbm_gbs": step_gbs, "cpu_baseline": cb, "e2e": e2e,
                "gpu_launches": int(launches), "clocks": clk, "kernel_ms": {k: v / max(nrec, 1) for k, v in tms.items()},
                "autotune": {"cell_warps_per_cta": tuned[0], "cell_ms_1_2_4_8": [float(x) for x in tuned[1]]},
-               "foil_2048x256": foil, "ensemble": ensemble, "served": served, "kedge_scan": kedge_scan,
+               "foil_2048x256": foil, "radiation_transport": rt, "ensemble": ensemble, "served": served, "kedge_scan": kedge_scan,
                "thermalization": thermal, "extreme_10keV": extreme}
         print(json.dumps(out))
     if dist:
         dist.destroy_process_group()
+
+
+def run_rt(pkg, tab, args):
+    """The 2D foil with radiation transport instead of the ballistic march
+    (rad cells of 8 x 8 PIC cells, the beam plus 4 polar x 2 azimuthal
+    ordinates, CIP): the same timing as the foil leg, with the transport's
+    share of the step (the "march" group of the timing)."""
+    import torch
+    cfg, pl = workload(None, "foil")
+    st = P.init_particles(cfg)
+    slab = pkg.Slab(cfg, tab, pl)
+    slab.load(st)
+    del st
+    slab.set_rt(coarsen=8, n_polar=4, n_azimuth=2, scheme=0)
+    stream = torch.cuda.current_stream()
+    slab.autotune(True)
+    slab.step(9)
+    slab.autotune(False)
+    slab.step(max(args.warmup, 3))
+    slab.sync()
+    ne0, ni0 = slab.counts()
+    slab.timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    slab.step(args.rt_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    tms, nrec = slab.timing(None)
+    ne1, ni1 = slab.counts()
+    d = slab.diagnostics()
+    slab.close()
+    n_mean = 0.5 * (ne0 + ni0 + ne1 + ni1)
+    return {"workload": cfg.name + ", radiation transport: rad cells 8 x 8, 1 + 4 x 2 ordinates, CIP",
+            "particles": int(n_mean), "steps": args.rt_steps, "value": n_mean * args.rt_steps / (ms * 1e-3),
+            "unit": UNIT, "ms_per_step": ms / args.rt_steps,
+            "transport_ms_per_step": tms["march"] / max(nrec, 1),
+            "kernel_ms": {k: v / max(nrec, 1) for k, v in tms.items()},
+            "transport_energy_gain_over_incident": d["e_rt_num"] / d["e_inc"] if d["e_inc"] > 0 else None}
 
 
 def run_foil(pkg, tab, args):
@@ -515,6 +556,8 @@ def main():
     ap.add_argument("--advance-fs", type=float, default=10.0,
                     help="simulated time run before the timed steps, outside the clock")
     ap.add_argument("--foil-steps", type=int, default=20, help="timed steps of the 2D foil leg (0: skip)")
+    ap.add_argument("--rt-steps", type=int, default=20,
+                    help="timed steps of the 2D foil with radiation transport (0: skip)")
     ap.add_argument("--ensemble", type=int, default=256, help="slabs of the batched ensemble (0: skip)")
     ap.add_argument("--serve-n", type=int, default=40, help="requests of the served trace (0: skip)")
     ap.add_argument("--serve-horizon-fs", type=float, default=150.0,
