@@ -24,6 +24,7 @@ inside the timed region.  The state (27 GB) is far larger than L2.
 of the same workload (a 64 x 64-cell patch of the slab).
 """
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -450,28 +451,39 @@ def run_ensemble(pkg, tab, args, rank):
 
 def run_served(pkg, tab, args):
     """Served loop: Poisson arrivals of slab requests, continuous batching
-    against the plain one-at-a-time form on the same trace."""
+    with admission by reserved footprint; more requests than fit at once,
+    so that arrivals queue.  The plain one-at-a-time form runs a fixed
+    sample of the same requests back to back (its rate under a backlog is
+    one request per service time, whatever the arrival times)."""
     from paper_1704_01202_gb300 import serve
     tr = P.request_trace(n=args.serve_n, rate_hz=200.0, seed=11, horizon_fs=args.serve_horizon_fs)
     # request payloads (initial particles) are built before the clock starts:
     # a client sends them with the request
     payload = {r.rid: P.init_particles(r.cfg) for r in tr}
     init = lambda r: payload[r.rid]  # noqa: E731
-    fp = [serve.footprint(r.cfg) for r in tr]
+    fp = [serve.footprint(r.cfg, r.pulse) for r in tr]
     slot_cells = max(r.cfg.nx for r in tr)
-    # resident capacity: room for about 64 average requests at once
-    cap_e = max(max(f[0] for f in fp), int(64 * sum(f[0] for f in fp) / len(fp)))
-    cap_i = max(max(f[1] for f in fp), int(64 * sum(f[1] for f in fp) / len(fp)))
-    b = serve.serve_batched(tr, tab, init, max_slabs=128, slot_cells=slot_cells,
-                            cap_e=cap_e, cap_i=cap_i, tick_steps=25)
-    o = serve.serve_one_at_a_time(tr, tab, init)
+    # resident capacity: the slots, and room for about serve_room average
+    # reservations at once
+    room = args.serve_room
+    cap_e = max(max(f[0] for f in fp), int(room * sum(f[0] for f in fp) / len(fp)))
+    cap_i = max(max(f[1] for f in fp), int(room * sum(f[1] for f in fp) / len(fp)))
+    b = serve.serve_batched(tr, tab, init, max_slabs=args.serve_slots, slot_cells=slot_cells,
+                            cap_e=cap_e, cap_i=cap_i, tick_steps=args.serve_tick)
+    sample = [dataclasses.replace(r, t_arrive=0.0) for r in tr[::args.serve_every]]
+    o = serve.serve_one_at_a_time(sample, tab, init)
     psteps = sum(r.nsteps * r.cfg.ncell * (r.cfg.ppc_e + r.cfg.ppc_i) for r in tr)
-    keys = ("slabs_per_s", "ttr_p50_s", "ttr_p99_s", "ttr_mean_s", "wall_s")
+    keys = ("slabs_per_s", "ttr_p50_s", "ttr_p99_s", "ttr_mean_s", "wall_s", "wait_p50_s", "wait_p99_s",
+            "max_queue", "preempted")
     return {"trace": f"{len(tr)} Poisson arrivals at 200/s, ensemble draws + thickness U(0.2, 2) um, "
                      f"each run {args.serve_horizon_fs:g} fs ({tr[0].nsteps} steps)",
-            "batched": {k: b[k] for k in keys}, "one_at_a_time": {k: o[k] for k in keys},
+            "batched": {k: b[k] for k in keys}, "failed": len(b["failed"]),
+            "one_at_a_time": {"slabs_per_s": o["slabs_per_s"], "wall_s": o["wall_s"],
+                              "service_p50_s": float(np.percentile(np.diff([0.0] + sorted(o["ttr"].values())), 50)),
+                              "sample": f"every {args.serve_every}th request ({len(sample)}), run back to back"},
             "speedup_slabs_per_s": b["slabs_per_s"] / o["slabs_per_s"],
-            "particle_steps": int(psteps), "max_slabs": 128, "slot_cells": slot_cells}
+            "particle_steps": int(psteps), "particle_steps_per_s": psteps / b["wall_s"],
+            "max_slabs": args.serve_slots, "room_avg_requests": room, "slot_cells": slot_cells}
 
 
 def run_kedge(pkg, tab, args):
@@ -559,7 +571,13 @@ def main():
     ap.add_argument("--rt-steps", type=int, default=20,
                     help="timed steps of the 2D foil with radiation transport (0: skip)")
     ap.add_argument("--ensemble", type=int, default=256, help="slabs of the batched ensemble (0: skip)")
-    ap.add_argument("--serve-n", type=int, default=40, help="requests of the served trace (0: skip)")
+    ap.add_argument("--serve-n", type=int, default=240, help="requests of the served trace (0: skip)")
+    ap.add_argument("--serve-slots", type=int, default=128, help="slots of the served batch")
+    ap.add_argument("--serve-room", type=float, default=96.0,
+                    help="electron and ion capacity of the served batch, in average request reservations")
+    ap.add_argument("--serve-tick", type=int, default=25, help="steps between admissions / retirements")
+    ap.add_argument("--serve-every", type=int, default=16,
+                    help="the one-at-a-time form runs every n-th request of the trace")
     ap.add_argument("--serve-horizon-fs", type=float, default=150.0,
                     help="simulated time per served request (the workload's 150 fs)")
     ap.add_argument("--kedge-points", type=int, default=12, help="photon energies of the K-edge sweep (0: skip)")

@@ -280,8 +280,29 @@ pic_status pic_batch_admit(pic_ctx *c, const pic_grid *g, const pic_species *s, 
  * slot is free again. */
 pic_status pic_batch_retire(pic_ctx *c, int slot);
 
-/* Slot state (0 free, 1 active, 2 retired, not yet emptied) and its step
- * count (synchronizes when step != NULL). */
+/* Electron budget of an active slot: the most electron slots the slab may
+ * hold after any step (its particles plus those it created; 0: no budget of
+ * its own, only the context's cap_e).  A step in which a cell would take
+ * the slab beyond its budget drops the electrons that cell created and
+ * fails that slab alone: it stops at the end of the step (its step count
+ * no longer advances, its particles are dropped by the next step) and
+ * pic_batch_slot reports state 3 once pic_step returns.  Retire a failed
+ * slot to free it; its diagnostics and particles are no longer available.
+ * With a budget on every active slot and the budgets summing to at most
+ * cap_e, the shared capacity cannot run out: a capacity failure stays with
+ * the slab that caused it (without budgets, running out of cap_e fails the
+ * whole step with PIC_ERR_CAPACITY and leaves every slab's state
+ * undefined).  Why a slab can outgrow a footprint bound: every partial
+ * photoionization (Sec. III, Eq. 2, an absorption of fewer photons than
+ * one ion weight) creates an electron macroparticle of fractional weight
+ * while the ion's charge advances by that fraction only, up to one per
+ * photon bin per cell per rad step.
+ * PIC_ERR_ARG: max_e < 0 or above cap_e; PIC_ERR_STATE: slot not active. */
+pic_status pic_batch_set_budget(pic_ctx *c, int slot, int64_t max_e);
+
+/* Slot state (0 free, 1 active, 2 retired, not yet emptied, 3 failed: went
+ * beyond its electron budget, stopped) and its step count (synchronizes
+ * when step != NULL). */
 pic_status pic_batch_slot(pic_ctx *c, int slot, int *state, uint32_t *step);
 
 /* Per-slot versions of pic_diagnostics, pic_counts, pic_get_electrons and
@@ -333,11 +354,13 @@ const char *pic_last_error(const pic_ctx *c);
 pic_status pic_philox_check(const uint32_t *ctr, const uint32_t key[2], uint32_t *out, int n);
 
 /* The in-cell ordering of the device (ascending key, ties by id; the
- * canonical order every per-cell rule follows), run on n <= 1024 given
- * entries by one warp with the algorithm a cell of that size uses:
+ * canonical order every per-cell rule follows), run on n <= 4096 given
+ * entries by one warp with the algorithm a cell of that size uses in the
+ * cell-kernel instance rmax (128, 512 or 1024: the largest cell it sorts in
+ * registers; the radix sort above 512, resp. 1024; rmax 128 takes n <= 128):
  * order[k] = index of the entry at position k.  For checking it against
- * other implementations. */
-pic_status pic_order_check(const uint64_t *key, const uint64_t *id, int n, uint16_t *order);
+ * other implementations.  PIC_ERR_ARG on other n or rmax. */
+pic_status pic_order_check(const uint64_t *key, const uint64_t *id, int n, int rmax, uint16_t *order);
 
 /* The same check without any device allocation.  The paper has no
  * counterpart: this serves callers that must not allocate, e.g. a host

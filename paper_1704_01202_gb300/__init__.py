@@ -43,7 +43,7 @@ ABI_FUNCTIONS = ["pic_required_bytes", "pic_init", "pic_source", "pic_load_elect
                  "pic_counts", "pic_get_electrons", "pic_get_ions", "pic_get_photons", "pic_get_fields",
                  "pic_get_current", "pic_launch_count", "pic_free", "pic_last_error", "pic_philox_check",
                  "pic_timing", "pic_batch_required_bytes", "pic_batch_init", "pic_batch_admit",
-                 "pic_batch_retire", "pic_batch_slot", "pic_batch_diagnostics", "pic_batch_counts",
+                 "pic_batch_retire", "pic_batch_set_budget", "pic_batch_slot", "pic_batch_diagnostics", "pic_batch_counts",
                  "pic_batch_get_electrons", "pic_batch_get_ions", "pic_philox_check_static",
                  "pic_use_graphs", "pic_autotune", "pic_order_check",
                  "pic_get_electrons64", "pic_get_ions64", "pic_real_bytes",
@@ -178,7 +178,7 @@ def lib(fp64: bool = False):
             L.pic_philox_check_static.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
                                                   C.POINTER(C.c_uint32), C.c_int]
             L.pic_use_graphs.argtypes = [_P, C.c_int]
-            L.pic_order_check.argtypes = [C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.c_int,
+            L.pic_order_check.argtypes = [C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.c_int, C.c_int,
                                           C.POINTER(C.c_uint16)]
             L.pic_autotune.argtypes = [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]
             L.pic_timing.argtypes = [_P, C.c_int, _D, C.POINTER(C.c_int64)]
@@ -196,6 +196,7 @@ def lib(fp64: bool = False):
                                           C.POINTER(C.c_uint32), C.POINTER(C.c_int)]
             L.pic_batch_retire.argtypes = [_P, C.c_int]
             L.pic_batch_slot.argtypes = [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_uint32)]
+            L.pic_batch_set_budget.argtypes = [_P, C.c_int, C.c_int64]
             L.pic_batch_diagnostics.argtypes = [_P, C.c_int, C.POINTER(Diag)]
             L.pic_batch_counts.argtypes = [_P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
             L.pic_batch_get_electrons.argtypes = [_P, C.c_int, _D, _D, _F, _F, C.POINTER(C.c_uint64)]
@@ -485,6 +486,9 @@ def _species(cfg, cap_e=0, cap_i=0) -> Species:
                    flags=cfg.flags, cap_e=cap_e, cap_i=cap_i)
 
 
+SLOT_FREE, SLOT_ACTIVE, SLOT_RETIRED, SLOT_FAILED = 0, 1, 2, 3
+
+
 class Batch:
     """Many independent 1D slabs stepped together (one launch of each kernel
     per step), admitted and retired between steps."""
@@ -534,10 +538,20 @@ class Batch:
         self._check(self.L.pic_batch_retire(self.h, slot), "pic_batch_retire")
         self.cfgs.pop(slot, None)
 
-    def slot(self, slot: int):
-        state, step = C.c_int(), C.c_uint32()
-        self._check(self.L.pic_batch_slot(self.h, slot, C.byref(state), C.byref(step)), "pic_batch_slot")
-        return state.value, step.value
+    def set_budget(self, slot: int, max_e: int):
+        """Electron budget of a slot (pic_batch_set_budget): beyond it the
+        slab alone fails (state FAILED after the step), not the batch."""
+        self._check(self.L.pic_batch_set_budget(self.h, slot, int(max_e)), "pic_batch_set_budget")
+
+    def failed(self) -> list:
+        """Slots that went beyond their electron budget (state FAILED)."""
+        return [k for k in list(self.cfgs) if self.slot(k, step=False)[0] == SLOT_FAILED]
+
+    def slot(self, slot: int, step: bool = True):
+        state, n = C.c_int(), C.c_uint32()
+        self._check(self.L.pic_batch_slot(self.h, slot, C.byref(state), C.byref(n) if step else None),
+                    "pic_batch_slot")
+        return state.value, n.value
 
     def counts(self, slot: int):
         ne, ni = C.c_int64(), C.c_int64()
@@ -573,12 +587,13 @@ def philox_check(ctr: np.ndarray, key) -> np.ndarray:
     return o
 
 
-def order_check(key: np.ndarray, ids: np.ndarray) -> np.ndarray:
-    """Device in-cell ordering of (key, id) entries: positions -> entry index."""
+def order_check(key: np.ndarray, ids: np.ndarray, rmax: int = 512) -> np.ndarray:
+    """Device in-cell ordering of (key, id) entries by the sort of the cell
+    kernel instance rmax (128, 512, 1024): positions -> entry index."""
     k = np.ascontiguousarray(key, dtype=np.uint64)
     i = np.ascontiguousarray(ids, dtype=np.uint64)
     o = np.zeros(k.size, dtype=np.uint16)
-    st = lib().pic_order_check(_p(k, C.c_uint64), _p(i, C.c_uint64), k.size, _p(o, C.c_uint16))
+    st = lib().pic_order_check(_p(k, C.c_uint64), _p(i, C.c_uint64), k.size, rmax, _p(o, C.c_uint16))
     if st != 0:
         raise PicError(f"pic_order_check: {STATUS.get(st, st)}")
     return o.astype(np.int64)

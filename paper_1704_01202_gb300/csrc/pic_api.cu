@@ -32,8 +32,9 @@ namespace {
 
 // device counters; [0, CNT_STEP_ZERO) are cleared at the start of a step
 constexpr int CNT_APPEND = 0, CNT_WORK = 1, CNT_WORK_T1 = 2, CNT_WORK_BIG = 3, CNT_OVF = 4, CNT_OVF2 = 5,
-              CNT_WORK_PUSH = 6, CNT_STEP_ZERO = 7, CNT_ERR = 8, CNT_MAXE = 9, CNT_MAXI = 10, CNT_NLOAD = 11,
-              CNT_HIST_E = 16, CNT_HIST_I = CNT_HIST_E + NHIST, NCOUNTERS = CNT_HIST_I + NHIST;
+              CNT_WORK_PUSH = 6, CNT_WORK_T2 = 7, CNT_OVF3 = 8, CNT_STEP_ZERO = 9, CNT_ERR = 10, CNT_MAXE = 11,
+              CNT_MAXI = 12, CNT_NLOAD = 13, CNT_HIST_E = 16, CNT_HIST_I = CNT_HIST_E + NHIST,
+              NCOUNTERS = CNT_HIST_I + NHIST;
 constexpr int NEV = 6;   // timing events per step
 // largest cell of the one-warp pass (the FP64 build's staging is twice as
 // wide and takes half the populations into the same shared memory)
@@ -60,7 +61,7 @@ struct pic_ctx {
     bool batch = false;
     int nslot = 1, slot_cells = 0, slot_pts = 0, slot_rows = 1;
     std::vector<SlabDev> slabs;          // host copy of every slot's description
-    std::vector<int> slot_state;         // 0 free, 1 active, 2 retired (emptied by the next step)
+    std::vector<int> slot_state;         // 0 free, 1 active, 2 retired (emptied by the next step), 3 failed
     std::vector<pic_grid> grids;         // grid of each slot as given
     struct Pending {                     // admitted, particles not yet on the device
         int slot;
@@ -78,6 +79,8 @@ struct pic_ctx {
     int cur = 0;
     int *cnt_e, *cnt_i, *fill_e, *fill_i, *bsum_e, *bsum_i;
     int *counters, *ovf_list, *ovf_list2, *cell_slab, *pt_slab, *row_slab, *row_idx;
+    int *slab_app, *slab_err;            // [nslot] per-slab appends of the step; budget failures
+    bool budgets = false;                // some slot has an electron budget
     SlabDev *d_slab;                     // [nslot]
     unsigned *d_steps;                   // [nslot]
     SlabTally *d_tally;                  // [nslot]
@@ -94,8 +97,11 @@ struct pic_ctx {
     // cells, when that is larger), then to the one-warp large-cell pass
     int cap_ce = 128, cap_ci = 32, cap_new = 96, wpc = 4;
     int t1_ce = 0, t1_ci = 0, t1_wpc = 1;    // t1_ce == 0: no tier 1
-    size_t smem_main = 0, smem_t1 = 0, smem_big = 0;
-    int nsm = 0, grid_main = 0, grid_t1 = 0, grid_big = 0, grid_push = 0;
+    int t2_ce = 0, t2_ci = 0, t2_wpc = 1;    // t2_ce == 0: no tier 2
+    size_t smem_main = 0, smem_t1 = 0, smem_t2 = 0, smem_big = 0;
+    int nsm = 0, grid_main = 0, grid_t1 = 0, grid_t2 = 0, grid_big = 0, grid_push = 0;
+    NewE *nw = nullptr;                  // created-electron scratch of the cell launches
+    size_t nw_entries = 0;
     int64_t launches = 0;
     bool loaded_e = false, loaded_i = false;
     std::vector<double> hv_tab, sigma;   // host copy of the photoionization table
@@ -108,6 +114,7 @@ struct pic_ctx {
     struct StepShape {
         const void *eA0, *iA0;
         int cur, ecur, grid_main, wpc, cap_ce, cap_ci, cap_new, nsub, t1_ce, t1_ci, t1_wpc, grid_t1;
+        int t2_ce, t2_ci, t2_wpc, grid_t2;
         size_t smem_main;
         bool march, field, rt;
     };
@@ -161,6 +168,17 @@ T *carve_arena(pic_ctx *c, size_t count)
     return p;
 }
 
+// Created-electron scratch of the cell launches, in entries: cap_new = 3 x
+// the ions a tier stages (at most 768 below the large-cell pass, whose
+// 1536 take one warp a CTA) for every warp resident at once, at most 16 a
+// SM (the register-bound instances) on up to 192 SMs, and no more warps
+// than cells (plus a CTA).  Launch grids are clamped to the slices.
+size_t nw_scratch_entries(int ncell)
+{
+    const size_t warps = std::min<size_t>(192 * 16, (size_t)ncell + 64);
+    return warps * 768;
+}
+
 size_t arena_need(int ncell, int npts, int nblk, int cap_e, int cap_i, int nslot, int nrows)
 {
     size_t b = 0;
@@ -168,11 +186,12 @@ size_t arena_need(int ncell, int npts, int nblk, int cap_e, int cap_i, int nslot
     b += 4 * al((size_t)cap_i * sizeof(real4)) + 2 * al((size_t)cap_i * 4);
     b += 4 * al((size_t)(ncell + 1) * 4) + al((size_t)ncell * 16) + 2 * al((size_t)nblk * 4);
     b += al(NCOUNTERS * 4) + al((size_t)ncell * 4) * 3;
-    b += al(sizeof(SlabDev) * (size_t)nslot) + al(4 * (size_t)nslot) + al(sizeof(SlabTally) * (size_t)nslot)
+    b += al(sizeof(SlabDev) * (size_t)nslot) + 3 * al(4 * (size_t)nslot) + al(sizeof(SlabTally) * (size_t)nslot)
          + al(sizeof(Tables)) + al(sizeof(EosTable));
     b += 3 * al((size_t)npts * 3 * sizeof(real)) + al((size_t)npts * 3 * 8) + al((size_t)npts * 4);
     b += 2 * al((size_t)nrows * 4);
     b += al((size_t)ncell * PIC_MAX_BINS * sizeof(ph2));
+    b += al(nw_scratch_entries(ncell) * sizeof(NewE));
     b += al((4 + NZ + 4096 + 8) * 8);
     return b + 4096;
 }
@@ -196,15 +215,29 @@ double sigma_table(const pic_ctx *c, int s, double hv)
 }
 
 // the cell-kernel instance for a launch staging up to ce electrons and ci
-// ions per cell: in-register sorts up to 128 entries, or up to 512
+// ions per cell: in-register sorts up to 128, 512 or 1024 entries
 typedef void (*CellKernel)(CellArgs);
-CellKernel cell_kernel(int ce, int ci) { return ce <= 128 && ci <= 128 ? k_cell<128> : k_cell<512>; }
-
-// largest warps per CTA of the cell kernel whose staging fits 200 KB
-int max_wpc(int ce, int ci, int cn)
+CellKernel cell_kernel(int ce, int ci)
 {
-    const size_t per = warp_mem_bytes(ce, ci, cn);
-    return std::max(1, (int)std::min<size_t>(8, (200 * 1024) / per));
+    const int r = rmax_for(ce, ci);
+    return r == 128 ? k_cell<128> : (r == 512 ? k_cell<512> : k_cell<1024>);
+}
+
+// largest warps per CTA of the cell kernel whose staging fits 200 KB (the
+// 1024 instance takes at most 4 warps a CTA)
+int max_wpc(int ce, int ci)
+{
+    const size_t per = warp_mem_bytes(ce, ci);
+    const int lim = rmax_for(ce, ci) > 512 ? 4 : 8;
+    return std::max(1, (int)std::min<size_t>(lim, (200 * 1024) / per));
+}
+
+// CTAs of a persistent cell launch: the resident ones on every SM, as many
+// as the created-electron scratch has warp slices for
+int cell_grid(const pic_ctx *c, int occ, int wpc, int cn)
+{
+    const int cap = (int)std::min<size_t>(c->nw_entries / ((size_t)wpc * cn), 1 << 30);
+    return std::max(1, std::min(std::max(1, occ) * c->nsm, cap));
 }
 
 pic_status cell_smem_attr(pic_ctx *c)
@@ -212,14 +245,15 @@ pic_status cell_smem_attr(pic_ctx *c)
     // the opt-in maximum (less the kernel's static shared memory), so that
     // occupancy can be asked for any staging size
     int dev = 0, optin = 0;
-    cudaFuncAttributes fa{};
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    CK(cudaFuncGetAttributes(&fa, k_cell<512>));
-    const size_t m = std::max(std::max(c->smem_main, c->smem_t1), c->smem_big);
-    const size_t lim = optin > (int)fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : m;
-    CK(cudaFuncSetAttribute(k_cell<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max(m, lim)));
-    CK(cudaFuncSetAttribute(k_cell<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max(m, lim)));
+    const size_t m = std::max(std::max(c->smem_main, c->smem_t1), std::max(c->smem_t2, c->smem_big));
+    for (CellKernel k : {k_cell<128>, k_cell<512>, k_cell<1024>}) {
+        cudaFuncAttributes fa{};
+        CK(cudaFuncGetAttributes(&fa, k));
+        const size_t lim = optin > (int)fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : m;
+        CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max(m, lim)));
+    }
     return PIC_OK;
 }
 
@@ -227,12 +261,12 @@ pic_status cell_smem_attr(pic_ctx *c)
 // resident per SM: with large cells the staging, not the registers, limits
 // residency, and fewer warps per CTA can let more CTAs share an SM.  Ties
 // go to the larger CTA.
-int best_wpc(pic_ctx *c, int ce, int ci, int cn)
+int best_wpc(pic_ctx *c, int ce, int ci)
 {
-    if (cell_smem_attr(c) != PIC_OK) return max_wpc(ce, ci, cn);
-    const size_t per = warp_mem_bytes(ce, ci, cn);
+    if (cell_smem_attr(c) != PIC_OK) return max_wpc(ce, ci);
+    const size_t per = warp_mem_bytes(ce, ci);
     int best = 1, best_warps = 0;
-    for (int w = 1; w <= max_wpc(ce, ci, cn); ++w) {
+    for (int w = 1; w <= max_wpc(ce, ci); ++w) {
         int occ = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cell_kernel(ce, ci), 32 * w, per * w) != cudaSuccess)
             continue;
@@ -245,12 +279,12 @@ int best_wpc(pic_ctx *c, int ce, int ci, int cn)
 pic_status set_wpc(pic_ctx *c, int wpc)
 {
     c->wpc = wpc;
-    c->smem_main = warp_mem_bytes(c->cap_ce, c->cap_ci, c->cap_new) * wpc;
+    c->smem_main = warp_mem_bytes(c->cap_ce, c->cap_ci) * wpc;
     pic_status r = cell_smem_attr(c);
     if (r != PIC_OK) return r;
     int occ = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cell_kernel(c->cap_ce, c->cap_ci), wpc * 32, c->smem_main));
-    c->grid_main = std::max(1, occ) * c->nsm;
+    c->grid_main = cell_grid(c, occ, wpc, c->cap_new);
     return PIC_OK;
 }
 
@@ -269,43 +303,67 @@ int cap_for_share(const int *hist, double share, int lo)
     return std::max(lo, 1 << (NHIST - 1));
 }
 
-// Staging sizes of the cell tiers from the last sort's cell populations:
-// tier 0 holds 75 % of the cells of each species (powers of two, at least
-// 64 electrons / 32 ions); tier 1 the largest cells x 1.25 (at most 1024 /
-// 256), launched only when larger than tier 0.  Warps per CTA of tier 0 from
-// the autotuner's choice for its sizes, else the most that fit.
+// v rounded up to a multiple of q, within [lo, hi]
+int round_cap(int v, int q, int lo, int hi) { return std::min(hi, std::max(lo, (v + q - 1) / q * q)); }
+
+// Staging sizes of the cell tiers from the last sort's cell populations.
+// Tier 0 holds 75 % of the cells of each species (powers of two, at least
+// 64 electrons / 32 ions).  The larger cells go up a chain of tiers sized
+// for the largest cell x 1.25 (the cells grow between two re-sizings):
+// tier 1 up to 1024 electrons / 256 ions (multiples of 128 / 32), tier 2
+// above that up to the large-cell pass's 2048 / 512 (multiples of 256 /
+// 64); each tier launched only when the one below cannot hold the largest
+// cells.  A staging just large enough for its cells keeps the most warps
+// resident on the SM, which the large cells' staging limits.  Warps per
+// CTA of tier 0 from the autotuner's choice for its sizes, else the most
+// that stay resident.
 pic_status configure_cell_launch(pic_ctx *c, const int *hist_e, const int *hist_i, int max_e, int max_i)
 {
+    const int want_e = (int)(max_e * 1.25) + 1, want_i = (int)(max_i * 1.25) + 1;
     int ce = std::min(cap_for_share(hist_e, 0.75, 64), 1024);
     int ci = std::min(cap_for_share(hist_i, 0.75, 32), 256);
-    int ce1 = std::min(next_pow2(std::max(64, (int)(max_e * 1.25) + 1)), 1024);
-    int ci1 = std::min(next_pow2(std::max(32, (int)(max_i * 1.25) + 1)), 256);
-    ce = std::min(ce, ce1);
-    ci = std::min(ci, ci1);
+    ce = std::min(ce, std::min(next_pow2(std::max(64, want_e)), 1024));
+    ci = std::min(ci, std::min(next_pow2(std::max(32, want_i)), 256));
     c->cap_ce = ce; c->cap_ci = ci; c->cap_new = 3 * ci;
-    if (ce1 > ce || ci1 > ci) {
-        c->t1_ce = ce1; c->t1_ci = ci1;
-        c->t1_wpc = best_wpc(c, ce1, ci1, 3 * ci1);
-        c->smem_t1 = warp_mem_bytes(ce1, ci1, 3 * ci1) * c->t1_wpc;
-    } else {
-        c->t1_ce = c->t1_ci = 0;
-        c->smem_t1 = 0;
+    c->t1_ce = c->t1_ci = c->t2_ce = c->t2_ci = 0;
+    c->smem_t1 = c->smem_t2 = 0;
+    if (want_e > ce || want_i > ci) {
+        c->t1_ce = round_cap(want_e, 128, ce, 1024);
+        c->t1_ci = round_cap(want_i, 32, ci, 256);
+        c->t1_wpc = best_wpc(c, c->t1_ce, c->t1_ci);
+        c->smem_t1 = warp_mem_bytes(c->t1_ce, c->t1_ci) * c->t1_wpc;
+        if (want_e > c->t1_ce || want_i > c->t1_ci) {
+            c->t2_ce = round_cap(want_e, 256, c->t1_ce, BIG_CE);
+            c->t2_ci = round_cap(want_i, 64, c->t1_ci, BIG_CI);
+            c->t2_wpc = best_wpc(c, c->t2_ce, c->t2_ci);
+            c->smem_t2 = warp_mem_bytes(c->t2_ce, c->t2_ci) * c->t2_wpc;
+        }
     }
-    int wpc = best_wpc(c, ce, ci, 3 * ci);
+    int wpc = best_wpc(c, ce, ci);
     for (const auto &t : c->tuned)
         if (t.ce == ce && t.ci == ci && t.done) wpc = t.wpc;
     pic_status r = set_wpc(c, wpc);
-    if (r != PIC_OK || !c->t1_ce) return r;
+    if (r != PIC_OK) return r;
     int occ = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cell_kernel(c->t1_ce, c->t1_ci), c->t1_wpc * 32,
-                                                     c->smem_t1));
-    c->grid_t1 = std::max(1, occ) * c->nsm;
+    if (c->t1_ce) {
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cell_kernel(c->t1_ce, c->t1_ci), c->t1_wpc * 32,
+                                                         c->smem_t1));
+        c->grid_t1 = cell_grid(c, occ, c->t1_wpc, 3 * c->t1_ci);
+    }
+    if (c->t2_ce) {
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cell_kernel(c->t2_ce, c->t2_ci), c->t2_wpc * 32,
+                                                         c->smem_t2));
+        c->grid_t2 = cell_grid(c, occ, c->t2_wpc, 3 * c->t2_ci);
+    }
     return PIC_OK;
 }
 
-// arguments of one cell-kernel launch: tier 0 (all cells), tier 1 (the
-// cells tier 0 could not stage) or the large-cell pass (the rest)
-enum CellTier { TIER0, TIER1, TIER_BIG };
+// arguments of one cell-kernel launch: tier 0 (all cells), tiers 1 and 2
+// (the cells the tier below could not stage) or the large-cell pass (the
+// rest).  The overflow lists alternate: tier 0 writes list 1, tier 1 reads
+// it and writes list 2, tier 2 reads list 2 and writes list 1 again (tier 1
+// has finished reading it), the large-cell pass reads the last one.
+enum CellTier { TIER0, TIER1, TIER2, TIER_BIG };
 
 CellArgs cell_args(pic_ctx *c, CellTier tier)
 {
@@ -316,6 +374,7 @@ CellArgs cell_args(pic_ctx *c, CellTier tier)
     a.cnt_e = c->cnt_e; a.cnt_i = c->cnt_i;
     a.append = c->counters + CNT_APPEND;
     a.cap_e = c->cap_e;
+    a.slab_app = c->slab_app; a.slab_err = c->slab_err;
     a.ncell = c->ncell;
     a.cell_slab = c->cell_slab;
     a.slabs = c->d_slab;
@@ -329,7 +388,7 @@ CellArgs cell_args(pic_ctx *c, CellTier tier)
     a.tab = c->d_tab;
     a.eos = c->d_eos;
     a.err = c->counters + CNT_ERR;
-    const bool t1 = c->t1_ce > 0;
+    a.nw = c->nw;
     if (tier == TIER0) {
         a.work = c->counters + CNT_WORK;
         a.list = nullptr; a.n_list = nullptr;
@@ -340,10 +399,16 @@ CellArgs cell_args(pic_ctx *c, CellTier tier)
         a.list = c->ovf_list; a.n_list = c->counters + CNT_OVF;
         a.ovf_list = c->ovf_list2; a.ovf_count = c->counters + CNT_OVF2;
         a.cap_ce = c->t1_ce; a.cap_ci = c->t1_ci; a.cap_new = 3 * c->t1_ci;
+    } else if (tier == TIER2) {
+        a.work = c->counters + CNT_WORK_T2;
+        a.list = c->ovf_list2; a.n_list = c->counters + CNT_OVF2;
+        a.ovf_list = c->ovf_list; a.ovf_count = c->counters + CNT_OVF3;
+        a.cap_ce = c->t2_ce; a.cap_ci = c->t2_ci; a.cap_new = 3 * c->t2_ci;
     } else {
         a.work = c->counters + CNT_WORK_BIG;
-        a.list = t1 ? c->ovf_list2 : c->ovf_list;
-        a.n_list = c->counters + (t1 ? CNT_OVF2 : CNT_OVF);
+        if (c->t2_ce) { a.list = c->ovf_list; a.n_list = c->counters + CNT_OVF3; }
+        else if (c->t1_ce) { a.list = c->ovf_list2; a.n_list = c->counters + CNT_OVF2; }
+        else { a.list = c->ovf_list; a.n_list = c->counters + CNT_OVF; }
         a.ovf_list = nullptr; a.ovf_count = nullptr;
         a.cap_ce = BIG_CE; a.cap_ci = BIG_CI; a.cap_new = 3 * BIG_CI;
     }
@@ -410,6 +475,7 @@ pic_ctx::StepShape step_shape(const pic_ctx *c)
     k.grid_main = c->grid_main; k.wpc = c->wpc; k.smem_main = c->smem_main;
     k.cap_ce = c->cap_ce; k.cap_ci = c->cap_ci; k.cap_new = c->cap_new;
     k.t1_ce = c->t1_ce; k.t1_ci = c->t1_ci; k.t1_wpc = c->t1_wpc; k.grid_t1 = c->grid_t1;
+    k.t2_ce = c->t2_ce; k.t2_ci = c->t2_ci; k.t2_wpc = c->t2_wpc; k.grid_t2 = c->grid_t2;
     k.rt = c->slabs[0].rt != 0;
     k.march = !k.rt && any_active(c, PIC_F_PHOTO, true);
     k.field = any_active(c, PIC_F_FIELD, false);
@@ -424,7 +490,8 @@ bool same_shape(const pic_ctx::StepShape &a, const pic_ctx::StepShape &b)
     return a.eA0 == b.eA0 && a.iA0 == b.iA0 && a.cur == b.cur && a.ecur == b.ecur && a.grid_main == b.grid_main &&
            a.wpc == b.wpc && a.smem_main == b.smem_main && a.cap_ce == b.cap_ce && a.cap_ci == b.cap_ci &&
            a.cap_new == b.cap_new && a.march == b.march && a.field == b.field && a.nsub == b.nsub && a.rt == b.rt &&
-           a.t1_ce == b.t1_ce && a.t1_ci == b.t1_ci && a.t1_wpc == b.t1_wpc && a.grid_t1 == b.grid_t1;
+           a.t1_ce == b.t1_ce && a.t1_ci == b.t1_ci && a.t1_wpc == b.t1_wpc && a.grid_t1 == b.grid_t1 &&
+           a.t2_ce == b.t2_ce && a.t2_ci == b.t2_ci && a.t2_wpc == b.t2_wpc && a.grid_t2 == b.grid_t2;
 }
 
 pic_status launch_step(pic_ctx *c)
@@ -467,8 +534,13 @@ pic_status launch_step(pic_ctx *c)
         cell_kernel(c->t1_ce, c->t1_ci)<<<c->grid_t1, c->t1_wpc * 32, c->smem_t1, st>>>(a1);
         ++c->launches;
     }
+    if (c->t2_ce) {
+        CellArgs a2 = cell_args(c, TIER2);
+        cell_kernel(c->t2_ce, c->t2_ci)<<<c->grid_t2, c->t2_wpc * 32, c->smem_t2, st>>>(a2);
+        ++c->launches;
+    }
     CellArgs ab = cell_args(c, TIER_BIG);
-    k_cell<512><<<c->grid_big, 32, c->smem_big, st>>>(ab);
+    cell_kernel(BIG_CE, BIG_CI)<<<c->grid_big, 32, c->smem_big, st>>>(ab);
     c->launches += 2;
     if (c->cell_ev_on) CK(cudaEventRecord(c->cell_ev[1], st));
     CK(cudaGetLastError());
@@ -514,7 +586,7 @@ pic_status launch_step(pic_ctx *c)
             c->launches += 3;
         }
     }
-    k_advance<<<(c->nslot + 127) / 128, 128, 0, st>>>(c->d_steps, c->d_slab, c->nslot);
+    k_advance<<<(c->nslot + 127) / 128, 128, 0, st>>>(c->d_steps, c->d_slab, c->nslot, c->slab_app, c->slab_err);
     ++c->launches;
     CK(cudaGetLastError());
     if (ev) CK(cudaEventRecord(ev[5], st));
@@ -617,6 +689,8 @@ pic_status reset_slot(pic_ctx *c, int k)
     CK(cudaMemsetAsync(c->photons + S.ph_off, 0, sizeof(ph2) * (size_t)c->slot_cells * PIC_MAX_BINS, st));
     CK(cudaMemcpyAsync(c->d_slab + k, &S, sizeof(SlabDev), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(c->d_steps + k, 0, sizeof(unsigned), st));
+    CK(cudaMemsetAsync(c->slab_app + k, 0, sizeof(int), st));
+    CK(cudaMemsetAsync(c->slab_err + k, 0, sizeof(int), st));
     CK(cudaMemsetAsync(c->d_tally + k, 0, sizeof(SlabTally), st));
     CK(cudaStreamSynchronize(st));      // the host copy of S may change after this call
     return PIC_OK;
@@ -682,6 +756,8 @@ pic_status ctx_create(pic_ctx **out, int nslot, int slot_cells, int slot_pts, in
     c->cell_slab = carve_arena<int>(c, c->ncell);
     c->d_slab = carve_arena<SlabDev>(c, nslot);
     c->d_steps = carve_arena<unsigned>(c, nslot);
+    c->slab_app = carve_arena<int>(c, nslot);
+    c->slab_err = carve_arena<int>(c, nslot);
     c->d_tally = carve_arena<SlabTally>(c, nslot);
     c->d_tab = carve_arena<Tables>(c, 1);
     c->d_eos = carve_arena<EosTable>(c, 1);
@@ -693,6 +769,8 @@ pic_status ctx_create(pic_ctx **out, int nslot, int slot_cells, int slot_pts, in
     c->row_slab = carve_arena<int>(c, c->nrows);
     c->row_idx = carve_arena<int>(c, c->nrows);
     c->photons = carve_arena<ph2>(c, (size_t)c->ncell * PIC_MAX_BINS);
+    c->nw_entries = nw_scratch_entries(c->ncell);
+    c->nw = carve_arena<NewE>(c, c->nw_entries);
     c->diag_buf = carve_arena<double>(c, 4 + NZ + 4096 + 8);
     if (!c->diag_buf) { pic_free(c); return PIC_ERR_OOM; }
 
@@ -739,8 +817,8 @@ pic_status ctx_create(pic_ctx **out, int nslot, int slot_cells, int slot_pts, in
     } while (0);
     pic_status rc = PIC_OK;
     if (e != cudaSuccess) { rc = cuda_fail(c, e, "init copies"); pic_free(c); return rc; }
-    c->smem_big = warp_mem_bytes(BIG_CE, BIG_CI, 3 * BIG_CI);
-    c->grid_big = c->nsm;
+    c->smem_big = warp_mem_bytes(BIG_CE, BIG_CI);
+    c->grid_big = cell_grid(c, 1, 1, 3 * BIG_CI);
     e = cudaFuncSetAttribute(k_march, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8);
     if (e != cudaSuccess) { rc = cuda_fail(c, e, "march attribute"); pic_free(c); return rc; }
     {
@@ -1151,7 +1229,7 @@ pic_status tune_step(pic_ctx *c, int n, int &k)
         c->tuned.push_back(pic_ctx::Tuned{c->cap_ce, c->cap_ci, c->wpc, {0, 0, 0, 0}, 0});
         t = &c->tuned.back();
     }
-    const int top = max_wpc(c->cap_ce, c->cap_ci, c->cap_new);
+    const int top = max_wpc(c->cap_ce, c->cap_ci);
     int shapes = 0;
     while (shapes < 4 && (1 << shapes) <= top) ++shapes;
     if (c->steps_done == 0 && k < n) {          // untimed first step of the context
@@ -1185,13 +1263,28 @@ pic_status tune_step(pic_ctx *c, int n, int &k)
     }
     if (r != PIC_OK) return r;
     t->done = t->tried >= (unsigned)(2 * shapes);
-    t->wpc = best_wpc(c, c->cap_ce, c->cap_ci, c->cap_new);  // undecided: the default
+    t->wpc = best_wpc(c, c->cap_ce, c->cap_ci);  // undecided: the default
     if (t->done) {
         float best = 3.4e38f;
         for (int q = 0; q < shapes; ++q)
             if (t->ms[q] < best) { best = t->ms[q]; t->wpc = 1 << q; }
     }
     return set_wpc(c, t->wpc);
+}
+
+// slabs that went beyond their electron budget were stopped on the device
+// (k_advance): mark them failed on the host too
+pic_status read_budget_failures(pic_ctx *c)
+{
+    std::vector<int> err(c->nslot);
+    CK(cudaMemcpyAsync(err.data(), c->slab_err, sizeof(int) * c->nslot, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < c->nslot; ++k)
+        if (err[k] && c->slot_state[k] == 1) {
+            c->slot_state[k] = 3;
+            c->slabs[k].active = 0;
+        }
+    return PIC_OK;
 }
 
 // Steps between two re-sizings of the cell tiers inside one pic_step call:
@@ -1216,7 +1309,7 @@ pic_status step_n(pic_ctx *c, int n)
     if (n > 0)
         for (int k = 0; k < c->nslot; ++k)
             if (c->slot_state[k] == 2) c->slot_state[k] = 0;
-    return PIC_OK;
+    return n > 0 && c->budgets ? read_budget_failures(c) : PIC_OK;
 }
 
 pic_status step_chunk(pic_ctx *c, int n)
@@ -1532,6 +1625,10 @@ pic_status pic_batch_admit(pic_ctx *c, const pic_grid *g, const pic_species *s, 
 pic_status pic_batch_retire(pic_ctx *c, int slot)
 {
     if (!batch_slot_ok(c, slot)) return PIC_ERR_ARG;
+    if (c->slot_state[slot] == 3) {              // failed: stopped on the device already
+        c->slot_state[slot] = 2;
+        return PIC_OK;
+    }
     if (c->slot_state[slot] != 1) return fail(c, PIC_ERR_STATE, "slot is not active");
     for (size_t q = 0; q < c->pending.size(); ++q)
         if (c->pending[q].slot == slot) {          // admitted, never on the device
@@ -1544,6 +1641,19 @@ pic_status pic_batch_retire(pic_ctx *c, int slot)
     CK(cudaMemcpyAsync(c->d_slab + slot, &c->slabs[slot], sizeof(SlabDev), cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     c->slot_state[slot] = 2;
+    return PIC_OK;
+}
+
+pic_status pic_batch_set_budget(pic_ctx *c, int slot, int64_t max_e)
+{
+    if (!batch_slot_ok(c, slot) || max_e < 0 || max_e > (int64_t)c->cap_e) return PIC_ERR_ARG;
+    if (c->slot_state[slot] != 1) return fail(c, PIC_ERR_STATE, "slot is not active");
+    c->slabs[slot].budget_e = (int)max_e;
+    if (max_e > 0) c->budgets = true;
+    for (const auto &p : c->pending)
+        if (p.slot == slot) return PIC_OK;      // uploaded with the admission
+    CK(cudaMemcpyAsync(c->d_slab + slot, &c->slabs[slot], sizeof(SlabDev), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
     return PIC_OK;
 }
 
@@ -1789,12 +1899,16 @@ pic_status pic_philox_check(const uint32_t *ctr, const uint32_t key[2], uint32_t
     return st;
 }
 
-pic_status pic_order_check(const uint64_t *key, const uint64_t *id, int n, uint16_t *order)
+pic_status pic_order_check(const uint64_t *key, const uint64_t *id, int n, int rmax, uint16_t *order)
 {
-    if (!key || !id || !order || n <= 0 || n > 1024) return PIC_ERR_ARG;
-    int np = 1;
-    while (np < n) np <<= 1;
-    const size_t smem = (size_t)np * 16 + (size_t)n * 16 + 256 * 4 + (size_t)np * 2;
+    if (!key || !id || !order || n <= 0 || n > 4096 || !(rmax == 128 || rmax == 512 || rmax == 1024) ||
+        (rmax == 128 && n > 128))
+        return PIC_ERR_ARG;
+    const size_t smem = (size_t)n * 32 + 256 * 4 + (size_t)n * 2;
+    void (*kern)(const unsigned long long *, const unsigned long long *, int, unsigned short *) =
+        rmax == 128 ? k_order_check<128> : (rmax == 512 ? k_order_check<512> : k_order_check<1024>);
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return PIC_ERR_CUDA;
     char *d = nullptr;
     const size_t bytes = (size_t)n * 16 + (size_t)n * 2;
     if (cudaMalloc(&d, bytes) != cudaSuccess) return PIC_ERR_OOM;
@@ -1805,7 +1919,7 @@ pic_status pic_order_check(const uint64_t *key, const uint64_t *id, int n, uint1
         cudaMemcpy(di, id, sizeof(uint64_t) * n, cudaMemcpyHostToDevice) != cudaSuccess)
         st = PIC_ERR_CUDA;
     if (st == PIC_OK) {
-        k_order_check<<<1, 32, smem>>>(dk, di, n, dout);
+        kern<<<1, 32, smem>>>(dk, di, n, dout);
         if (cudaGetLastError() != cudaSuccess ||
             cudaMemcpy(order, dout, sizeof(uint16_t) * n, cudaMemcpyDeviceToHost) != cudaSuccess)
             st = PIC_ERR_CUDA;

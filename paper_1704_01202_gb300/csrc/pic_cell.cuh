@@ -39,6 +39,8 @@ struct CellArgs {
     int *cnt_e, *cnt_i;  // per-cell counts of the next sort
     int *append;         // electrons appended this step
     int cap_e;           // electron capacity
+    int *slab_app;       // [slab] electrons appended this step (budgeted slabs)
+    int *slab_err;       // [slab] ERR_CAPACITY once a slab went beyond its budget
     int ncell;           // total cells (all slabs)
     const int *cell_slab;
     const SlabDev *slabs;
@@ -56,7 +58,8 @@ struct CellArgs {
     const int *list;     // cell list (NULL: all cells)
     const int *n_list;   // number of cells in the list (device)
     int *ovf_list, *ovf_count;   // cells too large for this pass
-    int cap_ce, cap_ci, cap_new; // per-cell shared-memory capacities
+    int cap_ce, cap_ci, cap_new; // per-cell capacities (staging; created electrons)
+    NewE *nw;            // created-electron scratch: cap_new entries per warp of the launch
 };
 
 // warp reductions: a fixed tree, result broadcast from lane 0 so every lane
@@ -111,51 +114,19 @@ __device__ __forceinline__ dd wbcast_dd(dd v, int src)
     return dd{__shfl_sync(FULL, v.hi, src), __shfl_sync(FULL, v.lo, src)};
 }
 
-// Ascending sort of n entries on (key, id), padded to a power of two.  Only
-// the 64-bit keys and the 16-bit slots move; ids stay in slot order and are
-// read only when two keys tie.  Afterwards id[] is rewritten into the sorted
-// order (through tmp, n entries of scratch).  Padding entries (slot 0xffff)
-// order after everything.
-template <class IdT>
-__device__ void warp_bitonic(unsigned long long *key, IdT *id, unsigned short *slot, unsigned long long *tmp, int n,
-                             int lane)
-{
-    int np = 1;
-    while (np < n) np <<= 1;
-    for (int k = n + lane; k < np; k += 32) { key[k] = ~0ull; slot[k] = 0xffff; }
-    __syncwarp();
-    for (int size = 2; size <= np; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int t = lane; t < (np >> 1); t += 32) {
-                int lo = 2 * t - (t & (stride - 1));
-                int hi = lo + stride;
-                bool asc = (lo & size) == 0;
-                unsigned long long kl = key[lo], kh = key[hi];
-                unsigned short sl = slot[lo], sh = slot[hi];
-                bool gt = kl > kh;
-                if (kl == kh) {
-                    const bool pl = sl == 0xffff, ph = sh == 0xffff;
-                    gt = pl || ph ? (pl && !ph) : id[sl] > id[sh];
-                }
-                if (gt == asc) {
-                    key[lo] = kh; key[hi] = kl;
-                    slot[lo] = sh; slot[hi] = sl;
-                }
-            }
-            __syncwarp();
-        }
-    }
-    for (int k = lane; k < n; k += 32) tmp[k] = (unsigned long long)id[slot[k]];
-    __syncwarp();
-    for (int k = lane; k < n; k += 32) id[k] = (IdT)tmp[k];
-    __syncwarp();
-}
+// Sort of the cells larger than the register sorts take (n > radix_min of
+// the kernel instance): a stable LSD radix sort (four 8-bit digits) of the
+// keys' high 32 bits packed with the slot, then the rare runs of equal high
+// words reordered by (low word, id) by one lane.  buf holds 2 n packed
+// entries, hist 256 counters.
+__host__ __device__ constexpr int radix_min(int rmax) { return rmax > 512 ? rmax : 512; }
 
-// Sort of larger cells (n > kRadixMin), same result as warp_bitonic: a
-// stable LSD radix sort (four 8-bit digits) of the keys' high 32 bits packed
-// with the slot, then the rare runs of equal high words reordered by (low
-// word, id) by one lane.  buf holds 2 n packed entries, hist 256 counters.
-constexpr int kRadixMin = 512;
+// the cell-kernel instance (largest register sort) of a staging of ce
+// electrons and ci ions per cell
+__host__ __device__ constexpr int rmax_for(int ce, int ci)
+{
+    return ce <= 128 && ci <= 128 ? 128 : (ce <= 512 && ci <= 512 ? 512 : 1024);
+}
 
 template <class IdT>
 __device__ void warp_radix(const unsigned long long *key, IdT *id, unsigned short *slot, unsigned long long *tmp,
@@ -228,10 +199,11 @@ __device__ void warp_radix(const unsigned long long *key, IdT *id, unsigned shor
 
 // Sort of up to 32 E entries in registers, E per lane (entry lane * E + j):
 // the bitonic network over (key high 48 bits | slot) words, compare-exchange
-// through warp shuffles across lanes and in place within a lane.  Gives the
-// (key, slot) order, which is the (key, id) order unless two keys share
-// their high 48 bits (probability ~n^2 / 2^49 per cell): then it returns
-// false and leaves key[], id[] and slot[] untouched for the exact sort.
+// through warp shuffles across lanes and in place within a lane.  That is
+// the (key, id) order unless two keys share their high 48 bits (probability
+// ~n^2 / 2^49 per cell); such runs are then put in (key, id) order by one
+// lane.  slot[k] gets the slot at position k, id[] the ids in that order
+// (through tmp, n entries of scratch, which may be the key array).
 template <int E, int S>
 __device__ __forceinline__ void reg_cmpx_in_lane(unsigned long long (&v)[E], int lane, int size)
 {
@@ -246,9 +218,30 @@ __device__ __forceinline__ void reg_cmpx_in_lane(unsigned long long (&v)[E], int
     }
 }
 
+// runs of equal high 48 key bits of a (high 48 bits, slot) order into
+// (key, id) order: insertion within each run, by one lane
+template <class IdT>
+__device__ void order_ties(const unsigned long long *key, const IdT *id, unsigned short *slot, int n)
+{
+    for (int k = 1; k < n; ++k) {
+        const int sb = slot[k];
+        const unsigned long long kb = key[sb];
+        int j = k - 1;
+        while (j >= 0) {
+            const int sa = slot[j];
+            const unsigned long long ka = key[sa];
+            if ((ka >> 16) != (kb >> 16)) break;
+            if (!(ka > kb || (ka == kb && id[sa] > id[sb]))) break;
+            slot[j + 1] = (unsigned short)sa;
+            --j;
+        }
+        slot[j + 1] = (unsigned short)sb;
+    }
+}
+
 template <int E, class IdT>
-__device__ __forceinline__ bool warp_sort_reg(const unsigned long long *key, IdT *id, unsigned short *slot, int n,
-                                              int lane)
+__device__ __forceinline__ void warp_sort_reg(const unsigned long long *key, IdT *id, unsigned short *slot,
+                                              unsigned long long *tmp, int n, int lane)
 {
     unsigned long long v[E];
 #pragma unroll
@@ -273,8 +266,10 @@ __device__ __forceinline__ bool warp_sort_reg(const unsigned long long *key, IdT
                 reg_cmpx_in_lane<E, 2>(v, lane, size);
             } else if (stride == 4) {
                 reg_cmpx_in_lane<E, 4>(v, lane, size);
-            } else {
+            } else if (stride == 8) {
                 reg_cmpx_in_lane<E, 8>(v, lane, size);
+            } else {
+                reg_cmpx_in_lane<E, 16>(v, lane, size);
             }
         }
     }
@@ -286,50 +281,49 @@ __device__ __forceinline__ bool warp_sort_reg(const unsigned long long *key, IdT
         tie |= lane * E + j + 1 < n && (v[j] >> 16) == (v[j + 1] >> 16);
     const unsigned long long nx = __shfl_down_sync(FULL, v[0], 1);
     tie |= lane < 31 && lane * E + E < n && (v[E - 1] >> 16) == (nx >> 16);
-    if (__any_sync(FULL, tie)) return false;
-    IdT idv[E];
 #pragma unroll
     for (int j = 0; j < E; ++j) {
         const int k = lane * E + j;
-        idv[j] = k < n ? id[(int)(v[j] & 0xffffu)] : (IdT)0;
+        if (k < n) slot[k] = (unsigned short)(v[j] & 0xffffu);
     }
     __syncwarp();
-#pragma unroll
-    for (int j = 0; j < E; ++j) {
-        const int k = lane * E + j;
-        if (k < n) { slot[k] = (unsigned short)(v[j] & 0xffffu); id[k] = idv[j]; }
+    if (__any_sync(FULL, tie)) {
+        if (lane == 0) order_ties<IdT>(key, id, slot, n);
+        __syncwarp();
     }
+    for (int k = lane; k < n; k += 32) tmp[k] = (unsigned long long)id[slot[k]];
     __syncwarp();
-    return true;
+    for (int k = lane; k < n; k += 32) id[k] = (IdT)tmp[k];
+    __syncwarp();
 }
 
 // the larger register sorts out of line: their 16-32 key registers would
 // otherwise raise the register pressure of the whole cell kernel
 template <int E, class IdT>
-__device__ __noinline__ bool warp_sort_reg_call(const unsigned long long *key, IdT *id, unsigned short *slot, int n,
-                                                int lane)
+__device__ __noinline__ void warp_sort_reg_call(const unsigned long long *key, IdT *id, unsigned short *slot,
+                                                unsigned long long *tmp, int n, int lane)
 {
-    return warp_sort_reg<E, IdT>(key, id, slot, n, lane);
+    warp_sort_reg<E, IdT>(key, id, slot, tmp, n, lane);
 }
 
-// The in-cell canonical order, ascending (key, id): registers up to RMAX
-// entries (128 or 512; the shared-memory network when high words tie or
-// the cell is larger), the radix sort above kRadixMin.  slot[] must hold
-// 0..n-1 on entry.
+// The in-cell canonical order, ascending (key, id): in registers up to
+// RMAX entries (128, 512 or 1024: the kernel instance), the radix sort
+// above radix_min(RMAX).  slot[] must hold 0..n-1 on entry; n is at most
+// RMAX when rbuf is NULL (the staging of a kernel instance without the
+// radix buffer never holds more).
 template <class IdT, int RMAX = 512>
 __device__ void warp_sort(unsigned long long *key, IdT *id, unsigned short *slot, unsigned long long *tmp,
                           unsigned long long *rbuf, int *rhist, int n, int lane)
 {
-    if (n > kRadixMin) { warp_radix<IdT>(key, id, slot, tmp, rbuf, rhist, n, lane); return; }
-    bool done = false;
-    if (n <= 32) done = warp_sort_reg<1, IdT>(key, id, slot, n, lane);
-    else if (n <= 64) done = warp_sort_reg<2, IdT>(key, id, slot, n, lane);
-    else if (n <= 128) done = warp_sort_reg<4, IdT>(key, id, slot, n, lane);
+    if (n > radix_min(RMAX)) { warp_radix<IdT>(key, id, slot, tmp, rbuf, rhist, n, lane); return; }
+    if (n <= 32) warp_sort_reg<1, IdT>(key, id, slot, tmp, n, lane);
+    else if (n <= 64) warp_sort_reg<2, IdT>(key, id, slot, tmp, n, lane);
+    else if (n <= 128) warp_sort_reg<4, IdT>(key, id, slot, tmp, n, lane);
     else if constexpr (RMAX > 128) {
-        if (n <= 256) done = warp_sort_reg_call<8, IdT>(key, id, slot, n, lane);
-        else done = warp_sort_reg_call<16, IdT>(key, id, slot, n, lane);
+        if (n <= 256) warp_sort_reg_call<8, IdT>(key, id, slot, tmp, n, lane);
+        else if (n <= 512) warp_sort_reg_call<16, IdT>(key, id, slot, tmp, n, lane);
+        else if constexpr (RMAX > 512) warp_sort_reg_call<32, IdT>(key, id, slot, tmp, n, lane);
     }
-    if (!done) warp_bitonic<IdT>(key, id, slot, tmp, n, lane);
 }
 
 __device__ __forceinline__ real cic_w(real x, int node)
@@ -349,11 +343,11 @@ struct WarpMem {
     unsigned long long *ikey;   // [cap_ci] sort key, later reused as nrec
     unsigned int *iid;          // [cap_ci] ids in canonical order
     unsigned short *iperm;      // [cap_ci]
-    NewE *nw;                   // [cap_new]
+    NewE *nw;                   // [cap_new] in global memory: the warp's slice of the scratch
     real *dE;                  // [16] continuum lowering per charge state
     real *Pz;                  // [16] impact-ionization probability per charge
     real4 *lz;                 // [NS] Lotz constants of one charge state: P, 1/P, ln P, a q
-    unsigned long long *rbuf;   // [2 max(cap_ce, cap_ci)] radix sort (only when a cell can exceed kRadixMin)
+    unsigned long long *rbuf;   // [2 max(cap_ce, cap_ci)] radix sort (only when a cell can exceed radix_min)
     int *rhist;                 // [256]
     dd *ph;                     // [2 MAXB] photon bin scratch
     int *phc;                   // [MAXB] events per bin so far
@@ -365,20 +359,23 @@ constexpr size_t kSmAlign = sizeof(real4) > 16 ? 32 : 16;
 constexpr size_t kKeyBytes = sizeof(real2) > 8 ? sizeof(real2) : 8;
 __host__ __device__ inline size_t amem(size_t x) { return (x + kSmAlign - 1) & ~(kSmAlign - 1); }
 
-__host__ __device__ inline size_t warp_mem_bytes(int ce, int ci, int cn)
+// Shared memory of one warp staging up to ce electrons and ci ions.  The
+// electrons a cell creates in a step (up to 3 per ion: impact, photo- and
+// Auger ionization) are rare; they live in the warp's slice of a global
+// scratch, which keeps the staging of large cells small.
+__host__ __device__ inline size_t warp_mem_bytes(int ce, int ci)
 {
     size_t b = 0;
     b += amem((size_t)ce * sizeof(real4)) + amem((size_t)ce * kKeyBytes) + amem((size_t)ce * 8) + amem((size_t)ce * 2);
     b += amem((size_t)ci * sizeof(real4)) + amem((size_t)ci * 4) + amem((size_t)ci * 8) + amem((size_t)ci * 4)
          + amem((size_t)ci * 2);
-    b += amem((size_t)cn * sizeof(NewE));
     b += amem(16 * sizeof(real)) * 2 + amem(NS * sizeof(real4)) + amem(2 * MAXB * sizeof(dd)) + amem(MAXB * 4);
     const int cm = ce > ci ? ce : ci;
-    if (cm > kRadixMin) b += amem((size_t)cm * 16) + 256 * 4;
+    if (cm > radix_min(rmax_for(ce, ci))) b += amem((size_t)cm * 16) + 256 * 4;
     return b;
 }
 
-__device__ inline WarpMem carve(char *base, int ce, int ci, int cn)
+__device__ inline WarpMem carve(char *base, int ce, int ci, NewE *nw)
 {
     WarpMem m;
     char *p = base;
@@ -391,7 +388,7 @@ __device__ inline WarpMem carve(char *base, int ce, int ci, int cn)
     m.ikey = (unsigned long long *)p; p += amem((size_t)ci * 8);
     m.iid = (unsigned int *)p; p += amem((size_t)ci * 4);
     m.iperm = (unsigned short *)p; p += amem((size_t)ci * 2);
-    m.nw = (NewE *)p; p += amem((size_t)cn * sizeof(NewE));
+    m.nw = nw;
     m.dE = (real *)p; p += amem(16 * sizeof(real));
     m.Pz = (real *)p; p += amem(16 * sizeof(real));
     m.lz = (real4 *)p; p += amem(NS * sizeof(real4));
@@ -399,7 +396,7 @@ __device__ inline WarpMem carve(char *base, int ce, int ci, int cn)
     m.phc = (int *)p; p += amem(MAXB * 4);
     const int cm = ce > ci ? ce : ci;
     m.rbuf = nullptr; m.rhist = nullptr;
-    if (cm > kRadixMin) {
+    if (cm > radix_min(rmax_for(ce, ci))) {
         m.rbuf = (unsigned long long *)p; p += amem((size_t)cm * 16);
         m.rhist = (int *)p;
     }

@@ -883,12 +883,26 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
     }
     // ---- created electrons: after the sorted range, at their ion, with their cell as key ----
     if (nnew > 0) {
-        int base = 0;
-        if (lane == 0) base = atomicAdd(a.append, nnew);
+        // a slab with a budget of its own keeps its electrons within it: a
+        // cell that would take it beyond drops what it created and fails
+        // the slab alone (it is stopped at the end of the step); the others
+        // never see the shared capacity run out when the budgets fit in it
+        int base = 0, fits = 1;
+        if (lane == 0) {
+            if (S.budget_e > 0) {
+                const int held = a.cs_e[S.cell0 + S.ncell] - a.cs_e[S.cell0];
+                if (held + atomicAdd(a.slab_app + s, nnew) + nnew > S.budget_e) {
+                    atomicOr(a.slab_err + s, ERR_CAPACITY);
+                    fits = 0;
+                }
+            }
+            if (fits) base = atomicAdd(a.append, nnew);
+        }
+        fits = __shfl_sync(FULL, fits, 0);
         base = __shfl_sync(FULL, base, 0);
         const int sorted = a.cs_e[a.ncell];
-        int n_ok = nnew;
-        if (sorted + base + nnew > a.cap_e) {
+        int n_ok = fits ? nnew : 0;
+        if (fits && sorted + base + nnew > a.cap_e) {
             if (lane == 0) atomicOr(a.err, ERR_CAPACITY);
             for (int k = sorted + base + lane; k < min(a.cap_e, sorted + base + nnew); k += 32) a.ekey[k] = -1;
             n_ok = 0;
@@ -919,9 +933,11 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
 // Cells whose population exceeds this launch's shared-memory capacity go to
 // a list for the large-cell launch.
 // RMAX: the largest cell sorted in registers (128: launches whose staging
-// holds at most 128 entries per species; 512: the launches for larger cells)
+// holds at most 128 entries per species; 512: up to 512; 1024: the launches
+// for larger cells, with up to 255 registers a thread for the 32-entry
+// register sort, radix-sorting cells above 1024).
 template <int RMAX>
-__global__ void __launch_bounds__(256, 2) k_cell(CellArgs a)
+__global__ void __launch_bounds__(RMAX > 512 ? 128 : 256, RMAX > 512 ? 1 : 2) k_cell(CellArgs a)
 {
     extern __shared__ __align__(kSmAlign) char smem[];
     __shared__ Tables T;
@@ -929,8 +945,8 @@ __global__ void __launch_bounds__(256, 2) k_cell(CellArgs a)
     for (int k = threadIdx.x; k < (int)(sizeof(Tables) / sizeof(real)); k += blockDim.x)
         ((real *)&T)[k] = ((const real *)a.tab)[k];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    WarpMem m = carve(smem + (size_t)warp * warp_mem_bytes(a.cap_ce, a.cap_ci, a.cap_new),
-                      a.cap_ce, a.cap_ci, a.cap_new);
+    WarpMem m = carve(smem + (size_t)warp * warp_mem_bytes(a.cap_ce, a.cap_ci), a.cap_ce, a.cap_ci,
+                      a.nw + (size_t)(blockIdx.x * nwarp + warp) * a.cap_new);
     const int total = a.list ? *a.n_list : a.ncell;
     WarpTally wt;
     wt.slab = -1;

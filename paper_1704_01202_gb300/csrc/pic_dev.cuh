@@ -188,6 +188,7 @@ struct SlabDev {
     int ipd;
     int nsub;               // field updates per step (1: the field speed below is resolved by dt)
     int shape;
+    int budget_e;           // electron slots the slab may hold after a step (0: only the context's capacity)
     real dx, dy, dt;
     real w_ion, m_ion, E_bulk, coulomb_log;
     real mur;              // first-order Mur coefficient

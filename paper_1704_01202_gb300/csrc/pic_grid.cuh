@@ -321,10 +321,17 @@ __global__ void k_e_full(FieldArgs a)
     }
 }
 
-__global__ void k_advance(unsigned *steps, const SlabDev *slabs, int nslab)
+// end of a step: every running slab's step count advances; a slab that
+// went beyond its electron budget this step stops (its particles are dropped
+// by the next push); the per-slab append counts start again from zero
+__global__ void k_advance(unsigned *steps, SlabDev *slabs, int nslab, int *slab_app, const int *slab_err)
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < nslab && slabs[s].active) steps[s] += 1u;
+    if (s >= nslab) return;
+    slab_app[s] = 0;
+    if (!slabs[s].active) return;
+    if (slab_err[s]) slabs[s].active = 0;
+    else steps[s] += 1u;
 }
 
 // keys of the sorted particles for a re-sort: their own cell, or -1 when
@@ -420,23 +427,23 @@ __global__ void k_photon_energy(const ph2 *ph, int ncell, int nb, const real *hv
     if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(out, v);
 }
 
-// the in-cell ordering of one cell (the cell kernel's warp_sort), run by
-// one warp on given keys and ids: order[k] = slot at position k
+// the in-cell ordering of one cell (the cell kernel's warp_sort of the
+// kernel instance RMAX), run by one warp on given keys and ids:
+// order[k] = slot at position k
+template <int RMAX>
 __global__ void k_order_check(const unsigned long long *key_in, const unsigned long long *id_in, int n,
                               unsigned short *order)
 {
     extern __shared__ __align__(16) char sm[];
-    int np = 1;
-    while (np < n) np <<= 1;
-    unsigned long long *key = (unsigned long long *)sm;                  // [np]
-    unsigned long long *id = key + np;                                    // [np]
-    unsigned long long *buf = id + np;                                    // [2 n]
+    unsigned long long *key = (unsigned long long *)sm;                  // [n]
+    unsigned long long *id = key + n;                                     // [n]
+    unsigned long long *buf = id + n;                                     // [2 n]
     int *hist = (int *)(buf + 2 * n);                                     // [256]
-    unsigned short *slot = (unsigned short *)(hist + 256);               // [np]
+    unsigned short *slot = (unsigned short *)(hist + 256);               // [n]
     const int lane = threadIdx.x;
     for (int k = lane; k < n; k += 32) { key[k] = key_in[k]; id[k] = id_in[k]; slot[k] = (unsigned short)k; }
     __syncwarp();
-    warp_sort<unsigned long long>(key, id, slot, key, buf, hist, n, lane);
+    warp_sort<unsigned long long, RMAX>(key, id, slot, key, buf, hist, n, lane);
     for (int k = lane; k < n; k += 32) order[k] = slot[k];
 }
 

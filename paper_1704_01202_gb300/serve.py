@@ -24,36 +24,76 @@ import numpy as np
 from . import Batch, Slab, default_capacity
 
 
-def footprint(cfg) -> tuple[int, int]:
-    """Worst-case electron and ion slots of a slab: every ion fully stripped."""
+F_PHOTO = 16          # the photoionization flag of pic_species
+
+
+def footprint(cfg, pulse=None, partial_per_cell: int = 1) -> tuple[int, int]:
+    """Electron and ion slots reserved for a slab at admission.
+
+    Electrons: the slab's own, one per charge its ions can still lose by
+    whole events (every ion stripped), and partial_per_cell partial-event
+    electrons per photon bin per cell: an absorption of fewer photons than
+    one ion weight (Sec. III, Eq. 2) creates an electron macroparticle of
+    fractional weight and advances the ion's charge by that fraction only,
+    so these electrons are not bounded by the charge the ions can lose.
+    Their worst case, one per bin per cell per rad step (partial_bound), is
+    far above what a slab creates; a slab that outgrows its reservation is
+    stopped by its budget and run again with a larger one."""
     n_e, n_i = cfg.ncell * cfg.ppc_e, cfg.ncell * cfg.ppc_i
-    return n_e + n_i * (13 - cfg.Z_init), n_i
+    nb = pulse.n_bins if pulse is not None and (cfg.flags & F_PHOTO) else 0
+    return n_e + n_i * (13 - cfg.Z_init) + cfg.ncell * nb * partial_per_cell, n_i
+
+
+def partial_bound(cfg, pulse, nsteps: int) -> int:
+    """Most partial-event electrons a slab can create in nsteps: one per
+    photon bin per cell per rad step."""
+    if pulse is None or not (cfg.flags & F_PHOTO) or cfg.rad_every <= 0:
+        return 0
+    return cfg.ncell * pulse.n_bins * (-(-nsteps // cfg.rad_every))
 
 
 def _summary(ttr: dict, t0: float, t_end: float, n: int) -> dict:
-    v = np.array([ttr[k] for k in sorted(ttr)])
+    v = np.array([ttr[k] for k in sorted(ttr)]) if ttr else np.zeros(1)
     return {"slabs": n, "wall_s": t_end - t0, "slabs_per_s": n / (t_end - t0),
             "ttr_p50_s": float(np.percentile(v, 50)), "ttr_p99_s": float(np.percentile(v, 99)),
             "ttr_mean_s": float(v.mean())}
 
 
 def serve_batched(trace, tables, init_state, max_slabs: int, slot_cells: int, cap_e: int, cap_i: int,
-                  tick_steps: int = 25, keep=None, diag_bins: int = 64, autotune: bool = False) -> dict:
+                  tick_steps: int = 25, keep=None, diag_bins: int = 64, autotune: bool = False,
+                  grow: int = 4, batch=None) -> dict:
     """Continuous batching of `trace` (requests sorted by arrival).
 
     init_state(request) -> ParticleState gives a request's particles (the
     request payload, on the host).  keep(rid) -> bool selects requests whose
-    final particles are returned (for tests).  Admission: first come first served, while a slot
-    is free and the reserved worst-case footprints fit cap_e / cap_i.
-    autotune: let the launch-shape autotuner time the cell kernel's warps
-    per CTA for each new staging size (results do not depend on it)."""
-    bt = Batch(tables, max_slabs, slot_cells, cap_e, cap_i)
+    final particles are returned (for tests).
+
+    Admission: first come first served, while a slot is free and the
+    request's reservation (footprint) fits beside the others' in cap_e /
+    cap_i; later arrivals wait in the queue.  Each admitted slab gets its
+    reservation as its electron budget on the device, so the reservations
+    never overcommit the shared capacity and a slab that outgrows its own is
+    stopped alone (pic_batch_set_budget) while the others run on.  Such a
+    slab is preempted: its slot and reservation are freed and it is queued
+    again, at the head, with grow times the partial-event allowance; its
+    result does not depend on where or when it runs, so the re-run returns
+    what an unconstrained run would.  A request whose reservation exceeds
+    cap_e before reaching its worst case fails alone (reported in
+    `failed`), as does one that outgrows even the worst-case reservation
+    (ions stripped again after recombining).  autotune: let the launch-shape autotuner time the cell
+    kernel's warps per CTA for each new staging size (results do not depend
+    on it).  batch: an object with the Batch interface to drive instead of
+    a new Batch (host-logic tests)."""
+    from . import SLOT_FAILED
+    bt = batch if batch is not None else Batch(tables, max_slabs, slot_cells, cap_e, cap_i)
     if autotune:
         bt.autotune(True)
     pending = list(trace)
-    active = {}                      # slot -> [request, steps left, footprint]
+    allowance = {}                   # rid -> partial-event electrons per bin per cell
+    active = {}                      # slot -> [request, steps left, reservation]
     res_e = res_i = 0
-    ttr, results, finals = {}, {}, {}
+    ttr, results, finals, failed = {}, {}, {}, {}
+    admitted_at, preempted, max_queue = {}, 0, 0
     t0 = time.perf_counter()
     try:
         while pending or active:
@@ -61,26 +101,53 @@ def serve_batched(trace, tables, init_state, max_slabs: int, slot_cells: int, ca
             # admit what has arrived, in order, while it fits
             while pending and pending[0].t_arrive <= now:
                 r = pending[0]
-                fe, fi = footprint(r.cfg)
+                a = allowance.setdefault(r.rid, 1)
+                fe, fi = footprint(r.cfg, r.pulse, a)
                 if r.cfg.nx > slot_cells or fe > cap_e or fi > cap_i:
-                    raise ValueError(f"request {r.rid} can never fit the batch")
+                    if a == 1:
+                        raise ValueError(f"request {r.rid} can never fit the batch")
+                    failed[r.rid] = f"needs more than {cap_e} electron slots"
+                    ttr[r.rid] = time.perf_counter() - t0 - r.t_arrive
+                    pending.pop(0)
+                    continue
                 if len(active) >= max_slabs or res_e + fe > cap_e or res_i + fi > cap_i:
                     break
                 slot = bt.admit(r.cfg, init_state(r), r.pulse)
+                bt.set_budget(slot, fe)
                 active[slot] = [r, r.nsteps, (fe, fi)]
+                admitted_at.setdefault(r.rid, now)
                 res_e, res_i = res_e + fe, res_i + fi
                 pending.pop(0)
+            max_queue = max(max_queue, sum(1 for q in pending if q.t_arrive <= now))
             if not active:
                 if pending:
                     time.sleep(max(0.0, pending[0].t_arrive - (time.perf_counter() - t0)))
                 continue
             n = min(tick_steps, min(a[1] for a in active.values()))
             bt.step(n)
+            stopped = set(bt.failed())
+            back = []
             for slot in list(active):
                 a = active[slot]
+                r = a[0]
+                if slot in stopped:
+                    # preempted: free the slot and the reservation, queue again
+                    # with a larger one (up to one partial-event electron per
+                    # bin per cell per rad step of the horizon)
+                    bt.retire(slot)
+                    res_e, res_i = res_e - a[2][0], res_i - a[2][1]
+                    del active[slot]
+                    worst = -(-r.nsteps // max(1, r.cfg.rad_every))
+                    if allowance[r.rid] >= worst:
+                        failed[r.rid] = f"went beyond the {a[2][0]} electron slots of its worst case"
+                        ttr[r.rid] = time.perf_counter() - t0 - r.t_arrive
+                        continue
+                    allowance[r.rid] = min(worst, allowance[r.rid] * grow)
+                    preempted += 1
+                    back.append(r)
+                    continue
                 a[1] -= n
                 if a[1] == 0:
-                    r = a[0]
                     results[r.rid] = bt.diagnostics(slot, n_E=diag_bins)
                     if keep is not None and keep(r.rid):
                         finals[r.rid] = (bt.electrons(slot), bt.ions(slot))
@@ -88,12 +155,17 @@ def serve_batched(trace, tables, init_state, max_slabs: int, slot_cells: int, ca
                     bt.retire(slot)
                     res_e, res_i = res_e - a[2][0], res_i - a[2][1]
                     del active[slot]
+            pending[:0] = sorted(back, key=lambda q: q.t_arrive)
         bt.sync()
         t_end = time.perf_counter()
     finally:
-        bt.close()
+        if batch is None:
+            bt.close()
     out = _summary(ttr, t0, t_end, len(trace))
-    out.update(results=results, finals=finals, ttr=ttr)
+    wait = np.array([admitted_at[k] - q.t_arrive for q in trace for k in [q.rid] if k in admitted_at])
+    out.update(results=results, finals=finals, ttr=ttr, failed=failed, preempted=preempted,
+               max_queue=max_queue, wait_p50_s=float(np.percentile(wait, 50)) if len(wait) else 0.0,
+               wait_p99_s=float(np.percentile(wait, 99)) if len(wait) else 0.0)
     return out
 
 
@@ -139,7 +211,7 @@ def main():
     tab = P.standin_tables()
     if args.static:
         tr = P.request_trace(n=args.static, rate_hz=200.0, seed=11, horizon_fs=args.horizon_fs)
-        fp = [footprint(r.cfg) for r in tr]
+        fp = [footprint(r.cfg, r.pulse) for r in tr]
         bt = Batch(tab, len(tr), max(r.cfg.nx for r in tr), sum(f[0] for f in fp) + 1024, sum(f[1] for f in fp) + 1024)
         try:
             bt.use_graphs(False)
@@ -156,7 +228,7 @@ def main():
         return
     tr = P.request_trace(n=args.requests, rate_hz=200.0, seed=11, horizon_fs=args.horizon_fs)
     payload = {r.rid: P.init_particles(r.cfg) for r in tr}
-    fp = [footprint(r.cfg) for r in tr]
+    fp = [footprint(r.cfg, r.pulse) for r in tr]
     cap_e = max(max(f[0] for f in fp), int(64 * sum(f[0] for f in fp) / len(fp)))
     cap_i = max(max(f[1] for f in fp), int(64 * sum(f[1] for f in fp) / len(fp)))
     b = serve_batched(tr, tab, lambda r: payload[r.rid], 128, max(r.cfg.nx for r in tr), cap_e, cap_i)

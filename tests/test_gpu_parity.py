@@ -398,20 +398,24 @@ def test_thermalization_conserves_cell_momentum_energy_gpu(tables):
     g.close()
 
 
-@pytest.mark.parametrize("n", [1, 2, 31, 64, 100, 128, 129, 300, 512, 513, 1000])
+@pytest.mark.parametrize("n", [1, 2, 31, 64, 100, 128, 129, 300, 512, 513, 1000, 1024, 1025, 2048, 4000])
 def test_cell_order_matches_lexsort(n):
-    """The device's in-cell ordering (bitonic up to 512 entries, radix sort
-    above) is the ascending (key, id) order: random keys, keys whose high
-    words collide, and fully equal keys broken by id."""
+    """The device's in-cell ordering (in registers up to 128, 512 or 1024
+    entries by kernel instance, the radix sort above) is the ascending
+    (key, id) order: random keys, keys whose high words collide, and fully
+    equal keys broken by id."""
     rng = np.random.default_rng(n)
     ids = rng.permutation(np.arange(10 * n, dtype=np.uint64))[:n]
     cases = [rng.integers(0, 2**63, n, dtype=np.uint64) * np.uint64(2) + rng.integers(0, 2, n, dtype=np.uint64),
              (rng.integers(0, 4, n, dtype=np.uint64) << np.uint64(32)) | rng.integers(0, 2**32, n, dtype=np.uint64),
              (rng.integers(0, 3, n, dtype=np.uint64) << np.uint64(40)) | rng.integers(0, 3, n, dtype=np.uint64)]
     for key in cases:
-        got = pkg.order_check(key, ids)
         ref = np.lexsort((ids, key))
-        assert np.array_equal(got, ref)
+        for rmax in (128, 512, 1024):
+            if rmax == 128 and n > 128:
+                continue
+            got = pkg.order_check(key, ids, rmax)
+            assert np.array_equal(got, ref), rmax
 
 
 def test_small_slab_full_500_steps(tables):
