@@ -474,7 +474,7 @@ def run_served(pkg, tab, args):
     o = serve.serve_one_at_a_time(sample, tab, init)
     psteps = sum(r.nsteps * r.cfg.ncell * (r.cfg.ppc_e + r.cfg.ppc_i) for r in tr)
     keys = ("slabs_per_s", "ttr_p50_s", "ttr_p99_s", "ttr_mean_s", "wall_s", "wait_p50_s", "wait_p99_s",
-            "max_queue", "preempted")
+            "max_queue", "preempted", "busy_s")
     return {"trace": f"{len(tr)} Poisson arrivals at 200/s, ensemble draws + thickness U(0.2, 2) um, "
                      f"each run {args.serve_horizon_fs:g} fs ({tr[0].nsteps} steps)",
             "batched": {k: b[k] for k in keys}, "failed": len(b["failed"]),

@@ -731,6 +731,7 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
         // kinetic energy and w * beta of each electron (canonical order), kept
         // in the sort-key storage, which is free until recombination
         real2 *ew = reinterpret_cast<real2 *>(m.ekey);
+        int nhot;
         if (!ew_ready) {
             dd pk = dd_zero();
             for (int k = lane; k < ne; k += 32) {
@@ -743,6 +744,34 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
             Kt = wsum_dd(pk);
         }
         __syncwarp();
+        // Electrons at or below the lowest lowered binding of every charge
+        // state present ionize nothing and add nothing to the sums: the
+        // others (a hot tail, typically a few per cent) are gathered in
+        // canonical order to the front of the storage, so that a warp's
+        // lanes do not idle beside the one lane with a hot electron.
+        nhot = ne;
+        {
+            real Pall = RF(3.0e38);
+            for (int z = 0; z < ZNUC; ++z) {
+                if (!(pmask & (1u << z))) continue;
+                if (lane < NS && subshell_occ(ZNUC - z, lane) > 0)
+                    Pall = r_fmin(Pall, lowered_binding(T, z, lane, m.dE[z]));
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) Pall = r_fmin(Pall, __shfl_xor_sync(FULL, Pall, o));
+            int nh = 0;
+            for (int b0 = 0; b0 < ne; b0 += 32) {
+                const int k = b0 + lane;
+                const real2 q = k < ne ? ew[k] : make_real2(RF(0.0), RF(0.0));
+                const bool hot = k < ne && q.x > Pall;
+                const unsigned bal = __ballot_sync(FULL, hot);
+                __syncwarp();
+                if (hot) ew[nh + __popc(bal & ((1u << lane) - 1u))] = q;
+                nh += __popc(bal);
+                __syncwarp();
+            }
+            nhot = nh;
+        }
         const real cfac = (real)(kCcmPerFs) * S.dt * nref;
         for (int z = 0; z < ZNUC; ++z) {
             if (!(pmask & (1u << z))) continue;
@@ -758,11 +787,18 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
                 m.lz[lane] = v;
             }
             __syncwarp();
+            // the lowest lowered binding of the charge state: electrons at
+            // or below it ionize no subshell and add nothing to the sum
+            real Pmin = RF(3.0e38);
+#pragma unroll
+            for (int sh = 0; sh < NS; ++sh)
+                if (m.lz[sh].w > RF(0.0)) Pmin = r_fmin(Pmin, m.lz[sh].x);
             // fast log / exp: a few ulp on a probability; only a decision
             // within that of its threshold could flip
             dd pr = dd_zero();
-            for (int k = lane; k < ne; k += 32) {
+            for (int k = lane; k < nhot; k += 32) {
                 const real2 q = ew[k];
+                if (!(q.x > Pmin)) continue;
                 const real E = q.x, lnE = r_flog(E), invE = RF(1.0) / E;
                 real sig = RF(0.0);
 #pragma unroll

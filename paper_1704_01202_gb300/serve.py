@@ -94,6 +94,7 @@ def serve_batched(trace, tables, init_state, max_slabs: int, slot_cells: int, ca
     res_e = res_i = 0
     ttr, results, finals, failed = {}, {}, {}, {}
     admitted_at, preempted, max_queue = {}, 0, 0
+    busy = {"step": 0.0, "admit": 0.0, "results": 0.0}   # host wall time by phase
     t0 = time.perf_counter()
     try:
         while pending or active:
@@ -112,8 +113,10 @@ def serve_batched(trace, tables, init_state, max_slabs: int, slot_cells: int, ca
                     continue
                 if len(active) >= max_slabs or res_e + fe > cap_e or res_i + fi > cap_i:
                     break
+                ta = time.perf_counter()
                 slot = bt.admit(r.cfg, init_state(r), r.pulse)
                 bt.set_budget(slot, fe)
+                busy["admit"] += time.perf_counter() - ta
                 active[slot] = [r, r.nsteps, (fe, fi)]
                 admitted_at.setdefault(r.rid, now)
                 res_e, res_i = res_e + fe, res_i + fi
@@ -124,8 +127,11 @@ def serve_batched(trace, tables, init_state, max_slabs: int, slot_cells: int, ca
                     time.sleep(max(0.0, pending[0].t_arrive - (time.perf_counter() - t0)))
                 continue
             n = min(tick_steps, min(a[1] for a in active.values()))
+            ts = time.perf_counter()
             bt.step(n)
             stopped = set(bt.failed())
+            tr_ = time.perf_counter()
+            busy["step"] += tr_ - ts
             back = []
             for slot in list(active):
                 a = active[slot]
@@ -156,6 +162,7 @@ def serve_batched(trace, tables, init_state, max_slabs: int, slot_cells: int, ca
                     res_e, res_i = res_e - a[2][0], res_i - a[2][1]
                     del active[slot]
             pending[:0] = sorted(back, key=lambda q: q.t_arrive)
+            busy["results"] += time.perf_counter() - tr_
         bt.sync()
         t_end = time.perf_counter()
     finally:
@@ -164,7 +171,7 @@ def serve_batched(trace, tables, init_state, max_slabs: int, slot_cells: int, ca
     out = _summary(ttr, t0, t_end, len(trace))
     wait = np.array([admitted_at[k] - q.t_arrive for q in trace for k in [q.rid] if k in admitted_at])
     out.update(results=results, finals=finals, ttr=ttr, failed=failed, preempted=preempted,
-               max_queue=max_queue, wait_p50_s=float(np.percentile(wait, 50)) if len(wait) else 0.0,
+               max_queue=max_queue, busy_s=busy, wait_p50_s=float(np.percentile(wait, 50)) if len(wait) else 0.0,
                wait_p99_s=float(np.percentile(wait, 99)) if len(wait) else 0.0)
     return out
 
