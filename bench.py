@@ -196,6 +196,27 @@ def capacity(cfg, n_e, n_i):
     return min(ce, int(9.5 * n_i) + 1024, (1 << 31) - (1 << 28)), ci
 
 
+ENERGY_KEYS = ("ke_e", "ke_i", "e_ion", "e_phot", "e_field", "e_esc", "e_trans", "e_ka_esc")
+
+
+def energy_total(d):
+    """Total energy of the diagnostics' bookkeeping (eV x weight): kinetic,
+    ionization, photons in the slab, fields, escaped and transmitted, minus
+    what the pulse brought in."""
+    return sum(d[k] for k in ENERGY_KEYS) - d["e_inc"]
+
+
+def energy_drift(d0, d1, d2, n01, n12):
+    """Relative change of the total energy per 1000 steps, over the advance
+    (d0 -> d1, n01 steps) and the timed steps (d1 -> d2), against the energy
+    the slab holds (kinetic + ionization + photons + fields) at d1."""
+    held = sum(d1[k] for k in ("ke_e", "ke_i", "e_ion", "e_phot", "e_field"))
+    out = {"reference": "energy held at the start of the timed steps", "held": held}
+    for name, a, b, n in (("advance", d0, d1, n01), ("timed", d1, d2, n12)):
+        out[name] = {"steps": n, "rel_per_1000_steps": (energy_total(b) - energy_total(a)) / held * 1000.0 / max(n, 1)}
+    return out
+
+
 def charge_states(csd, share=0.01):
     """Charge states holding more than `share` of the ions."""
     return [z for z, f in enumerate(csd) if f > share]
@@ -234,6 +255,7 @@ def run_gpu(args):
     tune_steps = 0 if args.no_autotune else min(9, n_adv)
     adv = {"steps": n_adv, "fs": n_adv * cfg.dt_fs}
     ne_a, ni_a = slab.counts()
+    d_start = slab.diagnostics()
     a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     a0.record(stream)
@@ -276,6 +298,8 @@ def run_gpu(args):
     tms, nrec = slab.timing(None)
     slab.timing(False)
     ne1, ni1 = slab.counts()
+    d_end = slab.diagnostics()
+    energy = energy_drift(d_start, dw, d_end, n_adv + args.warmup, args.steps)
     n_mean = 0.5 * (ne0 + ni0 + ne1 + ni1)
     ms, value = aggregate(ms, n_mean * args.steps, dist, "cuda")
 
@@ -321,7 +345,7 @@ def run_gpu(args):
                           "pulse_Wcm2": pl.I_peak_Wcm2, "pulse_peak_fs": pl.t_peak_fs,
                           "l2": f"state ({n_mean * 32 / 1e9:.0f} GB) larger than L2; no flush",
                           "parallelism": "replicas", "host_generation_s": round(t_gen, 1)},
-               "timed_window": window, "advance": adv,
+               "timed_window": window, "advance": adv, "energy_drift": energy,
                "roofline": roof, "step_hbm_gbs": step_gbs, "cpu_baseline": cb, "e2e": e2e,
                "gpu_launches": int(launches), "clocks": clk, "kernel_ms": {k: v / max(nrec, 1) for k, v in tms.items()},
                "autotune": {"cell_warps_per_cta": tuned[0], "cell_ms_1_2_4_8": [float(x) for x in tuned[1]]},

@@ -197,6 +197,29 @@ pic_status pic_rt_set(pic_ctx *c, const double *F, const double *Gx, const doubl
  * due to its bulk electrons ([ncell] each).  Synchronizes. */
 pic_status pic_rt_cells(pic_ctx *c, double *chi, double *emc, double *w, double *dE);
 
+/* Initial plasma of the slab (Sec. II's solid-density start, seeded on the
+ * device): ppc_e electrons and ppc_i ions in every cell at uniform random
+ * positions (y = 0.5 in 1D), ions at charge Z_init with full K shells,
+ * Maxwellian momenta at T_i, electrons Maxwellian at T_e except a
+ * beam_frac share (each electron drawn alone) at beam_E_eV with isotropic
+ * directions.  Weights: ions the species' w_ion, electrons
+ * Z_init ppc_i w_ion / ppc_e (the slab neutral).  Ids: cell-major
+ * positions, 0 .. ncell ppc - 1 per species.  Random numbers: Philox4x32-10
+ * keyed by (seed, id) on streams of their own.  Replaces any particles
+ * (pic_load_* remain for states built elsewhere). */
+typedef struct {
+    int ppc_e, ppc_i;       /* macro-electrons and macro-ions per cell (>= 1) */
+    int Z_init;             /* initial ion charge, 0 .. 12 */
+    double T_e_eV, T_i_eV;  /* Maxwellian temperatures (>= 0) */
+    double beam_frac;       /* share of electrons in the beam, 0 .. 1 */
+    double beam_E_eV;       /* beam kinetic energy (>= 0) */
+    uint64_t seed;          /* key of the seeding streams */
+} pic_seed_spec;
+
+/* PIC_ERR_ARG: spec out of range; PIC_ERR_CAPACITY: more particles than
+ * the capacity; PIC_ERR_STATE: batch context.  Synchronizes. */
+pic_status pic_seed(pic_ctx *c, const pic_seed_spec *s);
+
 /* Load particles from host memory (absolute positions in cell units).
  * u is [n][3]; ids must be unique per species.  Replaces any particles. */
 pic_status pic_load_electrons(pic_ctx *c, int64_t n, const double *X, const double *Y,
@@ -352,6 +375,14 @@ const char *pic_last_error(const pic_ctx *c);
 /* Philox4x32-10 of the device path, for checking it against other
  * implementations: out[4*i..] = philox(ctr[4*i..], key) for i < n. */
 pic_status pic_philox_check(const uint32_t *ctr, const uint32_t key[2], uint32_t *out, int n);
+
+/* The sum of n <= 2^24 FP32 terms x (host array) as the cell kernel forms
+ * its per-cell energy, weight and charge sums (Sec. IV's energy restore,
+ * Sec. II's cell moments): double-float pairs (a float hi + lo, ~44-48 bit
+ * significand; two doubles in the FP64 build) accumulated lane-strided by
+ * one warp and reduced by its fixed tree; *out = hi + lo.  For bounding that
+ * arithmetic against exact sums.  PIC_ERR_ARG on n out of range. */
+pic_status pic_dd_sum_check(const float *x, int n, double *out);
 
 /* The in-cell ordering of the device (ascending key, ties by id; the
  * canonical order every per-cell rule follows), run on n <= 4096 given

@@ -45,7 +45,7 @@ ABI_FUNCTIONS = ["pic_required_bytes", "pic_init", "pic_source", "pic_load_elect
                  "pic_timing", "pic_batch_required_bytes", "pic_batch_init", "pic_batch_admit",
                  "pic_batch_retire", "pic_batch_set_budget", "pic_batch_slot", "pic_batch_diagnostics", "pic_batch_counts",
                  "pic_batch_get_electrons", "pic_batch_get_ions", "pic_philox_check_static",
-                 "pic_use_graphs", "pic_autotune", "pic_order_check",
+                 "pic_use_graphs", "pic_autotune", "pic_order_check", "pic_dd_sum_check", "pic_seed",
                  "pic_get_electrons64", "pic_get_ions64", "pic_real_bytes",
                  "pic_rt", "pic_rt_get", "pic_rt_set", "pic_rt_cells"]
 
@@ -126,6 +126,12 @@ class Diag(C.Structure):
                 ("e_back", C.c_double), ("e_rt_num", C.c_double), ("e_rt_pend", C.c_double)]
 
 
+class SeedSpec(C.Structure):
+    _fields_ = [("ppc_e", C.c_int), ("ppc_i", C.c_int), ("Z_init", C.c_int), ("T_e_eV", C.c_double),
+                ("T_i_eV", C.c_double), ("beam_frac", C.c_double), ("beam_E_eV", C.c_double),
+                ("seed", C.c_uint64)]
+
+
 class RTConfig(C.Structure):
     _fields_ = [("coarsen", C.c_int), ("n_polar", C.c_int), ("n_azimuth", C.c_int), ("scheme", C.c_int)]
 
@@ -180,6 +186,8 @@ def lib(fp64: bool = False):
             L.pic_use_graphs.argtypes = [_P, C.c_int]
             L.pic_order_check.argtypes = [C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.c_int, C.c_int,
                                           C.POINTER(C.c_uint16)]
+            L.pic_dd_sum_check.argtypes = [_F, C.c_int, _D]
+            L.pic_seed.argtypes = [_P, C.POINTER(SeedSpec)]
             L.pic_autotune.argtypes = [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]
             L.pic_timing.argtypes = [_P, C.c_int, _D, C.POINTER(C.c_int64)]
             L.pic_rt.argtypes = [_P, C.POINTER(RTConfig)]
@@ -343,6 +351,15 @@ class Slab:
         self._check(self.L.pic_load_electrons(self.h, *e), "pic_load_electrons")
         _ik, i = _ion_args(st)
         self._check(self.L.pic_load_ions(self.h, *i), "pic_load_ions")
+
+    def seed(self, seed=None):
+        """Seed the initial plasma of the slab's configuration on the device
+        (pic_seed): ppc, temperatures, beam and Z_init of the config; the
+        config's seed unless one is given."""
+        c = self.cfg
+        spec = SeedSpec(c.ppc_e, c.ppc_i, c.Z_init, c.T_e_eV, c.T_i_eV, c.beam_frac, c.beam_E_eV,
+                        int(c.seed if seed is None else seed))
+        self._check(self.L.pic_seed(self.h, C.byref(spec)), "pic_seed")
 
     def step(self, n=1):
         self._check(self.L.pic_step(self.h, n), "pic_step")
@@ -585,6 +602,16 @@ def philox_check(ctr: np.ndarray, key) -> np.ndarray:
     if st != 0:
         raise PicError(f"pic_philox_check: {STATUS.get(st, st)}")
     return o
+
+
+def dd_sum_check(x: np.ndarray, fp64: bool = False) -> float:
+    """Sum of FP32 terms in the device's double-float cell-sum arithmetic."""
+    v = np.ascontiguousarray(x, dtype=np.float32)
+    out = np.zeros(1)
+    st = lib(fp64).pic_dd_sum_check(_p(v, C.c_float), v.size, _p(out))
+    if st != 0:
+        raise PicError(f"pic_dd_sum_check: {STATUS.get(st, st)}")
+    return float(out[0])
 
 
 def order_check(key: np.ndarray, ids: np.ndarray, rmax: int = 512) -> np.ndarray:

@@ -883,8 +883,9 @@ pic_status build_records(pic_ctx *c, int slot, const pic_grid *g, bool electrons
 
 // replace all particles of one species by host records (single-slab load):
 // records into the B buffers, count, scan, scatter into A
-pic_status load_species(pic_ctx *c, bool electrons, int64_t n, const std::vector<real4> &p0,
-                        const std::vector<real4> &p1, const std::vector<int> &key)
+// the n records of one species on the unsorted side (B buffers, keys) into
+// cell order on the sorted side
+pic_status sort_species(pic_ctx *c, bool electrons, int64_t n)
 {
     cudaStream_t st = c->stream;
     real4 *s0 = electrons ? c->eB0 : c->iB0, *s1 = electrons ? c->eB1 : c->iB1;
@@ -892,11 +893,6 @@ pic_status load_species(pic_ctx *c, bool electrons, int64_t n, const std::vector
     int *k = electrons ? c->ekey : c->ikey;
     int *cnt = electrons ? c->cnt_e : c->cnt_i, *fill = electrons ? c->fill_e : c->fill_i;
     int nn = (int)n;
-    if (n > 0) {
-        CK(cudaMemcpyAsync(s0, p0.data(), sizeof(real4) * n, cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(s1, p1.data(), sizeof(real4) * n, cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(k, key.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
-    }
     CK(cudaMemcpyAsync(c->counters + CNT_NLOAD, &nn, sizeof(int), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(cnt, 0, sizeof(int) * c->ncell, st));
     CK(cudaMemsetAsync(fill, 0, sizeof(int) * c->ncell, st));
@@ -909,6 +905,18 @@ pic_status load_species(pic_ctx *c, bool electrons, int64_t n, const std::vector
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));
     return PIC_OK;
+}
+
+pic_status load_species(pic_ctx *c, bool electrons, int64_t n, const std::vector<real4> &p0,
+                        const std::vector<real4> &p1, const std::vector<int> &key)
+{
+    cudaStream_t st = c->stream;
+    if (n > 0) {
+        CK(cudaMemcpyAsync(electrons ? c->eB0 : c->iB0, p0.data(), sizeof(real4) * n, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(electrons ? c->eB1 : c->iB1, p1.data(), sizeof(real4) * n, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(electrons ? c->ekey : c->ikey, key.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    }
+    return sort_species(c, electrons, n);
 }
 
 // Admission: host records are appended behind the sorted particles of each
@@ -1406,6 +1414,37 @@ pic_status pic_load_electrons(pic_ctx *c, int64_t n, const double *X, const doub
     if (r == PIC_OK) r = load_species(c, true, n, p0, p1, key);
     if (r == PIC_OK) c->loaded_e = true;
     return r;
+}
+
+pic_status pic_seed(pic_ctx *c, const pic_seed_spec *sp)
+{
+    if (!c || !sp) return PIC_ERR_ARG;
+    if (c->batch) return fail(c, PIC_ERR_STATE, "a batch context loads particles at admission");
+    if (sp->ppc_e < 1 || sp->ppc_i < 1 || sp->Z_init < 0 || sp->Z_init > 12 || !(sp->T_e_eV >= 0) ||
+        !(sp->T_i_eV >= 0) || !(sp->beam_frac >= 0 && sp->beam_frac <= 1) || !(sp->beam_E_eV >= 0))
+        return fail(c, PIC_ERR_ARG, "seed spec out of range");
+    const SlabDev &S = c->slabs[0];
+    const long long ne = (long long)S.ncell * sp->ppc_e, ni = (long long)S.ncell * sp->ppc_i;
+    if (ne > c->cap_e || ni > c->cap_i) return fail(c, PIC_ERR_CAPACITY, "seeded particles exceed the capacity");
+    const double w_ion = (double)S.w_ion;
+    const double gb = 1.0 + sp->beam_E_eV / kMeC2;
+    for (int e = 1; e >= 0; --e) {
+        SeedArgs a{};
+        a.p0 = e ? c->eB0 : c->iB0; a.p1 = e ? c->eB1 : c->iB1; a.key = e ? c->ekey : c->ikey;
+        a.n = e ? ne : ni; a.nx = S.nx; a.ny = S.ny; a.ppc = e ? sp->ppc_e : sp->ppc_i;
+        a.electrons = e;
+        a.sigma_u = e ? std::sqrt(sp->T_e_eV / kMeC2) : std::sqrt(sp->T_i_eV / ((double)S.m_ion * kMeC2));
+        a.beam_frac = sp->beam_frac; a.beam_u = std::sqrt(gb * gb - 1.0);
+        a.w = (float)(sp->Z_init * sp->ppc_i * w_ion / sp->ppc_e);
+        a.st = sp->Z_init;
+        a.seed = sp->seed;
+        k_seed<<<c->nsm * 8, 256, 0, c->stream>>>(a);
+        CK(cudaGetLastError());
+        pic_status r = sort_species(c, e != 0, a.n);
+        if (r != PIC_OK) return r;
+    }
+    c->loaded_e = c->loaded_i = true;
+    return PIC_OK;
 }
 
 pic_status pic_load_ions(pic_ctx *c, int64_t n, const double *X, const double *Y, const float *u,
@@ -1922,6 +1961,24 @@ pic_status pic_order_check(const uint64_t *key, const uint64_t *id, int n, int r
         kern<<<1, 32, smem>>>(dk, di, n, dout);
         if (cudaGetLastError() != cudaSuccess ||
             cudaMemcpy(order, dout, sizeof(uint16_t) * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+            st = PIC_ERR_CUDA;
+    }
+    cudaFree(d);
+    return st;
+}
+
+pic_status pic_dd_sum_check(const float *x, int n, double *out)
+{
+    if (!x || !out || n <= 0 || n > (1 << 24)) return PIC_ERR_ARG;
+    char *d = nullptr;
+    if (cudaMalloc(&d, sizeof(float) * (size_t)n + 16) != cudaSuccess) return PIC_ERR_OOM;
+    float *dx = (float *)(d + 16);
+    double *dout = (double *)d;
+    pic_status st = PIC_OK;
+    if (cudaMemcpy(dx, x, sizeof(float) * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess) st = PIC_ERR_CUDA;
+    if (st == PIC_OK) {
+        k_dd_check<<<1, 32>>>(dx, n, dout);
+        if (cudaGetLastError() != cudaSuccess || cudaMemcpy(out, dout, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
             st = PIC_ERR_CUDA;
     }
     cudaFree(d);

@@ -150,7 +150,7 @@ constexpr int MAXB = 8;         // photon bins
 // Philox stream purposes (counter word 3)
 enum : uint32_t { PU_PAIR_E = 1, PU_PAIR_I = 2, PU_COLL_EE = 3, PU_COLL_EI = 4,
                   PU_COLL_IE = 5, PU_ION = 6, PU_PHOTO_A = 7, PU_PHOTO_B = 8, PU_DECAY = 9,
-                  PU_THERM = 10 };
+                  PU_THERM = 10, PU_SEED_E = 11, PU_SEED_I = 12 };
 // kinds of created electrons: id high word = ((step + 1) << 2) | kind
 enum : uint32_t { KIND_IMPACT = 1, KIND_PHOTO = 2, KIND_AUGER = 3 };
 

@@ -447,6 +447,64 @@ __global__ void k_order_check(const unsigned long long *key_in, const unsigned l
     for (int k = lane; k < n; k += 32) order[k] = slot[k];
 }
 
+// ---------------- initial plasma on the device ----------------
+struct SeedArgs {
+    real4 *p0, *p1;          // records (unsorted side)
+    int *key;                // their cells
+    long long n;             // particles of the species
+    int nx, ny, ppc;
+    int electrons;
+    double sigma_u;          // sqrt(T / (m c^2)): spread of each momentum component
+    double beam_frac, beam_u;
+    float w;                 // electron weight
+    int st;                  // ion state Z | nK << 8
+    unsigned long long seed;
+};
+
+__device__ __forceinline__ double u01d(uint32_t x) { return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0); }
+
+// particle i of the species: cell i / ppc (cell-major), id i; three draws of
+// its own stream give the position, the beam choice and direction, and two
+// Box-Muller pairs for the Maxwellian
+__global__ void k_seed(SeedArgs a)
+{
+    const uint32_t pu = a.electrons ? PU_SEED_E : PU_SEED_I;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int g = (int)(i / a.ppc);
+        const U4 r0 = draw(a.seed, (unsigned long long)i, 0u, pu);
+        const U4 r1 = draw(a.seed, (unsigned long long)i, 1u, pu);
+        const real xi = u01(r0.x);
+        const real eta = a.ny > 1 ? u01(r0.y) : RF(0.5);
+        double ux, uy, uz;
+        if (a.electrons && u01d(r0.z) < a.beam_frac) {
+            const double c = 2.0 * u01d(r0.w) - 1.0, ph = 2.0 * kPi * u01d(r1.x);
+            const double sn = sqrt(fmax(0.0, 1.0 - c * c));
+            ux = a.beam_u * sn * cos(ph); uy = a.beam_u * sn * sin(ph); uz = a.beam_u * c;
+        } else {
+            const U4 r2 = draw(a.seed, (unsigned long long)i, 2u, pu);
+            const double m1 = sqrt(-2.0 * log(u01d(r2.x))), t1 = 2.0 * kPi * u01d(r2.y);
+            const double m2 = sqrt(-2.0 * log(u01d(r2.z))), t2 = 2.0 * kPi * u01d(r2.w);
+            ux = a.sigma_u * m1 * cos(t1); uy = a.sigma_u * m1 * sin(t1); uz = a.sigma_u * m2 * cos(t2);
+        }
+        a.p0[i] = make_real4(xi, eta, (real)ux, (real)uy);
+        a.p1[i] = a.electrons ? rec_e1((real)uz, (real)a.w, (uint64_t)i)
+                              : rec_i1((real)uz, RF(0.0), (uint32_t)i, a.st);
+        a.key[i] = g;
+    }
+}
+
+// the cell kernel's double-float sum of n terms, run by one warp (lane-
+// strided accumulation, then the fixed tree of wsum_dd): out = hi + lo
+__global__ void k_dd_check(const float *x, int n, double *out)
+{
+    const int lane = threadIdx.x;
+    dd acc = dd_zero();
+    for (int k = lane; k < n; k += 32) acc = dd_addf(acc, (real)x[k]);
+    acc = wsum_dd(acc);
+    if (lane == 0) out[0] = (double)acc.hi + (double)acc.lo;
+}
+
 __global__ void k_philox_check(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, int n)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
