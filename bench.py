@@ -49,9 +49,10 @@ CELL_BYTES_PER_PARTICLE = 68
 # whole step: cell kernel 68 B + scatter (36 B read, 32 B written)
 STEP_BYTES_PER_PARTICLE = 136
 # DRAM bytes per particle of the cell kernel, from one ncu capture of a
-# smaller slab of the same make-up (profiles/), scaled to a launch by the
-# particle count; None when no capture of the current kernel exists
-CELL_TRAFFIC_BYTES_PER_PARTICLE = None
+# smaller slab of the same make-up (1024 x 256 cells, tier-0 launch, ~27.5 M
+# particles: 1903 MB), scaled to a launch by the particle count; None when
+# no capture of the current kernel exists
+CELL_TRAFFIC_BYTES_PER_PARTICLE = 69
 
 
 def measured_peaks():
