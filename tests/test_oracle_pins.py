@@ -1,4 +1,4 @@
-"""Pins of four oracle functions by values the mathematics fixes (CPU only).
+"""Pins of five oracle functions by values the mathematics fixes (CPU only).
 
 * the EOS interpolation Zbar_EOS(n_i, T_e) that drives the recombination
   clamp (Sec. IV): exact on tables of a bilinear function, node and
@@ -14,7 +14,9 @@
   photoelectron carries exactly hv_b - E_b;
 * the diagnostics (Sec. VI): charge-state histogram with fractional charges
   split between Z and Z + 1, and the logarithmic electron energy
-  histogram, on hand-built states.
+  histogram, on hand-built states;
+* the per-electron collision momentum scale the parity tolerance uses
+  (test bookkeeping): the larger initial |u| of a fixed pair.
 """
 import math
 
@@ -286,3 +288,27 @@ def test_diagnostics_on_a_hand_built_state(tables):
     # more bins: each decade split in two (edges 0.1, 0.316, 1, 3.16, ...)
     _, e8 = o.diag(n_E=8, E_max=1000.0)
     assert np.allclose(e8, np.array([1, 2, 0, 3, 0, 4, 0, 11]) / 21.0, atol=1e-15)
+
+
+# ------------------------------------------- collision momentum scale ----
+
+def test_collision_scale_is_the_larger_pair_momentum(tables):
+    """The oracle's per-electron collision momentum scale (test
+    bookkeeping: the scale of the momentum tolerance of parity, no part of
+    the method): the larger |u| of the electron and its e-e partner before
+    their collision.  Two electrons per cell, so the pairing is fixed:
+    both get the larger initial |u| of their cell; with collisions off,
+    zero."""
+    for flags, on in ((P.F_COLL_EE, True), (P.F_IONIZE, False)):
+        cfg = P.cfg_small_1d(nx=3, ppc_e=2, ppc_i=1, T_e_eV=50.0, flags=flags)
+        st = P.init_particles(cfg)
+        o = oracle.OracleSlab(cfg, tables)
+        o.load(st)
+        o.step(1)
+        e = o.electrons()
+        cell = np.floor(st.eX).astype(int)
+        mag = np.sqrt((np.asarray(st.eu, dtype=np.float64) ** 2).sum(axis=1))
+        want = np.array([mag[cell == c].max() for c in cell]) if on else np.zeros(len(mag))
+        order = np.argsort(e["id"])
+        got = e["cscale"][order]
+        assert np.allclose(got, want[np.argsort(st.eid)], rtol=0, atol=0), (got, want)
