@@ -102,6 +102,8 @@ struct pic_ctx {
     int nsm = 0, grid_main = 0, grid_t1 = 0, grid_t2 = 0, grid_big = 0, grid_push = 0;
     NewE *nw = nullptr;                  // created-electron scratch of the cell launches
     size_t nw_entries = 0;
+    unsigned long long *gw = nullptr;    // global staging of the large-cell instances (ids, radix buffer)
+    size_t gw_words = 0;
     int64_t launches = 0;
     bool loaded_e = false, loaded_i = false;
     std::vector<double> hv_tab, sigma;   // host copy of the photoionization table
@@ -179,6 +181,15 @@ size_t nw_scratch_entries(int ncell)
     return warps * 768;
 }
 
+// Global staging of the large-cell instances, in 8-byte words: 1536 a warp
+// for as many warps (1024 ids, or ids and radix buffer above); the large
+// cells' warps are few, and their grids are clamped to the slices.
+size_t gw_scratch_words(int ncell)
+{
+    const size_t warps = std::min<size_t>(192 * 16, (size_t)ncell + 64);
+    return warps * 1536;
+}
+
 size_t arena_need(int ncell, int npts, int nblk, int cap_e, int cap_i, int nslot, int nrows)
 {
     size_t b = 0;
@@ -191,7 +202,7 @@ size_t arena_need(int ncell, int npts, int nblk, int cap_e, int cap_i, int nslot
     b += 3 * al((size_t)npts * 3 * sizeof(real)) + al((size_t)npts * 3 * 8) + al((size_t)npts * 4);
     b += 2 * al((size_t)nrows * 4);
     b += al((size_t)ncell * PIC_MAX_BINS * sizeof(ph2));
-    b += al(nw_scratch_entries(ncell) * sizeof(NewE));
+    b += al(nw_scratch_entries(ncell) * sizeof(NewE)) + al(gw_scratch_words(ncell) * 8);
     b += al((4 + NZ + 4096 + 8) * 8);
     return b + 4096;
 }
@@ -232,12 +243,14 @@ int max_wpc(int ce, int ci)
     return std::max(1, (int)std::min<size_t>(lim, (200 * 1024) / per));
 }
 
-// CTAs of a persistent cell launch: the resident ones on every SM, as many
-// as the created-electron scratch has warp slices for
-int cell_grid(const pic_ctx *c, int occ, int wpc, int cn)
+// CTAs of a persistent cell launch staging ce / ci: the resident ones on
+// every SM, as many as the global scratches have warp slices for
+int cell_grid(const pic_ctx *c, int occ, int wpc, int ce, int ci)
 {
-    const int cap = (int)std::min<size_t>(c->nw_entries / ((size_t)wpc * cn), 1 << 30);
-    return std::max(1, std::min(std::max(1, occ) * c->nsm, cap));
+    size_t cap = c->nw_entries / ((size_t)wpc * 3 * ci);
+    const size_t gw = warp_gmem_words(ce, ci);
+    if (gw) cap = std::min(cap, c->gw_words / ((size_t)wpc * gw));
+    return std::max(1, (int)std::min<size_t>((size_t)std::max(1, occ) * c->nsm, std::min<size_t>(cap, 1 << 30)));
 }
 
 pic_status cell_smem_attr(pic_ctx *c)
@@ -284,7 +297,7 @@ pic_status set_wpc(pic_ctx *c, int wpc)
     if (r != PIC_OK) return r;
     int occ = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cell_kernel(c->cap_ce, c->cap_ci), wpc * 32, c->smem_main));
-    c->grid_main = cell_grid(c, occ, wpc, c->cap_new);
+    c->grid_main = cell_grid(c, occ, wpc, c->cap_ce, c->cap_ci);
     return PIC_OK;
 }
 
@@ -348,12 +361,12 @@ pic_status configure_cell_launch(pic_ctx *c, const int *hist_e, const int *hist_
     if (c->t1_ce) {
         CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cell_kernel(c->t1_ce, c->t1_ci), c->t1_wpc * 32,
                                                          c->smem_t1));
-        c->grid_t1 = cell_grid(c, occ, c->t1_wpc, 3 * c->t1_ci);
+        c->grid_t1 = cell_grid(c, occ, c->t1_wpc, c->t1_ce, c->t1_ci);
     }
     if (c->t2_ce) {
         CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cell_kernel(c->t2_ce, c->t2_ci), c->t2_wpc * 32,
                                                          c->smem_t2));
-        c->grid_t2 = cell_grid(c, occ, c->t2_wpc, 3 * c->t2_ci);
+        c->grid_t2 = cell_grid(c, occ, c->t2_wpc, c->t2_ce, c->t2_ci);
     }
     return PIC_OK;
 }
@@ -389,6 +402,7 @@ CellArgs cell_args(pic_ctx *c, CellTier tier)
     a.eos = c->d_eos;
     a.err = c->counters + CNT_ERR;
     a.nw = c->nw;
+    a.gw = c->gw;
     if (tier == TIER0) {
         a.work = c->counters + CNT_WORK;
         a.list = nullptr; a.n_list = nullptr;
@@ -771,6 +785,8 @@ pic_status ctx_create(pic_ctx **out, int nslot, int slot_cells, int slot_pts, in
     c->photons = carve_arena<ph2>(c, (size_t)c->ncell * PIC_MAX_BINS);
     c->nw_entries = nw_scratch_entries(c->ncell);
     c->nw = carve_arena<NewE>(c, c->nw_entries);
+    c->gw_words = gw_scratch_words(c->ncell);
+    c->gw = carve_arena<unsigned long long>(c, c->gw_words);
     c->diag_buf = carve_arena<double>(c, 4 + NZ + 4096 + 8);
     if (!c->diag_buf) { pic_free(c); return PIC_ERR_OOM; }
 
@@ -818,7 +834,7 @@ pic_status ctx_create(pic_ctx **out, int nslot, int slot_cells, int slot_pts, in
     pic_status rc = PIC_OK;
     if (e != cudaSuccess) { rc = cuda_fail(c, e, "init copies"); pic_free(c); return rc; }
     c->smem_big = warp_mem_bytes(BIG_CE, BIG_CI);
-    c->grid_big = cell_grid(c, 1, 1, 3 * BIG_CI);
+    c->grid_big = cell_grid(c, 1, 1, BIG_CE, BIG_CI);
     e = cudaFuncSetAttribute(k_march, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8);
     if (e != cudaSuccess) { rc = cuda_fail(c, e, "march attribute"); pic_free(c); return rc; }
     {

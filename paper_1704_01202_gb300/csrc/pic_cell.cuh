@@ -60,6 +60,7 @@ struct CellArgs {
     int *ovf_list, *ovf_count;   // cells too large for this pass
     int cap_ce, cap_ci, cap_new; // per-cell capacities (staging; created electrons)
     NewE *nw;            // created-electron scratch: cap_new entries per warp of the launch
+    unsigned long long *gw;  // global staging: warp_gmem_words(cap_ce, cap_ci) words per warp
 };
 
 // warp reductions: a fixed tree, result broadcast from lane 0 so every lane
@@ -362,26 +363,43 @@ __host__ __device__ inline size_t amem(size_t x) { return (x + kSmAlign - 1) & ~
 // Shared memory of one warp staging up to ce electrons and ci ions.  The
 // electrons a cell creates in a step (up to 3 per ion: impact, photo- and
 // Auger ionization) are rare; they live in the warp's slice of a global
-// scratch, which keeps the staging of large cells small.
+// scratch, which keeps the staging of large cells small.  The instances
+// for cells above 128 entries, whose staging limits the warps resident on
+// an SM, also keep the electron ids (read once per collision) and the
+// radix buffer there (warp_gmem_words 8-byte words a warp).
+__host__ __device__ inline bool ids_in_gmem(int ce, int ci) { return rmax_for(ce, ci) > 128; }
+
+__host__ __device__ inline size_t warp_gmem_words(int ce, int ci)
+{
+    if (!ids_in_gmem(ce, ci)) return 0;
+    const int cm = ce > ci ? ce : ci;
+    return (size_t)ce + (cm > radix_min(rmax_for(ce, ci)) ? 2 * (size_t)cm : 0);
+}
+
 __host__ __device__ inline size_t warp_mem_bytes(int ce, int ci)
 {
+    const bool g = ids_in_gmem(ce, ci);
     size_t b = 0;
-    b += amem((size_t)ce * sizeof(real4)) + amem((size_t)ce * kKeyBytes) + amem((size_t)ce * 8) + amem((size_t)ce * 2);
+    b += amem((size_t)ce * sizeof(real4)) + amem((size_t)ce * kKeyBytes) + (g ? 0 : amem((size_t)ce * 8)) +
+         amem((size_t)ce * 2);
     b += amem((size_t)ci * sizeof(real4)) + amem((size_t)ci * 4) + amem((size_t)ci * 8) + amem((size_t)ci * 4)
          + amem((size_t)ci * 2);
     b += amem(16 * sizeof(real)) * 2 + amem(NS * sizeof(real4)) + amem(2 * MAXB * sizeof(dd)) + amem(MAXB * 4);
     const int cm = ce > ci ? ce : ci;
-    if (cm > radix_min(rmax_for(ce, ci))) b += amem((size_t)cm * 16) + 256 * 4;
+    if (cm > radix_min(rmax_for(ce, ci))) b += (g ? 0 : amem((size_t)cm * 16)) + 256 * 4;
     return b;
 }
 
-__device__ inline WarpMem carve(char *base, int ce, int ci, NewE *nw)
+// gw: the warp's slice of the global staging (warp_gmem_words words)
+__device__ inline WarpMem carve(char *base, int ce, int ci, NewE *nw, unsigned long long *gw)
 {
+    const bool g = ids_in_gmem(ce, ci);
     WarpMem m;
     char *p = base;
     m.eu = (real4 *)p; p += amem((size_t)ce * sizeof(real4));
     m.ekey = (unsigned long long *)p; p += amem((size_t)ce * kKeyBytes);
-    m.eid = (unsigned long long *)p; p += amem((size_t)ce * 8);
+    if (g) m.eid = gw;
+    else { m.eid = (unsigned long long *)p; p += amem((size_t)ce * 8); }
     m.eperm = (unsigned short *)p; p += amem((size_t)ce * 2);
     m.iu = (real4 *)p; p += amem((size_t)ci * sizeof(real4));
     m.ist = (int *)p; p += amem((size_t)ci * 4);
@@ -397,7 +415,8 @@ __device__ inline WarpMem carve(char *base, int ce, int ci, NewE *nw)
     const int cm = ce > ci ? ce : ci;
     m.rbuf = nullptr; m.rhist = nullptr;
     if (cm > radix_min(rmax_for(ce, ci))) {
-        m.rbuf = (unsigned long long *)p; p += amem((size_t)cm * 16);
+        if (g) m.rbuf = gw + ce;
+        else { m.rbuf = (unsigned long long *)p; p += amem((size_t)cm * 16); }
         m.rhist = (int *)p;
     }
     return m;

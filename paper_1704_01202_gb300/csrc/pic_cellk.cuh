@@ -981,8 +981,9 @@ __global__ void __launch_bounds__(RMAX > 512 ? 128 : 256, RMAX > 512 ? 1 : 2) k_
     for (int k = threadIdx.x; k < (int)(sizeof(Tables) / sizeof(real)); k += blockDim.x)
         ((real *)&T)[k] = ((const real *)a.tab)[k];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const size_t gwarp = (size_t)blockIdx.x * nwarp + warp;
     WarpMem m = carve(smem + (size_t)warp * warp_mem_bytes(a.cap_ce, a.cap_ci), a.cap_ce, a.cap_ci,
-                      a.nw + (size_t)(blockIdx.x * nwarp + warp) * a.cap_new);
+                      a.nw + gwarp * a.cap_new, a.gw + gwarp * warp_gmem_words(a.cap_ce, a.cap_ci));
     const int total = a.list ? *a.n_list : a.ncell;
     WarpTally wt;
     wt.slab = -1;
