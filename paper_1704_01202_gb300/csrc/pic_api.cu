@@ -181,13 +181,13 @@ size_t nw_scratch_entries(int ncell)
     return warps * 768;
 }
 
-// Global staging of the large-cell instances, in 8-byte words: 1536 a warp
-// for as many warps (1024 ids, or ids and radix buffer above); the large
-// cells' warps are few, and their grids are clamped to the slices.
+// Global staging of the large-cell instances, in 8-byte words: 2048 a warp
+// (ids and keys of 1024 electrons in the FP32 build) for as many warps; the
+// large cells' warps are few, and their grids are clamped to the slices.
 size_t gw_scratch_words(int ncell)
 {
     const size_t warps = std::min<size_t>(192 * 16, (size_t)ncell + 64);
-    return warps * 1536;
+    return warps * 2048;
 }
 
 size_t arena_need(int ncell, int npts, int nblk, int cap_e, int cap_i, int nslot, int nrows)

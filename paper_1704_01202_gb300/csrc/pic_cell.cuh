@@ -365,22 +365,24 @@ __host__ __device__ inline size_t amem(size_t x) { return (x + kSmAlign - 1) & ~
 // Auger ionization) are rare; they live in the warp's slice of a global
 // scratch, which keeps the staging of large cells small.  The instances
 // for cells above 128 entries, whose staging limits the warps resident on
-// an SM, also keep the electron ids (read once per collision) and the
-// radix buffer there (warp_gmem_words 8-byte words a warp).
+// an SM, also keep the electron ids (read once per collision), the sort
+// keys (later the per-electron scratch of the Lotz sums and of
+// recombination) and the radix buffer there (warp_gmem_words 8-byte words
+// a warp).
 __host__ __device__ inline bool ids_in_gmem(int ce, int ci) { return rmax_for(ce, ci) > 128; }
 
 __host__ __device__ inline size_t warp_gmem_words(int ce, int ci)
 {
     if (!ids_in_gmem(ce, ci)) return 0;
     const int cm = ce > ci ? ce : ci;
-    return (size_t)ce + (cm > radix_min(rmax_for(ce, ci)) ? 2 * (size_t)cm : 0);
+    return (size_t)ce * (1 + kKeyBytes / 8) + (cm > radix_min(rmax_for(ce, ci)) ? 2 * (size_t)cm : 0);
 }
 
 __host__ __device__ inline size_t warp_mem_bytes(int ce, int ci)
 {
     const bool g = ids_in_gmem(ce, ci);
     size_t b = 0;
-    b += amem((size_t)ce * sizeof(real4)) + amem((size_t)ce * kKeyBytes) + (g ? 0 : amem((size_t)ce * 8)) +
+    b += amem((size_t)ce * sizeof(real4)) + (g ? 0 : amem((size_t)ce * kKeyBytes) + amem((size_t)ce * 8)) +
          amem((size_t)ce * 2);
     b += amem((size_t)ci * sizeof(real4)) + amem((size_t)ci * 4) + amem((size_t)ci * 8) + amem((size_t)ci * 4)
          + amem((size_t)ci * 2);
@@ -397,9 +399,13 @@ __device__ inline WarpMem carve(char *base, int ce, int ci, NewE *nw, unsigned l
     WarpMem m;
     char *p = base;
     m.eu = (real4 *)p; p += amem((size_t)ce * sizeof(real4));
-    m.ekey = (unsigned long long *)p; p += amem((size_t)ce * kKeyBytes);
-    if (g) m.eid = gw;
-    else { m.eid = (unsigned long long *)p; p += amem((size_t)ce * 8); }
+    if (g) {
+        m.eid = gw;
+        m.ekey = gw + ce;
+    } else {
+        m.ekey = (unsigned long long *)p; p += amem((size_t)ce * kKeyBytes);
+        m.eid = (unsigned long long *)p; p += amem((size_t)ce * 8);
+    }
     m.eperm = (unsigned short *)p; p += amem((size_t)ce * 2);
     m.iu = (real4 *)p; p += amem((size_t)ci * sizeof(real4));
     m.ist = (int *)p; p += amem((size_t)ci * 4);
@@ -415,7 +421,7 @@ __device__ inline WarpMem carve(char *base, int ce, int ci, NewE *nw, unsigned l
     const int cm = ce > ci ? ce : ci;
     m.rbuf = nullptr; m.rhist = nullptr;
     if (cm > radix_min(rmax_for(ce, ci))) {
-        if (g) m.rbuf = gw + ce;
+        if (g) m.rbuf = gw + (size_t)ce * (1 + kKeyBytes / 8);
         else { m.rbuf = (unsigned long long *)p; p += amem((size_t)cm * 16); }
         m.rhist = (int *)p;
     }
