@@ -232,7 +232,17 @@ pic_status pic_load_ions(pic_ctx *c, int64_t n, const double *X, const double *Y
 pic_status pic_set_photons(pic_ctx *c, const double *ph);
 pic_status pic_set_fields(pic_ctx *c, const float *f6);
 
-/* Advance n PIC steps (asynchronous on the context stream). */
+/* Advance n PIC steps (asynchronous on the context stream; the call
+ * synchronizes every 32 steps to re-size the cell tiers).  Device-side
+ * problems are latched and reported by the next synchronizing call:
+ * PIC_ERR_CAPACITY when the electrons created in a step would exceed the
+ * context's capacity (or a cell outgrows the large-cell pass) and
+ * PIC_ERR_NUMERIC on a non-finite move.  After PIC_ERR_CAPACITY the
+ * electrons created in the failing cells are gone while their ions' charge
+ * states, photon numbers and tallies moved on: the state is no longer
+ * conserved and the context should be freed.  In a batch the error word is
+ * shared, so it stops every slab; electron budgets
+ * (pic_batch_set_budget) confine a capacity failure to its own slab. */
 pic_status pic_step(pic_ctx *c, int n);
 
 /* Wait for the stream; returns the latched device error, if any. */

@@ -114,3 +114,19 @@ def test_pairing_brute_force(n):
     chi2 = ((g - e) ** 2 / e).sum()
     dof = len(e) - 1
     assert stats.chi2.sf(chi2, dof) > 1e-4 if dof > 0 else abs(g[0] - e[0]) < 1e-9
+
+
+def _kat():
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "philox4x32_10_kat.json")
+    for v in json.load(open(path))["vectors"]:
+        yield ([int(x, 16) for x in v["ctr"]], [int(x, 16) for x in v["key"]], [int(x, 16) for x in v["out"]])
+
+
+def test_philox_published_known_answers():
+    """The oracle's Philox4x32-10 against the generator's published
+    known-answer vectors (tests/golden/philox4x32_10_kat.json)."""
+    for ctr, key, out in _kat():
+        got = oracle.philox(np.array([ctr], dtype=np.uint32), tuple(key)).ravel()
+        assert [int(x) for x in got] == out

@@ -64,3 +64,18 @@ def test_static_rejects_oversize():
     L = pkg.lib()
     st, _ = _call(L.pic_philox_check_static, np.zeros((MAX + 1, 4), np.uint32), np.zeros(2, np.uint32))
     assert pkg.STATUS[st] == "PIC_ERR_ARG"
+
+
+def test_static_known_answers():
+    """On its own: the static entry point against Philox4x32-10's published
+    known-answer vectors (tests/golden/philox4x32_10_kat.json)."""
+    import json
+    import os
+    pkg.build()
+    L = pkg.lib()
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "philox4x32_10_kat.json")
+    for v in json.load(open(path))["vectors"]:
+        ctr = np.array([[int(x, 16) for x in v["ctr"]]], dtype=np.uint32)
+        key = np.array([int(x, 16) for x in v["key"]], dtype=np.uint32)
+        st, out = _call(L.pic_philox_check_static, ctr, key)
+        assert st == 0 and [int(x) for x in out.ravel()] == [int(x, 16) for x in v["out"]]
