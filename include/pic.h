@@ -232,6 +232,25 @@ pic_status pic_load_ions(pic_ctx *c, int64_t n, const double *X, const double *Y
 pic_status pic_set_photons(pic_ctx *c, const double *ph);
 pic_status pic_set_fields(pic_ctx *c, const float *f6);
 
+/* Checkpoint / restore of a single-slab context: a host image of the
+ * sorted particles, the fields, the photon numbers, the tallies, the step
+ * count and, in transport mode, the transport's state.  The random streams
+ * are keyed by (seed, id, step, purpose), so nothing of the generator is
+ * saved: a context restored from an image continues as the original would,
+ * particle for particle (diagnostic sums agree to their atomic summation
+ * order).  pic_checkpoint_bytes: the image size now (0 for a batch context
+ * or before particles are loaded; synchronizes).  pic_checkpoint writes it
+ * to host memory of at least that size (PIC_ERR_ARG if smaller;
+ * synchronizes).  pic_restore loads an image into a context created with
+ * the same grid, species, tables and pulse (and pic_rt setting), replacing
+ * its particles and state; PIC_ERR_ARG for an image of another slab, build
+ * or setting, or a truncated one; PIC_ERR_CAPACITY when its particles do
+ * not fit.  Launch-shape tuning and step graphs are not part of the image
+ * (they change no result). */
+size_t pic_checkpoint_bytes(pic_ctx *c);
+pic_status pic_checkpoint(pic_ctx *c, void *host, size_t bytes);
+pic_status pic_restore(pic_ctx *c, const void *host, size_t bytes);
+
 /* Advance n PIC steps (asynchronous on the context stream; the call
  * synchronizes every 32 steps to re-size the cell tiers).  Device-side
  * problems are latched and reported by the next synchronizing call:

@@ -45,7 +45,7 @@ ABI_FUNCTIONS = ["pic_required_bytes", "pic_init", "pic_source", "pic_load_elect
                  "pic_timing", "pic_batch_required_bytes", "pic_batch_init", "pic_batch_admit",
                  "pic_batch_retire", "pic_batch_set_budget", "pic_batch_slot", "pic_batch_diagnostics", "pic_batch_counts",
                  "pic_batch_get_electrons", "pic_batch_get_ions", "pic_philox_check_static",
-                 "pic_use_graphs", "pic_autotune", "pic_order_check", "pic_dd_sum_check", "pic_seed",
+                 "pic_use_graphs", "pic_autotune", "pic_order_check", "pic_dd_sum_check", "pic_seed", "pic_checkpoint_bytes", "pic_checkpoint", "pic_restore",
                  "pic_get_electrons64", "pic_get_ions64", "pic_real_bytes",
                  "pic_rt", "pic_rt_get", "pic_rt_set", "pic_rt_cells"]
 
@@ -188,6 +188,10 @@ def lib(fp64: bool = False):
                                           C.POINTER(C.c_uint16)]
             L.pic_dd_sum_check.argtypes = [_F, C.c_int, _D]
             L.pic_seed.argtypes = [_P, C.POINTER(SeedSpec)]
+            L.pic_checkpoint_bytes.argtypes = [_P]
+            L.pic_checkpoint_bytes.restype = C.c_size_t
+            L.pic_checkpoint.argtypes = [_P, C.c_void_p, C.c_size_t]
+            L.pic_restore.argtypes = [_P, C.c_void_p, C.c_size_t]
             L.pic_autotune.argtypes = [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]
             L.pic_timing.argtypes = [_P, C.c_int, _D, C.POINTER(C.c_int64)]
             L.pic_rt.argtypes = [_P, C.POINTER(RTConfig)]
@@ -360,6 +364,20 @@ class Slab:
         spec = SeedSpec(c.ppc_e, c.ppc_i, c.Z_init, c.T_e_eV, c.T_i_eV, c.beam_frac, c.beam_E_eV,
                         int(c.seed if seed is None else seed))
         self._check(self.L.pic_seed(self.h, C.byref(spec)), "pic_seed")
+
+    def checkpoint(self) -> bytes:
+        """Host image of the slab's state (pic_checkpoint)."""
+        n = self.L.pic_checkpoint_bytes(self.h)
+        if n == 0:
+            raise PicError("pic_checkpoint_bytes: nothing to checkpoint")
+        buf = C.create_string_buffer(n)
+        self._check(self.L.pic_checkpoint(self.h, buf, n), "pic_checkpoint")
+        return buf.raw
+
+    def restore(self, image: bytes):
+        """Load a host image written by checkpoint() (pic_restore)."""
+        buf = C.create_string_buffer(image, len(image))
+        self._check(self.L.pic_restore(self.h, buf, len(image)), "pic_restore")
 
     def step(self, n=1):
         self._check(self.L.pic_step(self.h, n), "pic_step")

@@ -138,6 +138,7 @@ struct pic_ctx {
     int graph_next = 0;
     // radiation transport mode (pic_rt): device memory the context owns
     void *rt_mem = nullptr;
+    size_t rt_bytes = 0;                 // its size (one block, checkpointed whole)
     int rt_nord = 0;
 };
 
@@ -1869,6 +1870,7 @@ pic_status pic_rt(pic_ctx *c, const pic_rt_config *rt)
     char *mem = nullptr;
     CK(cudaMalloc(&mem, bytes));
     c->rt_mem = mem;
+    c->rt_bytes = bytes;
     CK(cudaMemsetAsync(mem, 0, bytes, c->stream));
     char *q = mem;
     S.rt_F = (double *)q; q += al(nf * 8);
@@ -1981,6 +1983,147 @@ pic_status pic_order_check(const uint64_t *key, const uint64_t *id, int n, int r
     }
     cudaFree(d);
     return st;
+}
+
+}  // extern "C"
+
+namespace {
+
+// ---------------- checkpoint / restore ----------------
+// Host image of a single-slab context: a header, the sorted particle records
+// with their cell starts, the current E and B, the photon numbers, the
+// tallies, the step count and, in transport mode, the transport's block.
+// The random streams are keyed by (seed, id, step, purpose), so nothing of
+// the generator needs saving: a restored context continues bit for bit.
+struct CkptHeader {
+    char magic[8];
+    int32_t version, real_bytes, nx, ny, nb, rt;
+    int64_t n_e, n_i;
+    uint32_t step, pad;
+    double dx, dy, dt, w_ion;
+    uint64_t rt_bytes, total;
+};
+constexpr char kCkptMagic[8] = {'P', 'I', 'C', 'C', 'K', 'P', 'T', '1'};
+
+size_t ckpt_bytes(const pic_ctx *c, int64_t ne, int64_t ni)
+{
+    const size_t cs = 2 * sizeof(int) * (size_t)(c->ncell + 1);
+    return sizeof(CkptHeader) + 2 * sizeof(real4) * (size_t)(ne + ni) + cs + 6 * sizeof(real) * (size_t)c->npts +
+           sizeof(ph2) * (size_t)c->ncell * PIC_MAX_BINS + sizeof(SlabTally) + c->rt_bytes;
+}
+
+pic_status ckpt_counts(pic_ctx *c, int64_t *ne, int64_t *ni)
+{
+    int v[2];
+    CK(cudaMemcpyAsync(&v[0], c->csE[c->cur] + c->ncell, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&v[1], c->csI[c->cur] + c->ncell, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *ne = v[0]; *ni = v[1];
+    return PIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t pic_checkpoint_bytes(pic_ctx *c)
+{
+    if (!c || c->batch || !c->loaded_e || !c->loaded_i) return 0;
+    int64_t ne = 0, ni = 0;
+    if (ckpt_counts(c, &ne, &ni) != PIC_OK) return 0;
+    return ckpt_bytes(c, ne, ni);
+}
+
+pic_status pic_checkpoint(pic_ctx *c, void *host, size_t bytes)
+{
+    if (!c || !host) return PIC_ERR_ARG;
+    if (c->batch) return fail(c, PIC_ERR_STATE, "checkpoints are of single-slab contexts");
+    if (!c->loaded_e || !c->loaded_i) return fail(c, PIC_ERR_STATE, "nothing loaded");
+    pic_status r = read_device_error(c);
+    if (r != PIC_OK) return r;
+    int64_t ne = 0, ni = 0;
+    if ((r = ckpt_counts(c, &ne, &ni)) != PIC_OK) return r;
+    const size_t need = ckpt_bytes(c, ne, ni);
+    if (bytes < need) return fail(c, PIC_ERR_ARG, "checkpoint buffer too small");
+    const SlabDev &S = c->slabs[0];
+    const pic_grid &g = c->grids[0];
+    CkptHeader h{};
+    std::memcpy(h.magic, kCkptMagic, 8);
+    h.version = 1; h.real_bytes = (int)sizeof(real); h.nx = g.nx; h.ny = g.ny; h.nb = S.nb; h.rt = S.rt;
+    h.n_e = ne; h.n_i = ni; h.dx = g.dx_nm; h.dy = g.dy_nm; h.dt = g.dt_fs; h.w_ion = (double)S.w_ion;
+    h.rt_bytes = c->rt_bytes; h.total = need;
+    cudaStream_t st = c->stream;
+    CK(cudaMemcpyAsync(&h.step, c->d_steps, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    char *p = (char *)host + sizeof(CkptHeader);
+    auto get = [&](const void *src, size_t n) -> cudaError_t {
+        cudaError_t e = n ? cudaMemcpyAsync(p, src, n, cudaMemcpyDeviceToHost, st) : cudaSuccess;
+        p += n;
+        return e;
+    };
+    CK(get(c->eA0, sizeof(real4) * ne)); CK(get(c->eA1, sizeof(real4) * ne));
+    CK(get(c->iA0, sizeof(real4) * ni)); CK(get(c->iA1, sizeof(real4) * ni));
+    CK(get(c->csE[c->cur], sizeof(int) * (size_t)(c->ncell + 1)));
+    CK(get(c->csI[c->cur], sizeof(int) * (size_t)(c->ncell + 1)));
+    CK(get(c->E[c->ecur], sizeof(real) * 3 * (size_t)c->npts));
+    CK(get(c->B, sizeof(real) * 3 * (size_t)c->npts));
+    CK(get(c->photons, sizeof(ph2) * (size_t)c->ncell * PIC_MAX_BINS));
+    CK(get(c->d_tally, sizeof(SlabTally)));
+    if (c->rt_bytes) CK(get(c->rt_mem, c->rt_bytes));
+    CK(cudaStreamSynchronize(st));
+    std::memcpy(host, &h, sizeof(CkptHeader));
+    return PIC_OK;
+}
+
+pic_status pic_restore(pic_ctx *c, const void *host, size_t bytes)
+{
+    if (!c || !host || bytes < sizeof(CkptHeader)) return PIC_ERR_ARG;
+    if (c->batch) return fail(c, PIC_ERR_STATE, "checkpoints are of single-slab contexts");
+    CkptHeader h;
+    std::memcpy(&h, host, sizeof(CkptHeader));
+    const SlabDev &S = c->slabs[0];
+    const pic_grid &g = c->grids[0];
+    if (std::memcmp(h.magic, kCkptMagic, 8) || h.version != 1 || h.real_bytes != (int)sizeof(real))
+        return fail(c, PIC_ERR_ARG, "not a checkpoint of this build");
+    if (h.nx != g.nx || h.ny != g.ny || h.dx != g.dx_nm || h.dy != g.dy_nm || h.dt != g.dt_fs ||
+        h.w_ion != (double)S.w_ion || h.nb != S.nb || h.rt != S.rt || h.rt_bytes != c->rt_bytes)
+        return fail(c, PIC_ERR_ARG, "checkpoint of another slab, pulse or transport setting");
+    if (h.n_e < 0 || h.n_i < 0 || h.total != ckpt_bytes(c, h.n_e, h.n_i) || bytes < h.total)
+        return fail(c, PIC_ERR_ARG, "checkpoint truncated");
+    if (h.n_e > c->cap_e || h.n_i > c->cap_i) return fail(c, PIC_ERR_CAPACITY, "checkpoint exceeds the capacity");
+    const char *p = (const char *)host + sizeof(CkptHeader);
+    const int64_t ne = h.n_e, ni = h.n_i;
+    std::vector<real4> e0(ne), e1(ne), i0(ni), i1(ni);
+    std::vector<int> cse(c->ncell + 1), csi(c->ncell + 1);
+    auto take = [&](void *dst, size_t n) { std::memcpy(dst, p, n); p += n; };
+    take(e0.data(), sizeof(real4) * ne); take(e1.data(), sizeof(real4) * ne);
+    take(i0.data(), sizeof(real4) * ni); take(i1.data(), sizeof(real4) * ni);
+    take(cse.data(), sizeof(int) * cse.size()); take(csi.data(), sizeof(int) * csi.size());
+    if (cse[0] != 0 || csi[0] != 0 || cse[c->ncell] != ne || csi[c->ncell] != ni)
+        return fail(c, PIC_ERR_ARG, "checkpoint cell starts inconsistent");
+    std::vector<int> ke(ne), ki(ni);
+    for (int g2 = 0; g2 < c->ncell; ++g2) {
+        if (cse[g2 + 1] < cse[g2] || csi[g2 + 1] < csi[g2]) return fail(c, PIC_ERR_ARG, "checkpoint cell starts inconsistent");
+        for (int k = cse[g2]; k < cse[g2 + 1]; ++k) ke[k] = g2;
+        for (int k = csi[g2]; k < csi[g2 + 1]; ++k) ki[k] = g2;
+    }
+    pic_status r = load_species(c, true, ne, e0, e1, ke);
+    if (r == PIC_OK) r = load_species(c, false, ni, i0, i1, ki);
+    if (r != PIC_OK) return r;
+    cudaStream_t st = c->stream;
+    auto put = [&](void *dst, size_t n) -> cudaError_t {
+        cudaError_t e = n ? cudaMemcpyAsync(dst, p, n, cudaMemcpyHostToDevice, st) : cudaSuccess;
+        p += n;
+        return e;
+    };
+    CK(put(c->E[c->ecur], sizeof(real) * 3 * (size_t)c->npts));
+    CK(put(c->B, sizeof(real) * 3 * (size_t)c->npts));
+    CK(put(c->photons, sizeof(ph2) * (size_t)c->ncell * PIC_MAX_BINS));
+    CK(put(c->d_tally, sizeof(SlabTally)));
+    if (c->rt_bytes) CK(put(c->rt_mem, c->rt_bytes));
+    CK(cudaMemcpyAsync(c->d_steps, &h.step, sizeof(unsigned), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    c->loaded_e = c->loaded_i = true;
+    return PIC_OK;
 }
 
 pic_status pic_dd_sum_check(const float *x, int n, double *out)
