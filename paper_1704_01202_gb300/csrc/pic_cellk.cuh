@@ -896,16 +896,20 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
     //      canonical order, which the push kernel follows ----
     for (int k = lane; k < ne; k += 32) a.eord[e0 + k] = m.eperm[k];
     for (int k = lane; k < ni; k += 32) a.iord[i0 + k] = m.iperm[k];
-    real wsum = RF(0.0);
     for (int k = lane; k < ne; k += 32) {
         real4 u = m.eu[k];
         reinterpret_cast<real2 *>(a.e0 + e0 + k)[1] = make_real2(u.x, u.y);
         reinterpret_cast<real2 *>(a.e1 + e0 + k)[0] = make_real2(u.z, u.w);
-        wsum += u.w > RF(0.0) ? u.w : RF(0.0);
     }
     if (rad && S.rt) {
         // transport mode: the cell's electron weight after the step, created
         // electrons included: its share of the next heating of its rad cell
+        // (summed in canonical order: the slots' order is the scatter's)
+        real wsum = RF(0.0);
+        for (int k = lane; k < ne; k += 32) {
+            const real w = m.eu[m.eperm[k]].w;
+            wsum += w > RF(0.0) ? w : RF(0.0);
+        }
         for (int k = lane; k < nnew; k += 32) wsum += m.nw[k].w;
         wsum = wsum_f(wsum);
         if (lane == 0) S.rt_w[lc] = (float)wsum;
