@@ -235,12 +235,15 @@ CellKernel cell_kernel(int ce, int ci)
     return r == 128 ? k_cell<128> : (r == 512 ? k_cell<512> : k_cell<1024>);
 }
 
-// largest warps per CTA of the cell kernel whose staging fits 200 KB (the
-// 1024 instance takes at most 4 warps a CTA)
+// largest warps per CTA of the cell kernel whose staging fits 200 KB, at
+// most 8 and at most what the instance's launch bounds allow
 int max_wpc(int ce, int ci)
 {
     const size_t per = warp_mem_bytes(ce, ci);
-    const int lim = rmax_for(ce, ci) > 512 ? 4 : 8;
+    int lim = 8;
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, cell_kernel(ce, ci)) == cudaSuccess && fa.maxThreadsPerBlock >= 32)
+        lim = std::min(lim, fa.maxThreadsPerBlock / 32);
     return std::max(1, (int)std::min<size_t>(lim, (200 * 1024) / per));
 }
 
