@@ -240,13 +240,22 @@ def run_gpu(args):
     # replicas: every rank runs its own slab with its own seed
     cfg.seed = cfg.seed + rank
     tab = P.standin_tables()
+    # one GPU: the initial state built on the host and loaded (the e2e leg
+    # needs the host copy); several: seeded on each device (pic_seed, the
+    # same distributions), since N host copies of a 0.84e9-particle state
+    # would take N x ~80 GB of host memory
+    host_state = world == 1
     t_gen = time.perf_counter()
-    st = P.init_particles(cfg)
+    st = P.init_particles(cfg) if host_state else None
     t_gen = time.perf_counter() - t_gen
-    n0 = st.n_e + st.n_i
-    cap_e, cap_i = capacity(cfg, st.n_e, st.n_i)
+    n_e0, n_i0 = (st.n_e, st.n_i) if host_state else (cfg.ncell * cfg.ppc_e, cfg.ncell * cfg.ppc_i)
+    n0 = n_e0 + n_i0
+    cap_e, cap_i = capacity(cfg, n_e0, n_i0)
     slab = pkg.Slab(cfg, tab, pl, cap_e=cap_e, cap_i=cap_i)
-    slab.load(st)
+    if host_state:
+        slab.load(st)
+    else:
+        slab.seed()
     stream = torch.cuda.current_stream()
 
     # advance outside the clock, timed as a whole for the mean; its last
@@ -323,8 +332,11 @@ def run_gpu(args):
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and host_state:
         e2e = run_e2e(pkg, cfg, tab, pl, st, args, world, n0, (cap_e, cap_i))
+    elif not args.no_e2e:
+        e2e = {"value": None, "skipped": "N > 1: a host copy of the initial state per rank would need N x ~80 GB "
+                                         "of host memory; the state was seeded on each device"}
     del st
     torch.cuda.empty_cache()
     foil = run_foil(pkg, tab, args) if args.foil_steps > 0 and args.workload != "foil" else None
@@ -345,7 +357,8 @@ def run_gpu(args):
                           "particles_start": int(n0), "ppc": [cfg.ppc_e, cfg.ppc_i], "pulse_keV": pl.hv_eV / 1e3,
                           "pulse_Wcm2": pl.I_peak_Wcm2, "pulse_peak_fs": pl.t_peak_fs,
                           "l2": f"state ({n_mean * 32 / 1e9:.0f} GB) larger than L2; no flush",
-                          "parallelism": "replicas", "host_generation_s": round(t_gen, 1)},
+                          "parallelism": "replicas", "host_generation_s": round(t_gen, 1),
+                          "initial_state": "host generator, loaded" if host_state else "seeded on the device"},
                "timed_window": window, "advance": adv, "energy_drift": energy,
                "roofline": roof, "step_hbm_gbs": step_gbs, "cpu_baseline": cb, "e2e": e2e,
                "gpu_launches": int(launches), "clocks": clk, "kernel_ms": {k: v / max(nrec, 1) for k, v in tms.items()},
