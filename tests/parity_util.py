@@ -97,7 +97,7 @@ def classify(cfg, st, g_e, o_e, g_i, o_i, near, n_draw, n_dec):
     to the fast one.
 
     A decision that lies within 2^-20 of its threshold (|x - thr| <= 2^-20
-    |thr|, the survey's definition of a threshold flip) may go the other
+    |thr|: the definition of a threshold flip used here) may go the other
     way in FP32; its consequences stay inside its cell but spread there (the
     impact-ionization payment and the collision energy restore scale every
     electron of the cell, an extra or missing ionization moves the
@@ -181,7 +181,7 @@ def flip_summary(cls):
             f"{cls['near']} near-threshold decisions, cells with differences {cls['flip_cells'][:8]} {kinds[:8]}")
 
 
-# the benchmark spec's bound on threshold flips: fewer than 1e-5 of the draws
+# the bound on threshold flips: fewer than 1e-5 of the draws
 FLIP_SHARE = 1e-5
 
 
