@@ -341,6 +341,7 @@ def run_gpu(args):
     torch.cuda.empty_cache()
     foil = run_foil(pkg, tab, args) if args.foil_steps > 0 and args.workload != "foil" else None
     rt = run_rt(pkg, tab, args) if args.rt_steps > 0 else None
+    mc_energy = run_mc_energy(pkg, tab, args) if args.mc_energy_steps > 0 else None
     ensemble = run_ensemble(pkg, tab, args, rank) if args.ensemble > 0 else None
     served = run_served(pkg, tab, args) if args.serve_n > 0 else None
     kedge_scan = run_kedge(pkg, tab, args) if args.kedge_points > 0 else None
@@ -360,6 +361,7 @@ def run_gpu(args):
                           "parallelism": "replicas", "host_generation_s": round(t_gen, 1),
                           "initial_state": "host generator, loaded" if host_state else "seeded on the device"},
                "timed_window": window, "advance": adv, "energy_drift": energy,
+               "energy_drift_collisions_and_atomic": mc_energy,
                "roofline": roof, "step_hbm_gbs": step_gbs, "cpu_baseline": cb, "e2e": e2e,
                "gpu_launches": int(launches), "clocks": clk, "kernel_ms": {k: v / max(nrec, 1) for k, v in tms.items()},
                "autotune": {"cell_warps_per_cta": tuned[0], "cell_ms_1_2_4_8": [float(x) for x in tuned[1]]},
@@ -442,6 +444,27 @@ def run_foil(pkg, tab, args):
     return {"workload": cfg.name, "particles": int(n_mean), "steps": args.foil_steps,
             "value": n_mean * args.foil_steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / args.foil_steps,
             "kernel_ms": {k: v / max(nrec, 1) for k, v in tms.items()}}
+
+
+def run_mc_energy(pkg, tab, args):
+    """Energy bookkeeping of the collision and atomic operators alone at
+    scale: a 1024 x 256-cell slab of the headline's make-up with push and
+    fields off (every other process on, the pulse peak moved to 2 fs so that
+    photoionization and K decay run), --mc-energy-steps steps seeded on the
+    device: the total energy's relative change per 1000 steps."""
+    cfg, pl = workload((1024, 256), "large")
+    cfg.flags = cfg.flags & ~(P.F_PUSH | P.F_FIELD)
+    pl.t_peak_fs = 2.0
+    slab = pkg.Slab(cfg, tab, pl)
+    slab.seed()
+    d0 = slab.diagnostics()
+    slab.step(args.mc_energy_steps)
+    d1 = slab.diagnostics()
+    slab.close()
+    held = sum(d1[k] for k in ("ke_e", "ke_i", "e_ion", "e_phot"))
+    return {"workload": cfg.name + ", push and fields off, pulse peak at 2 fs", "steps": args.mc_energy_steps,
+            "rel_per_1000_steps": (energy_total(d1) - energy_total(d0)) / held * 1000.0 / args.mc_energy_steps,
+            "events": {k: d1["counts"][k] for k in ("ION", "REC", "PH0", "AUG", "KA", "EE", "EI")}}
 
 
 def run_ensemble(pkg, tab, args, rank):
@@ -608,6 +631,8 @@ def main():
     ap.add_argument("--foil-steps", type=int, default=20, help="timed steps of the 2D foil leg (0: skip)")
     ap.add_argument("--rt-steps", type=int, default=20,
                     help="timed steps of the 2D foil with radiation transport (0: skip)")
+    ap.add_argument("--mc-energy-steps", type=int, default=500,
+                    help="steps of the collision / atomic energy bookkeeping leg (0: skip)")
     ap.add_argument("--ensemble", type=int, default=256, help="slabs of the batched ensemble (0: skip)")
     ap.add_argument("--serve-n", type=int, default=240, help="requests of the served trace (0: skip)")
     ap.add_argument("--serve-slots", type=int, default=128, help="slots of the served batch")
