@@ -8,6 +8,7 @@
 // 1D slots into which slabs are admitted, and from which they are retired,
 // between steps.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -512,8 +513,28 @@ bool same_shape(const pic_ctx::StepShape &a, const pic_ctx::StepShape &b)
            a.t2_ce == b.t2_ce && a.t2_ci == b.t2_ci && a.t2_wpc == b.t2_wpc && a.grid_t2 == b.grid_t2;
 }
 
+// NVTX ranges around the launches of a step (header-only NVTX 3: nothing
+// happens unless a profiler is attached): the step, then one nested range
+// per phase; inside a graph capture they mark the capture
+struct NvRanges {
+    bool open = false;
+    explicit NvRanges(const char *name) { nvtxRangePushA(name); }
+    void phase(const char *name)
+    {
+        if (open) nvtxRangePop();
+        nvtxRangePushA(name);
+        open = true;
+    }
+    ~NvRanges()
+    {
+        if (open) nvtxRangePop();
+        nvtxRangePop();
+    }
+};
+
 pic_status launch_step(pic_ctx *c)
 {
+    NvRanges nv("pic step");
     cudaStream_t st = c->stream;
     const pic_ctx::StepShape shape = step_shape(c);
     cudaEvent_t *ev = timing_slot(c);
@@ -522,6 +543,7 @@ pic_status launch_step(pic_ctx *c)
     CK(cudaMemsetAsync(c->counters, 0, sizeof(int) * CNT_STEP_ZERO, st));          // append, work counters, lists
     CK(cudaMemsetAsync(c->J, 0, sizeof(unsigned long long) * 3 * (size_t)c->npts, st));
     if (shape.rt) {
+        nv.phase("radiation transport");
         // radiation transport (single-slab contexts): the kernels return at
         // once on steps that are not rad steps
         const SlabDev &S = c->slabs[0];
@@ -539,12 +561,14 @@ pic_status launch_step(pic_ctx *c)
         k_rt_publish<<<std::min((S.ncell + 255) / 256, c->nsm * 8), 256, 0, st>>>(ra);
         ++c->launches;
     } else if (shape.march) {
+        nv.phase("photon march");
         MarchArgs m{c->d_slab, c->d_steps, c->row_slab, c->row_idx, c->photons, c->d_tally};
         k_march<<<c->nrows, 256, (size_t)c->max_row_nx * 8, st>>>(m);
         ++c->launches;
     }
     if (ev) CK(cudaEventRecord(ev[1], st));
     if (c->cell_ev_on) CK(cudaEventRecord(c->cell_ev[0], st));
+    nv.phase("collisions and atomic processes");
     CellArgs a0 = cell_args(c, TIER0);
     cell_kernel(c->cap_ce, c->cap_ci)<<<c->grid_main, c->wpc * 32, c->smem_main, st>>>(a0);
     if (c->t1_ce) {
@@ -563,6 +587,7 @@ pic_status launch_step(pic_ctx *c)
     if (c->cell_ev_on) CK(cudaEventRecord(c->cell_ev[1], st));
     CK(cudaGetLastError());
     if (ev) CK(cudaEventRecord(ev[2], st));
+    nv.phase("push and deposit");
     PushArgs pa{};
     pa.e0 = c->eA0; pa.e1 = c->eA1; pa.ekey = c->ekey; pa.cs_e = c->csE[c->cur];
     pa.eord = c->eord; pa.iord = c->iord;
@@ -577,6 +602,7 @@ pic_status launch_step(pic_ctx *c)
     CK(cudaGetLastError());
     if (ev) CK(cudaEventRecord(ev[3], st));
     const int nxt = c->cur ^ 1;
+    nv.phase("counting sort");
     pic_status r = run_scan(c, 3, nxt);
     if (r != PIC_OK) return r;
     int sgrid = c->nsm * 8;
@@ -589,6 +615,7 @@ pic_status launch_step(pic_ctx *c)
     c->launches += 2;
     if (ev) CK(cudaEventRecord(ev[4], st));
     if (shape.field) {
+        nv.phase("fields");
         const int nsub = shape.nsub;
         FieldArgs f{};
         f.slabs = c->d_slab; f.pt_slab = c->pt_slab; f.npts = c->npts; f.B = c->B; f.J = c->J;
