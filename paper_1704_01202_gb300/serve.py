@@ -77,10 +77,10 @@ def serve_batched(trace, tables, init_state, max_slabs: int, slot_cells: int, ca
     slab is preempted: its slot and reservation are freed and it is queued
     again, at the head, with grow times the partial-event allowance; its
     result does not depend on where or when it runs, so the re-run returns
-    what an unconstrained run would.  A request whose reservation exceeds
-    cap_e before reaching its worst case fails alone (reported in
-    `failed`), as does one that outgrows even the worst-case reservation
-    (ions stripped again after recombining).  autotune: let the launch-shape autotuner time the cell
+    what an unconstrained run would.  The allowance grows up to the worst
+    case or the most cap_e holds; a request that outgrows that fails alone
+    (reported in `failed`; beyond the worst case only when its ions are
+    stripped again after recombining).  autotune: let the launch-shape autotuner time the cell
     kernel's warps per CTA for each new staging size (results do not depend
     on it).  batch: an object with the Batch interface to drive instead of
     a new Batch (host-logic tests)."""
@@ -144,11 +144,14 @@ def serve_batched(trace, tables, init_state, max_slabs: int, slot_cells: int, ca
                     res_e, res_i = res_e - a[2][0], res_i - a[2][1]
                     del active[slot]
                     worst = -(-r.nsteps // max(1, r.cfg.rad_every))
-                    if allowance[r.rid] >= worst:
-                        failed[r.rid] = f"went beyond the {a[2][0]} electron slots of its worst case"
+                    per = max(1, r.cfg.ncell * (r.pulse.n_bins if r.pulse is not None else 1))
+                    fits = (cap_e - footprint(r.cfg, r.pulse, 0)[0]) // per    # the most the capacity holds
+                    if allowance[r.rid] >= min(worst, fits):
+                        failed[r.rid] = f"went beyond the {a[2][0]} electron slots of its " + \
+                                        ("worst case" if allowance[r.rid] >= worst else "largest reservation")
                         ttr[r.rid] = time.perf_counter() - t0 - r.t_arrive
                         continue
-                    allowance[r.rid] = min(worst, allowance[r.rid] * grow)
+                    allowance[r.rid] = min(worst, fits, allowance[r.rid] * grow)
                     preempted += 1
                     back.append(r)
                     continue

@@ -138,3 +138,18 @@ def test_a_request_larger_than_the_batch_is_refused():
     with pytest.raises(ValueError, match="never fit"):
         serve.serve_batched(tr, None, lambda r: None, max_slabs=2, slot_cells=16, cap_e=fe - 1,
                             cap_i=10**6, batch=fb)
+
+
+def test_the_reservation_grows_up_to_what_the_capacity_holds():
+    """The preempted request's allowance grows by 4 each time, but not past
+    the most the capacity holds: with cap_e = 500 (own electrons and
+    charge reserve 280, 20 slots per allowance step) it runs at allowance 11,
+    where the unclamped 16 would not fit and the request would fail."""
+    tr = [_request(k, nx=10, ppc_i=2, nsteps=60) for k in range(2)]
+    n_end = 80 + 6 * 60                                    # 440 electrons at the end
+    assert serve.footprint(tr[0].cfg, tr[0].pulse, 4)[0] < n_end <= serve.footprint(tr[0].cfg, tr[0].pulse, 11)[0]
+    fb = FakeBatch(cap_e=500, cap_i=10**6, max_slabs=4, growth={100: 6})
+    out = serve.serve_batched(tr, None, lambda r: None, max_slabs=4, slot_cells=16, cap_e=500,
+                              cap_i=10**6, tick_steps=10, batch=fb)
+    assert sorted(out["results"]) == [0, 1] and not out["failed"]
+    assert out["preempted"] == 2 and out["results"][0]["steps"] == 60
