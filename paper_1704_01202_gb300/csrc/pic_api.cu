@@ -75,7 +75,7 @@ struct pic_ctx {
 
     real4 *eA0, *eA1, *eB0, *eB1;
     real4 *iA0, *iA1, *iB0, *iB1;
-    int *ekey, *ikey, *eord, *iord;
+    int *ekey, *ikey;
     int *csE[2], *csI[2];
     int cur = 0;
     int *cnt_e, *cnt_i, *fill_e, *fill_i, *bsum_e, *bsum_i;
@@ -183,20 +183,21 @@ size_t nw_scratch_entries(int ncell)
     return warps * 768;
 }
 
-// Global staging of the large-cell instances, in 8-byte words: 2048 a warp
-// (ids and keys of 1024 electrons in the FP32 build) for as many warps; the
+// Global staging of the large-cell instances, in 8-byte words: 3072 a warp
+// (ids, keys and positions of 1024 electrons in the FP32 build) for as many
+// warps; the
 // large cells' warps are few, and their grids are clamped to the slices.
 size_t gw_scratch_words(int ncell)
 {
     const size_t warps = std::min<size_t>(192 * 16, (size_t)ncell + 64);
-    return warps * 2048;
+    return warps * 3072;
 }
 
 size_t arena_need(int ncell, int npts, int nblk, int cap_e, int cap_i, int nslot, int nrows)
 {
     size_t b = 0;
-    b += 4 * al((size_t)cap_e * sizeof(real4)) + 2 * al((size_t)cap_e * 4);
-    b += 4 * al((size_t)cap_i * sizeof(real4)) + 2 * al((size_t)cap_i * 4);
+    b += 4 * al((size_t)cap_e * sizeof(real4)) + al((size_t)cap_e * 4);
+    b += 4 * al((size_t)cap_i * sizeof(real4)) + al((size_t)cap_i * 4);
     b += 4 * al((size_t)(ncell + 1) * 4) + al((size_t)ncell * 16) + 2 * al((size_t)nblk * 4);
     b += al(NCOUNTERS * 4) + al((size_t)ncell * 4) * 3;
     b += al(sizeof(SlabDev) * (size_t)nslot) + 3 * al(4 * (size_t)nslot) + al(sizeof(SlabTally) * (size_t)nslot)
@@ -387,7 +388,6 @@ CellArgs cell_args(pic_ctx *c, CellTier tier)
 {
     CellArgs a{};
     a.e0 = c->eA0; a.e1 = c->eA1; a.ekey = c->ekey; a.cs_e = c->csE[c->cur];
-    a.eord = c->eord; a.iord = c->iord;
     a.i0 = c->iA0; a.i1 = c->iA1; a.ikey = c->ikey; a.cs_i = c->csI[c->cur];
     a.cnt_e = c->cnt_e; a.cnt_i = c->cnt_i;
     a.append = c->counters + CNT_APPEND;
@@ -590,7 +590,6 @@ pic_status launch_step(pic_ctx *c)
     nv.phase("push and deposit");
     PushArgs pa{};
     pa.e0 = c->eA0; pa.e1 = c->eA1; pa.ekey = c->ekey; pa.cs_e = c->csE[c->cur];
-    pa.eord = c->eord; pa.iord = c->iord;
     pa.i0 = c->iA0; pa.i1 = c->iA1; pa.ikey = c->ikey; pa.cs_i = c->csI[c->cur];
     pa.cnt_e = c->cnt_e; pa.cnt_i = c->cnt_i; pa.append = c->counters + CNT_APPEND; pa.cap_e = c->cap_e;
     pa.ncell = c->ncell; pa.cell_slab = c->cell_slab; pa.slabs = c->d_slab; pa.tally = c->d_tally;
@@ -786,11 +785,9 @@ pic_status ctx_create(pic_ctx **out, int nslot, int slot_cells, int slot_pts, in
     c->eA0 = carve_arena<real4>(c, cap_e); c->eA1 = carve_arena<real4>(c, cap_e);
     c->eB0 = carve_arena<real4>(c, cap_e); c->eB1 = carve_arena<real4>(c, cap_e);
     c->ekey = carve_arena<int>(c, cap_e);
-    c->eord = carve_arena<int>(c, cap_e);
     c->iA0 = carve_arena<real4>(c, cap_i); c->iA1 = carve_arena<real4>(c, cap_i);
     c->iB0 = carve_arena<real4>(c, cap_i); c->iB1 = carve_arena<real4>(c, cap_i);
     c->ikey = carve_arena<int>(c, cap_i);
-    c->iord = carve_arena<int>(c, cap_i);
     for (int k = 0; k < 2; ++k) { c->csE[k] = carve_arena<int>(c, c->ncell + 1); c->csI[k] = carve_arena<int>(c, c->ncell + 1); }
     c->cnt_e = carve_arena<int>(c, 4 * (size_t)c->ncell);
     c->cnt_i = c->cnt_e + c->ncell; c->fill_e = c->cnt_i + c->ncell; c->fill_i = c->fill_e + c->ncell;

@@ -31,7 +31,6 @@ struct NewE {            // an electron created in this cell this step
 struct CellArgs {
     real4 *e0, *e1;     // electrons (xi, eta, ux, uy), (uz, w, id_lo, id_hi)
     int *ekey;           // next cell of each electron slot (-1: gone)
-    int *eord, *iord;    // canonical order of each cell: slot of position k
     const int *cs_e;     // cell start of electrons [ncell + 1]
     real4 *i0, *i1;     // ions (xi, eta, ux, uy), (uz, zfrac, id, Z | nK << 8)
     int *ikey;
@@ -339,6 +338,8 @@ struct WarpMem {
     unsigned long long *ekey;   // [cap_ce] sort key, later reused as real take
     unsigned long long *eid;    // [cap_ce] ids in canonical order
     unsigned short *eperm;      // [cap_ce] canonical position -> slot
+    real2 *epos;               // [cap_ce] positions in the cell (slot order)
+    real2 *ipos;               // [cap_ci] ion positions in the cell (slot order)
     real4 *iu;                 // [cap_ci] ux uy uz zfrac (slot order)
     int *ist;                   // [cap_ci] Z | nK << 8 (slot order)
     unsigned long long *ikey;   // [cap_ci] sort key, later reused as nrec
@@ -367,23 +368,25 @@ __host__ __device__ inline size_t amem(size_t x) { return (x + kSmAlign - 1) & ~
 // for cells above 128 entries, whose staging limits the warps resident on
 // an SM, also keep the electron ids (read once per collision), the sort
 // keys (later the per-electron scratch of the Lotz sums and of
-// recombination) and the radix buffer there (warp_gmem_words 8-byte words
-// a warp).
+// recombination), the positions (read back once, at the write-back) and
+// the radix buffer there (warp_gmem_words 8-byte words a warp).
 __host__ __device__ inline bool ids_in_gmem(int ce, int ci) { return rmax_for(ce, ci) > 128; }
 
 __host__ __device__ inline size_t warp_gmem_words(int ce, int ci)
 {
     if (!ids_in_gmem(ce, ci)) return 0;
     const int cm = ce > ci ? ce : ci;
-    return (size_t)ce * (1 + kKeyBytes / 8) + (cm > radix_min(rmax_for(ce, ci)) ? 2 * (size_t)cm : 0);
+    return (size_t)ce * (1 + kKeyBytes / 8 + sizeof(real2) / 8) +
+           (cm > radix_min(rmax_for(ce, ci)) ? 2 * (size_t)cm : 0);
 }
 
 __host__ __device__ inline size_t warp_mem_bytes(int ce, int ci)
 {
     const bool g = ids_in_gmem(ce, ci);
     size_t b = 0;
-    b += amem((size_t)ce * sizeof(real4)) + (g ? 0 : amem((size_t)ce * kKeyBytes) + amem((size_t)ce * 8)) +
-         amem((size_t)ce * 2);
+    b += amem((size_t)ce * sizeof(real4)) +
+         (g ? 0 : amem((size_t)ce * kKeyBytes) + amem((size_t)ce * 8) + amem((size_t)ce * sizeof(real2))) +
+         amem((size_t)ce * 2) + amem((size_t)ci * sizeof(real2));
     b += amem((size_t)ci * sizeof(real4)) + amem((size_t)ci * 4) + amem((size_t)ci * 8) + amem((size_t)ci * 4)
          + amem((size_t)ci * 2);
     b += amem(16 * sizeof(real)) * 2 + amem(NS * sizeof(real4)) + amem(2 * MAXB * sizeof(dd)) + amem(MAXB * 4);
@@ -402,11 +405,14 @@ __device__ inline WarpMem carve(char *base, int ce, int ci, NewE *nw, unsigned l
     if (g) {
         m.eid = gw;
         m.ekey = gw + ce;
+        m.epos = reinterpret_cast<real2 *>(gw + (size_t)ce * (1 + kKeyBytes / 8));
     } else {
         m.ekey = (unsigned long long *)p; p += amem((size_t)ce * kKeyBytes);
         m.eid = (unsigned long long *)p; p += amem((size_t)ce * 8);
+        m.epos = (real2 *)p; p += amem((size_t)ce * sizeof(real2));
     }
     m.eperm = (unsigned short *)p; p += amem((size_t)ce * 2);
+    m.ipos = (real2 *)p; p += amem((size_t)ci * sizeof(real2));
     m.iu = (real4 *)p; p += amem((size_t)ci * sizeof(real4));
     m.ist = (int *)p; p += amem((size_t)ci * 4);
     m.ikey = (unsigned long long *)p; p += amem((size_t)ci * 8);
@@ -421,7 +427,7 @@ __device__ inline WarpMem carve(char *base, int ce, int ci, NewE *nw, unsigned l
     const int cm = ce > ci ? ce : ci;
     m.rbuf = nullptr; m.rhist = nullptr;
     if (cm > radix_min(rmax_for(ce, ci))) {
-        if (g) m.rbuf = gw + (size_t)ce * (1 + kKeyBytes / 8);
+        if (g) m.rbuf = gw + (size_t)ce * (1 + kKeyBytes / 8 + sizeof(real2) / 8);
         else { m.rbuf = (unsigned long long *)p; p += amem((size_t)cm * 16); }
         m.rhist = (int *)p;
     }

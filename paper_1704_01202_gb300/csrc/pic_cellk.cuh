@@ -538,6 +538,7 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
     for (int k = lane; k < ne; k += 32) {
         real4 P0 = a.e0[e0 + k], P1 = a.e1[e0 + k];
         m.eu[k] = make_real4(P0.z, P0.w, P1.x, P1.y);
+        m.epos[k] = make_real2(P0.x, P0.y);
         unsigned long long id = rec_eid(P1);
         U4 r = draw(seed, id, step, PU_PAIR_E);
         m.ekey[k] = ((unsigned long long)r.x << 32) | r.y;
@@ -547,6 +548,7 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
     for (int k = lane; k < ni; k += 32) {
         real4 P0 = a.i0[i0 + k], P1 = a.i1[i0 + k];
         m.iu[k] = make_real4(P0.z, P0.w, P1.x, P1.y);
+        m.ipos[k] = make_real2(P0.x, P0.y);
         m.ist[k] = rec_ist(P1);
         unsigned id = rec_iid(P1);
         U4 r = draw(seed, (unsigned long long)id, step, PU_PAIR_I);
@@ -892,14 +894,14 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
     if (rad && (flags & 32u) && ni >= 1) stage_decay(a, m, T, S, cc, lane, nnew, wt);
     if (rad && (flags & 256u)) stage_therm(a, m, cc, lane, nnew);
 
-    // ---- write the collided state back (positions unchanged) and the
-    //      canonical order, which the push kernel follows ----
-    for (int k = lane; k < ne; k += 32) a.eord[e0 + k] = m.eperm[k];
-    for (int k = lane; k < ni; k += 32) a.iord[i0 + k] = m.iperm[k];
+    // ---- write the collided state back, each cell's records in its
+    //      canonical order (the order the push kernel follows) ----
     for (int k = lane; k < ne; k += 32) {
-        real4 u = m.eu[k];
-        reinterpret_cast<real2 *>(a.e0 + e0 + k)[1] = make_real2(u.x, u.y);
-        reinterpret_cast<real2 *>(a.e1 + e0 + k)[0] = make_real2(u.z, u.w);
+        const int sl = m.eperm[k];
+        const real4 u = m.eu[sl];
+        const real2 x = m.epos[sl];
+        a.e0[e0 + k] = make_real4(x.x, x.y, u.x, u.y);
+        a.e1[e0 + k] = rec_e1(u.z, u.w, m.eid[k]);
     }
     if (rad && S.rt) {
         // transport mode: the cell's electron weight after the step, created
@@ -913,13 +915,6 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
         for (int k = lane; k < nnew; k += 32) wsum += m.nw[k].w;
         wsum = wsum_f(wsum);
         if (lane == 0) S.rt_w[lc] = (float)wsum;
-    }
-    for (int k = lane; k < ni; k += 32) {
-        real4 u = m.iu[k];
-        reinterpret_cast<real2 *>(a.i0 + i0 + k)[1] = make_real2(u.x, u.y);
-        real4 *r1 = a.i1 + i0 + k;
-        reinterpret_cast<real2 *>(r1)[0] = make_real2(u.z, u.w);
-        r1->w = bits_real((uint32_t)m.ist[k]);
     }
     // ---- created electrons: after the sorted range, at their ion, with their cell as key ----
     if (nnew > 0) {
@@ -957,6 +952,16 @@ __device__ void process_round(const CellArgs &a, const WarpMem &m, const Tables 
             a.e1[sorted + base + k] = rec_e1(q.uz, q.w, ((unsigned long long)idhi << 32) | rec_iid(I1));
             a.ekey[sorted + base + k] = g;
         }
+    }
+    __syncwarp();
+    // ions last: the created electrons above read their parent ions' records
+    // at the ions' slots
+    for (int k = lane; k < ni; k += 32) {
+        const int sl = m.iperm[k];
+        const real4 u = m.iu[sl];
+        const real2 x = m.ipos[sl];
+        a.i0[i0 + k] = make_real4(x.x, x.y, u.x, u.y);
+        a.i1[i0 + k] = rec_i1(u.z, u.w, m.iid[k], m.ist[sl]);
     }
 
     // ---- tallies (lane-uniform) ----
@@ -1010,14 +1015,9 @@ __global__ void __launch_bounds__(RMAX > 512 ? 128 : 256, RMAX > 512 ? 1 : 2) k_
                     // no larger pass left: report, and drop the cell's particles so
                     // that the next sort stays consistent
                     if (lane == 0) atomicOr(a.err, ERR_CELL_OVERFLOW);
-                    for (int k = a.cs_e[g] + lane; k < a.cs_e[g + 1]; k += 32) {
+                    for (int k = a.cs_e[g] + lane; k < a.cs_e[g + 1]; k += 32)
                         reinterpret_cast<real *>(a.e1 + k)[1] = RF(0.0);
-                        a.eord[k] = k - a.cs_e[g];
-                    }
-                    for (int k = a.cs_i[g] + lane; k < a.cs_i[g + 1]; k += 32) {
-                        a.i1[k].w = bits_real(0xffu);
-                        a.iord[k] = k - a.cs_i[g];
-                    }
+                    for (int k = a.cs_i[g] + lane; k < a.cs_i[g + 1]; k += 32) a.i1[k].w = bits_real(0xffu);
                 }
                 g = -1;
             }

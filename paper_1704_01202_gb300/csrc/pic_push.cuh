@@ -16,7 +16,6 @@ namespace pic {
 struct PushArgs {
     real4 *e0, *e1;
     int *ekey;
-    const int *eord, *iord;   // canonical order of each cell (from the collision kernel)
     const int *cs_e;
     real4 *i0, *i1;
     int *ikey;
@@ -276,13 +275,13 @@ __device__ void push_cell(const PushArgs &a, const SlabDev &S, int s, int g, int
         real4 *R0 = elec ? a.e0 : a.i0, *R1 = elec ? a.e1 : a.i1;
         int *key = elec ? a.ekey : a.ikey;
         int *cnt = elec ? a.cnt_e : a.cnt_i;
-        const int *ord = elec ? a.eord : a.iord;
         const int n = k1 - k0;
         // every lane runs the same number of iterations (the warp reductions
         // of the deposit need all 32 lanes)
         for (int base = 0; base < n; base += 32) {
             const bool have = base + lane < n;
-            const int k = have ? k0 + min(max(ord[k0 + base + lane], 0), n - 1) : k0;
+            // the collision kernel left each cell's records in canonical order
+            const int k = have ? k0 + base + lane : k0;
             int nk = -1;
             real x0 = RF(0.), y0 = RF(0.), x1 = RF(0.), y1 = RF(0.), qw = RF(0.), qwby = RF(0.), qwbz = RF(0.);
             bool dep_short = false;
