@@ -44,15 +44,15 @@ import pic_inputs as P  # noqa: E402
 METRIC = "collided particle-steps/s"
 UNIT = "particle-steps/s"
 # algorithmic bytes per particle of the per-cell kernel: the 32 B record
-# read and written once, plus the 4 B next-cell key
-CELL_BYTES_PER_PARTICLE = 68
-# whole step: cell kernel 68 B + scatter (36 B read, 32 B written)
-STEP_BYTES_PER_PARTICLE = 136
+# read and written once (written back in the cell's canonical order)
+CELL_BYTES_PER_PARTICLE = 64
+# whole step: cell kernel 64 B + scatter (36 B read, 32 B written)
+STEP_BYTES_PER_PARTICLE = 132
 # DRAM bytes per particle of the cell kernel, from one ncu capture of a
-# smaller slab of the same make-up (1024 x 256 cells, tier-0 launch, ~27.5 M
-# particles: 1903 MB), scaled to a launch by the particle count; None when
-# no capture of the current kernel exists
-CELL_TRAFFIC_BYTES_PER_PARTICLE = 69
+# smaller slab of the same make-up, scaled to a launch by the particle
+# count; None when no capture of the current kernel exists (the last one,
+# 69 B per particle, predates the canonical-order write-back)
+CELL_TRAFFIC_BYTES_PER_PARTICLE = None
 
 
 def measured_peaks():
