@@ -49,10 +49,11 @@ CELL_BYTES_PER_PARTICLE = 64
 # whole step: cell kernel 64 B + scatter (36 B read, 32 B written)
 STEP_BYTES_PER_PARTICLE = 132
 # DRAM bytes per particle of the cell kernel, from one ncu capture of a
-# smaller slab of the same make-up, scaled to a launch by the particle
-# count; None when no capture of the current kernel exists (the last one,
-# 69 B per particle, predates the canonical-order write-back)
-CELL_TRAFFIC_BYTES_PER_PARTICLE = None
+# smaller slab of the same make-up (1024 x 256 cells, 28.0 M particles:
+# 1782.5 MB on a plain step, 1829.6 MB on a radiation step, 64.0 B per
+# particle over the five-step cycle), scaled to a launch by the particle
+# count; None when no capture of the current kernel exists
+CELL_TRAFFIC_BYTES_PER_PARTICLE = 64.0
 
 
 def measured_peaks():
