@@ -3,7 +3,8 @@ paper_facts.json, each with its section): the cold K edge, how far K-shell
 photoionization reaches at three photon energies under Ecker-Kroell
 lowering (Sec. V, Eq. 4; Sec. VI B), the KLL Auger energy (Sec. VI B), the
 photoelectron energy of the 10 keV case (Sec. VI C), the time steps and
-the free-electron room per cell (Sec. VI).  The atomic data are stand-ins,
+the free-electron room per cell (Sec. VI), and the K-vacancy decay
+branching and lifetime rule (Sec. IV).  The atomic data are stand-ins,
 so these check that the stand-ins and the oracle's continuum lowering,
 Auger and photoelectron energies land where the paper says the method
 lands."""
@@ -100,3 +101,23 @@ def test_time_steps_and_electron_room():
     from paper_1704_01202_gb300.serve import footprint
     one = P.cfg_small_1d(nx=1, ppc_i=g["ions_per_cell"], ppc_e=3 * g["ions_per_cell"])
     assert footprint(one)[0] == g["value"]
+
+
+def test_k_vacancy_decay_tables(tables):
+    """Sec. IV: a K vacancy in Al with a full L shell decays by KLL Auger
+    about 96 % of the time, and above 10 bound electrons the lifetime is
+    linear in the bound-electron count between 10 and the neutral atom's 13
+    (the oracle's branching follows 1 - omega_K of the table; see
+    test_oracle_atomic's decay test)."""
+    f = FACTS["kll_auger_share"]
+    om = np.asarray(tables["omegaK"], dtype=np.float64)
+    tau = np.asarray(tables["tauK"], dtype=np.float64)
+    for nb in f["bound_electrons"]:
+        assert abs((1.0 - om[nb, 0]) - f["value"]) <= f["abs_tol"], (nb, om[nb, 0])
+    g = FACTS["k_lifetime_rule"]
+    lo, hi = g["full_l_shell_from"], g["neutral"]
+    for nk in (0, 1):
+        assert tau[lo, nk] > 0 and tau[hi, nk] > 0
+        for nb in range(lo + 1, hi):
+            lin = tau[lo, nk] + (nb - lo) / (hi - lo) * (tau[hi, nk] - tau[lo, nk])
+            assert abs(tau[nb, nk] - lin) <= 1e-12 * lin, (nb, nk)
