@@ -4,7 +4,7 @@ photoionization reaches at three photon energies under Ecker-Kroell
 lowering (Sec. V, Eq. 4; Sec. VI B), the KLL Auger energy (Sec. VI B), the
 photoelectron energy of the 10 keV case (Sec. VI C), the time steps and
 the free-electron room per cell (Sec. VI), and the K-vacancy decay
-branching and lifetime rule (Sec. IV).  The atomic data are stand-ins,
+branching and lifetime rule (Sec. III).  The atomic data are stand-ins,
 so these check that the stand-ins and the oracle's continuum lowering,
 Auger and photoelectron energies land where the paper says the method
 lands."""
@@ -104,7 +104,7 @@ def test_time_steps_and_electron_room():
 
 
 def test_k_vacancy_decay_tables(tables):
-    """Sec. IV: a K vacancy in Al with a full L shell decays by KLL Auger
+    """Sec. III: a K vacancy in Al with a full L shell decays by KLL Auger
     about 96 % of the time, and above 10 bound electrons the lifetime is
     linear in the bound-electron count between 10 and the neutral atom's 13
     (the oracle's branching follows 1 - omega_K of the table; see
