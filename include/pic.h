@@ -197,7 +197,7 @@ pic_status pic_rt_set(pic_ctx *c, const double *F, const double *Gx, const doubl
  * due to its bulk electrons ([ncell] each).  Synchronizes. */
 pic_status pic_rt_cells(pic_ctx *c, double *chi, double *emc, double *w, double *dE);
 
-/* Initial plasma of the slab (Sec. II's solid-density start, seeded on the
+/* Initial plasma of the slab (the solid Al target of Sec. VI, seeded on the
  * device): ppc_e electrons and ppc_i ions in every cell at uniform random
  * positions (y = 0.5 in 1D), ions at charge Z_init with full K shells,
  * Maxwellian momenta at T_i, electrons Maxwellian at T_e except a

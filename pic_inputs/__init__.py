@@ -473,7 +473,8 @@ def request_trace(n: int = 2000, rate_hz: float = 200.0, seed: int = 11, horizon
     """Poisson arrivals of slab requests.  Each request is an ensemble draw
     plus a foil thickness ~ U(0.2, 2) um; the cell size is thickness / cells,
     with the cell count capped so that cells stay at least min_dx_nm wide
-    (finer cells would only multiply the field subcycles)."""
+    (finer cells would only lower the field speed the step resolves and
+    multiply the cells)."""
     rng = np.random.default_rng(seed)
     t = np.cumsum(rng.exponential(1.0 / rate_hz, n))
     out = []

@@ -31,8 +31,8 @@ def _built():
 
 
 def _slabs():
-    """Three 1D slabs of different sizes, seeds, weights and subcycle
-    counts; A has every process on and a pulse."""
+    """Three 1D slabs of different sizes, seeds, weights and cell widths
+    (so different field speeds); A has every process on and a pulse."""
     a = P.cfg_small_1d(nx=48, seed=11, ppc_e=96, ppc_i=24, rad_every=1, flags=P.F_ALL)
     b = P.cfg_small_1d(nx=64, seed=12, ppc_e=128, ppc_i=32)
     c = P.cfg_small_1d(nx=30, seed=13, ppc_e=64, ppc_i=16, dx_nm=2.5, Z_init=4)

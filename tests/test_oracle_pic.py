@@ -3,7 +3,8 @@
 The paper's PICLS is a PIC code (Sec. I, VI: absorbing boundaries, sheath
 fields) but prints none of its particle or field algorithms; the oracle
 uses a relativistic Boris push, Esirkepov's charge-conserving deposit with
-linear shapes and a subcycled Yee solver with first-order Mur boundaries.
+linear shapes and a Yee solver (one update per step at the field speed the
+step resolves) with first-order Mur boundaries.
 Pinned by: the discrete continuity equation, Gauss's law carried by the
 solver, the cold plasma frequency, exact vacuum propagation at the magic
 time step, and determinism across thread counts.
