@@ -18,7 +18,8 @@ value: particle-steps/s with the state resident in HBM (device-timed with
 CUDA events on the context stream, K steps between a synchronize on each
 side).  e2e: the same metric through the public API with host buffers:
 the H2D load of the initial state and a D2H diagnostics read every step
-inside the timed region.  The state (27 GB) is far larger than L2.
+inside the timed region.  The state (27 GB at the start, ~32 GB at the
+timed steps) is far larger than L2.
 
 --impl reference: the FP64 oracle on the host cores, on a bounded sample
 of the same workload (a 64 x 64-cell patch of the slab).
@@ -26,7 +27,6 @@ of the same workload (a 64 x 64-cell patch of the slab).
 import argparse
 import dataclasses
 import json
-import math
 import os
 import statistics
 import subprocess

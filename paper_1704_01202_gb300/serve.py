@@ -84,7 +84,6 @@ def serve_batched(trace, tables, init_state, max_slabs: int, slot_cells: int, ca
     kernel's warps per CTA for each new staging size (results do not depend
     on it).  batch: an object with the Batch interface to drive instead of
     a new Batch (host-logic tests)."""
-    from . import SLOT_FAILED
     bt = batch if batch is not None else Batch(tables, max_slabs, slot_cells, cap_e, cap_i)
     if autotune:
         bt.autotune(True)

@@ -9,7 +9,6 @@ exact invariants and binomial statistics.
 import math
 
 import numpy as np
-import pytest
 from scipy import special
 
 import oracle
