@@ -24,7 +24,17 @@
  * problems (cell overflow, capacity, numeric) latch an error word that the
  * next synchronizing call (pic_sync, pic_diagnostics, pic_get_*) returns;
  * pic_last_error gives a message.  A context is used by one host thread at
- * a time.
+ * a time.  Where a declaration lists no errors of its own: PIC_ERR_ARG for
+ * a NULL context or array, a negative count, a slot out of range or a value
+ * out of its stated range (a per-slot batch call on a single-slab context
+ * has no such slot: PIC_ERR_ARG too); PIC_ERR_STATE for a single-slab call
+ * on a batch context; PIC_ERR_CUDA when a CUDA runtime call fails.
+ *
+ * Ownership: host arrays are read or written during the call only; the
+ * library keeps no pointer to them (tables and pulses are copied).  The
+ * device arena given to pic_init or pic_batch_init stays the caller's and
+ * must outlive the context; with a NULL arena the context allocates its own
+ * and pic_free releases it.
  */
 #ifndef PIC_H
 #define PIC_H
