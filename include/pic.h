@@ -97,7 +97,8 @@ typedef struct {
     int ipd_model;          /* PIC_IPD_* (Sec. V) */
     double coulomb_log;     /* > 0: fixed; <= 0: computed per cell */
     unsigned flags;         /* PIC_F_* */
-    int cap_e, cap_i;       /* particle capacity of the slab (0: 4x / 1x loaded) */
+    int cap_e, cap_i;       /* particle capacity of the slab: > 0 for pic_init;
+                             * ignored by pic_batch_admit (the batch's own) */
 } pic_species;
 
 /* Atomic data (Sec. III-V).  Copied at pic_init; the caller keeps its
