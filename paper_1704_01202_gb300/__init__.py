@@ -216,7 +216,7 @@ def lib(fp64: bool = False):
                                              C.POINTER(C.c_int32), C.POINTER(C.c_uint32)]
             for name in ABI_FUNCTIONS:
                 if name not in ("pic_required_bytes", "pic_launch_count", "pic_last_error",
-                                "pic_batch_required_bytes"):
+                                "pic_batch_required_bytes", "pic_checkpoint_bytes"):
                     getattr(L, name).restype = C.c_int
             if L.pic_real_bytes() != (8 if fp64 else 4):
                 raise RuntimeError(f"{path} is not the {'FP64' if fp64 else 'FP32'} build")
