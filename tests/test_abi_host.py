@@ -3,7 +3,8 @@ pic_required_bytes / pic_batch_required_bytes (bytes per particle slot as
 the HBM layout states them, the large 2D slab's arena within one GB300),
 the refusal of invalid grids, species and sizes, and the PIC_ERR_ARG answer
 of every call to a NULL context or out-of-range size, all of which the
-library checks before it touches the device (no CUDA call is made here)."""
+library checks before it touches the device (no CUDA call is made here),
+and the binding's ctypes signatures against the header's prototypes."""
 import ctypes as C
 
 import numpy as np
@@ -152,3 +153,52 @@ def test_check_entries_refuse_bad_sizes(build):
     px = x.ctypes.data_as(C.POINTER(C.c_float))
     assert L.pic_dd_sum_check(px, 0, C.byref(d)) == PIC_ERR_ARG
     assert L.pic_dd_sum_check(px, (1 << 24) + 1, C.byref(d)) == PIC_ERR_ARG
+
+
+def _prototypes():
+    """(result type, [parameter types]) of every function include/pic.h
+    declares, comments removed and whitespace normalized."""
+    import os
+    import re
+    src = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "pic.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"([A-Za-z_][\w \*]*?)\b(pic_\w+)\s*\(([^;{]*?)\)\s*;", src):
+        ret, name, params = " ".join(m.group(1).split()), m.group(2), " ".join(m.group(3).split())
+        types = []
+        for p in ([] if params in ("", "void") else params.split(",")):
+            p = p.strip()
+            arr = p.endswith("]")
+            p = re.sub(r"\[\d*\]$", "", p)
+            t = re.sub(r"\b\w+$", "", p).replace(" ", "").replace("const", "")
+            types.append(t + ("*" if arr else ""))
+        out[name] = (ret.replace("const ", "").replace(" ", ""), types)
+    return out
+
+
+_CTYPE = {"int": C.c_int, "int64_t": C.c_int64, "size_t": C.c_size_t, "void*": C.c_void_p,
+          "pic_ctx*": C.c_void_p, "pic_ctx**": C.POINTER(C.c_void_p), "double*": C.POINTER(C.c_double),
+          "float*": C.POINTER(C.c_float), "uint64_t*": C.POINTER(C.c_uint64),
+          "uint32_t*": C.POINTER(C.c_uint32), "int32_t*": C.POINTER(C.c_int32),
+          "uint16_t*": C.POINTER(C.c_uint16), "int*": C.POINTER(C.c_int), "int64_t*": C.POINTER(C.c_int64),
+          "pic_grid*": C.POINTER(Grid), "pic_species*": C.POINTER(Species), "pic_tables*": C.POINTER(Tables),
+          "pic_pulse*": C.POINTER(pkg.Pulse), "pic_diag*": C.POINTER(pkg.Diag),
+          "pic_seed_spec*": C.POINTER(pkg.SeedSpec), "pic_rt_config*": C.POINTER(pkg.RTConfig)}
+_RTYPE = {"pic_status": C.c_int, "int": C.c_int, "size_t": C.c_size_t, "int64_t": C.c_int64, "char*": C.c_char_p}
+
+
+def test_binding_signatures_match_the_header(build):
+    """Every function's ctypes argument and result types in the binding
+    are the ones its C prototype gives (a narrower integer or a wrong
+    pointer type would corrupt values silently)."""
+    L, _ = build
+    protos = _prototypes()
+    assert sorted(protos) == sorted(pkg.ABI_FUNCTIONS)
+    for name, (ret, params) in protos.items():
+        f = getattr(L, name)
+        assert f.restype is _RTYPE[ret], (name, ret, f.restype)
+        if not params:
+            continue
+        assert f.argtypes is not None, name
+        want = [_CTYPE[t] for t in params]
+        assert list(f.argtypes) == want, (name, params, f.argtypes)
