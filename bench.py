@@ -192,10 +192,11 @@ def run_reference(args):
 def capacity(cfg, n_e, n_i):
     """Particle capacity of the timed slab: electrons for a mean charge up to
     9.5 on the large slab (the precision study's figure), for full
-    stripping otherwise (below 2^31 slots)."""
+    stripping otherwise, within what 32-bit particle indices hold
+    (cap_e + 3 cap_i below 2^31)."""
     import paper_1704_01202_gb300 as pkg
     ce, ci = pkg.default_capacity(n_e, n_i, cfg.Z_init)
-    return min(ce, int(9.5 * n_i) + 1024, (1 << 31) - (1 << 28)), ci
+    return min(ce, int(9.5 * n_i) + 1024, (1 << 31) - 1 - 3 * ci), ci
 
 
 ENERGY_KEYS = ("ke_e", "ke_i", "e_ion", "e_phot", "e_field", "e_esc", "e_trans", "e_ka_esc")

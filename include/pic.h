@@ -97,8 +97,11 @@ typedef struct {
     int ipd_model;          /* PIC_IPD_* (Sec. V) */
     double coulomb_log;     /* > 0: fixed; <= 0: computed per cell */
     unsigned flags;         /* PIC_F_* */
-    int cap_e, cap_i;       /* particle capacity of the slab: > 0 for pic_init;
-                             * ignored by pic_batch_admit (the batch's own) */
+    int cap_e, cap_i;       /* particle capacity of the slab: > 0 with
+                             * cap_e + 3 cap_i < 2^31 for pic_init (a step
+                             * appends at most three electrons per ion, and
+                             * particle indices are 32-bit); ignored by
+                             * pic_batch_admit (the batch's own) */
 } pic_species;
 
 /* Atomic data (Sec. III-V).  Copied at pic_init; the caller keeps its
@@ -156,7 +159,9 @@ typedef struct {
     double e_back, e_rt_num, e_rt_pend;
 } pic_diag;
 
-/* Bytes of device memory pic_init needs for this slab. */
+/* Bytes of device memory pic_init needs for this slab (n_e_cap / n_i_cap
+ * > 0 override the species' capacities); 0 for an invalid grid or
+ * capacities pic_init would refuse. */
 size_t pic_required_bytes(const pic_grid *g, const pic_species *s, int n_e_cap, int n_i_cap);
 
 /* Create a context for one slab.  arena/arena_bytes: caller-owned device
@@ -321,7 +326,8 @@ pic_status pic_get_current(pic_ctx *c, double *j3);
 size_t pic_batch_required_bytes(int max_slabs, int slot_cells, int cap_e, int cap_i);
 
 /* Create an empty batch context of max_slabs slots of slot_cells cells
- * (2..8192).  cap_e / cap_i: particle capacity summed over all slabs.
+ * (2..8192).  cap_e / cap_i: particle capacity summed over all slabs, > 0
+ * with cap_e + 3 cap_i < 2^31 (as for pic_init; PIC_ERR_ARG otherwise).
  * arena / stream as in pic_init. */
 pic_status pic_batch_init(pic_ctx **out, int max_slabs, int slot_cells, int cap_e, int cap_i,
                           const pic_tables *t, void *arena, size_t arena_bytes, void *stream);

@@ -268,6 +268,16 @@ def default_capacity(n_e: int, n_i: int, z_init: int, headroom: float = 1.3) -> 
     return cap_e, n_i + 1024
 
 
+def check_capacity(cap_e: int, cap_i: int) -> None:
+    """Refuse capacities the C ABI cannot take, before they reach a 32-bit
+    ctypes field (which would wrap them silently): both positive and
+    cap_e + 3 cap_i below 2^31 (a step appends at most three electrons per
+    ion after the held ones, and particle indices are 32-bit)."""
+    if cap_e <= 0 or cap_i <= 0 or cap_e + 3 * cap_i > (1 << 31) - 1:
+        raise PicError(f"capacity cap_e={cap_e}, cap_i={cap_i} out of range: both > 0 and "
+                       f"cap_e + 3 cap_i < 2^31; pass smaller capacities")
+
+
 class Slab:
     """One slab on the GPU, driven through the C ABI."""
 
@@ -280,6 +290,7 @@ class Slab:
             ce, ci = default_capacity(cfg.ncell * cfg.ppc_e, cfg.ncell * cfg.ppc_i, cfg.Z_init)
             cap_e = cap_e if cap_e > 0 else ce
             cap_i = cap_i if cap_i > 0 else ci
+        check_capacity(cap_e, cap_i)
         self.species = _species(cfg, cap_e, cap_i)
         self._t, self._keep = _tables(tables)
         self.arena = None
@@ -534,6 +545,7 @@ class Batch:
             raise PicError("no CUDA device")
         self.L = lib()
         self.max_slabs, self.slot_cells = max_slabs, slot_cells
+        check_capacity(cap_e, cap_i)
         self._t, self._keep = _tables(tables)
         nbytes = self.L.pic_batch_required_bytes(max_slabs, slot_cells, cap_e, cap_i)
         if nbytes == 0:

@@ -658,6 +658,11 @@ bool valid_grid(const pic_grid *g)
            g->cfl > 0 && (long long)g->nx * g->ny <= (1LL << 30);
 }
 
+// Particle capacities: the electrons a step creates (at most three per ion:
+// impact, photo- and Auger ionization) are appended after the held ones and
+// every particle index is 32-bit, so cap_e + 3 cap_i must stay below 2^31.
+bool caps_fit(long long ce, long long ci) { return ce > 0 && ci > 0 && ce + 3 * ci <= 0x7fffffffLL; }
+
 bool valid_species(const pic_species *s)
 {
     return s && s->w_ion > 0 && s->m_ion_me > 0 && s->n_ref_cm3 > 0 && s->ipd_model >= 0 && s->ipd_model <= 2;
@@ -1412,6 +1417,7 @@ size_t pic_required_bytes(const pic_grid *g, const pic_species *s, int n_e_cap, 
     int ncell = g->nx * g->ny, npts = (g->nx + 1) * g->ny;
     int nblk = (ncell + SCAN_TILE - 1) / SCAN_TILE;
     int ce = n_e_cap > 0 ? n_e_cap : s->cap_e, ci = n_i_cap > 0 ? n_i_cap : s->cap_i;
+    if (!caps_fit(ce, ci)) return 0;
     return arena_need(ncell, npts, nblk, ce, ci, 1, g->ny);
 }
 
@@ -1420,7 +1426,7 @@ pic_status pic_init(pic_ctx **out, const pic_grid *g, const pic_species *s, cons
 {
     if (!out || !t) return PIC_ERR_ARG;
     *out = nullptr;
-    if (!valid_grid(g) || !valid_species(s) || s->cap_e <= 0 || s->cap_i <= 0) return PIC_ERR_ARG;
+    if (!valid_grid(g) || !valid_species(s) || !caps_fit(s->cap_e, s->cap_i)) return PIC_ERR_ARG;
     pic_ctx *c = nullptr;
     pic_status r = ctx_create(&c, 1, g->nx * g->ny, (g->nx + 1) * g->ny, g->ny, g->nx, s->cap_e, s->cap_i, t, arena,
                               arena_bytes, stream);
@@ -1643,7 +1649,7 @@ pic_status pic_diagnostics(pic_ctx *c, pic_diag *out)
 
 size_t pic_batch_required_bytes(int max_slabs, int slot_cells, int cap_e, int cap_i)
 {
-    if (max_slabs < 1 || slot_cells < 2 || slot_cells > 8192 || cap_e <= 0 || cap_i <= 0) return 0;
+    if (max_slabs < 1 || slot_cells < 2 || slot_cells > 8192 || !caps_fit(cap_e, cap_i)) return 0;
     long long ncell = (long long)max_slabs * slot_cells, npts = (long long)max_slabs * (slot_cells + 1);
     if (npts > (1LL << 30)) return 0;
     int nblk = (int)((ncell + SCAN_TILE - 1) / SCAN_TILE);

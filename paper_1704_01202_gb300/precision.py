@@ -24,7 +24,7 @@ def run_study(tables, cfg, pulse, state, steps: int, every: int, cap_e: int = 0,
     up to ~9.5 over the slab)."""
     import torch
     from . import Slab
-    cap_e = cap_e or min(int(9.5 * state.n_i) + 1024, (1 << 31) - (1 << 28))
+    cap_e = cap_e or min(int(9.5 * state.n_i) + 1024, (1 << 31) - 1 - 3 * (state.n_i + 1024))
     t0 = time.perf_counter()
     g = Slab(cfg, tables, pulse, cap_e=cap_e, cap_i=state.n_i + 1024)
     try:

@@ -202,3 +202,40 @@ def test_binding_signatures_match_the_header(build):
         assert f.argtypes is not None, name
         want = [_CTYPE[t] for t in params]
         assert list(f.argtypes) == want, (name, params, f.argtypes)
+
+
+def test_capacities_stay_within_32_bit_particle_indices(build):
+    """cap_e + 3 cap_i must stay below 2^31 (a step appends at most three
+    electrons per ion after the held ones): the library refuses beyond, at
+    pic_required_bytes, pic_init and pic_batch_required_bytes, and the
+    binding refuses before a value can wrap in a 32-bit ctypes field."""
+    L, _ = build
+    cfg = P.cfg_small_1d()
+    top = (1 << 31) - 1
+    ci = 1 << 20
+    assert _req(L, cfg, top - 3 * ci, ci) > 0
+    assert _req(L, cfg, top - 3 * ci + 1, ci) == 0
+    assert L.pic_batch_required_bytes(2, 64, top - 3 * ci, ci) > 0
+    assert L.pic_batch_required_bytes(2, 64, top - 3 * ci + 1, ci) == 0
+    ctx = C.c_void_p()
+    s = _species(cfg, top - 3 * ci + 1, ci)
+    assert L.pic_init(C.byref(ctx), C.byref(_grid(cfg)), C.byref(s), C.byref(Tables()), None, 0,
+                      None) == PIC_ERR_ARG
+    pkg.check_capacity(top - 3 * ci, ci)
+    for ce, c_i in ((top - 3 * ci + 1, ci), (4_500_000_000, 1000), (0, 10), (10, 0), (-5, 10)):
+        with pytest.raises(pkg.PicError, match="capacity"):
+            pkg.check_capacity(ce, c_i)
+
+
+def test_bench_capacity_of_the_large_slab():
+    import importlib.util
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("bench_cap", os.path.join(root, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    cfg = P.cfg_large_2d()
+    n_e, n_i = cfg.ncell * cfg.ppc_e, cfg.ncell * cfg.ppc_i
+    ce, ci = bench.capacity(cfg, n_e, n_i)
+    assert ce == int(9.5 * n_i) + 1024 and ci == n_i + 1024     # room for a mean charge of 9.5
+    pkg.check_capacity(ce, ci)
