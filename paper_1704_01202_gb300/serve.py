@@ -80,7 +80,9 @@ def serve_batched(trace, tables, init_state, max_slabs: int, slot_cells: int, ca
     what an unconstrained run would.  The allowance grows up to the worst
     case or the most cap_e holds; a request that outgrows that fails alone
     (reported in `failed`; beyond the worst case only when its ions are
-    stripped again after recombining).  autotune: let the launch-shape autotuner time the cell
+    stripped again after recombining).  A request wider than a slot, or
+    whose first reservation is beyond the batch's capacity, is refused alone
+    on arrival (also in `failed`).  autotune: let the launch-shape autotuner time the cell
     kernel's warps per CTA for each new staging size (results do not depend
     on it).  batch: an object with the Batch interface to drive instead of
     a new Batch (host-logic tests)."""
@@ -104,9 +106,14 @@ def serve_batched(trace, tables, init_state, max_slabs: int, slot_cells: int, ca
                 a = allowance.setdefault(r.rid, 1)
                 fe, fi = footprint(r.cfg, r.pulse, a)
                 if r.cfg.nx > slot_cells or fe > cap_e or fi > cap_i:
-                    if a == 1:
-                        raise ValueError(f"request {r.rid} can never fit the batch")
-                    failed[r.rid] = f"needs more than {cap_e} electron slots"
+                    # refused alone; the rest of the trace is served
+                    if r.cfg.nx > slot_cells:
+                        failed[r.rid] = f"{r.cfg.nx} cells, more than a slot's {slot_cells}"
+                    elif a == 1:
+                        failed[r.rid] = f"its footprint ({fe} electron, {fi} ion slots) is beyond the batch's " \
+                                        f"capacity ({cap_e}, {cap_i})"
+                    else:
+                        failed[r.rid] = f"needs more than {cap_e} electron slots"
                     ttr[r.rid] = time.perf_counter() - t0 - r.t_arrive
                     pending.pop(0)
                     continue

@@ -1,11 +1,10 @@
 """Host logic of the served loop, without a GPU: admission by reservation,
 queueing, electron budgets, preemption of a slab that outgrows its
-reservation and its re-run with a larger one, and the failure of a request
-that can never fit, against a stand-in for the batch context that grows
-each slab's electrons at a scripted rate."""
+reservation and its re-run with a larger one, the failure of a request
+that can never fit and the refusal on arrival of one wider than a slot or
+larger than the batch, each alone, against a stand-in for the batch
+context that grows each slab's electrons at a scripted rate."""
 from dataclasses import dataclass, field
-
-import pytest
 
 import pic_inputs as P
 from paper_1704_01202_gb300 import SLOT_ACTIVE, SLOT_FAILED, serve
@@ -131,13 +130,22 @@ def test_a_request_that_cannot_fit_fails_alone():
     assert out["slabs"] == 3
 
 
-def test_a_request_larger_than_the_batch_is_refused():
-    tr = [_request(0, nx=10, ppc_i=2, nsteps=10)]
-    fe = serve.footprint(tr[0].cfg, tr[0].pulse)[0]
-    fb = FakeBatch(cap_e=fe - 1, cap_i=10**6, max_slabs=2, growth={})
-    with pytest.raises(ValueError, match="never fit"):
-        serve.serve_batched(tr, None, lambda r: None, max_slabs=2, slot_cells=16, cap_e=fe - 1,
-                            cap_i=10**6, batch=fb)
+def test_a_request_larger_than_the_batch_is_refused_alone():
+    """A request whose footprint is beyond the capacity, or which is wider
+    than a slot, is refused on arrival; the others are served."""
+    small = [_request(k, nx=10, ppc_i=2, nsteps=10) for k in (0, 2)]
+    fe = serve.footprint(small[0].cfg, small[0].pulse)[0]
+    big = _request(1, nx=12, ppc_i=40, nsteps=10)
+    wide = _request(3, nx=20, ppc_i=2, nsteps=10)
+    assert serve.footprint(big.cfg, big.pulse)[0] > 2 * fe
+    tr = [small[0], big, small[1], wide]
+    fb = FakeBatch(cap_e=2 * fe, cap_i=10**6, max_slabs=2, growth={})
+    out = serve.serve_batched(tr, None, lambda r: None, max_slabs=2, slot_cells=16, cap_e=2 * fe,
+                              cap_i=10**6, tick_steps=5, batch=fb)
+    assert sorted(out["results"]) == [0, 2]
+    assert sorted(out["failed"]) == [1, 3]
+    assert "capacity" in out["failed"][1] and "slot" in out["failed"][3]
+    assert [e[1] for e in fb.log if e[0] == "admit"] == [100, 102]
 
 
 def test_the_reservation_grows_up_to_what_the_capacity_holds():
