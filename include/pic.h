@@ -237,7 +237,13 @@ typedef struct {
 pic_status pic_seed(pic_ctx *c, const pic_seed_spec *s);
 
 /* Load particles from host memory (absolute positions in cell units).
- * u is [n][3]; ids must be unique per species.  Replaces any particles. */
+ * u is [n][3]; ids must be unique per species.  Replaces any particles.
+ * Ions: Z 0..13, nK (K vacancies against the lowest configuration of the
+ * 13 - Z bound electrons) 0..min(2, 13 - Z), zfrac (charge carried toward
+ * Z + 1 by partial photoionization) in [0, 1).  The arrays are read during
+ * the call only.  PIC_ERR_ARG for a position outside the slab or an ion
+ * state out of range; PIC_ERR_CAPACITY for more particles than the
+ * capacity; PIC_ERR_STATE on a batch context (which loads at admission). */
 pic_status pic_load_electrons(pic_ctx *c, int64_t n, const double *X, const double *Y,
                               const float *u, const float *w, const uint64_t *id);
 pic_status pic_load_ions(pic_ctx *c, int64_t n, const double *X, const double *Y,

@@ -904,7 +904,11 @@ pic_status build_records(pic_ctx *c, int slot, const pic_grid *g, bool electrons
             if (electrons) {
                 p1[k] = rec_e1(u[3 * k + 2], w_or_zf[k], eid[k]);
             } else {
-                if (Z[k] < 0 || Z[k] > ZNUC || nK[k] < 0 || nK[k] > 2) return 2;
+                // charge 0..13, K vacancies at most the K electrons of the
+                // lowest configuration of the bound electrons, fraction in [0, 1)
+                if (Z[k] < 0 || Z[k] > ZNUC || nK[k] < 0 || nK[k] > std::min(2, ZNUC - Z[k]) ||
+                    !(w_or_zf[k] >= 0.0f && w_or_zf[k] < 1.0f))
+                    return 2;
                 int stv = Z[k] | (nK[k] << 8);
                 p1[k] = rec_i1(u[3 * k + 2], w_or_zf[k], iid[k], stv);
             }
