@@ -266,8 +266,10 @@ pic_status pic_set_fields(pic_ctx *c, const float *f6);
  * synchronizes).  pic_restore loads an image into a context created with
  * the same grid, species, tables and pulse (and pic_rt setting), replacing
  * its particles and state; PIC_ERR_ARG for an image of another slab, build
- * or setting, or a truncated one; PIC_ERR_CAPACITY when its particles do
- * not fit.  Launch-shape tuning and step graphs are not part of the image
+ * or setting, a truncated one, or one whose cell starts or records are out
+ * of range (offsets in the cell outside [0, 1), ion states beyond the
+ * loaders' rules): a damaged image is refused, never read out of bounds on
+ * the device; PIC_ERR_CAPACITY when its particles do not fit.  Launch-shape tuning and step graphs are not part of the image
  * (they change no result). */
 size_t pic_checkpoint_bytes(pic_ctx *c);
 pic_status pic_checkpoint(pic_ctx *c, void *host, size_t bytes);

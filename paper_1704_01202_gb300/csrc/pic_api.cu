@@ -2137,6 +2137,18 @@ pic_status pic_restore(pic_ctx *c, const void *host, size_t bytes)
     take(cse.data(), sizeof(int) * cse.size()); take(csi.data(), sizeof(int) * csi.size());
     if (cse[0] != 0 || csi[0] != 0 || cse[c->ncell] != ne || csi[c->ncell] != ni)
         return fail(c, PIC_ERR_ARG, "checkpoint cell starts inconsistent");
+    // the records index the device's atomic tables and current stencils: a
+    // damaged image is refused (the loaders' rules) rather than read out of
+    // bounds on the device
+    auto in_cell = [](const real4 &q) { return q.x >= (real)0 && q.x < (real)1 && q.y >= (real)0 && q.y < (real)1; };
+    for (int64_t k = 0; k < ne; ++k)
+        if (!in_cell(e0[k])) return fail(c, PIC_ERR_ARG, "checkpoint electron record out of range");
+    for (int64_t k = 0; k < ni; ++k) {
+        const unsigned st = (unsigned)rec_ist(i1[k]), Z = st & 0xffu, nK = st >> 8;
+        if (!in_cell(i0[k]) || Z > (unsigned)ZNUC || nK > (unsigned)std::min(2, ZNUC - (int)Z) ||
+            !(i1[k].y >= (real)0 && i1[k].y < (real)1))
+            return fail(c, PIC_ERR_ARG, "checkpoint ion record out of range");
+    }
     std::vector<int> ke(ne), ki(ni);
     for (int g2 = 0; g2 < c->ncell; ++g2) {
         if (cse[g2 + 1] < cse[g2] || csi[g2 + 1] < csi[g2]) return fail(c, PIC_ERR_ARG, "checkpoint cell starts inconsistent");
