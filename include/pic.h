@@ -77,7 +77,8 @@ enum { PIC_IPD_NONE = 0, PIC_IPD_EK = 1, PIC_IPD_SP = 2 };
 
 /* Grid of one slab (Sec. VI: PIC grid, dt_PIC, dt_rad = rad_every dt_PIC).
  * ny == 1 is a 1D slab.  y is periodic; x boundaries absorb particles and
- * fields (first-order Mur). */
+ * fields (first-order Mur).  Valid: 2 <= nx <= 8192, ny >= 1, nx ny <= 2^30,
+ * dx, dy, dt and cfl positive and finite. */
 typedef struct {
     int nx, ny;
     double dx_nm, dy_nm;
@@ -88,7 +89,9 @@ typedef struct {
                              * min(c, cfl / (dt sqrt(1/dx^2 + [ny>1]/dy^2))) */
 } pic_grid;
 
-/* Species and model switches of one slab.  Ions share one weight. */
+/* Species and model switches of one slab.  Ions share one weight.  Valid:
+ * n_ref, w_ion and m_ion positive and finite, coulomb_log finite, E_bulk
+ * not NaN, ipd_model a PIC_IPD_* value. */
 typedef struct {
     double n_ref_cm3;       /* density unit of the weights */
     double w_ion;           /* common ion weight */
@@ -121,7 +124,9 @@ typedef struct {
 } pic_tables;
 
 /* XFEL pulse entering at x = 0 (Sec. VI): Gaussian (FWHM) or flat-top
- * intensity, n_bins photon-energy bins across the bandwidth. */
+ * intensity, n_bins photon-energy bins across the bandwidth.  Valid: shape
+ * 0 or 1, hv > 0, I_peak, fwhm and bandwidth >= 0, all finite (spot_sigma
+ * not NaN). */
 typedef struct {
     int shape;              /* 0 Gaussian, 1 flat-top */
     double I_peak_Wcm2, fwhm_fs, t_peak_fs, hv_eV, bandwidth_eV;

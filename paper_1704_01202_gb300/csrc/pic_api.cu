@@ -654,8 +654,10 @@ pic_status read_device_error(pic_ctx *c)
 
 bool valid_grid(const pic_grid *g)
 {
-    return g && g->nx >= 2 && g->ny >= 1 && g->nx <= 8192 && g->dx_nm > 0 && g->dy_nm > 0 && g->dt_fs > 0 &&
-           g->cfl > 0 && (long long)g->nx * g->ny <= (1LL << 30);
+    using std::isfinite;
+    return g && g->nx >= 2 && g->ny >= 1 && g->nx <= 8192 && g->dx_nm > 0 && isfinite(g->dx_nm) &&
+           g->dy_nm > 0 && isfinite(g->dy_nm) && g->dt_fs > 0 && isfinite(g->dt_fs) && g->cfl > 0 &&
+           isfinite(g->cfl) && (long long)g->nx * g->ny <= (1LL << 30);
 }
 
 // Particle capacities: the electrons a step creates (at most three per ion:
@@ -665,13 +667,19 @@ bool caps_fit(long long ce, long long ci) { return ce > 0 && ci > 0 && ce + 3 * 
 
 bool valid_species(const pic_species *s)
 {
-    return s && s->w_ion > 0 && s->m_ion_me > 0 && s->n_ref_cm3 > 0 && s->ipd_model >= 0 && s->ipd_model <= 2;
+    using std::isfinite;
+    return s && s->w_ion > 0 && isfinite(s->w_ion) && s->m_ion_me > 0 && isfinite(s->m_ion_me) &&
+           s->n_ref_cm3 > 0 && isfinite(s->n_ref_cm3) && s->ipd_model >= 0 && s->ipd_model <= 2 &&
+           !std::isnan(s->E_bulk_eV) && isfinite(s->coulomb_log);
 }
 
 bool valid_pulse(const pic_pulse *p)
 {
-    return p && p->n_bins >= 1 && p->n_bins <= PIC_MAX_BINS && p->hv_eV > 0 && p->fwhm_fs >= 0 &&
-           p->bandwidth_eV >= 0;
+    using std::isfinite;
+    return p && (p->shape == 0 || p->shape == 1) && p->n_bins >= 1 && p->n_bins <= PIC_MAX_BINS &&
+           p->hv_eV > 0 && isfinite(p->hv_eV) && p->fwhm_fs >= 0 && isfinite(p->fwhm_fs) &&
+           p->bandwidth_eV >= 0 && isfinite(p->bandwidth_eV) && p->I_peak_Wcm2 >= 0 &&
+           isfinite(p->I_peak_Wcm2) && isfinite(p->t_peak_fs) && !std::isnan(p->spot_sigma_nm);
 }
 
 // description of the slab of slot k, inactive until it is switched on

@@ -239,3 +239,30 @@ def test_bench_capacity_of_the_large_slab():
     ce, ci = bench.capacity(cfg, n_e, n_i)
     assert ce == int(9.5 * n_i) + 1024 and ci == n_i + 1024     # room for a mean charge of 9.5
     pkg.check_capacity(ce, ci)
+
+
+def test_non_finite_inputs_are_refused(build):
+    """Cell sizes, steps and Courant numbers must be finite, and so must the
+    species' weights, masses, densities and Coulomb logarithm: pic_init
+    refuses before anything reaches the device."""
+    L, _ = build
+    cfg = P.cfg_small_1d()
+    tabs = Tables()
+    ctx = C.c_void_p()
+    for field in ("dx_nm", "dy_nm", "dt_fs", "cfl"):
+        for v in (float("inf"), float("nan")):
+            g = _grid(cfg)
+            setattr(g, field, v)
+            assert _req_g(L, g, cfg) == 0, (field, v)
+            assert L.pic_init(C.byref(ctx), C.byref(g), C.byref(_species(cfg, 4096, 1024)), C.byref(tabs),
+                              None, 0, None) == PIC_ERR_ARG, (field, v)
+    for field in ("w_ion", "m_ion_me", "n_ref_cm3", "coulomb_log", "E_bulk_eV"):
+        s = _species(cfg, 4096, 1024)
+        setattr(s, field, float("nan"))
+        assert L.pic_init(C.byref(ctx), C.byref(_grid(cfg)), C.byref(s), C.byref(tabs), None, 0,
+                          None) == PIC_ERR_ARG, field
+
+
+def _req_g(L, g, cfg):
+    s = _species(cfg)
+    return L.pic_required_bytes(C.byref(g), C.byref(s), 1024, 256)
