@@ -231,9 +231,9 @@ pic_status pic_rt_cells(pic_ctx *c, double *chi, double *emc, double *w, double 
 typedef struct {
     int ppc_e, ppc_i;       /* macro-electrons and macro-ions per cell (>= 1) */
     int Z_init;             /* initial ion charge, 0 .. 12 */
-    double T_e_eV, T_i_eV;  /* Maxwellian temperatures (>= 0) */
+    double T_e_eV, T_i_eV;  /* Maxwellian temperatures (>= 0, finite) */
     double beam_frac;       /* share of electrons in the beam, 0 .. 1 */
-    double beam_E_eV;       /* beam kinetic energy (>= 0) */
+    double beam_E_eV;       /* beam kinetic energy (>= 0, finite) */
     uint64_t seed;          /* key of the seeding streams */
 } pic_seed_spec;
 

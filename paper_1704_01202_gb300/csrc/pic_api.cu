@@ -1482,8 +1482,9 @@ pic_status pic_seed(pic_ctx *c, const pic_seed_spec *sp)
 {
     if (!c || !sp) return PIC_ERR_ARG;
     if (c->batch) return fail(c, PIC_ERR_STATE, "a batch context loads particles at admission");
-    if (sp->ppc_e < 1 || sp->ppc_i < 1 || sp->Z_init < 0 || sp->Z_init > 12 || !(sp->T_e_eV >= 0) ||
-        !(sp->T_i_eV >= 0) || !(sp->beam_frac >= 0 && sp->beam_frac <= 1) || !(sp->beam_E_eV >= 0))
+    if (sp->ppc_e < 1 || sp->ppc_i < 1 || sp->Z_init < 0 || sp->Z_init > 12 ||
+        !(sp->T_e_eV >= 0 && std::isfinite(sp->T_e_eV)) || !(sp->T_i_eV >= 0 && std::isfinite(sp->T_i_eV)) ||
+        !(sp->beam_frac >= 0 && sp->beam_frac <= 1) || !(sp->beam_E_eV >= 0 && std::isfinite(sp->beam_E_eV)))
         return fail(c, PIC_ERR_ARG, "seed spec out of range");
     const SlabDev &S = c->slabs[0];
     const long long ne = (long long)S.ncell * sp->ppc_e, ni = (long long)S.ncell * sp->ppc_i;
