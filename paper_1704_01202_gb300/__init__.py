@@ -474,12 +474,21 @@ class Slab:
         return finish()
 
 
+def _same_length(kind, n, *arrays, u):
+    """The library reads n of each: refuse arrays of another length (or a
+    momentum array that is not n x 3) instead of reading past them."""
+    if any(x.ndim != 1 or x.size != n for x in arrays) or u.shape != (n, 3):
+        raise PicError(f"{kind} arrays of different lengths: {[x.shape for x in arrays]} and u {u.shape} "
+                       f"for {n} particles")
+
+
 def _electron_args(st):
     """Contiguous copies of a particle state's electrons and the (n, X, Y, u,
     w, id) arguments pointing into them (keep the copies alive for the call)."""
     a = [np.ascontiguousarray(st.eX, dtype=np.float64), np.ascontiguousarray(st.eY, dtype=np.float64),
          np.ascontiguousarray(st.eu, dtype=np.float32), np.ascontiguousarray(st.ew, dtype=np.float32),
          np.ascontiguousarray(st.eid, dtype=np.uint64)]
+    _same_length("electron", a[0].size, a[1], a[3], a[4], u=a[2])
     return a, (a[0].size, _p(a[0]), _p(a[1]), _p(a[2], C.c_float), _p(a[3], C.c_float), _p(a[4], C.c_uint64))
 
 
@@ -488,6 +497,7 @@ def _ion_args(st):
          np.ascontiguousarray(st.iu, dtype=np.float32), np.ascontiguousarray(st.izf, dtype=np.float32),
          np.ascontiguousarray(st.iZ, dtype=np.int32), np.ascontiguousarray(st.inK, dtype=np.int32),
          np.ascontiguousarray(st.iid, dtype=np.uint32)]
+    _same_length("ion", a[0].size, a[1], a[3], a[4], a[5], a[6], u=a[2])
     return a, (a[0].size, _p(a[0]), _p(a[1]), _p(a[2], C.c_float), _p(a[3], C.c_float), _p(a[4], C.c_int32),
             _p(a[5], C.c_int32), _p(a[6], C.c_uint32))
 

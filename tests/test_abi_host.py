@@ -266,3 +266,26 @@ def test_non_finite_inputs_are_refused(build):
 def _req_g(L, g, cfg):
     s = _species(cfg)
     return L.pic_required_bytes(C.byref(g), C.byref(s), 1024, 256)
+
+
+def test_particle_arrays_of_unequal_length_are_refused():
+    """The binding passes one count for all of a species' arrays: arrays of
+    another length are refused before the library could read past them."""
+    cfg = P.cfg_small_1d(nx=4, ppc_e=4, ppc_i=1)
+    st = P.init_particles(cfg)
+    pkg._electron_args(st)
+    pkg._ion_args(st)
+    for field, cut in (("eY", slice(0, -1)), ("ew", slice(0, -1)), ("eid", slice(0, -1)), ("eu", slice(0, -1))):
+        bad = P.init_particles(cfg)
+        setattr(bad, field, getattr(bad, field)[cut])
+        with pytest.raises(pkg.PicError, match="lengths"):
+            pkg._electron_args(bad)
+    bad = P.init_particles(cfg)
+    bad.eu = bad.eu[:, :2]
+    with pytest.raises(pkg.PicError, match="lengths"):
+        pkg._electron_args(bad)
+    for field in ("iY", "izf", "iZ", "inK", "iid", "iu"):
+        bad = P.init_particles(cfg)
+        setattr(bad, field, getattr(bad, field)[:-1])
+        with pytest.raises(pkg.PicError, match="lengths"):
+            pkg._ion_args(bad)
