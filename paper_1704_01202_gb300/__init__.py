@@ -353,6 +353,9 @@ class Slab:
         F = np.ascontiguousarray(F, dtype=np.float64)
         Gx = np.zeros_like(F) if Gx is None else np.ascontiguousarray(Gx, dtype=np.float64)
         Gy = np.zeros_like(F) if Gy is None else np.ascontiguousarray(Gy, dtype=np.float64)
+        n = self.nord * self.n_bins * self.nry * self.nrx
+        for name, x in (("F", F), ("Gx", Gx), ("Gy", Gy)):
+            _expect_size(x, n, f"rad field {name}")
         self._check(self.L.pic_rt_set(self.h, _p(F), _p(Gx), _p(Gy)), "pic_rt_set")
 
     def rt_cells(self):
@@ -447,6 +450,7 @@ class Slab:
 
     def set_photons(self, ph):
         a = np.ascontiguousarray(ph, dtype=np.float64)
+        _expect_size(a, self.cfg.ny * self.cfg.nx * self.n_bins, "photon numbers")
         self._check(self.L.pic_set_photons(self.h, _p(a)), "pic_set_photons")
 
     def photons(self):
@@ -456,6 +460,7 @@ class Slab:
 
     def set_fields(self, f: dict):
         a = np.ascontiguousarray(np.stack([f[k] for k in ("ex", "ey", "ez", "bx", "by", "bz")]), dtype=np.float32)
+        _expect_size(a, 6 * self.cfg.ny * (self.cfg.nx + 1), "fields")
         self._check(self.L.pic_set_fields(self.h, _p(a, C.c_float)), "pic_set_fields")
 
     def fields(self):
@@ -472,6 +477,12 @@ class Slab:
         d, finish = _diag_out(n_E, E_max)
         self._check(self.L.pic_diagnostics(self.h, C.byref(d)), "pic_diagnostics")
         return finish()
+
+
+def _expect_size(a, n, what):
+    """The library reads n values: refuse an array of another size."""
+    if a.size != n:
+        raise PicError(f"{what}: {a.size} values where the slab has {n}")
 
 
 def _same_length(kind, n, *arrays, u):

@@ -289,3 +289,26 @@ def test_particle_arrays_of_unequal_length_are_refused():
         setattr(bad, field, getattr(bad, field)[:-1])
         with pytest.raises(pkg.PicError, match="lengths"):
             pkg._ion_args(bad)
+
+
+def test_setters_refuse_arrays_of_another_size():
+    """Photon numbers, fields and the rad field are read by count: a wrong
+    size is refused in the binding, before the library is called (the slab
+    here has no context at all)."""
+    cfg = P.cfg_small_1d(nx=8)
+    s = object.__new__(pkg.Slab)
+    s.cfg, s.n_bins, s.L, s.h = cfg, 2, None, None
+    s.nord, s.nry, s.nrx = 3, 1, 4
+    with pytest.raises(pkg.PicError, match="photon numbers"):
+        s.set_photons(np.zeros((cfg.ny, cfg.nx, 3)))
+    f = P.random_fields(cfg, 1)
+    f["ez"] = f["ez"][:, :-1]
+    with pytest.raises((pkg.PicError, ValueError)):
+        s.set_fields(f)
+    f = {k: np.zeros((cfg.ny, cfg.nx)) for k in ("ex", "ey", "ez", "bx", "by", "bz")}
+    with pytest.raises(pkg.PicError, match="fields"):
+        s.set_fields(f)
+    with pytest.raises(pkg.PicError, match="rad field F"):
+        s.set_rt_field(np.zeros((3, 2, 1, 5)))
+    with pytest.raises(pkg.PicError, match="rad field Gy"):
+        s.set_rt_field(np.zeros((3, 2, 1, 4)), np.zeros((3, 2, 1, 4)), np.zeros(3))
