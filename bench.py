@@ -54,6 +54,11 @@ STEP_BYTES_PER_PARTICLE = 132
 # particle over the five-step cycle), scaled to a launch by the particle
 # count; None when no capture of the current kernel exists
 CELL_TRAFFIC_BYTES_PER_PARTICLE = 64.0
+# warp instructions per particle of the cell kernel, from the same capture
+# (104 on a radiation step, 89 on the others: 92 over the five-step cycle);
+# the kernel is bound by instruction issue, so the bench also sets its
+# time against the SM issue rate
+CELL_WARP_INSTR_PER_PARTICLE = 92.0
 
 
 def measured_peaks():
@@ -189,6 +194,19 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def issue_rate(cell_ms, n_particles, n_sm, sm_mhz):
+    """The cell kernel against the SM issue rate: warp instructions per
+    particle x particles over its time, against four schedulers per SM
+    issuing one warp instruction a cycle at the SM clock sampled during the
+    timed steps (the maximum clock when no sample exists)."""
+    mhz = sm_mhz if sm_mhz else 2070.0
+    peak = 4.0 * n_sm * mhz * 1e6
+    achieved = CELL_WARP_INSTR_PER_PARTICLE * n_particles / (cell_ms * 1e-3)
+    return {"achieved": achieved, "peak": peak, "unit": "warp instructions/s", "frac": achieved / peak,
+            "warp_instructions_per_particle": CELL_WARP_INSTR_PER_PARTICLE, "sm": n_sm, "sm_mhz": mhz,
+            "source": "instructions per particle from ncu (profiles/)"}
+
+
 def capacity(cfg, n_e, n_i):
     """Particle capacity of the timed slab: electrons for a mean charge up to
     9.5 on the large slab (the precision study's figure), for full
@@ -317,6 +335,7 @@ def run_gpu(args):
 
     # dominant kernel roofline: the per-cell kernel
     peak, peak_kind = measured_peaks()
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     cell_ms = tms["cell"] / max(nrec, 1)
     achieved = CELL_BYTES_PER_PARTICLE * n_mean / (cell_ms * 1e-3) / 1e9
     traffic = CELL_TRAFFIC_BYTES_PER_PARTICLE * n_mean if CELL_TRAFFIC_BYTES_PER_PARTICLE else None
@@ -325,7 +344,8 @@ def run_gpu(args):
                                                 "scaled by particles (profiles/)",
             "kernel": "k_cell", "peak_source": peak_kind,
             "bytes_per_particle": CELL_BYTES_PER_PARTICLE, "kernel_ms_per_step": cell_ms,
-            "share_of_step": tms["cell"] / max(tms["step"], 1e-9)}
+            "share_of_step": tms["cell"] / max(tms["step"], 1e-9),
+            "issue": issue_rate(cell_ms, n_mean, n_sm, clk.get("sm_mhz"))}
     step_gbs = STEP_BYTES_PER_PARTICLE * n_mean / (ms / args.steps * 1e-3) / 1e9
 
     # end to end through the public API with host buffers

@@ -75,3 +75,13 @@ def test_clock_samples(bench):
 def test_single_rank_aggregate(bench):
     ms, value = bench.aggregate(250.0, 1.0e9 * 20)
     assert ms == 250.0 and value == pytest.approx(1.0e9 * 20 / 0.25)
+
+
+def test_issue_rate(bench):
+    """The cell kernel against the SM issue rate: 92 warp instructions per
+    particle; four schedulers per SM, one warp instruction a cycle."""
+    r = bench.issue_rate(100.0, 1.0e9, 152, 2000.0)
+    assert r["peak"] == pytest.approx(4 * 152 * 2.0e9)
+    assert r["achieved"] == pytest.approx(92.0 * 1.0e9 / 0.1)
+    assert r["frac"] == pytest.approx(92.0e10 / (4 * 152 * 2.0e9))
+    assert bench.issue_rate(100.0, 1.0e9, 152, None)["sm_mhz"] == 2070.0
