@@ -197,7 +197,8 @@ pic_status pic_source(pic_ctx *c, const pic_pulse *p);
  * cos(theta) times n_azimuth azimuths in (0, pi) (2D; the lower hemisphere
  * is the mirror image).  Single-slab contexts only, after pic_source; nx
  * (and ny in 2D) multiples of coarsen, at most 4096 rad cells along each
- * axis, n_polar 0..16, n_azimuth 1..16.  The context allocates the field
+ * axis, n_polar 0..16, n_azimuth 1..16, c dt_rad at most 61 rad cells
+ * (the beam's inflow ghost nodes).  The context allocates the field
  * (cudaMalloc) and frees it in pic_free.  PIC_ERR_STATE without a pulse,
  * on a batch context or when already on; PIC_ERR_ARG for invalid sizes. */
 typedef struct {

@@ -1880,6 +1880,14 @@ pic_status pic_rt(pic_ctx *c, const pic_rt_config *rt)
         rt->n_polar > 16 || (d2 && (rt->n_azimuth < 1 || rt->n_azimuth > 16)) || (rt->scheme != 0 && rt->scheme != 1))
         return fail(c, PIC_ERR_ARG, "invalid radiation transport setting");
     if (c->rt_mem) return fail(c, PIC_ERR_STATE, "radiation transport already on");
+    // the beam enters through ghost nodes: c dt_rad may span at most the
+    // RT_GHOST - 3 rad cells they hold along any axis
+    {
+        const double dtr = (double)S.rad_every * (double)S.dt;
+        const double dmin = (d2 ? std::min((double)S.dx, (double)S.dy) : (double)S.dx) * R;
+        if (!(kCnmPerFs * dtr <= (RT_GHOST - 3) * dmin))
+            return fail(c, PIC_ERR_ARG, "radiation transport: c dt_rad spans more rad cells than the inflow holds");
+    }
     const int nb = S.nb, nrx = S.nx / R, nry = d2 ? S.ny / R : 1, nrc = nrx * nry;
     const int naz = d2 ? rt->n_azimuth : 1, nord = 1 + rt->n_polar * naz;
     // ordinates: the beam along +x, then Gauss-Legendre nodes of mu =
