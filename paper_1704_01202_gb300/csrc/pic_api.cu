@@ -43,10 +43,11 @@ constexpr int BIG_CE = sizeof(real) == 8 ? 1024 : 2048, BIG_CI = sizeof(real) ==
 
 size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// smallest power of two >= x, from 32, at most 2^30 (no signed overflow)
 int next_pow2(int x)
 {
     int p = 32;
-    while (p < x) p <<= 1;
+    while (p < x && p < (1 << 30)) p <<= 1;
     return p;
 }
 
@@ -338,7 +339,9 @@ int round_cap(int v, int q, int lo, int hi) { return std::min(hi, std::max(lo, (
 // that stay resident.
 pic_status configure_cell_launch(pic_ctx *c, const int *hist_e, const int *hist_i, int max_e, int max_i)
 {
-    const int want_e = (int)(max_e * 1.25) + 1, want_i = (int)(max_i * 1.25) + 1;
+    // the largest cells x 1.25, kept well inside int (the tiers stop at 2048)
+    const int want_e = (int)std::min(max_e * 1.25 + 1.0, (double)(1 << 30));
+    const int want_i = (int)std::min(max_i * 1.25 + 1.0, (double)(1 << 30));
     int ce = std::min(cap_for_share(hist_e, 0.75, 64), 1024);
     int ci = std::min(cap_for_share(hist_i, 0.75, 32), 256);
     ce = std::min(ce, std::min(next_pow2(std::max(64, want_e)), 1024));
