@@ -77,7 +77,7 @@ enum { PIC_IPD_NONE = 0, PIC_IPD_EK = 1, PIC_IPD_SP = 2 };
 
 /* Grid of one slab (Sec. VI: PIC grid, dt_PIC, dt_rad = rad_every dt_PIC).
  * ny == 1 is a 1D slab.  y is periodic; x boundaries absorb particles and
- * fields (first-order Mur).  Valid: 2 <= nx <= 8192, ny >= 1, nx ny <= 2^30,
+ * fields (first-order Mur).  Valid: 2 <= nx <= 8192, ny >= 1, (nx + 1) ny <= 2^27,
  * dx, dy, dt and cfl positive and finite. */
 typedef struct {
     int nx, ny;

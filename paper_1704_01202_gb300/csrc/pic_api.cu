@@ -43,6 +43,11 @@ constexpr int BIG_CE = sizeof(real) == 8 ? 1024 : 2048, BIG_CI = sizeof(real) ==
 
 size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Most cells (and grid points) of a context: 2^27, sixteen times the large
+// 2D slab, so that cell counts times photon bins (8) or field components
+// stay inside 32-bit int indices on the device.
+constexpr long long kMaxCells = 1LL << 27;
+
 // smallest power of two >= x, from 32, at most 2^30 (no signed overflow)
 int next_pow2(int x)
 {
@@ -660,7 +665,7 @@ bool valid_grid(const pic_grid *g)
     using std::isfinite;
     return g && g->nx >= 2 && g->ny >= 1 && g->nx <= 8192 && g->dx_nm > 0 && isfinite(g->dx_nm) &&
            g->dy_nm > 0 && isfinite(g->dy_nm) && g->dt_fs > 0 && isfinite(g->dt_fs) && g->cfl > 0 &&
-           isfinite(g->cfl) && (long long)g->nx * g->ny <= (1LL << 30);
+           isfinite(g->cfl) && (long long)(g->nx + 1) * g->ny <= kMaxCells;
 }
 
 // Particle capacities: the electrons a step creates (at most three per ion:
@@ -763,7 +768,7 @@ pic_status ctx_create(pic_ctx **out, int nslot, int slot_cells, int slot_pts, in
     if (t->n_hv < 2 || !t->hv_tab || !t->sigma_photo || t->n_T < 1 || t->n_n < 1 || t->n_T > EOS_MAX_T ||
         t->n_n > EOS_MAX_N || !t->eos_T || !t->eos_n || !t->eos_Zbar)
         return PIC_ERR_TABLE;
-    if ((long long)nslot * slot_cells > (1LL << 30) || (long long)nslot * slot_pts > (1LL << 30)) return PIC_ERR_ARG;
+    if ((long long)nslot * slot_cells > kMaxCells || (long long)nslot * slot_pts > kMaxCells) return PIC_ERR_ARG;
     pic_ctx *c = new pic_ctx();
     c->stream = (cudaStream_t)stream;
     c->nslot = nslot;
@@ -1667,7 +1672,7 @@ size_t pic_batch_required_bytes(int max_slabs, int slot_cells, int cap_e, int ca
 {
     if (max_slabs < 1 || slot_cells < 2 || slot_cells > 8192 || !caps_fit(cap_e, cap_i)) return 0;
     long long ncell = (long long)max_slabs * slot_cells, npts = (long long)max_slabs * (slot_cells + 1);
-    if (npts > (1LL << 30)) return 0;
+    if (npts > kMaxCells) return 0;
     int nblk = (int)((ncell + SCAN_TILE - 1) / SCAN_TILE);
     return arena_need((int)ncell, (int)npts, nblk, cap_e, cap_i, max_slabs, max_slabs);
 }

@@ -70,10 +70,12 @@ def test_required_bytes_refuses_invalid_grids(build):
         setattr(g, field, value)
         assert L.pic_required_bytes(C.byref(g), C.byref(s), 1024, 256) == 0, field
     g = _grid(cfg)
-    g.nx, g.ny = 8192, (1 << 30) // 8192 + 1          # more than 2^30 cells
+    g.nx, g.ny = 8191, (1 << 27) // 8192 + 1          # more than 2^27 grid points
     assert L.pic_required_bytes(C.byref(g), C.byref(s), 1024, 256) == 0
-    g.ny = (1 << 30) // 8192
+    g.ny = (1 << 27) // 8192
     assert L.pic_required_bytes(C.byref(g), C.byref(s), 1024, 256) > 0
+    assert L.pic_batch_required_bytes((1 << 27) // 4097 + 1, 4096, 1024, 256) == 0
+    assert L.pic_batch_required_bytes((1 << 27) // 4097, 4096, 1024, 256) > 0
 
 
 def test_batch_required_bytes(build):
