@@ -261,10 +261,11 @@ def _small_slab_run(tables, key, checkpoints=False):
 
 def test_full_step_energy_drift_matches_oracle(tables):
     """With the push, the deposit and the fields on, the total energy of the
-    small 1D slab is not conserved by the explicit PIC step: it dips (field
-    energy radiated through the absorbing boundaries is not tallied) and
-    then rises through the residual numerical heating of cells ~50 Debye
-    lengths wide.  That drift belongs to the scheme, so the device's drift
+    small 1D slab is not conserved by the explicit PIC step: it dips while
+    the fields build up from the particles' noise and then rises through
+    the residual numerical heating of cells ~50 Debye lengths wide (the
+    field-particle coupling; the field energy leaving through the absorbing
+    boundaries is a small part of either).  That drift belongs to the scheme, so the device's drift
     curve (every 100 steps, eight Philox keys) must match the oracle's
     (eight keys from the same initial state, tests/golden/oracle_spread.json)
     mean for mean within Welch's bound, with a floor of 1e-5 of the initial
