@@ -85,3 +85,24 @@ def test_issue_rate(bench):
     assert r["achieved"] == pytest.approx(92.0 * 1.0e9 / 0.1)
     assert r["frac"] == pytest.approx(92.0e10 / (4 * 152 * 2.0e9))
     assert bench.issue_rate(100.0, 1.0e9, 152, None)["sm_mhz"] == 2070.0
+
+
+def test_profile_commands_use_existing_bench_options(bench):
+    """Every command under profiles/ that runs bench.py passes only options
+    the bench parses (the summaries give runnable commands)."""
+    import glob
+    import re
+    known = set(re.findall(r'add_argument\("(--[\w-]+)"', open(os.path.join(ROOT, "bench.py")).read()))
+    assert "--steps" in known and "--no-cpu" in known
+    seen = 0
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        text = open(path).read().replace("\\\n", " ")
+        for line in text.splitlines():
+            if "python bench.py" not in line:
+                continue
+            seen += 1
+            args = line.split("python bench.py", 1)[1].split()
+            for a in args:
+                if a.startswith("--"):
+                    assert a in known, (os.path.basename(path), a)
+    assert seen >= 4
